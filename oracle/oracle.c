@@ -1,0 +1,281 @@
+/*
+ * oracle.c -- TEST INFRASTRUCTURE ONLY: the reference computation that the CUDA
+ * path is checked against.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library; the product path never
+ * does.  It shares no code with the CUDA library.
+ *
+ * Everything is plain, sequential FP64 and follows the paper's statement:
+ *
+ *   D. Hong, "Optimized on-line computation of PageRank algorithm".
+ *   Section 2.1   : X = dPX + (1-d)V, P_ij = p(i,j) = probability of j -> i,
+ *                   so column j of P holds 1/outdeg(j) on each child of j.
+ *   Section 2.2   : fluid F_0 = (1-d)V, F_n = (I - J_in + dPJ_in) F_{n-1},
+ *                   history H_n = sum_k J_ik F_{k-1}, and ALGO-REF.
+ *   Section 3.3   : "About dangling nodes": a node with no child loses its
+ *                   fluid (R -= sent) and P is never completed.
+ *   Section 4     : the sequence choices ALGO-PER, ALGO-RAND, ALGO-MAX, the
+ *                   threshold sweeps that replace argmax, MAT-ITER and its
+ *                   stopping rule |X_n - X_{n-1}| d/(1-d) < Target.
+ *
+ * Readings of points the paper leaves open (threshold schedule, snapshot sweep,
+ * tie-breaks) are stated beside the code that takes them.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+typedef int32_t i32;
+typedef int64_t i64;
+typedef uint64_t u64;
+
+/* ------------------------------------------------------------- graph views */
+
+/* out-degree #out_i = number of listed out-links (multi-edges counted) */
+void orc_outdeg(i32 n, const i32 *row_ptr, i32 *outdeg) {
+    for (i32 i = 0; i < n; ++i) outdeg[i] = row_ptr[i + 1] - row_ptr[i];
+}
+
+/*
+ * In-link lists (the "collection" view of the introduction): in_ptr[n+1],
+ * in_src[L].  Row j lists every i with an edge i -> j, in ascending i
+ * (a counting sort that walks the out-lists in order).
+ */
+void orc_transpose(i32 n, const i32 *row_ptr, const i32 *col_idx, i32 *in_ptr, i32 *in_src) {
+    i64 L = row_ptr[n];
+    for (i32 j = 0; j <= n; ++j) in_ptr[j] = 0;
+    for (i64 e = 0; e < L; ++e) in_ptr[col_idx[e] + 1] += 1;
+    for (i32 j = 0; j < n; ++j) in_ptr[j + 1] += in_ptr[j];
+    i32 *fill = (i32 *)malloc(sizeof(i32) * (size_t)(n > 0 ? n : 1));
+    for (i32 j = 0; j < n; ++j) fill[j] = in_ptr[j];
+    for (i32 i = 0; i < n; ++i)
+        for (i32 e = row_ptr[i]; e < row_ptr[i + 1]; ++e) in_src[fill[col_idx[e]]++] = i;
+    free(fill);
+}
+
+/*
+ * Degree bins: node i belongs to bin b = the number of cut values c with
+ * outdeg_i > c (cuts ascending).  bin_ptr[nb+1] delimits, in bin_ids[n], each
+ * bin's node list in ascending id.
+ */
+void orc_bins(i32 n, const i32 *row_ptr, i32 ncut, const i32 *cuts, i32 *bin_of, i32 *bin_ptr, i32 *bin_ids) {
+    i32 nb = ncut + 1;
+    for (i32 b = 0; b <= nb; ++b) bin_ptr[b] = 0;
+    for (i32 i = 0; i < n; ++i) {
+        i32 deg = row_ptr[i + 1] - row_ptr[i], b = 0;
+        for (i32 c = 0; c < ncut; ++c) if (deg > cuts[c]) b = c + 1;
+        bin_of[i] = b;
+        bin_ptr[b + 1] += 1;
+    }
+    for (i32 b = 0; b < nb; ++b) bin_ptr[b + 1] += bin_ptr[b];
+    i32 pos[64];
+    for (i32 b = 0; b < nb && b < 64; ++b) pos[b] = bin_ptr[b];
+    for (i32 i = 0; i < n; ++i) bin_ids[pos[bin_of[i]]++] = i;
+}
+
+/* ------------------------------------------------------ random sequence I */
+
+/* SplitMix64 (Steele, Lea & Flood 2014), used here only for ALGO-RAND picks */
+static u64 orc_splitmix(u64 z) {
+    z += 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+/* ------------------------------------------------------------ D-iteration */
+
+enum { ORC_PER = 0, ORC_RAND = 1, ORC_MAX = 2, ORC_THRESH = 3, ORC_SWEEP = 4 };
+
+typedef struct {
+    double R;          /* the residual R of ALGO-REF at exit */
+    double l1F;        /* |F|_1 recomputed by a plain sum at exit */
+    i64 pushes;        /* diffusions that moved non-zero fluid */
+    i64 edges;         /* elementary steps: out-links used by those diffusions */
+    i64 picks;         /* entries of the sequence I drawn, zero-fluid ones included */
+    i64 sweeps;        /* threshold sweeps (THRESH / SWEEP orders) */
+    i32 converged;     /* 1 if R/(1-d) <= tol at exit */
+} orc_stats;
+
+/* Initialization of ALGO-REF: H = 0, F = (1-d)V, R = 1-d (V is normalized). */
+double orc_init(i32 n, double d, const double *V, double *F, double *H) {
+    for (i32 i = 0; i < n; ++i) { H[i] = 0.0; F[i] = (1.0 - d) * V[i]; }
+    return 1.0 - d;
+}
+
+/*
+ * One diffusion of node i (the loop body of ALGO-REF with the dangling-node
+ * condition of Section 3.3):
+ *   sent := F[i]; H[i] += sent; F[i] := 0;
+ *   no child:  R -= sent
+ *   otherwise: F[j] += sent * p(j,i) * d for every child j;  R -= sent*(1-d)
+ * p(j,i) = 1/outdeg(i) per listed out-link.
+ */
+static void diffuse(i32 i, const i32 *row_ptr, const i32 *col_idx, double d, double *F, double *H,
+                    double *R, orc_stats *st) {
+    double sent = F[i];
+    H[i] += sent;
+    F[i] = 0.0;
+    i32 beg = row_ptr[i], end = row_ptr[i + 1];
+    if (end == beg) {
+        *R -= sent;
+    } else {
+        double p = 1.0 / (double)(end - beg);
+        for (i32 e = beg; e < end; ++e) F[col_idx[e]] += sent * p * d;
+        *R -= sent * (1.0 - d);
+    }
+    st->pushes += 1;
+    st->edges += end - beg;
+}
+
+/*
+ * Run D-iteration on the state (F, H, R) until R/(1-d) <= tol or max_pushes
+ * diffusions have been made.  F and H are updated in place, so a second call
+ * resumes where the first stopped.  Orders of the sequence I (Section 4):
+ *
+ *   ORC_PER    i_n = n mod N.
+ *   ORC_RAND   i_n uniform on {0..N-1} (SplitMix64 of seed + n).
+ *   ORC_MAX    i_n = argmax F (lowest index on ties).
+ *   ORC_THRESH threshold sweeps: visit i = 0..N-1 and diffuse every i whose
+ *              current F_i > T (F_i read at its turn, Gauss-Seidel style).
+ *   ORC_SWEEP  threshold sweeps on a snapshot: S = {i : F_i > T} is fixed at
+ *              the start of the sweep, all of S hands its fluid to H, then all
+ *              of S pushes.  This is the diffusion of the set S at once,
+ *              F' = (I - J_S + dPJ_S)F, H' = H + J_S F with J_S = sum_{i in S} J_i,
+ *              for which Theorem 1 holds by the same induction.
+ *
+ * Threshold schedule (the paper only says the threshold is scaled down
+ * progressively): T = beta * R / N before each sweep; a sweep that diffuses
+ * nothing halves T for the next one.  With beta < 1 the largest entry
+ * (>= |F|/N) always qualifies, which is the condition under which the Lemma of
+ * Section 3.1 gives the contraction factor 1 - (1-d)/N.
+ *
+ * Zero-fluid picks of PER / RAND are skipped without counting (Section 4.2).
+ * The sequential orders test the stop rule after every diffusion, like the
+ * while-loop of ALGO-REF; ORC_SWEEP tests it between sweeps.
+ * Returns 0 if converged, 1 if max_pushes was reached first.
+ */
+int orc_diter(i32 n, const i32 *row_ptr, const i32 *col_idx, double d, double *F, double *H, double R,
+              double tol, int mode, double beta, u64 seed, i64 max_pushes, orc_stats *st) {
+    memset(st, 0, sizeof(*st));
+    i64 zero_run = 0;
+    double T = beta * R / (double)n;
+    i32 *S = NULL;
+    double *sent = NULL;
+    if (mode == ORC_SWEEP) {
+        S = (i32 *)malloc(sizeof(i32) * (size_t)n);
+        sent = (double *)malloc(sizeof(double) * (size_t)n);
+    }
+    while (R / (1.0 - d) > tol && st->pushes < max_pushes) {
+        if (mode == ORC_PER || mode == ORC_RAND) {
+            i32 i = (mode == ORC_PER) ? (i32)(st->picks % n)
+                                      : (i32)(orc_splitmix(seed + (u64)st->picks) % (u64)n);
+            st->picks += 1;
+            if (F[i] == 0.0) {
+                /* every entry zero: nothing is left to diffuse (R only drifted) */
+                if (++zero_run > 64 * (i64)n) break;
+                continue;
+            }
+            zero_run = 0;
+            diffuse(i, row_ptr, col_idx, d, F, H, &R, st);
+        } else if (mode == ORC_MAX) {
+            i32 best = 0;
+            for (i32 i = 1; i < n; ++i) if (F[i] > F[best]) best = i;
+            st->picks += 1;
+            if (F[best] == 0.0) break;
+            diffuse(best, row_ptr, col_idx, d, F, H, &R, st);
+        } else if (mode == ORC_THRESH) {
+            i64 before = st->pushes;
+            for (i32 i = 0; i < n; ++i) {
+                if (F[i] > T) {
+                    st->picks += 1;
+                    diffuse(i, row_ptr, col_idx, d, F, H, &R, st);
+                    if (R / (1.0 - d) <= tol || st->pushes >= max_pushes) break;
+                }
+            }
+            st->sweeps += 1;
+            if (st->pushes == before) {
+                if (T == 0.0) break;       /* F is identically zero */
+                T = T / 2.0;
+            } else {
+                T = beta * R / (double)n;
+            }
+        } else if (mode == ORC_SWEEP) {
+            i32 ns = 0;
+            for (i32 i = 0; i < n; ++i) if (F[i] > T) S[ns++] = i;
+            for (i32 k = 0; k < ns; ++k) {
+                i32 i = S[k];
+                sent[k] = F[i];
+                H[i] += sent[k];
+                F[i] = 0.0;
+            }
+            for (i32 k = 0; k < ns; ++k) {
+                i32 i = S[k];
+                i32 beg = row_ptr[i], end = row_ptr[i + 1];
+                if (end == beg) {
+                    R -= sent[k];
+                } else {
+                    double p = 1.0 / (double)(end - beg);
+                    for (i32 e = beg; e < end; ++e) F[col_idx[e]] += sent[k] * p * d;
+                    R -= sent[k] * (1.0 - d);
+                }
+                st->edges += end - beg;
+            }
+            st->pushes += ns;
+            st->picks += ns;
+            st->sweeps += 1;
+            if (ns == 0) {
+                if (T == 0.0) break;
+                T = T / 2.0;
+            } else {
+                T = beta * R / (double)n;
+            }
+        } else {
+            free(S); free(sent);
+            return -1;
+        }
+    }
+    free(S); free(sent);
+    double l1 = 0.0;
+    for (i32 i = 0; i < n; ++i) l1 += fabs(F[i]);
+    st->R = R;
+    st->l1F = l1;
+    st->converged = (R / (1.0 - d) <= tol) ? 1 : 0;
+    return st->converged ? 0 : 1;
+}
+
+/* ------------------------------------------------------ power iteration */
+
+/*
+ * MAT-ITER on the uncompleted P (Section 4, with the stop rule of Section 4):
+ *   X_0 = 0,  X_{n+1} = dPX_n + (1-d)V,
+ *   stop when |X_{n+1} - X_n|_1 * d/(1-d) < tol  or after max_iter products.
+ * From X_0 = 0 the iterate X_n equals the partial series S_{n-1} of
+ * Section 2.2.  Each product uses every listed out-link once (L elementary
+ * steps).  Returns 0 if the stop rule was met.
+ */
+int orc_power(i32 n, const i32 *row_ptr, const i32 *col_idx, double d, const double *V, double tol,
+              i64 max_iter, double *X, i64 *iters, double *last_delta) {
+    double *Y = (double *)malloc(sizeof(double) * (size_t)n);
+    for (i32 i = 0; i < n; ++i) X[i] = 0.0;
+    i64 it = 0;
+    double delta = INFINITY;
+    int ok = 0;
+    while (it < max_iter) {
+        for (i32 j = 0; j < n; ++j) Y[j] = (1.0 - d) * V[j];
+        for (i32 i = 0; i < n; ++i) {
+            i32 beg = row_ptr[i], end = row_ptr[i + 1];
+            if (end == beg) continue;
+            double p = 1.0 / (double)(end - beg);
+            for (i32 e = beg; e < end; ++e) Y[col_idx[e]] += d * p * X[i];
+        }
+        delta = 0.0;
+        for (i32 j = 0; j < n; ++j) { delta += fabs(Y[j] - X[j]); X[j] = Y[j]; }
+        ++it;
+        if (delta * d / (1.0 - d) < tol) { ok = 1; break; }
+    }
+    free(Y);
+    *iters = it;
+    *last_delta = delta;
+    return ok ? 0 : 1;
+}

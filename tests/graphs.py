@@ -1,0 +1,52 @@
+"""Small hand-made graphs (CSR of out-links) used by the tests."""
+import numpy as np
+
+
+def csr(n, edges):
+    """CSR from an edge list [(i, j), ...] in the given order (multi-edges kept)."""
+    rows = [[] for _ in range(n)]
+    for i, j in edges:
+        rows[i].append(j)
+    row_ptr = np.zeros(n + 1, dtype=np.int32)
+    for i in range(n):
+        row_ptr[i + 1] = row_ptr[i] + len(rows[i])
+    col_idx = np.array([j for r in rows for j in r], dtype=np.int32)
+    return row_ptr, col_idx
+
+
+def chain(n):
+    return csr(n, [(i, i + 1) for i in range(n - 1)])
+
+
+def cycle(n):
+    return csr(n, [(i, (i + 1) % n) for i in range(n)])
+
+
+def star(m):
+    """node 0 -> 1..m, leaves dangling"""
+    return csr(m + 1, [(0, k) for k in range(1, m + 1)])
+
+
+def complete(n):
+    return csr(n, [(i, j) for i in range(n) for j in range(n) if i != j])
+
+
+def random_graph(n, p_dangling, max_deg, rng, self_loops=True, multi=True):
+    edges = []
+    for i in range(n):
+        if rng.random() < p_dangling:
+            continue
+        k = int(rng.integers(1, max_deg + 1))
+        for _ in range(k):
+            j = int(rng.integers(0, n))
+            if not self_loops and j == i:
+                continue
+            edges.append((i, j))
+    if not multi:
+        edges = sorted(set(edges))
+    return csr(n, edges)
+
+
+def random_v(n, rng):
+    v = rng.random(n) + 0.05
+    return v / v.sum()

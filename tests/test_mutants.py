@@ -1,0 +1,78 @@
+"""Plant plausible mistakes in copies of the oracle and check the pins catch each.
+
+Each mutant is oracle.c with one textual change (a dropped term, a wrong sign,
+a transposed operand, a wrong degree), compiled with gcc into a temporary
+library.  A battery of the pins of test_oracle_pins.py must fail for every
+mutant and pass for the unmodified source.  Everything runs on the CPU.
+"""
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import ge
+from tests import graphs
+
+D = 0.85
+
+MUTANTS = {
+    "push_drops_d": ("F[col_idx[e]] += sent * p * d;", "F[col_idx[e]] += sent * p;"),
+    "dangling_keeps_mass": ("        *R -= sent;\n", "        *R -= sent * (1.0 - d);\n"),
+    "history_not_updated": ("    H[i] += sent;\n    F[i] = 0.0;", "    F[i] = 0.0;"),
+    "residual_wrong_factor": ("        *R -= sent * (1.0 - d);\n    }", "        *R -= sent * d;\n    }"),
+    "degree_off_by_one": ("double p = 1.0 / (double)(end - beg);", "double p = 1.0 / (double)(end - beg + 1);"),
+    "power_transposed": ("Y[col_idx[e]] += d * p * X[i];", "Y[i] += d * p * X[col_idx[e]];"),
+    "sweep_reads_after_push": ("                sent[k] = F[i];\n                H[i] += sent[k];\n                F[i] = 0.0;\n",
+                               "                sent[k] = F[i];\n                H[i] += sent[k];\n"),
+    "sweep_skips_dangling": ("                    R -= sent[k];\n", "                    R -= 0.0;\n"),
+    "init_wrong_scale": ("F[i] = (1.0 - d) * V[i];", "F[i] = V[i];"),
+    "transpose_order": ("in_src[fill[col_idx[e]]++] = i;", "in_src[fill[col_idx[e]]++] = col_idx[e];"),
+}
+
+
+def _battery(lib):
+    """True when every pin holds for the library `lib`."""
+    rng = np.random.default_rng(77)
+    n = 40
+    rp, ci = graphs.random_graph(n, 0.2, 6, rng)
+    V = graphs.random_v(n, rng)
+    X = ge.pagerank_dense(n, rp, ci, D, V)
+    P = ge.transition_matrix(n, rp, ci)
+    ok = True
+    for mode in ["per", "sweep", "thresh"]:
+        r = oracle.diter(n, rp, ci, D, V, 1e-10, mode=mode, max_pushes=200000, lib=lib)
+        ok &= bool(r.converged)
+        ok &= bool(np.abs(X - r.H).sum() <= r.l1F / (1 - D) + 1e-14)
+        ok &= bool(abs(r.R - r.l1F) < 1e-14)
+        r = oracle.diter(n, rp, ci, D, V, 0.0, mode=mode, max_pushes=30, lib=lib)
+        ok &= bool(np.abs(r.H + r.F - (1 - D) * V - D * P @ r.H).max() < 1e-15)
+    Xp, it, delta, conv = oracle.power(n, rp, ci, D, V, 1e-11, lib=lib)
+    ok &= bool(conv and np.abs(X - Xp).sum() <= 1e-11)
+    in_ptr, in_src = oracle.transpose(n, rp, ci, lib=lib)
+    want = [i for _j, i in sorted((int(j), i) for i in range(n) for j in ci[rp[i]:rp[i + 1]])]
+    ok &= in_src.tolist() == want
+    return ok
+
+
+def _compile(src_text, tmp_path, name):
+    src = tmp_path / f"{name}.c"
+    src.write_text(src_text)
+    out = tmp_path / f"lib{name}.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", str(out), str(src),
+                    "-lm"], check=True)
+    return oracle.load(str(out))
+
+
+def test_unmodified_oracle_passes_battery():
+    assert _battery(oracle.load())
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    text = open(os.path.join(os.path.dirname(oracle.__file__), "oracle.c")).read()
+    old, new = MUTANTS[name]
+    assert text.count(old) >= 1, f"mutation site for {name} not found"
+    lib = _compile(text.replace(old, new), tmp_path, name)
+    assert not _battery(lib), f"mutant {name} survived the pins"
