@@ -1,0 +1,360 @@
+#!/usr/bin/env python3
+"""Benchmark: D-iteration edge pushes/s to L1 residual 1e-8 on one GB300, vs the same GPU's power iteration.
+
+Workload (default): the Zipf graph at scale -- N = 2^24 nodes, exactly 12% dangling,
+other out-degrees Zipf(2.1) clipped to [1, 50000], targets drawn proportional to
+rank^-0.9 over permuted ids, int32 CSR, d = 0.85, V = 1/N, FP64, stop when the
+Theorem 2 bound |F|_1/(1-d) <= 1e-8.  Synthetic and seeded (graphgen, seed 1).
+
+One step = one full solve on the device-resident graph: initialization, threshold
+sweeps (scan/exchange, push, finalize) in one CUDA-graph while-loop, the exact
+|F|_1 confirmation and the copy of H to a device buffer.  value = edges pushed
+by all ranks / max over ranks of the device time of K steps.
+
+Besides the headline the JSON line reports: the power iteration (MAT-ITER, pull
+SpMV) to the paper's stop rule at the same tolerance on the same GPU; the
+per-kernel roofline of a profiled solve (same kernels, launched one by one with
+CUDA events around each); an end-to-end number through the C ABI with pinned
+host buffers (create from host CSR + solve + H to host, every step); SM clocks
+sampled during the timed region; and the oracle (sequential FP64 CPU snapshot
+sweeps) timed on a bounded sample on the host cores.
+
+--impl reference times the oracle alone, as it stands, on the host cores.
+Multi-GPU: replicas only (each rank solves its own copy; no collective on the
+data path), launched with torchrun; rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "edge pushes/s to L1 resid 1e-8 vs GPU power iter; PPR queries/s, p50/p99 ms"
+UNIT = "edge pushes/s"
+WORKLOADS = {
+    "zipf24": dict(kind="zipf", n=1 << 24, alpha=2.1, kmax=50000, dangling=0.12, target_exp=0.9, d=0.85, tol=1e-8,
+                   label="Zipf N=2^24, outdeg Zipf(2.1) clipped [1,50000] + 12% dangling, targets ~ rank^-0.9, "
+                         "d=0.85, V=1/N, FP64, L1 bound 1e-8"),
+    "zipf20": dict(kind="zipf", n=1 << 20, alpha=2.1, kmax=50000, dangling=0.12, target_exp=0.9, d=0.85, tol=1e-8,
+                   label="Zipf N=2^20 (reduced size for quick runs), d=0.85, V=1/N, FP64, L1 bound 1e-8"),
+    "uniform1e4": dict(kind="uniform", n=10000, dmax=20, d=0.85, tol=1e-10 / 0.15,
+                       label="uniform outdeg U{0..20}, N=10^4, d=0.85, V=1/N, FP64, |F|_1 < 1e-10"),
+}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def make_graph(w, seed=1):
+    import graphgen as gg
+    if w["kind"] == "zipf":
+        return gg.zipf_graph(w["n"], alpha=w["alpha"], kmax=w["kmax"], dangling_frac=w["dangling"],
+                             target_exp=w["target_exp"], seed=seed)
+    return gg.uniform_graph(w["n"], w["dmax"], seed=seed)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": smax, "reasons": ["no samples"]}
+        loaded = sorted(sm)[len(sm) // 2:] if len(sm) > 2 else sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(g, w, max_pushes, cores=1):
+    """The oracle (sequential FP64 snapshot sweeps, as it stands) on a bounded sample of the same solve."""
+    import graphgen as gg
+    import oracle
+    V = gg.uniform_v(g.n)
+    t0 = time.perf_counter()
+    r = oracle.diter(g.n, g.row_ptr, g.col_idx, w["d"], V, w["tol"], mode="sweep", beta=0.5, max_pushes=max_pushes)
+    dt = time.perf_counter() - t0
+    return {"value": r.edges / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"oracle snapshot sweeps (beta=0.5) from F_0 on the same graph, cut at {max_pushes} diffusions: "
+                      f"{r.sweeps} sweeps, {r.edges} edge pushes in {dt:.1f} s on 1 host core "
+                      f"({'converged' if r.converged else 'not converged'})",
+            "seconds": dt, "edges": int(r.edges), "sweeps": int(r.sweeps), "converged": bool(r.converged)}
+
+
+def run_reference(args, w):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    g = make_graph(w)
+    cap = args.cpu_pushes if args.cpu_pushes > 0 else 8 * g.n
+    vals, secs = [], []
+    for k in range(args.warmup + args.steps):
+        cb = cpu_baseline(g, w, cap)
+        if k >= args.warmup:
+            vals.append(cb["value"])
+            secs.append(cb["seconds"])
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["label"], "n": g.n, "nnz": g.nnz},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="zipf24", choices=sorted(WORKLOADS))
+    ap.add_argument("--beta", type=float, default=0.5)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-pushes", type=int, default=0, help="diffusions in the oracle sample (0: 8N, more than the full solve needs)")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("warm-up below 3 is not allowed; using 3")
+        args.warmup = 3
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    import paper_1202_6158_gb300 as di
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    t0 = time.perf_counter()
+    g = make_graph(w)
+    gen_s = time.perf_counter() - t0
+    log(f"[rank {rank}] graph n={g.n} nnz={g.nnz} generated in {gen_s:.1f}s")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    rp_d = torch.from_numpy(g.row_ptr).to(dev)
+    ci_d = torch.from_numpy(g.col_idx).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    G = di.DiGraph(g.n, rp_d, ci_d, w["d"])
+    torch.cuda.synchronize()
+    create_ms = 1e3 * (time.perf_counter() - t0)
+    H = torch.empty(g.n, dtype=torch.float64, device=dev)
+    X = torch.empty(g.n, dtype=torch.float64, device=dev)
+    tol = w["tol"]
+
+    # ---- warm-up, then K timed solves on device-resident inputs
+    for _ in range(args.warmup):
+        G.solve(tol, H_out=H, beta=args.beta)
+    torch.cuda.synchronize()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    edges = 0
+    launches = 0
+    sweeps = []
+    with ClockSampler(local) as clocks:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _, st = G.solve(tol, H_out=H, beta=args.beta)
+            edges += st["edges_pushed"]
+            launches += st["kernel_launches"]
+            sweeps.append(st["sweeps"])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    bound = st["bound"]
+    clk = clocks.summary()
+
+    # ---- power iteration to the paper's stop rule at the same tolerance, same GPU and graph
+    for _ in range(2):
+        G.power(tol, X_out=X)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(args.steps):
+        _, pst = G.power(tol, X_out=X)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    pms = p0.elapsed_time(p1) / args.steps
+    p_edges = pst["edges_pushed"]
+    agree = float((H - X).abs().sum().item())
+
+    # ---- profiled solve: per-kernel CUDA-event times and algorithmic bytes from the trace
+    G.solve(tol, H_out=H, beta=args.beta, profile=1, trace=1)
+    prof = G.profile()
+    trace = G.trace()
+    s_f = 8
+    push_bytes = sum(20 * t["edges"] + 16 * t["pushed"] for t in trace)
+    scan_bytes = sum(g.n * s_f + t["sources"] * (s_f + 16 + 8) + 16 * t["pushed"] for t in trace)
+    hbm_peak, peak_kind = load_peaks()
+    kernels = {
+        "push": {"ms": prof["push_ms"], "launches": prof["sweeps"], "alg_bytes": push_bytes},
+        "scan": {"ms": prof["scan_ms"], "launches": prof["sweeps"], "alg_bytes": scan_bytes},
+    }
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    kd = kernels[dom]
+    achieved = kd["alg_bytes"] / (kd["ms"] * 1e-3) / 1e9 if kd["ms"] > 0 else None
+    traffic = None
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": (achieved / hbm_peak) if achieved else None, "traffic": traffic,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else
+                "fallback 6800 GB/s",
+                "alg_bytes_per_launch": kd["alg_bytes"] / max(1, kd["launches"]),
+                "avg_launch_us": 1e3 * kd["ms"] / max(1, kd["launches"]),
+                "per_kernel": {k: {"ms_total": v["ms"], "launches": v["launches"],
+                                   "GBps": v["alg_bytes"] / (v["ms"] * 1e-3) / 1e9 if v["ms"] > 0 else None}
+                               for k, v in kernels.items()},
+                "finalize_ms_total": prof["finalize_ms"]}
+
+    # ---- end to end through the C ABI with pinned host buffers
+    rp_h = torch.from_numpy(g.row_ptr).pin_memory()
+    ci_h = torch.from_numpy(g.col_idx).pin_memory()
+    H_h = torch.empty(g.n, dtype=torch.float64).pin_memory()
+    e2e_edges = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        with di.DiGraph(g.n, rp_h, ci_h, w["d"]) as Ge:
+            _, est = Ge.solve(tol, H_out=H_h, beta=args.beta)
+            e2e_edges += est["edges_pushed"]
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    h2d = 4 * (g.n + 1) + 4 * g.nnz
+    d2h = 8 * g.n
+
+    # ---- aggregate over ranks: sum of work, max of time
+    tot_edges, max_ms, tot_e2e_edges, max_e2e = edges, ms, e2e_edges, e2e_s
+    if dist is not None:
+        t = torch.tensor([edges, e2e_edges], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        tm = torch.tensor([ms, e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        tot_edges, tot_e2e_edges = float(t[0]), float(t[1])
+        max_ms, max_e2e = float(tm[0]), float(tm[1])
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cap = args.cpu_pushes if args.cpu_pushes > 0 else 8 * g.n
+        cpu = cpu_baseline(g, w, cap)
+        cpu.pop("seconds", None)
+
+    if rank == 0:
+        value = tot_edges / (max_ms * 1e-3)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["label"], "n": g.n, "nnz": g.nnz, "d": w["d"], "tol": tol, "beta": args.beta,
+                       "parallelism": "replicas" if world > 1 else "single-gpu",
+                       "l2": "inputs larger than L2 (CSR + F + H of the solve exceed 129 MB)"},
+            "time_to_residual_ms": {"diter": max_ms / args.steps, "power": pms,
+                                    "speedup_vs_power": pms / (max_ms / args.steps)},
+            "diter": {"edges_per_solve": edges // args.steps, "sweeps": sweeps[-1], "bound": bound,
+                      "edges_over_L": edges / args.steps / g.nnz},
+            "power_iteration": {"iters": pst["sweeps"], "edges": p_edges, "value": p_edges / (pms * 1e-3),
+                                "unit": UNIT, "bound": pst["bound"], "l1_diff_vs_diter": agree},
+            "create_ms": create_ms,
+            "roofline": roofline,
+            "e2e": {"value": tot_e2e_edges / max_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h,
+                    "what": "pinned host CSR -> di_graph_create (copy, validation, ingest) -> di_solve to host H -> "
+                            "di_free, host wall clock"},
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "gpu_launches": launches,
+            "host": {"nproc": os.cpu_count()},
+        }
+        print(json.dumps(line), flush=True)
+    G.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,212 @@
+/*
+ * diter.h -- C ABI of libditer: D-iteration (fluid diffusion) PageRank on one
+ * GB300 GPU (sm_103a).
+ *
+ * The method is D. Hong, "Optimized on-line computation of PageRank
+ * algorithm":
+ *   Section 2.1  the problem  X = dPX + (1-d)V  with P_ij the probability of the
+ *                move j -> i (column j of P spreads 1/outdeg(j) over the children
+ *                of j) and V a normalized personalization vector;
+ *   Section 2.2  fluid F_0 = (1-d)V, history H, and ALGO-REF: pick a node, move
+ *                its fluid into H, push d*F_i/outdeg_i along every out-link,
+ *                decrement the residual R by (1-d)F_i, stop when
+ *                R/(1-d) <= target;
+ *   Theorem 2    |X - H_n|_1 = |F_n|_1/(1-d)  (an upper bound with dangling
+ *                nodes, Section 3.3);
+ *   Section 3.3  dangling nodes: their fluid leaves the system (R -= F_i) and P
+ *                is never completed;
+ *   Section 4.2  threshold sweeps: every node above a threshold diffuses in the
+ *                same step and the threshold is lowered progressively.
+ *
+ * Conventions for every call:
+ *   - Node ids are int32 in [0, n).  The graph is a CSR of OUT-links: row i of
+ *     (row_ptr, col_idx) lists the children of node i; multi-edges and
+ *     self-loops are allowed and each listed edge carries 1/outdeg(i).
+ *   - Pointers marked "host or device" may point to either; the library finds
+ *     out with cudaPointerGetAttributes.  Inputs are copied at the call; the
+ *     caller keeps ownership of every buffer it passes.  Outputs are written
+ *     into caller-owned buffers.
+ *   - Every call returns a di_status and never aborts; di_last_error() gives a
+ *     thread-local message for the last failure.  All work is issued on the
+ *     stream given at graph creation; calls that return results synchronize
+ *     that stream before returning.
+ *   - A di_graph is thread-compatible, not thread-safe: do not use one graph
+ *     from two host threads at once.
+ */
+#ifndef DITER_H
+#define DITER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct di_graph di_graph; /* opaque; owns all of its device memory */
+
+typedef enum {
+    DI_OK = 0,
+    DI_EINVAL = 1,         /* invalid argument or graph (message says which) */
+    DI_ENOMEM = 2,         /* device allocation failed */
+    DI_ECUDA = 3,          /* a CUDA runtime call failed */
+    DI_ENOTCONVERGED = 4,  /* a limit stopped the solve first; outputs are still written */
+    DI_ETIMEOUT = 5,       /* a bounded device-side wait gave up */
+    DI_EKERNEL = 6         /* a kernel reported an internal error (non-finite residual, ...) */
+} di_status;
+
+typedef enum {
+    DI_FP64 = 0,        /* fluid, pushes, history and residual all in FP64 */
+    DI_FP32_MIXED = 1   /* fluid and pushes in FP32; history and |F|_1 reductions in FP64 */
+} di_prec;
+
+typedef struct {
+    double bound;          /* |F|_1/(1-d) recomputed exactly at exit: the Theorem 2 bound on |X - H|_1 */
+    double l1_F;           /* |F|_1 recomputed at exit (FP64 sum) */
+    double R;              /* the tracked residual R of ALGO-REF at exit */
+    int64_t edges_pushed;  /* elementary steps (Section 4.2): out-links used by the diffusions */
+    int64_t sources_pushed;/* diffusions made (one per selected node per sweep) */
+    int32_t sweeps;        /* threshold sweeps (D-iteration) or products (power iteration) */
+    int32_t converged;     /* 1 if the stop rule was met */
+    double seconds;        /* device time from initialization to the confirmed stop (CUDA events) */
+    int64_t kernel_launches; /* kernels this call ran on the GPU (each graph-loop iteration counted) */
+} di_stats;
+
+typedef struct {
+    double tol;              /* target on |F|_1/(1-d); > 0 */
+    double beta;             /* threshold T = beta * R / n before each sweep (default 0.5) */
+    int64_t max_edge_pushes; /* stop with DI_ENOTCONVERGED beyond this many elementary steps (<= 0: none) */
+    int32_t max_sweeps;      /* stop with DI_ENOTCONVERGED after this many sweeps (<= 0: 1,000,000) */
+    int32_t prec;            /* a di_prec value */
+    int32_t normalize;       /* 0: raw H (uncompleted P); 1: H/|H|_1 (Section 3.3 renormalization) */
+    int32_t trace;           /* 1: record one di_sweep_record per sweep, read with di_get_trace */
+    int32_t profile;         /* 1: launch each sweep's kernels from the host with CUDA events around
+                                each one (same kernels and arguments, no graph); read with di_get_profile */
+} di_solve_opts;
+
+typedef struct {
+    double l1_F;           /* exact |F|_1 at the start of the sweep */
+    double removed;        /* sum over selected nodes of (1-d)*sent, or sent for dangling ones */
+    double R;              /* residual after the sweep: l1_F - removed */
+    double T;              /* threshold the sweep used */
+    int64_t sources;       /* nodes selected */
+    int64_t edges;         /* out-links pushed */
+    int64_t pushed;        /* selected nodes with at least one out-link (frontier entries) */
+} di_sweep_record;
+
+typedef struct {
+    double scan_ms;        /* summed CUDA-event time of the sweep scan kernel */
+    double push_ms;        /* summed CUDA-event time of the push kernel */
+    double finalize_ms;    /* summed CUDA-event time of the finalize kernel */
+    int32_t sweeps;        /* launches of each of the three kernels */
+    int32_t pad;
+} di_profile;
+
+/* ------------------------------------------------------------------ graphs */
+
+/*
+ * Build a device-resident graph for the problem X = dPX + (1-d)V (Section 2.1).
+ *   n        number of nodes, 1 <= n < 2^31 - 1
+ *   row_ptr  host or device, int32[n+1]; row_ptr[0] = 0, non-decreasing,
+ *            row_ptr[n] = nnz
+ *   col_idx  host or device, int32[nnz]; every entry in [0, n)
+ *   nnz      number of edges, 0 <= nnz < 2^31
+ *   d        damping factor, 0 < d < 1 (d = 1 is the non-terminating case the
+ *            paper contrasts with, Section 2.2 remark)
+ *   V        host or device, double[n], V >= 0, finite, |V|_1 = 1 within 1e-12;
+ *            NULL means the uniform vector 1/n (not stored)
+ *   stream   a cudaStream_t to issue all work on; NULL means the legacy default
+ *            stream
+ * The library validates everything on the device and builds, with its own
+ * kernels: out-degrees, the in-link lists used by di_power, and the degree
+ * bins.  On failure *out is NULL and nothing is leaked.
+ */
+di_status di_graph_create(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, int64_t nnz, double d,
+                          const double *V, void *stream, di_graph **out);
+
+/* Release a graph and all of its device memory.  NULL is allowed. */
+void di_free(di_graph *g);
+
+/* n, nnz and d of a graph (any pointer may be NULL). */
+di_status di_graph_info(const di_graph *g, int32_t *n, int64_t *nnz, double *d);
+
+/*
+ * Copy derived structures to caller buffers (host or device), for checks:
+ *   outdeg   int32[n]
+ *   in_ptr   int32[n+1], in_src int32[nnz]: in-link lists, sources ascending
+ *   bin_of   int32[n]: out-degree bin (0 dangling, 1..3 by the cut values)
+ *   in_bin_of int32[n]: in-degree bin used by the pull kernel of di_power
+ *   cuts     int32[4]: {out_cut1, out_cut2, in_cut1, in_cut2}
+ * Any pointer may be NULL to skip that array.
+ */
+di_status di_graph_export(const di_graph *g, int32_t *outdeg, int32_t *in_ptr, int32_t *in_src, int32_t *bin_of,
+                          int32_t *in_bin_of, int32_t *cuts);
+
+/* ------------------------------------------------------------------ solves */
+
+/*
+ * D-iteration with threshold sweeps (ALGO-REF with the dangling-node rule,
+ * Sections 2.2 and 3.3; sweeps per Section 4.2).  Each sweep selects
+ * S = {i : F_i > T} on a snapshot of F, moves F_i into H_i for all of S, then
+ * pushes d*F_i/outdeg_i along every out-link of every i in S (dangling nodes
+ * push nothing).  T = beta*R/n, halved after a sweep that selects nothing.
+ * The loop stops when R/(1-d) <= tol and the exact |F|_1 confirms it.
+ *   H_out  host or device double[n] (caller-owned), receives H (or H/|H|_1)
+ *   st     may be NULL
+ * Returns DI_ENOTCONVERGED (with H_out and st filled) if a limit hit first.
+ */
+di_status di_solve(di_graph *g, double tol, int64_t max_edge_pushes, di_prec prec, double *H_out, int normalize,
+                   di_stats *st);
+
+/* di_solve with every option (defaults when opts fields are zero, see di_solve_opts). */
+di_status di_solve_ex(di_graph *g, const di_solve_opts *opts, double *H_out, di_stats *st);
+
+/*
+ * Personalized query: di_solve with V replaced by the seed distribution
+ * (Section 2.1: V is the personalization vector), V_s = w_s / sum(w) on the
+ * seeds and 0 elsewhere.
+ *   seeds   host or device int32[nseeds], distinct ids in [0, n)
+ *   w       host or device double[nseeds] >= 0 with positive sum; NULL = uniform
+ */
+di_status di_query(di_graph *g, const int32_t *seeds, const double *w, int32_t nseeds, double tol, di_prec prec,
+                   double *H_out, di_stats *st);
+
+/*
+ * Power iteration on the uncompleted P (MAT-ITER, Section 4): X_0 = 0,
+ * X_{k+1} = dPX_k + (1-d)V, computed by a pull over in-links; stops when
+ * |X_{k+1} - X_k|_1 * d/(1-d) < tol (the paper's rule).  FP64.
+ *   X_out  host or device double[n]
+ * st->sweeps counts products, st->edges_pushed = products * nnz.
+ */
+di_status di_power(di_graph *g, double tol, int32_t max_iter, double *X_out, di_stats *st);
+
+/*
+ * Per-sweep records of the last solve made with opts.trace = 1.
+ *   out  host di_sweep_record[cap]; *count receives the number available
+ *        (records beyond cap are not copied).
+ */
+di_status di_get_trace(const di_graph *g, di_sweep_record *out, int32_t cap, int32_t *count);
+
+/*
+ * Current fluid F and history H of the last D-iteration solve (FP64 copies,
+ * host or device double[n] each; either may be NULL).  With the residual they
+ * are the complete state (Theorem 1: H + F = F_0 + dPH), used by checks.
+ */
+di_status di_get_state(const di_graph *g, double *F_out, double *H_out);
+
+/*
+ * Per-kernel device times of the last solve made with opts.profile = 1.
+ *   out  host di_profile*
+ */
+di_status di_get_profile(const di_graph *g, di_profile *out);
+
+/* Message of the last failure on this host thread ("" if none). */
+const char *di_last_error(void);
+
+/* Library version string. */
+const char *di_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DITER_H */

@@ -128,6 +128,13 @@ static void diffuse(i32 i, const i32 *row_ptr, const i32 *col_idx, double d, dou
     st->edges += end - beg;
 }
 
+/* plain sum of |F_i|: the L1 norm that R stands for (Theorem 2) */
+static double l1_norm(i32 n, const double *F) {
+    double s = 0.0;
+    for (i32 i = 0; i < n; ++i) s += fabs(F[i]);
+    return s;
+}
+
 /*
  * Run D-iteration on the state (F, H, R) until R/(1-d) <= tol or max_pushes
  * diffusions have been made.  F and H are updated in place, so a second call
@@ -150,6 +157,15 @@ static void diffuse(i32 i, const i32 *row_ptr, const i32 *col_idx, double d, dou
  * (>= |F|/N) always qualifies, which is the condition under which the Lemma of
  * Section 3.1 gives the contraction factor 1 - (1-d)/N.
  *
+ * The residual R.  ALGO-REF keeps R by decrement; in exact arithmetic R equals
+ * |F|_1 at every step (F only loses what R loses), and Theorem 2 is stated for
+ * |F|_1.  In floating point the decrement drifts by rounding, which at tight
+ * targets can hold R above the target after F has in fact met it.  The oracle
+ * therefore keeps the decrement of ALGO-REF between re-synchronisations with
+ * the plain sum of F: at the start of every sweep (THRESH, SWEEP), after every
+ * N picks (PER, RAND, MAX), and before it accepts a stop.  A run cut short by
+ * max_pushes reports the decremented R as it stands.
+ *
  * Zero-fluid picks of PER / RAND are skipped without counting (Section 4.2).
  * The sequential orders test the stop rule after every diffusion, like the
  * while-loop of ALGO-REF; ORC_SWEEP tests it between sweeps.
@@ -158,32 +174,49 @@ static void diffuse(i32 i, const i32 *row_ptr, const i32 *col_idx, double d, dou
 int orc_diter(i32 n, const i32 *row_ptr, const i32 *col_idx, double d, double *F, double *H, double R,
               double tol, int mode, double beta, u64 seed, i64 max_pushes, orc_stats *st) {
     memset(st, 0, sizeof(*st));
+    if (mode < ORC_PER || mode > ORC_SWEEP) return -1;
+    const int sweeping = (mode == ORC_THRESH || mode == ORC_SWEEP);
     i64 zero_run = 0;
     double T = beta * R / (double)n;
+    int first = 1, last_empty = 0;
     i32 *S = NULL;
     double *sent = NULL;
     if (mode == ORC_SWEEP) {
         S = (i32 *)malloc(sizeof(i32) * (size_t)n);
         sent = (double *)malloc(sizeof(double) * (size_t)n);
     }
-    while (R / (1.0 - d) > tol && st->pushes < max_pushes) {
-        if (mode == ORC_PER || mode == ORC_RAND) {
-            i32 i = (mode == ORC_PER) ? (i32)(st->picks % n)
-                                      : (i32)(orc_splitmix(seed + (u64)st->picks) % (u64)n);
+    for (;;) {
+        if (st->pushes >= max_pushes) break;
+        if (sweeping) {
+            if (!first) {
+                R = l1_norm(n, F);
+                T = last_empty ? T / 2.0 : beta * R / (double)n;
+            }
+            first = 0;
+        }
+        if (!isfinite(R)) break;             /* F overflowed: report, never loop */
+        if (R / (1.0 - d) <= tol) {
+            R = l1_norm(n, F);               /* accept a stop only on the exact norm */
+            if (R / (1.0 - d) <= tol) break;
+            if (sweeping) T = beta * R / (double)n;
+        }
+        if (mode == ORC_PER || mode == ORC_RAND || mode == ORC_MAX) {
+            i32 i;
+            if (mode == ORC_MAX) {
+                i = 0;
+                for (i32 k = 1; k < n; ++k) if (F[k] > F[i]) i = k;
+            } else {
+                i = (mode == ORC_PER) ? (i32)(st->picks % n) : (i32)(orc_splitmix(seed + (u64)st->picks) % (u64)n);
+            }
             st->picks += 1;
+            if (st->picks % n == 0) R = l1_norm(n, F);
             if (F[i] == 0.0) {
-                /* every entry zero: nothing is left to diffuse (R only drifted) */
-                if (++zero_run > 64 * (i64)n) break;
+                /* every entry zero: nothing is left to diffuse */
+                if (mode == ORC_MAX || ++zero_run > 64 * (i64)n) { R = l1_norm(n, F); break; }
                 continue;
             }
             zero_run = 0;
             diffuse(i, row_ptr, col_idx, d, F, H, &R, st);
-        } else if (mode == ORC_MAX) {
-            i32 best = 0;
-            for (i32 i = 1; i < n; ++i) if (F[i] > F[best]) best = i;
-            st->picks += 1;
-            if (F[best] == 0.0) break;
-            diffuse(best, row_ptr, col_idx, d, F, H, &R, st);
         } else if (mode == ORC_THRESH) {
             i64 before = st->pushes;
             for (i32 i = 0; i < n; ++i) {
@@ -194,13 +227,9 @@ int orc_diter(i32 n, const i32 *row_ptr, const i32 *col_idx, double d, double *F
                 }
             }
             st->sweeps += 1;
-            if (st->pushes == before) {
-                if (T == 0.0) break;       /* F is identically zero */
-                T = T / 2.0;
-            } else {
-                T = beta * R / (double)n;
-            }
-        } else if (mode == ORC_SWEEP) {
+            last_empty = (st->pushes == before);
+            if (last_empty && T == 0.0) break;   /* F is identically zero */
+        } else {
             i32 ns = 0;
             for (i32 i = 0; i < n; ++i) if (F[i] > T) S[ns++] = i;
             for (i32 k = 0; k < ns; ++k) {
@@ -224,23 +253,14 @@ int orc_diter(i32 n, const i32 *row_ptr, const i32 *col_idx, double d, double *F
             st->pushes += ns;
             st->picks += ns;
             st->sweeps += 1;
-            if (ns == 0) {
-                if (T == 0.0) break;
-                T = T / 2.0;
-            } else {
-                T = beta * R / (double)n;
-            }
-        } else {
-            free(S); free(sent);
-            return -1;
+            last_empty = (ns == 0);
+            if (last_empty && T == 0.0) break;
         }
     }
     free(S); free(sent);
-    double l1 = 0.0;
-    for (i32 i = 0; i < n; ++i) l1 += fabs(F[i]);
     st->R = R;
-    st->l1F = l1;
-    st->converged = (R / (1.0 - d) <= tol) ? 1 : 0;
+    st->l1F = l1_norm(n, F);
+    st->converged = (st->l1F / (1.0 - d) <= tol) ? 1 : 0;
     return st->converged ? 0 : 1;
 }
 

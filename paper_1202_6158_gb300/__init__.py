@@ -1,0 +1,176 @@
+"""D-iteration (fluid diffusion) PageRank on one GB300 GPU.
+
+Python front end of libditer (include/diter.h).  The names follow the C ABI:
+``di_graph_create``, ``di_solve``, ``di_solve_ex``, ``di_query``, ``di_power``,
+``di_graph_export``, ``di_get_trace``, ``di_get_state``, ``di_free``; the
+:class:`DiGraph` class wraps a graph handle with the same calls as methods.
+Arrays are numpy arrays or torch tensors, on the host or on the device.
+
+The method is D. Hong, "Optimized on-line computation of PageRank algorithm":
+fluid F_0 = (1-d)V is diffused along out-links (ALGO-REF, Section 2.2, with the
+dangling-node rule of Section 3.3) in threshold sweeps (Section 4.2) until
+|F|_1/(1-d), the Theorem 2 bound on |X - H|_1, meets the target.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (DI_EINVAL, DI_ENOTCONVERGED, DI_FP32_MIXED, DI_FP64, DI_OK, DiError, check, di_profile,
+                   di_solve_opts, di_stats, di_sweep_record, ptr)
+
+__all__ = ["DiGraph", "DiError", "DI_FP64", "DI_FP32_MIXED", "DI_OK", "DI_EINVAL", "DI_ENOTCONVERGED",
+           "di_graph_create", "di_free", "di_solve", "di_solve_ex", "di_query", "di_power", "di_graph_export",
+           "di_get_trace", "di_get_state", "di_get_profile", "di_version", "load"]
+
+
+def load():
+    return _lib.load()
+
+
+def di_version() -> str:
+    return load().di_version().decode()
+
+
+def di_graph_create(n, row_ptr, col_idx, d, V=None, stream=None) -> int:
+    """Create a device graph; returns the opaque handle (an int)."""
+    lib = load()
+    out = ctypes.c_void_p()
+    nnz = int(len(col_idx)) if col_idx is not None else 0
+    if stream is None:
+        stream = _lib.current_stream()
+    check(lib.di_graph_create(int(n), ptr(row_ptr), ptr(col_idx) if nnz else None, nnz, float(d), ptr(V), stream,
+                              ctypes.byref(out)))
+    return out.value
+
+
+def di_free(handle) -> None:
+    if handle:
+        load().di_free(handle)
+
+
+def di_solve(handle, tol, H_out, max_edge_pushes=0, prec=DI_FP64, normalize=0, allow_unconverged=False):
+    st = di_stats()
+    ok = (DI_OK, DI_ENOTCONVERGED) if allow_unconverged else (DI_OK,)
+    rc = check(load().di_solve(handle, float(tol), int(max_edge_pushes), int(prec), ptr(H_out), int(normalize),
+                               ctypes.byref(st)), ok)
+    return rc, st.as_dict()
+
+
+def di_solve_ex(handle, H_out, tol, beta=0.5, max_edge_pushes=0, max_sweeps=0, prec=DI_FP64, normalize=0, trace=0,
+                profile=0, allow_unconverged=False):
+    o = di_solve_opts(float(tol), float(beta), int(max_edge_pushes), int(max_sweeps), int(prec), int(normalize),
+                      int(trace), int(profile))
+    st = di_stats()
+    ok = (DI_OK, DI_ENOTCONVERGED) if allow_unconverged else (DI_OK,)
+    rc = check(load().di_solve_ex(handle, ctypes.byref(o), ptr(H_out), ctypes.byref(st)), ok)
+    return rc, st.as_dict()
+
+
+def di_query(handle, seeds, w, tol, H_out, prec=DI_FP64):
+    st = di_stats()
+    check(load().di_query(handle, ptr(seeds), ptr(w), int(len(seeds)), float(tol), int(prec), ptr(H_out),
+                          ctypes.byref(st)))
+    return st.as_dict()
+
+
+def di_power(handle, tol, X_out, max_iter=0, allow_unconverged=False):
+    st = di_stats()
+    ok = (DI_OK, DI_ENOTCONVERGED) if allow_unconverged else (DI_OK,)
+    rc = check(load().di_power(handle, float(tol), int(max_iter), ptr(X_out), ctypes.byref(st)), ok)
+    return rc, st.as_dict()
+
+
+def di_graph_export(handle, outdeg=None, in_ptr=None, in_src=None, bin_of=None, in_bin_of=None, cuts=None):
+    check(load().di_graph_export(handle, ptr(outdeg), ptr(in_ptr), ptr(in_src), ptr(bin_of), ptr(in_bin_of),
+                                 ptr(cuts)))
+
+
+def di_get_trace(handle, cap=4096):
+    recs = (di_sweep_record * max(cap, 1))()
+    cnt = ctypes.c_int32(0)
+    check(load().di_get_trace(handle, recs, int(cap), ctypes.byref(cnt)))
+    k = min(cnt.value, cap)
+    return [{f: getattr(recs[i], f) for f, _ in di_sweep_record._fields_} for i in range(k)]
+
+
+def di_get_state(handle, F_out=None, H_out=None):
+    check(load().di_get_state(handle, ptr(F_out), ptr(H_out)))
+
+
+def di_get_profile(handle) -> dict:
+    p = di_profile()
+    check(load().di_get_profile(handle, ctypes.byref(p)))
+    return {"scan_ms": p.scan_ms, "push_ms": p.push_ms, "finalize_ms": p.finalize_ms, "sweeps": p.sweeps}
+
+
+class DiGraph:
+    """A device-resident graph (CSR of out-links) with damping d and personalization V."""
+
+    def __init__(self, n, row_ptr, col_idx, d=0.85, V=None, stream=None):
+        self.n = int(n)
+        self.nnz = int(len(col_idx))
+        self.d = float(d)
+        self.handle = di_graph_create(n, np.ascontiguousarray(row_ptr, dtype=np.int32)
+                                      if isinstance(row_ptr, (list, np.ndarray)) else row_ptr,
+                                      np.ascontiguousarray(col_idx, dtype=np.int32)
+                                      if isinstance(col_idx, (list, np.ndarray)) else col_idx,
+                                      d, V, stream)
+
+    def close(self):
+        if self.handle:
+            di_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def solve(self, tol, H_out=None, **kw):
+        """D-iteration to |F|_1/(1-d) <= tol; returns (H, stats)."""
+        H = H_out if H_out is not None else np.empty(self.n, dtype=np.float64)
+        _rc, st = di_solve_ex(self.handle, H, tol, **kw)
+        return H, st
+
+    def query(self, seeds, tol, w=None, H_out=None, prec=DI_FP64):
+        H = H_out if H_out is not None else np.empty(self.n, dtype=np.float64)
+        s = np.ascontiguousarray(seeds, dtype=np.int32) if isinstance(seeds, (list, np.ndarray)) else seeds
+        ww = np.ascontiguousarray(w, dtype=np.float64) if isinstance(w, (list, np.ndarray)) else w
+        st = di_query(self.handle, s, ww, tol, H, prec)
+        return H, st
+
+    def power(self, tol, X_out=None, max_iter=0, allow_unconverged=False):
+        X = X_out if X_out is not None else np.empty(self.n, dtype=np.float64)
+        _rc, st = di_power(self.handle, tol, X, max_iter, allow_unconverged)
+        return X, st
+
+    def export(self):
+        n, L = self.n, self.nnz
+        out = {"outdeg": np.empty(n, np.int32), "in_ptr": np.empty(n + 1, np.int32),
+               "in_src": np.empty(max(L, 1), np.int32), "bin_of": np.empty(n, np.int32),
+               "in_bin_of": np.empty(n, np.int32), "cuts": np.empty(4, np.int32)}
+        di_graph_export(self.handle, **out)
+        out["in_src"] = out["in_src"][:L]
+        return out
+
+    def trace(self, cap=4096):
+        return di_get_trace(self.handle, cap)
+
+    def profile(self):
+        return di_get_profile(self.handle)
+
+    def state(self):
+        F = np.empty(self.n, np.float64)
+        H = np.empty(self.n, np.float64)
+        di_get_state(self.handle, F, H)
+        return F, H

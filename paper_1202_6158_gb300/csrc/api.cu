@@ -1,0 +1,308 @@
+// api.cu -- the extern "C" entry points of libditer (declared in include/diter.h).
+//
+// This file does argument checks, host/device pointer detection, ownership and
+// error reporting.  All arithmetic of the method runs in the kernels of
+// graph_build.cu, sweep.cu and power.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace diter {
+
+static thread_local std::string g_last_error;
+
+di_status set_error(di_status s, const std::string &msg) {
+    g_last_error = msg;
+    return s;
+}
+
+di_status cuda_fail(cudaError_t e, const char *what) {
+    cudaGetLastError();  // clear a sticky launch error so the next call starts clean
+    if (e == cudaErrorMemoryAllocation)
+        return set_error(DI_ENOMEM, std::string("out of device memory in ") + what);
+    return set_error(DI_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+static bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static di_status copy_in(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return DI_OK;
+    DI_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    return DI_OK;
+}
+
+static void free_graph(di_graph *g) {
+    if (!g) return;
+    if (g->stream || g->cap) cudaStreamSynchronize(g->stream);
+    for (int k = 0; k < 3; ++k) {
+        if (g->exec[k]) cudaGraphExecDestroy(g->exec[k]);
+        if (g->graph[k]) cudaGraphDestroy(g->graph[k]);
+    }
+    void *bufs[] = {g->row_ptr, g->col_idx, g->in_ptr, g->in_src, g->bin_of, g->in_bin_of, g->pull_ids, g->V,
+                    g->long_prefix, g->region, g->fcount, g->frontier, g->F64, g->F32, g->H, g->part, g->st,
+                    g->trace, g->X, g->Z[0], g->Z[1], g->Ylong, g->ppart, g->pst};
+    for (void *b : bufs)
+        if (b) cudaFreeAsync(b, g->stream);
+    cudaStreamSynchronize(g->stream);
+    if (g->h_st) cudaFreeHost(g->h_st);
+    if (g->h_pst) cudaFreeHost(g->h_pst);
+    if (g->ev0) cudaEventDestroy(g->ev0);
+    if (g->ev1) cudaEventDestroy(g->ev1);
+    for (int k = 0; k < 4; ++k)
+        if (g->pev[k]) cudaEventDestroy(g->pev[k]);
+    if (g->cap) cudaStreamDestroy(g->cap);
+    cudaGetLastError();
+    delete g;
+}
+
+static di_status check_graph(const di_graph *g) {
+    if (!g) return set_error(DI_EINVAL, "graph is NULL");
+    return DI_OK;
+}
+
+}  // namespace diter
+
+using namespace diter;
+
+extern "C" {
+
+const char *di_last_error(void) { return g_last_error.c_str(); }
+
+const char *di_version(void) { return "libditer 0.1 (D-iteration, sm_103a)"; }
+
+di_status di_graph_create(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, int64_t nnz, double d,
+                          const double *V, void *stream, di_graph **out) {
+    g_last_error.clear();
+    if (!out) return set_error(DI_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n == INT32_MAX) return set_error(DI_EINVAL, "n must be in [1, 2^31-2]");
+    if (nnz < 0 || nnz >= INT32_MAX) return set_error(DI_EINVAL, "nnz must be in [0, 2^31-1)");
+    if (!row_ptr) return set_error(DI_EINVAL, "row_ptr is NULL");
+    if (nnz > 0 && !col_idx) return set_error(DI_EINVAL, "col_idx is NULL");
+    if (!(d > 0.0 && d < 1.0)) return set_error(DI_EINVAL, "d must satisfy 0 < d < 1");
+    di_graph *g = new di_graph();
+    g->n = n;
+    g->nnz = nnz;
+    g->d = d;
+    g->stream = (cudaStream_t)stream;
+    auto fail = [&](di_status s) {
+        std::string msg = g_last_error;
+        free_graph(g);
+        g_last_error = msg;
+        return s;
+    };
+    cudaError_t e = cudaGetDevice(&g->dev);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaGetDevice"));
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->dev);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaDeviceGetAttribute"));
+    g->num_sms = sms > 0 ? sms : 152;
+    if ((e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking)) != cudaSuccess)
+        return fail(cuda_fail(e, "cudaStreamCreate"));
+    if ((e = cudaEventCreate(&g->ev0)) != cudaSuccess) return fail(cuda_fail(e, "cudaEventCreate"));
+    if ((e = cudaEventCreate(&g->ev1)) != cudaSuccess) return fail(cuda_fail(e, "cudaEventCreate"));
+    for (int k = 0; k < 4; ++k)
+        if ((e = cudaEventCreate(&g->pev[k])) != cudaSuccess) return fail(cuda_fail(e, "cudaEventCreate"));
+    if ((e = cudaMallocHost(&g->h_st, sizeof(SolveState))) != cudaSuccess) return fail(cuda_fail(e, "cudaMallocHost"));
+    if ((e = cudaMallocHost(&g->h_pst, sizeof(PowerState))) != cudaSuccess) return fail(cuda_fail(e, "cudaMallocHost"));
+    memset(g->h_st, 0, sizeof(SolveState));
+    memset(g->h_pst, 0, sizeof(PowerState));
+    cudaStream_t s = g->stream;
+    if ((e = cudaMallocAsync(&g->row_ptr, sizeof(int) * (size_t)(n + 1), s)) != cudaSuccess)
+        return fail(cuda_fail(e, "cudaMallocAsync(row_ptr)"));
+    if ((e = cudaMallocAsync(&g->col_idx, sizeof(int) * (size_t)std::max<int64_t>(nnz, 1), s)) != cudaSuccess)
+        return fail(cuda_fail(e, "cudaMallocAsync(col_idx)"));
+    di_status r = copy_in(g->row_ptr, row_ptr, sizeof(int) * (size_t)(n + 1), s);
+    if (r == DI_OK) r = copy_in(g->col_idx, col_idx, sizeof(int) * (size_t)nnz, s);
+    if (r != DI_OK) return fail(r);
+    if (V) {
+        if ((e = cudaMallocAsync(&g->V, sizeof(double) * (size_t)n, s)) != cudaSuccess)
+            return fail(cuda_fail(e, "cudaMallocAsync(V)"));
+        if ((r = copy_in(g->V, V, sizeof(double) * (size_t)n, s)) != DI_OK) return fail(r);
+        if ((r = validate_v(g, g->V)) != DI_OK) return fail(r);
+    }
+    if ((r = build_graph(g, g->row_ptr, g->col_idx)) != DI_OK) return fail(r);
+    if ((r = sweep_alloc(g)) != DI_OK) return fail(r);
+    if ((r = power_alloc(g)) != DI_OK) return fail(r);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(cuda_fail(e, "graph create"));
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_fail(e, "graph create"));
+    *out = g;
+    return DI_OK;
+}
+
+void di_free(di_graph *g) { free_graph(g); }
+
+di_status di_graph_info(const di_graph *g, int32_t *n, int64_t *nnz, double *d) {
+    if (check_graph(g) != DI_OK) return DI_EINVAL;
+    if (n) *n = g->n;
+    if (nnz) *nnz = g->nnz;
+    if (d) *d = g->d;
+    return DI_OK;
+}
+
+}  // extern "C"
+
+namespace diter {
+namespace {
+__global__ void k_outdeg(int n, const int *__restrict__ row_ptr, int *__restrict__ out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = row_ptr[i + 1] - row_ptr[i];
+}
+}  // namespace
+
+static di_status copy_out(void *dst, const void *src_dev, size_t bytes, cudaStream_t s) {
+    if (!dst || bytes == 0) return DI_OK;
+    DI_CUDA(cudaMemcpyAsync(dst, src_dev, bytes, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            s));
+    return DI_OK;
+}
+}  // namespace diter
+
+extern "C" {
+
+di_status di_graph_export(const di_graph *g, int32_t *outdeg, int32_t *in_ptr, int32_t *in_src, int32_t *bin_of,
+                          int32_t *in_bin_of, int32_t *cuts) {
+    g_last_error.clear();
+    if (check_graph(g) != DI_OK) return DI_EINVAL;
+    cudaStream_t s = g->stream;
+    const size_t n = (size_t)g->n;
+    if (outdeg) {
+        int *tmp = nullptr;
+        DI_CUDA(cudaMallocAsync(&tmp, sizeof(int) * n, s));
+        k_outdeg<<<std::max(1, std::min(1216, (int)((n + 255) / 256))), 256, 0, s>>>(g->n, g->row_ptr, tmp);
+        di_status r = copy_out(outdeg, tmp, sizeof(int) * n, s);
+        cudaFreeAsync(tmp, s);
+        if (r != DI_OK) return r;
+    }
+    di_status r = copy_out(in_ptr, g->in_ptr, sizeof(int) * (n + 1), s);
+    if (r == DI_OK) r = copy_out(in_src, g->in_src, sizeof(int) * (size_t)g->nnz, s);
+    if (r == DI_OK) r = copy_out(bin_of, g->bin_of, sizeof(int) * n, s);
+    if (r == DI_OK) r = copy_out(in_bin_of, g->in_bin_of, sizeof(int) * n, s);
+    if (r != DI_OK) return r;
+    DI_CUDA(cudaStreamSynchronize(s));
+    if (cuts) {
+        cuts[0] = kOutCut1;
+        cuts[1] = kOutCut2;
+        cuts[2] = kInCut1;
+        cuts[3] = kInCut2;
+    }
+    return DI_OK;
+}
+
+di_status di_solve_ex(di_graph *g, const di_solve_opts *opts, double *H_out, di_stats *st) {
+    g_last_error.clear();
+    if (check_graph(g) != DI_OK) return DI_EINVAL;
+    if (!opts) return set_error(DI_EINVAL, "opts is NULL");
+    di_solve_opts o = *opts;
+    if (!(o.tol > 0.0) || !std::isfinite(o.tol)) return set_error(DI_EINVAL, "tol must be finite and > 0");
+    if (!(o.beta >= 0.0) || !std::isfinite(o.beta)) return set_error(DI_EINVAL, "beta must be finite and >= 0");
+    if (o.prec != DI_FP64 && o.prec != DI_FP32_MIXED) return set_error(DI_EINVAL, "prec must be DI_FP64 or DI_FP32_MIXED");
+    return run_solve(g, o, nullptr, nullptr, 0, 1.0, H_out, is_device_ptr(H_out), st);
+}
+
+di_status di_solve(di_graph *g, double tol, int64_t max_edge_pushes, di_prec prec, double *H_out, int normalize,
+                   di_stats *st) {
+    di_solve_opts o;
+    memset(&o, 0, sizeof(o));
+    o.tol = tol;
+    o.beta = 0.5;
+    o.max_edge_pushes = max_edge_pushes;
+    o.prec = (int32_t)prec;
+    o.normalize = normalize;
+    return di_solve_ex(g, &o, H_out, st);
+}
+
+di_status di_query(di_graph *g, const int32_t *seeds, const double *w, int32_t nseeds, double tol, di_prec prec,
+                   double *H_out, di_stats *st) {
+    g_last_error.clear();
+    if (check_graph(g) != DI_OK) return DI_EINVAL;
+    if (nseeds < 1 || !seeds) return set_error(DI_EINVAL, "a query needs at least one seed");
+    if (!(tol > 0.0) || !std::isfinite(tol)) return set_error(DI_EINVAL, "tol must be finite and > 0");
+    if (prec != DI_FP64 && prec != DI_FP32_MIXED) return set_error(DI_EINVAL, "prec must be DI_FP64 or DI_FP32_MIXED");
+    cudaStream_t s = g->stream;
+    std::vector<int32_t> hs((size_t)nseeds);
+    std::vector<double> hw(w ? (size_t)nseeds : 0);
+    DI_CUDA(cudaMemcpyAsync(hs.data(), seeds, sizeof(int32_t) * nseeds,
+                            is_device_ptr(seeds) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
+    if (w)
+        DI_CUDA(cudaMemcpyAsync(hw.data(), w, sizeof(double) * nseeds,
+                                is_device_ptr(w) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
+    DI_CUDA(cudaStreamSynchronize(s));
+    double wsum = 0.0;
+    for (int k = 0; k < nseeds; ++k) {
+        if (hs[k] < 0 || hs[k] >= g->n) return set_error(DI_EINVAL, "seed id outside [0, n)");
+        double wk = w ? hw[k] : 1.0;
+        if (!std::isfinite(wk) || wk < 0.0) return set_error(DI_EINVAL, "seed weights must be finite and >= 0");
+        wsum += wk;
+    }
+    if (!(wsum > 0.0)) return set_error(DI_EINVAL, "seed weights must have a positive sum");
+    int *dseeds = nullptr;
+    double *dw = nullptr;
+    DI_CUDA(cudaMallocAsync(&dseeds, sizeof(int) * nseeds, s));
+    DI_CUDA(cudaMemcpyAsync(dseeds, hs.data(), sizeof(int) * nseeds, cudaMemcpyHostToDevice, s));
+    if (w) {
+        DI_CUDA(cudaMallocAsync(&dw, sizeof(double) * nseeds, s));
+        DI_CUDA(cudaMemcpyAsync(dw, hw.data(), sizeof(double) * nseeds, cudaMemcpyHostToDevice, s));
+    }
+    di_solve_opts o;
+    memset(&o, 0, sizeof(o));
+    o.tol = tol;
+    o.beta = 0.5;
+    o.prec = (int32_t)prec;
+    di_status r = run_solve(g, o, dseeds, dw, nseeds, wsum, H_out, is_device_ptr(H_out), st);
+    cudaFreeAsync(dseeds, s);
+    if (dw) cudaFreeAsync(dw, s);
+    return r;
+}
+
+di_status di_power(di_graph *g, double tol, int32_t max_iter, double *X_out, di_stats *st) {
+    g_last_error.clear();
+    if (check_graph(g) != DI_OK) return DI_EINVAL;
+    if (!(tol > 0.0) || !std::isfinite(tol)) return set_error(DI_EINVAL, "tol must be finite and > 0");
+    if (max_iter <= 0) max_iter = 100000;
+    return run_power(g, tol, max_iter, X_out, is_device_ptr(X_out), st);
+}
+
+di_status di_get_trace(const di_graph *g, di_sweep_record *out, int32_t cap, int32_t *count) {
+    g_last_error.clear();
+    if (check_graph(g) != DI_OK) return DI_EINVAL;
+    int avail = g->last_trace_on ? std::min(g->h_st->sweeps, kTraceCap) : 0;
+    if (count) *count = avail;
+    int k = std::min(avail, std::max(0, (int)cap));
+    if (out && k > 0) {
+        DI_CUDA(cudaMemcpyAsync(out, g->trace, sizeof(di_sweep_record) * k, cudaMemcpyDeviceToHost, g->stream));
+        DI_CUDA(cudaStreamSynchronize(g->stream));
+    }
+    return DI_OK;
+}
+
+di_status di_get_profile(const di_graph *g, di_profile *out) {
+    g_last_error.clear();
+    if (check_graph(g) != DI_OK) return DI_EINVAL;
+    if (!out) return set_error(DI_EINVAL, "out is NULL");
+    *out = g->prof;
+    return DI_OK;
+}
+
+di_status di_get_state(const di_graph *g, double *F_out, double *H_out) {
+    g_last_error.clear();
+    if (check_graph(g) != DI_OK) return DI_EINVAL;
+    if (g->last_prec < 0) return set_error(DI_EINVAL, "no D-iteration solve has run on this graph");
+    return copy_state(g, F_out, is_device_ptr(F_out), H_out, is_device_ptr(H_out));
+}
+
+}  // extern "C"

@@ -1,0 +1,507 @@
+// graph_build.cu -- graph ingest on the device (create time).
+//
+// Everything the solves need is derived here by our own kernels, from the
+// out-link CSR of the problem statement (Section 2.1: column j of P spreads
+// 1/outdeg(j) over the children of j; Section 3.3: dangling columns stay zero):
+//   * validation of the CSR and of V (error flags, no traps);
+//   * out-degree bins (0 dangling, 1 thread, 2 warp, 3 CTA) and, per sweep-scan
+//     chunk, the offsets at which each bin's selected nodes are written;
+//   * the in-link CSR (a stable LSD radix sort of (target, source) pairs, so
+//     every in-row lists its sources in ascending order and the result is
+//     unique, hence bit-exact against any correct construction);
+//   * in-degree bins for the pull kernel and the chunk tasks of its longest rows.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+
+namespace diter {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// exclusive scan of one int per thread over a 256-thread block; *total gets the block sum
+__device__ int block_excl_scan(int v, int *total) {
+    __shared__ int ws[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int s = lane < 8 ? ws[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            int y = __shfl_up_sync(kFull, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < 8) ws[lane] = s;
+    }
+    __syncthreads();
+    int excl = x - v + (w > 0 ? ws[w - 1] : 0);
+    *total = ws[7];
+    __syncthreads();
+    return excl;
+}
+
+// ---------------------------------------------------------------- validation
+
+enum : int { kBadRowPtr0 = 1, kBadRowPtrN = 2, kNotMonotone = 4, kColRange = 8, kVNeg = 16, kVNonFinite = 32 };
+
+__global__ void k_validate_csr(int n, long long nnz, const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
+                               int *flags) {
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    int f = 0;
+    if (tid == 0) {
+        if (row_ptr[0] != 0) f |= kBadRowPtr0;
+        if ((long long)row_ptr[n] != nnz) f |= kBadRowPtrN;
+    }
+    for (long long i = tid; i < n; i += stride)
+        if (row_ptr[i + 1] < row_ptr[i]) f |= kNotMonotone;
+    for (long long e = tid; e < nnz; e += stride) {
+        int j = col_idx[e];
+        if (j < 0 || j >= n) f |= kColRange;
+    }
+    if (f) atomicOr(flags, f);
+}
+
+__global__ void k_validate_v(int n, const double *__restrict__ V, int *flags, double *sum) {
+    double s = 0.0;
+    int f = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double v = V[i];
+        if (!isfinite(v)) f |= kVNonFinite;
+        else if (v < 0.0) f |= kVNeg;
+        else s += v;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(kFull, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(sum, s);
+    if (f) atomicOr(flags, f);
+}
+
+// ------------------------------------------------------- degrees and bins
+
+__global__ void k_out_bins(int n, const int *__restrict__ row_ptr, int cut1, int cut2, int *__restrict__ bin_of) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int deg = row_ptr[i + 1] - row_ptr[i];
+        bin_of[i] = deg == 0 ? 0 : (deg <= cut1 ? 1 : (deg <= cut2 ? 2 : 3));
+    }
+}
+
+// per scan chunk: how many nodes of bins 1..3 it holds
+__global__ void k_chunk_bin_counts(int n, int chunk, const int *__restrict__ bin_of, int *__restrict__ cnt, int G) {
+    __shared__ int c[4];
+    if (threadIdx.x < 4) c[threadIdx.x] = 0;
+    __syncthreads();
+    long long beg = (long long)blockIdx.x * chunk, end = min((long long)n, beg + chunk);
+    int l1 = 0, l2 = 0, l3 = 0;
+    for (long long i = beg + threadIdx.x; i < end; i += blockDim.x) {
+        int b = bin_of[i];
+        l1 += b == 1;
+        l2 += b == 2;
+        l3 += b == 3;
+    }
+    atomicAdd(&c[1], l1);
+    atomicAdd(&c[2], l2);
+    atomicAdd(&c[3], l3);
+    __syncthreads();
+    if (threadIdx.x < 3) cnt[threadIdx.x * G + blockIdx.x] = c[threadIdx.x + 1];
+}
+
+// region[b][c] = (nodes of bins < b) + (nodes of bin b in chunks < c); b = 0..2 stands for bins 1..3
+__global__ void k_region_scan(int G, const int *__restrict__ cnt, int *__restrict__ region) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    long long base = 0;
+    for (int b = 0; b < 3; ++b) {
+        long long run = 0;
+        for (int c = 0; c < G; ++c) {
+            region[b * (G + 1) + c] = (int)(base + run);
+            run += cnt[b * G + c];
+        }
+        region[b * (G + 1) + G] = (int)(base + run);
+        base += run;
+    }
+}
+
+__global__ void k_in_bins(int n, const int *__restrict__ in_ptr, int cut1, int cut2, int *__restrict__ in_bin_of) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int deg = in_ptr[i + 1] - in_ptr[i];
+        in_bin_of[i] = deg <= cut1 ? 0 : (deg <= cut2 ? 1 : 2);
+    }
+}
+
+__global__ void k_iota(int n, int *__restrict__ out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (int)i;
+}
+
+// number of pull chunk tasks of each long row
+__global__ void k_long_tasks(int nlong, const int *__restrict__ ids, const int *__restrict__ in_ptr, int chunk,
+                             int *__restrict__ ntasks) {
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nlong; r += (long long)gridDim.x * blockDim.x) {
+        int j = ids[r];
+        ntasks[r] = (in_ptr[j + 1] - in_ptr[j] + chunk - 1) / chunk;
+    }
+}
+
+// ----------------------------------------------------------- generic scan
+
+constexpr int kScanItems = 16;
+constexpr int kScanBlock = 256 * kScanItems;
+
+__global__ void k_scan_reduce(const int *__restrict__ in, long long m, int *__restrict__ sums) {
+    long long base = (long long)blockIdx.x * kScanBlock + (long long)threadIdx.x * kScanItems;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < m) s += in[base + k];
+    int total;
+    block_excl_scan(s, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// single CTA: exclusive scan of the block sums, in place
+__global__ void k_scan_top(int nb, int *__restrict__ sums) {
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        int v = i < nb ? sums[i] : 0;
+        int total;
+        int ex = block_excl_scan(v, &total);
+        if (i < nb) sums[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += total;
+        __syncthreads();
+    }
+}
+
+__global__ void k_scan_down(const int *__restrict__ in, long long m, const int *__restrict__ sums, int *__restrict__ out) {
+    long long base = (long long)blockIdx.x * kScanBlock + (long long)threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < m ? in[base + k] : 0;
+        s += v[k];
+    }
+    int total;
+    int run = block_excl_scan(s, &total) + sums[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < m) {
+            out[base + k] = run;
+            run += v[k];
+        }
+}
+
+// out[0..m) = exclusive scan of in[0..m); out may alias in
+di_status exclusive_scan(const int *in, int *out, long long m, cudaStream_t s) {
+    if (m <= 0) return DI_OK;
+    int nb = ceil_div(m, kScanBlock);
+    int *sums = nullptr;
+    DI_CUDA(cudaMallocAsync(&sums, sizeof(int) * (size_t)nb, s));
+    k_scan_reduce<<<nb, 256, 0, s>>>(in, m, sums);
+    k_scan_top<<<1, 256, 0, s>>>(nb, sums);
+    k_scan_down<<<nb, 256, 0, s>>>(in, m, sums, out);
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(sums, s);
+    if (e != cudaSuccess) return cuda_fail(e, "exclusive_scan");
+    return DI_OK;
+}
+
+// ------------------------------------------------- stable LSD radix pass
+
+constexpr int kRadixThreads = 256;
+constexpr int kRadixItems = 8;                       // per thread
+constexpr int kRadixTile = kRadixThreads * kRadixItems;
+constexpr int kRadixWarps = kRadixThreads / 32;
+
+__global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const int *__restrict__ keys, long long m, int shift,
+                                                              int mask, int nb, int *__restrict__ hist, int ntiles) {
+    __shared__ int h[257];
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    long long base = (long long)blockIdx.x * kRadixTile;
+#pragma unroll
+    for (int it = 0; it < kRadixItems; ++it) {
+        long long idx = base + it * kRadixThreads + threadIdx.x;
+        if (idx < m) atomicAdd(&h[(keys[idx] >> shift) & mask], 1);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[(long long)b * ntiles + blockIdx.x] = h[b];
+}
+
+// Stable scatter: items of a tile keep their input order within each digit.
+// Warp w owns items [tile + w*256, tile + (w+1)*256) in iterations of 32.
+__global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const int *__restrict__ keys_in,
+                                                                 const int *__restrict__ vals_in,
+                                                                 int *__restrict__ keys_out, int *__restrict__ vals_out,
+                                                                 long long m, int shift, int mask, int nb,
+                                                                 const int *__restrict__ offs, int ntiles) {
+    __shared__ int wc[kRadixWarps][257];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int b = threadIdx.x; b < kRadixWarps * 257; b += blockDim.x) (&wc[0][0])[b] = 0;
+    __syncthreads();
+    long long base = (long long)blockIdx.x * kRadixTile + (long long)w * (32 * kRadixItems);
+    int key[kRadixItems], val[kRadixItems], dig[kRadixItems], rnk[kRadixItems];
+    const unsigned lt = lanemask_lt();
+#pragma unroll
+    for (int it = 0; it < kRadixItems; ++it) {
+        long long idx = base + it * 32 + lane;
+        bool ok = idx < m;
+        key[it] = ok ? keys_in[idx] : 0;
+        val[it] = ok ? vals_in[idx] : 0;
+        dig[it] = ok ? ((key[it] >> shift) & mask) : nb;  // bucket nb collects the padding
+        unsigned peers = __match_any_sync(kFull, dig[it]);
+        int before = wc[w][dig[it]];
+        __syncwarp();
+        int r = __popc(peers & lt);
+        if (r == 0) wc[w][dig[it]] = before + __popc(peers);
+        __syncwarp();
+        rnk[it] = before + r;
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        int run = 0;
+        for (int ww = 0; ww < kRadixWarps; ++ww) {
+            int t = wc[ww][b];
+            wc[ww][b] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kRadixItems; ++it) {
+        if (dig[it] == nb) continue;
+        long long pos = (long long)offs[(long long)dig[it] * ntiles + blockIdx.x] + wc[w][dig[it]] + rnk[it];
+        keys_out[pos] = key[it];
+        vals_out[pos] = val[it];
+    }
+}
+
+// One stable counting-sort pass by digit (key >> shift) & mask, nb = mask + 1 <= 256 buckets.
+di_status radix_pass(const int *keys_in, const int *vals_in, int *keys_out, int *vals_out, long long m, int shift,
+                     int mask, cudaStream_t s) {
+    if (m <= 0) return DI_OK;
+    int nb = mask + 1;
+    int ntiles = ceil_div(m, kRadixTile);
+    long long hn = (long long)nb * ntiles;
+    int *hist = nullptr;
+    DI_CUDA(cudaMallocAsync(&hist, sizeof(int) * (size_t)hn, s));
+    k_radix_hist<<<ntiles, kRadixThreads, 0, s>>>(keys_in, m, shift, mask, nb, hist, ntiles);
+    di_status r = exclusive_scan(hist, hist, hn, s);
+    if (r == DI_OK) {
+        k_radix_scatter<<<ntiles, kRadixThreads, 0, s>>>(keys_in, vals_in, keys_out, vals_out, m, shift, mask, nb, hist,
+                                                         ntiles);
+    }
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(hist, s);
+    if (r != DI_OK) return r;
+    if (e != cudaSuccess) return cuda_fail(e, "radix_pass");
+    return DI_OK;
+}
+
+// --------------------------------------------------------------- transpose
+
+// source node of every edge position: the row whose range holds e
+__global__ void k_expand_rows(int n, long long nnz, const int *__restrict__ row_ptr, int *__restrict__ src) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = n;  // find the last i with row_ptr[i] <= e
+        while (hi - lo > 1) {
+            int mid = lo + (hi - lo) / 2;
+            if ((long long)row_ptr[mid] <= e) lo = mid; else hi = mid;
+        }
+        src[e] = lo;
+    }
+}
+
+__global__ void k_count_in(long long nnz, const int *__restrict__ col_idx, int *__restrict__ indeg) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (long long)gridDim.x * blockDim.x)
+        atomicAdd(&indeg[col_idx[e]], 1);
+}
+
+int grid_for(long long work, int threads, int num_sms) {
+    long long b = (work + threads - 1) / threads;
+    long long cap = (long long)num_sms * 16;
+    return (int)std::max(1LL, std::min(b, cap));
+}
+
+}  // namespace
+
+di_status validate_v(di_graph *g, const double *V_dev) {
+    cudaStream_t s = g->stream;
+    struct Tmp { int flags; int pad; double sum; };
+    Tmp *t = nullptr;
+    DI_CUDA(cudaMallocAsync(&t, sizeof(Tmp), s));
+    DI_CUDA(cudaMemsetAsync(t, 0, sizeof(Tmp), s));
+    k_validate_v<<<grid_for(g->n, 256, g->num_sms), 256, 0, s>>>(g->n, V_dev, &t->flags, &t->sum);
+    Tmp h{};
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, t, sizeof(Tmp), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(t, s);
+    if (e != cudaSuccess) return cuda_fail(e, "validate V");
+    if (h.flags & kVNonFinite) return set_error(DI_EINVAL, "V has a NaN or infinite entry");
+    if (h.flags & kVNeg) return set_error(DI_EINVAL, "V has a negative entry");
+    if (!(fabs(h.sum - 1.0) <= 1e-12))
+        return set_error(DI_EINVAL, "V must be normalized: |V|_1 = " + std::to_string(h.sum));
+    return DI_OK;
+}
+
+di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_dev) {
+    cudaStream_t s = g->stream;
+    const int n = g->n;
+    const long long L = g->nnz;
+    (void)row_ptr_dev;
+    (void)col_idx_dev;
+
+    // 1. validation of the CSR copy
+    {
+        int *flags = nullptr;
+        DI_CUDA(cudaMallocAsync(&flags, sizeof(int), s));
+        DI_CUDA(cudaMemsetAsync(flags, 0, sizeof(int), s));
+        k_validate_csr<<<grid_for(std::max<long long>(n, L), 256, g->num_sms), 256, 0, s>>>(n, L, g->row_ptr, g->col_idx,
+                                                                                          flags);
+        int hf = 0;
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFreeAsync(flags, s);
+        if (e != cudaSuccess) return cuda_fail(e, "validate CSR");
+        if (hf & kBadRowPtr0) return set_error(DI_EINVAL, "row_ptr[0] must be 0");
+        if (hf & kBadRowPtrN) return set_error(DI_EINVAL, "row_ptr[n] must equal nnz");
+        if (hf & kNotMonotone) return set_error(DI_EINVAL, "row_ptr must be non-decreasing");
+        if (hf & kColRange) return set_error(DI_EINVAL, "col_idx has an entry outside [0, n)");
+    }
+
+    // 2. out-degree bins and per-chunk frontier regions
+    DI_CUDA(cudaMallocAsync(&g->bin_of, sizeof(int) * (size_t)n, s));
+    k_out_bins<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, g->row_ptr, kOutCut1, kOutCut2, g->bin_of);
+    g->G = std::max(1, std::min(kMaxScanBlocks, ceil_div(n, kChunkAlign)));
+    g->chunk = ceil_div(ceil_div(n, g->G), kChunkAlign) * kChunkAlign;
+    g->G = ceil_div(n, g->chunk);
+    {
+        int *cnt = nullptr;
+        DI_CUDA(cudaMallocAsync(&cnt, sizeof(int) * 3 * (size_t)g->G, s));
+        DI_CUDA(cudaMallocAsync(&g->region, sizeof(int) * 3 * (size_t)(g->G + 1), s));
+        DI_CUDA(cudaMallocAsync(&g->fcount, sizeof(int) * 3 * (size_t)g->G, s));
+        DI_CUDA(cudaMemsetAsync(g->fcount, 0, sizeof(int) * 3 * (size_t)g->G, s));
+        k_chunk_bin_counts<<<g->G, 256, 0, s>>>(n, g->chunk, g->bin_of, cnt, g->G);
+        k_region_scan<<<1, 32, 0, s>>>(g->G, cnt, g->region);
+        std::vector<int> h(3 * (size_t)(g->G + 1));
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h.data(), g->region, sizeof(int) * h.size(), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFreeAsync(cnt, s);
+        if (e != cudaSuccess) return cuda_fail(e, "frontier regions");
+        int G = g->G;
+        int t1 = h[0 * (G + 1) + G], t2 = h[1 * (G + 1) + G] - t1, t3 = h[2 * (G + 1) + G] - t1 - t2;
+        g->bin_count[1] = t1;
+        g->bin_count[2] = t2;
+        g->bin_count[3] = t3;
+        g->bin_count[0] = n - t1 - t2 - t3;
+    }
+
+    // 3. in-link CSR: stable LSD radix sort of (target, source) pairs in source order
+    DI_CUDA(cudaMallocAsync(&g->in_ptr, sizeof(int) * (size_t)(n + 1), s));
+    DI_CUDA(cudaMallocAsync(&g->in_src, sizeof(int) * (size_t)std::max<long long>(L, 1), s));
+    DI_CUDA(cudaMemsetAsync(g->in_ptr, 0, sizeof(int) * (size_t)(n + 1), s));
+    if (L > 0) {
+        k_count_in<<<grid_for(L, 256, g->num_sms), 256, 0, s>>>(L, g->col_idx, g->in_ptr);
+        int *ka = nullptr, *kb = nullptr, *va = nullptr, *vtmp = nullptr;
+        DI_CUDA(cudaMallocAsync(&ka, sizeof(int) * (size_t)L, s));
+        DI_CUDA(cudaMallocAsync(&kb, sizeof(int) * (size_t)L, s));
+        DI_CUDA(cudaMallocAsync(&va, sizeof(int) * (size_t)L, s));
+        DI_CUDA(cudaMallocAsync(&vtmp, sizeof(int) * (size_t)L, s));
+        DI_CUDA(cudaMemcpyAsync(ka, g->col_idx, sizeof(int) * (size_t)L, cudaMemcpyDeviceToDevice, s));
+        k_expand_rows<<<grid_for(L, 256, g->num_sms), 256, 0, s>>>(n, L, g->row_ptr, va);
+        int bits = 1;
+        while (bits < 31 && (1LL << bits) < (long long)n) ++bits;
+        int passes = (bits + 7) / 8;
+        // keys ping-pong between ka and kb; values alternate between va and vtmp and
+        // the last pass writes them into in_src
+        int *kin = ka, *kout = kb, *vin = va, *vout = nullptr;
+        for (int p = 0; p < passes; ++p) {
+            bool last = (p == passes - 1);
+            vout = last ? g->in_src : (vin == va ? vtmp : va);
+            di_status r = radix_pass(kin, vin, kout, vout, L, 8 * p, 0xff, s);
+            if (r != DI_OK) return r;
+            std::swap(kin, kout);
+            vin = vout;
+        }
+        cudaFreeAsync(ka, s);
+        cudaFreeAsync(kb, s);
+        cudaFreeAsync(va, s);
+        cudaFreeAsync(vtmp, s);
+    }
+    {
+        di_status r = exclusive_scan(g->in_ptr, g->in_ptr, (long long)n + 1, s);
+        if (r != DI_OK) return r;
+    }
+
+    // 4. in-degree bins and the ids of each bin, ascending (one stable pass)
+    DI_CUDA(cudaMallocAsync(&g->in_bin_of, sizeof(int) * (size_t)n, s));
+    DI_CUDA(cudaMallocAsync(&g->pull_ids, sizeof(int) * (size_t)n, s));
+    k_in_bins<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, g->in_ptr, kInCut1, kInCut2, g->in_bin_of);
+    {
+        int *iota = nullptr, *ksorted = nullptr;
+        DI_CUDA(cudaMallocAsync(&iota, sizeof(int) * (size_t)n, s));
+        DI_CUDA(cudaMallocAsync(&ksorted, sizeof(int) * (size_t)n, s));
+        k_iota<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, iota);
+        di_status r = radix_pass(g->in_bin_of, iota, ksorted, g->pull_ids, n, 0, 3, s);
+        cudaFreeAsync(iota, s);
+        if (r != DI_OK) { cudaFreeAsync(ksorted, s); return r; }
+        // bin sizes: per-tile histograms of the bin ids, summed on the host
+        int counts[3] = {0, 0, 0};
+        int ntiles = ceil_div(n, kRadixTile);
+        int *th = nullptr;
+        DI_CUDA(cudaMallocAsync(&th, sizeof(int) * 4 * (size_t)ntiles, s));
+        k_radix_hist<<<ntiles, kRadixThreads, 0, s>>>(g->in_bin_of, n, 0, 3, 4, th, ntiles);
+        std::vector<int> hth(4 * (size_t)ntiles);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hth.data(), th, sizeof(int) * hth.size(), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFreeAsync(th, s);
+        cudaFreeAsync(ksorted, s);
+        if (e != cudaSuccess) return cuda_fail(e, "in-degree bins");
+        for (int b = 0; b < 3; ++b)
+            for (int t = 0; t < ntiles; ++t) counts[b] += hth[(size_t)b * ntiles + t];
+        for (int b = 0; b < 3; ++b) g->in_bin_count[b] = counts[b];
+        g->n_long_rows = counts[2];
+    }
+
+    // 5. chunk tasks of the longest in-rows
+    DI_CUDA(cudaMallocAsync(&g->long_prefix, sizeof(int) * (size_t)(g->n_long_rows + 1), s));
+    DI_CUDA(cudaMemsetAsync(g->long_prefix, 0, sizeof(int) * (size_t)(g->n_long_rows + 1), s));
+    if (g->n_long_rows > 0) {
+        const int *long_ids = g->pull_ids + g->in_bin_count[0] + g->in_bin_count[1];
+        k_long_tasks<<<grid_for(g->n_long_rows, 256, g->num_sms), 256, 0, s>>>(g->n_long_rows, long_ids, g->in_ptr,
+                                                                              kPullChunk, g->long_prefix);
+        di_status r = exclusive_scan(g->long_prefix, g->long_prefix, (long long)g->n_long_rows + 1, s);
+        if (r != DI_OK) return r;
+        int tot = 0;
+        DI_CUDA(cudaMemcpyAsync(&tot, g->long_prefix + g->n_long_rows, sizeof(int), cudaMemcpyDeviceToHost, s));
+        DI_CUDA(cudaStreamSynchronize(s));
+        g->n_long_tasks = tot;
+    }
+    DI_CUDA(cudaGetLastError());
+    return DI_OK;
+}
+
+}  // namespace diter

@@ -1,0 +1,172 @@
+// internal.h -- private structures of libditer shared by its translation units.
+//
+// Device layout of one graph (n nodes, L edges), all owned by di_graph:
+//   row_ptr int32[n+1], col_idx int32[L]        out-link CSR (the input, copied)
+//   in_ptr  int32[n+1], in_src  int32[L]        in-link CSR, sources ascending
+//   bin_of  int32[n]                            out-degree bin (0 dangling, 1 thread, 2 warp, 3 CTA)
+//   in_bin_of int32[n], pull_ids int32[n]       in-degree bin and ids grouped by it
+//   F64 / F32  [n padded to 4]                  fluid F (one of the two per solve)
+//   H       double[n]                           history H
+//   frontier FEntry[n - dangling]               per-sweep selected nodes; bin b, chunk c
+//                                               writes at base_b + region[b][c] + k
+//   X, Z[2]  double[n]                          power-iteration iterate and d*x/outdeg
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/diter.h"
+
+namespace diter {
+
+// ------------------------------------------------------------------ tunables
+constexpr int kScanThreads = 256;       // threads of the sweep scan / push CTAs
+constexpr int kScanVec = 2;             // fluid elements per thread per tile (16 B of FP64)
+constexpr int kScanTile = kScanThreads * kScanVec;
+constexpr int kChunkAlign = 1024;       // scan chunks are multiples of the FP32 tile (256 x float4)
+constexpr int kMaxScanBlocks = 152 * 8; // 8 CTAs per SM on 152 SMs
+constexpr int kOutCut1 = 8;             // out-degree <= cut1: one thread per source
+constexpr int kOutCut2 = 1024;          // out-degree <= cut2: one warp per source; above: whole CTA
+constexpr int kInCut1 = 8;              // in-degree <= cut1: one thread per row (pull)
+constexpr int kInCut2 = 2048;           // in-degree <= cut2: one warp per row; above: chunked
+constexpr int kPullChunk = 2048;        // in-links per chunk task for the longest rows
+constexpr int kTraceCap = 4096;         // sweep records kept when tracing
+
+// one selected node of a sweep: its out-link range and the amount each child receives
+struct __align__(16) FEntry {
+    int beg;    // row_ptr[i]
+    int deg;    // outdeg(i) > 0
+    double w;   // d * sent / outdeg(i)
+};
+
+// per-CTA results of the sweep scan, reduced in fixed order by the finalize kernel
+struct __align__(16) ScanPartial {
+    double l1;        // sum of F over the CTA's chunk before selection
+    double removed;   // (1-d)*sent for nodes with children, sent for dangling nodes
+    long long edges;  // out-links of the selected nodes
+    long long srcs;   // selected nodes
+    long long entries;// selected nodes with out-links (frontier entries written)
+    long long pad;
+};
+
+// device-resident control block of one solve
+struct SolveState {
+    double R;              // residual after the last sweep
+    double T;              // threshold of the next sweep
+    double tolR;           // stop when R <= tolR (= tol * (1 - d))
+    double beta;
+    double one_minus_d;
+    double l1_exact;       // exact |F|_1 written by the confirmation kernel
+    long long edges;       // cumulative out-links pushed
+    long long srcs;        // cumulative selected nodes
+    long long max_edges;
+    int sweeps;
+    int max_sweeps;
+    int done;              // 0 running, 1 converged, 2 limit reached, 3 non-finite residual
+    int trace_on;
+    int body_runs;         // executions of the finalize kernel (one per loop iteration)
+    int pad[3];
+};
+
+struct PowerState {
+    double delta;          // |X_k - X_{k-1}|_1 of the last product
+    double tol;            // stop when delta * d/(1-d) < tol
+    double d;
+    int iters;
+    int max_iters;
+    int done;              // 1 stop rule met, 2 limit reached, 3 non-finite
+    int cur;               // which Z buffer holds d*X/outdeg of the current iterate
+};
+
+struct PowerPartial {
+    double delta;
+    double pad;
+};
+
+}  // namespace diter
+
+struct di_graph {
+    int n = 0;
+    long long nnz = 0;
+    double d = 0.85;
+    int dev = 0;
+    int num_sms = 152;
+    cudaStream_t stream = nullptr;     // user stream
+    cudaStream_t cap = nullptr;        // private stream used for graph capture
+
+    // graph
+    int *row_ptr = nullptr, *col_idx = nullptr;
+    int *in_ptr = nullptr, *in_src = nullptr;
+    int *bin_of = nullptr, *in_bin_of = nullptr, *pull_ids = nullptr;
+    double *V = nullptr;               // NULL: uniform 1/n
+    int bin_count[4] = {0, 0, 0, 0};   // static out-degree bin sizes
+    int in_bin_count[3] = {0, 0, 0};
+    int n_long_rows = 0;               // rows of in-degree bin 2
+    int *long_prefix = nullptr;        // [n_long_rows + 1] exclusive prefix of chunk tasks
+    int n_long_tasks = 0;
+
+    // sweep structures
+    int G = 0;                         // scan CTAs
+    int chunk = 0;                     // nodes per scan CTA (multiple of kScanTile)
+    int *region = nullptr;             // [3][G+1]: exclusive offsets of bins 1..3 per chunk
+    int *fcount = nullptr;             // [3][G]: entries written per chunk in the last sweep
+    diter::FEntry *frontier = nullptr; // capacity n - dangling
+    double *F64 = nullptr;
+    float *F32 = nullptr;
+    double *H = nullptr;
+    diter::ScanPartial *part = nullptr;
+    diter::SolveState *st = nullptr;
+    di_sweep_record *trace = nullptr;
+    int last_prec = -1;
+    int last_trace_on = 0;
+    di_profile prof = {};
+    cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};
+
+    // power iteration
+    double *X = nullptr;
+    double *Z[2] = {nullptr, nullptr};
+    double *Ylong = nullptr;           // accumulators of the chunked rows
+    diter::PowerPartial *ppart = nullptr;
+    diter::PowerState *pst = nullptr;
+    int pull_blocks[3] = {0, 0, 0};
+
+    // captured solve loops: [0] FP64 sweeps, [1] FP32-mixed sweeps, [2] power iteration
+    cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
+    cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
+
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    diter::SolveState *h_st = nullptr; // pinned host mirror
+    diter::PowerState *h_pst = nullptr;
+};
+
+namespace diter {
+
+// error plumbing (api.cu)
+di_status set_error(di_status s, const std::string &msg);
+di_status cuda_fail(cudaError_t e, const char *what);
+
+// graph ingest (graph_build.cu)
+di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_dev);
+di_status validate_v(di_graph *g, const double *V_dev);
+
+// sweeps (sweep.cu)
+di_status sweep_alloc(di_graph *g);
+di_status run_solve(di_graph *g, const di_solve_opts &o, const int *seeds_dev, const double *seed_w_dev, int nseeds,
+                    double wsum, double *H_out, bool out_on_device, di_stats *st);
+di_status copy_state(const di_graph *g, double *F_out, bool F_dev, double *H_out, bool H_dev);
+
+// power iteration (power.cu)
+di_status power_alloc(di_graph *g);
+di_status run_power(di_graph *g, double tol, int max_iter, double *X_out, bool out_on_device, di_stats *st);
+
+// helpers
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace diter
+
+#define DI_CUDA(call)                                                 \
+    do {                                                              \
+        cudaError_t _e = (call);                                      \
+        if (_e != cudaSuccess) return diter::cuda_fail(_e, #call);    \
+    } while (0)

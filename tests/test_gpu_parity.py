@@ -1,0 +1,291 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle, on seeded synthetic graphs.
+
+Bars (written in each test):
+  * CSR-derived structures (out-degrees, in-link lists, degree bins): bit-exact.
+  * FP64 D-iteration vs the oracle's snapshot sweeps with the same threshold
+    schedule: |H_gpu - H_oracle|_1 <= 1e-12 when both run to bound <= 1e-13,
+    and <= max(bounds) + 1e-12 at looser targets (both under-approximate X,
+    Theorem 2).  The sweep count and the elementary-step count agree exactly.
+  * FP32-mixed D-iteration: |H - H_oracle|_1 <= 2e-6.
+  * Power iteration: same number of products and |X - X_oracle|_1 <= 1e-12.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from oracle import ge
+from tests import graphs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+D = 0.85
+BETA = 0.5
+
+
+@pytest.fixture(scope="module")
+def di():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1202_6158_gb300 as di
+    di.load()
+    return di
+
+
+def case_graphs():
+    rng = np.random.default_rng(7)
+    out = {}
+    g = gg.uniform_graph(10000, 20, seed=1)
+    out["uniform_1e4"] = (g.n, g.row_ptr, g.col_idx)
+    g = gg.zipf_graph(1 << 14, kmax=5000, seed=2)
+    out["zipf_2e14_hubs"] = (g.n, g.row_ptr, g.col_idx)
+    g = gg.rmat_graph(12, 16, seed=3)
+    out["rmat_12"] = (g.n, g.row_ptr, g.col_idx)
+    rp, ci = graphs.star(3000)
+    out["star_3000"] = (3001, rp, ci)
+    rp, ci = graphs.csr(5000, [(i, 4999) for i in range(4999)] + [(4999, 0)])
+    out["in_hub_5000"] = (5000, rp, ci)
+    rp, ci = graphs.random_graph(1025, 0.1, 12, rng)
+    out["random_1025_multi"] = (1025, rp, ci)
+    rp, ci = graphs.complete(50)
+    out["complete_50"] = (50, rp, ci)
+    out["empty_7"] = (7, np.zeros(8, np.int32), np.zeros(0, np.int32))
+    return out
+
+
+CASES = case_graphs()
+
+
+# ------------------------------------------------------------- graph ingest
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_derived_structures_bit_exact(di, name):
+    n, rp, ci = CASES[name]
+    with di.DiGraph(n, rp, ci, D) as g:
+        ex = g.export()
+    c1, c2, ic1, ic2 = ex["cuts"].tolist()
+    assert np.array_equal(ex["outdeg"], oracle.outdeg(n, rp))
+    in_ptr, in_src = oracle.transpose(n, rp, ci)
+    assert np.array_equal(ex["in_ptr"], in_ptr)
+    assert np.array_equal(ex["in_src"], in_src)
+    bin_of, _, _ = oracle.bins(n, rp, [0, c1, c2])
+    assert np.array_equal(ex["bin_of"], bin_of)
+    in_bin_of, _, _ = oracle.bins(n, in_ptr, [ic1, ic2])
+    assert np.array_equal(ex["in_bin_of"], in_bin_of)
+
+
+# ------------------------------------------------------------ D-iteration
+
+def _solve(di, n, rp, ci, tol, V=None, **kw):
+    with di.DiGraph(n, rp, ci, D, V=V) as g:
+        H, st = g.solve(tol, beta=kw.pop("beta", BETA), **kw)
+        F, H2 = g.state()
+        tr = g.trace() if kw.get("trace") else None
+    assert np.array_equal(H, H2)
+    return H, F, st, tr
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fp64_tight_parity_with_oracle_sweeps(di, name):
+    """Both to bound <= 1e-13: |H_gpu - H_oracle|_1 <= 1e-12, same sweeps and elementary steps."""
+    n, rp, ci = CASES[name]
+    V = gg.uniform_v(n)
+    tol = 1e-13
+    H, F, st, _ = _solve(di, n, rp, ci, tol)
+    r = oracle.diter(n, rp, ci, D, V, tol, mode="sweep", beta=BETA)
+    assert st["converged"] == 1 and st["bound"] <= tol
+    assert abs(st["l1_F"] - np.abs(F).sum()) <= 1e-15 + 1e-12 * st["l1_F"]
+    assert np.abs(H - r.H).sum() <= 1e-12
+    assert st["sweeps"] == r.sweeps
+    assert st["edges_pushed"] == r.edges
+    assert st["sources_pushed"] == r.pushes
+    assert np.all(F >= 0) and np.all(H >= 0)
+
+
+def test_config1_target_and_order_independence(di):
+    """Uniform-degree graph, d=0.85, V=1/N, stop at |F|_1 < 1e-10: within bounds of every oracle order."""
+    n, rp, ci = CASES["uniform_1e4"]
+    V = gg.uniform_v(n)
+    tol = 1e-10 / (1 - D)
+    H, F, st, _ = _solve(di, n, rp, ci, tol)
+    assert st["l1_F"] < 1e-10
+    for mode in ["sweep", "thresh", "per", "rand"]:
+        r = oracle.diter(n, rp, ci, D, V, tol, mode=mode, beta=BETA, seed=5)
+        assert np.abs(H - r.H).sum() <= max(st["bound"], r.l1F / (1 - D)) + 1e-12, mode
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_against_gaussian_elimination(di, seed):
+    """Small graphs with multi-edges, self-loops, dangling nodes: |X - H|_1 <= bound, 0 <= H <= X."""
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(2, 300))
+    rp, ci = graphs.random_graph(n, 0.15, 9, rng)
+    V = graphs.random_v(n, rng)
+    X = ge.pagerank_dense(n, rp, ci, D, V)
+    H, F, st, _ = _solve(di, n, rp, ci, 1e-12, V=V)
+    assert np.abs(X - H).sum() <= st["bound"] + 1e-14
+    assert np.all(H <= X + 1e-15)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 1023, 1024, 1025, 4097, 70001])
+def test_ragged_sizes(di, n):
+    rng = np.random.default_rng(n)
+    rp, ci = graphs.random_graph(n, 0.1, 6, rng)
+    V = gg.uniform_v(n)
+    H, F, st, _ = _solve(di, n, rp, ci, 1e-13)
+    r = oracle.diter(n, rp, ci, D, V, 1e-13, mode="sweep", beta=BETA)
+    assert np.abs(H - r.H).sum() <= 1e-12
+    assert st["sweeps"] == r.sweeps
+
+
+def test_theorem1_on_device_state(di):
+    """After k sweeps the device state satisfies H + F = F_0 + dPH (Theorem 1)."""
+    import scipy.sparse as sp
+    n, rp, ci = CASES["zipf_2e14_hubs"]
+    deg = np.diff(rp)
+    src = np.repeat(np.arange(n), deg)
+    P = sp.csr_matrix((1.0 / deg[src], (ci, src)), shape=(n, n))
+    F0 = (1 - D) * gg.uniform_v(n)
+    for k in [1, 2, 5, 20]:
+        H, F, st, _ = _solve(di, n, rp, ci, 1e-14, max_sweeps=k, allow_unconverged=True)
+        assert st["sweeps"] == k
+        resid = H + F - F0 - D * (P @ H)
+        assert np.abs(resid).max() <= 1e-15
+        r = oracle.diter(n, rp, ci, D, gg.uniform_v(n), 0.0, mode="sweep", beta=BETA, max_pushes=st["sources_pushed"])
+        assert np.abs(H - r.H).sum() <= 1e-13
+        assert np.abs(F - r.F).sum() <= 1e-13
+
+
+def test_trace_records(di):
+    n, rp, ci = CASES["rmat_12"]
+    H, F, st, tr = _solve(di, n, rp, ci, 1e-10, trace=1)
+    assert len(tr) == st["sweeps"]
+    assert sum(t["edges"] for t in tr) == st["edges_pushed"]
+    assert all(tr[k + 1]["l1_F"] <= tr[k]["l1_F"] * (1 + 1e-12) for k in range(len(tr) - 1))
+    assert tr[-1]["R"] <= 1e-10 * (1 - D)
+
+
+def test_fp32_mixed_precision(di):
+    """FP32 fluid and pushes, FP64 H and residual: |H - H_oracle|_1 <= 2e-6."""
+    for name in ["uniform_1e4", "zipf_2e14_hubs", "rmat_12"]:
+        n, rp, ci = CASES[name]
+        V = gg.uniform_v(n)
+        H, F, st, _ = _solve(di, n, rp, ci, 1e-7, prec=di.DI_FP32_MIXED)
+        r = oracle.diter(n, rp, ci, D, V, 1e-12, mode="sweep", beta=BETA)
+        assert np.abs(H - r.H).sum() <= 2e-6, name
+        assert st["bound"] <= 1e-7 * (1 + 1e-6)
+
+
+def test_normalized_output(di):
+    n, rp, ci = CASES["uniform_1e4"]
+    with di.DiGraph(n, rp, ci, D) as g:
+        H, st = g.solve(1e-10, normalize=1)
+        Hr, _ = g.solve(1e-10)
+    assert abs(H.sum() - 1.0) < 1e-13
+    assert np.allclose(H, Hr / Hr.sum(), rtol=1e-14, atol=0)
+
+
+def test_personalized_query(di):
+    n, rp, ci = CASES["rmat_12"]
+    seeds = gg.seed_set(n, 1, 32, seed=11, q=0)
+    V = np.zeros(n)
+    V[seeds] = 1.0 / len(seeds)
+    with di.DiGraph(n, rp, ci, D) as g:
+        H, st = g.query(seeds, 1e-12)
+        w = np.arange(1, len(seeds) + 1, dtype=np.float64)
+        Hw, stw = g.query(seeds, 1e-12, w=w)
+    r = oracle.diter(n, rp, ci, D, V, 1e-12, mode="sweep", beta=BETA)
+    assert np.abs(H - r.H).sum() <= max(st["bound"], r.l1F / (1 - D)) + 1e-12
+    Vw = np.zeros(n)
+    Vw[seeds] = w / w.sum()
+    rw = oracle.diter(n, rp, ci, D, Vw, 1e-12, mode="sweep", beta=BETA)
+    assert np.abs(Hw - rw.H).sum() <= max(stw["bound"], rw.l1F / (1 - D)) + 1e-12
+
+
+def test_explicit_v(di):
+    n, rp, ci = CASES["zipf_2e14_hubs"]
+    rng = np.random.default_rng(3)
+    V = graphs.random_v(n, rng)
+    H, F, st, _ = _solve(di, n, rp, ci, 1e-13, V=V)
+    r = oracle.diter(n, rp, ci, D, V, 1e-13, mode="sweep", beta=BETA)
+    assert np.abs(H - r.H).sum() <= 1e-12
+
+
+def test_device_buffers(di):
+    n, rp, ci = CASES["rmat_12"]
+    dev = torch.device("cuda")
+    rp_t = torch.from_numpy(rp).to(dev)
+    ci_t = torch.from_numpy(ci).to(dev)
+    H_t = torch.empty(n, dtype=torch.float64, device=dev)
+    with di.DiGraph(n, rp_t, ci_t, D) as g:
+        g.solve(1e-12, H_out=H_t)
+        torch.cuda.synchronize()
+        H_host, _ = g.solve(1e-12)
+    assert np.abs(H_t.cpu().numpy() - H_host).sum() <= 1e-13
+
+
+def test_limits_report_not_converged(di):
+    n, rp, ci = CASES["uniform_1e4"]
+    with di.DiGraph(n, rp, ci, D) as g:
+        H = np.empty(n)
+        rc, st = di.di_solve_ex(g.handle, H, 1e-12, max_edge_pushes=50000, allow_unconverged=True)
+        assert rc == di.DI_ENOTCONVERGED and not st["converged"]
+        assert st["edges_pushed"] >= 50000 and st["bound"] > 1e-12
+        rc, st2 = di.di_solve_ex(g.handle, H, 1e-12, max_sweeps=3, allow_unconverged=True)
+        assert rc == di.DI_ENOTCONVERGED and st2["sweeps"] == 3
+        with pytest.raises(di.DiError):
+            g.solve(1e-12, max_sweeps=3)
+        # a target met at the start needs no sweep (the while-test of ALGO-REF comes first)
+        _, st3 = g.solve(1.0)
+        assert st3["sweeps"] == 0 and st3["converged"]
+
+
+def test_invalid_inputs(di):
+    n, rp, ci = CASES["rmat_12"]
+    bad = ci.copy()
+    bad[5] = n
+    with pytest.raises(di.DiError, match="col_idx"):
+        di.DiGraph(n, rp, bad, D)
+    rp2 = rp.copy()
+    rp2[10], rp2[11] = rp2[11], rp2[10] - 1
+    with pytest.raises(di.DiError):
+        di.DiGraph(n, rp2, ci, D)
+    V = gg.uniform_v(n)
+    V[0] = -V[0]
+    with pytest.raises(di.DiError, match="negative"):
+        di.DiGraph(n, rp, ci, D, V=V)
+    V = gg.uniform_v(n) * 1.01
+    with pytest.raises(di.DiError, match="normalized"):
+        di.DiGraph(n, rp, ci, D, V=V)
+    with pytest.raises(di.DiError):
+        di.DiGraph(n, rp, ci, 1.0)
+    with di.DiGraph(n, rp, ci, D) as g:
+        with pytest.raises(di.DiError):
+            g.solve(0.0)
+        with pytest.raises(di.DiError, match="seed"):
+            g.query([n + 3], 1e-6)
+
+
+# --------------------------------------------------------- power iteration
+
+@pytest.mark.parametrize("name", ["uniform_1e4", "zipf_2e14_hubs", "rmat_12", "in_hub_5000", "star_3000", "empty_7"])
+def test_power_iteration_matches_oracle(di, name):
+    n, rp, ci = CASES[name]
+    V = gg.uniform_v(n)
+    tol = 1e-12
+    with di.DiGraph(n, rp, ci, D) as g:
+        X, st = g.power(tol)
+    Xo, it, delta, ok = oracle.power(n, rp, ci, D, V, tol)
+    assert ok and st["converged"]
+    assert st["sweeps"] == it
+    assert np.abs(X - Xo).sum() <= 1e-12
+    assert st["edges_pushed"] == it * len(ci)
+
+
+def test_power_and_diter_agree(di):
+    n, rp, ci = CASES["zipf_2e14_hubs"]
+    with di.DiGraph(n, rp, ci, D) as g:
+        X, stp = g.power(1e-11)
+        H, std = g.solve(1e-11)
+    assert np.abs(X - H).sum() <= 2e-11

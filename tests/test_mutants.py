@@ -48,6 +48,8 @@ def _battery(lib):
         ok &= bool(abs(r.R - r.l1F) < 1e-14)
         r = oracle.diter(n, rp, ci, D, V, 0.0, mode=mode, max_pushes=30, lib=lib)
         ok &= bool(np.abs(r.H + r.F - (1 - D) * V - D * P @ r.H).max() < 1e-15)
+        # within a sweep (or fewer than N picks) R is the decremented value of ALGO-REF
+        ok &= bool(abs(r.R - r.l1F) < 1e-15)
     Xp, it, delta, conv = oracle.power(n, rp, ci, D, V, 1e-11, lib=lib)
     ok &= bool(conv and np.abs(X - Xp).sum() <= 1e-11)
     in_ptr, in_src = oracle.transpose(n, rp, ci, lib=lib)
