@@ -264,6 +264,10 @@ def main():
     p_edges = pst["edges_pushed"]
     agree = float((H - X).abs().sum().item())
 
+    # ---- profiled power iteration: pull kernel CUDA-event time
+    _, ppst = G.power(tol, X_out=X, profile=1)
+    pull_bytes_iter = g.nnz * (4 + 8) + g.n * (4 + 4 + 3 * 8 + 8)   # in_src + gather, per row: id, in_ptr, x rw, z, 1/deg
+
     # ---- profiled solve: per-kernel CUDA-event times and algorithmic bytes from the trace
     G.solve(tol, H_out=H, beta=args.beta, profile=1, trace=1)
     prof = G.profile()
@@ -276,6 +280,7 @@ def main():
         "push": {"ms": prof["push_ms"], "launches": prof["sweeps"], "alg_bytes": push_bytes},
         "scan": {"ms": prof["scan_ms"], "launches": prof["sweeps"], "alg_bytes": scan_bytes},
     }
+    pull = {"ms": ppst["pull_ms"], "launches": ppst["sweeps"], "alg_bytes": pull_bytes_iter * ppst["sweeps"]}
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     kd = kernels[dom]
     achieved = kd["alg_bytes"] / (kd["ms"] * 1e-3) / 1e9 if kd["ms"] > 0 else None
@@ -288,7 +293,7 @@ def main():
                 "avg_launch_us": 1e3 * kd["ms"] / max(1, kd["launches"]),
                 "per_kernel": {k: {"ms_total": v["ms"], "launches": v["launches"],
                                    "GBps": v["alg_bytes"] / (v["ms"] * 1e-3) / 1e9 if v["ms"] > 0 else None}
-                               for k, v in kernels.items()},
+                               for k, v in list(kernels.items()) + [("pull (power iteration)", pull)]},
                 "finalize_ms_total": prof["finalize_ms"]}
 
     # ---- end to end through the C ABI with pinned host buffers

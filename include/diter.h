@@ -91,6 +91,8 @@ typedef struct {
     int64_t sources;       /* nodes selected */
     int64_t edges;         /* out-links pushed */
     int64_t pushed;        /* selected nodes with at least one out-link (frontier entries) */
+    double scan_ms;        /* CUDA-event time of the sweep's scan kernel (profiled solves, else 0) */
+    double push_ms;        /* CUDA-event time of the sweep's push kernel (profiled solves, else 0) */
 } di_sweep_record;
 
 typedef struct {
@@ -141,6 +143,14 @@ di_status di_graph_info(const di_graph *g, int32_t *n, int64_t *nnz, double *d);
 di_status di_graph_export(const di_graph *g, int32_t *outdeg, int32_t *in_ptr, int32_t *in_src, int32_t *bin_of,
                           int32_t *in_bin_of, int32_t *cuts);
 
+/*
+ * The hot targets of a graph: the (at most 256) nodes with the largest
+ * in-degree, at least 32, ties broken by the lower id, in that order.  The push
+ * kernel sums the fluid sent to them in shared memory before adding it to F.
+ *   ids    host or device int32[256] (may be NULL); *count receives how many
+ */
+di_status di_graph_hot_targets(const di_graph *g, int32_t *ids, int32_t *count);
+
 /* ------------------------------------------------------------------ solves */
 
 /*
@@ -178,6 +188,15 @@ di_status di_query(di_graph *g, const int32_t *seeds, const double *w, int32_t n
  * st->sweeps counts products, st->edges_pushed = products * nnz.
  */
 di_status di_power(di_graph *g, double tol, int32_t max_iter, double *X_out, di_stats *st);
+
+/*
+ * di_power with a profiling switch.  profile = 1 launches each product's two
+ * kernels (pull, finalize) from the host with CUDA events around each, instead
+ * of the captured graph loop; the summed event times are written to *pull_ms and
+ * *finalize_ms (either may be NULL).  Results are identical to di_power.
+ */
+di_status di_power_ex(di_graph *g, double tol, int32_t max_iter, int32_t profile, double *X_out, di_stats *st,
+                      double *pull_ms, double *finalize_ms);
 
 /*
  * Per-sweep records of the last solve made with opts.trace = 1.

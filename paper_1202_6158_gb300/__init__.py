@@ -22,7 +22,7 @@ from ._lib import (DI_EINVAL, DI_ENOTCONVERGED, DI_FP32_MIXED, DI_FP64, DI_OK, D
                    di_solve_opts, di_stats, di_sweep_record, ptr)
 
 __all__ = ["DiGraph", "DiError", "DI_FP64", "DI_FP32_MIXED", "DI_OK", "DI_EINVAL", "DI_ENOTCONVERGED",
-           "di_graph_create", "di_free", "di_solve", "di_solve_ex", "di_query", "di_power", "di_graph_export",
+           "di_graph_create", "di_free", "di_solve", "di_solve_ex", "di_query", "di_power", "di_power_ex", "di_graph_export",
            "di_get_trace", "di_get_state", "di_get_profile", "di_version", "load"]
 
 
@@ -81,6 +81,17 @@ def di_power(handle, tol, X_out, max_iter=0, allow_unconverged=False):
     ok = (DI_OK, DI_ENOTCONVERGED) if allow_unconverged else (DI_OK,)
     rc = check(load().di_power(handle, float(tol), int(max_iter), ptr(X_out), ctypes.byref(st)), ok)
     return rc, st.as_dict()
+
+
+def di_power_ex(handle, tol, X_out, max_iter=0, profile=0, allow_unconverged=False):
+    st = di_stats()
+    pm, fm = ctypes.c_double(0), ctypes.c_double(0)
+    ok = (DI_OK, DI_ENOTCONVERGED) if allow_unconverged else (DI_OK,)
+    rc = check(load().di_power_ex(handle, float(tol), int(max_iter), int(profile), ptr(X_out), ctypes.byref(st),
+                                  ctypes.byref(pm), ctypes.byref(fm)), ok)
+    d = st.as_dict()
+    d["pull_ms"], d["finalize_ms"] = pm.value, fm.value
+    return rc, d
 
 
 def di_graph_export(handle, outdeg=None, in_ptr=None, in_src=None, bin_of=None, in_bin_of=None, cuts=None):
@@ -149,9 +160,9 @@ class DiGraph:
         st = di_query(self.handle, s, ww, tol, H, prec)
         return H, st
 
-    def power(self, tol, X_out=None, max_iter=0, allow_unconverged=False):
+    def power(self, tol, X_out=None, max_iter=0, allow_unconverged=False, profile=0):
         X = X_out if X_out is not None else np.empty(self.n, dtype=np.float64)
-        _rc, st = di_power(self.handle, tol, X, max_iter, allow_unconverged)
+        _rc, st = di_power_ex(self.handle, tol, X, max_iter, profile, allow_unconverged)
         return X, st
 
     def export(self):
@@ -162,6 +173,12 @@ class DiGraph:
         di_graph_export(self.handle, **out)
         out["in_src"] = out["in_src"][:L]
         return out
+
+    def hot_targets(self):
+        ids = np.empty(256, np.int32)
+        cnt = ctypes.c_int32(0)
+        check(load().di_graph_hot_targets(self.handle, ptr(ids), ctypes.byref(cnt)))
+        return ids[:cnt.value].copy()
 
     def trace(self, cap=4096):
         return di_get_trace(self.handle, cap)

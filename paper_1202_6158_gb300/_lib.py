@@ -45,7 +45,8 @@ class di_solve_opts(ctypes.Structure):
 
 class di_sweep_record(ctypes.Structure):
     _fields_ = [("l1_F", ctypes.c_double), ("removed", ctypes.c_double), ("R", ctypes.c_double), ("T", ctypes.c_double),
-                ("sources", ctypes.c_int64), ("edges", ctypes.c_int64), ("pushed", ctypes.c_int64)]
+                ("sources", ctypes.c_int64), ("edges", ctypes.c_int64), ("pushed", ctypes.c_int64),
+                ("scan_ms", ctypes.c_double), ("push_ms", ctypes.c_double)]
 
 
 class di_profile(ctypes.Structure):
@@ -70,10 +71,13 @@ def load(path: str = LIB_PATH):
         "di_free": ([vp], None),
         "di_graph_info": ([vp, vp, vp, vp], ctypes.c_int),
         "di_graph_export": ([vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "di_graph_hot_targets": ([vp, vp, ctypes.POINTER(i32)], ctypes.c_int),
         "di_solve": ([vp, f64, i64, ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(di_stats)], ctypes.c_int),
         "di_solve_ex": ([vp, ctypes.POINTER(di_solve_opts), vp, ctypes.POINTER(di_stats)], ctypes.c_int),
         "di_query": ([vp, vp, vp, i32, f64, ctypes.c_int, vp, ctypes.POINTER(di_stats)], ctypes.c_int),
         "di_power": ([vp, f64, i32, vp, ctypes.POINTER(di_stats)], ctypes.c_int),
+        "di_power_ex": ([vp, f64, i32, i32, vp, ctypes.POINTER(di_stats), ctypes.POINTER(f64), ctypes.POINTER(f64)],
+                        ctypes.c_int),
         "di_get_trace": ([vp, vp, i32, ctypes.POINTER(i32)], ctypes.c_int),
         "di_get_state": ([vp, vp, vp], ctypes.c_int),
         "di_get_profile": ([vp, ctypes.POINTER(di_profile)], ctypes.c_int),

@@ -53,6 +53,7 @@ static void free_graph(di_graph *g) {
         if (g->graph[k]) cudaGraphDestroy(g->graph[k]);
     }
     void *bufs[] = {g->row_ptr, g->col_idx, g->in_ptr, g->in_src, g->bin_of, g->in_bin_of, g->pull_ids, g->V,
+                    g->inv_deg, g->inv_deg32, g->hot_ids,
                     g->long_prefix, g->region, g->fcount, g->frontier, g->F64, g->F32, g->H, g->part, g->st,
                     g->trace, g->X, g->Z[0], g->Z[1], g->Ylong, g->ppart, g->pst};
     for (void *b : bufs)
@@ -65,6 +66,7 @@ static void free_graph(di_graph *g) {
     for (int k = 0; k < 4; ++k)
         if (g->pev[k]) cudaEventDestroy(g->pev[k]);
     if (g->cap) cudaStreamDestroy(g->cap);
+    delete[] g->sweep_ms;
     cudaGetLastError();
     delete g;
 }
@@ -120,6 +122,7 @@ di_status di_graph_create(int32_t n, const int32_t *row_ptr, const int32_t *col_
     if ((e = cudaMallocHost(&g->h_st, sizeof(SolveState))) != cudaSuccess) return fail(cuda_fail(e, "cudaMallocHost"));
     if ((e = cudaMallocHost(&g->h_pst, sizeof(PowerState))) != cudaSuccess) return fail(cuda_fail(e, "cudaMallocHost"));
     memset(g->h_st, 0, sizeof(SolveState));
+    g->sweep_ms = new float[2 * kTraceCap]();
     memset(g->h_pst, 0, sizeof(PowerState));
     cudaStream_t s = g->stream;
     if ((e = cudaMallocAsync(&g->row_ptr, sizeof(int) * (size_t)(n + 1), s)) != cudaSuccess)
@@ -203,6 +206,18 @@ di_status di_graph_export(const di_graph *g, int32_t *outdeg, int32_t *in_ptr, i
     return DI_OK;
 }
 
+di_status di_graph_hot_targets(const di_graph *g, int32_t *ids, int32_t *count) {
+    g_last_error.clear();
+    if (check_graph(g) != DI_OK) return DI_EINVAL;
+    if (count) *count = g->n_hot;
+    if (ids && g->n_hot > 0) {
+        di_status r = copy_out(ids, g->hot_ids, sizeof(int) * (size_t)g->n_hot, g->stream);
+        if (r != DI_OK) return r;
+        DI_CUDA(cudaStreamSynchronize(g->stream));
+    }
+    return DI_OK;
+}
+
 di_status di_solve_ex(di_graph *g, const di_solve_opts *opts, double *H_out, di_stats *st) {
     g_last_error.clear();
     if (check_graph(g) != DI_OK) return DI_EINVAL;
@@ -274,7 +289,19 @@ di_status di_power(di_graph *g, double tol, int32_t max_iter, double *X_out, di_
     if (check_graph(g) != DI_OK) return DI_EINVAL;
     if (!(tol > 0.0) || !std::isfinite(tol)) return set_error(DI_EINVAL, "tol must be finite and > 0");
     if (max_iter <= 0) max_iter = 100000;
-    return run_power(g, tol, max_iter, X_out, is_device_ptr(X_out), st);
+    return run_power(g, tol, max_iter, 0, X_out, is_device_ptr(X_out), st);
+}
+
+di_status di_power_ex(di_graph *g, double tol, int32_t max_iter, int32_t profile, double *X_out, di_stats *st,
+                      double *pull_ms, double *finalize_ms) {
+    g_last_error.clear();
+    if (check_graph(g) != DI_OK) return DI_EINVAL;
+    if (!(tol > 0.0) || !std::isfinite(tol)) return set_error(DI_EINVAL, "tol must be finite and > 0");
+    if (max_iter <= 0) max_iter = 100000;
+    di_status r = run_power(g, tol, max_iter, profile, X_out, is_device_ptr(X_out), st);
+    if (pull_ms) *pull_ms = g->pprof_ms[0];
+    if (finalize_ms) *finalize_ms = g->pprof_ms[1];
+    return r;
 }
 
 di_status di_get_trace(const di_graph *g, di_sweep_record *out, int32_t cap, int32_t *count) {
@@ -286,6 +313,11 @@ di_status di_get_trace(const di_graph *g, di_sweep_record *out, int32_t cap, int
     if (out && k > 0) {
         DI_CUDA(cudaMemcpyAsync(out, g->trace, sizeof(di_sweep_record) * k, cudaMemcpyDeviceToHost, g->stream));
         DI_CUDA(cudaStreamSynchronize(g->stream));
+        if (g->sweep_ms && g->prof.sweeps == avail)
+            for (int i = 0; i < k; ++i) {
+                out[i].scan_ms = g->sweep_ms[2 * i];
+                out[i].push_ms = g->sweep_ms[2 * i + 1];
+            }
     }
     return DI_OK;
 }

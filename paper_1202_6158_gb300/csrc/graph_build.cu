@@ -94,10 +94,15 @@ __global__ void k_validate_v(int n, const double *__restrict__ V, int *flags, do
 
 // ------------------------------------------------------- degrees and bins
 
-__global__ void k_out_bins(int n, const int *__restrict__ row_ptr, int cut1, int cut2, int *__restrict__ bin_of) {
+// out-degree bin and d/outdeg of every node (the one division per node the solves need)
+__global__ void k_out_bins(int n, const int *__restrict__ row_ptr, int cut1, int cut2, double d, int *__restrict__ bin_of,
+                           double *__restrict__ inv_deg, float *__restrict__ inv_deg32) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         int deg = row_ptr[i + 1] - row_ptr[i];
         bin_of[i] = deg == 0 ? 0 : (deg <= cut1 ? 1 : (deg <= cut2 ? 2 : 3));
+        double w = deg ? d / (double)deg : 0.0;
+        inv_deg[i] = w;
+        inv_deg32[i] = (float)w;
     }
 }
 
@@ -335,6 +340,37 @@ __global__ void k_count_in(long long nnz, const int *__restrict__ col_idx, int *
         atomicAdd(&indeg[col_idx[e]], 1);
 }
 
+// key that sorts nodes by in-degree, largest first (stable: ties keep ascending ids)
+__global__ void k_indeg_key(int n, const int *__restrict__ in_ptr, int *__restrict__ key) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        key[i] = 0x7fffffff - (in_ptr[i + 1] - in_ptr[i]);
+}
+
+__global__ void k_fill(long long m, int v, int *__restrict__ out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x)
+        out[i] = v;
+}
+
+__global__ void k_hot_slots(int k, const int *__restrict__ hot_ids, int *__restrict__ slot_of) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < k; s += gridDim.x * blockDim.x) slot_of[hot_ids[s]] = s;
+}
+
+// re-encode edges into hot targets as -1 - slot (the push keeps those sums in shared memory)
+__global__ void k_encode_hot(long long nnz, const int *__restrict__ slot_of, int *__restrict__ col_idx) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (long long)gridDim.x * blockDim.x) {
+        const int s = slot_of[col_idx[e]];
+        if (s >= 0) col_idx[e] = -1 - s;
+    }
+}
+
+// number of the first k sorted ids whose in-degree reaches the minimum
+__global__ void k_count_hot(int k, const int *__restrict__ sorted_key, int min_deg, int *__restrict__ count) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int c = 0;
+    while (c < k && 0x7fffffff - sorted_key[c] >= min_deg) ++c;
+    *count = c;
+}
+
 int grid_for(long long work, int threads, int num_sms) {
     long long b = (work + threads - 1) / threads;
     long long cap = (long long)num_sms * 16;
@@ -391,8 +427,12 @@ di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_de
 
     // 2. out-degree bins and per-chunk frontier regions
     DI_CUDA(cudaMallocAsync(&g->bin_of, sizeof(int) * (size_t)n, s));
-    k_out_bins<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, g->row_ptr, kOutCut1, kOutCut2, g->bin_of);
-    g->G = std::max(1, std::min(kMaxScanBlocks, ceil_div(n, kChunkAlign)));
+    DI_CUDA(cudaMallocAsync(&g->inv_deg, sizeof(double) * (size_t)n, s));
+    DI_CUDA(cudaMallocAsync(&g->inv_deg32, sizeof(float) * (size_t)n, s));
+    k_out_bins<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, g->row_ptr, kOutCut1, kOutCut2, g->d, g->bin_of,
+                                                           g->inv_deg, g->inv_deg32);
+    // one wave of scan CTAs (every chunk resident at once), at most kMaxScanBlocks
+    g->G = std::max(1, std::min(std::min(kMaxScanBlocks, g->num_sms * scan_blocks_per_sm()), ceil_div(n, kChunkAlign)));
     g->chunk = ceil_div(ceil_div(n, g->G), kChunkAlign) * kChunkAlign;
     g->G = ceil_div(n, g->chunk);
     {
@@ -499,6 +539,44 @@ di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_de
         DI_CUDA(cudaMemcpyAsync(&tot, g->long_prefix + g->n_long_rows, sizeof(int), cudaMemcpyDeviceToHost, s));
         DI_CUDA(cudaStreamSynchronize(s));
         g->n_long_tasks = tot;
+    }
+    // 6. hot targets: the kHotSlots largest in-degrees (at least kHotMinInDeg), ties by lower id;
+    //    their edges are re-encoded so the push sums them in shared memory
+    DI_CUDA(cudaMallocAsync(&g->hot_ids, sizeof(int) * kHotSlots, s));
+    g->n_hot = 0;
+    if (L > 0) {
+        int *ka = nullptr, *kb = nullptr, *va = nullptr, *vb = nullptr, *cnt = nullptr;
+        DI_CUDA(cudaMallocAsync(&ka, sizeof(int) * (size_t)n, s));
+        DI_CUDA(cudaMallocAsync(&kb, sizeof(int) * (size_t)n, s));
+        DI_CUDA(cudaMallocAsync(&va, sizeof(int) * (size_t)n, s));
+        DI_CUDA(cudaMallocAsync(&vb, sizeof(int) * (size_t)n, s));
+        DI_CUDA(cudaMallocAsync(&cnt, sizeof(int), s));
+        k_indeg_key<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, g->in_ptr, ka);
+        k_iota<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, va);
+        for (int p = 0; p < 4; ++p) {
+            di_status r = radix_pass(ka, va, kb, vb, n, 8 * p, 0xff, s);
+            if (r != DI_OK) return r;
+            std::swap(ka, kb);
+            std::swap(va, vb);
+        }
+        const int k = std::min(kHotSlots, n);
+        k_count_hot<<<1, 32, 0, s>>>(k, ka, kHotMinInDeg, cnt);
+        int hk = 0;
+        DI_CUDA(cudaMemcpyAsync(&hk, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+        DI_CUDA(cudaStreamSynchronize(s));
+        g->n_hot = hk;
+        if (hk > 0) {
+            DI_CUDA(cudaMemcpyAsync(g->hot_ids, va, sizeof(int) * hk, cudaMemcpyDeviceToDevice, s));
+            int *slot_of = kb;  // reuse: n ints
+            k_fill<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, -1, slot_of);
+            k_hot_slots<<<1, 256, 0, s>>>(hk, g->hot_ids, slot_of);
+            k_encode_hot<<<grid_for(L, 256, g->num_sms), 256, 0, s>>>(L, slot_of, g->col_idx);
+        }
+        cudaFreeAsync(ka, s);
+        cudaFreeAsync(kb, s);
+        cudaFreeAsync(va, s);
+        cudaFreeAsync(vb, s);
+        cudaFreeAsync(cnt, s);
     }
     DI_CUDA(cudaGetLastError());
     return DI_OK;

@@ -1,7 +1,9 @@
 // internal.h -- private structures of libditer shared by its translation units.
 //
 // Device layout of one graph (n nodes, L edges), all owned by di_graph:
-//   row_ptr int32[n+1], col_idx int32[L]        out-link CSR (the input, copied)
+//   row_ptr int32[n+1], col_idx int32[L]        out-link CSR (the input, copied); after ingest an
+//                                               edge to hot target slot s is stored as -1 - s
+//   hot_ids int32[n_hot]                        the hot targets (top in-degree, ties by lower id)
 //   in_ptr  int32[n+1], in_src  int32[L]        in-link CSR, sources ascending
 //   bin_of  int32[n]                            out-degree bin (0 dangling, 1 thread, 2 warp, 3 CTA)
 //   in_bin_of int32[n], pull_ids int32[n]       in-degree bin and ids grouped by it
@@ -32,22 +34,29 @@ constexpr int kInCut1 = 8;              // in-degree <= cut1: one thread per row
 constexpr int kInCut2 = 2048;           // in-degree <= cut2: one warp per row; above: chunked
 constexpr int kPullChunk = 2048;        // in-links per chunk task for the longest rows
 constexpr int kTraceCap = 4096;         // sweep records kept when tracing
+constexpr int kHotSlots = 256;          // most-linked-to targets accumulated in shared memory by the push
+constexpr int kHotMinInDeg = 32;        // a target needs at least this many in-links to get a slot
 
 // one selected node of a sweep: its out-link range and the amount each child receives
-struct __align__(16) FEntry {
+template <typename FT>
+struct __align__(16) FEntryT {
     int beg;    // row_ptr[i]
     int deg;    // outdeg(i) > 0
-    double w;   // d * sent / outdeg(i)
+    FT w;       // d * sent / outdeg(i), in the fluid's precision
 };
+using FEntry = FEntryT<double>;  // 16 bytes; the FP32 form is padded to the same size
 
-// per-CTA results of the sweep scan, reduced in fixed order by the finalize kernel
+// per-CTA results of the sweep scan, reduced in fixed order by the finalize kernel.
+// Fluid sums are 64-bit fixed point at the sweep's scale 2^-S (see fixed_scale).
 struct __align__(16) ScanPartial {
-    double l1;        // sum of F over the CTA's chunk before selection
-    double removed;   // (1-d)*sent for nodes with children, sent for dangling nodes
-    long long edges;  // out-links of the selected nodes
-    long long srcs;   // selected nodes
-    long long entries;// selected nodes with out-links (frontier entries written)
-    long long pad;
+    long long l1;      // sum of F over the CTA's chunk before selection (fixed point)
+    long long out;     // fluid of selected nodes with children (fixed point)
+    long long dng;     // fluid of selected dangling nodes (fixed point)
+    long long edges;   // out-links of the selected nodes
+    long long srcs;    // selected nodes
+    long long entries; // selected nodes with out-links (frontier entries written)
+    double l1d;        // FP64 sum, used by the exact confirmation kernel
+    double pad;
 };
 
 // device-resident control block of one solve
@@ -100,11 +109,15 @@ struct di_graph {
     int *in_ptr = nullptr, *in_src = nullptr;
     int *bin_of = nullptr, *in_bin_of = nullptr, *pull_ids = nullptr;
     double *V = nullptr;               // NULL: uniform 1/n
+    double *inv_deg = nullptr;         // d / outdeg(i), 0 for dangling nodes (FP64)
+    float *inv_deg32 = nullptr;        // the same rounded to FP32
     int bin_count[4] = {0, 0, 0, 0};   // static out-degree bin sizes
     int in_bin_count[3] = {0, 0, 0};
     int n_long_rows = 0;               // rows of in-degree bin 2
     int *long_prefix = nullptr;        // [n_long_rows + 1] exclusive prefix of chunk tasks
     int n_long_tasks = 0;
+    int *hot_ids = nullptr;            // [kHotSlots] node id of each hot slot
+    int n_hot = 0;
 
     // sweep structures
     int G = 0;                         // scan CTAs
@@ -121,6 +134,7 @@ struct di_graph {
     int last_prec = -1;
     int last_trace_on = 0;
     di_profile prof = {};
+    float *sweep_ms = nullptr;         // host: [kTraceCap][2] scan and push event times of a profiled solve
     cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};
 
     // power iteration
@@ -130,6 +144,7 @@ struct di_graph {
     diter::PowerPartial *ppart = nullptr;
     diter::PowerState *pst = nullptr;
     int pull_blocks[3] = {0, 0, 0};
+    double pprof_ms[2] = {0.0, 0.0};   // profiled power iteration: pull, finalize
 
     // captured solve loops: [0] FP64 sweeps, [1] FP32-mixed sweeps, [2] power iteration
     cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
@@ -158,7 +173,9 @@ di_status copy_state(const di_graph *g, double *F_out, bool F_dev, double *H_out
 
 // power iteration (power.cu)
 di_status power_alloc(di_graph *g);
-di_status run_power(di_graph *g, double tol, int max_iter, double *X_out, bool out_on_device, di_stats *st);
+di_status run_power(di_graph *g, double tol, int max_iter, int profile, double *X_out, bool out_on_device,
+                    di_stats *st);
+int scan_blocks_per_sm();
 
 // helpers
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }

@@ -43,25 +43,43 @@ __device__ double block_sum_d(double v, double *sh) {
 
 struct PullArgs {
     int n;
-    const int *in_ptr, *in_src, *row_ptr, *pull_ids, *long_ids, *long_prefix;
+    const int *in_ptr, *in_src, *pull_ids, *long_ids, *long_prefix;
+    const double *inv_deg;  // d / outdeg, 0 for dangling nodes
     int cnt0, cnt1, nlong, ntasks;
     int BA, BB;
     const double *V;  // NULL: uniform
-    double omd, d, u;
+    double omd, d, u, omdu;
     double *X, *Z0, *Z1, *Ylong;
     PowerPartial *pp;
     PowerState *pst;
 };
 
 __device__ __forceinline__ double v_of(const PullArgs &a, int j) { return a.V ? a.V[j] : a.u; }
+// (1-d) V_j
+__device__ __forceinline__ double omdv_of(const PullArgs &a, int j) { return a.V ? a.omd * a.V[j] : a.omdu; }
 
 // finish row j with its new value y; returns |y - x_j|
 __device__ __forceinline__ double finish_row(const PullArgs &a, double *zn, int j, double y) {
     double dlt = fabs(y - a.X[j]);
     a.X[j] = y;
-    const int deg = a.row_ptr[j + 1] - a.row_ptr[j];
-    zn[j] = deg ? (a.d * y) / (double)deg : 0.0;
+    zn[j] = y * a.inv_deg[j];
     return dlt;
+}
+
+// sum of z over a row of at most kInCut1 in-links: index loads, then gathers, then
+// the adds in ascending order
+__device__ __forceinline__ double short_row_sum(const PullArgs &a, const double *__restrict__ zc, int b, int e) {
+    int s[kInCut1];
+#pragma unroll
+    for (int t = 0; t < kInCut1; ++t) s[t] = b + t < e ? __ldg(a.in_src + b + t) : -1;
+    double z[kInCut1];
+#pragma unroll
+    for (int t = 0; t < kInCut1; ++t) z[t] = s[t] >= 0 ? zc[s[t]] : 0.0;
+    double acc = 0.0;
+#pragma unroll
+    for (int t = 0; t < kInCut1; ++t)
+        if (s[t] >= 0) acc += z[t];
+    return acc;
 }
 
 __global__ void __launch_bounds__(256) k_pull(PullArgs a) {
@@ -73,12 +91,19 @@ __global__ void __launch_bounds__(256) k_pull(PullArgs a) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double delta = 0.0;
     if ((int)blockIdx.x < a.BA) {
-        for (long long r = (long long)blockIdx.x * 256 + threadIdx.x; r < a.cnt0; r += (long long)a.BA * 256) {
+        const long long stride = (long long)a.BA * 256;
+        long long r = (long long)blockIdx.x * 256 + threadIdx.x;
+        for (; r + stride < a.cnt0; r += 2 * stride) {  // two rows in flight
+            const int j0 = a.pull_ids[r], j1 = a.pull_ids[r + stride];
+            const int b0 = a.in_ptr[j0], e0 = a.in_ptr[j0 + 1], b1 = a.in_ptr[j1], e1 = a.in_ptr[j1 + 1];
+            const double s0 = short_row_sum(a, zc, b0, e0);
+            const double s1 = short_row_sum(a, zc, b1, e1);
+            delta += finish_row(a, zn, j0, omdv_of(a, j0) + s0);
+            delta += finish_row(a, zn, j1, omdv_of(a, j1) + s1);
+        }
+        if (r < a.cnt0) {
             const int j = a.pull_ids[r];
-            const int b = a.in_ptr[j], e = a.in_ptr[j + 1];
-            double acc = 0.0;
-            for (int k = b; k < e; ++k) acc += zc[a.in_src[k]];
-            delta += finish_row(a, zn, j, a.omd * v_of(a, j) + acc);
+            delta += finish_row(a, zn, j, omdv_of(a, j) + short_row_sum(a, zc, a.in_ptr[j], a.in_ptr[j + 1]));
         }
     } else if ((int)blockIdx.x < a.BA + a.BB) {
         const long long wid = (long long)(blockIdx.x - a.BA) * 8 + w, nw = (long long)a.BB * 8;
@@ -88,7 +113,7 @@ __global__ void __launch_bounds__(256) k_pull(PullArgs a) {
             double acc = 0.0;
             for (int k = b + lane; k < e; k += 32) acc += zc[a.in_src[k]];
             acc = warp_sum_d(acc);
-            if (lane == 0) delta += finish_row(a, zn, j, a.omd * v_of(a, j) + acc);
+            if (lane == 0) delta += finish_row(a, zn, j, omdv_of(a, j) + acc);
         }
     } else {
         const int BC = gridDim.x - a.BA - a.BB;
@@ -112,10 +137,10 @@ __global__ void __launch_bounds__(256) k_pull(PullArgs a) {
     if (threadIdx.x == 0) a.pp[blockIdx.x].delta = delta;
 }
 
-__global__ void k_power_finalize(PullArgs a, int nparts, cudaGraphConditionalHandle handle) {
+__global__ void k_power_finalize(PullArgs a, int nparts, cudaGraphConditionalHandle handle, int in_graph) {
     __shared__ double sh[8];
     if (a.pst->done) {
-        if (threadIdx.x == 0) cudaGraphSetConditional(handle, 0);
+        if (threadIdx.x == 0 && in_graph) cudaGraphSetConditional(handle, 0);
         return;
     }
     const int cur = a.pst->cur;
@@ -124,7 +149,7 @@ __global__ void k_power_finalize(PullArgs a, int nparts, cudaGraphConditionalHan
     for (int r = threadIdx.x; r < a.nlong; r += blockDim.x) {
         const int j = a.long_ids[r];
         delta += finish_row(a, zn, j, a.Ylong[r]);
-        a.Ylong[r] = a.omd * v_of(a, j);
+        a.Ylong[r] = omdv_of(a, j);
     }
     delta = block_sum_d(delta, sh);
     double parts = 0.0;
@@ -141,7 +166,7 @@ __global__ void k_power_finalize(PullArgs a, int nparts, cudaGraphConditionalHan
     else if (dl * p->d / (1.0 - p->d) < p->tol) done = 1;
     else if (p->iters >= p->max_iters) done = 2;
     p->done = done;
-    if (done) cudaGraphSetConditional(handle, 0);
+    if (done && in_graph) cudaGraphSetConditional(handle, 0);
 }
 
 __global__ void k_power_init(PullArgs a, double tol, int max_iters) {
@@ -151,7 +176,7 @@ __global__ void k_power_init(PullArgs a, double tol, int max_iters) {
         a.Z1[i] = 0.0;
     }
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < a.nlong; r += (long long)gridDim.x * blockDim.x)
-        a.Ylong[r] = a.omd * v_of(a, a.long_ids[r]);
+        a.Ylong[r] = omdv_of(a, a.long_ids[r]);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.pst->delta = 0.0;
         a.pst->tol = tol;
@@ -168,7 +193,7 @@ PullArgs make_args(di_graph *g) {
     a.n = g->n;
     a.in_ptr = g->in_ptr;
     a.in_src = g->in_src;
-    a.row_ptr = g->row_ptr;
+    a.inv_deg = g->inv_deg;
     a.pull_ids = g->pull_ids;
     a.cnt0 = g->in_bin_count[0];
     a.cnt1 = g->in_bin_count[1];
@@ -182,6 +207,7 @@ PullArgs make_args(di_graph *g) {
     a.omd = 1.0 - g->d;
     a.d = g->d;
     a.u = 1.0 / (double)g->n;
+    a.omdu = a.omd * a.u;
     a.X = g->X;
     a.Z0 = g->Z[0];
     a.Z1 = g->Z[1];
@@ -216,7 +242,7 @@ di_status build_power_graph(di_graph *g) {
     e = cudaStreamBeginCaptureToGraph(g->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(e, "cudaStreamBeginCaptureToGraph"); }
     k_pull<<<nparts, 256, 0, g->cap>>>(a);
-    k_power_finalize<<<1, 256, 0, g->cap>>>(a, nparts, handle);
+    k_power_finalize<<<1, 256, 0, g->cap>>>(a, nparts, handle, 1);
     cudaGraph_t captured = nullptr;
     e = cudaStreamEndCapture(g->cap, &captured);
     if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(e, "cudaStreamEndCapture"); }
@@ -247,18 +273,41 @@ di_status power_alloc(di_graph *g) {
     return DI_OK;
 }
 
-di_status run_power(di_graph *g, double tol, int max_iter, double *X_out, bool out_dev, di_stats *st) {
+di_status run_power(di_graph *g, double tol, int max_iter, int profile, double *X_out, bool out_dev, di_stats *st) {
     cudaStream_t s = g->stream;
     if (!g->exec[2]) {
         di_status r = build_power_graph(g);
         if (r != DI_OK) return r;
     }
     PullArgs a = make_args(g);
+    const int nparts = g->pull_blocks[0] + g->pull_blocks[1] + g->pull_blocks[2];
     DI_CUDA(cudaEventRecord(g->ev0, s));
     const int grid = std::max(1, std::min(g->num_sms * 8, (g->n + 255) / 256));
     k_power_init<<<grid, 256, 0, s>>>(a, tol, max_iter);
     DI_CUDA(cudaGetLastError());
-    DI_CUDA(cudaGraphLaunch(g->exec[2], s));
+    g->pprof_ms[0] = g->pprof_ms[1] = 0.0;
+    if (profile) {
+        // the graph body's two kernels launched from the host with events around each
+        cudaGraphConditionalHandle none = 0;
+        for (;;) {
+            DI_CUDA(cudaEventRecord(g->pev[0], s));
+            k_pull<<<nparts, 256, 0, s>>>(a);
+            DI_CUDA(cudaEventRecord(g->pev[1], s));
+            k_power_finalize<<<1, 256, 0, s>>>(a, nparts, none, 0);
+            DI_CUDA(cudaEventRecord(g->pev[2], s));
+            DI_CUDA(cudaGetLastError());
+            DI_CUDA(cudaMemcpyAsync(g->h_pst, g->pst, sizeof(PowerState), cudaMemcpyDeviceToHost, s));
+            DI_CUDA(cudaStreamSynchronize(s));
+            float t0 = 0.f, t1 = 0.f;
+            DI_CUDA(cudaEventElapsedTime(&t0, g->pev[0], g->pev[1]));
+            DI_CUDA(cudaEventElapsedTime(&t1, g->pev[1], g->pev[2]));
+            g->pprof_ms[0] += t0;
+            g->pprof_ms[1] += t1;
+            if (g->h_pst->done) break;
+        }
+    } else {
+        DI_CUDA(cudaGraphLaunch(g->exec[2], s));
+    }
     DI_CUDA(cudaEventRecord(g->ev1, s));
     DI_CUDA(cudaMemcpyAsync(g->h_pst, g->pst, sizeof(PowerState), cudaMemcpyDeviceToHost, s));
     if (X_out)

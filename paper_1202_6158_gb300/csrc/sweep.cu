@@ -49,11 +49,14 @@ template <typename FT> struct Vec;
 template <> struct Vec<double> { using T = double2; static constexpr int N = 2; };
 template <> struct Vec<float> { using T = float4; static constexpr int N = 4; };
 
+// Fire-and-forget reductions into F (performed by the L2 atomic units).  No memory
+// clobber: nothing in a push kernel reads F, so loads may be scheduled freely
+// around these.
 __device__ __forceinline__ void red_add(double *p, double v) {
-    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v));
 }
 __device__ __forceinline__ void red_add(float *p, float v) {
-    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v));
 }
 
 template <typename T>
@@ -134,30 +137,82 @@ __global__ void k_init_control(SolveState *st, double R0, double tolR, double be
 
 // ------------------------------------------------------------------- scan
 
+// Fixed-point fluid sums.  GB300 issues only a couple of FP64 instructions per
+// clock per SM, so the per-element sums of a sweep are made on the integer pipe:
+// each F_i >= 0 is turned into floor(F_i * 2^S) exactly by shifting its mantissa,
+// and the 64-bit integers are added.  S is chosen per sweep from the previous
+// residual R (every F_i and every partial sum is at most about R) so that the
+// total stays below 2^62; the result is independent of summation order and is
+// within n * 2^-S, i.e. about n * 2^-61 * R, of the exact sum.
+__device__ __forceinline__ int fixed_scale(double R) {
+    const long long b = __double_as_longlong(R);
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;  // R < 2^(e+1)
+    return 60 - e;                                   // 2R * 2^S < 2^62
+}
+
+__device__ __forceinline__ long long to_fixed(double x, int S) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    const unsigned long long m = (b & 0xfffffffffffffull) | (e ? (1ull << 52) : 0ull);
+    int pos = (e ? e : 1) - 1075 + S;               // x * 2^S = m * 2^pos
+    if (pos > 9) pos = 9;                           // only if x > 2R, which F never is
+    if (pos >= 0) return (long long)(m << pos);
+    if (pos <= -64) return 0;
+    return (long long)(m >> (-pos));
+}
+
+__device__ __forceinline__ long long to_fixed(float x, int S) { return to_fixed((double)x, S); }
+
+template <typename FT>
+struct ScanOps;
+
+// FP64 fluid: the threshold test compares bit patterns as signed integers, which
+// orders non-negative doubles exactly like their values (F >= 0 throughout).
+template <>
+struct ScanOps<double> {
+    using VT = double2;
+    static constexpr int VN = 2;
+    using Key = long long;
+    __device__ static Key key(double T) { return __double_as_longlong(T); }
+    __device__ static bool above(double f, Key k) { return __double_as_longlong(f) > k; }
+};
+
+template <>
+struct ScanOps<float> {
+    using VT = float4;
+    static constexpr int VN = 4;
+    using Key = float;
+    __device__ static Key key(double T) { return (float)T; }
+    __device__ static bool above(float f, Key k) { return f > k; }
+};
+
 template <typename FT>
 __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int n, int chunk, FT *__restrict__ F,
                                                              double *__restrict__ H, const int *__restrict__ row_ptr,
+                                                             const FT *__restrict__ inv_deg,
                                                              const int *__restrict__ region, int G,
-                                                             int *__restrict__ fcount, FEntry *__restrict__ frontier,
+                                                             int *__restrict__ fcount, FEntryT<FT> *__restrict__ frontier,
                                                              ScanPartial *__restrict__ part,
                                                              const SolveState *__restrict__ st, double d) {
-    using VT = typename Vec<FT>::T;
-    constexpr int VN = Vec<FT>::N;
+    using Ops = ScanOps<FT>;
+    using VT = typename Ops::VT;
+    constexpr int VN = Ops::VN;
     constexpr int NW = kScanThreads / 32;
     __shared__ int s_wcnt[3][NW];
     __shared__ double s_red_d[NW];
     __shared__ long long s_red_l[NW];
     if (st->done) return;
-    const double T = st->T;
+    const typename Ops::Key key = Ops::key(st->T);
+    const int S = fixed_scale(st->R);
     const int c = blockIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const long long beg = (long long)c * chunk;
     const long long end = min((long long)n, beg + chunk);
     int run0 = region[0 * (G + 1) + c], run1 = region[1 * (G + 1) + c], run2 = region[2 * (G + 1) + c];
     const int start0 = run0, start1 = run1, start2 = run2;
-    double l1 = 0.0, removed = 0.0;
-    long long edges = 0, srcs = 0, entries = 0;
-    const double dd = d, omd = 1.0 - d;
+    long long l1 = 0;                 // |F|_1 over this thread's elements (fixed point)
+    long long sent_out = 0, sent_dng = 0;  // fluid moved by selected nodes with / without children
+    int edges = 0, srcs = 0, entries = 0;
 
     for (long long t0 = beg; t0 < end; t0 += (long long)kScanThreads * VN) {
         const long long i0 = t0 + (long long)threadIdx.x * VN;
@@ -172,31 +227,32 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int n, int chunk, F
             for (int k = 0; k < VN; ++k) f[k] = (FT)0;
         }
         int bin[VN];
-        FEntry ent[VN];
+        FEntryT<FT> ent[VN];
         bool any = false;
 #pragma unroll
         for (int k = 0; k < VN; ++k) {
             const long long i = i0 + k;
-            const double fv = (double)f[k];
-            l1 += fv;
+            const FT fv = f[k];
+            const long long fx = to_fixed(fv, S);
+            l1 += fx;
             bin[k] = -1;
-            if (i < end && fv > T) {
+            if (i < end && Ops::above(fv, key)) {
                 any = true;
                 srcs += 1;
-                H[i] += fv;
+                H[i] += (double)fv;                 // J_i F: the fluid moves into the history
                 f[k] = (FT)0;
                 const int rb = row_ptr[i];
                 const int deg = row_ptr[i + 1] - rb;
                 if (deg == 0) {
-                    removed += fv;
+                    sent_dng += fx;                 // a dangling node's fluid leaves (Section 3.3)
                 } else {
-                    removed += omd * fv;
+                    sent_out += fx;
                     edges += deg;
                     entries += 1;
                     bin[k] = deg <= kOutCut1 ? 0 : (deg <= kOutCut2 ? 1 : 2);
                     ent[k].beg = rb;
                     ent[k].deg = deg;
-                    ent[k].w = (dd * fv) / (double)deg;
+                    ent[k].w = fv * inv_deg[i];     // d * sent / outdeg(i)
                 }
             }
         }
@@ -253,77 +309,131 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int n, int chunk, F
         fcount[1 * G + c] = run1 - start1;
         fcount[2 * G + c] = run2 - start2;
     }
-    double bl1 = block_sum(l1, s_red_d);
-    double brem = block_sum(removed, s_red_d);
-    long long bed = block_sum(edges, s_red_l);
-    long long bsr = block_sum(srcs, s_red_l);
-    long long ben = block_sum(entries, s_red_l);
+    (void)s_red_d;
+    const long long bl1 = block_sum(l1, s_red_l);
+    const long long bout = block_sum(sent_out, s_red_l);
+    const long long bdng = block_sum(sent_dng, s_red_l);
+    const long long bed = block_sum((long long)edges, s_red_l);
+    const long long bsr = block_sum((long long)srcs, s_red_l);
+    const long long ben = block_sum((long long)entries, s_red_l);
     if (threadIdx.x == 0) {
         ScanPartial p;
         p.l1 = bl1;
-        p.removed = brem;
+        p.out = bout;
+        p.dng = bdng;
         p.edges = bed;
         p.srcs = bsr;
         p.entries = ben;
-        p.pad = 0;
+        p.l1d = 0.0;
+        p.pad = 0.0;
         part[c] = p;
     }
 }
 
 // ------------------------------------------------------------------- push
 
+// One elementary step F_j += w.  Edges into the hot targets (the most-linked-to
+// nodes, encoded as -1 - slot) are summed in the CTA's shared memory: on power-law
+// graphs a single target can receive a few percent of all pushes, and same-address
+// reductions serialize in one L2 slice.
 template <typename FT>
-__device__ __forceinline__ void push_row_lanes(const int *__restrict__ col_idx, FT *__restrict__ F, int beg, int deg,
-                                               FT w, int lane, int width) {
-    // head up to a 16-byte boundary, then int4 loads, then the tail
+__device__ __forceinline__ void push_one(FT *__restrict__ F, FT *hot, int c, FT w) {
+    if (c >= 0) red_add(F + c, w);
+    else atomicAdd(hot + (-1 - c), w);
+}
+
+// Rows of the warp and CTA bins: the head up to a 16-byte boundary, then int4
+// loads two at a time (all loads of a step are issued before its reductions),
+// then the tail.
+template <typename FT>
+__device__ __forceinline__ void push_row_lanes(const int *__restrict__ col_idx, FT *__restrict__ F, FT *hot, int beg,
+                                               int deg, FT w, int lane, int width) {
     const int head = min(deg, (4 - (beg & 3)) & 3);
-    for (int t = lane; t < head; t += width) red_add(F + col_idx[beg + t], w);
+    if (lane < head) push_one(F, hot, __ldg(col_idx + beg + lane), w);
     const int body = (deg - head) >> 2;
     const int4 *v4 = reinterpret_cast<const int4 *>(col_idx + beg + head);
-    for (int k = lane; k < body; k += width) {
-        int4 q = __ldg(v4 + k);
-        red_add(F + q.x, w);
-        red_add(F + q.y, w);
-        red_add(F + q.z, w);
-        red_add(F + q.w, w);
+    int k = lane;
+    for (; k + width < body; k += 2 * width) {
+        const int4 q = __ldg(v4 + k);
+        const int4 r = __ldg(v4 + k + width);
+        push_one(F, hot, q.x, w);
+        push_one(F, hot, q.y, w);
+        push_one(F, hot, q.z, w);
+        push_one(F, hot, q.w, w);
+        push_one(F, hot, r.x, w);
+        push_one(F, hot, r.y, w);
+        push_one(F, hot, r.z, w);
+        push_one(F, hot, r.w, w);
     }
-    const int done = head + 4 * body;
-    for (int t = done + lane; t < deg; t += width) red_add(F + col_idx[beg + t], w);
+    if (k < body) {
+        const int4 q = __ldg(v4 + k);
+        push_one(F, hot, q.x, w);
+        push_one(F, hot, q.y, w);
+        push_one(F, hot, q.z, w);
+        push_one(F, hot, q.w, w);
+    }
+    const int t = head + 4 * body + lane;
+    if (t < deg) push_one(F, hot, __ldg(col_idx + beg + t), w);
+}
+
+// a thread-bin row (1..kOutCut1 out-links): all index loads first, then the reductions
+template <typename FT>
+__device__ __forceinline__ void push_short_row(const int *__restrict__ col_idx, FT *__restrict__ F, FT *hot,
+                                               const FEntryT<FT> &e) {
+    int c[kOutCut1];
+#pragma unroll
+    for (int t = 0; t < kOutCut1; ++t) c[t] = t < e.deg ? __ldg(col_idx + e.beg + t) : 0;
+#pragma unroll
+    for (int t = 0; t < kOutCut1; ++t)
+        if (t < e.deg) push_one(F, hot, c[t], e.w);
 }
 
 template <typename FT>
 __global__ void __launch_bounds__(kScanThreads) k_sweep_push(const int *__restrict__ col_idx, FT *__restrict__ F,
                                                              const int *__restrict__ region,
                                                              const int *__restrict__ fcount, int G,
-                                                             const FEntry *__restrict__ frontier,
+                                                             const FEntryT<FT> *__restrict__ frontier,
+                                                             const int *__restrict__ hot_ids, int n_hot,
                                                              const SolveState *__restrict__ st) {
+    __shared__ FT hot[kHotSlots];
     if (st->done) return;
+    for (int t = threadIdx.x; t < kHotSlots; t += kScanThreads) hot[t] = (FT)0;
+    __syncthreads();
     const int c = blockIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     // CTA per source: the largest out-degrees
     {
         const int base = region[2 * (G + 1) + c], cnt = fcount[2 * G + c];
         for (int k = 0; k < cnt; ++k) {
-            const FEntry e = frontier[base + k];
-            push_row_lanes(col_idx, F, e.beg, e.deg, (FT)e.w, threadIdx.x, kScanThreads);
+            const FEntryT<FT> e = frontier[base + k];
+            push_row_lanes(col_idx, F, hot, e.beg, e.deg, e.w, threadIdx.x, kScanThreads);
         }
     }
     // warp per source
     {
         const int base = region[1 * (G + 1) + c], cnt = fcount[1 * G + c];
         for (int k = w; k < cnt; k += kScanThreads / 32) {
-            const FEntry e = frontier[base + k];
-            push_row_lanes(col_idx, F, e.beg, e.deg, (FT)e.w, lane, 32);
+            const FEntryT<FT> e = frontier[base + k];
+            push_row_lanes(col_idx, F, hot, e.beg, e.deg, e.w, lane, 32);
         }
     }
-    // thread per source
+    // thread per source, two sources in flight per thread
     {
         const int base = region[0 * (G + 1) + c], cnt = fcount[0 * G + c];
-        for (int k = threadIdx.x; k < cnt; k += kScanThreads) {
-            const FEntry e = frontier[base + k];
-            const FT wv = (FT)e.w;
-            for (int t = 0; t < e.deg; ++t) red_add(F + __ldg(col_idx + e.beg + t), wv);
+        int k = threadIdx.x;
+        for (; k + kScanThreads < cnt; k += 2 * kScanThreads) {
+            const FEntryT<FT> e0 = frontier[base + k];
+            const FEntryT<FT> e1 = frontier[base + k + kScanThreads];
+            push_short_row(col_idx, F, hot, e0);
+            push_short_row(col_idx, F, hot, e1);
         }
+        if (k < cnt) push_short_row(col_idx, F, hot, frontier[base + k]);
+    }
+    // the CTA's sums for the hot targets go to F once
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_hot; t += kScanThreads) {
+        const FT v = hot[t];
+        if (v != (FT)0) red_add(F + hot_ids[t], v);
     }
 }
 
@@ -341,23 +451,29 @@ __global__ void k_sweep_finalize(int n, int G, const ScanPartial *__restrict__ p
         }
         return;
     }
-    double l1 = 0.0, rem = 0.0;
-    long long ed = 0, sr = 0, en = 0;
+    (void)s_d;
+    long long fl1 = 0, fout = 0, fdng = 0, ed = 0, sr = 0, en = 0;
     for (int c = threadIdx.x; c < G; c += blockDim.x) {
-        l1 += part[c].l1;
-        rem += part[c].removed;
+        fl1 += part[c].l1;
+        fout += part[c].out;
+        fdng += part[c].dng;
         ed += part[c].edges;
         sr += part[c].srcs;
         en += part[c].entries;
     }
-    l1 = block_sum(l1, s_d);
-    rem = block_sum(rem, s_d);
+    fl1 = block_sum(fl1, s_l);
+    fout = block_sum(fout, s_l);
+    fdng = block_sum(fdng, s_l);
     ed = block_sum(ed, s_l);
     sr = block_sum(sr, s_l);
     en = block_sum(en, s_l);
     if (threadIdx.x != 0) return;
     st->body_runs += 1;
     const double Tused = st->T;
+    const int S = fixed_scale(st->R);  // the scale the scan used (st->R is still the previous residual)
+    const double l1 = ldexp((double)fl1, -S);
+    // removed mass: (1-d)*sent for nodes with children, sent for dangling nodes (Section 3.3)
+    const double rem = st->one_minus_d * ldexp((double)fout, -S) + ldexp((double)fdng, -S);
     const double R = l1 - rem;  // |F|_1 after the sweep (exact arithmetic)
     st->sweeps += 1;
     st->edges += ed;
@@ -371,6 +487,8 @@ __global__ void k_sweep_finalize(int n, int G, const ScanPartial *__restrict__ p
         r.sources = sr;
         r.edges = ed;
         r.pushed = en;
+        r.scan_ms = 0.0;
+        r.push_ms = 0.0;
         trace[st->sweeps - 1] = r;
     }
     st->R = R;
@@ -395,14 +513,14 @@ __global__ void __launch_bounds__(kScanThreads) k_l1_partials(int n, int chunk, 
     double a = 0.0;
     for (long long i = beg + threadIdx.x; i < end; i += blockDim.x) a += fabs((double)F[i]);
     a = block_sum(a, s);
-    if (threadIdx.x == 0) part[blockIdx.x].l1 = a;
+    if (threadIdx.x == 0) part[blockIdx.x].l1d = a;
 }
 
 // sum the partials in fixed order; a stop that the exact norm does not confirm resumes
 __global__ void k_confirm(int G, int n, const ScanPartial *__restrict__ part, SolveState *__restrict__ st) {
     __shared__ double s[8];
     double a = 0.0;
-    for (int c = threadIdx.x; c < G; c += blockDim.x) a += part[c].l1;
+    for (int c = threadIdx.x; c < G; c += blockDim.x) a += part[c].l1d;
     a = block_sum(a, s);
     if (threadIdx.x == 0) {
         st->l1_exact = a;
@@ -444,6 +562,11 @@ __global__ void k_to_double(int n, const FT *__restrict__ in, double *__restrict
         out[i] = (double)in[i];
 }
 
+template <typename FT> const FT *inv_deg_of(di_graph *g);
+template <> const double *inv_deg_of<double>(di_graph *g) { return g->inv_deg; }
+template <> const float *inv_deg_of<float>(di_graph *g) { return g->inv_deg32; }
+template <typename FT> FEntryT<FT> *frontier_of(di_graph *g) { return reinterpret_cast<FEntryT<FT> *>(g->frontier); }
+
 int elem_grid(di_graph *g, long long work) {
     long long b = (work + 255) / 256;
     return (int)std::max(1LL, std::min(b, (long long)g->num_sms * 8));
@@ -468,9 +591,10 @@ di_status build_sweep_graph(di_graph *g, int slot, FT *F) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     e = cudaStreamBeginCaptureToGraph(g->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(e, "cudaStreamBeginCaptureToGraph"); }
-    k_sweep_scan<FT><<<g->G, kScanThreads, 0, g->cap>>>(g->n, g->chunk, F, g->H, g->row_ptr, g->region, g->G, g->fcount,
-                                                         g->frontier, g->part, g->st, g->d);
-    k_sweep_push<FT><<<g->G, kScanThreads, 0, g->cap>>>(g->col_idx, F, g->region, g->fcount, g->G, g->frontier, g->st);
+    k_sweep_scan<FT><<<g->G, kScanThreads, 0, g->cap>>>(g->n, g->chunk, F, g->H, g->row_ptr, inv_deg_of<FT>(g), g->region,
+                                                         g->G, g->fcount, frontier_of<FT>(g), g->part, g->st, g->d);
+    k_sweep_push<FT><<<g->G, kScanThreads, 0, g->cap>>>(g->col_idx, F, g->region, g->fcount, g->G, frontier_of<FT>(g),
+                                                         g->hot_ids, g->n_hot, g->st);
     k_sweep_finalize<<<1, 256, 0, g->cap>>>(g->n, g->G, g->part, g->st, g->trace, handle, 1);
     cudaGraph_t captured = nullptr;
     e = cudaStreamEndCapture(g->cap, &captured);
@@ -516,11 +640,12 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, const
             cudaGraphConditionalHandle none = 0;
             for (;;) {
                 DI_CUDA(cudaEventRecord(g->pev[0], s));
-                k_sweep_scan<FT><<<g->G, kScanThreads, 0, s>>>(n, g->chunk, F, g->H, g->row_ptr, g->region, g->G,
-                                                              g->fcount, g->frontier, g->part, g->st, g->d);
+                k_sweep_scan<FT><<<g->G, kScanThreads, 0, s>>>(n, g->chunk, F, g->H, g->row_ptr, inv_deg_of<FT>(g),
+                                                              g->region, g->G, g->fcount, frontier_of<FT>(g), g->part,
+                                                              g->st, g->d);
                 DI_CUDA(cudaEventRecord(g->pev[1], s));
                 k_sweep_push<FT><<<g->G, kScanThreads, 0, s>>>(g->col_idx, F, g->region, g->fcount, g->G,
-                                                              g->frontier, g->st);
+                                                              frontier_of<FT>(g), g->hot_ids, g->n_hot, g->st);
                 DI_CUDA(cudaEventRecord(g->pev[2], s));
                 k_sweep_finalize<<<1, 256, 0, s>>>(n, g->G, g->part, g->st, g->trace, none, 0);
                 DI_CUDA(cudaEventRecord(g->pev[3], s));
@@ -534,6 +659,10 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, const
                 g->prof.scan_ms += t0;
                 g->prof.push_ms += t1;
                 g->prof.finalize_ms += t2;
+                if (g->sweep_ms && g->prof.sweeps < kTraceCap) {
+                    g->sweep_ms[2 * g->prof.sweeps] = t0;
+                    g->sweep_ms[2 * g->prof.sweeps + 1] = t1;
+                }
                 g->prof.sweeps += 1;
                 if (g->h_st->done != 0) break;
             }
@@ -590,6 +719,14 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, const
 }
 
 }  // namespace
+
+int scan_blocks_per_sm() {
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_sweep_scan<double>, kScanThreads, 0) != cudaSuccess) a = 4;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep_scan<float>, kScanThreads, 0) != cudaSuccess) b = 4;
+    cudaGetLastError();
+    return std::max(1, std::min(a, b));
+}
 
 di_status sweep_alloc(di_graph *g) {
     cudaStream_t s = g->stream;

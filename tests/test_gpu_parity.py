@@ -75,6 +75,18 @@ def test_derived_structures_bit_exact(di, name):
     assert np.array_equal(ex["in_bin_of"], in_bin_of)
 
 
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_hot_targets_bit_exact(di, name):
+    """The push's shared-memory targets: top-256 in-degree (>= 32), ties by lower id."""
+    n, rp, ci = CASES[name]
+    with di.DiGraph(n, rp, ci, D) as g:
+        hot = g.hot_targets()
+    indeg = np.bincount(ci, minlength=n)
+    order = np.lexsort((np.arange(n), -indeg))[:256]
+    want = order[indeg[order] >= 32]
+    assert np.array_equal(hot, want)
+
+
 # ------------------------------------------------------------ D-iteration
 
 def _solve(di, n, rp, ci, tol, V=None, **kw):
