@@ -132,16 +132,21 @@ void di_free(di_graph *g);
 di_status di_graph_info(const di_graph *g, int32_t *n, int64_t *nnz, double *d);
 
 /*
- * Copy derived structures to caller buffers (host or device), for checks:
+ * Copy derived structures to caller buffers (host or device), for checks.  The
+ * library numbers nodes internally: the hot targets (di_graph_hot_targets) come
+ * first, in that order, then every other node in input order.  Every array
+ * below except perm is in that internal numbering.
+ *   perm     int32[n]: perm[r] = input id of internal node r
  *   outdeg   int32[n]
  *   in_ptr   int32[n+1], in_src int32[nnz]: in-link lists, sources ascending
  *   bin_of   int32[n]: out-degree bin (0 dangling, 1..3 by the cut values)
  *   in_bin_of int32[n]: in-degree bin used by the pull kernel of di_power
  *   cuts     int32[4]: {out_cut1, out_cut2, in_cut1, in_cut2}
- * Any pointer may be NULL to skip that array.
+ * Any pointer may be NULL to skip that array.  Inputs (V, seeds) and outputs
+ * (H, F, X) of every other call are in the caller's numbering.
  */
-di_status di_graph_export(const di_graph *g, int32_t *outdeg, int32_t *in_ptr, int32_t *in_src, int32_t *bin_of,
-                          int32_t *in_bin_of, int32_t *cuts);
+di_status di_graph_export(const di_graph *g, int32_t *perm, int32_t *outdeg, int32_t *in_ptr, int32_t *in_src,
+                          int32_t *bin_of, int32_t *in_bin_of, int32_t *cuts);
 
 /*
  * The hot targets of a graph: the (at most 256) nodes with the largest

@@ -94,9 +94,9 @@ def di_power_ex(handle, tol, X_out, max_iter=0, profile=0, allow_unconverged=Fal
     return rc, d
 
 
-def di_graph_export(handle, outdeg=None, in_ptr=None, in_src=None, bin_of=None, in_bin_of=None, cuts=None):
-    check(load().di_graph_export(handle, ptr(outdeg), ptr(in_ptr), ptr(in_src), ptr(bin_of), ptr(in_bin_of),
-                                 ptr(cuts)))
+def di_graph_export(handle, perm=None, outdeg=None, in_ptr=None, in_src=None, bin_of=None, in_bin_of=None, cuts=None):
+    check(load().di_graph_export(handle, ptr(perm), ptr(outdeg), ptr(in_ptr), ptr(in_src), ptr(bin_of),
+                                 ptr(in_bin_of), ptr(cuts)))
 
 
 def di_get_trace(handle, cap=4096):
@@ -167,7 +167,7 @@ class DiGraph:
 
     def export(self):
         n, L = self.n, self.nnz
-        out = {"outdeg": np.empty(n, np.int32), "in_ptr": np.empty(n + 1, np.int32),
+        out = {"perm": np.empty(n, np.int32), "outdeg": np.empty(n, np.int32), "in_ptr": np.empty(n + 1, np.int32),
                "in_src": np.empty(max(L, 1), np.int32), "bin_of": np.empty(n, np.int32),
                "in_bin_of": np.empty(n, np.int32), "cuts": np.empty(4, np.int32)}
         di_graph_export(self.handle, **out)

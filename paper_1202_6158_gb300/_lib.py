@@ -70,7 +70,7 @@ def load(path: str = LIB_PATH):
         "di_graph_create": ([i32, vp, vp, i64, f64, vp, vp, ctypes.POINTER(vp)], ctypes.c_int),
         "di_free": ([vp], None),
         "di_graph_info": ([vp, vp, vp, vp], ctypes.c_int),
-        "di_graph_export": ([vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "di_graph_export": ([vp, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
         "di_graph_hot_targets": ([vp, vp, ctypes.POINTER(i32)], ctypes.c_int),
         "di_solve": ([vp, f64, i64, ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(di_stats)], ctypes.c_int),
         "di_solve_ex": ([vp, ctypes.POINTER(di_solve_opts), vp, ctypes.POINTER(di_stats)], ctypes.c_int),

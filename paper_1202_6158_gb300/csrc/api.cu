@@ -53,8 +53,8 @@ static void free_graph(di_graph *g) {
         if (g->graph[k]) cudaGraphDestroy(g->graph[k]);
     }
     void *bufs[] = {g->row_ptr, g->col_idx, g->in_ptr, g->in_src, g->bin_of, g->in_bin_of, g->pull_ids, g->V,
-                    g->inv_deg, g->inv_deg32, g->hot_ids,
-                    g->long_prefix, g->region, g->fcount, g->frontier, g->F64, g->F32, g->H, g->part, g->st,
+                    g->inv_deg, g->inv_deg32, g->hot_ids, g->perm, g->new_of, g->rec64, g->rec32,
+                    g->long_prefix, g->region, g->fcount, g->pre, g->ticket, g->sel, g->cls, g->F64, g->F32, g->H, g->part, g->st,
                     g->trace, g->X, g->Z[0], g->Z[1], g->Ylong, g->ppart, g->pst};
     for (void *b : bufs)
         if (b) cudaFreeAsync(b, g->stream);
@@ -177,8 +177,8 @@ static di_status copy_out(void *dst, const void *src_dev, size_t bytes, cudaStre
 
 extern "C" {
 
-di_status di_graph_export(const di_graph *g, int32_t *outdeg, int32_t *in_ptr, int32_t *in_src, int32_t *bin_of,
-                          int32_t *in_bin_of, int32_t *cuts) {
+di_status di_graph_export(const di_graph *g, int32_t *perm, int32_t *outdeg, int32_t *in_ptr, int32_t *in_src,
+                          int32_t *bin_of, int32_t *in_bin_of, int32_t *cuts) {
     g_last_error.clear();
     if (check_graph(g) != DI_OK) return DI_EINVAL;
     cudaStream_t s = g->stream;
@@ -191,7 +191,8 @@ di_status di_graph_export(const di_graph *g, int32_t *outdeg, int32_t *in_ptr, i
         cudaFreeAsync(tmp, s);
         if (r != DI_OK) return r;
     }
-    di_status r = copy_out(in_ptr, g->in_ptr, sizeof(int) * (n + 1), s);
+    di_status r = copy_out(perm, g->perm, sizeof(int) * n, s);
+    if (r == DI_OK) r = copy_out(in_ptr, g->in_ptr, sizeof(int) * (n + 1), s);
     if (r == DI_OK) r = copy_out(in_src, g->in_src, sizeof(int) * (size_t)g->nnz, s);
     if (r == DI_OK) r = copy_out(bin_of, g->bin_of, sizeof(int) * n, s);
     if (r == DI_OK) r = copy_out(in_bin_of, g->in_bin_of, sizeof(int) * n, s);

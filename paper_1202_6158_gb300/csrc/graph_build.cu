@@ -94,49 +94,57 @@ __global__ void k_validate_v(int n, const double *__restrict__ V, int *flags, do
 
 // ------------------------------------------------------- degrees and bins
 
-// out-degree bin and d/outdeg of every node (the one division per node the solves need)
+// out-degree class and d/outdeg of every node (the one division per node the solves need),
+// and the packed row record {start, outdeg, d/outdeg} the push reads with one access
 __global__ void k_out_bins(int n, const int *__restrict__ row_ptr, int cut1, int cut2, double d, int *__restrict__ bin_of,
-                           double *__restrict__ inv_deg, float *__restrict__ inv_deg32) {
+                           unsigned char *__restrict__ cls, double *__restrict__ inv_deg, float *__restrict__ inv_deg32,
+                           RowRec<double> *__restrict__ rec64, RowRec<float> *__restrict__ rec32) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        int deg = row_ptr[i + 1] - row_ptr[i];
-        bin_of[i] = deg == 0 ? 0 : (deg <= cut1 ? 1 : (deg <= cut2 ? 2 : 3));
+        const int beg = row_ptr[i];
+        const int deg = row_ptr[i + 1] - beg;
+        int b = deg == 0 ? 0 : (deg <= cut1 ? 1 : (deg <= cut2 ? 2 : 3));
+        bin_of[i] = b;
+        cls[i] = (unsigned char)b;
         double w = deg ? d / (double)deg : 0.0;
         inv_deg[i] = w;
         inv_deg32[i] = (float)w;
+        RowRec<double> r64;
+        r64.beg = beg;
+        r64.deg = deg;
+        r64.inv = w;
+        rec64[i] = r64;
+        RowRec<float> r32;
+        r32.beg = beg;
+        r32.deg = deg;
+        r32.inv = (float)w;
+        rec32[i] = r32;
     }
 }
 
-// per scan chunk: how many nodes of bins 1..3 it holds
-__global__ void k_chunk_bin_counts(int n, int chunk, const int *__restrict__ bin_of, int *__restrict__ cnt, int G) {
-    __shared__ int c[4];
-    if (threadIdx.x < 4) c[threadIdx.x] = 0;
+// per warp sub-chunk: how many nodes of each class it holds
+__global__ void k_sub_counts(int n, int wchunk, const unsigned char *__restrict__ cls, int *__restrict__ cnt, int W) {
+    __shared__ int c[kLists];
+    if (threadIdx.x < kLists) c[threadIdx.x] = 0;
     __syncthreads();
-    long long beg = (long long)blockIdx.x * chunk, end = min((long long)n, beg + chunk);
-    int l1 = 0, l2 = 0, l3 = 0;
-    for (long long i = beg + threadIdx.x; i < end; i += blockDim.x) {
-        int b = bin_of[i];
-        l1 += b == 1;
-        l2 += b == 2;
-        l3 += b == 3;
-    }
-    atomicAdd(&c[1], l1);
-    atomicAdd(&c[2], l2);
-    atomicAdd(&c[3], l3);
+    const long long beg = (long long)blockIdx.x * wchunk, end = min((long long)n, beg + wchunk);
+    int l[kLists] = {0, 0, 0, 0};
+    for (long long i = beg + threadIdx.x; i < end; i += blockDim.x) l[cls[i]] += 1;
+    for (int L = 0; L < kLists; ++L) atomicAdd(&c[L], l[L]);
     __syncthreads();
-    if (threadIdx.x < 3) cnt[threadIdx.x * G + blockIdx.x] = c[threadIdx.x + 1];
+    if (threadIdx.x < kLists) cnt[threadIdx.x * W + blockIdx.x] = c[threadIdx.x];
 }
 
-// region[b][c] = (nodes of bins < b) + (nodes of bin b in chunks < c); b = 0..2 stands for bins 1..3
-__global__ void k_region_scan(int G, const int *__restrict__ cnt, int *__restrict__ region) {
+// region[L][g] = (nodes of classes < L) + (nodes of class L in sub-chunks < g)
+__global__ void k_region_scan(int W, const int *__restrict__ cnt, int *__restrict__ region) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     long long base = 0;
-    for (int b = 0; b < 3; ++b) {
+    for (int L = 0; L < kLists; ++L) {
         long long run = 0;
-        for (int c = 0; c < G; ++c) {
-            region[b * (G + 1) + c] = (int)(base + run);
-            run += cnt[b * G + c];
+        for (int g = 0; g < W; ++g) {
+            region[L * (W + 1) + g] = (int)(base + run);
+            run += cnt[L * W + g];
         }
-        region[b * (G + 1) + G] = (int)(base + run);
+        region[L * (W + 1) + W] = (int)(base + run);
         base += run;
     }
 }
@@ -340,27 +348,10 @@ __global__ void k_count_in(long long nnz, const int *__restrict__ col_idx, int *
         atomicAdd(&indeg[col_idx[e]], 1);
 }
 
-// key that sorts nodes by in-degree, largest first (stable: ties keep ascending ids)
-__global__ void k_indeg_key(int n, const int *__restrict__ in_ptr, int *__restrict__ key) {
+// key that sorts nodes by in-degree, largest first (a stable sort keeps ascending ids on ties)
+__global__ void k_indeg_key_direct(int n, const int *__restrict__ indeg, int *__restrict__ key) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        key[i] = 0x7fffffff - (in_ptr[i + 1] - in_ptr[i]);
-}
-
-__global__ void k_fill(long long m, int v, int *__restrict__ out) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (long long)gridDim.x * blockDim.x)
-        out[i] = v;
-}
-
-__global__ void k_hot_slots(int k, const int *__restrict__ hot_ids, int *__restrict__ slot_of) {
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < k; s += gridDim.x * blockDim.x) slot_of[hot_ids[s]] = s;
-}
-
-// re-encode edges into hot targets as -1 - slot (the push keeps those sums in shared memory)
-__global__ void k_encode_hot(long long nnz, const int *__restrict__ slot_of, int *__restrict__ col_idx) {
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (long long)gridDim.x * blockDim.x) {
-        const int s = slot_of[col_idx[e]];
-        if (s >= 0) col_idx[e] = -1 - s;
-    }
+        key[i] = 0x7fffffff - indeg[i];
 }
 
 // number of the first k sorted ids whose in-degree reaches the minimum
@@ -369,6 +360,47 @@ __global__ void k_count_hot(int k, const int *__restrict__ sorted_key, int min_d
     int c = 0;
     while (c < k && 0x7fffffff - sorted_key[c] >= min_deg) ++c;
     *count = c;
+}
+
+// flag[i] = 1 everywhere, then 0 for the first k ids of the in-degree order (the hot targets)
+__global__ void k_hot_flags(int n, int *__restrict__ flag) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        flag[i] = 1;
+}
+
+__global__ void k_mark_hot(int k, const int *__restrict__ by_indeg, int *__restrict__ flag) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < k; r += gridDim.x * blockDim.x) flag[by_indeg[r]] = 0;
+}
+
+__global__ void k_inverse(int n, const int *__restrict__ perm, int *__restrict__ inv) {
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+        inv[perm[r]] = (int)r;
+}
+
+// out-degree of internal node r (the input node perm[r]); deg[n] = 0 so a scan gives row_ptr
+__global__ void k_perm_deg(int n, const int *__restrict__ perm, const int *__restrict__ row_ptr, int *__restrict__ deg) {
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r <= n; r += (long long)gridDim.x * blockDim.x)
+        deg[r] = r < n ? row_ptr[perm[r] + 1] - row_ptr[perm[r]] : 0;
+}
+
+// edge e of the relabeled CSR: its row r by binary search, then the input edge it copies
+__global__ void k_perm_cols(int n, long long nnz, const int *__restrict__ perm, const int *__restrict__ new_of,
+                            const int *__restrict__ row_ptr_in, const int *__restrict__ col_in,
+                            const int *__restrict__ row_ptr_out, int *__restrict__ col_out) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = n;
+        while (hi - lo > 1) {
+            int mid = lo + (hi - lo) / 2;
+            if ((long long)row_ptr_out[mid] <= e) lo = mid; else hi = mid;
+        }
+        const long long src_e = (long long)row_ptr_in[perm[lo]] + (e - row_ptr_out[lo]);
+        col_out[e] = new_of[col_in[src_e]];
+    }
+}
+
+__global__ void k_perm_values(int n, const int *__restrict__ perm, const double *__restrict__ in, double *__restrict__ out) {
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+        out[r] = in[perm[r]];
 }
 
 int grid_for(long long work, int threads, int num_sms) {
@@ -425,37 +457,123 @@ di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_de
         if (hf & kColRange) return set_error(DI_EINVAL, "col_idx has an entry outside [0, n)");
     }
 
-    // 2. out-degree bins and per-chunk frontier regions
-    DI_CUDA(cudaMallocAsync(&g->bin_of, sizeof(int) * (size_t)n, s));
-    DI_CUDA(cudaMallocAsync(&g->inv_deg, sizeof(double) * (size_t)n, s));
-    DI_CUDA(cudaMallocAsync(&g->inv_deg32, sizeof(float) * (size_t)n, s));
-    k_out_bins<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, g->row_ptr, kOutCut1, kOutCut2, g->d, g->bin_of,
-                                                           g->inv_deg, g->inv_deg32);
+    // 1b. internal numbering: the hot targets -- the kHotSlots largest in-degrees (at least
+    //     kHotMinInDeg), ties by lower input id, found by a stable LSD radix sort -- become ids
+    //     0..n_hot-1; every other node keeps its input order after them.  The push sums the
+    //     hot targets' fluid in shared memory with a single compare; the rest stay spread over
+    //     the L2 slices as the input spreads them.
+    {
+        int *indeg = nullptr, *ka = nullptr, *kb = nullptr, *va = nullptr, *vb = nullptr, *cnt = nullptr;
+        DI_CUDA(cudaMallocAsync(&indeg, sizeof(int) * (size_t)n, s));
+        DI_CUDA(cudaMallocAsync(&ka, sizeof(int) * (size_t)n, s));
+        DI_CUDA(cudaMallocAsync(&kb, sizeof(int) * (size_t)n, s));
+        DI_CUDA(cudaMallocAsync(&va, sizeof(int) * (size_t)n, s));
+        DI_CUDA(cudaMallocAsync(&vb, sizeof(int) * (size_t)n, s));
+        DI_CUDA(cudaMallocAsync(&cnt, sizeof(int), s));
+        DI_CUDA(cudaMemsetAsync(indeg, 0, sizeof(int) * (size_t)n, s));
+        if (L > 0) k_count_in<<<grid_for(L, 256, g->num_sms), 256, 0, s>>>(L, g->col_idx, indeg);
+        k_indeg_key_direct<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, indeg, ka);
+        k_iota<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, va);
+        for (int p = 0; p < 4; ++p) {
+            di_status r = radix_pass(ka, va, kb, vb, n, 8 * p, 0xff, s);
+            if (r != DI_OK) return r;
+            std::swap(ka, kb);
+            std::swap(va, vb);
+        }
+        // va: ids by in-degree, largest first; ka: the sorted keys
+        const int k = std::min(kHotSlots, n);
+        k_count_hot<<<1, 32, 0, s>>>(k, ka, kHotMinInDeg, cnt);
+        int hk = 0;
+        DI_CUDA(cudaMemcpyAsync(&hk, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+        DI_CUDA(cudaStreamSynchronize(s));
+        g->n_hot = hk;
+        DI_CUDA(cudaMallocAsync(&g->hot_ids, sizeof(int) * kHotSlots, s));
+        if (hk > 0) DI_CUDA(cudaMemcpyAsync(g->hot_ids, va, sizeof(int) * hk, cudaMemcpyDeviceToDevice, s));
+        // perm: the hot ids in in-degree order, then every other id ascending (a stable
+        // two-bucket pass on "not hot" puts the hot ids first; they are then overwritten
+        // with their in-degree order)
+        k_hot_flags<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, kb);           // kb[i] = 1
+        if (hk > 0) k_mark_hot<<<1, 256, 0, s>>>(hk, va, kb);                      // kb[hot] = 0
+        k_iota<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, vb);
+        {
+            di_status r = radix_pass(kb, vb, ka, va + 0, n, 0, 1, s);  // va <- ids, hot first (ascending)
+            if (r != DI_OK) return r;
+        }
+        if (hk > 0) DI_CUDA(cudaMemcpyAsync(va, g->hot_ids, sizeof(int) * hk, cudaMemcpyDeviceToDevice, s));
+        g->perm = va;
+        DI_CUDA(cudaMallocAsync(&g->new_of, sizeof(int) * (size_t)n, s));
+        k_inverse<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, g->perm, g->new_of);
+        // relabeled CSR
+        int *rp2 = nullptr, *ci2 = nullptr;
+        DI_CUDA(cudaMallocAsync(&rp2, sizeof(int) * (size_t)(n + 1), s));
+        DI_CUDA(cudaMallocAsync(&ci2, sizeof(int) * (size_t)std::max<long long>(L, 1), s));
+        k_perm_deg<<<grid_for((long long)n + 1, 256, g->num_sms), 256, 0, s>>>(n, g->perm, g->row_ptr, rp2);
+        di_status r = exclusive_scan(rp2, rp2, (long long)n + 1, s);
+        if (r != DI_OK) return r;
+        if (L > 0)
+            k_perm_cols<<<grid_for(L, 256, g->num_sms), 256, 0, s>>>(n, L, g->perm, g->new_of, g->row_ptr, g->col_idx,
+                                                                    rp2, ci2);
+        cudaFreeAsync(g->row_ptr, s);
+        cudaFreeAsync(g->col_idx, s);
+        g->row_ptr = rp2;
+        g->col_idx = ci2;
+        if (g->V) {
+            double *v2 = nullptr;
+            DI_CUDA(cudaMallocAsync(&v2, sizeof(double) * (size_t)n, s));
+            k_perm_values<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, g->perm, g->V, v2);
+            cudaFreeAsync(g->V, s);
+            g->V = v2;
+        }
+        cudaFreeAsync(indeg, s);
+        cudaFreeAsync(ka, s);
+        cudaFreeAsync(kb, s);
+        cudaFreeAsync(vb, s);
+        cudaFreeAsync(cnt, s);
+        DI_CUDA(cudaGetLastError());
+    }
+
+    // 2. out-degree classes and the per-warp frontier regions of the sweep scan
     // one wave of scan CTAs (every chunk resident at once), at most kMaxScanBlocks
     g->G = std::max(1, std::min(std::min(kMaxScanBlocks, g->num_sms * scan_blocks_per_sm()), ceil_div(n, kChunkAlign)));
     g->chunk = ceil_div(ceil_div(n, g->G), kChunkAlign) * kChunkAlign;
     g->G = ceil_div(n, g->chunk);
+    g->W = g->G * kWarps;
+    const long long npad = (long long)g->G * g->chunk;
+    DI_CUDA(cudaMallocAsync(&g->bin_of, sizeof(int) * (size_t)n, s));
+    DI_CUDA(cudaMallocAsync(&g->cls, (size_t)npad, s));
+    DI_CUDA(cudaMemsetAsync(g->cls, 0, (size_t)npad, s));
+    DI_CUDA(cudaMallocAsync(&g->inv_deg, sizeof(double) * (size_t)n, s));
+    DI_CUDA(cudaMallocAsync(&g->inv_deg32, sizeof(float) * (size_t)n, s));
+    DI_CUDA(cudaMallocAsync(&g->rec64, sizeof(RowRec<double>) * (size_t)n, s));
+    DI_CUDA(cudaMallocAsync(&g->rec32, sizeof(RowRec<float>) * (size_t)n, s));
+    k_out_bins<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, g->row_ptr, kOutCut1, kOutCut2, g->d, g->bin_of, g->cls,
+                                                           g->inv_deg, g->inv_deg32, g->rec64, g->rec32);
     {
+        const int W = g->W;
         int *cnt = nullptr;
-        DI_CUDA(cudaMallocAsync(&cnt, sizeof(int) * 3 * (size_t)g->G, s));
-        DI_CUDA(cudaMallocAsync(&g->region, sizeof(int) * 3 * (size_t)(g->G + 1), s));
-        DI_CUDA(cudaMallocAsync(&g->fcount, sizeof(int) * 3 * (size_t)g->G, s));
-        DI_CUDA(cudaMemsetAsync(g->fcount, 0, sizeof(int) * 3 * (size_t)g->G, s));
-        k_chunk_bin_counts<<<g->G, 256, 0, s>>>(n, g->chunk, g->bin_of, cnt, g->G);
-        k_region_scan<<<1, 32, 0, s>>>(g->G, cnt, g->region);
-        std::vector<int> h(3 * (size_t)(g->G + 1));
+        DI_CUDA(cudaMallocAsync(&cnt, sizeof(int) * kLists * (size_t)W, s));
+        DI_CUDA(cudaMallocAsync(&g->region, sizeof(int) * kLists * (size_t)(W + 1), s));
+        DI_CUDA(cudaMallocAsync(&g->fcount, sizeof(int) * kLists * (size_t)W, s));
+        DI_CUDA(cudaMemsetAsync(g->fcount, 0, sizeof(int) * kLists * (size_t)W, s));
+        DI_CUDA(cudaMallocAsync(&g->pre, sizeof(int) * kLists * (size_t)(W + 1), s));
+        DI_CUDA(cudaMemsetAsync(g->pre, 0, sizeof(int) * kLists * (size_t)(W + 1), s));
+        DI_CUDA(cudaMallocAsync(&g->ticket, sizeof(unsigned), s));
+        DI_CUDA(cudaMemsetAsync(g->ticket, 0, sizeof(unsigned), s));
+        k_sub_counts<<<W, 256, 0, s>>>(n, g->chunk / kWarps, g->cls, cnt, W);
+        k_region_scan<<<1, 32, 0, s>>>(W, cnt, g->region);
+        std::vector<int> h(kLists * (size_t)(W + 1));
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(h.data(), g->region, sizeof(int) * h.size(), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         cudaFreeAsync(cnt, s);
         if (e != cudaSuccess) return cuda_fail(e, "frontier regions");
-        int G = g->G;
-        int t1 = h[0 * (G + 1) + G], t2 = h[1 * (G + 1) + G] - t1, t3 = h[2 * (G + 1) + G] - t1 - t2;
-        g->bin_count[1] = t1;
-        g->bin_count[2] = t2;
-        g->bin_count[3] = t3;
-        g->bin_count[0] = n - t1 - t2 - t3;
+        long long prev = 0;
+        for (int L = 0; L < kLists; ++L) {
+            long long end = h[(size_t)L * (W + 1) + W];
+            g->bin_count[L] = (int)(end - prev);
+            prev = end;
+        }
     }
 
     // 3. in-link CSR: stable LSD radix sort of (target, source) pairs in source order
@@ -539,44 +657,6 @@ di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_de
         DI_CUDA(cudaMemcpyAsync(&tot, g->long_prefix + g->n_long_rows, sizeof(int), cudaMemcpyDeviceToHost, s));
         DI_CUDA(cudaStreamSynchronize(s));
         g->n_long_tasks = tot;
-    }
-    // 6. hot targets: the kHotSlots largest in-degrees (at least kHotMinInDeg), ties by lower id;
-    //    their edges are re-encoded so the push sums them in shared memory
-    DI_CUDA(cudaMallocAsync(&g->hot_ids, sizeof(int) * kHotSlots, s));
-    g->n_hot = 0;
-    if (L > 0) {
-        int *ka = nullptr, *kb = nullptr, *va = nullptr, *vb = nullptr, *cnt = nullptr;
-        DI_CUDA(cudaMallocAsync(&ka, sizeof(int) * (size_t)n, s));
-        DI_CUDA(cudaMallocAsync(&kb, sizeof(int) * (size_t)n, s));
-        DI_CUDA(cudaMallocAsync(&va, sizeof(int) * (size_t)n, s));
-        DI_CUDA(cudaMallocAsync(&vb, sizeof(int) * (size_t)n, s));
-        DI_CUDA(cudaMallocAsync(&cnt, sizeof(int), s));
-        k_indeg_key<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, g->in_ptr, ka);
-        k_iota<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, va);
-        for (int p = 0; p < 4; ++p) {
-            di_status r = radix_pass(ka, va, kb, vb, n, 8 * p, 0xff, s);
-            if (r != DI_OK) return r;
-            std::swap(ka, kb);
-            std::swap(va, vb);
-        }
-        const int k = std::min(kHotSlots, n);
-        k_count_hot<<<1, 32, 0, s>>>(k, ka, kHotMinInDeg, cnt);
-        int hk = 0;
-        DI_CUDA(cudaMemcpyAsync(&hk, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
-        DI_CUDA(cudaStreamSynchronize(s));
-        g->n_hot = hk;
-        if (hk > 0) {
-            DI_CUDA(cudaMemcpyAsync(g->hot_ids, va, sizeof(int) * hk, cudaMemcpyDeviceToDevice, s));
-            int *slot_of = kb;  // reuse: n ints
-            k_fill<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, -1, slot_of);
-            k_hot_slots<<<1, 256, 0, s>>>(hk, g->hot_ids, slot_of);
-            k_encode_hot<<<grid_for(L, 256, g->num_sms), 256, 0, s>>>(L, slot_of, g->col_idx);
-        }
-        cudaFreeAsync(ka, s);
-        cudaFreeAsync(kb, s);
-        cudaFreeAsync(va, s);
-        cudaFreeAsync(vb, s);
-        cudaFreeAsync(cnt, s);
     }
     DI_CUDA(cudaGetLastError());
     return DI_OK;

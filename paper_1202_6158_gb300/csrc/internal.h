@@ -1,16 +1,19 @@
 // internal.h -- private structures of libditer shared by its translation units.
 //
 // Device layout of one graph (n nodes, L edges), all owned by di_graph:
-//   row_ptr int32[n+1], col_idx int32[L]        out-link CSR (the input, copied); after ingest an
-//                                               edge to hot target slot s is stored as -1 - s
-//   hot_ids int32[n_hot]                        the hot targets (top in-degree, ties by lower id)
+//   perm    int32[n], new_of int32[n]           internal numbering: nodes sorted by in-degree, largest
+//                                               first (stable); perm[r] = input id of internal node r,
+//                                               new_of = its inverse.  Every array below is indexed by
+//                                               internal ids; inputs and outputs are mapped at the edges.
+//   row_ptr int32[n+1], col_idx int32[L]        out-link CSR in internal ids
+//   hot_ids int32[n_hot]                        input ids of the hot targets = internal 0..n_hot-1
 //   in_ptr  int32[n+1], in_src  int32[L]        in-link CSR, sources ascending
-//   bin_of  int32[n]                            out-degree bin (0 dangling, 1 thread, 2 warp, 3 CTA)
+//   bin_of  int32[n], cls uint8[npad]           out-degree class (0 dangling, 1 thread, 2 warp, 3 CTA)
 //   in_bin_of int32[n], pull_ids int32[n]       in-degree bin and ids grouped by it
 //   F64 / F32  [n padded to 4]                  fluid F (one of the two per solve)
 //   H       double[n]                           history H
-//   frontier FEntry[n - dangling]               per-sweep selected nodes; bin b, chunk c
-//                                               writes at base_b + region[b][c] + k
+//   sel     Sel[n]                              per-sweep selected nodes (id, sent); list L of
+//                                               warp sub-chunk g is written at region[L][g] + k
 //   X, Z[2]  double[n]                          power-iteration iterate and d*x/outdeg
 #pragma once
 
@@ -26,7 +29,10 @@ namespace diter {
 constexpr int kScanThreads = 256;       // threads of the sweep scan / push CTAs
 constexpr int kScanVec = 2;             // fluid elements per thread per tile (16 B of FP64)
 constexpr int kScanTile = kScanThreads * kScanVec;
-constexpr int kChunkAlign = 1024;       // scan chunks are multiples of the FP32 tile (256 x float4)
+constexpr int kChunkAlign = 1024;       // scan chunks are multiples of 8 warp steps
+constexpr int kWarps = kScanThreads / 32;  // warps per scan / push CTA; each owns a sub-chunk
+constexpr int kStep = 128;              // nodes a warp reads per step (4 per lane)
+constexpr int kLists = 4;               // selected nodes: 0 dangling, 1 thread, 2 warp, 3 CTA per source
 constexpr int kMaxScanBlocks = 152 * 8; // 8 CTAs per SM on 152 SMs
 constexpr int kOutCut1 = 8;             // out-degree <= cut1: one thread per source
 constexpr int kOutCut2 = 1024;          // out-degree <= cut2: one warp per source; above: whole CTA
@@ -34,17 +40,25 @@ constexpr int kInCut1 = 8;              // in-degree <= cut1: one thread per row
 constexpr int kInCut2 = 2048;           // in-degree <= cut2: one warp per row; above: chunked
 constexpr int kPullChunk = 2048;        // in-links per chunk task for the longest rows
 constexpr int kTraceCap = 4096;         // sweep records kept when tracing
+constexpr int kExactEvery = 4;          // the scan sums |F|_1 exactly every this many sweeps
 constexpr int kHotSlots = 256;          // most-linked-to targets accumulated in shared memory by the push
 constexpr int kHotMinInDeg = 32;        // a target needs at least this many in-links to get a slot
 
-// one selected node of a sweep: its out-link range and the amount each child receives
+// one selected node of a sweep and the fluid it hands over
 template <typename FT>
-struct __align__(16) FEntryT {
-    int beg;    // row_ptr[i]
-    int deg;    // outdeg(i) > 0
-    FT w;       // d * sent / outdeg(i), in the fluid's precision
+struct __align__(16) Sel {
+    int node;
+    int pad;
+    FT sent;    // F_node at the snapshot, in the fluid's precision
 };
-using FEntry = FEntryT<double>;  // 16 bytes; the FP32 form is padded to the same size
+
+// a node's out-link range and d/outdeg, read by the push with one 16-byte access
+template <typename FT>
+struct __align__(16) RowRec {
+    int beg;
+    int deg;
+    FT inv;
+};
 
 // per-CTA results of the sweep scan, reduced in fixed order by the finalize kernel.
 // Fluid sums are 64-bit fixed point at the sweep's scale 2^-S (see fixed_scale).
@@ -52,9 +66,9 @@ struct __align__(16) ScanPartial {
     long long l1;      // sum of F over the CTA's chunk before selection (fixed point)
     long long out;     // fluid of selected nodes with children (fixed point)
     long long dng;     // fluid of selected dangling nodes (fixed point)
-    long long edges;   // out-links of the selected nodes
+    long long edges;   // out-links of the selected nodes (written by the push kernel)
     long long srcs;    // selected nodes
-    long long entries; // selected nodes with out-links (frontier entries written)
+    long long entries; // selected nodes with out-links
     double l1d;        // FP64 sum, used by the exact confirmation kernel
     double pad;
 };
@@ -75,7 +89,8 @@ struct SolveState {
     int done;              // 0 running, 1 converged, 2 limit reached, 3 non-finite residual
     int trace_on;
     int body_runs;         // executions of the finalize kernel (one per loop iteration)
-    int pad[3];
+    int exact;             // 1 when the sweep now running sums |F|_1 exactly (every kExactEvery sweeps)
+    int pad[2];
 };
 
 struct PowerState {
@@ -108,23 +123,31 @@ struct di_graph {
     int *row_ptr = nullptr, *col_idx = nullptr;
     int *in_ptr = nullptr, *in_src = nullptr;
     int *bin_of = nullptr, *in_bin_of = nullptr, *pull_ids = nullptr;
+    unsigned char *cls = nullptr;      // [npad] out-degree class per node, 0 on the padding
     double *V = nullptr;               // NULL: uniform 1/n
     double *inv_deg = nullptr;         // d / outdeg(i), 0 for dangling nodes (FP64)
     float *inv_deg32 = nullptr;        // the same rounded to FP32
-    int bin_count[4] = {0, 0, 0, 0};   // static out-degree bin sizes
+    diter::RowRec<double> *rec64 = nullptr;  // [n] {row start, outdeg, d/outdeg}
+    diter::RowRec<float> *rec32 = nullptr;   // [n] the same with d/outdeg in FP32
+    int bin_count[4] = {0, 0, 0, 0};   // static out-degree class sizes
     int in_bin_count[3] = {0, 0, 0};
     int n_long_rows = 0;               // rows of in-degree bin 2
     int *long_prefix = nullptr;        // [n_long_rows + 1] exclusive prefix of chunk tasks
     int n_long_tasks = 0;
-    int *hot_ids = nullptr;            // [kHotSlots] node id of each hot slot
+    int *hot_ids = nullptr;            // [kHotSlots] input id of each hot target (internal ids 0..n_hot-1)
     int n_hot = 0;
+    int *perm = nullptr;               // [n] internal -> input id
+    int *new_of = nullptr;             // [n] input -> internal id
 
     // sweep structures
     int G = 0;                         // scan CTAs
-    int chunk = 0;                     // nodes per scan CTA (multiple of kScanTile)
-    int *region = nullptr;             // [3][G+1]: exclusive offsets of bins 1..3 per chunk
-    int *fcount = nullptr;             // [3][G]: entries written per chunk in the last sweep
-    diter::FEntry *frontier = nullptr; // capacity n - dangling
+    int chunk = 0;                     // nodes per scan CTA (multiple of kChunkAlign)
+    int W = 0;                         // warp sub-chunks, G * kWarps, chunk / kWarps nodes each
+    int *region = nullptr;             // [kLists][W+1]: offset of each list's entries per sub-chunk
+    int *fcount = nullptr;             // [kLists][W]: entries written per sub-chunk in the last sweep
+    int *pre = nullptr;                // [kLists][W+1]: exclusive prefix of fcount, per list (last scan CTA)
+    unsigned *ticket = nullptr;        // finished scan CTAs of the current sweep
+    void *sel = nullptr;               // Sel<FT>[n]: the selected nodes of a sweep
     double *F64 = nullptr;
     float *F32 = nullptr;
     double *H = nullptr;
@@ -170,6 +193,7 @@ di_status sweep_alloc(di_graph *g);
 di_status run_solve(di_graph *g, const di_solve_opts &o, const int *seeds_dev, const double *seed_w_dev, int nseeds,
                     double wsum, double *H_out, bool out_on_device, di_stats *st);
 di_status copy_state(const di_graph *g, double *F_out, bool F_dev, double *H_out, bool H_dev);
+di_status gather_x(di_graph *g, const double *src, double *dst, bool dst_dev);
 
 // power iteration (power.cu)
 di_status power_alloc(di_graph *g);

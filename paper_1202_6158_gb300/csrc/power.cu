@@ -310,9 +310,10 @@ di_status run_power(di_graph *g, double tol, int max_iter, int profile, double *
     }
     DI_CUDA(cudaEventRecord(g->ev1, s));
     DI_CUDA(cudaMemcpyAsync(g->h_pst, g->pst, sizeof(PowerState), cudaMemcpyDeviceToHost, s));
-    if (X_out)
-        DI_CUDA(cudaMemcpyAsync(X_out, g->X, sizeof(double) * (size_t)g->n,
-                                out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (X_out) {
+        di_status r = gather_x(g, g->X, X_out, out_dev);
+        if (r != DI_OK) return r;
+    }
     DI_CUDA(cudaStreamSynchronize(s));
     float ms = 0.f;
     DI_CUDA(cudaEventElapsedTime(&ms, g->ev0, g->ev1));

@@ -3,36 +3,35 @@
 // One sweep (Section 4.2: every node whose fluid is above a threshold is
 // chosen, and the threshold is lowered progressively) is three kernels:
 //
-//   k_sweep_scan<FT>   reads all of F once (128-bit loads).  It sums |F|_1
-//                      exactly in FP64 and selects S = {i : F_i > T}.  For each
-//                      selected node it moves the fluid into the history
-//                      (H_i += sent, F_i = 0: the J_i F step of Section 2.2), adds
-//                      (1-d)*sent to the removed mass (sent for a dangling node,
-//                      Section 3.3) and appends {row start, outdeg, d*sent/outdeg}
-//                      to the frontier list of the node's out-degree bin.  Lists
-//                      are written per scan chunk at offsets fixed at create time,
-//                      in ascending id, with no atomics (warp ballot-free scans
-//                      of per-thread counts, block prefix through shared memory).
-//   k_sweep_push<FT>   one CTA per scan chunk pushes its chunk's frontier:
-//                      F_j += d*sent/outdeg_i along every out-link (ALGO-REF's
-//                      inner loop) with red.global.add; a CTA per source above
-//                      kOutCut2 out-links, a warp per source above kOutCut1, a
-//                      thread per source otherwise; column indices come in as
-//                      128-bit loads.
-//   k_sweep_finalize   one CTA reduces the per-chunk partials in fixed order,
+//   k_sweep_scan<FT>   streams F and the one-byte out-degree class of every node
+//                      (no dependent loads, no block barriers).  It sums |F|_1 in
+//                      exact 64-bit fixed point, selects S = {i : F_i > T} (for
+//                      FP64 an integer compare of the bit patterns), zeroes F_i for
+//                      the selected nodes and appends (i, sent) to the list of the
+//                      node's class, in ascending id, with warp prefix sums; each
+//                      warp writes at offsets fixed at create time, so there are
+//                      no atomics.  It also sums the removed mass: (1-d)*sent for
+//                      nodes with children, sent for dangling ones (Section 3.3).
+//   k_sweep_push<FT>   adds sent to H_i (the J_i F step of Section 2.2) and pushes
+//                      d*sent/outdeg_i along every out-link (ALGO-REF's inner loop)
+//                      with red.global.add; a CTA per node above kOutCut2
+//                      out-links, a warp per node above kOutCut1, a lane per node
+//                      otherwise; 128-bit column-index loads; the most-linked-to
+//                      targets are summed in shared memory first.
+//   k_sweep_finalize   one CTA reduces the per-CTA partials in fixed order,
 //                      R = |F|_1 - removed, sets the next threshold
 //                      T = beta*R/n (halved after an empty sweep), and stops the
 //                      CUDA-graph while-loop when R <= tol*(1-d) or a limit hits.
 //
-// All of S gives its fluid to H before any push (the scan kernel finishes
-// before the push kernel starts), so a sweep is the diffusion of the set S on
-// a snapshot of F: F' = (I - J_S + dPJ_S)F, H' = H + J_S F.  Theorem 1
+// All of S gives up its fluid before any push (the scan kernel finishes before
+// the push kernel starts), so a sweep is the diffusion of the set S on a
+// snapshot of F: F' = (I - J_S + dPJ_S)F, H' = H + J_S F.  Theorem 1
 // (H + F = F_0 + dPH) holds after every sweep by the induction of Section 3.1.
 // Fluid pushed into a node of S during the push stays in F for a later sweep.
 //
 // The whole loop is one CUDA graph: a while-conditional node whose body is the
 // three kernels, so a solve makes no host round trip per sweep.  After the loop
-// the exact |F|_1 is recomputed in fixed order to confirm the stop.
+// the exact |F|_1 is recomputed in FP64 to confirm the stop.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -109,10 +108,10 @@ __global__ void k_init_zero(int npad, int n, FT *__restrict__ F, double *__restr
 // F_0 = (1-d) * w_s / sum(w) on the seeds (V of a personalized query)
 template <typename FT>
 __global__ void k_init_seeds(int nseeds, const int *__restrict__ seeds, const double *__restrict__ w, double wsum,
-                             double one_minus_d, FT *__restrict__ F) {
+                             double one_minus_d, const int *__restrict__ new_of, FT *__restrict__ F) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nseeds; k += gridDim.x * blockDim.x) {
         double v = (w ? w[k] : 1.0) / wsum;
-        atomicAdd(&F[seeds[k]], (FT)(one_minus_d * v));
+        atomicAdd(&F[new_of[seeds[k]]], (FT)(one_minus_d * v));
     }
 }
 
@@ -163,6 +162,33 @@ __device__ __forceinline__ long long to_fixed(double x, int S) {
 
 __device__ __forceinline__ long long to_fixed(float x, int S) { return to_fixed((double)x, S); }
 
+// Streaming loads of the scan carry an L2 evict-first policy so that the scan's
+// pass over all of F does not push the push kernel's working set out of L2.  (F is
+// written by the scan itself, so its loads stay on the coherent path; the class
+// bytes are read-only.)
+__device__ __forceinline__ unsigned long long evict_first_policy() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ double2 ld_stream(const double2 *a, unsigned long long pol) {
+    double2 v;
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+                 : "=d"(v.x), "=d"(v.y) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float4 ld_stream(const float4 *a, unsigned long long pol) {
+    float4 v;
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(a), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ unsigned ld_stream(const unsigned *a, unsigned long long pol) {
+    unsigned v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+    return v;
+}
+
 template <typename FT>
 struct ScanOps;
 
@@ -170,271 +196,402 @@ struct ScanOps;
 // orders non-negative doubles exactly like their values (F >= 0 throughout).
 template <>
 struct ScanOps<double> {
-    using VT = double2;
-    static constexpr int VN = 2;
     using Key = long long;
     __device__ static Key key(double T) { return __double_as_longlong(T); }
     __device__ static bool above(double f, Key k) { return __double_as_longlong(f) > k; }
+    // four consecutive values starting at a 32-byte boundary
+    __device__ static void load4(const double *p, double v[4], unsigned long long pol) {
+        const double2 a = ld_stream(reinterpret_cast<const double2 *>(p), pol);
+        const double2 b = ld_stream(reinterpret_cast<const double2 *>(p) + 1, pol);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    __device__ static void store4(double *p, const double v[4]) {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+    }
 };
 
 template <>
 struct ScanOps<float> {
-    using VT = float4;
-    static constexpr int VN = 4;
     using Key = float;
     __device__ static Key key(double T) { return (float)T; }
     __device__ static bool above(float f, Key k) { return f > k; }
+    __device__ static void load4(const float *p, float v[4], unsigned long long pol) {
+        const float4 a = ld_stream(reinterpret_cast<const float4 *>(p), pol);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+    __device__ static void store4(float *p, const float v[4]) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
 };
 
+// The sweep scan streams F and the one-byte out-degree class of every node and
+// does no dependent load: each warp owns a sub-chunk of chunk/8 nodes, reads it
+// 128 nodes per step (4 per lane, the next step's loads issued before the current
+// step is processed), and appends the selected nodes (id, sent) of each class to
+// that class's list in ascending id order with a warp prefix sum; the lists'
+// per-sub-chunk capacities are fixed at create time, so no atomics are needed.
+// The last scan CTA to finish (a ticket counter, no waiting) turns the per-sub-chunk
+// counts into exclusive prefix sums per list, so the push can spread the selected
+// nodes evenly over all its warps whatever their distribution over the chunks.
+// Each thread sums a contiguous run of sub-chunks for every list, one block scan
+// covers the four lists, then each thread writes its run.
+__device__ void prefix_counts(const int *__restrict__ fcount, int W, int *__restrict__ pre) {
+    constexpr int kCap = 8192;                     // sub-chunks staged per pass (32 KB)
+    __shared__ int s_c[kCap];
+    __shared__ int s_w[kWarps];
+    __shared__ int s_carry;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int L = 0; L < kLists; ++L) {
+        if (threadIdx.x == 0) s_carry = 0;
+        for (int base = 0; base < W; base += kCap) {
+            const int m = min(kCap, W - base);
+            // coalesced loads, all in flight together
+            for (int t = threadIdx.x; t < m; t += kScanThreads) s_c[t] = __ldcg(fcount + L * W + base + t);
+            __syncthreads();
+            const int per = (m + kScanThreads - 1) / kScanThreads;
+            const int g0 = min(m, threadIdx.x * per), g1 = min(m, g0 + per);
+            int a = 0;
+            for (int g = g0; g < g1; ++g) a += s_c[g];
+            int x = a;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) s_w[w] = x;
+            __syncthreads();
+            int off = s_carry, tot = 0;
+            for (int k = 0; k < kWarps; ++k) {
+                off += k < w ? s_w[k] : 0;
+                tot += s_w[k];
+            }
+            int run = off + x - a;
+            for (int g = g0; g < g1; ++g) {
+                pre[L * (W + 1) + base + g] = run;
+                run += s_c[g];
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) s_carry += tot;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) pre[L * (W + 1) + W] = s_carry;
+        __syncthreads();
+    }
+}
+
 template <typename FT>
-__global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int n, int chunk, FT *__restrict__ F,
-                                                             double *__restrict__ H, const int *__restrict__ row_ptr,
-                                                             const FT *__restrict__ inv_deg,
-                                                             const int *__restrict__ region, int G,
-                                                             int *__restrict__ fcount, FEntryT<FT> *__restrict__ frontier,
+__global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__restrict__ F,
+                                                             const unsigned char *__restrict__ cls,
+                                                             const int *__restrict__ region, int W,
+                                                             int *__restrict__ fcount, int *__restrict__ pre,
+                                                             unsigned *__restrict__ ticket, Sel<FT> *__restrict__ sel,
                                                              ScanPartial *__restrict__ part,
-                                                             const SolveState *__restrict__ st, double d) {
+                                                             const SolveState *__restrict__ st) {
     using Ops = ScanOps<FT>;
-    using VT = typename Ops::VT;
-    constexpr int VN = Ops::VN;
-    constexpr int NW = kScanThreads / 32;
-    __shared__ int s_wcnt[3][NW];
-    __shared__ double s_red_d[NW];
-    __shared__ long long s_red_l[NW];
+    __shared__ long long s_red[kWarps];
+    __shared__ unsigned s_ticket;
     if (st->done) return;
     const typename Ops::Key key = Ops::key(st->T);
     const int S = fixed_scale(st->R);
-    const int c = blockIdx.x;
+    const bool exact = (st->sweeps % kExactEvery) == 0;  // the exact |F|_1 of this sweep's start
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const long long beg = (long long)c * chunk;
-    const long long end = min((long long)n, beg + chunk);
-    int run0 = region[0 * (G + 1) + c], run1 = region[1 * (G + 1) + c], run2 = region[2 * (G + 1) + c];
-    const int start0 = run0, start1 = run1, start2 = run2;
-    long long l1 = 0;                 // |F|_1 over this thread's elements (fixed point)
-    long long sent_out = 0, sent_dng = 0;  // fluid moved by selected nodes with / without children
-    int edges = 0, srcs = 0, entries = 0;
-
-    for (long long t0 = beg; t0 < end; t0 += (long long)kScanThreads * VN) {
-        const long long i0 = t0 + (long long)threadIdx.x * VN;
-        FT f[VN];
-        if (i0 < end) {
-            VT v = *reinterpret_cast<const VT *>(F + i0);
-            const FT *pv = reinterpret_cast<const FT *>(&v);
+    const int g = blockIdx.x * kWarps + w;
+    const long long wbeg = (long long)g * wchunk;
+    int run[kLists], start[kLists];
 #pragma unroll
-            for (int k = 0; k < VN; ++k) f[k] = pv[k];
-        } else {
-#pragma unroll
-            for (int k = 0; k < VN; ++k) f[k] = (FT)0;
+    for (int L = 0; L < kLists; ++L) start[L] = run[L] = region[L * (W + 1) + g];
+    long long l1 = 0, s_out = 0, s_dng = 0;  // fixed point: |F|_1, fluid of selected nodes with / without children
+    int srcs = 0, entries = 0;
+    const int nsteps = wchunk / kStep;
+    FT cur[4], nxt[4];
+    unsigned ccur, cnxt = 0;
+    const unsigned long long pol = evict_first_policy();
+    Ops::load4(F + wbeg + 4 * lane, cur, pol);
+    ccur = ld_stream(reinterpret_cast<const unsigned *>(cls + wbeg + 4 * lane), pol);
+    for (int s = 0; s < nsteps; ++s) {
+        const long long i0 = wbeg + (long long)s * kStep + 4 * lane;
+        if (s + 1 < nsteps) {
+            Ops::load4(F + i0 + kStep, nxt, pol);
+            cnxt = ld_stream(reinterpret_cast<const unsigned *>(cls + i0 + kStep), pol);
         }
-        int bin[VN];
-        FEntryT<FT> ent[VN];
+        int lst[4];
+        FT sent[4];
         bool any = false;
+        unsigned packed = 0;  // per-list counts of this lane, 8 bits each
 #pragma unroll
-        for (int k = 0; k < VN; ++k) {
-            const long long i = i0 + k;
-            const FT fv = f[k];
-            const long long fx = to_fixed(fv, S);
-            l1 += fx;
-            bin[k] = -1;
-            if (i < end && Ops::above(fv, key)) {
+        for (int k = 0; k < 4; ++k) {
+            sent[k] = cur[k];
+            const bool pick = Ops::above(cur[k], key);
+            long long fx = 0;
+            if (exact || pick) fx = to_fixed(cur[k], S);
+            if (exact) l1 += fx;
+            lst[k] = -1;
+            if (pick) {
+                const int c = (ccur >> (8 * k)) & 0xff;
                 any = true;
                 srcs += 1;
-                H[i] += (double)fv;                 // J_i F: the fluid moves into the history
-                f[k] = (FT)0;
-                const int rb = row_ptr[i];
-                const int deg = row_ptr[i + 1] - rb;
-                if (deg == 0) {
-                    sent_dng += fx;                 // a dangling node's fluid leaves (Section 3.3)
-                } else {
-                    sent_out += fx;
-                    edges += deg;
-                    entries += 1;
-                    bin[k] = deg <= kOutCut1 ? 0 : (deg <= kOutCut2 ? 1 : 2);
-                    ent[k].beg = rb;
-                    ent[k].deg = deg;
-                    ent[k].w = fv * inv_deg[i];     // d * sent / outdeg(i)
-                }
+                lst[k] = c;
+                packed += 1u << (8 * c);
+                cur[k] = (FT)0;                 // J_i F leaves F ...
+                if (c == 0) s_dng += fx;        // ... and a dangling node's fluid leaves the system (Section 3.3)
+                else { s_out += fx; entries += 1; }
             }
         }
-        if (any) {
-            VT v;
-            FT *pv = reinterpret_cast<FT *>(&v);
-#pragma unroll
-            for (int k = 0; k < VN; ++k) pv[k] = f[k];
-            *reinterpret_cast<VT *>(F + i0) = v;
-        }
-        // ordered compaction of the tile, one bin at a time
-        int excl[3], tot[3];
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            int cnt = 0;
-#pragma unroll
-            for (int k = 0; k < VN; ++k) cnt += (bin[k] == b);
-            int x = cnt;
+        if (any) Ops::store4(F + i0, cur);
+        // one warp prefix sum gives the offsets of all four lists (each field stays below 256)
+        if (__any_sync(kFull, packed)) {
+            unsigned x = packed;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(kFull, x, o);
+                const unsigned y = __shfl_up_sync(kFull, x, o);
                 if (lane >= o) x += y;
             }
-            excl[b] = x - cnt;
-            if (lane == 31) s_wcnt[b][w] = x;
-        }
-        __syncthreads();
+            const unsigned excl = x - packed, total = __shfl_sync(kFull, x, 31);
+            unsigned loc = 0;
 #pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            int off = 0, all = 0;
-#pragma unroll
-            for (int k = 0; k < NW; ++k) {
-                int v = s_wcnt[b][k];
-                off += (k < w) ? v : 0;
-                all += v;
+            for (int k = 0; k < 4; ++k) {
+                const int L = lst[k];
+                if (L >= 0) {
+                    const int sh = 8 * L;
+                    const int base = L == 0 ? run[0] : (L == 1 ? run[1] : (L == 2 ? run[2] : run[3]));
+                    const int idx = base + (int)((excl >> sh) & 0xff) + (int)((loc >> sh) & 0xff);
+                    loc += 1u << sh;
+                    Sel<FT> e;
+                    e.node = (int)(i0 + k);
+                    e.pad = 0;
+                    e.sent = sent[k];
+                    sel[idx] = e;
+                }
             }
-            excl[b] += off;
-            tot[b] = all;
-        }
-        __syncthreads();
-        int p0 = run0 + excl[0], p1 = run1 + excl[1], p2 = run2 + excl[2];
 #pragma unroll
-        for (int k = 0; k < VN; ++k) {
-            if (bin[k] == 0) frontier[p0++] = ent[k];
-            else if (bin[k] == 1) frontier[p1++] = ent[k];
-            else if (bin[k] == 2) frontier[p2++] = ent[k];
+            for (int L = 0; L < kLists; ++L) run[L] += (int)((total >> (8 * L)) & 0xff);
         }
-        run0 += tot[0];
-        run1 += tot[1];
-        run2 += tot[2];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
+        ccur = cnxt;
     }
-    if (threadIdx.x == 0) {
-        fcount[0 * G + c] = run0 - start0;
-        fcount[1 * G + c] = run1 - start1;
-        fcount[2 * G + c] = run2 - start2;
+    if (lane == 0) {
+#pragma unroll
+        for (int L = 0; L < kLists; ++L) fcount[L * W + g] = run[L] - start[L];
     }
-    (void)s_red_d;
-    const long long bl1 = block_sum(l1, s_red_l);
-    const long long bout = block_sum(sent_out, s_red_l);
-    const long long bdng = block_sum(sent_dng, s_red_l);
-    const long long bed = block_sum((long long)edges, s_red_l);
-    const long long bsr = block_sum((long long)srcs, s_red_l);
-    const long long ben = block_sum((long long)entries, s_red_l);
+    const long long bl1 = block_sum(l1, s_red);
+    const long long bout = block_sum(s_out, s_red);
+    const long long bdng = block_sum(s_dng, s_red);
+    const long long bsr = block_sum((long long)srcs, s_red);
+    const long long ben = block_sum((long long)entries, s_red);
     if (threadIdx.x == 0) {
         ScanPartial p;
         p.l1 = bl1;
         p.out = bout;
         p.dng = bdng;
-        p.edges = bed;
+        p.edges = 0;
         p.srcs = bsr;
         p.entries = ben;
         p.l1d = 0.0;
         p.pad = 0.0;
-        part[c] = p;
+        part[blockIdx.x] = p;
+    }
+    // every CTA publishes its counts, then takes a ticket; the last one builds the prefixes
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1u);
+    __syncthreads();
+    if (s_ticket == gridDim.x - 1) {
+        __threadfence();
+        prefix_counts(fcount, W, pre);
+        if (threadIdx.x == 0) *ticket = 0u;
     }
 }
 
 // ------------------------------------------------------------------- push
 
 // One elementary step F_j += w.  Edges into the hot targets (the most-linked-to
-// nodes, encoded as -1 - slot) are summed in the CTA's shared memory: on power-law
-// graphs a single target can receive a few percent of all pushes, and same-address
-// reductions serialize in one L2 slice.
+// nodes, internal ids 0..n_hot-1) are summed in the CTA's shared memory: on
+// power-law graphs a single target can receive a few percent of all pushes, and
+// same-address reductions serialize in one L2 slice.
 template <typename FT>
-__device__ __forceinline__ void push_one(FT *__restrict__ F, FT *hot, int c, FT w) {
-    if (c >= 0) red_add(F + c, w);
-    else atomicAdd(hot + (-1 - c), w);
+__device__ __forceinline__ void push_one(FT *__restrict__ F, FT *hot, int n_hot, int c, FT w) {
+    if (c >= n_hot) red_add(F + c, w);
+    else atomicAdd(hot + c, w);
 }
 
-// Rows of the warp and CTA bins: the head up to a 16-byte boundary, then int4
+// Rows of the warp and CTA classes: the head up to a 16-byte boundary, then int4
 // loads two at a time (all loads of a step are issued before its reductions),
 // then the tail.
 template <typename FT>
-__device__ __forceinline__ void push_row_lanes(const int *__restrict__ col_idx, FT *__restrict__ F, FT *hot, int beg,
-                                               int deg, FT w, int lane, int width) {
+__device__ __forceinline__ void push_row_lanes(const int *__restrict__ col_idx, FT *__restrict__ F, FT *hot, int n_hot,
+                                               int beg, int deg, FT w, int lane, int width) {
     const int head = min(deg, (4 - (beg & 3)) & 3);
-    if (lane < head) push_one(F, hot, __ldg(col_idx + beg + lane), w);
+    if (lane < head) push_one(F, hot, n_hot, __ldg(col_idx + beg + lane), w);
     const int body = (deg - head) >> 2;
     const int4 *v4 = reinterpret_cast<const int4 *>(col_idx + beg + head);
     int k = lane;
     for (; k + width < body; k += 2 * width) {
         const int4 q = __ldg(v4 + k);
         const int4 r = __ldg(v4 + k + width);
-        push_one(F, hot, q.x, w);
-        push_one(F, hot, q.y, w);
-        push_one(F, hot, q.z, w);
-        push_one(F, hot, q.w, w);
-        push_one(F, hot, r.x, w);
-        push_one(F, hot, r.y, w);
-        push_one(F, hot, r.z, w);
-        push_one(F, hot, r.w, w);
+        push_one(F, hot, n_hot, q.x, w);
+        push_one(F, hot, n_hot, q.y, w);
+        push_one(F, hot, n_hot, q.z, w);
+        push_one(F, hot, n_hot, q.w, w);
+        push_one(F, hot, n_hot, r.x, w);
+        push_one(F, hot, n_hot, r.y, w);
+        push_one(F, hot, n_hot, r.z, w);
+        push_one(F, hot, n_hot, r.w, w);
     }
     if (k < body) {
         const int4 q = __ldg(v4 + k);
-        push_one(F, hot, q.x, w);
-        push_one(F, hot, q.y, w);
-        push_one(F, hot, q.z, w);
-        push_one(F, hot, q.w, w);
+        push_one(F, hot, n_hot, q.x, w);
+        push_one(F, hot, n_hot, q.y, w);
+        push_one(F, hot, n_hot, q.z, w);
+        push_one(F, hot, n_hot, q.w, w);
     }
     const int t = head + 4 * body + lane;
-    if (t < deg) push_one(F, hot, __ldg(col_idx + beg + t), w);
+    if (t < deg) push_one(F, hot, n_hot, __ldg(col_idx + beg + t), w);
 }
 
-// a thread-bin row (1..kOutCut1 out-links): all index loads first, then the reductions
-template <typename FT>
-__device__ __forceinline__ void push_short_row(const int *__restrict__ col_idx, FT *__restrict__ F, FT *hot,
-                                               const FEntryT<FT> &e) {
-    int c[kOutCut1];
-#pragma unroll
-    for (int t = 0; t < kOutCut1; ++t) c[t] = t < e.deg ? __ldg(col_idx + e.beg + t) : 0;
-#pragma unroll
-    for (int t = 0; t < kOutCut1; ++t)
-        if (t < e.deg) push_one(F, hot, c[t], e.w);
+// sub-chunk holding item t of a list: the last g with pre[g] <= t
+__device__ __forceinline__ int find_sub(const int *__restrict__ pre, int W, int t) {
+    int lo = 0, hi = W;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(pre + mid) <= t) lo = mid; else hi = mid;
+    }
+    return lo;
 }
 
+// The push.  The selected nodes of each class are numbered 0..total-1 through the
+// prefix sums of the scan, and spread over the whole grid: a CTA per node of the
+// largest class, a warp per node of the middle class, and for the smallest class
+// and the dangling nodes contiguous ranges of 64 per warp (a lane per node, two in
+// flight).  For every selected node i it adds sent to H_i (the J_i F step of
+// Section 2.2) and, unless i is dangling, adds d*sent/outdeg(i) to F_j along every
+// out-link (ALGO-REF's inner loop), every load of a node issued before its
+// reductions.
 template <typename FT>
-__global__ void __launch_bounds__(kScanThreads) k_sweep_push(const int *__restrict__ col_idx, FT *__restrict__ F,
-                                                             const int *__restrict__ region,
-                                                             const int *__restrict__ fcount, int G,
-                                                             const FEntryT<FT> *__restrict__ frontier,
-                                                             const int *__restrict__ hot_ids, int n_hot,
+__global__ void __launch_bounds__(kScanThreads) k_sweep_push(const RowRec<FT> *__restrict__ rec,
+                                                             const int *__restrict__ col_idx, FT *__restrict__ F,
+                                                             double *__restrict__ H, const int *__restrict__ region,
+                                                             const int *__restrict__ pre, int W,
+                                                             const Sel<FT> *__restrict__ sel, int n_hot,
+                                                             ScanPartial *__restrict__ part,
                                                              const SolveState *__restrict__ st) {
     __shared__ FT hot[kHotSlots];
+    __shared__ long long s_red[kWarps];
+    __shared__ int s_idx;
     if (st->done) return;
     for (int t = threadIdx.x; t < kHotSlots; t += kScanThreads) hot[t] = (FT)0;
     __syncthreads();
-    const int c = blockIdx.x;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    // CTA per source: the largest out-degrees
+    const int nwarps = gridDim.x * kWarps, gw = blockIdx.x * kWarps + w;
+    const int *pre3 = pre + 3 * (W + 1), *pre2 = pre + 2 * (W + 1), *pre1 = pre + 1 * (W + 1), *pre0 = pre;
+    long long edges = 0;
+    // class 3: the whole CTA per node
+    const int tot3 = __ldg(pre3 + W);
+    for (int t = blockIdx.x; t < tot3; t += gridDim.x) {
+        if (threadIdx.x == 0) {
+            const int gs = find_sub(pre3, W, t);
+            s_idx = region[3 * (W + 1) + gs] + (t - __ldg(pre3 + gs));
+        }
+        __syncthreads();
+        const Sel<FT> e = sel[s_idx];
+        __syncthreads();
+        const RowRec<FT> rr = rec[e.node];
+        const int b = rr.beg, deg = rr.deg;
+        const FT wv = e.sent * rr.inv;
+        if (threadIdx.x == 0) {
+            H[e.node] += (double)e.sent;
+            edges += deg;
+        }
+        push_row_lanes(col_idx, F, hot, n_hot, b, deg, wv, threadIdx.x, kScanThreads);
+    }
+    // class 2: a warp per node
+    const int tot2 = __ldg(pre2 + W);
+    for (int t = gw; t < tot2; t += nwarps) {
+        int idx = 0;
+        if (lane == 0) {
+            const int gs = find_sub(pre2, W, t);
+            idx = region[2 * (W + 1) + gs] + (t - __ldg(pre2 + gs));
+        }
+        idx = __shfl_sync(kFull, idx, 0);
+        const Sel<FT> e = sel[idx];
+        const RowRec<FT> rr = rec[e.node];
+        const int b = rr.beg, deg = rr.deg;
+        const FT wv = e.sent * rr.inv;
+        if (lane == 0) {
+            H[e.node] += (double)e.sent;
+            edges += deg;
+        }
+        push_row_lanes(col_idx, F, hot, n_hot, b, deg, wv, lane, 32);
+    }
+    // class 0: dangling nodes only move their fluid into H; a contiguous range per warp
     {
-        const int base = region[2 * (G + 1) + c], cnt = fcount[2 * G + c];
-        for (int k = 0; k < cnt; ++k) {
-            const FEntryT<FT> e = frontier[base + k];
-            push_row_lanes(col_idx, F, hot, e.beg, e.deg, e.w, threadIdx.x, kScanThreads);
+        const int tot0 = __ldg(pre0 + W);
+        const int per = (tot0 + nwarps - 1) / nwarps;
+        const int t_beg = min(tot0, gw * per), t_end = min(tot0, t_beg + per);
+        int gl = 0;
+        if (t_beg < t_end) {
+            if (lane == 0) gl = find_sub(pre0, W, t_beg);
+            gl = __shfl_sync(kFull, gl, 0);
+        }
+        for (int t = t_beg + lane; t < t_end; t += 32) {
+            while (__ldg(pre0 + gl + 1) <= t) ++gl;
+            const Sel<FT> e = sel[region[0 * (W + 1) + gl] + (t - __ldg(pre0 + gl))];
+            H[e.node] += (double)e.sent;
         }
     }
-    // warp per source
+    // class 1: a lane per node, two nodes in flight, a contiguous range per warp
     {
-        const int base = region[1 * (G + 1) + c], cnt = fcount[1 * G + c];
-        for (int k = w; k < cnt; k += kScanThreads / 32) {
-            const FEntryT<FT> e = frontier[base + k];
-            push_row_lanes(col_idx, F, hot, e.beg, e.deg, e.w, lane, 32);
+        const int tot1 = __ldg(pre1 + W);
+        const int per = (tot1 + nwarps - 1) / nwarps;
+        const int t_beg = min(tot1, gw * per), t_end = min(tot1, t_beg + per);
+        int gs = 0;
+        if (t_beg < t_end) {
+            if (lane == 0) gs = find_sub(pre1, W, t_beg);
+            gs = __shfl_sync(kFull, gs, 0);
         }
-    }
-    // thread per source, two sources in flight per thread
-    {
-        const int base = region[0 * (G + 1) + c], cnt = fcount[0 * G + c];
-        int k = threadIdx.x;
-        for (; k + kScanThreads < cnt; k += 2 * kScanThreads) {
-            const FEntryT<FT> e0 = frontier[base + k];
-            const FEntryT<FT> e1 = frontier[base + k + kScanThreads];
-            push_short_row(col_idx, F, hot, e0);
-            push_short_row(col_idx, F, hot, e1);
+        int ga = gs;
+        for (int t0 = t_beg; t0 < t_end; t0 += 64) {
+            const int ta = t0 + lane, tb = t0 + 32 + lane;
+            const bool has0 = ta < t_end, has1 = tb < t_end;
+            if (!has0) break;
+            while (__ldg(pre1 + ga + 1) <= ta) ++ga;
+            int gb = ga;
+            if (has1)
+                while (__ldg(pre1 + gb + 1) <= tb) ++gb;
+            const Sel<FT> e0 = sel[region[1 * (W + 1) + ga] + (ta - __ldg(pre1 + ga))];
+            const Sel<FT> e1 = has1 ? sel[region[1 * (W + 1) + gb] + (tb - __ldg(pre1 + gb))] : e0;
+            ga = gb;
+            const RowRec<FT> r0 = rec[e0.node], r1 = rec[e1.node];
+            const int b0 = r0.beg, d0 = r0.deg;
+            const int b1 = r1.beg, d1 = has1 ? r1.deg : 0;
+            const FT w0 = e0.sent * r0.inv, w1 = e1.sent * r1.inv;
+            const double h0 = H[e0.node];
+            const double h1 = has1 ? H[e1.node] : 0.0;
+            int c0[kOutCut1], c1[kOutCut1];
+#pragma unroll
+            for (int k = 0; k < kOutCut1; ++k) {
+                c0[k] = k < d0 ? __ldg(col_idx + b0 + k) : 0;
+                c1[k] = k < d1 ? __ldg(col_idx + b1 + k) : 0;
+            }
+            H[e0.node] = h0 + (double)e0.sent;
+            if (has1) H[e1.node] = h1 + (double)e1.sent;
+            edges += d0 + d1;
+#pragma unroll
+            for (int k = 0; k < kOutCut1; ++k) {
+                if (k < d0) push_one(F, hot, n_hot, c0[k], w0);
+                if (k < d1) push_one(F, hot, n_hot, c1[k], w1);
+            }
         }
-        if (k < cnt) push_short_row(col_idx, F, hot, frontier[base + k]);
     }
     // the CTA's sums for the hot targets go to F once
     __syncthreads();
     for (int t = threadIdx.x; t < n_hot; t += kScanThreads) {
         const FT v = hot[t];
-        if (v != (FT)0) red_add(F + hot_ids[t], v);
+        if (v != (FT)0) red_add(F + t, v);
     }
+    const long long be = block_sum(edges, s_red);
+    if (threadIdx.x == 0) part[blockIdx.x].edges = be;
 }
 
 // --------------------------------------------------------------- finalize
@@ -471,7 +628,10 @@ __global__ void k_sweep_finalize(int n, int G, const ScanPartial *__restrict__ p
     st->body_runs += 1;
     const double Tused = st->T;
     const int S = fixed_scale(st->R);  // the scale the scan used (st->R is still the previous residual)
-    const double l1 = ldexp((double)fl1, -S);
+    // every kExactEvery sweeps the scan summed all of F; in between |F|_1 is the previous
+    // residual (the removed masses are exact, only the pushes' roundings separate them)
+    const bool exact = (st->sweeps % kExactEvery) == 0;
+    const double l1 = exact ? ldexp((double)fl1, -S) : st->R;
     // removed mass: (1-d)*sent for nodes with children, sent for dangling nodes (Section 3.3)
     const double rem = st->one_minus_d * ldexp((double)fout, -S) + ldexp((double)fdng, -S);
     const double R = l1 - rem;  // |F|_1 after the sweep (exact arithmetic)
@@ -543,33 +703,68 @@ __global__ void k_sum_h(int n, const double *__restrict__ H, double *out_partial
     if (threadIdx.x == 0) out_partials[blockIdx.x] = a;
 }
 
-__global__ void k_scale_copy(int n, const double *__restrict__ H, const double *__restrict__ partials, int np,
-                             double *__restrict__ out) {
-    __shared__ double inv;
+// out[i] = src[new_of[i]] * scale, back in the caller's numbering; with partials the scale
+// is 1/sum(partials) (the Section 3.3 renormalization H/|H|_1)
+template <typename FT>
+__global__ void k_gather_out(int n, const int *__restrict__ new_of, const FT *__restrict__ src,
+                             const double *__restrict__ partials, int np, double *__restrict__ out) {
+    __shared__ double scale;
     if (threadIdx.x == 0) {
-        double a = 0.0;
-        for (int k = 0; k < np; ++k) a += partials[k];
-        inv = a > 0.0 ? 1.0 / a : 0.0;
+        double a = 1.0;
+        if (partials) {
+            a = 0.0;
+            for (int k = 0; k < np; ++k) a += partials[k];
+            a = a > 0.0 ? 1.0 / a : 0.0;
+        }
+        scale = a;
     }
     __syncthreads();
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        out[i] = H[i] * inv;
-}
-
-template <typename FT>
-__global__ void k_to_double(int n, const FT *__restrict__ in, double *__restrict__ out) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        out[i] = (double)in[i];
+        out[i] = (double)src[new_of[i]] * scale;
 }
 
 template <typename FT> const FT *inv_deg_of(di_graph *g);
 template <> const double *inv_deg_of<double>(di_graph *g) { return g->inv_deg; }
 template <> const float *inv_deg_of<float>(di_graph *g) { return g->inv_deg32; }
-template <typename FT> FEntryT<FT> *frontier_of(di_graph *g) { return reinterpret_cast<FEntryT<FT> *>(g->frontier); }
+template <typename FT> const RowRec<FT> *rec_of(di_graph *g);
+template <> const RowRec<double> *rec_of<double>(di_graph *g) { return g->rec64; }
+template <> const RowRec<float> *rec_of<float>(di_graph *g) { return g->rec32; }
+template <typename FT> Sel<FT> *sel_of(di_graph *g) { return reinterpret_cast<Sel<FT> *>(g->sel); }
+
+template <typename FT>
+void launch_scan(di_graph *g, FT *F, cudaStream_t s) {
+    k_sweep_scan<FT><<<g->G, kScanThreads, 0, s>>>(g->chunk / kWarps, F, g->cls, g->region, g->W, g->fcount, g->pre,
+                                                   g->ticket, sel_of<FT>(g), g->part, g->st);
+}
+
+template <typename FT>
+void launch_push(di_graph *g, FT *F, cudaStream_t s) {
+    k_sweep_push<FT><<<g->G, kScanThreads, 0, s>>>(rec_of<FT>(g), g->col_idx, F, g->H, g->region,
+                                                   g->pre, g->W, sel_of<FT>(g), g->n_hot, g->part, g->st);
+}
 
 int elem_grid(di_graph *g, long long work) {
     long long b = (work + 255) / 256;
     return (int)std::max(1LL, std::min(b, (long long)g->num_sms * 8));
+}
+
+// src (internal numbering) -> dst (caller's numbering, host or device)
+template <typename FT>
+di_status gather_out(di_graph *g, const FT *src, const double *partials, int np, double *dst, bool dst_dev) {
+    cudaStream_t s = g->stream;
+    const int n = g->n;
+    if (dst_dev) {
+        k_gather_out<FT><<<elem_grid(g, n), 256, 0, s>>>(n, g->new_of, src, partials, np, dst);
+        DI_CUDA(cudaGetLastError());
+        return DI_OK;
+    }
+    double *tmp = nullptr;
+    DI_CUDA(cudaMallocAsync(&tmp, sizeof(double) * (size_t)n, s));
+    k_gather_out<FT><<<elem_grid(g, n), 256, 0, s>>>(n, g->new_of, src, partials, np, tmp);
+    DI_CUDA(cudaGetLastError());
+    DI_CUDA(cudaMemcpyAsync(dst, tmp, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, s));
+    cudaFreeAsync(tmp, s);
+    return DI_OK;
 }
 
 // Build the while-loop graph of one precision: body = scan -> push -> finalize.
@@ -591,10 +786,8 @@ di_status build_sweep_graph(di_graph *g, int slot, FT *F) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     e = cudaStreamBeginCaptureToGraph(g->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(e, "cudaStreamBeginCaptureToGraph"); }
-    k_sweep_scan<FT><<<g->G, kScanThreads, 0, g->cap>>>(g->n, g->chunk, F, g->H, g->row_ptr, inv_deg_of<FT>(g), g->region,
-                                                         g->G, g->fcount, frontier_of<FT>(g), g->part, g->st, g->d);
-    k_sweep_push<FT><<<g->G, kScanThreads, 0, g->cap>>>(g->col_idx, F, g->region, g->fcount, g->G, frontier_of<FT>(g),
-                                                         g->hot_ids, g->n_hot, g->st);
+    launch_scan<FT>(g, F, g->cap);
+    launch_push<FT>(g, F, g->cap);
     k_sweep_finalize<<<1, 256, 0, g->cap>>>(g->n, g->G, g->part, g->st, g->trace, handle, 1);
     cudaGraph_t captured = nullptr;
     e = cudaStreamEndCapture(g->cap, &captured);
@@ -622,7 +815,7 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, const
     if (seeds) {
         k_init_zero<FT><<<elem_grid(g, npad), 256, 0, s>>>(npad, n, F, g->H);
         k_init_seeds<FT><<<std::max(1, std::min(1024, (nseeds + 255) / 256)), 256, 0, s>>>(nseeds, seeds, seed_w, wsum,
-                                                                                          omd, F);
+                                                                                          omd, g->new_of, F);
     } else {
         k_init_state<FT><<<elem_grid(g, npad), 256, 0, s>>>(n, npad, F, g->H, g->V, omd);
     }
@@ -640,12 +833,9 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, const
             cudaGraphConditionalHandle none = 0;
             for (;;) {
                 DI_CUDA(cudaEventRecord(g->pev[0], s));
-                k_sweep_scan<FT><<<g->G, kScanThreads, 0, s>>>(n, g->chunk, F, g->H, g->row_ptr, inv_deg_of<FT>(g),
-                                                              g->region, g->G, g->fcount, frontier_of<FT>(g), g->part,
-                                                              g->st, g->d);
+                launch_scan<FT>(g, F, s);
                 DI_CUDA(cudaEventRecord(g->pev[1], s));
-                k_sweep_push<FT><<<g->G, kScanThreads, 0, s>>>(g->col_idx, F, g->region, g->fcount, g->G,
-                                                              frontier_of<FT>(g), g->hot_ids, g->n_hot, g->st);
+                launch_push<FT>(g, F, s);
                 DI_CUDA(cudaEventRecord(g->pev[2], s));
                 k_sweep_finalize<<<1, 256, 0, s>>>(n, g->G, g->part, g->st, g->trace, none, 0);
                 DI_CUDA(cudaEventRecord(g->pev[3], s));
@@ -677,25 +867,17 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, const
         if (g->h_st->done != 0) break;
     }
     DI_CUDA(cudaEventRecord(g->ev1, s));
-    // outputs
-    if (o.normalize) {
+    // outputs, in the caller's numbering
+    if (H_out) {
         const int np = elem_grid(g, n);
         double *partials = nullptr;
-        DI_CUDA(cudaMallocAsync(&partials, sizeof(double) * (size_t)np, s));
-        k_sum_h<<<np, 256, 0, s>>>(n, g->H, partials);
-        if (out_dev) {
-            k_scale_copy<<<elem_grid(g, n), 256, 0, s>>>(n, g->H, partials, np, H_out);
-        } else {
-            double *dtmp = nullptr;
-            DI_CUDA(cudaMallocAsync(&dtmp, sizeof(double) * (size_t)n, s));
-            k_scale_copy<<<elem_grid(g, n), 256, 0, s>>>(n, g->H, partials, np, dtmp);
-            DI_CUDA(cudaMemcpyAsync(H_out, dtmp, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, s));
-            cudaFreeAsync(dtmp, s);
+        if (o.normalize) {
+            DI_CUDA(cudaMallocAsync(&partials, sizeof(double) * (size_t)np, s));
+            k_sum_h<<<np, 256, 0, s>>>(n, g->H, partials);
         }
-        cudaFreeAsync(partials, s);
-    } else if (H_out) {
-        DI_CUDA(cudaMemcpyAsync(H_out, g->H, sizeof(double) * (size_t)n,
-                                out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+        di_status r = gather_out<double>(g, g->H, partials, np, H_out, out_dev);
+        if (partials) cudaFreeAsync(partials, s);
+        if (r != DI_OK) return r;
     }
     DI_CUDA(cudaStreamSynchronize(s));
     float ms = 0.f;
@@ -732,9 +914,8 @@ di_status sweep_alloc(di_graph *g) {
     cudaStream_t s = g->stream;
     const int n = g->n;
     const int npad = g->G * g->chunk;
-    const long long cap = std::max<long long>(1, (long long)g->bin_count[1] + g->bin_count[2] + g->bin_count[3]);
     DI_CUDA(cudaMallocAsync(&g->H, sizeof(double) * (size_t)npad, s));
-    DI_CUDA(cudaMallocAsync(&g->frontier, sizeof(FEntry) * (size_t)cap, s));
+    DI_CUDA(cudaMallocAsync(&g->sel, sizeof(Sel<double>) * (size_t)std::max(1, n), s));
     DI_CUDA(cudaMallocAsync(&g->part, sizeof(ScanPartial) * (size_t)g->G, s));
     DI_CUDA(cudaMallocAsync(&g->st, sizeof(SolveState), s));
     DI_CUDA(cudaMemsetAsync(g->st, 0, sizeof(SolveState), s));
@@ -768,28 +949,24 @@ di_status run_solve(di_graph *g, const di_solve_opts &o, const int *seeds, const
     return solve_impl<float>(g, o, g->F32, 1, seeds, seed_w, nseeds, wsum, H_out, out_dev, st);
 }
 
-di_status copy_state(const di_graph *g, double *F_out, bool F_dev, double *H_out, bool H_dev) {
-    cudaStream_t s = g->stream;
-    const int n = g->n;
+di_status gather_x(di_graph *g, const double *src, double *dst, bool dst_dev) {
+    return gather_out<double>(g, src, nullptr, 0, dst, dst_dev);
+}
+
+di_status copy_state(const di_graph *gc, double *F_out, bool F_dev, double *H_out, bool H_dev) {
+    di_graph *g = const_cast<di_graph *>(gc);
     if (F_out) {
-        if (g->last_prec == DI_FP32_MIXED && g->F32) {
-            double *tmp = nullptr;
-            DI_CUDA(cudaMallocAsync(&tmp, sizeof(double) * (size_t)n, s));
-            k_to_double<float><<<std::max(1, std::min(1216, (n + 255) / 256)), 256, 0, s>>>(n, g->F32, tmp);
-            DI_CUDA(cudaMemcpyAsync(F_out, tmp, sizeof(double) * (size_t)n,
-                                    F_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-            cudaFreeAsync(tmp, s);
-        } else if (g->F64) {
-            DI_CUDA(cudaMemcpyAsync(F_out, g->F64, sizeof(double) * (size_t)n,
-                                    F_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-        } else {
-            return set_error(DI_EINVAL, "no solve has run on this graph");
-        }
+        di_status r;
+        if (g->last_prec == DI_FP32_MIXED && g->F32) r = gather_out<float>(g, g->F32, nullptr, 0, F_out, F_dev);
+        else if (g->F64) r = gather_out<double>(g, g->F64, nullptr, 0, F_out, F_dev);
+        else return set_error(DI_EINVAL, "no solve has run on this graph");
+        if (r != DI_OK) return r;
     }
-    if (H_out)
-        DI_CUDA(cudaMemcpyAsync(H_out, g->H, sizeof(double) * (size_t)n,
-                                H_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-    DI_CUDA(cudaStreamSynchronize(s));
+    if (H_out) {
+        di_status r = gather_out<double>(g, g->H, nullptr, 0, H_out, H_dev);
+        if (r != DI_OK) return r;
+    }
+    DI_CUDA(cudaStreamSynchronize(g->stream));
     return DI_OK;
 }
 
