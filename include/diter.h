@@ -223,6 +223,33 @@ di_status di_get_state(const di_graph *g, double *F_out, double *H_out);
  */
 di_status di_get_profile(const di_graph *g, di_profile *out);
 
+/*
+ * di_power without any device allocation.  The paper has no counterpart: this
+ * is a service for callers that cannot call cudaMalloc -- code running while a
+ * CUDA graph is being captured, services that must not grow their device memory
+ * after start-up or that hand out memory only from their own pools, plug-ins in
+ * a host program that owns the GPU's allocator.  It runs the same power
+ * iteration as di_power (X_0 = 0, X_{k+1} = dPX_k + (1-d)/n with the uniform V,
+ * stop when |X_{k+1} - X_k|_1 * d/(1-d) < tol) on the caller's device arrays:
+ *   n        nodes, 1 <= n <= 65536 (larger n is rejected with DI_EINVAL)
+ *   in_ptr   device int32[n+1], in_src device int32[nnz]: the in-link lists
+ *            (row j lists every i with an edge i -> j; any order)
+ *   row_ptr  device int32[n+1]: the out-link row pointers (out-degrees)
+ *   X_out    device double[n], receives X
+ * Its working memory (about 1 MB: two n-sized buffers, partial sums, a control
+ * block) is one static array inside the library, present on every GPU that
+ * loads the library until the process exits.  Every call shares that array and
+ * it keeps the last call's contents, so calls that overlap on the GPU (two
+ * streams, two host threads) race: issue them one after another.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture begins.  The inputs are
+ * checked on the device first (DI_EINVAL names the bad array).  Nothing here
+ * calls cudaMalloc, cudaFree or any allocating routine.
+ */
+di_status di_power_noalloc(int32_t n, const int32_t *in_ptr, const int32_t *in_src, int64_t nnz,
+                           const int32_t *row_ptr, double d, double tol, int32_t max_iter, double *X_out,
+                           di_stats *st, void *stream);
+
 /* Message of the last failure on this host thread ("" if none). */
 const char *di_last_error(void);
 

@@ -23,7 +23,7 @@ from ._lib import (DI_EINVAL, DI_ENOTCONVERGED, DI_FP32_MIXED, DI_FP64, DI_OK, D
 
 __all__ = ["DiGraph", "DiError", "DI_FP64", "DI_FP32_MIXED", "DI_OK", "DI_EINVAL", "DI_ENOTCONVERGED",
            "di_graph_create", "di_free", "di_solve", "di_solve_ex", "di_query", "di_power", "di_power_ex", "di_graph_export",
-           "di_get_trace", "di_get_state", "di_get_profile", "di_version", "load"]
+           "di_get_trace", "di_get_state", "di_get_profile", "di_power_noalloc", "di_version", "load"]
 
 
 def load():
@@ -92,6 +92,21 @@ def di_power_ex(handle, tol, X_out, max_iter=0, profile=0, allow_unconverged=Fal
     d = st.as_dict()
     d["pull_ms"], d["finalize_ms"] = pm.value, fm.value
     return rc, d
+
+
+def di_power_noalloc(n, in_ptr, in_src, row_ptr, d, tol, X_out, max_iter=0, stream=None, allow_unconverged=False):
+    """Power iteration on caller-owned device arrays that allocates no device memory (n <= 65536).
+
+    For callers that cannot allocate (inside a CUDA-graph capture, fixed memory
+    pools, hosts that own the allocator).  All arrays must be device memory.
+    """
+    st = di_stats()
+    if stream is None:
+        stream = _lib.current_stream()
+    ok = (DI_OK, DI_ENOTCONVERGED) if allow_unconverged else (DI_OK,)
+    rc = check(load().di_power_noalloc(int(n), ptr(in_ptr), ptr(in_src), int(len(in_src)), ptr(row_ptr), float(d),
+                                       float(tol), int(max_iter), ptr(X_out), ctypes.byref(st), stream), ok)
+    return rc, st.as_dict()
 
 
 def di_graph_export(handle, perm=None, outdeg=None, in_ptr=None, in_src=None, bin_of=None, in_bin_of=None, cuts=None):
