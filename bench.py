@@ -73,7 +73,7 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms while running."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -89,7 +89,7 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -126,6 +126,31 @@ class ClockSampler:
         loaded = sorted(sm)[len(sm) // 2:] if len(sm) > 2 else sm
         return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def push_traffic():
+    """DRAM bytes per push launch from the committed ncu summary, if sweep.cu is unchanged since.
+
+    profiles/push_sweep_zipf24.md records the sha256 of csrc/sweep.cu it was taken
+    with; a different hash means the kernel changed and the counters no longer apply.
+    """
+    import hashlib
+    src = os.path.join(ROOT, "paper_1202_6158_gb300", "csrc", "sweep.cu")
+    summ = os.path.join(ROOT, "profiles", "push_sweep_zipf24.md")
+    if not (os.path.exists(src) and os.path.exists(summ)):
+        return None
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    vals = {}
+    for line in open(summ):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("sweep.cu sha256") != digest:
+        return None
+    try:
+        return float(vals["dram bytes per launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def dist_env():
@@ -177,7 +202,7 @@ def run_reference(args, w):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="zipf24", choices=sorted(WORKLOADS))
@@ -284,7 +309,7 @@ def main():
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     kd = kernels[dom]
     achieved = kd["alg_bytes"] / (kd["ms"] * 1e-3) / 1e9 if kd["ms"] > 0 else None
-    traffic = None
+    traffic = push_traffic() if dom == "push" else None
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": (achieved / hbm_peak) if achieved else None, "traffic": traffic,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else

@@ -134,18 +134,13 @@ __global__ void k_sub_counts(int n, int wchunk, const unsigned char *__restrict_
     if (threadIdx.x < kLists) cnt[threadIdx.x * W + blockIdx.x] = c[threadIdx.x];
 }
 
-// region[L][g] = (nodes of classes < L) + (nodes of class L in sub-chunks < g)
-__global__ void k_region_scan(int W, const int *__restrict__ cnt, int *__restrict__ region) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    long long base = 0;
-    for (int L = 0; L < kLists; ++L) {
-        long long run = 0;
-        for (int g = 0; g < W; ++g) {
-            region[L * (W + 1) + g] = (int)(base + run);
-            run += cnt[L * W + g];
-        }
-        region[L * (W + 1) + W] = (int)(base + run);
-        base += run;
+// region[L][g] = (nodes of classes < L) + (nodes of class L in sub-chunks < g), from the
+// exclusive scan x of the flattened counts [kLists * W + 1]: region[L][g] = x[L*W + g]
+__global__ void k_region_layout(int W, const int *__restrict__ x, int *__restrict__ region) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < (long long)kLists * (W + 1);
+         t += (long long)gridDim.x * blockDim.x) {
+        const int L = (int)(t / (W + 1)), g = (int)(t % (W + 1));
+        region[t] = x[(long long)L * W + g];
     }
 }
 
@@ -551,7 +546,8 @@ di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_de
     {
         const int W = g->W;
         int *cnt = nullptr;
-        DI_CUDA(cudaMallocAsync(&cnt, sizeof(int) * kLists * (size_t)W, s));
+        DI_CUDA(cudaMallocAsync(&cnt, sizeof(int) * (kLists * (size_t)W + 1), s));
+        DI_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (kLists * (size_t)W + 1), s));
         DI_CUDA(cudaMallocAsync(&g->region, sizeof(int) * kLists * (size_t)(W + 1), s));
         DI_CUDA(cudaMallocAsync(&g->fcount, sizeof(int) * kLists * (size_t)W, s));
         DI_CUDA(cudaMemsetAsync(g->fcount, 0, sizeof(int) * kLists * (size_t)W, s));
@@ -560,7 +556,11 @@ di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_de
         DI_CUDA(cudaMallocAsync(&g->ticket, sizeof(unsigned), s));
         DI_CUDA(cudaMemsetAsync(g->ticket, 0, sizeof(unsigned), s));
         k_sub_counts<<<W, 256, 0, s>>>(n, g->chunk / kWarps, g->cls, cnt, W);
-        k_region_scan<<<1, 32, 0, s>>>(W, cnt, g->region);
+        {
+            di_status r = exclusive_scan(cnt, cnt, (long long)kLists * W + 1, s);
+            if (r != DI_OK) return r;
+        }
+        k_region_layout<<<grid_for((long long)kLists * (W + 1), 256, g->num_sms), 256, 0, s>>>(W, cnt, g->region);
         std::vector<int> h(kLists * (size_t)(W + 1));
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess)
