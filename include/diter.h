@@ -186,6 +186,28 @@ di_status di_query(di_graph *g, const int32_t *seeds, const double *w, int32_t n
                    double *H_out, di_stats *st);
 
 /*
+ * Up to 64 personalized queries solved together (Section 2.1: V is the
+ * personalization vector; each query has its own V_q).  Their fluids share one
+ * interleaved FP32 row per node (64 lanes, 256 bytes), so each read of a node's
+ * out-links serves every query; histories are FP64.  A sweep selects node i when
+ * some query that has not stopped has F_q[i] > T_q (T_q = 0.5 R_q/n), moves the
+ * whole row into H and pushes it along the out-links.  Each query stops when its
+ * own |F_q|_1/(1-d) <= tol, confirmed in FP64.
+ *   k         1 <= k <= 64 queries
+ *   seed_ptr  host or device int32[k+1]: query q's seeds are seeds[seed_ptr[q] ..
+ *             seed_ptr[q+1]), at least one each (duplicates add their weights)
+ *   seeds     host or device int32[seed_ptr[k]], ids in [0, n)
+ *   w         host or device double[seed_ptr[k]] >= 0 (NULL: uniform over each
+ *             query's seeds); each query's weights need a positive sum
+ *   H_out     host or device double[k][n]: query q's H at H_out[q*n .. q*n+n)
+ *   st_q      host di_stats[k] (may be NULL): per-query bound and convergence
+ *   st_all    host di_stats (may be NULL): sweeps, pushed out-links (each serves
+ *             all k queries), device seconds
+ */
+di_status di_query_batch(di_graph *g, int32_t k, const int32_t *seed_ptr, const int32_t *seeds, const double *w,
+                         double tol, double *H_out, di_stats *st_q, di_stats *st_all);
+
+/*
  * Power iteration on the uncompleted P (MAT-ITER, Section 4): X_0 = 0,
  * X_{k+1} = dPX_k + (1-d)V, computed by a pull over in-links; stops when
  * |X_{k+1} - X_k|_1 * d/(1-d) < tol (the paper's rule).  FP64.

@@ -22,7 +22,7 @@ from ._lib import (DI_EINVAL, DI_ENOTCONVERGED, DI_FP32_MIXED, DI_FP64, DI_OK, D
                    di_solve_opts, di_stats, di_sweep_record, ptr)
 
 __all__ = ["DiGraph", "DiError", "DI_FP64", "DI_FP32_MIXED", "DI_OK", "DI_EINVAL", "DI_ENOTCONVERGED",
-           "di_graph_create", "di_free", "di_solve", "di_solve_ex", "di_query", "di_power", "di_power_ex", "di_graph_export",
+           "di_graph_create", "di_free", "di_solve", "di_solve_ex", "di_query", "di_query_batch", "di_power", "di_power_ex", "di_graph_export",
            "di_get_trace", "di_get_state", "di_get_profile", "di_power_noalloc", "di_version", "load"]
 
 
@@ -74,6 +74,26 @@ def di_query(handle, seeds, w, tol, H_out, prec=DI_FP64):
     check(load().di_query(handle, ptr(seeds), ptr(w), int(len(seeds)), float(tol), int(prec), ptr(H_out),
                           ctypes.byref(st)))
     return st.as_dict()
+
+
+def di_query_batch(handle, seed_lists, tol, H_out, weights=None):
+    """Up to 64 personalized queries at once; seed_lists is a list of seed-id arrays.
+
+    Returns (per-query stats list, batch stats).  H_out is double[k][n] (host or device).
+    """
+    k = len(seed_lists)
+    seed_ptr = np.zeros(k + 1, np.int32)
+    seed_ptr[1:] = np.cumsum([len(s) for s in seed_lists])
+    seeds = np.ascontiguousarray(np.concatenate([np.asarray(s, np.int32) for s in seed_lists] or
+                                                [np.zeros(1, np.int32)]), dtype=np.int32)
+    w = None
+    if weights is not None:
+        w = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float64) for x in weights]), dtype=np.float64)
+    st_q = (di_stats * max(k, 1))()
+    st_all = di_stats()
+    check(load().di_query_batch(handle, k, ptr(seed_ptr), ptr(seeds), ptr(w), float(tol), ptr(H_out), st_q,
+                                ctypes.byref(st_all)))
+    return [st_q[i].as_dict() for i in range(k)], st_all.as_dict()
 
 
 def di_power(handle, tol, X_out, max_iter=0, allow_unconverged=False):
@@ -174,6 +194,12 @@ class DiGraph:
         ww = np.ascontiguousarray(w, dtype=np.float64) if isinstance(w, (list, np.ndarray)) else w
         st = di_query(self.handle, s, ww, tol, H, prec)
         return H, st
+
+    def query_batch(self, seed_lists, tol, H_out=None, weights=None):
+        """Personalized queries solved together; returns (H [k, n], per-query stats, batch stats)."""
+        H = H_out if H_out is not None else np.empty((len(seed_lists), self.n), dtype=np.float64)
+        st_q, st_all = di_query_batch(self.handle, seed_lists, tol, H, weights)
+        return H, st_q, st_all
 
     def power(self, tol, X_out=None, max_iter=0, allow_unconverged=False, profile=0):
         X = X_out if X_out is not None else np.empty(self.n, dtype=np.float64)

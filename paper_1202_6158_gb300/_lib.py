@@ -76,6 +76,7 @@ def load(path: str = LIB_PATH):
         "di_solve_ex": ([vp, ctypes.POINTER(di_solve_opts), vp, ctypes.POINTER(di_stats)], ctypes.c_int),
         "di_query": ([vp, vp, vp, i32, f64, ctypes.c_int, vp, ctypes.POINTER(di_stats)], ctypes.c_int),
         "di_power": ([vp, f64, i32, vp, ctypes.POINTER(di_stats)], ctypes.c_int),
+        "di_query_batch": ([vp, i32, vp, vp, vp, f64, vp, vp, ctypes.POINTER(di_stats)], ctypes.c_int),
         "di_power_ex": ([vp, f64, i32, i32, vp, ctypes.POINTER(di_stats), ctypes.POINTER(f64), ctypes.POINTER(f64)],
                         ctypes.c_int),
         "di_get_trace": ([vp, vp, i32, ctypes.POINTER(i32)], ctypes.c_int),

@@ -48,12 +48,13 @@ static di_status copy_in(void *dst, const void *src, size_t bytes, cudaStream_t 
 static void free_graph(di_graph *g) {
     if (!g) return;
     if (g->stream || g->cap) cudaStreamSynchronize(g->stream);
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 4; ++k) {
         if (g->exec[k]) cudaGraphExecDestroy(g->exec[k]);
         if (g->graph[k]) cudaGraphDestroy(g->graph[k]);
     }
     void *bufs[] = {g->row_ptr, g->col_idx, g->in_ptr, g->in_src, g->bin_of, g->in_bin_of, g->pull_ids, g->V,
                     g->inv_deg, g->inv_deg32, g->hot_ids, g->perm, g->new_of, g->rec64, g->rec32,
+                    g->Fb, g->Hb, g->selb_rows, g->selb_node, g->bq, g->bctl,
                     g->long_prefix, g->region, g->fcount, g->pre, g->ticket, g->sel, g->cls, g->F64, g->F32, g->H, g->part, g->st,
                     g->trace, g->X, g->Z[0], g->Z[1], g->Ylong, g->ppart, g->pst};
     for (void *b : bufs)
@@ -61,6 +62,8 @@ static void free_graph(di_graph *g) {
     cudaStreamSynchronize(g->stream);
     if (g->h_st) cudaFreeHost(g->h_st);
     if (g->h_pst) cudaFreeHost(g->h_pst);
+    if (g->h_bq) cudaFreeHost(g->h_bq);
+    if (g->h_bctl) cudaFreeHost(g->h_bctl);
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
     for (int k = 0; k < 4; ++k)
@@ -283,6 +286,44 @@ di_status di_query(di_graph *g, const int32_t *seeds, const double *w, int32_t n
     cudaFreeAsync(dseeds, s);
     if (dw) cudaFreeAsync(dw, s);
     return r;
+}
+
+di_status di_query_batch(di_graph *g, int32_t k, const int32_t *seed_ptr, const int32_t *seeds, const double *w,
+                         double tol, double *H_out, di_stats *st_q, di_stats *st_all) {
+    g_last_error.clear();
+    if (check_graph(g) != DI_OK) return DI_EINVAL;
+    if (k < 1 || k > kLanes) return set_error(DI_EINVAL, "a batch holds 1 to 64 queries");
+    if (!seed_ptr || !seeds) return set_error(DI_EINVAL, "seed_ptr and seeds are required");
+    if (!(tol > 0.0) || !std::isfinite(tol)) return set_error(DI_EINVAL, "tol must be finite and > 0");
+    cudaStream_t s = g->stream;
+    std::vector<int32_t> hp((size_t)k + 1);
+    DI_CUDA(cudaMemcpyAsync(hp.data(), seed_ptr, sizeof(int32_t) * (k + 1),
+                            is_device_ptr(seed_ptr) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
+    DI_CUDA(cudaStreamSynchronize(s));
+    if (hp[0] != 0) return set_error(DI_EINVAL, "seed_ptr[0] must be 0");
+    for (int q = 0; q < k; ++q)
+        if (hp[q + 1] <= hp[q]) return set_error(DI_EINVAL, "every query needs at least one seed");
+    const int total = hp[k];
+    std::vector<int32_t> hs((size_t)total);
+    std::vector<double> hw(w ? (size_t)total : 0);
+    DI_CUDA(cudaMemcpyAsync(hs.data(), seeds, sizeof(int32_t) * total,
+                            is_device_ptr(seeds) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
+    if (w)
+        DI_CUDA(cudaMemcpyAsync(hw.data(), w, sizeof(double) * total,
+                                is_device_ptr(w) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
+    DI_CUDA(cudaStreamSynchronize(s));
+    for (int q = 0; q < k; ++q) {
+        double sum = 0.0;
+        for (int t = hp[q]; t < hp[q + 1]; ++t) {
+            if (hs[t] < 0 || hs[t] >= g->n) return set_error(DI_EINVAL, "seed id outside [0, n)");
+            const double wt = w ? hw[t] : 1.0;
+            if (!std::isfinite(wt) || wt < 0.0) return set_error(DI_EINVAL, "seed weights must be finite and >= 0");
+            sum += wt;
+        }
+        if (!(sum > 0.0)) return set_error(DI_EINVAL, "each query's seed weights need a positive sum");
+    }
+    return run_query_batch(g, k, hp.data(), hs.data(), w ? hw.data() : nullptr, tol, 0.5, 1000000, H_out,
+                           is_device_ptr(H_out), st_q, st_all);
 }
 
 di_status di_power(di_graph *g, double tol, int32_t max_iter, double *X_out, di_stats *st) {

@@ -1,0 +1,560 @@
+// batch.cu -- up to 64 personalized queries diffused together.
+//
+// Each query q has its own personalization vector V_q (its seed distribution;
+// Section 2.1: V is the personalization vector), its own fluid F_q, history H_q
+// and residual R_q.  The fluids are interleaved: row i of Fb holds F_q[i] for the
+// 64 lanes q (256 bytes, FP32), so one read of node i's out-links serves every
+// query.  One sweep:
+//
+//   k_bscan    streams Fb (a half-warp per node row, one float4 of 4 queries per
+//              lane).  Node i is selected when F_q[i] > T_q for some query q that
+//              has not converged; its whole row is then exchanged -- every lane's
+//              fluid moves -- which is a diffusion of node i for every query (any
+//              choice of nodes is a valid sequence, Section 2.2).  The selected
+//              (i, row) pairs go to the class lists of the single-query path,
+//              through the same per-warp offsets; per-query |F|_1 and removed
+//              mass are summed per lane and added to per-query accumulators.
+//   k_bpush    adds the row to H_i (FP64) and, unless i is dangling, adds
+//              row * d/outdeg(i) to the row of every child with one
+//              red.global.add.v4.f32 per lane (256 bytes per out-link); the
+//              hottest targets' rows are summed in shared memory first.
+//   k_bfinalize  one thread per query: R_q = |F_q|_1 - removed_q, T_q = beta R_q/n,
+//              a query stops when R_q <= tol (1-d); the while-loop ends when all
+//              have stopped.
+//
+// Then |F_q|_1 is recomputed in FP64 per query to confirm each stop, as for a
+// single solve.  The loop is one CUDA graph (while-conditional node).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace diter {
+namespace {
+
+__device__ __forceinline__ void red_add_v4(float *p, float4 v) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w));
+}
+
+__global__ void k_binit(long long rows, int n, float *__restrict__ Fb, double *__restrict__ Hb) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < rows * kLanes;
+         t += (long long)gridDim.x * blockDim.x) {
+        Fb[t] = 0.f;
+        if (t < (long long)n * kLanes) Hb[t] = 0.0;
+    }
+}
+
+// F_q = (1-d) w_s / sum(w) on the seeds of query q
+__global__ void k_bseeds(int nitems, const int *__restrict__ q_of, const int *__restrict__ seeds,
+                         const double *__restrict__ val, const int *__restrict__ new_of, float *__restrict__ Fb) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nitems; t += gridDim.x * blockDim.x)
+        atomicAdd(&Fb[(long long)new_of[seeds[t]] * kLanes + q_of[t]], (float)val[t]);
+}
+
+__global__ void k_bctl_init(int k, BatchQ *__restrict__ bq, BatchCtl *__restrict__ ctl, double tol, double omd,
+                            double beta, int n, int max_sweeps) {
+    const int q = threadIdx.x;
+    if (q < kLanes) {
+        BatchQ b;
+        b.R = omd;
+        b.tolR = tol * omd;
+        b.l1_acc = 0.0;
+        b.rem_acc = 0.0;
+        b.l1_exact = 0.0;
+        b.active = q < k ? 1 : 0;
+        b.done = q < k ? (omd <= b.tolR ? 1 : 0) : 1;
+        b.T = b.done ? INFINITY : beta * omd / (double)n;
+        b.selected = 0;
+        bq[q] = b;
+    }
+    if (q == 0) {
+        ctl->sweeps = 0;
+        ctl->max_sweeps = max_sweeps;
+        ctl->edges = 0;
+        ctl->srcs = 0;
+        ctl->beta = beta;
+        ctl->body_runs = 0;
+        int all = 1;
+        for (int i = 0; i < k; ++i) all &= (omd <= tol * omd) ? 1 : 0;
+        ctl->all_done = all;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_bscan(int wchunk, float *__restrict__ Fb,
+                                                        const unsigned char *__restrict__ cls,
+                                                        const int *__restrict__ region, int W,
+                                                        int *__restrict__ fcount, int *__restrict__ pre,
+                                                        unsigned *__restrict__ ticket, int *__restrict__ sel_node,
+                                                        float *__restrict__ sel_rows, BatchQ *__restrict__ bq,
+                                                        BatchCtl *__restrict__ ctl, double d) {
+    __shared__ double s_l1[kLanes], s_rem[kLanes];
+    __shared__ int s_sel[kLanes];
+    __shared__ unsigned s_ticket;
+    if (ctl->all_done) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, h = lane >> 4, l16 = lane & 15;
+    if (threadIdx.x < kLanes) {
+        s_l1[threadIdx.x] = 0.0;
+        s_rem[threadIdx.x] = 0.0;
+        s_sel[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    float T4[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) T4[k] = (float)bq[4 * l16 + k].T;  // +inf for queries that stopped
+    const float omd = (float)(1.0 - d);
+    const int g = blockIdx.x * kWarps + w;
+    const long long wbeg = (long long)g * wchunk;
+    int run[kLists], start[kLists];
+#pragma unroll
+    for (int L = 0; L < kLists; ++L) start[L] = run[L] = region[L * (W + 1) + g];
+    float l1[4] = {0.f, 0.f, 0.f, 0.f}, rem[4] = {0.f, 0.f, 0.f, 0.f};
+    int sel4[4] = {0, 0, 0, 0};
+    int nsel = 0;
+    const int nsteps = wchunk / 2;
+    float4 cur = *reinterpret_cast<const float4 *>(Fb + (wbeg + h) * kLanes + 4 * l16);
+    int ccur = cls[wbeg + h];
+    for (int s = 0; s < nsteps; ++s) {
+        const long long node = wbeg + 2LL * s + h;
+        float4 nxt = make_float4(0.f, 0.f, 0.f, 0.f);
+        int cnxt = 0;
+        if (s + 1 < nsteps) {
+            nxt = *reinterpret_cast<const float4 *>(Fb + (node + 2) * kLanes + 4 * l16);
+            cnxt = cls[node + 2];
+        }
+        const float v[4] = {cur.x, cur.y, cur.z, cur.w};
+        bool above = false;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            l1[k] += v[k];
+            const bool a = v[k] > T4[k];
+            above |= a;
+            sel4[k] += a ? 1 : 0;
+        }
+        const unsigned bal = __ballot_sync(kFull, above);
+        const bool act = h == 0 ? (bal & 0xffffu) != 0 : (bal >> 16) != 0;
+        const int a0 = (bal & 0xffffu) != 0, a1 = (bal >> 16) != 0;
+        const int c0 = __shfl_sync(kFull, ccur, 0), c1 = __shfl_sync(kFull, ccur, 16);
+        if (act) {
+            const float f = ccur == 0 ? 1.f : omd;  // a dangling node's fluid leaves entirely (Section 3.3)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) rem[k] += f * v[k];
+            const int L = ccur;
+            const int base = L == 0 ? run[0] : (L == 1 ? run[1] : (L == 2 ? run[2] : run[3]));
+            const int pos = base + ((h == 1 && a0 && c0 == L) ? 1 : 0);
+            *reinterpret_cast<float4 *>(sel_rows + (long long)pos * kLanes + 4 * l16) = cur;
+            if (l16 == 0) {
+                sel_node[pos] = (int)node;
+                nsel += 1;
+            }
+            *reinterpret_cast<float4 *>(Fb + node * kLanes + 4 * l16) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int L = 0; L < kLists; ++L) run[L] += (a0 && c0 == L) + (a1 && c1 == L);
+        cur = nxt;
+        ccur = cnxt;
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int L = 0; L < kLists; ++L) fcount[L * W + g] = run[L] - start[L];
+    }
+    // per-query sums: the two half-warps, then the CTA, then one atomic per query
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        l1[k] += __shfl_xor_sync(kFull, l1[k], 16);
+        rem[k] += __shfl_xor_sync(kFull, rem[k], 16);
+        sel4[k] += __shfl_xor_sync(kFull, sel4[k], 16);
+    }
+    if (h == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            atomicAdd(&s_l1[4 * l16 + k], (double)l1[k]);
+            atomicAdd(&s_rem[4 * l16 + k], (double)rem[k]);
+            atomicAdd(&s_sel[4 * l16 + k], sel4[k]);
+        }
+    }
+    __syncthreads();
+    if (l16 == 0 && nsel) atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->srcs), (unsigned long long)nsel);
+    if (threadIdx.x < kLanes && bq[threadIdx.x].active) {
+        atomicAdd(&bq[threadIdx.x].l1_acc, s_l1[threadIdx.x]);
+        atomicAdd(&bq[threadIdx.x].rem_acc, s_rem[threadIdx.x]);
+        if (s_sel[threadIdx.x]) atomicAdd(&bq[threadIdx.x].selected, s_sel[threadIdx.x]);
+    }
+    // the last CTA turns the per-warp counts into prefix sums for the push
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1u);
+    __syncthreads();
+    if (s_ticket == gridDim.x - 1) {
+        __threadfence();
+        prefix_counts(fcount, W, pre);
+        if (threadIdx.x == 0) *ticket = 0u;
+    }
+}
+
+// one out-link j of a selected node: this lane's 4 queries of row j += wv
+__device__ __forceinline__ void bpush_edge(float *__restrict__ Fb, float *hot, int n_hot, int j, int l16, float4 wv) {
+    if (j < n_hot) {
+        float *hp = hot + j * kLanes + 4 * l16;
+        atomicAdd(hp, wv.x);
+        atomicAdd(hp + 1, wv.y);
+        atomicAdd(hp + 2, wv.z);
+        atomicAdd(hp + 3, wv.w);
+    } else {
+        red_add_v4(Fb + (long long)j * kLanes + 4 * l16, wv);
+    }
+}
+
+// one selected node's row: H += row; then row * d/outdeg to every child (16 lanes x float4)
+__device__ __forceinline__ void bpush_node(int node, const float4 row, int l16, int cls_node,
+                                           const RowRec<float> *__restrict__ rec, const int *__restrict__ col_idx,
+                                           float *__restrict__ Fb, double *__restrict__ Hb, float *hot, int n_hot,
+                                           int e_beg, int e_step, bool do_h, long long &edges) {
+    if (do_h) {
+        double2 *hp = reinterpret_cast<double2 *>(Hb + (long long)node * kLanes + 4 * l16);
+        double2 a = hp[0], b = hp[1];
+        a.x += row.x;
+        a.y += row.y;
+        b.x += row.z;
+        b.y += row.w;
+        hp[0] = a;
+        hp[1] = b;
+    }
+    if (cls_node == 0) return;
+    const RowRec<float> rr = rec[node];
+    const float4 wv = make_float4(row.x * rr.inv, row.y * rr.inv, row.z * rr.inv, row.w * rr.inv);
+    if (do_h && l16 == 0) edges += rr.deg;
+    int e = e_beg;
+    const int end = rr.deg;
+    for (; e + 3 * e_step < end; e += 4 * e_step) {
+        const int j0 = __ldg(col_idx + rr.beg + e), j1 = __ldg(col_idx + rr.beg + e + e_step);
+        const int j2 = __ldg(col_idx + rr.beg + e + 2 * e_step), j3 = __ldg(col_idx + rr.beg + e + 3 * e_step);
+        bpush_edge(Fb, hot, n_hot, j0, l16, wv);
+        bpush_edge(Fb, hot, n_hot, j1, l16, wv);
+        bpush_edge(Fb, hot, n_hot, j2, l16, wv);
+        bpush_edge(Fb, hot, n_hot, j3, l16, wv);
+    }
+    for (; e < end; e += e_step) bpush_edge(Fb, hot, n_hot, __ldg(col_idx + rr.beg + e), l16, wv);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_bpush(const RowRec<float> *__restrict__ rec,
+                                                        const int *__restrict__ col_idx, float *__restrict__ Fb,
+                                                        double *__restrict__ Hb, const unsigned char *__restrict__ cls,
+                                                        const int *__restrict__ region, const int *__restrict__ pre,
+                                                        int W, const int *__restrict__ sel_node,
+                                                        const float *__restrict__ sel_rows, int n_hot,
+                                                        BatchCtl *__restrict__ ctl) {
+    __shared__ float hot[kBatchHot * kLanes];
+    __shared__ long long s_red[kWarps];
+    __shared__ int s_idx;
+    if (ctl->all_done) return;
+    for (int t = threadIdx.x; t < kBatchHot * kLanes; t += kScanThreads) hot[t] = 0.f;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, h = lane >> 4, l16 = lane & 15;
+    const int hw = threadIdx.x >> 4;                        // half-warp in the CTA (0..15)
+    const int nhw = gridDim.x * (kScanThreads / 16), ghw = blockIdx.x * (kScanThreads / 16) + hw;
+    (void)w;
+    (void)h;
+    long long edges = 0;
+    // class 3: the whole CTA per node, each half-warp taking every 16th out-link
+    {
+        const int *p3 = pre + 3 * (W + 1);
+        const int tot = __ldg(p3 + W);
+        for (int t = blockIdx.x; t < tot; t += gridDim.x) {
+            if (threadIdx.x == 0) {
+                const int gs = find_sub(p3, W, t);
+                s_idx = region[3 * (W + 1) + gs] + (t - __ldg(p3 + gs));
+            }
+            __syncthreads();
+            const int pos = s_idx;
+            __syncthreads();
+            const int node = sel_node[pos];
+            const float4 row = *reinterpret_cast<const float4 *>(sel_rows + (long long)pos * kLanes + 4 * l16);
+            if (hw == 0) {  // H once
+                double2 *hp = reinterpret_cast<double2 *>(Hb + (long long)node * kLanes + 4 * l16);
+                double2 a = hp[0], b = hp[1];
+                a.x += row.x;
+                a.y += row.y;
+                b.x += row.z;
+                b.y += row.w;
+                hp[0] = a;
+                hp[1] = b;
+                if (l16 == 0) edges += rec[node].deg;
+            }
+            bpush_node(node, row, l16, 3, rec, col_idx, Fb, Hb, hot, n_hot, hw, kScanThreads / 16, false, edges);
+        }
+    }
+    // classes 0, 1, 2: a half-warp per node, contiguous ranges per half-warp
+    for (int L = 0; L < 3; ++L) {
+        const int *pl = pre + L * (W + 1);
+        const int tot = __ldg(pl + W);
+        const int per = (tot + nhw - 1) / nhw;
+        const int t_beg = min(tot, ghw * per), t_end = min(tot, t_beg + per);
+        if (t_beg >= t_end) continue;
+        int gl = find_sub(pl, W, t_beg);
+        for (int t = t_beg; t < t_end; ++t) {
+            while (__ldg(pl + gl + 1) <= t) ++gl;
+            const int pos = region[L * (W + 1) + gl] + (t - __ldg(pl + gl));
+            const int node = sel_node[pos];
+            const float4 row = *reinterpret_cast<const float4 *>(sel_rows + (long long)pos * kLanes + 4 * l16);
+            bpush_node(node, row, l16, L, rec, col_idx, Fb, Hb, hot, n_hot, 0, 1, true, edges);
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_hot * kLanes; t += kScanThreads) {
+        const float v = hot[t];
+        if (v != 0.f) atomicAdd(Fb + t, v);
+    }
+    const long long be = block_sum(edges, s_red);
+    if (threadIdx.x == 0 && be) atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->edges),
+                                          (unsigned long long)be);
+}
+
+__global__ void k_bfinalize(int n, BatchQ *__restrict__ bq, BatchCtl *__restrict__ ctl,
+                            cudaGraphConditionalHandle handle, int in_graph) {
+    __shared__ int s_open;
+    if (ctl->all_done) {
+        if (threadIdx.x == 0) {
+            ctl->body_runs += 1;
+            if (in_graph) cudaGraphSetConditional(handle, 0);
+        }
+        return;
+    }
+    if (threadIdx.x == 0) s_open = 0;
+    __syncthreads();
+    const int q = threadIdx.x;
+    if (q < kLanes) {
+        BatchQ b = bq[q];
+        if (b.active) {
+            const double R = b.l1_acc - b.rem_acc;  // |F_q|_1 after the sweep
+            const double Rprev = b.R;
+            b.R = R > 0.0 ? R : 0.0;
+            b.l1_acc = 0.0;
+            b.rem_acc = 0.0;
+            if (!b.done) {
+                if (b.R <= b.tolR) {
+                    b.done = 1;
+                    b.T = INFINITY;
+                } else {
+                    // T_q = beta R_q / n; halved when the query selected no node this sweep
+                    b.T = (b.selected == 0 || !(b.R < Rprev)) ? 0.5 * b.T : ctl->beta * b.R / (double)n;
+                    atomicAdd(&s_open, 1);
+                }
+            }
+            b.selected = 0;
+            bq[q] = b;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctl->body_runs += 1;
+        ctl->sweeps += 1;
+        if (s_open == 0 || ctl->sweeps >= ctl->max_sweeps) {
+            ctl->all_done = s_open == 0 ? 1 : 2;
+            if (in_graph) cudaGraphSetConditional(handle, 0);
+        }
+    }
+}
+
+// exact per-query |F_q|_1 in FP64 (a lane per query column, rows strided over the grid)
+__global__ void k_bl1_exact(long long rows, const float *__restrict__ Fb, BatchQ *__restrict__ bq) {
+    const int q = threadIdx.x & (kLanes - 1);
+    const int rstep = (gridDim.x * blockDim.x) / kLanes;
+    double a = 0.0;
+    for (long long r = (long long)(blockIdx.x * blockDim.x + threadIdx.x) / kLanes; r < rows; r += rstep)
+        a += fabs((double)Fb[r * kLanes + q]);
+    atomicAdd(&bq[q].l1_exact, a);
+}
+
+__global__ void k_bzero_exact(BatchQ *__restrict__ bq) {
+    if (threadIdx.x < kLanes) bq[threadIdx.x].l1_exact = 0.0;
+}
+
+// a stop the exact norm does not confirm re-opens that query
+__global__ void k_bconfirm(int n, BatchQ *__restrict__ bq, BatchCtl *__restrict__ ctl) {
+    __shared__ int s_open;
+    if (threadIdx.x == 0) s_open = 0;
+    __syncthreads();
+    const int q = threadIdx.x;
+    if (q < kLanes && bq[q].active && bq[q].done && !(bq[q].l1_exact <= bq[q].tolR)) {
+        bq[q].done = 0;
+        bq[q].R = bq[q].l1_exact;
+        bq[q].T = ctl->beta * bq[q].l1_exact / (double)n;
+        atomicAdd(&s_open, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_open && ctl->all_done == 1) ctl->all_done = 0;
+}
+
+// out[q][i] = Hb[new_of[i]][q] for the first k queries, back in the caller's numbering
+__global__ void k_bgather(int n, int k, const int *__restrict__ new_of, const double *__restrict__ Hb,
+                          double *__restrict__ out) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < (long long)n * kLanes;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / kLanes), q = (int)(t % kLanes);
+        if (q < k) out[(long long)q * n + i] = Hb[(long long)new_of[i] * kLanes + q];
+    }
+}
+
+di_status build_batch_graph(di_graph *g) {
+    cudaGraph_t graph = nullptr;
+    DI_CUDA(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle handle;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(e, "cudaGraphConditionalHandleCreate"); }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(e, "cudaGraphAddNode(conditional)"); }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(g->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(e, "cudaStreamBeginCaptureToGraph"); }
+    const int nhot = std::min(g->n_hot, kBatchHot);
+    k_bscan<<<g->G, kScanThreads, 0, g->cap>>>(g->chunk / kWarps, g->Fb, g->cls, g->region, g->W, g->fcount, g->pre,
+                                               g->ticket, g->selb_node, g->selb_rows, g->bq, g->bctl, g->d);
+    k_bpush<<<g->G, kScanThreads, 0, g->cap>>>(g->rec32, g->col_idx, g->Fb, g->Hb, g->cls, g->region, g->pre, g->W,
+                                               g->selb_node, g->selb_rows, nhot, g->bctl);
+    k_bfinalize<<<1, kLanes, 0, g->cap>>>(g->n, g->bq, g->bctl, handle, 1);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(g->cap, &captured);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(e, "cudaStreamEndCapture"); }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(e, "cudaGraphInstantiate(batch)"); }
+    g->graph[3] = graph;
+    g->exec[3] = exec;
+    return DI_OK;
+}
+
+di_status batch_alloc(di_graph *g) {
+    if (g->Fb) return DI_OK;
+    cudaStream_t s = g->stream;
+    const long long rows = (long long)g->G * g->chunk;
+    DI_CUDA(cudaMallocAsync(&g->Fb, sizeof(float) * kLanes * (size_t)rows, s));
+    DI_CUDA(cudaMallocAsync(&g->Hb, sizeof(double) * kLanes * (size_t)g->n, s));
+    DI_CUDA(cudaMallocAsync(&g->selb_rows, sizeof(float) * kLanes * (size_t)g->n, s));
+    DI_CUDA(cudaMallocAsync(&g->selb_node, sizeof(int) * (size_t)g->n, s));
+    DI_CUDA(cudaMallocAsync(&g->bq, sizeof(BatchQ) * kLanes, s));
+    DI_CUDA(cudaMallocAsync(&g->bctl, sizeof(BatchCtl), s));
+    DI_CUDA(cudaMallocHost(&g->h_bq, sizeof(BatchQ) * kLanes));
+    DI_CUDA(cudaMallocHost(&g->h_bctl, sizeof(BatchCtl)));
+    return DI_OK;
+}
+
+}  // namespace
+
+di_status run_query_batch(di_graph *g, int k, const int *seed_ptr, const int *seeds, const double *w, double tol,
+                          double beta, int max_sweeps, double *H_out, bool out_dev, di_stats *st_q, di_stats *st_all) {
+    cudaStream_t s = g->stream;
+    di_status r = batch_alloc(g);
+    if (r != DI_OK) return r;
+    if (!g->exec[3]) {
+        r = build_batch_graph(g);
+        if (r != DI_OK) return r;
+    }
+    const int n = g->n;
+    const double omd = 1.0 - g->d;
+    const long long rows = (long long)g->G * g->chunk;
+    // seed items (query, seed, (1-d) w / sum w) prepared on the host
+    const int nitems = seed_ptr[k];
+    std::vector<int> q_of(nitems);
+    std::vector<double> val(nitems);
+    for (int q = 0; q < k; ++q) {
+        double sum = 0.0;
+        for (int t = seed_ptr[q]; t < seed_ptr[q + 1]; ++t) sum += w ? w[t] : 1.0;
+        for (int t = seed_ptr[q]; t < seed_ptr[q + 1]; ++t) {
+            q_of[t] = q;
+            val[t] = omd * (w ? w[t] : 1.0) / sum;
+        }
+    }
+    int *d_q = nullptr, *d_seeds = nullptr;
+    double *d_val = nullptr;
+    DI_CUDA(cudaMallocAsync(&d_q, sizeof(int) * nitems, s));
+    DI_CUDA(cudaMallocAsync(&d_seeds, sizeof(int) * nitems, s));
+    DI_CUDA(cudaMallocAsync(&d_val, sizeof(double) * nitems, s));
+    DI_CUDA(cudaMemcpyAsync(d_q, q_of.data(), sizeof(int) * nitems, cudaMemcpyHostToDevice, s));
+    DI_CUDA(cudaMemcpyAsync(d_seeds, seeds, sizeof(int) * nitems, cudaMemcpyHostToDevice, s));
+    DI_CUDA(cudaMemcpyAsync(d_val, val.data(), sizeof(double) * nitems, cudaMemcpyHostToDevice, s));
+    DI_CUDA(cudaEventRecord(g->ev0, s));
+    const int grid = (int)std::max(1LL, std::min((rows * kLanes + 255) / 256, (long long)g->num_sms * 8));
+    k_binit<<<grid, 256, 0, s>>>(rows, n, g->Fb, g->Hb);
+    k_bseeds<<<std::max(1, std::min(1024, (nitems + 255) / 256)), 256, 0, s>>>(nitems, d_q, d_seeds, d_val, g->new_of,
+                                                                           g->Fb);
+    k_bctl_init<<<1, kLanes, 0, s>>>(k, g->bq, g->bctl, tol, omd, beta, n, max_sweeps);
+    DI_CUDA(cudaGetLastError());
+    int attempts = 0;
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        ++attempts;
+        DI_CUDA(cudaGraphLaunch(g->exec[3], s));
+        k_bzero_exact<<<1, kLanes, 0, s>>>(g->bq);
+        k_bl1_exact<<<grid, 256, 0, s>>>(rows, g->Fb, g->bq);
+        k_bconfirm<<<1, kLanes, 0, s>>>(n, g->bq, g->bctl);
+        DI_CUDA(cudaGetLastError());
+        DI_CUDA(cudaMemcpyAsync(g->h_bctl, g->bctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
+        DI_CUDA(cudaStreamSynchronize(s));
+        if (g->h_bctl->all_done != 0) break;
+    }
+    DI_CUDA(cudaEventRecord(g->ev1, s));
+    if (H_out) {
+        double *dst = H_out, *tmp = nullptr;
+        if (!out_dev) {
+            DI_CUDA(cudaMallocAsync(&tmp, sizeof(double) * (size_t)n * k, s));
+            dst = tmp;
+        }
+        k_bgather<<<grid, 256, 0, s>>>(n, k, g->new_of, g->Hb, dst);
+        DI_CUDA(cudaGetLastError());
+        if (tmp) {
+            DI_CUDA(cudaMemcpyAsync(H_out, tmp, sizeof(double) * (size_t)n * k, cudaMemcpyDeviceToHost, s));
+            cudaFreeAsync(tmp, s);
+        }
+    }
+    DI_CUDA(cudaMemcpyAsync(g->h_bq, g->bq, sizeof(BatchQ) * kLanes, cudaMemcpyDeviceToHost, s));
+    DI_CUDA(cudaStreamSynchronize(s));
+    cudaFreeAsync(d_q, s);
+    cudaFreeAsync(d_seeds, s);
+    cudaFreeAsync(d_val, s);
+    float ms = 0.f;
+    DI_CUDA(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+    const BatchCtl &c = *g->h_bctl;
+    bool all_conv = true;
+    for (int q = 0; q < k; ++q) {
+        const BatchQ &b = g->h_bq[q];
+        const bool conv = b.done && b.l1_exact <= b.tolR;
+        all_conv &= conv;
+        if (st_q) {
+            st_q[q].bound = b.l1_exact / omd;
+            st_q[q].l1_F = b.l1_exact;
+            st_q[q].R = b.R;
+            st_q[q].edges_pushed = c.edges;
+            st_q[q].sources_pushed = c.srcs;
+            st_q[q].sweeps = c.sweeps;
+            st_q[q].converged = conv ? 1 : 0;
+            st_q[q].seconds = ms * 1e-3;
+            st_q[q].kernel_launches = 0;
+        }
+    }
+    if (st_all) {
+        double worst = 0.0;
+        for (int q = 0; q < k; ++q) worst = std::max(worst, g->h_bq[q].l1_exact / omd);
+        st_all->bound = worst;
+        st_all->l1_F = worst * omd;
+        st_all->R = 0.0;
+        st_all->edges_pushed = c.edges;
+        st_all->sources_pushed = c.srcs;
+        st_all->sweeps = c.sweeps;
+        st_all->converged = all_conv ? 1 : 0;
+        st_all->seconds = ms * 1e-3;
+        st_all->kernel_launches = 3 + 3LL * c.body_runs + 3LL * attempts;
+    }
+    if (c.all_done == 2 || !all_conv) return set_error(DI_ENOTCONVERGED, "a batched query stopped at a limit");
+    return DI_OK;
+}
+
+}  // namespace diter

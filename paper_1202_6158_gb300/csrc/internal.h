@@ -93,6 +93,33 @@ struct SolveState {
     int pad[2];
 };
 
+// batched personalized queries: up to kLanes queries interleaved in one fluid row
+constexpr int kLanes = 64;              // queries per batch (the width of a fluid row)
+constexpr int kBatchHot = 32;           // hot targets whose rows the batched push sums in shared memory
+
+struct BatchQ {            // per query
+    double R;              // residual after the last sweep
+    double T;              // threshold of the next sweep (+inf once the query has stopped)
+    double tolR;           // stop when R <= tolR
+    double l1_acc;         // |F_q|_1 summed by the current sweep's scan
+    double rem_acc;        // mass removed by the current sweep
+    double l1_exact;       // FP64 |F_q|_1 of the confirmation
+    int active;            // a query occupies this lane
+    int done;              // stopped
+    int selected;          // lanes of this query above its threshold in the current sweep
+    int pad;
+};
+
+struct BatchCtl {
+    long long edges;       // out-links pushed (each serves all lanes)
+    long long srcs;        // selected nodes
+    double beta;
+    int sweeps;
+    int max_sweeps;
+    int all_done;          // 1 every query stopped, 2 a limit hit
+    int body_runs;
+};
+
 struct PowerState {
     double delta;          // |X_k - X_{k-1}|_1 of the last product
     double tol;            // stop when delta * d/(1-d) < tol
@@ -169,9 +196,17 @@ struct di_graph {
     int pull_blocks[3] = {0, 0, 0};
     double pprof_ms[2] = {0.0, 0.0};   // profiled power iteration: pull, finalize
 
-    // captured solve loops: [0] FP64 sweeps, [1] FP32-mixed sweeps, [2] power iteration
-    cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
-    cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
+    // batched queries (allocated at the first batch)
+    float *Fb = nullptr;               // [rows][kLanes] interleaved fluid, FP32
+    double *Hb = nullptr;              // [n][kLanes] histories, FP64
+    float *selb_rows = nullptr;        // [n][kLanes] rows of the selected nodes of a sweep
+    int *selb_node = nullptr;          // [n]
+    diter::BatchQ *bq = nullptr, *h_bq = nullptr;
+    diter::BatchCtl *bctl = nullptr, *h_bctl = nullptr;
+
+    // captured solve loops: [0] FP64 sweeps, [1] FP32-mixed sweeps, [2] power iteration, [3] batch
+    cudaGraph_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaGraphExec_t exec[4] = {nullptr, nullptr, nullptr, nullptr};
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     diter::SolveState *h_st = nullptr; // pinned host mirror
@@ -200,6 +235,10 @@ di_status power_alloc(di_graph *g);
 di_status run_power(di_graph *g, double tol, int max_iter, int profile, double *X_out, bool out_on_device,
                     di_stats *st);
 int scan_blocks_per_sm();
+
+// batched queries (batch.cu)
+di_status run_query_batch(di_graph *g, int k, const int *seed_ptr, const int *seeds, const double *w, double tol,
+                          double beta, int max_sweeps, double *H_out, bool out_dev, di_stats *st_q, di_stats *st_all);
 
 // helpers
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }

@@ -37,48 +37,15 @@
 #include <algorithm>
 #include <cmath>
 
+#include "device_common.cuh"
 #include "internal.h"
 
 namespace diter {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-
 template <typename FT> struct Vec;
 template <> struct Vec<double> { using T = double2; static constexpr int N = 2; };
 template <> struct Vec<float> { using T = float4; static constexpr int N = 4; };
-
-// Fire-and-forget reductions into F (performed by the L2 atomic units).  No memory
-// clobber: nothing in a push kernel reads F, so loads may be scheduled freely
-// around these.
-__device__ __forceinline__ void red_add(double *p, double v) {
-    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v));
-}
-__device__ __forceinline__ void red_add(float *p, float v) {
-    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v));
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-    return v;
-}
-
-// deterministic block sum (256 threads): warp trees then a fixed-order tree of 8 warp sums
-template <typename T>
-__device__ T block_sum(T v, T *sh) {
-    v = warp_sum(v);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    T r = T(0);
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += sh[k];
-    }
-    __syncthreads();
-    return r;  // valid in thread 0
-}
 
 // ------------------------------------------------------------------- init
 
@@ -162,33 +129,6 @@ __device__ __forceinline__ long long to_fixed(double x, int S) {
 
 __device__ __forceinline__ long long to_fixed(float x, int S) { return to_fixed((double)x, S); }
 
-// Streaming loads of the scan carry an L2 evict-first policy so that the scan's
-// pass over all of F does not push the push kernel's working set out of L2.  (F is
-// written by the scan itself, so its loads stay on the coherent path; the class
-// bytes are read-only.)
-__device__ __forceinline__ unsigned long long evict_first_policy() {
-    unsigned long long p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ double2 ld_stream(const double2 *a, unsigned long long pol) {
-    double2 v;
-    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
-                 : "=d"(v.x), "=d"(v.y) : "l"(a), "l"(pol));
-    return v;
-}
-__device__ __forceinline__ float4 ld_stream(const float4 *a, unsigned long long pol) {
-    float4 v;
-    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(a), "l"(pol));
-    return v;
-}
-__device__ __forceinline__ unsigned ld_stream(const unsigned *a, unsigned long long pol) {
-    unsigned v;
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
-    return v;
-}
-
 template <typename FT>
 struct ScanOps;
 
@@ -231,55 +171,6 @@ struct ScanOps<float> {
 // step is processed), and appends the selected nodes (id, sent) of each class to
 // that class's list in ascending id order with a warp prefix sum; the lists'
 // per-sub-chunk capacities are fixed at create time, so no atomics are needed.
-// The last scan CTA to finish (a ticket counter, no waiting) turns the per-sub-chunk
-// counts into exclusive prefix sums per list, so the push can spread the selected
-// nodes evenly over all its warps whatever their distribution over the chunks.
-// Each thread sums a contiguous run of sub-chunks for every list, one block scan
-// covers the four lists, then each thread writes its run.
-__device__ void prefix_counts(const int *__restrict__ fcount, int W, int *__restrict__ pre) {
-    constexpr int kCap = 8192;                     // sub-chunks staged per pass (32 KB)
-    __shared__ int s_c[kCap];
-    __shared__ int s_w[kWarps];
-    __shared__ int s_carry;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int L = 0; L < kLists; ++L) {
-        if (threadIdx.x == 0) s_carry = 0;
-        for (int base = 0; base < W; base += kCap) {
-            const int m = min(kCap, W - base);
-            // coalesced loads, all in flight together
-            for (int t = threadIdx.x; t < m; t += kScanThreads) s_c[t] = __ldcg(fcount + L * W + base + t);
-            __syncthreads();
-            const int per = (m + kScanThreads - 1) / kScanThreads;
-            const int g0 = min(m, threadIdx.x * per), g1 = min(m, g0 + per);
-            int a = 0;
-            for (int g = g0; g < g1; ++g) a += s_c[g];
-            int x = a;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(kFull, x, o);
-                if (lane >= o) x += y;
-            }
-            if (lane == 31) s_w[w] = x;
-            __syncthreads();
-            int off = s_carry, tot = 0;
-            for (int k = 0; k < kWarps; ++k) {
-                off += k < w ? s_w[k] : 0;
-                tot += s_w[k];
-            }
-            int run = off + x - a;
-            for (int g = g0; g < g1; ++g) {
-                pre[L * (W + 1) + base + g] = run;
-                run += s_c[g];
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) s_carry += tot;
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) pre[L * (W + 1) + W] = s_carry;
-        __syncthreads();
-    }
-}
-
 template <typename FT>
 __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__restrict__ F,
                                                              const unsigned char *__restrict__ cls,
@@ -448,16 +339,6 @@ __device__ __forceinline__ void push_row_lanes(const int *__restrict__ col_idx, 
     }
     const int t = head + 4 * body + lane;
     if (t < deg) push_one(F, hot, n_hot, __ldg(col_idx + beg + t), w);
-}
-
-// sub-chunk holding item t of a list: the last g with pre[g] <= t
-__device__ __forceinline__ int find_sub(const int *__restrict__ pre, int W, int t) {
-    int lo = 0, hi = W;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(pre + mid) <= t) lo = mid; else hi = mid;
-    }
-    return lo;
 }
 
 // The push.  The selected nodes of each class are numbered 0..total-1 through the
