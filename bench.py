@@ -175,6 +175,40 @@ def cpu_baseline(g, w, max_pushes, cores=1):
             "seconds": dt, "edges": int(r.edges), "sweeps": int(r.sweeps), "converged": bool(r.converged)}
 
 
+def bench_ppr(di, torch, dev, nbatches=3):
+    """Batched personalized queries: R-MAT scale 20 (edge factor 16, a,b,c = .57,.19,.19, duplicates removed),
+    d = 0.85, 64 queries with 1..32 uniform seeds, per-query bound 1e-6; one batch vs 64 single queries."""
+    import graphgen as gg
+    g = gg.rmat_graph(20, 16, seed=1)
+    seeds = gg.seed_sets(g.n, 64, 1, 32, seed=7)
+    G = di.DiGraph(g.n, torch.from_numpy(g.row_ptr).to(dev), torch.from_numpy(g.col_idx).to(dev), 0.85)
+    H = torch.empty((64, g.n), dtype=torch.float64, device=dev)
+    for _ in range(2):
+        G.query_batch(seeds, 1e-6, H_out=H)
+    torch.cuda.synchronize()
+    lat = []
+    for _ in range(nbatches):
+        t0 = time.perf_counter()
+        _, stq, sta = G.query_batch(seeds, 1e-6, H_out=H)
+        torch.cuda.synchronize()
+        lat.append(time.perf_counter() - t0)
+    h1 = torch.empty(g.n, dtype=torch.float64, device=dev)
+    for q in range(2):
+        G.query(seeds[q], 1e-6, H_out=h1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for q in range(64):
+        G.query(seeds[q], 1e-6, H_out=h1)
+    torch.cuda.synchronize()
+    single = time.perf_counter() - t0
+    G.close()
+    med = float(np.median(lat))
+    return {"workload": "R-MAT scale 20 (n=%d, L=%d), 64 queries x 1-32 seeds, d=0.85, per-query bound 1e-6" % (g.n, g.nnz),
+            "batched_queries_per_s": 64 / med, "batch_ms": 1e3 * med, "sweeps": sta["sweeps"],
+            "max_bound": max(s["bound"] for s in stq), "single_fp64_queries_per_s": 64 / single,
+            "speedup": (64 / med) / (64 / single), "lane_dtype": "f32 fluid rows, f64 histories"}
+
+
 def run_reference(args, w):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -210,6 +244,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-pushes", type=int, default=0, help="diffusions in the oracle sample (0: 8N, more than the full solve needs)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ppr", action="store_true", help="skip the batched personalized-query measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warm-up below 3 is not allowed; using 3")
@@ -347,6 +382,10 @@ def main():
         tot_edges, tot_e2e_edges = float(t[0]), float(t[1])
         max_ms, max_e2e = float(tm[0]), float(tm[1])
 
+    ppr = None
+    if rank == 0 and not args.no_ppr:
+        ppr = bench_ppr(di, torch, dev)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cap = args.cpu_pushes if args.cpu_pushes > 0 else 8 * g.n
@@ -375,6 +414,7 @@ def main():
                     "what": "pinned host CSR -> di_graph_create (copy, validation, ingest) -> di_solve to host H -> "
                             "di_free, host wall clock"},
             "cpu_baseline": cpu,
+            "ppr_batch": ppr,
             "clocks": clk,
             "gpu_launches": launches,
             "host": {"nproc": os.cpu_count()},

@@ -48,9 +48,13 @@ static di_status copy_in(void *dst, const void *src, size_t bytes, cudaStream_t 
 static void free_graph(di_graph *g) {
     if (!g) return;
     if (g->stream || g->cap) cudaStreamSynchronize(g->stream);
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 3; ++k) {
         if (g->exec[k]) cudaGraphExecDestroy(g->exec[k]);
         if (g->graph[k]) cudaGraphDestroy(g->graph[k]);
+    }
+    for (int k = 0; k < 4; ++k) {
+        if (g->bexec[k]) cudaGraphExecDestroy(g->bexec[k]);
+        if (g->bgraph[k]) cudaGraphDestroy(g->bgraph[k]);
     }
     void *bufs[] = {g->row_ptr, g->col_idx, g->in_ptr, g->in_src, g->bin_of, g->in_bin_of, g->pull_ids, g->V,
                     g->inv_deg, g->inv_deg32, g->hot_ids, g->perm, g->new_of, g->rec64, g->rec32,

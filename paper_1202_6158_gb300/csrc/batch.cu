@@ -40,19 +40,19 @@ __device__ __forceinline__ void red_add_v4(float *p, float4 v) {
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w));
 }
 
-__global__ void k_binit(long long rows, int n, float *__restrict__ Fb, double *__restrict__ Hb) {
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < rows * kLanes;
+__global__ void k_binit(long long rows, int n, int K, float *__restrict__ Fb, double *__restrict__ Hb) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < rows * K;
          t += (long long)gridDim.x * blockDim.x) {
         Fb[t] = 0.f;
-        if (t < (long long)n * kLanes) Hb[t] = 0.0;
+        if (t < (long long)n * K) Hb[t] = 0.0;
     }
 }
 
 // F_q = (1-d) w_s / sum(w) on the seeds of query q
-__global__ void k_bseeds(int nitems, const int *__restrict__ q_of, const int *__restrict__ seeds,
+__global__ void k_bseeds(int nitems, int K, const int *__restrict__ q_of, const int *__restrict__ seeds,
                          const double *__restrict__ val, const int *__restrict__ new_of, float *__restrict__ Fb) {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nitems; t += gridDim.x * blockDim.x)
-        atomicAdd(&Fb[(long long)new_of[seeds[t]] * kLanes + q_of[t]], (float)val[t]);
+        atomicAdd(&Fb[(long long)new_of[seeds[t]] * K + q_of[t]], (float)val[t]);
 }
 
 __global__ void k_bctl_init(int k, BatchQ *__restrict__ bq, BatchCtl *__restrict__ ctl, double tol, double omd,
@@ -84,6 +84,8 @@ __global__ void k_bctl_init(int k, BatchQ *__restrict__ bq, BatchCtl *__restrict
     }
 }
 
+// LPN lanes per node row (K = 4 LPN queries, a float4 per lane); 32/LPN rows per warp step
+template <int LPN>
 __global__ void __launch_bounds__(kScanThreads) k_bscan(int wchunk, float *__restrict__ Fb,
                                                         const unsigned char *__restrict__ cls,
                                                         const int *__restrict__ region, int W,
@@ -91,12 +93,15 @@ __global__ void __launch_bounds__(kScanThreads) k_bscan(int wchunk, float *__res
                                                         unsigned *__restrict__ ticket, int *__restrict__ sel_node,
                                                         float *__restrict__ sel_rows, BatchQ *__restrict__ bq,
                                                         BatchCtl *__restrict__ ctl, double d) {
-    __shared__ double s_l1[kLanes], s_rem[kLanes];
-    __shared__ int s_sel[kLanes];
+    constexpr int K = 4 * LPN, NPS = 32 / LPN;
+    __shared__ double s_l1[K], s_rem[K];
+    __shared__ int s_sel[K];
     __shared__ unsigned s_ticket;
     if (ctl->all_done) return;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, h = lane >> 4, l16 = lane & 15;
-    if (threadIdx.x < kLanes) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, h = lane / LPN, lq = lane % LPN;
+    const unsigned gmask = ((LPN == 32 ? 0xffffffffu : ((1u << LPN) - 1u))) << (h * LPN);
+    const unsigned lt = (1u << lane) - 1u;
+    if (threadIdx.x < K) {
         s_l1[threadIdx.x] = 0.0;
         s_rem[threadIdx.x] = 0.0;
         s_sel[threadIdx.x] = 0;
@@ -104,7 +109,7 @@ __global__ void __launch_bounds__(kScanThreads) k_bscan(int wchunk, float *__res
     __syncthreads();
     float T4[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) T4[k] = (float)bq[4 * l16 + k].T;  // +inf for queries that stopped
+    for (int k = 0; k < 4; ++k) T4[k] = (float)bq[4 * lq + k].T;  // +inf for queries that stopped
     const float omd = (float)(1.0 - d);
     const int g = blockIdx.x * kWarps + w;
     const long long wbeg = (long long)g * wchunk;
@@ -114,16 +119,16 @@ __global__ void __launch_bounds__(kScanThreads) k_bscan(int wchunk, float *__res
     float l1[4] = {0.f, 0.f, 0.f, 0.f}, rem[4] = {0.f, 0.f, 0.f, 0.f};
     int sel4[4] = {0, 0, 0, 0};
     int nsel = 0;
-    const int nsteps = wchunk / 2;
-    float4 cur = *reinterpret_cast<const float4 *>(Fb + (wbeg + h) * kLanes + 4 * l16);
+    const int nsteps = wchunk / NPS;
+    float4 cur = *reinterpret_cast<const float4 *>(Fb + (wbeg + h) * K + 4 * lq);
     int ccur = cls[wbeg + h];
     for (int s = 0; s < nsteps; ++s) {
-        const long long node = wbeg + 2LL * s + h;
+        const long long node = wbeg + (long long)NPS * s + h;
         float4 nxt = make_float4(0.f, 0.f, 0.f, 0.f);
         int cnxt = 0;
         if (s + 1 < nsteps) {
-            nxt = *reinterpret_cast<const float4 *>(Fb + (node + 2) * kLanes + 4 * l16);
-            cnxt = cls[node + 2];
+            nxt = *reinterpret_cast<const float4 *>(Fb + (node + NPS) * K + 4 * lq);
+            cnxt = cls[node + NPS];
         }
         const float v[4] = {cur.x, cur.y, cur.z, cur.w};
         bool above = false;
@@ -135,25 +140,27 @@ __global__ void __launch_bounds__(kScanThreads) k_bscan(int wchunk, float *__res
             sel4[k] += a ? 1 : 0;
         }
         const unsigned bal = __ballot_sync(kFull, above);
-        const bool act = h == 0 ? (bal & 0xffffu) != 0 : (bal >> 16) != 0;
-        const int a0 = (bal & 0xffffu) != 0, a1 = (bal >> 16) != 0;
-        const int c0 = __shfl_sync(kFull, ccur, 0), c1 = __shfl_sync(kFull, ccur, 16);
+        const bool act = (bal & gmask) != 0;
+        // ordered positions: one bit per group leader for each class
+        const bool leader = lq == 0;
+        int pos = 0;
+#pragma unroll
+        for (int L = 0; L < kLists; ++L) {
+            const unsigned bits = __ballot_sync(kFull, leader && act && ccur == L);
+            if (ccur == L) pos = run[L] + __popc(bits & lt & ~gmask & ((1u << (h * LPN)) - 1u));
+            run[L] += __popc(bits);
+        }
         if (act) {
             const float f = ccur == 0 ? 1.f : omd;  // a dangling node's fluid leaves entirely (Section 3.3)
 #pragma unroll
             for (int k = 0; k < 4; ++k) rem[k] += f * v[k];
-            const int L = ccur;
-            const int base = L == 0 ? run[0] : (L == 1 ? run[1] : (L == 2 ? run[2] : run[3]));
-            const int pos = base + ((h == 1 && a0 && c0 == L) ? 1 : 0);
-            *reinterpret_cast<float4 *>(sel_rows + (long long)pos * kLanes + 4 * l16) = cur;
-            if (l16 == 0) {
+            *reinterpret_cast<float4 *>(sel_rows + (long long)pos * K + 4 * lq) = cur;
+            if (lq == 0) {
                 sel_node[pos] = (int)node;
                 nsel += 1;
             }
-            *reinterpret_cast<float4 *>(Fb + node * kLanes + 4 * l16) = make_float4(0.f, 0.f, 0.f, 0.f);
+            *reinterpret_cast<float4 *>(Fb + node * K + 4 * lq) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-#pragma unroll
-        for (int L = 0; L < kLists; ++L) run[L] += (a0 && c0 == L) + (a1 && c1 == L);
         cur = nxt;
         ccur = cnxt;
     }
@@ -161,24 +168,27 @@ __global__ void __launch_bounds__(kScanThreads) k_bscan(int wchunk, float *__res
 #pragma unroll
         for (int L = 0; L < kLists; ++L) fcount[L * W + g] = run[L] - start[L];
     }
-    // per-query sums: the two half-warps, then the CTA, then one atomic per query
+    // per-query sums: the groups of a warp, then the CTA, then one atomic per query
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        l1[k] += __shfl_xor_sync(kFull, l1[k], 16);
-        rem[k] += __shfl_xor_sync(kFull, rem[k], 16);
-        sel4[k] += __shfl_xor_sync(kFull, sel4[k], 16);
+    for (int o = LPN; o < 32; o <<= 1) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            l1[k] += __shfl_xor_sync(kFull, l1[k], o);
+            rem[k] += __shfl_xor_sync(kFull, rem[k], o);
+            sel4[k] += __shfl_xor_sync(kFull, sel4[k], o);
+        }
     }
     if (h == 0) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            atomicAdd(&s_l1[4 * l16 + k], (double)l1[k]);
-            atomicAdd(&s_rem[4 * l16 + k], (double)rem[k]);
-            atomicAdd(&s_sel[4 * l16 + k], sel4[k]);
+            atomicAdd(&s_l1[4 * lq + k], (double)l1[k]);
+            atomicAdd(&s_rem[4 * lq + k], (double)rem[k]);
+            atomicAdd(&s_sel[4 * lq + k], sel4[k]);
         }
     }
     __syncthreads();
-    if (l16 == 0 && nsel) atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->srcs), (unsigned long long)nsel);
-    if (threadIdx.x < kLanes && bq[threadIdx.x].active) {
+    if (lq == 0 && nsel) atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->srcs), (unsigned long long)nsel);
+    if (threadIdx.x < K && bq[threadIdx.x].active) {
         atomicAdd(&bq[threadIdx.x].l1_acc, s_l1[threadIdx.x]);
         atomicAdd(&bq[threadIdx.x].rem_acc, s_rem[threadIdx.x]);
         if (s_sel[threadIdx.x]) atomicAdd(&bq[threadIdx.x].selected, s_sel[threadIdx.x]);
@@ -196,25 +206,27 @@ __global__ void __launch_bounds__(kScanThreads) k_bscan(int wchunk, float *__res
 }
 
 // one out-link j of a selected node: this lane's 4 queries of row j += wv
+template <int K>
 __device__ __forceinline__ void bpush_edge(float *__restrict__ Fb, float *hot, int n_hot, int j, int l16, float4 wv) {
     if (j < n_hot) {
-        float *hp = hot + j * kLanes + 4 * l16;
+        float *hp = hot + j * K + 4 * l16;
         atomicAdd(hp, wv.x);
         atomicAdd(hp + 1, wv.y);
         atomicAdd(hp + 2, wv.z);
         atomicAdd(hp + 3, wv.w);
     } else {
-        red_add_v4(Fb + (long long)j * kLanes + 4 * l16, wv);
+        red_add_v4(Fb + (long long)j * K + 4 * l16, wv);
     }
 }
 
 // one selected node's row: H += row; then row * d/outdeg to every child (16 lanes x float4)
+template <int K>
 __device__ __forceinline__ void bpush_node(int node, const float4 row, int l16, int cls_node,
                                            const RowRec<float> *__restrict__ rec, const int *__restrict__ col_idx,
                                            float *__restrict__ Fb, double *__restrict__ Hb, float *hot, int n_hot,
                                            int e_beg, int e_step, bool do_h, long long &edges) {
     if (do_h) {
-        double2 *hp = reinterpret_cast<double2 *>(Hb + (long long)node * kLanes + 4 * l16);
+        double2 *hp = reinterpret_cast<double2 *>(Hb + (long long)node * K + 4 * l16);
         double2 a = hp[0], b = hp[1];
         a.x += row.x;
         a.y += row.y;
@@ -232,34 +244,33 @@ __device__ __forceinline__ void bpush_node(int node, const float4 row, int l16, 
     for (; e + 3 * e_step < end; e += 4 * e_step) {
         const int j0 = __ldg(col_idx + rr.beg + e), j1 = __ldg(col_idx + rr.beg + e + e_step);
         const int j2 = __ldg(col_idx + rr.beg + e + 2 * e_step), j3 = __ldg(col_idx + rr.beg + e + 3 * e_step);
-        bpush_edge(Fb, hot, n_hot, j0, l16, wv);
-        bpush_edge(Fb, hot, n_hot, j1, l16, wv);
-        bpush_edge(Fb, hot, n_hot, j2, l16, wv);
-        bpush_edge(Fb, hot, n_hot, j3, l16, wv);
+        bpush_edge<K>(Fb, hot, n_hot, j0, l16, wv);
+        bpush_edge<K>(Fb, hot, n_hot, j1, l16, wv);
+        bpush_edge<K>(Fb, hot, n_hot, j2, l16, wv);
+        bpush_edge<K>(Fb, hot, n_hot, j3, l16, wv);
     }
-    for (; e < end; e += e_step) bpush_edge(Fb, hot, n_hot, __ldg(col_idx + rr.beg + e), l16, wv);
+    for (; e < end; e += e_step) bpush_edge<K>(Fb, hot, n_hot, __ldg(col_idx + rr.beg + e), l16, wv);
 }
 
+template <int LPN>
 __global__ void __launch_bounds__(kScanThreads) k_bpush(const RowRec<float> *__restrict__ rec,
                                                         const int *__restrict__ col_idx, float *__restrict__ Fb,
-                                                        double *__restrict__ Hb, const unsigned char *__restrict__ cls,
-                                                        const int *__restrict__ region, const int *__restrict__ pre,
-                                                        int W, const int *__restrict__ sel_node,
+                                                        double *__restrict__ Hb, const int *__restrict__ region,
+                                                        const int *__restrict__ pre, int W,
+                                                        const int *__restrict__ sel_node,
                                                         const float *__restrict__ sel_rows, int n_hot,
                                                         BatchCtl *__restrict__ ctl) {
-    __shared__ float hot[kBatchHot * kLanes];
+    constexpr int K = 4 * LPN, GPC = kScanThreads / LPN;   // lane groups per CTA
+    __shared__ float hot[kBatchHot * K];
     __shared__ long long s_red[kWarps];
     __shared__ int s_idx;
     if (ctl->all_done) return;
-    for (int t = threadIdx.x; t < kBatchHot * kLanes; t += kScanThreads) hot[t] = 0.f;
+    for (int t = threadIdx.x; t < kBatchHot * K; t += kScanThreads) hot[t] = 0.f;
     __syncthreads();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, h = lane >> 4, l16 = lane & 15;
-    const int hw = threadIdx.x >> 4;                        // half-warp in the CTA (0..15)
-    const int nhw = gridDim.x * (kScanThreads / 16), ghw = blockIdx.x * (kScanThreads / 16) + hw;
-    (void)w;
-    (void)h;
+    const int grp = threadIdx.x / LPN, lq = threadIdx.x % LPN;
+    const int ngrp = gridDim.x * GPC, ggrp = blockIdx.x * GPC + grp;
     long long edges = 0;
-    // class 3: the whole CTA per node, each half-warp taking every 16th out-link
+    // class 3: the whole CTA per node, each lane group taking every GPC-th out-link
     {
         const int *p3 = pre + 3 * (W + 1);
         const int tot = __ldg(p3 + W);
@@ -272,9 +283,9 @@ __global__ void __launch_bounds__(kScanThreads) k_bpush(const RowRec<float> *__r
             const int pos = s_idx;
             __syncthreads();
             const int node = sel_node[pos];
-            const float4 row = *reinterpret_cast<const float4 *>(sel_rows + (long long)pos * kLanes + 4 * l16);
-            if (hw == 0) {  // H once
-                double2 *hp = reinterpret_cast<double2 *>(Hb + (long long)node * kLanes + 4 * l16);
+            const float4 row = *reinterpret_cast<const float4 *>(sel_rows + (long long)pos * K + 4 * lq);
+            if (grp == 0) {  // H once
+                double2 *hp = reinterpret_cast<double2 *>(Hb + (long long)node * K + 4 * lq);
                 double2 a = hp[0], b = hp[1];
                 a.x += row.x;
                 a.y += row.y;
@@ -282,29 +293,29 @@ __global__ void __launch_bounds__(kScanThreads) k_bpush(const RowRec<float> *__r
                 b.y += row.w;
                 hp[0] = a;
                 hp[1] = b;
-                if (l16 == 0) edges += rec[node].deg;
+                if (lq == 0) edges += rec[node].deg;
             }
-            bpush_node(node, row, l16, 3, rec, col_idx, Fb, Hb, hot, n_hot, hw, kScanThreads / 16, false, edges);
+            bpush_node<K>(node, row, lq, 3, rec, col_idx, Fb, Hb, hot, n_hot, grp, GPC, false, edges);
         }
     }
-    // classes 0, 1, 2: a half-warp per node, contiguous ranges per half-warp
+    // classes 0, 1, 2: a lane group per node, contiguous ranges per group
     for (int L = 0; L < 3; ++L) {
         const int *pl = pre + L * (W + 1);
         const int tot = __ldg(pl + W);
-        const int per = (tot + nhw - 1) / nhw;
-        const int t_beg = min(tot, ghw * per), t_end = min(tot, t_beg + per);
+        const int per = (tot + ngrp - 1) / ngrp;
+        const int t_beg = min(tot, ggrp * per), t_end = min(tot, t_beg + per);
         if (t_beg >= t_end) continue;
         int gl = find_sub(pl, W, t_beg);
         for (int t = t_beg; t < t_end; ++t) {
             while (__ldg(pl + gl + 1) <= t) ++gl;
             const int pos = region[L * (W + 1) + gl] + (t - __ldg(pl + gl));
             const int node = sel_node[pos];
-            const float4 row = *reinterpret_cast<const float4 *>(sel_rows + (long long)pos * kLanes + 4 * l16);
-            bpush_node(node, row, l16, L, rec, col_idx, Fb, Hb, hot, n_hot, 0, 1, true, edges);
+            const float4 row = *reinterpret_cast<const float4 *>(sel_rows + (long long)pos * K + 4 * lq);
+            bpush_node<K>(node, row, lq, L, rec, col_idx, Fb, Hb, hot, n_hot, 0, 1, true, edges);
         }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < n_hot * kLanes; t += kScanThreads) {
+    for (int t = threadIdx.x; t < n_hot * K; t += kScanThreads) {
         const float v = hot[t];
         if (v != 0.f) atomicAdd(Fb + t, v);
     }
@@ -360,12 +371,12 @@ __global__ void k_bfinalize(int n, BatchQ *__restrict__ bq, BatchCtl *__restrict
 }
 
 // exact per-query |F_q|_1 in FP64 (a lane per query column, rows strided over the grid)
-__global__ void k_bl1_exact(long long rows, const float *__restrict__ Fb, BatchQ *__restrict__ bq) {
-    const int q = threadIdx.x & (kLanes - 1);
-    const int rstep = (gridDim.x * blockDim.x) / kLanes;
+__global__ void k_bl1_exact(long long rows, int K, const float *__restrict__ Fb, BatchQ *__restrict__ bq) {
+    const int q = threadIdx.x % K;
+    const int rstep = (gridDim.x * blockDim.x) / K;
     double a = 0.0;
-    for (long long r = (long long)(blockIdx.x * blockDim.x + threadIdx.x) / kLanes; r < rows; r += rstep)
-        a += fabs((double)Fb[r * kLanes + q]);
+    for (long long r = (long long)(blockIdx.x * blockDim.x + threadIdx.x) / K; r < rows; r += rstep)
+        a += fabs((double)Fb[r * K + q]);
     atomicAdd(&bq[q].l1_exact, a);
 }
 
@@ -390,16 +401,28 @@ __global__ void k_bconfirm(int n, BatchQ *__restrict__ bq, BatchCtl *__restrict_
 }
 
 // out[q][i] = Hb[new_of[i]][q] for the first k queries, back in the caller's numbering
-__global__ void k_bgather(int n, int k, const int *__restrict__ new_of, const double *__restrict__ Hb,
+__global__ void k_bgather(int n, int k, int K, const int *__restrict__ new_of, const double *__restrict__ Hb,
                           double *__restrict__ out) {
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < (long long)n * kLanes;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < (long long)n * K;
          t += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(t / kLanes), q = (int)(t % kLanes);
-        if (q < k) out[(long long)q * n + i] = Hb[(long long)new_of[i] * kLanes + q];
+        const int i = (int)(t / K), q = (int)(t % K);
+        if (q < k) out[(long long)q * n + i] = Hb[(long long)new_of[i] * K + q];
     }
 }
 
-di_status build_batch_graph(di_graph *g) {
+template <int LPN>
+void capture_batch_body(di_graph *g, cudaGraphConditionalHandle handle) {
+    const int nhot = std::min(g->n_hot, kBatchHot);
+    k_bscan<LPN><<<g->G, kScanThreads, 0, g->cap>>>(g->chunk / kWarps, g->Fb, g->cls, g->region, g->W, g->fcount,
+                                                    g->pre, g->ticket, g->selb_node, g->selb_rows, g->bq, g->bctl,
+                                                    g->d);
+    k_bpush<LPN><<<g->G, kScanThreads, 0, g->cap>>>(g->rec32, g->col_idx, g->Fb, g->Hb, g->region, g->pre, g->W,
+                                                    g->selb_node, g->selb_rows, nhot, g->bctl);
+    k_bfinalize<<<1, kLanes, 0, g->cap>>>(g->n, g->bq, g->bctl, handle, 1);
+}
+
+// widths 8, 16, 32, 64 queries use slots 0..3
+di_status build_batch_graph(di_graph *g, int slot) {
     cudaGraph_t graph = nullptr;
     DI_CUDA(cudaGraphCreate(&graph, 0));
     cudaGraphConditionalHandle handle;
@@ -416,20 +439,20 @@ di_status build_batch_graph(di_graph *g) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     e = cudaStreamBeginCaptureToGraph(g->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(e, "cudaStreamBeginCaptureToGraph"); }
-    const int nhot = std::min(g->n_hot, kBatchHot);
-    k_bscan<<<g->G, kScanThreads, 0, g->cap>>>(g->chunk / kWarps, g->Fb, g->cls, g->region, g->W, g->fcount, g->pre,
-                                               g->ticket, g->selb_node, g->selb_rows, g->bq, g->bctl, g->d);
-    k_bpush<<<g->G, kScanThreads, 0, g->cap>>>(g->rec32, g->col_idx, g->Fb, g->Hb, g->cls, g->region, g->pre, g->W,
-                                               g->selb_node, g->selb_rows, nhot, g->bctl);
-    k_bfinalize<<<1, kLanes, 0, g->cap>>>(g->n, g->bq, g->bctl, handle, 1);
+    switch (slot) {
+        case 0: capture_batch_body<2>(g, handle); break;
+        case 1: capture_batch_body<4>(g, handle); break;
+        case 2: capture_batch_body<8>(g, handle); break;
+        default: capture_batch_body<16>(g, handle); break;
+    }
     cudaGraph_t captured = nullptr;
     e = cudaStreamEndCapture(g->cap, &captured);
     if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(e, "cudaStreamEndCapture"); }
     cudaGraphExec_t exec = nullptr;
     e = cudaGraphInstantiate(&exec, graph, 0);
     if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(e, "cudaGraphInstantiate(batch)"); }
-    g->graph[3] = graph;
-    g->exec[3] = exec;
+    g->bgraph[slot] = graph;
+    g->bexec[slot] = exec;
     return DI_OK;
 }
 
@@ -455,8 +478,11 @@ di_status run_query_batch(di_graph *g, int k, const int *seed_ptr, const int *se
     cudaStream_t s = g->stream;
     di_status r = batch_alloc(g);
     if (r != DI_OK) return r;
-    if (!g->exec[3]) {
-        r = build_batch_graph(g);
+    // the narrowest row that holds the batch: 8, 16, 32 or 64 queries
+    const int slot = k <= 8 ? 0 : (k <= 16 ? 1 : (k <= 32 ? 2 : 3));
+    const int K = 8 << slot;
+    if (!g->bexec[slot]) {
+        r = build_batch_graph(g, slot);
         if (r != DI_OK) return r;
     }
     const int n = g->n;
@@ -483,18 +509,18 @@ di_status run_query_batch(di_graph *g, int k, const int *seed_ptr, const int *se
     DI_CUDA(cudaMemcpyAsync(d_seeds, seeds, sizeof(int) * nitems, cudaMemcpyHostToDevice, s));
     DI_CUDA(cudaMemcpyAsync(d_val, val.data(), sizeof(double) * nitems, cudaMemcpyHostToDevice, s));
     DI_CUDA(cudaEventRecord(g->ev0, s));
-    const int grid = (int)std::max(1LL, std::min((rows * kLanes + 255) / 256, (long long)g->num_sms * 8));
-    k_binit<<<grid, 256, 0, s>>>(rows, n, g->Fb, g->Hb);
-    k_bseeds<<<std::max(1, std::min(1024, (nitems + 255) / 256)), 256, 0, s>>>(nitems, d_q, d_seeds, d_val, g->new_of,
-                                                                           g->Fb);
+    const int grid = (int)std::max(1LL, std::min((rows * K + 255) / 256, (long long)g->num_sms * 8));
+    k_binit<<<grid, 256, 0, s>>>(rows, n, K, g->Fb, g->Hb);
+    k_bseeds<<<std::max(1, std::min(1024, (nitems + 255) / 256)), 256, 0, s>>>(nitems, K, d_q, d_seeds, d_val,
+                                                                           g->new_of, g->Fb);
     k_bctl_init<<<1, kLanes, 0, s>>>(k, g->bq, g->bctl, tol, omd, beta, n, max_sweeps);
     DI_CUDA(cudaGetLastError());
     int attempts = 0;
     for (int attempt = 0; attempt < 8; ++attempt) {
         ++attempts;
-        DI_CUDA(cudaGraphLaunch(g->exec[3], s));
+        DI_CUDA(cudaGraphLaunch(g->bexec[slot], s));
         k_bzero_exact<<<1, kLanes, 0, s>>>(g->bq);
-        k_bl1_exact<<<grid, 256, 0, s>>>(rows, g->Fb, g->bq);
+        k_bl1_exact<<<grid, 256, 0, s>>>(rows, K, g->Fb, g->bq);
         k_bconfirm<<<1, kLanes, 0, s>>>(n, g->bq, g->bctl);
         DI_CUDA(cudaGetLastError());
         DI_CUDA(cudaMemcpyAsync(g->h_bctl, g->bctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
@@ -508,7 +534,7 @@ di_status run_query_batch(di_graph *g, int k, const int *seed_ptr, const int *se
             DI_CUDA(cudaMallocAsync(&tmp, sizeof(double) * (size_t)n * k, s));
             dst = tmp;
         }
-        k_bgather<<<grid, 256, 0, s>>>(n, k, g->new_of, g->Hb, dst);
+        k_bgather<<<grid, 256, 0, s>>>(n, k, K, g->new_of, g->Hb, dst);
         DI_CUDA(cudaGetLastError());
         if (tmp) {
             DI_CUDA(cudaMemcpyAsync(H_out, tmp, sizeof(double) * (size_t)n * k, cudaMemcpyDeviceToHost, s));

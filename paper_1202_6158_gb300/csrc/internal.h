@@ -204,9 +204,12 @@ struct di_graph {
     diter::BatchQ *bq = nullptr, *h_bq = nullptr;
     diter::BatchCtl *bctl = nullptr, *h_bctl = nullptr;
 
-    // captured solve loops: [0] FP64 sweeps, [1] FP32-mixed sweeps, [2] power iteration, [3] batch
-    cudaGraph_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
-    cudaGraphExec_t exec[4] = {nullptr, nullptr, nullptr, nullptr};
+    // captured solve loops: [0] FP64 sweeps, [1] FP32-mixed sweeps, [2] power iteration
+    cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
+    cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
+    // batch loops for rows of 8, 16, 32, 64 queries
+    cudaGraph_t bgraph[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaGraphExec_t bexec[4] = {nullptr, nullptr, nullptr, nullptr};
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     diter::SolveState *h_st = nullptr; // pinned host mirror
