@@ -128,24 +128,32 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def push_traffic():
-    """DRAM bytes per push launch from the committed ncu summary, if sweep.cu is unchanged since.
-
-    profiles/push_sweep_zipf24.md records the sha256 of csrc/sweep.cu it was taken
-    with; a different hash means the kernel changed and the counters no longer apply.
-    """
+def push_sources_digest():
+    """sha256 over the sources the push kernel is compiled from (sweep.cu and its two headers)."""
     import hashlib
-    src = os.path.join(ROOT, "paper_1202_6158_gb300", "csrc", "sweep.cu")
+    h = hashlib.sha256()
+    for name in ("sweep.cu", "device_common.cuh", "internal.h"):
+        with open(os.path.join(ROOT, "paper_1202_6158_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def push_traffic():
+    """DRAM bytes per push launch from the committed ncu summary, if the push sources are unchanged since.
+
+    profiles/push_sweep_zipf24.md records the digest of the push kernel's sources it
+    was taken with; a different digest means the kernel changed and the counters no
+    longer apply.
+    """
     summ = os.path.join(ROOT, "profiles", "push_sweep_zipf24.md")
-    if not (os.path.exists(src) and os.path.exists(summ)):
+    if not os.path.exists(summ):
         return None
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
     vals = {}
     for line in open(summ):
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("sweep.cu sha256") != digest:
+    if vals.get("push sources sha256") != push_sources_digest():
         return None
     try:
         return float(vals["dram bytes per launch"])

@@ -246,6 +246,115 @@ di_status di_get_state(const di_graph *g, double *F_out, double *H_out);
 di_status di_get_profile(const di_graph *g, di_profile *out);
 
 /*
+ * Serving: a continuous stream of personalized queries over several graphs.
+ *
+ * Personalized PageRank (Section 2.1: V is the personalization vector) solved
+ * by threshold sweeps (Section 4.2) on interleaved query lanes, as in
+ * di_query_batch; queries on one graph share one read of each out-link list.
+ * The diffusions of different queries are independent and any order of
+ * diffusions reaches the same limit (Section 2.2), so a query gives the same
+ * answer (within the two bounds) whether it runs alone or among others, and
+ * lanes can be reused mid-flight: between two rounds of sweeps, queries that
+ * met their bound leave their lanes and queued queries take them, while the
+ * other lanes carry on.
+ *
+ * Each graph gets a lane pool of 8, 16, 32 or 64 lanes; a lane costs about
+ * 16 bytes per node (FP32 fluid, FP64 history, FP32 sweep copy).  Queries take
+ * the lowest free lanes, and each round runs on rows of 8, 16, 32 or 64 lanes,
+ * the narrowest that covers every busy lane, so light load moves short rows.
+ * The pools are sized at creation by di_plan_lanes under mem_budget bytes.
+ * Each pool runs on its own CUDA stream, so rounds of different graphs overlap.
+ *
+ * The server is driven from one host thread: di_server_submit queues, and
+ * di_server_poll does all the work (finishing rounds, copying results out,
+ * admitting queued queries, launching the next rounds) and returns finished
+ * queries.  Nothing runs between polls except the rounds already launched.
+ */
+typedef struct di_server di_server; /* opaque; owns its lane pools and streams */
+
+typedef struct {
+    int64_t ticket;       /* returned by di_server_submit */
+    int32_t graph;        /* index of the graph in di_server_create's list */
+    int32_t status;       /* DI_OK, or DI_ENOTCONVERGED if the lane's sweep limit stopped it */
+    double bound;         /* exact |F_q|_1/(1-d) when it stopped: |X_q - H_q|_1 <= bound */
+    int32_t sweeps;       /* sweeps the query took part in */
+    int32_t lane;         /* lane it ran in */
+    double t_submit;      /* di_clock() at di_server_submit */
+    double t_admit;       /* di_clock() when it was given a lane */
+    double t_done;        /* di_clock() when its H was in the caller's buffer */
+} di_completion;
+
+/*
+ * Lane counts under a memory budget (host only, no GPU needed).
+ *   lane_bytes[i]   bytes one lane of graph i costs; fixed_bytes[i] the rest of its pool
+ *   lanes_out[i]    receives 64, 32, 16 or 8
+ * Every graph starts at 64 lanes; while the total is above budget, the graph whose
+ * lanes cost the most (lowest index on ties) is halved, down to 8.  DI_ENOMEM if
+ * 8 lanes each do not fit.
+ */
+di_status di_plan_lanes(const int64_t *lane_bytes, const int64_t *fixed_bytes, int32_t ngraphs, int64_t budget,
+                        int32_t *lanes_out);
+
+/*
+ * Create a server over ngraphs graphs (not owned; they must outlive the server and
+ * must not be used by other calls while it exists).
+ *   mem_budget    device bytes the lane pools may take (<= 0: no limit, 64 lanes each)
+ *   round_sweeps  a round returns to the host after this many sweeps at most (1..1024)
+ *   lane_sweeps   a query stops with DI_ENOTCONVERGED after this many sweeps (>= 1)
+ */
+di_status di_server_create(di_graph *const *graphs, int32_t ngraphs, int64_t mem_budget, int32_t round_sweeps,
+                           int32_t lane_sweeps, di_server **out);
+
+/* Lanes of each graph's pool (host int32[ngraphs]). */
+di_status di_server_lanes(const di_server *s, int32_t *lanes_out);
+
+/*
+ * Queue one query on graph `graph`: V uniform over seeds (w == NULL) or
+ * proportional to w, stop when |F_q|_1/(1-d) <= tol.
+ *   seeds, w  host arrays of nseeds entries (copied at the call)
+ *   H_out     NULL (result dropped), device memory, page-locked host memory (written
+ *             by the kernel directly), or pageable host memory (staged through the
+ *             device); n doubles in input numbering; must stay valid until the query
+ *             completes
+ *   ticket    receives the query's ticket
+ */
+di_status di_server_submit(di_server *s, int32_t graph, const int32_t *seeds, const double *w, int32_t nseeds,
+                           double tol, double *H_out, int64_t *ticket);
+
+/*
+ * Make progress and collect finished queries: returns as soon as at least one
+ * query finished, or after wait_s seconds (0: one pass, no waiting).
+ *   out   host di_completion[cap]; *nout receives the number written (finished
+ *         queries beyond cap are kept for the next call)
+ */
+di_status di_server_poll(di_server *s, double wait_s, di_completion *out, int32_t cap, int32_t *nout);
+
+/* Counters of one graph's lane pool since the server was created. */
+typedef struct {
+    int64_t rounds;          /* launches of the sweep loop */
+    int64_t sweeps;          /* sweeps run; each serves every busy lane */
+    int64_t edges_pushed;    /* out-links pushed; each serves every lane of the row */
+    int64_t sources_pushed;  /* selected nodes */
+    int64_t admitted;        /* queries given a lane */
+    int64_t completed;       /* queries copied out */
+    int64_t width_sweeps;    /* sum over rounds of sweeps x lanes per row of that round's loop */
+    double device_ms;        /* CUDA-event time of the rounds, from lane admission to the lane-state copy */
+    int32_t lanes;
+    int32_t pad;
+} di_server_graph_stats;
+
+di_status di_server_stats(const di_server *s, int32_t graph, di_server_graph_stats *out);
+
+/* Queries queued (no lane yet) and running (in a lane or being copied out). */
+di_status di_server_pending(const di_server *s, int64_t *queued, int64_t *running);
+
+/* Waits for launched work, then frees everything; queries not completed are dropped.  NULL-safe. */
+void di_server_free(di_server *s);
+
+/* Seconds on the monotonic host clock used for di_completion times. */
+double di_clock(void);
+
+/*
  * di_power without any device allocation.  The paper has no counterpart: this
  * is a service for callers that cannot call cudaMalloc -- code running while a
  * CUDA graph is being captured, services that must not grow their device memory

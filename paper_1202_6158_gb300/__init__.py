@@ -18,12 +18,14 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (DI_EINVAL, DI_ENOTCONVERGED, DI_FP32_MIXED, DI_FP64, DI_OK, DiError, check, di_profile,
-                   di_solve_opts, di_stats, di_sweep_record, ptr)
+from ._lib import (DI_EINVAL, DI_ENOMEM, DI_ENOTCONVERGED, DI_FP32_MIXED, DI_FP64, DI_OK, DiError, check,
+                   di_completion, di_profile, di_server_graph_stats, di_solve_opts, di_stats, di_sweep_record, ptr)
 
 __all__ = ["DiGraph", "DiError", "DI_FP64", "DI_FP32_MIXED", "DI_OK", "DI_EINVAL", "DI_ENOTCONVERGED",
            "di_graph_create", "di_free", "di_solve", "di_solve_ex", "di_query", "di_query_batch", "di_power", "di_power_ex", "di_graph_export",
-           "di_get_trace", "di_get_state", "di_get_profile", "di_power_noalloc", "di_version", "load"]
+           "di_get_trace", "di_get_state", "di_get_profile", "di_power_noalloc", "di_version", "load",
+           "di_plan_lanes", "di_server_create", "di_server_lanes", "di_server_submit", "di_server_poll",
+           "di_server_pending", "di_server_stats", "di_server_free", "di_clock", "DiServer"]
 
 
 def load():
@@ -232,3 +234,132 @@ class DiGraph:
         H = np.empty(self.n, np.float64)
         di_get_state(self.handle, F, H)
         return F, H
+
+
+# ------------------------------------------------------------------ serving
+
+def di_clock() -> float:
+    """Seconds on the library's monotonic clock (the clock of di_completion times)."""
+    return load().di_clock()
+
+
+def di_plan_lanes(lane_bytes, fixed_bytes, budget) -> list:
+    """Lanes per graph (64/32/16/8) under a device-memory budget (host only)."""
+    lb = np.ascontiguousarray(lane_bytes, dtype=np.int64)
+    fb = np.ascontiguousarray(fixed_bytes, dtype=np.int64)
+    out = np.empty(len(lb), np.int32)
+    check(load().di_plan_lanes(ptr(lb), ptr(fb), len(lb), int(budget), ptr(out)))
+    return out.tolist()
+
+
+def di_server_create(graph_handles, mem_budget=0, round_sweeps=16, lane_sweeps=100000) -> int:
+    arr = (ctypes.c_void_p * len(graph_handles))(*graph_handles)
+    out = ctypes.c_void_p()
+    check(load().di_server_create(ctypes.cast(arr, ctypes.c_void_p), len(graph_handles), int(mem_budget),
+                                  int(round_sweeps), int(lane_sweeps), ctypes.byref(out)))
+    return out.value
+
+
+def di_server_lanes(handle, ngraphs) -> list:
+    out = np.empty(ngraphs, np.int32)
+    check(load().di_server_lanes(handle, ptr(out)))
+    return out.tolist()
+
+
+def di_server_submit(handle, graph, seeds, tol, H_out=None, w=None) -> int:
+    s = np.ascontiguousarray(seeds, dtype=np.int32)
+    ww = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+    t = ctypes.c_int64(0)
+    check(load().di_server_submit(handle, int(graph), ptr(s), ptr(ww), len(s), float(tol), ptr(H_out),
+                                  ctypes.byref(t)))
+    return t.value
+
+
+def di_server_poll(handle, wait_s=0.0, cap=256) -> list:
+    out = (di_completion * cap)()
+    n = ctypes.c_int32(0)
+    check(load().di_server_poll(handle, float(wait_s), out, cap, ctypes.byref(n)))
+    return [out[i].as_dict() for i in range(n.value)]
+
+
+def di_server_stats(handle, graph) -> dict:
+    st = di_server_graph_stats()
+    check(load().di_server_stats(handle, int(graph), ctypes.byref(st)))
+    return st.as_dict()
+
+
+def di_server_pending(handle) -> tuple:
+    q, r = ctypes.c_int64(0), ctypes.c_int64(0)
+    check(load().di_server_pending(handle, ctypes.byref(q), ctypes.byref(r)))
+    return q.value, r.value
+
+
+def di_server_free(handle) -> None:
+    if handle:
+        load().di_server_free(handle)
+
+
+class DiServer:
+    """Continuous batching of personalized queries over several DiGraphs.
+
+    ``submit`` queues a query and returns its ticket; ``poll`` advances every
+    graph's lanes and returns finished queries (dicts of di_completion fields).
+    The H of a query is written to the buffer given at submit (n doubles: numpy,
+    pinned or CUDA tensor), or dropped when none is given.
+    """
+
+    def __init__(self, graphs, mem_budget=0, round_sweeps=16, lane_sweeps=100000):
+        self.graphs = list(graphs)
+        self.handle = di_server_create([g.handle for g in self.graphs], mem_budget, round_sweeps, lane_sweeps)
+        self._keep = {}   # ticket -> output buffer, alive until the query completes
+
+    def lanes(self):
+        return di_server_lanes(self.handle, len(self.graphs))
+
+    def submit(self, graph, seeds, tol, H_out=None, w=None):
+        t = di_server_submit(self.handle, graph, seeds, tol, H_out, w)
+        if H_out is not None:
+            self._keep[t] = H_out
+        return t
+
+    def poll(self, wait_s=0.0, cap=256):
+        done = di_server_poll(self.handle, wait_s, cap)
+        for c in done:
+            self._keep.pop(c["ticket"], None)
+        return done
+
+    def pending(self):
+        return di_server_pending(self.handle)
+
+    def stats(self, graph):
+        return di_server_stats(self.handle, graph)
+
+    def drain(self, timeout_s=600.0):
+        """Poll until nothing is queued or running; returns every completion seen."""
+        out = []
+        t_end = di_clock() + timeout_s
+        while True:
+            q, r = self.pending()
+            if q == 0 and r == 0:
+                return out
+            if di_clock() > t_end:
+                raise DiError(_lib.DI_ETIMEOUT, "drain timed out")
+            out += self.poll(0.05)
+
+    def close(self):
+        if self.handle:
+            di_server_free(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -54,6 +54,24 @@ class di_profile(ctypes.Structure):
                 ("sweeps", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
+class di_completion(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_int64), ("graph", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("bound", ctypes.c_double), ("sweeps", ctypes.c_int32), ("lane", ctypes.c_int32),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class di_server_graph_stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int64), ("sweeps", ctypes.c_int64), ("edges_pushed", ctypes.c_int64),
+                ("sources_pushed", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("width_sweeps", ctypes.c_int64), ("device_ms", ctypes.c_double), ("lanes", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
 _lib = None
 
 
@@ -83,6 +101,15 @@ def load(path: str = LIB_PATH):
         "di_get_state": ([vp, vp, vp], ctypes.c_int),
         "di_get_profile": ([vp, ctypes.POINTER(di_profile)], ctypes.c_int),
         "di_power_noalloc": ([i32, vp, vp, i64, vp, f64, f64, i32, vp, ctypes.POINTER(di_stats), vp], ctypes.c_int),
+        "di_plan_lanes": ([vp, vp, i32, i64, vp], ctypes.c_int),
+        "di_server_create": ([vp, i32, i64, i32, i32, ctypes.POINTER(vp)], ctypes.c_int),
+        "di_server_lanes": ([vp, vp], ctypes.c_int),
+        "di_server_submit": ([vp, i32, vp, vp, i32, f64, vp, ctypes.POINTER(i64)], ctypes.c_int),
+        "di_server_poll": ([vp, f64, vp, i32, ctypes.POINTER(i32)], ctypes.c_int),
+        "di_server_stats": ([vp, i32, ctypes.POINTER(di_server_graph_stats)], ctypes.c_int),
+        "di_server_pending": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64)], ctypes.c_int),
+        "di_server_free": ([vp], None),
+        "di_clock": ([], f64),
         "di_last_error": ([], ctypes.c_char_p),
         "di_version": ([], ctypes.c_char_p),
     }

@@ -28,7 +28,7 @@ di_status cuda_fail(cudaError_t e, const char *what) {
     return set_error(DI_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-static bool is_device_ptr(const void *p) {
+bool is_device_ptr(const void *p) {
     if (!p) return false;
     cudaPointerAttributes a;
     cudaError_t e = cudaPointerGetAttributes(&a, p);
@@ -37,6 +37,21 @@ static bool is_device_ptr(const void *p) {
         return false;
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// the address a kernel writes p through: p itself for device memory, the mapped address
+// for page-locked host memory, NULL for pageable host memory (the caller stages the copy)
+void *kernel_ptr(void *p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) return a.devicePointer;
+    return nullptr;
 }
 
 static di_status copy_in(void *dst, const void *src, size_t bytes, cudaStream_t s) {
@@ -52,13 +67,9 @@ static void free_graph(di_graph *g) {
         if (g->exec[k]) cudaGraphExecDestroy(g->exec[k]);
         if (g->graph[k]) cudaGraphDestroy(g->graph[k]);
     }
-    for (int k = 0; k < 4; ++k) {
-        if (g->bexec[k]) cudaGraphExecDestroy(g->bexec[k]);
-        if (g->bgraph[k]) cudaGraphDestroy(g->bgraph[k]);
-    }
+    pool_free(g->bp, g->stream);
     void *bufs[] = {g->row_ptr, g->col_idx, g->in_ptr, g->in_src, g->bin_of, g->in_bin_of, g->pull_ids, g->V,
                     g->inv_deg, g->inv_deg32, g->hot_ids, g->perm, g->new_of, g->rec64, g->rec32,
-                    g->Fb, g->Hb, g->selb_rows, g->selb_node, g->bq, g->bctl,
                     g->long_prefix, g->region, g->fcount, g->pre, g->ticket, g->sel, g->cls, g->F64, g->F32, g->H, g->part, g->st,
                     g->trace, g->X, g->Z[0], g->Z[1], g->Ylong, g->ppart, g->pst};
     for (void *b : bufs)
@@ -66,8 +77,6 @@ static void free_graph(di_graph *g) {
     cudaStreamSynchronize(g->stream);
     if (g->h_st) cudaFreeHost(g->h_st);
     if (g->h_pst) cudaFreeHost(g->h_pst);
-    if (g->h_bq) cudaFreeHost(g->h_bq);
-    if (g->h_bctl) cudaFreeHost(g->h_bctl);
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
     for (int k = 0; k < 4; ++k)

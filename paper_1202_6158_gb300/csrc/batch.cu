@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <vector>
 
@@ -69,6 +70,8 @@ __global__ void k_bctl_init(int k, BatchQ *__restrict__ bq, BatchCtl *__restrict
         b.done = q < k ? (omd <= b.tolR ? 1 : 0) : 1;
         b.T = b.done ? INFINITY : beta * omd / (double)n;
         b.selected = 0;
+        b.sweeps = 0;
+        b.confirmed = 0;
         bq[q] = b;
     }
     if (q == 0) {
@@ -78,6 +81,11 @@ __global__ void k_bctl_init(int k, BatchQ *__restrict__ bq, BatchCtl *__restrict
         ctl->srcs = 0;
         ctl->beta = beta;
         ctl->body_runs = 0;
+        ctl->round_sweeps = 0;
+        ctl->round_cap = max_sweeps;
+        ctl->stop_on_done = 0;
+        ctl->lane_max_sweeps = INT_MAX;
+        ctl->newly = 0;
         int all = 1;
         for (int i = 0; i < k; ++i) all &= (omd <= tol * omd) ? 1 : 0;
         ctl->all_done = all;
@@ -86,7 +94,7 @@ __global__ void k_bctl_init(int k, BatchQ *__restrict__ bq, BatchCtl *__restrict
 
 // LPN lanes per node row (K = 4 LPN queries, a float4 per lane); 32/LPN rows per warp step
 template <int LPN>
-__global__ void __launch_bounds__(kScanThreads) k_bscan(int wchunk, float *__restrict__ Fb,
+__global__ void __launch_bounds__(kScanThreads) k_bscan(int wchunk, int S, float *__restrict__ Fb,
                                                         const unsigned char *__restrict__ cls,
                                                         const int *__restrict__ region, int W,
                                                         int *__restrict__ fcount, int *__restrict__ pre,
@@ -120,14 +128,14 @@ __global__ void __launch_bounds__(kScanThreads) k_bscan(int wchunk, float *__res
     int sel4[4] = {0, 0, 0, 0};
     int nsel = 0;
     const int nsteps = wchunk / NPS;
-    float4 cur = *reinterpret_cast<const float4 *>(Fb + (wbeg + h) * K + 4 * lq);
+    float4 cur = *reinterpret_cast<const float4 *>(Fb + (wbeg + h) * S + 4 * lq);
     int ccur = cls[wbeg + h];
     for (int s = 0; s < nsteps; ++s) {
         const long long node = wbeg + (long long)NPS * s + h;
         float4 nxt = make_float4(0.f, 0.f, 0.f, 0.f);
         int cnxt = 0;
         if (s + 1 < nsteps) {
-            nxt = *reinterpret_cast<const float4 *>(Fb + (node + NPS) * K + 4 * lq);
+            nxt = *reinterpret_cast<const float4 *>(Fb + (node + NPS) * S + 4 * lq);
             cnxt = cls[node + NPS];
         }
         const float v[4] = {cur.x, cur.y, cur.z, cur.w};
@@ -159,7 +167,7 @@ __global__ void __launch_bounds__(kScanThreads) k_bscan(int wchunk, float *__res
                 sel_node[pos] = (int)node;
                 nsel += 1;
             }
-            *reinterpret_cast<float4 *>(Fb + node * K + 4 * lq) = make_float4(0.f, 0.f, 0.f, 0.f);
+            *reinterpret_cast<float4 *>(Fb + node * S + 4 * lq) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         cur = nxt;
         ccur = cnxt;
@@ -207,7 +215,8 @@ __global__ void __launch_bounds__(kScanThreads) k_bscan(int wchunk, float *__res
 
 // one out-link j of a selected node: this lane's 4 queries of row j += wv
 template <int K>
-__device__ __forceinline__ void bpush_edge(float *__restrict__ Fb, float *hot, int n_hot, int j, int l16, float4 wv) {
+__device__ __forceinline__ void bpush_edge(float *__restrict__ Fb, int S, float *hot, int n_hot, int j, int l16,
+                                           float4 wv) {
     if (j < n_hot) {
         float *hp = hot + j * K + 4 * l16;
         atomicAdd(hp, wv.x);
@@ -215,7 +224,7 @@ __device__ __forceinline__ void bpush_edge(float *__restrict__ Fb, float *hot, i
         atomicAdd(hp + 2, wv.z);
         atomicAdd(hp + 3, wv.w);
     } else {
-        red_add_v4(Fb + (long long)j * K + 4 * l16, wv);
+        red_add_v4(Fb + (long long)j * S + 4 * l16, wv);
     }
 }
 
@@ -223,10 +232,10 @@ __device__ __forceinline__ void bpush_edge(float *__restrict__ Fb, float *hot, i
 template <int K>
 __device__ __forceinline__ void bpush_node(int node, const float4 row, int l16, int cls_node,
                                            const RowRec<float> *__restrict__ rec, const int *__restrict__ col_idx,
-                                           float *__restrict__ Fb, double *__restrict__ Hb, float *hot, int n_hot,
+                                           float *__restrict__ Fb, double *__restrict__ Hb, int S, float *hot, int n_hot,
                                            int e_beg, int e_step, bool do_h, long long &edges) {
     if (do_h) {
-        double2 *hp = reinterpret_cast<double2 *>(Hb + (long long)node * K + 4 * l16);
+        double2 *hp = reinterpret_cast<double2 *>(Hb + (long long)node * S + 4 * l16);
         double2 a = hp[0], b = hp[1];
         a.x += row.x;
         a.y += row.y;
@@ -244,18 +253,18 @@ __device__ __forceinline__ void bpush_node(int node, const float4 row, int l16, 
     for (; e + 3 * e_step < end; e += 4 * e_step) {
         const int j0 = __ldg(col_idx + rr.beg + e), j1 = __ldg(col_idx + rr.beg + e + e_step);
         const int j2 = __ldg(col_idx + rr.beg + e + 2 * e_step), j3 = __ldg(col_idx + rr.beg + e + 3 * e_step);
-        bpush_edge<K>(Fb, hot, n_hot, j0, l16, wv);
-        bpush_edge<K>(Fb, hot, n_hot, j1, l16, wv);
-        bpush_edge<K>(Fb, hot, n_hot, j2, l16, wv);
-        bpush_edge<K>(Fb, hot, n_hot, j3, l16, wv);
+        bpush_edge<K>(Fb, S, hot, n_hot, j0, l16, wv);
+        bpush_edge<K>(Fb, S, hot, n_hot, j1, l16, wv);
+        bpush_edge<K>(Fb, S, hot, n_hot, j2, l16, wv);
+        bpush_edge<K>(Fb, S, hot, n_hot, j3, l16, wv);
     }
-    for (; e < end; e += e_step) bpush_edge<K>(Fb, hot, n_hot, __ldg(col_idx + rr.beg + e), l16, wv);
+    for (; e < end; e += e_step) bpush_edge<K>(Fb, S, hot, n_hot, __ldg(col_idx + rr.beg + e), l16, wv);
 }
 
 template <int LPN>
 __global__ void __launch_bounds__(kScanThreads) k_bpush(const RowRec<float> *__restrict__ rec,
                                                         const int *__restrict__ col_idx, float *__restrict__ Fb,
-                                                        double *__restrict__ Hb, const int *__restrict__ region,
+                                                        double *__restrict__ Hb, int S, const int *__restrict__ region,
                                                         const int *__restrict__ pre, int W,
                                                         const int *__restrict__ sel_node,
                                                         const float *__restrict__ sel_rows, int n_hot,
@@ -285,7 +294,7 @@ __global__ void __launch_bounds__(kScanThreads) k_bpush(const RowRec<float> *__r
             const int node = sel_node[pos];
             const float4 row = *reinterpret_cast<const float4 *>(sel_rows + (long long)pos * K + 4 * lq);
             if (grp == 0) {  // H once
-                double2 *hp = reinterpret_cast<double2 *>(Hb + (long long)node * K + 4 * lq);
+                double2 *hp = reinterpret_cast<double2 *>(Hb + (long long)node * S + 4 * lq);
                 double2 a = hp[0], b = hp[1];
                 a.x += row.x;
                 a.y += row.y;
@@ -295,7 +304,7 @@ __global__ void __launch_bounds__(kScanThreads) k_bpush(const RowRec<float> *__r
                 hp[1] = b;
                 if (lq == 0) edges += rec[node].deg;
             }
-            bpush_node<K>(node, row, lq, 3, rec, col_idx, Fb, Hb, hot, n_hot, grp, GPC, false, edges);
+            bpush_node<K>(node, row, lq, 3, rec, col_idx, Fb, Hb, S, hot, n_hot, grp, GPC, false, edges);
         }
     }
     // classes 0, 1, 2: a lane group per node, contiguous ranges per group
@@ -311,22 +320,24 @@ __global__ void __launch_bounds__(kScanThreads) k_bpush(const RowRec<float> *__r
             const int pos = region[L * (W + 1) + gl] + (t - __ldg(pl + gl));
             const int node = sel_node[pos];
             const float4 row = *reinterpret_cast<const float4 *>(sel_rows + (long long)pos * K + 4 * lq);
-            bpush_node<K>(node, row, lq, L, rec, col_idx, Fb, Hb, hot, n_hot, 0, 1, true, edges);
+            bpush_node<K>(node, row, lq, L, rec, col_idx, Fb, Hb, S, hot, n_hot, 0, 1, true, edges);
         }
     }
     __syncthreads();
     for (int t = threadIdx.x; t < n_hot * K; t += kScanThreads) {
         const float v = hot[t];
-        if (v != 0.f) atomicAdd(Fb + t, v);
+        if (v != 0.f) atomicAdd(Fb + (long long)(t / K) * S + t % K, v);
     }
     const long long be = block_sum(edges, s_red);
     if (threadIdx.x == 0 && be) atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->edges),
                                           (unsigned long long)be);
 }
 
+// one thread per lane.  The loop ends when no lane is open or at the sweep limit; a
+// serving round also ends after round_cap sweeps, or when a lane stops (stop_on_done).
 __global__ void k_bfinalize(int n, BatchQ *__restrict__ bq, BatchCtl *__restrict__ ctl,
                             cudaGraphConditionalHandle handle, int in_graph) {
-    __shared__ int s_open;
+    __shared__ int s_open, s_newly;
     if (ctl->all_done) {
         if (threadIdx.x == 0) {
             ctl->body_runs += 1;
@@ -334,7 +345,10 @@ __global__ void k_bfinalize(int n, BatchQ *__restrict__ bq, BatchCtl *__restrict
         }
         return;
     }
-    if (threadIdx.x == 0) s_open = 0;
+    if (threadIdx.x == 0) {
+        s_open = 0;
+        s_newly = 0;
+    }
     __syncthreads();
     const int q = threadIdx.x;
     if (q < kLanes) {
@@ -346,9 +360,12 @@ __global__ void k_bfinalize(int n, BatchQ *__restrict__ bq, BatchCtl *__restrict
             b.l1_acc = 0.0;
             b.rem_acc = 0.0;
             if (!b.done) {
-                if (b.R <= b.tolR) {
-                    b.done = 1;
+                b.sweeps += 1;
+                if (b.R <= b.tolR || b.sweeps >= ctl->lane_max_sweeps) {
+                    b.done = b.R <= b.tolR ? 1 : 2;
                     b.T = INFINITY;
+                    b.l1_exact = 0.0;  // summed by the confirmation that follows the loop
+                    atomicAdd(&s_newly, 1);
                 } else {
                     // T_q = beta R_q / n; halved when the query selected no node this sweep
                     b.T = (b.selected == 0 || !(b.R < Rprev)) ? 0.5 * b.T : ctl->beta * b.R / (double)n;
@@ -363,20 +380,25 @@ __global__ void k_bfinalize(int n, BatchQ *__restrict__ bq, BatchCtl *__restrict
     if (threadIdx.x == 0) {
         ctl->body_runs += 1;
         ctl->sweeps += 1;
-        if (s_open == 0 || ctl->sweeps >= ctl->max_sweeps) {
-            ctl->all_done = s_open == 0 ? 1 : 2;
-            if (in_graph) cudaGraphSetConditional(handle, 0);
-        }
+        ctl->round_sweeps += 1;
+        if (s_newly) ctl->newly = 1;
+        if (s_open == 0)
+            ctl->all_done = 1;
+        else if (ctl->sweeps >= ctl->max_sweeps)
+            ctl->all_done = 2;
+        const bool stop = ctl->all_done != 0 || ctl->round_sweeps >= ctl->round_cap ||
+                          (ctl->stop_on_done && s_newly != 0);
+        if (stop && in_graph) cudaGraphSetConditional(handle, 0);
     }
 }
 
 // exact per-query |F_q|_1 in FP64 (a lane per query column, rows strided over the grid)
-__global__ void k_bl1_exact(long long rows, int K, const float *__restrict__ Fb, BatchQ *__restrict__ bq) {
+__global__ void k_bl1_exact(long long rows, int K, int S, const float *__restrict__ Fb, BatchQ *__restrict__ bq) {
     const int q = threadIdx.x % K;
     const int rstep = (gridDim.x * blockDim.x) / K;
     double a = 0.0;
     for (long long r = (long long)(blockIdx.x * blockDim.x + threadIdx.x) / K; r < rows; r += rstep)
-        a += fabs((double)Fb[r * K + q]);
+        a += fabs((double)Fb[r * S + q]);
     atomicAdd(&bq[q].l1_exact, a);
 }
 
@@ -410,19 +432,142 @@ __global__ void k_bgather(int n, int k, int K, const int *__restrict__ new_of, c
     }
 }
 
-template <int LPN>
-void capture_batch_body(di_graph *g, cudaGraphConditionalHandle handle) {
-    const int nhot = std::min(g->n_hot, kBatchHot);
-    k_bscan<LPN><<<g->G, kScanThreads, 0, g->cap>>>(g->chunk / kWarps, g->Fb, g->cls, g->region, g->W, g->fcount,
-                                                    g->pre, g->ticket, g->selb_node, g->selb_rows, g->bq, g->bctl,
-                                                    g->d);
-    k_bpush<LPN><<<g->G, kScanThreads, 0, g->cap>>>(g->rec32, g->col_idx, g->Fb, g->Hb, g->region, g->pre, g->W,
-                                                    g->selb_node, g->selb_rows, nhot, g->bctl);
-    k_bfinalize<<<1, kLanes, 0, g->cap>>>(g->n, g->bq, g->bctl, handle, 1);
+// ---------------------------------------------------------------- serving rounds
+//
+// A serving loop keeps each lane busy with a stream of queries: between two launches
+// of the captured loop, stopped lanes are copied out and cleared, and new queries
+// start in the freed lanes while the others carry on where they were.
+
+// frees and starts lanes, then opens the round
+__global__ void k_bround_begin(LaneAdmin a, int n, double omd, double beta, int round_cap, int lane_max,
+                               BatchQ *__restrict__ bq, BatchCtl *__restrict__ ctl) {
+    __shared__ int s_open;
+    if (threadIdx.x == 0) s_open = 0;
+    __syncthreads();
+    const int q = threadIdx.x;
+    if (q < kLanes) {
+        BatchQ b = bq[q];
+        const unsigned long long bit = 1ull << q;
+        if ((a.retire | a.admit) & bit) {
+            b.R = 0.0;
+            b.T = INFINITY;
+            b.tolR = 0.0;
+            b.l1_acc = 0.0;
+            b.rem_acc = 0.0;
+            b.l1_exact = 0.0;
+            b.active = 0;
+            b.done = 1;
+            b.selected = 0;
+            b.sweeps = 0;
+            b.confirmed = 0;
+        }
+        if (a.admit & bit) {  // F_q = (1-d) V_q was added by the seeding kernel: R_q = 1-d
+            b.active = 1;
+            b.R = omd;
+            b.tolR = a.tolR[q];
+            b.done = omd <= b.tolR ? 1 : 0;
+            b.T = b.done ? INFINITY : beta * omd / (double)n;
+        }
+        if (b.active && !b.done) atomicAdd(&s_open, 1);
+        bq[q] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctl->round_sweeps = 0;
+        ctl->round_cap = round_cap;
+        ctl->stop_on_done = 1;
+        ctl->lane_max_sweeps = lane_max;
+        ctl->max_sweeps = INT_MAX;
+        ctl->beta = beta;
+        ctl->newly = 0;
+        ctl->all_done = s_open ? 0 : 1;
+    }
 }
 
-// widths 8, 16, 32, 64 queries use slots 0..3
-di_status build_batch_graph(di_graph *g, int slot) {
+// exact FP64 |F_q|_1 of the lanes that stopped and are not confirmed yet; each thread
+// keeps one lane and strides over the rows
+__global__ void k_bl1_pending(long long rows, int K, const float *__restrict__ Fb, BatchQ *__restrict__ bq) {
+    __shared__ int s_lane[kLanes];
+    __shared__ double s_acc[kLanes];
+    __shared__ int s_P;
+    if (threadIdx.x == 0) {
+        int P = 0;
+        for (int q = 0; q < K; ++q)
+            if (bq[q].active && bq[q].done && !bq[q].confirmed) s_lane[P++] = q;
+        s_P = P;
+    }
+    if (threadIdx.x < kLanes) s_acc[threadIdx.x] = 0.0;
+    __syncthreads();
+    const int P = s_P;
+    if (P == 0) return;
+    const long long total = (long long)gridDim.x * blockDim.x;
+    const long long Tp = (total / P) * P;
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid < Tp) {
+        const int li = (int)(gid % P), q = s_lane[li];
+        const long long rstep = Tp / P;
+        double acc = 0.0;
+        for (long long r = gid / P; r < rows; r += rstep) acc += fabs((double)Fb[r * K + q]);
+        atomicAdd(&s_acc[li], acc);
+    }
+    __syncthreads();
+    if (threadIdx.x < P) atomicAdd(&bq[s_lane[threadIdx.x]].l1_exact, s_acc[threadIdx.x]);
+}
+
+// a stop the exact norm does not confirm re-opens that lane; a lane at its sweep limit is
+// confirmed as it stands (its bound is the exact norm)
+__global__ void k_bconfirm_pending(int n, double beta, BatchQ *__restrict__ bq) {
+    const int q = threadIdx.x;
+    if (q >= kLanes) return;
+    BatchQ b = bq[q];
+    if (!(b.active && b.done && !b.confirmed)) return;
+    b.R = b.l1_exact;
+    if (b.done == 2 || b.l1_exact <= b.tolR) {
+        b.confirmed = 1;
+    } else {
+        b.done = 0;
+        b.T = beta * b.l1_exact / (double)n;
+    }
+    bq[q] = b;
+}
+
+// out_l[perm[r]] = Hb[r][lane_l]; the lane's history and fluid columns are cleared
+__global__ void k_blane_retire(LaneRetire rl, int n, int K, const int *__restrict__ perm, double *__restrict__ Hb,
+                               float *__restrict__ Fb) {
+    const int cnt = rl.count;
+    const long long total = (long long)n * cnt;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long r = t / cnt;
+        const int li = (int)(t - r * cnt), q = rl.lane[li];
+        const long long at = r * K + q;
+        const double v = Hb[at];
+        Hb[at] = 0.0;
+        Fb[at] = 0.f;
+        if (rl.out[li]) rl.out[li][perm[r]] = v;
+    }
+}
+
+template <int LPN>
+void capture_batch_body(di_graph *g, BatchPool *p, cudaGraphConditionalHandle handle, int S) {
+    const int nhot = std::min(g->n_hot, kBatchHot);
+    k_bscan<LPN><<<g->G, kScanThreads, 0, g->cap>>>(g->chunk / kWarps, S, p->Fb, g->cls, g->region, g->W, p->fcount,
+                                                    p->pre, p->ticket, p->selb_node, p->selb_rows, p->bq, p->bctl,
+                                                    g->d);
+    k_bpush<LPN><<<push_grid(g), kScanThreads, 0, g->cap>>>(g->rec32, g->col_idx, p->Fb, p->Hb, S, g->region, p->pre, g->W,
+                                                    p->selb_node, p->selb_rows, nhot, p->bctl);
+    k_bfinalize<<<1, kLanes, 0, g->cap>>>(g->n, p->bq, p->bctl, handle, 1);
+}
+
+int batch_grid(const di_graph *g, long long work) {
+    return (int)std::max(1LL, std::min((work + 255) / 256, (long long)g->num_sms * 8));
+}
+
+}  // namespace
+
+// widths 8, 16, 32, 64 lanes use slots 0..3
+di_status pool_build_loop(di_graph *g, BatchPool *p, int slot) {
+    if (p->exec[slot]) return DI_OK;
     cudaGraph_t graph = nullptr;
     DI_CUDA(cudaGraphCreate(&graph, 0));
     cudaGraphConditionalHandle handle;
@@ -439,11 +584,12 @@ di_status build_batch_graph(di_graph *g, int slot) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     e = cudaStreamBeginCaptureToGraph(g->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(e, "cudaStreamBeginCaptureToGraph"); }
+    const int S = p->stride ? p->stride : 8 << slot;
     switch (slot) {
-        case 0: capture_batch_body<2>(g, handle); break;
-        case 1: capture_batch_body<4>(g, handle); break;
-        case 2: capture_batch_body<8>(g, handle); break;
-        default: capture_batch_body<16>(g, handle); break;
+        case 0: capture_batch_body<2>(g, p, handle, S); break;
+        case 1: capture_batch_body<4>(g, p, handle, S); break;
+        case 2: capture_batch_body<8>(g, p, handle, S); break;
+        default: capture_batch_body<16>(g, p, handle, S); break;
     }
     cudaGraph_t captured = nullptr;
     e = cudaStreamEndCapture(g->cap, &captured);
@@ -451,43 +597,106 @@ di_status build_batch_graph(di_graph *g, int slot) {
     cudaGraphExec_t exec = nullptr;
     e = cudaGraphInstantiate(&exec, graph, 0);
     if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(e, "cudaGraphInstantiate(batch)"); }
-    g->bgraph[slot] = graph;
-    g->bexec[slot] = exec;
+    p->graph[slot] = graph;
+    p->exec[slot] = exec;
     return DI_OK;
 }
 
-di_status batch_alloc(di_graph *g) {
-    if (g->Fb) return DI_OK;
-    cudaStream_t s = g->stream;
+long long pool_bytes(const di_graph *g, int lanes) {
+    const long long rows = (long long)g->G * g->chunk, n = g->n;
+    return lanes * (4 * rows + 12 * n) + 4 * n + (long long)sizeof(int) * kLists * (2 * g->W + 1) +
+           (long long)(sizeof(BatchQ) * kLanes + sizeof(BatchCtl)) + 256;
+}
+
+di_status pool_alloc(di_graph *g, BatchPool *p, int lanes, cudaStream_t s) {
+    if (p->Fb) return DI_OK;
     const long long rows = (long long)g->G * g->chunk;
-    DI_CUDA(cudaMallocAsync(&g->Fb, sizeof(float) * kLanes * (size_t)rows, s));
-    DI_CUDA(cudaMallocAsync(&g->Hb, sizeof(double) * kLanes * (size_t)g->n, s));
-    DI_CUDA(cudaMallocAsync(&g->selb_rows, sizeof(float) * kLanes * (size_t)g->n, s));
-    DI_CUDA(cudaMallocAsync(&g->selb_node, sizeof(int) * (size_t)g->n, s));
-    DI_CUDA(cudaMallocAsync(&g->bq, sizeof(BatchQ) * kLanes, s));
-    DI_CUDA(cudaMallocAsync(&g->bctl, sizeof(BatchCtl), s));
-    DI_CUDA(cudaMallocHost(&g->h_bq, sizeof(BatchQ) * kLanes));
-    DI_CUDA(cudaMallocHost(&g->h_bctl, sizeof(BatchCtl)));
+    p->rows = rows;
+    p->cap_lanes = lanes;
+    DI_CUDA(cudaMallocAsync(&p->Fb, sizeof(float) * lanes * (size_t)rows, s));
+    DI_CUDA(cudaMallocAsync(&p->Hb, sizeof(double) * lanes * (size_t)g->n, s));
+    DI_CUDA(cudaMallocAsync(&p->selb_rows, sizeof(float) * lanes * (size_t)g->n, s));
+    DI_CUDA(cudaMallocAsync(&p->selb_node, sizeof(int) * (size_t)g->n, s));
+    DI_CUDA(cudaMallocAsync(&p->fcount, sizeof(int) * kLists * (size_t)g->W, s));
+    DI_CUDA(cudaMallocAsync(&p->pre, sizeof(int) * kLists * (size_t)(g->W + 1), s));
+    DI_CUDA(cudaMallocAsync(&p->ticket, sizeof(unsigned), s));
+    DI_CUDA(cudaMallocAsync(&p->bq, sizeof(BatchQ) * kLanes, s));
+    DI_CUDA(cudaMallocAsync(&p->bctl, sizeof(BatchCtl), s));
+    DI_CUDA(cudaMemsetAsync(p->ticket, 0, sizeof(unsigned), s));
+    DI_CUDA(cudaMallocHost(&p->h_bq, sizeof(BatchQ) * kLanes));
+    DI_CUDA(cudaMallocHost(&p->h_bctl, sizeof(BatchCtl)));
     return DI_OK;
 }
 
-}  // namespace
+void pool_free(BatchPool *p, cudaStream_t s) {
+    if (!p) return;
+    for (int k = 0; k < 4; ++k) {
+        if (p->exec[k]) cudaGraphExecDestroy(p->exec[k]);
+        if (p->graph[k]) cudaGraphDestroy(p->graph[k]);
+    }
+    void *bufs[] = {p->Fb, p->Hb, p->selb_rows, p->selb_node, p->fcount, p->pre, p->ticket, p->bq, p->bctl};
+    for (void *b : bufs)
+        if (b) cudaFreeAsync(b, s);
+    cudaStreamSynchronize(s);
+    if (p->h_bq) cudaFreeHost(p->h_bq);
+    if (p->h_bctl) cudaFreeHost(p->h_bctl);
+    cudaGetLastError();
+    delete p;
+}
+
+// zero fluid and histories; every lane idle
+di_status pool_reset(di_graph *g, BatchPool *p, int K, double beta, cudaStream_t s) {
+    k_binit<<<batch_grid(g, p->rows * K), 256, 0, s>>>(p->rows, g->n, K, p->Fb, p->Hb);
+    k_bctl_init<<<1, kLanes, 0, s>>>(0, p->bq, p->bctl, 1.0, 1.0 - g->d, beta, g->n, INT_MAX);
+    DI_CUDA(cudaGetLastError());
+    return DI_OK;
+}
+
+di_status pool_seed(di_graph *g, BatchPool *p, int K, int nitems, const int *q_dev, const int *seeds_dev,
+                    const double *val_dev, cudaStream_t s) {
+    if (nitems <= 0) return DI_OK;
+    k_bseeds<<<std::max(1, std::min(1024, (nitems + 255) / 256)), 256, 0, s>>>(nitems, K, q_dev, seeds_dev, val_dev,
+                                                                           g->new_of, p->Fb);
+    DI_CUDA(cudaGetLastError());
+    return DI_OK;
+}
+
+di_status pool_retire(di_graph *g, BatchPool *p, int K, const LaneRetire &r, cudaStream_t s) {
+    if (r.count <= 0) return DI_OK;
+    k_blane_retire<<<batch_grid(g, (long long)g->n * r.count), 256, 0, s>>>(r, g->n, K, g->perm, p->Hb, p->Fb);
+    DI_CUDA(cudaGetLastError());
+    return DI_OK;
+}
+
+di_status pool_launch_round(di_graph *g, BatchPool *p, int slot, const LaneAdmin &a, int round_cap, int lane_max,
+                            double beta, cudaStream_t s) {
+    const int S = p->stride ? p->stride : 8 << slot;
+    k_bround_begin<<<1, kLanes, 0, s>>>(a, g->n, 1.0 - g->d, beta, round_cap, lane_max, p->bq, p->bctl);
+    DI_CUDA(cudaGetLastError());
+    DI_CUDA(cudaGraphLaunch(p->exec[slot], s));
+    k_bl1_pending<<<batch_grid(g, p->rows * (8 << slot)), 256, 0, s>>>(p->rows, S, p->Fb, p->bq);
+    k_bconfirm_pending<<<1, kLanes, 0, s>>>(g->n, beta, p->bq);
+    DI_CUDA(cudaGetLastError());
+    DI_CUDA(cudaMemcpyAsync(p->h_bq, p->bq, sizeof(BatchQ) * kLanes, cudaMemcpyDeviceToHost, s));
+    DI_CUDA(cudaMemcpyAsync(p->h_bctl, p->bctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
+    return DI_OK;
+}
 
 di_status run_query_batch(di_graph *g, int k, const int *seed_ptr, const int *seeds, const double *w, double tol,
                           double beta, int max_sweeps, double *H_out, bool out_dev, di_stats *st_q, di_stats *st_all) {
     cudaStream_t s = g->stream;
-    di_status r = batch_alloc(g);
+    if (!g->bp) g->bp = new BatchPool();
+    BatchPool *p = g->bp;
+    di_status r = pool_alloc(g, p, kLanes, s);
     if (r != DI_OK) return r;
     // the narrowest row that holds the batch: 8, 16, 32 or 64 queries
-    const int slot = k <= 8 ? 0 : (k <= 16 ? 1 : (k <= 32 ? 2 : 3));
+    const int slot = lane_slot(k);
     const int K = 8 << slot;
-    if (!g->bexec[slot]) {
-        r = build_batch_graph(g, slot);
-        if (r != DI_OK) return r;
-    }
+    r = pool_build_loop(g, p, slot);
+    if (r != DI_OK) return r;
     const int n = g->n;
     const double omd = 1.0 - g->d;
-    const long long rows = (long long)g->G * g->chunk;
+    const long long rows = p->rows;
     // seed items (query, seed, (1-d) w / sum w) prepared on the host
     const int nitems = seed_ptr[k];
     std::vector<int> q_of(nitems);
@@ -509,23 +718,23 @@ di_status run_query_batch(di_graph *g, int k, const int *seed_ptr, const int *se
     DI_CUDA(cudaMemcpyAsync(d_seeds, seeds, sizeof(int) * nitems, cudaMemcpyHostToDevice, s));
     DI_CUDA(cudaMemcpyAsync(d_val, val.data(), sizeof(double) * nitems, cudaMemcpyHostToDevice, s));
     DI_CUDA(cudaEventRecord(g->ev0, s));
-    const int grid = (int)std::max(1LL, std::min((rows * K + 255) / 256, (long long)g->num_sms * 8));
-    k_binit<<<grid, 256, 0, s>>>(rows, n, K, g->Fb, g->Hb);
+    const int grid = batch_grid(g, rows * K);
+    k_binit<<<grid, 256, 0, s>>>(rows, n, K, p->Fb, p->Hb);
     k_bseeds<<<std::max(1, std::min(1024, (nitems + 255) / 256)), 256, 0, s>>>(nitems, K, d_q, d_seeds, d_val,
-                                                                           g->new_of, g->Fb);
-    k_bctl_init<<<1, kLanes, 0, s>>>(k, g->bq, g->bctl, tol, omd, beta, n, max_sweeps);
+                                                                           g->new_of, p->Fb);
+    k_bctl_init<<<1, kLanes, 0, s>>>(k, p->bq, p->bctl, tol, omd, beta, n, max_sweeps);
     DI_CUDA(cudaGetLastError());
     int attempts = 0;
     for (int attempt = 0; attempt < 8; ++attempt) {
         ++attempts;
-        DI_CUDA(cudaGraphLaunch(g->bexec[slot], s));
-        k_bzero_exact<<<1, kLanes, 0, s>>>(g->bq);
-        k_bl1_exact<<<grid, 256, 0, s>>>(rows, K, g->Fb, g->bq);
-        k_bconfirm<<<1, kLanes, 0, s>>>(n, g->bq, g->bctl);
+        DI_CUDA(cudaGraphLaunch(p->exec[slot], s));
+        k_bzero_exact<<<1, kLanes, 0, s>>>(p->bq);
+        k_bl1_exact<<<grid, 256, 0, s>>>(rows, K, K, p->Fb, p->bq);
+        k_bconfirm<<<1, kLanes, 0, s>>>(n, p->bq, p->bctl);
         DI_CUDA(cudaGetLastError());
-        DI_CUDA(cudaMemcpyAsync(g->h_bctl, g->bctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
+        DI_CUDA(cudaMemcpyAsync(p->h_bctl, p->bctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
         DI_CUDA(cudaStreamSynchronize(s));
-        if (g->h_bctl->all_done != 0) break;
+        if (p->h_bctl->all_done != 0) break;
     }
     DI_CUDA(cudaEventRecord(g->ev1, s));
     if (H_out) {
@@ -534,25 +743,25 @@ di_status run_query_batch(di_graph *g, int k, const int *seed_ptr, const int *se
             DI_CUDA(cudaMallocAsync(&tmp, sizeof(double) * (size_t)n * k, s));
             dst = tmp;
         }
-        k_bgather<<<grid, 256, 0, s>>>(n, k, K, g->new_of, g->Hb, dst);
+        k_bgather<<<grid, 256, 0, s>>>(n, k, K, g->new_of, p->Hb, dst);
         DI_CUDA(cudaGetLastError());
         if (tmp) {
             DI_CUDA(cudaMemcpyAsync(H_out, tmp, sizeof(double) * (size_t)n * k, cudaMemcpyDeviceToHost, s));
             cudaFreeAsync(tmp, s);
         }
     }
-    DI_CUDA(cudaMemcpyAsync(g->h_bq, g->bq, sizeof(BatchQ) * kLanes, cudaMemcpyDeviceToHost, s));
+    DI_CUDA(cudaMemcpyAsync(p->h_bq, p->bq, sizeof(BatchQ) * kLanes, cudaMemcpyDeviceToHost, s));
     DI_CUDA(cudaStreamSynchronize(s));
     cudaFreeAsync(d_q, s);
     cudaFreeAsync(d_seeds, s);
     cudaFreeAsync(d_val, s);
     float ms = 0.f;
     DI_CUDA(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
-    const BatchCtl &c = *g->h_bctl;
+    const BatchCtl &c = *p->h_bctl;
     bool all_conv = true;
     for (int q = 0; q < k; ++q) {
-        const BatchQ &b = g->h_bq[q];
-        const bool conv = b.done && b.l1_exact <= b.tolR;
+        const BatchQ &b = p->h_bq[q];
+        const bool conv = b.done == 1 && b.l1_exact <= b.tolR;
         all_conv &= conv;
         if (st_q) {
             st_q[q].bound = b.l1_exact / omd;
@@ -568,7 +777,7 @@ di_status run_query_batch(di_graph *g, int k, const int *seed_ptr, const int *se
     }
     if (st_all) {
         double worst = 0.0;
-        for (int q = 0; q < k; ++q) worst = std::max(worst, g->h_bq[q].l1_exact / omd);
+        for (int q = 0; q < k; ++q) worst = std::max(worst, p->h_bq[q].l1_exact / omd);
         st_all->bound = worst;
         st_all->l1_F = worst * omd;
         st_all->R = 0.0;

@@ -97,7 +97,7 @@ struct SolveState {
 constexpr int kLanes = 64;              // queries per batch (the width of a fluid row)
 constexpr int kBatchHot = 32;           // hot targets whose rows the batched push sums in shared memory
 
-struct BatchQ {            // per query
+struct BatchQ {            // per query lane
     double R;              // residual after the last sweep
     double T;              // threshold of the next sweep (+inf once the query has stopped)
     double tolR;           // stop when R <= tolR
@@ -105,9 +105,11 @@ struct BatchQ {            // per query
     double rem_acc;        // mass removed by the current sweep
     double l1_exact;       // FP64 |F_q|_1 of the confirmation
     int active;            // a query occupies this lane
-    int done;              // stopped
+    int done;              // 0 running, 1 stopped on its bound, 2 stopped at its sweep limit
     int selected;          // lanes of this query above its threshold in the current sweep
-    int pad;
+    int sweeps;            // sweeps this query has taken part in
+    int confirmed;         // the stop was checked against the exact FP64 |F_q|_1
+    int pad[3];
 };
 
 struct BatchCtl {
@@ -116,8 +118,28 @@ struct BatchCtl {
     double beta;
     int sweeps;
     int max_sweeps;
-    int all_done;          // 1 every query stopped, 2 a limit hit
+    int all_done;          // 1 no lane open, 2 the loop's sweep limit hit
     int body_runs;
+    int round_sweeps;      // sweeps of the current launch of the loop
+    int round_cap;         // the loop returns after this many sweeps
+    int stop_on_done;      // the loop also returns when a lane stops
+    int lane_max_sweeps;   // a lane stops (done = 2) after this many sweeps
+    int newly;             // a lane stopped in the current launch
+    int pad;
+};
+
+// lanes to free and lanes to start, applied by the kernel that opens a round of the serving loop
+struct LaneAdmin {
+    unsigned long long retire;
+    unsigned long long admit;
+    double tolR[kLanes];
+};
+
+// lanes whose histories are copied out (and whose columns are cleared) in one launch
+struct LaneRetire {
+    int count;
+    int lane[kLanes];
+    double *out[kLanes];   // n doubles each, input numbering; NULL: clear only
 };
 
 struct PowerState {
@@ -133,6 +155,26 @@ struct PowerState {
 struct PowerPartial {
     double delta;
     double pad;
+};
+
+// interleaved query lanes with their own sweep scratch: the buffers of di_query_batch,
+// and of each graph a serving loop holds
+struct BatchPool {
+    int cap_lanes = 0;                 // lanes per row the buffers hold
+    int stride = 0;                    // floats between rows: 0 = the loop's width (a fresh batch packs its rows);
+                                       // a serving pool keeps cap_lanes and runs narrower loops on the low lanes
+    long long rows = 0;                // fluid rows (n padded to the scan layout)
+    float *Fb = nullptr;               // [rows][K] interleaved fluid, FP32
+    double *Hb = nullptr;              // [n][K] histories, FP64
+    float *selb_rows = nullptr;        // [n][K] rows of the selected nodes of a sweep
+    int *selb_node = nullptr;          // [n]
+    int *fcount = nullptr, *pre = nullptr;
+    unsigned *ticket = nullptr;
+    BatchQ *bq = nullptr, *h_bq = nullptr;
+    BatchCtl *bctl = nullptr, *h_bctl = nullptr;
+    // captured loops for rows of 8, 16, 32, 64 lanes
+    cudaGraph_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaGraphExec_t exec[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 }  // namespace diter
@@ -197,19 +239,11 @@ struct di_graph {
     double pprof_ms[2] = {0.0, 0.0};   // profiled power iteration: pull, finalize
 
     // batched queries (allocated at the first batch)
-    float *Fb = nullptr;               // [rows][kLanes] interleaved fluid, FP32
-    double *Hb = nullptr;              // [n][kLanes] histories, FP64
-    float *selb_rows = nullptr;        // [n][kLanes] rows of the selected nodes of a sweep
-    int *selb_node = nullptr;          // [n]
-    diter::BatchQ *bq = nullptr, *h_bq = nullptr;
-    diter::BatchCtl *bctl = nullptr, *h_bctl = nullptr;
+    diter::BatchPool *bp = nullptr;
 
     // captured solve loops: [0] FP64 sweeps, [1] FP32-mixed sweeps, [2] power iteration
     cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
     cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
-    // batch loops for rows of 8, 16, 32, 64 queries
-    cudaGraph_t bgraph[4] = {nullptr, nullptr, nullptr, nullptr};
-    cudaGraphExec_t bexec[4] = {nullptr, nullptr, nullptr, nullptr};
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     diter::SolveState *h_st = nullptr; // pinned host mirror
@@ -242,9 +276,27 @@ int scan_blocks_per_sm();
 // batched queries (batch.cu)
 di_status run_query_batch(di_graph *g, int k, const int *seed_ptr, const int *seeds, const double *w, double tol,
                           double beta, int max_sweeps, double *H_out, bool out_dev, di_stats *st_q, di_stats *st_all);
+di_status pool_alloc(di_graph *g, BatchPool *p, int lanes, cudaStream_t s);
+void pool_free(BatchPool *p, cudaStream_t s);
+long long pool_bytes(const di_graph *g, int lanes);
+di_status pool_build_loop(di_graph *g, BatchPool *p, int slot);
+inline int lane_slot(int k) { return k <= 8 ? 0 : (k <= 16 ? 1 : (k <= 32 ? 2 : 3)); }
+// one round of the serving loop on stream s: free and start lanes, diffuse, confirm stops, copy the lane states back
+di_status pool_launch_round(di_graph *g, BatchPool *p, int slot, const LaneAdmin &a, int round_cap, int lane_max,
+                            double beta, cudaStream_t s);
+di_status pool_seed(di_graph *g, BatchPool *p, int K, int nitems, const int *q_dev, const int *seeds_dev,
+                    const double *val_dev, cudaStream_t s);
+di_status pool_retire(di_graph *g, BatchPool *p, int K, const LaneRetire &r, cudaStream_t s);
+di_status pool_reset(di_graph *g, BatchPool *p, int K, double beta, cudaStream_t s);
+
+// pointer kinds (api.cu): device or host-mapped memory a kernel can write, else pageable host memory
+bool is_device_ptr(const void *p);
+void *kernel_ptr(void *p);
 
 // helpers
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+// push CTAs: the pushes scale with edges, not nodes, so small graphs still get 4 CTAs per SM
+inline int push_grid(const di_graph *g) { return g->G > 4 * g->num_sms ? g->G : 4 * g->num_sms; }
 
 }  // namespace diter
 

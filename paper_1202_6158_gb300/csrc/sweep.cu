@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_push(const RowRec<FT> *_
                                                              double *__restrict__ H, const int *__restrict__ region,
                                                              const int *__restrict__ pre, int W,
                                                              const Sel<FT> *__restrict__ sel, int n_hot,
-                                                             ScanPartial *__restrict__ part,
+                                                             ScanPartial *__restrict__ part, int G,
                                                              const SolveState *__restrict__ st) {
     __shared__ FT hot[kHotSlots];
     __shared__ long long s_red[kWarps];
@@ -472,7 +472,9 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_push(const RowRec<FT> *_
         if (v != (FT)0) red_add(F + t, v);
     }
     const long long be = block_sum(edges, s_red);
-    if (threadIdx.x == 0) part[blockIdx.x].edges = be;
+    // the scan zeroed the G partials' edge counts; the push grid may be wider than G
+    if (threadIdx.x == 0 && be)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&part[blockIdx.x % G].edges), (unsigned long long)be);
 }
 
 // --------------------------------------------------------------- finalize
@@ -620,8 +622,8 @@ void launch_scan(di_graph *g, FT *F, cudaStream_t s) {
 
 template <typename FT>
 void launch_push(di_graph *g, FT *F, cudaStream_t s) {
-    k_sweep_push<FT><<<g->G, kScanThreads, 0, s>>>(rec_of<FT>(g), g->col_idx, F, g->H, g->region,
-                                                   g->pre, g->W, sel_of<FT>(g), g->n_hot, g->part, g->st);
+    k_sweep_push<FT><<<push_grid(g), kScanThreads, 0, s>>>(rec_of<FT>(g), g->col_idx, F, g->H, g->region, g->pre,
+                                                           g->W, sel_of<FT>(g), g->n_hot, g->part, g->G, g->st);
 }
 
 int elem_grid(di_graph *g, long long work) {
