@@ -11,6 +11,10 @@ Contents (each function cites the passage it follows):
   3.3) in the orders of Section 4 (PER, RAND, MAX) and threshold sweeps
   (sequential THRESH and snapshot SWEEP), in C (``oracle.c``).
 * :func:`power`        -- MAT-ITER on the uncompleted P with the paper's stop rule.
+* :func:`update`       -- the injection F_0' = F_n0 + d(P'-P)H_n0 of the updating
+  equation (Section 3.2); :func:`run` then continues on P' (signed fluid).
+* :func:`selection_weights` -- the ALGO-OP / ALGO-OP2 weights of Section 4.3,
+  used by ``select="op"`` / ``"op2"`` in :func:`run` and :func:`diter`.
 * :func:`transpose`, :func:`bins` -- in-link lists and degree bins.
 * :mod:`oracle.ge`     -- dense Gaussian elimination of (I - dP)X = (1-d)V in FP64
   and in exact rationals (Section 2.1's fixed point written out).
@@ -71,7 +75,8 @@ def _bind(lib):
     lib.orc_init.restype = ctypes.c_double
     lib.orc_diter.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_double, f64p, f64p, ctypes.c_double,
                               ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_int64,
-                              ctypes.POINTER(Stats)]
+                              ctypes.POINTER(ctypes.c_float), ctypes.c_double, ctypes.POINTER(Stats)]
+    lib.orc_update_inject.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, ctypes.c_double, f64p, f64p]
     lib.orc_diter.restype = ctypes.c_int
     lib.orc_power.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_double, f64p, ctypes.c_double,
                               ctypes.c_int64, f64p, i64p, f64p]
@@ -126,23 +131,77 @@ def init(n, d, V, lib=None):
     return F, H, R
 
 
-def run(n, row_ptr, col_idx, d, F, H, R, tol, mode="sweep", beta=0.5, seed=0, max_pushes=1 << 62, lib=None):
-    """Continue D-iteration on the state (F, H, R) in place (ALGO-REF, Sections 2.2 and 3.3)."""
+def selection_weights(n, row_ptr, col_idx, select):
+    """ALGO-OP / ALGO-OP2 selection weights (Section 4.3) and the threshold scale.
+
+    "op":  w_i = 1/((#in_i + 1)(#out_i + 1));  "op2": w_i = 1/(#out_i + 1).
+    Each weight is the FP64 quotient of 1 by the integer product, rounded to FP32.
+    wscale = 2^floor(log2(mean_i w_i)), the mean taken over the FP32 weights in FP64.
+    """
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    outdeg = np.diff(row_ptr)
+    if select == "op":
+        indeg = np.bincount(np.asarray(col_idx, dtype=np.int64), minlength=n)[:n]
+        c = (indeg + 1) * (outdeg + 1)
+    elif select == "op2":
+        c = outdeg + 1
+    else:
+        raise ValueError(f"unknown selection {select}")
+    w = (1.0 / c.astype(np.float64)).astype(np.float32)
+    mean = float(np.sum(w.astype(np.float64))) / n
+    _m, ex = np.frexp(mean)
+    return np.ascontiguousarray(w), float(np.ldexp(1.0, int(ex) - 1))
+
+
+def run(n, row_ptr, col_idx, d, F, H, R, tol, mode="sweep", beta=0.5, seed=0, max_pushes=1 << 62, lib=None,
+        select=None):
+    """Continue D-iteration on the state (F, H, R) in place (ALGO-REF, Sections 2.2 and 3.3).
+
+    select = "op" / "op2" chooses nodes by |F_i| w_i (Section 4.3) in the MAX and sweep orders.
+    """
     lib = lib or load()
     rp, rpp = _i32(row_ptr)
     ci, cip = _i32(col_idx if len(col_idx) else np.zeros(1, np.int32))
     st = Stats()
     m = MODES[mode] if isinstance(mode, str) else int(mode)
-    rc = lib.orc_diter(n, rpp, cip, d, _f64(F), _f64(H), R, tol, m, beta, seed, max_pushes, ctypes.byref(st))
+    wp, wscale = None, 1.0
+    if select is not None and select != "ref":
+        w, wscale = selection_weights(n, rp, ci[:int(rp[n])], select)
+        wp = w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    rc = lib.orc_diter(n, rpp, cip, d, _f64(F), _f64(H), R, tol, m, beta, seed, max_pushes, wp, wscale,
+                       ctypes.byref(st))
     if rc < 0:
         raise ValueError(f"oracle: unknown mode {mode}")
     return DiterResult(H, F, st.R, st.l1F, st.pushes, st.edges, st.picks, st.sweeps, bool(st.converged))
 
 
-def diter(n, row_ptr, col_idx, d, V, tol, mode="sweep", beta=0.5, seed=0, max_pushes=1 << 62, lib=None):
+def diter(n, row_ptr, col_idx, d, V, tol, mode="sweep", beta=0.5, seed=0, max_pushes=1 << 62, lib=None,
+          select=None):
     """D-iteration from the initial state to R/(1-d) <= tol (ALGO-REF, Sections 2.2, 3.3, 4)."""
     F, H, R = init(n, d, V, lib)
-    return run(n, row_ptr, col_idx, d, F, H, R, tol, mode, beta, seed, max_pushes, lib)
+    return run(n, row_ptr, col_idx, d, F, H, R, tol, mode, beta, seed, max_pushes, lib, select)
+
+
+def update(n, rp_old, ci_old, rp_new, ci_new, d, F, H, lib=None):
+    """F_0' = F + d(P' - P)H (Section 3.2, updating equation); returns a new array."""
+    lib = lib or load()
+    _a, pa = _i32(rp_old)
+    _b, pb = _i32(ci_old if len(ci_old) else np.zeros(1, np.int32))
+    _c, pc = _i32(rp_new)
+    _e, pe = _i32(ci_new if len(ci_new) else np.zeros(1, np.int32))
+    F2 = np.array(F, dtype=np.float64, copy=True)
+    Hc = np.ascontiguousarray(H, dtype=np.float64)
+    lib.orc_update_inject(n, pa, pb, pc, pe, d, _f64(Hc), _f64(F2))
+    return F2
+
+
+def solve_update(n, rp_old, ci_old, rp_new, ci_new, d, F, H, tol, mode="sweep", beta=0.5, max_pushes=1 << 62,
+                 lib=None):
+    """Continue a run on P (state F, H) on the updated graph P' to |F'|_1/(1-d) <= tol (Section 3.2)."""
+    F2 = update(n, rp_old, ci_old, rp_new, ci_new, d, F, H, lib)
+    H2 = np.array(H, dtype=np.float64, copy=True)
+    R = float(np.abs(F2).sum())
+    return run(n, rp_new, ci_new, d, F2, H2, R, tol, mode, beta, max_pushes=max_pushes, lib=lib)
 
 
 def power(n, row_ptr, col_idx, d, V, tol, max_iter=100000, lib=None):

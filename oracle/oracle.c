@@ -107,9 +107,13 @@ double orc_init(i32 n, double d, const double *V, double *F, double *H) {
  * One diffusion of node i (the loop body of ALGO-REF with the dangling-node
  * condition of Section 3.3):
  *   sent := F[i]; H[i] += sent; F[i] := 0;
- *   no child:  R -= sent
- *   otherwise: F[j] += sent * p(j,i) * d for every child j;  R -= sent*(1-d)
- * p(j,i) = 1/outdeg(i) per listed out-link.
+ *   no child:  R -= |sent|
+ *   otherwise: F[j] += sent * p(j,i) * d for every child j;  R -= |sent|*(1-d)
+ * p(j,i) = 1/outdeg(i) per listed out-link.  The fluid is non-negative except
+ * after a graph update, whose injected fluid d(P'-P)H may hold negative terms
+ * (Section 3.2, "Updating equation"); the diffusion is linear, so signed fluid
+ * moves the same way, and since |F_j + x| <= |F_j| + |x| the decrement by |sent|
+ * keeps R an upper bound on |F|_1.
  */
 static void diffuse(i32 i, const i32 *row_ptr, const i32 *col_idx, double d, double *F, double *H,
                     double *R, orc_stats *st) {
@@ -118,11 +122,11 @@ static void diffuse(i32 i, const i32 *row_ptr, const i32 *col_idx, double d, dou
     F[i] = 0.0;
     i32 beg = row_ptr[i], end = row_ptr[i + 1];
     if (end == beg) {
-        *R -= sent;
+        *R -= fabs(sent);
     } else {
         double p = 1.0 / (double)(end - beg);
         for (i32 e = beg; e < end; ++e) F[col_idx[e]] += sent * p * d;
-        *R -= sent * (1.0 - d);
+        *R -= fabs(sent) * (1.0 - d);
     }
     st->pushes += 1;
     st->edges += end - beg;
@@ -136,16 +140,38 @@ static double l1_norm(i32 n, const double *F) {
 }
 
 /*
+ * Selection weights (Section 4.3, ALGO-OP and ALGO-OP2).  ALGO-OP replaces the
+ * argmax of F by the argmax of F_i / ((#in_i + 1)(#out_i + 1)) and ALGO-OP2 by
+ * the argmax of F_i / (#out_i + 1); wsel[i] holds 1/((#in_i+1)(#out_i+1)) or
+ * 1/(#out_i+1), or wsel is NULL for the plain choice.  The argmax compares
+ * |F_i| * wsel[i] in FP64.  A threshold sweep with weights selects i when
+ * (float)|F_i| * wsel[i] > (float)(T * wscale), the product and the compare
+ * made in FP32 (a selection rule only decides which diffusions happen, and any
+ * choice converges, Section 2.2); wscale is the power of two nearest below the
+ * mean weight, which keeps the weighted threshold on the scale of F * w.
+ */
+static double pick_key(const double *F, const float *wsel, i32 i) {
+    return wsel ? fabs(F[i]) * (double)wsel[i] : fabs(F[i]);
+}
+
+static int above(double f, const float *wsel, i32 i, double T, double wscale) {
+    if (!wsel) return fabs(f) > T;
+    float a = (float)fabs(f) * wsel[i];
+    float t = (float)(T * wscale);
+    return a > t;
+}
+
+/*
  * Run D-iteration on the state (F, H, R) until R/(1-d) <= tol or max_pushes
  * diffusions have been made.  F and H are updated in place, so a second call
  * resumes where the first stopped.  Orders of the sequence I (Section 4):
  *
  *   ORC_PER    i_n = n mod N.
  *   ORC_RAND   i_n uniform on {0..N-1} (SplitMix64 of seed + n).
- *   ORC_MAX    i_n = argmax F (lowest index on ties).
+ *   ORC_MAX    i_n = argmax |F| (lowest index on ties).
  *   ORC_THRESH threshold sweeps: visit i = 0..N-1 and diffuse every i whose
- *              current F_i > T (F_i read at its turn, Gauss-Seidel style).
- *   ORC_SWEEP  threshold sweeps on a snapshot: S = {i : F_i > T} is fixed at
+ *              current |F_i| > T (F_i read at its turn, Gauss-Seidel style).
+ *   ORC_SWEEP  threshold sweeps on a snapshot: S = {i : |F_i| > T} is fixed at
  *              the start of the sweep, all of S hands its fluid to H, then all
  *              of S pushes.  This is the diffusion of the set S at once,
  *              F' = (I - J_S + dPJ_S)F, H' = H + J_S F with J_S = sum_{i in S} J_i,
@@ -172,7 +198,8 @@ static double l1_norm(i32 n, const double *F) {
  * Returns 0 if converged, 1 if max_pushes was reached first.
  */
 int orc_diter(i32 n, const i32 *row_ptr, const i32 *col_idx, double d, double *F, double *H, double R,
-              double tol, int mode, double beta, u64 seed, i64 max_pushes, orc_stats *st) {
+              double tol, int mode, double beta, u64 seed, i64 max_pushes, const float *wsel, double wscale,
+              orc_stats *st) {
     memset(st, 0, sizeof(*st));
     if (mode < ORC_PER || mode > ORC_SWEEP) return -1;
     const int sweeping = (mode == ORC_THRESH || mode == ORC_SWEEP);
@@ -204,7 +231,7 @@ int orc_diter(i32 n, const i32 *row_ptr, const i32 *col_idx, double d, double *F
             i32 i;
             if (mode == ORC_MAX) {
                 i = 0;
-                for (i32 k = 1; k < n; ++k) if (F[k] > F[i]) i = k;
+                for (i32 k = 1; k < n; ++k) if (pick_key(F, wsel, k) > pick_key(F, wsel, i)) i = k;
             } else {
                 i = (mode == ORC_PER) ? (i32)(st->picks % n) : (i32)(orc_splitmix(seed + (u64)st->picks) % (u64)n);
             }
@@ -220,7 +247,7 @@ int orc_diter(i32 n, const i32 *row_ptr, const i32 *col_idx, double d, double *F
         } else if (mode == ORC_THRESH) {
             i64 before = st->pushes;
             for (i32 i = 0; i < n; ++i) {
-                if (F[i] > T) {
+                if (above(F[i], wsel, i, T, wscale)) {
                     st->picks += 1;
                     diffuse(i, row_ptr, col_idx, d, F, H, &R, st);
                     if (R / (1.0 - d) <= tol || st->pushes >= max_pushes) break;
@@ -231,7 +258,7 @@ int orc_diter(i32 n, const i32 *row_ptr, const i32 *col_idx, double d, double *F
             if (last_empty && T == 0.0) break;   /* F is identically zero */
         } else {
             i32 ns = 0;
-            for (i32 i = 0; i < n; ++i) if (F[i] > T) S[ns++] = i;
+            for (i32 i = 0; i < n; ++i) if (above(F[i], wsel, i, T, wscale)) S[ns++] = i;
             for (i32 k = 0; k < ns; ++k) {
                 i32 i = S[k];
                 sent[k] = F[i];
@@ -242,11 +269,11 @@ int orc_diter(i32 n, const i32 *row_ptr, const i32 *col_idx, double d, double *F
                 i32 i = S[k];
                 i32 beg = row_ptr[i], end = row_ptr[i + 1];
                 if (end == beg) {
-                    R -= sent[k];
+                    R -= fabs(sent[k]);
                 } else {
                     double p = 1.0 / (double)(end - beg);
                     for (i32 e = beg; e < end; ++e) F[col_idx[e]] += sent[k] * p * d;
-                    R -= sent[k] * (1.0 - d);
+                    R -= fabs(sent[k]) * (1.0 - d);
                 }
                 st->edges += end - beg;
             }
@@ -262,6 +289,33 @@ int orc_diter(i32 n, const i32 *row_ptr, const i32 *col_idx, double d, double *F
     st->l1F = l1_norm(n, F);
     st->converged = (st->l1F / (1.0 - d) <= tol) ? 1 : 0;
     return st->converged ? 0 : 1;
+}
+
+/* ---------------------------------------------------------- graph update */
+
+/*
+ * The updating equation (Section 3.2).  A run on P stopped at (F_n0, H_n0);
+ * the graph becomes P'.  Continuing with P' from the fluid
+ *   F_0' = F_n0 + d(P' - P) H_n0
+ * and the history H_n0 reaches H_n0 + H'_inf, the solution of X = dP'X + F_0
+ * (the theorem after the updating equation).  This writes F_0' into F:
+ * every node i takes back d*H_i/#out_i from each child under P and hands it to
+ * each child under P' (a dangling node passes nothing in either graph).
+ */
+void orc_update_inject(i32 n, const i32 *rp_old, const i32 *ci_old, const i32 *rp_new, const i32 *ci_new,
+                       double d, const double *H, double *F) {
+    for (i32 i = 0; i < n; ++i) {
+        i32 beg = rp_old[i], end = rp_old[i + 1];
+        if (end == beg) continue;
+        double p = 1.0 / (double)(end - beg);
+        for (i32 e = beg; e < end; ++e) F[ci_old[e]] -= H[i] * p * d;
+    }
+    for (i32 i = 0; i < n; ++i) {
+        i32 beg = rp_new[i], end = rp_new[i + 1];
+        if (end == beg) continue;
+        double p = 1.0 / (double)(end - beg);
+        for (i32 e = beg; e < end; ++e) F[ci_new[e]] += H[i] * p * d;
+    }
 }
 
 /* ------------------------------------------------------ power iteration */

@@ -50,3 +50,22 @@ def random_graph(n, p_dangling, max_deg, rng, self_loops=True, multi=True):
 def random_v(n, rng):
     v = rng.random(n) + 0.05
     return v / v.sum()
+
+
+def modify(n, row_ptr, col_idx, rng, drop=0.1, add=0.1):
+    """An updated graph: each edge dropped with probability `drop`, about add*L new
+    random edges, one linked node made dangling and one dangling node given links."""
+    edges = [(i, int(j)) for i in range(n) for j in col_idx[row_ptr[i]:row_ptr[i + 1]]]
+    keep = [e for e in edges if rng.random() >= drop]
+    for _ in range(max(1, int(add * len(edges)))):
+        keep.append((int(rng.integers(0, n)), int(rng.integers(0, n))))
+    outdeg = np.diff(np.asarray(row_ptr))
+    linked = [i for i in range(n) if outdeg[i] > 0]
+    dangling = [i for i in range(n) if outdeg[i] == 0]
+    if linked:
+        gone = linked[int(rng.integers(0, len(linked)))]
+        keep = [e for e in keep if e[0] != gone]
+    if dangling:
+        new = dangling[int(rng.integers(0, len(dangling)))]
+        keep += [(new, int(rng.integers(0, n))) for _ in range(3)]
+    return csr(n, keep)

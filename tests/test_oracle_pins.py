@@ -277,3 +277,128 @@ def test_bins_brute_force():
     for b in range(len(cuts) + 1):
         ids = bin_ids[bin_ptr[b]:bin_ptr[b + 1]].tolist()
         assert ids == [i for i in range(n) if want[i] == b]
+
+
+# ------------------------------------------------- graph update (Section 3.2)
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+@pytest.mark.parametrize("tol0", [1e-1, 1e-3, 1e-6])
+def test_update_reaches_the_updated_fixed_point(seed, tol0):
+    """A run on P stopped at bound tol0, continued on P' from F_0' = F + d(P'-P)H, ends
+    within its bound of the solution of X = dP'X + (1-d)V (the theorem after Theorem 3)."""
+    rng = np.random.default_rng(seed)
+    n = 60
+    rp, ci = graphs.random_graph(n, 0.15, 6, rng)
+    rp2, ci2 = graphs.modify(n, rp, ci, rng)
+    V = graphs.random_v(n, rng)
+    X2 = ge.pagerank_dense(n, rp2, ci2, D, V)
+    r0 = oracle.diter(n, rp, ci, D, V, tol0, mode="sweep")
+    for mode in ("sweep", "max", "per"):
+        r1 = oracle.solve_update(n, rp, ci, rp2, ci2, D, r0.F, r0.H, 1e-12, mode=mode, max_pushes=10 ** 7)
+        assert r1.converged
+        assert np.abs(X2 - r1.H).sum() <= r1.l1F / (1 - D) + 1e-13
+
+
+def test_update_injection_keeps_theorem1_for_the_new_graph():
+    """After the injection, H + F' = F_0 + dP'H: the state is a D-iteration state of P'."""
+    rng = np.random.default_rng(9)
+    n = 50
+    rp, ci = graphs.random_graph(n, 0.2, 5, rng)
+    rp2, ci2 = graphs.modify(n, rp, ci, rng)
+    V = graphs.random_v(n, rng)
+    r0 = oracle.diter(n, rp, ci, D, V, 1e-4, mode="sweep")
+    F2 = oracle.update(n, rp, ci, rp2, ci2, D, r0.F, r0.H)
+    P2 = ge.transition_matrix(n, rp2, ci2)
+    assert (F2 < 0).any(), "the update should inject negative fluid somewhere"
+    assert np.abs(r0.H + F2 - (1 - D) * V - D * P2 @ r0.H).max() < 1e-15
+    # the signed fluid keeps moving: |F|_1 never grows along the continued run
+    prev = np.abs(F2).sum()
+    F, H = F2.copy(), r0.H.copy()
+    for _ in range(20):
+        r = oracle.run(n, rp2, ci2, D, F, H, float(np.abs(F).sum()), 0.0, mode="max", max_pushes=3)
+        cur = np.abs(r.F).sum()
+        assert cur <= prev * (1 + 1e-15)
+        assert r.R >= cur - 1e-15        # R stays an upper bound on |F|_1
+        prev = cur
+
+
+def test_theorem3_update_identity():
+    """Theorem 3: X' - X = (I - dP')^-1 d(P' - P) X, checked with exact rational elimination."""
+    from fractions import Fraction as Fr
+    rng = np.random.default_rng(4)
+    n = 7
+    rp, ci = graphs.random_graph(n, 0.2, 3, rng)
+    rp2, ci2 = graphs.modify(n, rp, ci, rng)
+    d = Fr(17, 20)
+    V = [Fr(1, n)] * n
+    X = ge.solve_exact(n, rp, ci, d, V)
+    X2 = ge.solve_exact(n, rp2, ci2, d, V)
+
+    def P(rp_, ci_, x):
+        y = [Fr(0)] * n
+        for i in range(n):
+            deg = rp_[i + 1] - rp_[i]
+            for e in range(rp_[i], rp_[i + 1]):
+                y[ci_[e]] += x[i] / deg
+        return y
+    rhs = [d * (a - b) for a, b in zip(P(rp2, ci2, X), P(rp, ci, X))]
+    # (I - dP') (X' - X) = d(P' - P) X
+    diff = [a - b for a, b in zip(X2, X)]
+    lhs = [a - d * b for a, b in zip(diff, P(rp2, ci2, diff))]
+    assert lhs == rhs
+
+
+def test_update_with_the_same_graph_injects_nothing():
+    rng = np.random.default_rng(12)
+    n = 30
+    rp, ci = graphs.random_graph(n, 0.2, 4, rng)
+    V = graphs.random_v(n, rng)
+    r0 = oracle.diter(n, rp, ci, D, V, 1e-3, mode="sweep")
+    F2 = oracle.update(n, rp, ci, rp, ci, D, r0.F, r0.H)
+    assert np.abs(F2 - r0.F).max() < 1e-17
+
+
+# ---------------------------------------------- ALGO-OP / ALGO-OP2 (Section 4.3)
+
+def test_selection_weights_by_hand():
+    rp, ci = graphs.star(4)               # 0 -> 1..4; leaves dangling
+    w, wscale = oracle.selection_weights(5, rp, ci, "op")
+    # centre: #in 0, #out 4 -> 1/5; leaves: #in 1, #out 0 -> 1/2
+    assert w.tolist() == [np.float32(1 / 5), np.float32(0.5), np.float32(0.5), np.float32(0.5), np.float32(0.5)]
+    assert wscale == 0.25                 # mean 0.44 -> 2^-2
+    w2, wscale2 = oracle.selection_weights(5, rp, ci, "op2")
+    assert w2.tolist() == [np.float32(0.2), 1.0, 1.0, 1.0, 1.0]
+    assert wscale2 == 0.5                 # mean 0.84 -> 2^-1
+
+
+@pytest.mark.parametrize("sel", ["op", "op2"])
+def test_op_argmax_and_first_sweep(sel):
+    rng = np.random.default_rng(21)
+    n = 40
+    rp, ci = graphs.random_graph(n, 0.2, 8, rng)
+    V = graphs.random_v(n, rng)
+    F0 = (1 - D) * V
+    w, wscale = oracle.selection_weights(n, rp, ci, sel)
+    i_star = int(np.argmax(F0 * w.astype(np.float64)))
+    assert i_star != int(np.argmax(F0)), "the weights should change the first choice on this graph"
+    r = oracle.diter(n, rp, ci, D, V, 0.0, mode="max", max_pushes=1, select=sel)
+    assert np.flatnonzero(r.H).tolist() == [i_star]
+    S1 = np.flatnonzero(np.float32(F0) * w > np.float32(0.5 * (1 - D) / n * wscale))
+    r = oracle.diter(n, rp, ci, D, V, 0.0, mode="sweep", max_pushes=1, select=sel)
+    assert np.flatnonzero(r.H).tolist() == S1.tolist()
+
+
+@pytest.mark.parametrize("sel", ["op", "op2"])
+@pytest.mark.parametrize("mode", ["max", "sweep", "thresh"])
+def test_op_orders_reach_the_fixed_point(sel, mode):
+    """Any choice of the sequence converges to X (Section 2.2); ALGO-OP is one such choice."""
+    for seed in range(3):
+        rng = np.random.default_rng(100 + seed)
+        n = 50
+        rp, ci = graphs.random_graph(n, 0.15, 6, rng)
+        V = graphs.random_v(n, rng)
+        X = ge.pagerank_dense(n, rp, ci, D, V)
+        r = oracle.diter(n, rp, ci, D, V, 1e-12, mode=mode, select=sel, max_pushes=10 ** 7)
+        assert r.converged
+        assert np.abs(X - r.H).sum() <= r.l1F / (1 - D) + 1e-13
+        assert np.all(r.H <= X + 1e-15)
