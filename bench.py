@@ -217,6 +217,134 @@ def bench_ppr(di, torch, dev, nbatches=3):
             "speedup": (64 / med) / (64 / single), "lane_dtype": "f32 fluid rows, f64 histories"}
 
 
+def bench_mixed(di, torch, scale=23, ds=(0.85, 0.99), tol=1e-7, ref_tol=1e-10):
+    """FP32-mixed against FP64 D-iteration on R-MAT (scale 23, edge factor 16, a,b,c = .57,.19,.19, duplicates
+    removed), V = 1/N, bound 1e-7, d = 0.85 and 0.99.  The FP64 solve to bound 1e-10 is the reference H_ref
+    (|X - H_ref|_1 <= 1e-10); the error of each result is |H - H_ref|_1 + 1e-10."""
+    import graphgen as gg
+    g = gg.rmat_graph(scale, 16, seed=1)
+    out = {"workload": "R-MAT scale %d (n=%d, L=%d), V=1/N, L1 bound %g, FP32-mixed vs FP64" % (scale, g.n, g.nnz, tol),
+           "reference": "FP64 D-iteration to bound %g" % ref_tol, "runs": []}
+    dev = torch.device("cuda")
+    for d in ds:
+        G = di.DiGraph(g.n, g.row_ptr, g.col_idx, d)
+        Href = torch.empty(g.n, dtype=torch.float64, device=dev)
+        H = torch.empty(g.n, dtype=torch.float64, device=dev)
+        G.solve(tol, H_out=H)                       # warm-up: graph capture, buffers
+        G.solve(tol, H_out=H, prec=di.DI_FP32_MIXED)
+        _, sref = G.solve(ref_tol, H_out=Href)
+        run = {"d": d}
+        for name, prec in (("fp64", di.DI_FP64), ("fp32_mixed", di.DI_FP32_MIXED)):
+            _, st = G.solve(tol, H_out=H, prec=prec)
+            torch.cuda.synchronize()
+            err = float((H - Href).abs().sum().item()) + ref_tol
+            run[name] = {"ms": 1e3 * st["seconds"], "edge_pushes_per_s": st["edges_pushed"] / st["seconds"],
+                         "sweeps": st["sweeps"], "edges": st["edges_pushed"], "bound": st["bound"],
+                         "l1_error_vs_reference": err}
+        run["fp32_speedup"] = run["fp64"]["ms"] / run["fp32_mixed"]["ms"]
+        out["runs"].append(run)
+        log(f"mixed precision d={d}: {run}")
+        G.close()
+    return out
+
+
+def serve_trace(gs, rate, duration, seed):
+    """Poisson arrivals at `rate` for `duration` s, graph uniform, seed sets of 1..16 distinct uniform nodes."""
+    import graphgen as gg
+    rng = np.random.default_rng(seed)
+    nreq = int(rng.poisson(rate * duration))
+    arr = np.sort(rng.uniform(0.0, duration, nreq))
+    gof = rng.integers(0, len(gs), nreq)
+    seeds = [gg.seed_set(gs[k].n, 1, 16, 500 + int(k), i) for i, k in enumerate(gof)]
+    return arr, gof, seeds
+
+
+def serve_run(di, srv, gs, ring, trace, tol, warm):
+    """Open-loop replay through the server; latency = result in host memory - scheduled arrival."""
+    arr, gof, seeds = trace
+    arrival = {}
+    lat = []
+    per_g = [[] for _ in gs]
+    t0 = di.di_clock() + 0.02
+    i, n = 0, len(arr)
+    t_first = t_last = None
+    while True:
+        now = di.di_clock()
+        while i < n and t0 + arr[i] <= now:
+            k = int(gof[i])
+            tk = srv.submit(k, seeds[i], tol, ring[k][i % len(ring[k])])
+            arrival[tk] = (t0 + arr[i], k, arr[i] >= warm)
+            i += 1
+        for c in srv.poll(0.0 if i < n else 0.01):
+            a, k, counted = arrival.pop(c["ticket"])
+            if counted:
+                lat.append(c["t_done"] - a)
+                per_g[k].append(c["t_done"] - a)
+                t_first = a if t_first is None else min(t_first, a)
+                t_last = c["t_done"] if t_last is None else max(t_last, c["t_done"])
+        if i >= n and not arrival:
+            break
+        if now - t0 > 300:
+            raise RuntimeError("serving trace did not drain in 300 s")
+    lat = np.array(lat) * 1e3
+    return {"offered_per_s": n / arr[-1] if n else 0.0, "queries": int(len(lat)),
+            "queries_per_s": len(lat) / (t_last - t_first) if len(lat) else 0.0,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "p50_ms_per_graph": [round(float(np.percentile(np.array(v) * 1e3, 50)), 2) if v else None
+                                 for v in per_g]}
+
+
+def serve_one_at_a_time(di, Gs, gs, ring, trace, tol, count):
+    """The same arrival stream's first `count` queries, one at a time (di_query, FP64) in arrival order."""
+    arr, gof, seeds = trace
+    lat, t_first, t_end = [], None, None
+    t0 = di.di_clock() + 0.02
+    for i in range(min(count, len(arr))):
+        a = t0 + arr[i]
+        while di.di_clock() < a:
+            pass
+        k = int(gof[i])
+        Gs[k].query(seeds[i], tol, H_out=ring[k][0])
+        t_end = di.di_clock()
+        lat.append(t_end - a)
+        t_first = a if t_first is None else t_first
+    lat = np.array(lat) * 1e3
+    return {"queries": int(len(lat)), "queries_per_s": len(lat) / (t_end - t_first),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+
+
+def bench_serve(di, torch, scales=(16, 18, 20, 21, 22, 23), tol=1e-6, budget=120e9,
+                runs=((2000.0, 2.0), (100.0, 4.0)), warm=0.5, base_count=100):
+    """Continuous batching over six R-MAT graphs (edge factor 16, d = 0.85), Poisson arrivals, graph uniform,
+    seed sets U{1..16}, per-query bound 1e-6, lane pools under a 120 GB budget; every H copied to pinned host
+    memory.  Queries arriving in the first `warm` seconds of a trace are not counted."""
+    import graphgen as gg
+    t = time.time()
+    gs = [gg.rmat_graph(s, 16, seed=100 + s) for s in scales]
+    Gs = [di.DiGraph(g.n, g.row_ptr, g.col_idx, 0.85) for g in gs]
+    ring = [[torch.empty(g.n, dtype=torch.float64).pin_memory() for _ in range(4)] for g in gs]
+    torch.cuda.synchronize()
+    log(f"serving graphs ready in {time.time() - t:.1f}s")
+    out = {"workload": "6 R-MAT graphs, scales %s, edge factor 16, d=0.85; Poisson arrivals, graph uniform, "
+                       "1-16 uniform seeds, per-query bound 1e-6, H to pinned host memory" % (list(scales),),
+           "nnz": [g.nnz for g in gs], "budget_bytes": int(budget)}
+    with di.DiServer(Gs, mem_budget=int(budget), round_sweeps=8) as srv:
+        out["lanes"] = srv.lanes()
+        serve_run(di, srv, gs, ring, serve_trace(gs, 50.0, 0.5, 7), tol, 0.0)   # warm-up
+        for rate, dur in runs:
+            trace = serve_trace(gs, rate, dur, int(rate))
+            out["poisson_%d" % int(rate)] = serve_run(di, srv, gs, ring, trace, tol, warm)
+            log(f"serving at {rate} q/s: {out['poisson_%d' % int(rate)]}")
+        out["device_ms_per_graph"] = [round(srv.stats(k)["device_ms"], 1) for k in range(len(gs))]
+    trace = serve_trace(gs, runs[0][0], runs[0][1], int(runs[0][0]))
+    out["one_at_a_time"] = serve_one_at_a_time(di, Gs, gs, ring, trace, tol, base_count)
+    out["one_at_a_time"]["what"] = "first %d queries of the %d q/s trace, di_query FP64 one by one" % (
+        base_count, int(runs[0][0]))
+    for G in Gs:
+        G.close()
+    return out
+
+
 def run_reference(args, w):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -253,6 +381,8 @@ def main():
     ap.add_argument("--cpu-pushes", type=int, default=0, help="diffusions in the oracle sample (0: 8N, more than the full solve needs)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ppr", action="store_true", help="skip the batched personalized-query measurement")
+    ap.add_argument("--no-serve", action="store_true", help="skip the continuous-batching serving measurement")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-mixed vs FP64 measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warm-up below 3 is not allowed; using 3")
@@ -394,6 +524,14 @@ def main():
     if rank == 0 and not args.no_ppr:
         ppr = bench_ppr(di, torch, dev)
 
+    mixed = None
+    if rank == 0 and not args.no_mixed:
+        mixed = bench_mixed(di, torch)
+
+    serve = None
+    if rank == 0 and not args.no_serve:
+        serve = bench_serve(di, torch)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cap = args.cpu_pushes if args.cpu_pushes > 0 else 8 * g.n
@@ -423,6 +561,8 @@ def main():
                             "di_free, host wall clock"},
             "cpu_baseline": cpu,
             "ppr_batch": ppr,
+            "serving": serve,
+            "mixed_precision": mixed,
             "clocks": clk,
             "gpu_launches": launches,
             "host": {"nproc": os.cpu_count()},

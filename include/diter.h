@@ -81,7 +81,25 @@ typedef struct {
     int32_t trace;           /* 1: record one di_sweep_record per sweep, read with di_get_trace */
     int32_t profile;         /* 1: launch each sweep's kernels from the host with CUDA events around
                                 each one (same kernels and arguments, no graph); read with di_get_profile */
+    int32_t select;          /* a di_select value: which nodes a sweep diffuses (default DI_SELECT_REF) */
+    int32_t pad;
 } di_solve_opts;
+
+/*
+ * Node choice of a threshold sweep.  Section 4.3 compares ALGO-MAX (argmax F)
+ * with two variants that divide F by a cost:
+ *   ALGO-OP   argmax F_i / ((#in_i + 1)(#out_i + 1))  (#out: a diffusion costs
+ *             #out steps; #in: fluid arriving by many links is worth letting
+ *             accumulate)
+ *   ALGO-OP2  argmax F_i / (#out_i + 1).
+ * As threshold sweeps: DI_SELECT_REF diffuses every node with |F_i| > T;
+ * DI_SELECT_OP / _OP2 diffuse every node with (float)|F_i| * w_i >
+ * (float)(T * s), w_i = 1/((#in_i+1)(#out_i+1)) or 1/(#out_i+1) rounded to
+ * FP32, and s the power of two nearest below the mean of w (so that T * s is on
+ * the scale of F * w).  Any choice converges to the same X (Section 2.2); only
+ * the number of steps differs.
+ */
+typedef enum { DI_SELECT_REF = 0, DI_SELECT_OP = 1, DI_SELECT_OP2 = 2 } di_select;
 
 typedef struct {
     double l1_F;           /* exact |F|_1 at the start of the sweep */
@@ -176,6 +194,25 @@ di_status di_solve(di_graph *g, double tol, int64_t max_edge_pushes, di_prec pre
 di_status di_solve_ex(di_graph *g, const di_solve_opts *opts, double *H_out, di_stats *st);
 
 /*
+ * Continue a solve after the graph changed (Section 3.2, updating equation).
+ * g_old holds the state (F_n0, H_n0) of its last FP64 solve on P, stopped at any
+ * bound; g_new is the updated graph P' (same n and d).  The solve continues on
+ * P' from the injected fluid F_0' = F_n0 + d(P' - P)H_n0 and the history H_n0;
+ * its limit solves X = dP'X + F_0 with the old F_0 = (1-d)V (the theorem after
+ * Theorem 3), so only the change is diffused.  The injected fluid can be
+ * negative: sweeps select on |F_i|, R decreases by (1-d)|sent| and stays an
+ * upper bound on |F|_1, and st->bound = |F|_1/(1-d) is still a bound on
+ * |X - H|_1 since |(I - dP')^-1|_1 <= 1/(1-d).  The new state is kept in g_new,
+ * which can then be updated in turn.  g_old == g_new continues the same solve.
+ *   opts   tol, beta, limits, trace, profile, select as for di_solve_ex;
+ *          prec must be DI_FP64
+ *   H_out  host or device double[n]: H_n0 + H'
+ * g_old is read; nothing of it changes.
+ */
+di_status di_solve_update(di_graph *g_old, di_graph *g_new, const di_solve_opts *opts, double *H_out,
+                          di_stats *st);
+
+/*
  * Personalized query: di_solve with V replaced by the seed distribution
  * (Section 2.1: V is the personalization vector), V_s = w_s / sum(w) on the
  * seeds and 0 elsewhere.
@@ -188,7 +225,8 @@ di_status di_query(di_graph *g, const int32_t *seeds, const double *w, int32_t n
 /*
  * Up to 64 personalized queries solved together (Section 2.1: V is the
  * personalization vector; each query has its own V_q).  Their fluids share one
- * interleaved FP32 row per node (64 lanes, 256 bytes), so each read of a node's
+ * interleaved FP32 row per node (4, 8, 16, 32 or 64 lanes, the narrowest that
+ * holds k; 4 bytes per lane), so each read of a node's
  * out-links serves every query; histories are FP64.  A sweep selects node i when
  * some query that has not stopped has F_q[i] > T_q (T_q = 0.5 R_q/n), moves the
  * whole row into H and pushes it along the out-links.  Each query stops when its
@@ -260,10 +298,12 @@ di_status di_get_profile(const di_graph *g, di_profile *out);
  *
  * Each graph gets a lane pool of 8, 16, 32 or 64 lanes; a lane costs about
  * 16 bytes per node (FP32 fluid, FP64 history, FP32 sweep copy).  Queries take
- * the lowest free lanes, and each round runs on rows of 8, 16, 32 or 64 lanes,
+ * the lowest free lanes, and each round runs on rows of 4, 8, 16, 32 or 64 lanes,
  * the narrowest that covers every busy lane, so light load moves short rows.
  * The pools are sized at creation by di_plan_lanes under mem_budget bytes.
- * Each pool runs on its own CUDA stream, so rounds of different graphs overlap.
+ * Each pool runs on its own CUDA stream, so rounds of different graphs overlap;
+ * smaller graphs get higher stream priorities, so their short rounds are not
+ * queued behind the long rounds of large graphs.
  *
  * The server is driven from one host thread: di_server_submit queues, and
  * di_server_poll does all the work (finishing rounds, copying results out,

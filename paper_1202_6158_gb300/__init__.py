@@ -22,7 +22,7 @@ from ._lib import (DI_EINVAL, DI_ENOMEM, DI_ENOTCONVERGED, DI_FP32_MIXED, DI_FP6
                    di_completion, di_profile, di_server_graph_stats, di_solve_opts, di_stats, di_sweep_record, ptr)
 
 __all__ = ["DiGraph", "DiError", "DI_FP64", "DI_FP32_MIXED", "DI_OK", "DI_EINVAL", "DI_ENOTCONVERGED",
-           "di_graph_create", "di_free", "di_solve", "di_solve_ex", "di_query", "di_query_batch", "di_power", "di_power_ex", "di_graph_export",
+           "di_graph_create", "di_free", "di_solve", "di_solve_ex", "di_solve_update", "di_query", "di_query_batch", "di_power", "di_power_ex", "di_graph_export",
            "di_get_trace", "di_get_state", "di_get_profile", "di_power_noalloc", "di_version", "load",
            "di_plan_lanes", "di_server_create", "di_server_lanes", "di_server_submit", "di_server_poll",
            "di_server_pending", "di_server_stats", "di_server_free", "di_clock", "DiServer"]
@@ -61,13 +61,28 @@ def di_solve(handle, tol, H_out, max_edge_pushes=0, prec=DI_FP64, normalize=0, a
     return rc, st.as_dict()
 
 
+def _opts(tol, beta, max_edge_pushes, max_sweeps, prec, normalize, trace, profile, select):
+    sel = _lib.SELECT[select] if isinstance(select, str) else int(select)
+    return di_solve_opts(float(tol), float(beta), int(max_edge_pushes), int(max_sweeps), int(prec), int(normalize),
+                         int(trace), int(profile), sel, 0)
+
+
 def di_solve_ex(handle, H_out, tol, beta=0.5, max_edge_pushes=0, max_sweeps=0, prec=DI_FP64, normalize=0, trace=0,
-                profile=0, allow_unconverged=False):
-    o = di_solve_opts(float(tol), float(beta), int(max_edge_pushes), int(max_sweeps), int(prec), int(normalize),
-                      int(trace), int(profile))
+                profile=0, allow_unconverged=False, select="ref"):
+    o = _opts(tol, beta, max_edge_pushes, max_sweeps, prec, normalize, trace, profile, select)
     st = di_stats()
     ok = (DI_OK, DI_ENOTCONVERGED) if allow_unconverged else (DI_OK,)
     rc = check(load().di_solve_ex(handle, ctypes.byref(o), ptr(H_out), ctypes.byref(st)), ok)
+    return rc, st.as_dict()
+
+
+def di_solve_update(old_handle, new_handle, H_out, tol, beta=0.5, max_edge_pushes=0, max_sweeps=0, trace=0,
+                    profile=0, allow_unconverged=False, select="ref"):
+    """Continue old_handle's FP64 state on the updated graph new_handle (Section 3.2)."""
+    o = _opts(tol, beta, max_edge_pushes, max_sweeps, DI_FP64, 0, trace, profile, select)
+    st = di_stats()
+    ok = (DI_OK, DI_ENOTCONVERGED) if allow_unconverged else (DI_OK,)
+    rc = check(load().di_solve_update(old_handle, new_handle, ctypes.byref(o), ptr(H_out), ctypes.byref(st)), ok)
     return rc, st.as_dict()
 
 
@@ -188,6 +203,12 @@ class DiGraph:
         """D-iteration to |F|_1/(1-d) <= tol; returns (H, stats)."""
         H = H_out if H_out is not None else np.empty(self.n, dtype=np.float64)
         _rc, st = di_solve_ex(self.handle, H, tol, **kw)
+        return H, st
+
+    def update_from(self, old, tol, H_out=None, **kw):
+        """Continue `old`'s last FP64 solve on this (updated) graph (Section 3.2); returns (H, stats)."""
+        H = H_out if H_out is not None else np.empty(self.n, dtype=np.float64)
+        _rc, st = di_solve_update(old.handle, self.handle, H, tol, **kw)
         return H, st
 
     def query(self, seeds, tol, w=None, H_out=None, prec=DI_FP64):

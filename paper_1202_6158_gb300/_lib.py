@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(HERE, "libditer.so")
 
 DI_OK, DI_EINVAL, DI_ENOMEM, DI_ECUDA, DI_ENOTCONVERGED, DI_ETIMEOUT, DI_EKERNEL = range(7)
 DI_FP64, DI_FP32_MIXED = 0, 1
+DI_SELECT_REF, DI_SELECT_OP, DI_SELECT_OP2 = 0, 1, 2
+SELECT = {"ref": DI_SELECT_REF, "op": DI_SELECT_OP, "op2": DI_SELECT_OP2}
 STATUS_NAMES = {0: "DI_OK", 1: "DI_EINVAL", 2: "DI_ENOMEM", 3: "DI_ECUDA", 4: "DI_ENOTCONVERGED", 5: "DI_ETIMEOUT",
                 6: "DI_EKERNEL"}
 
@@ -40,7 +42,8 @@ class di_stats(ctypes.Structure):
 class di_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("beta", ctypes.c_double), ("max_edge_pushes", ctypes.c_int64),
                 ("max_sweeps", ctypes.c_int32), ("prec", ctypes.c_int32), ("normalize", ctypes.c_int32),
-                ("trace", ctypes.c_int32), ("profile", ctypes.c_int32)]
+                ("trace", ctypes.c_int32), ("profile", ctypes.c_int32), ("select", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
 
 class di_sweep_record(ctypes.Structure):
@@ -92,6 +95,7 @@ def load(path: str = LIB_PATH):
         "di_graph_hot_targets": ([vp, vp, ctypes.POINTER(i32)], ctypes.c_int),
         "di_solve": ([vp, f64, i64, ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(di_stats)], ctypes.c_int),
         "di_solve_ex": ([vp, ctypes.POINTER(di_solve_opts), vp, ctypes.POINTER(di_stats)], ctypes.c_int),
+        "di_solve_update": ([vp, vp, ctypes.POINTER(di_solve_opts), vp, ctypes.POINTER(di_stats)], ctypes.c_int),
         "di_query": ([vp, vp, vp, i32, f64, ctypes.c_int, vp, ctypes.POINTER(di_stats)], ctypes.c_int),
         "di_power": ([vp, f64, i32, vp, ctypes.POINTER(di_stats)], ctypes.c_int),
         "di_query_batch": ([vp, i32, vp, vp, vp, f64, vp, vp, ctypes.POINTER(di_stats)], ctypes.c_int),

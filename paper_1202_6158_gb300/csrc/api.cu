@@ -63,14 +63,14 @@ static di_status copy_in(void *dst, const void *src, size_t bytes, cudaStream_t 
 static void free_graph(di_graph *g) {
     if (!g) return;
     if (g->stream || g->cap) cudaStreamSynchronize(g->stream);
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 7; ++k) {
         if (g->exec[k]) cudaGraphExecDestroy(g->exec[k]);
         if (g->graph[k]) cudaGraphDestroy(g->graph[k]);
     }
     pool_free(g->bp, g->stream);
     void *bufs[] = {g->row_ptr, g->col_idx, g->in_ptr, g->in_src, g->bin_of, g->in_bin_of, g->pull_ids, g->V,
                     g->inv_deg, g->inv_deg32, g->hot_ids, g->perm, g->new_of, g->rec64, g->rec32,
-                    g->long_prefix, g->region, g->fcount, g->pre, g->ticket, g->sel, g->cls, g->F64, g->F32, g->H, g->part, g->st,
+                    g->wsel[0], g->wsel[1], g->long_prefix, g->region, g->fcount, g->pre, g->ticket, g->sel, g->cls, g->F64, g->F32, g->H, g->part, g->st,
                     g->trace, g->X, g->Z[0], g->Z[1], g->Ylong, g->ppart, g->pst};
     for (void *b : bufs)
         if (b) cudaFreeAsync(b, g->stream);
@@ -243,7 +243,24 @@ di_status di_solve_ex(di_graph *g, const di_solve_opts *opts, double *H_out, di_
     if (!(o.tol > 0.0) || !std::isfinite(o.tol)) return set_error(DI_EINVAL, "tol must be finite and > 0");
     if (!(o.beta >= 0.0) || !std::isfinite(o.beta)) return set_error(DI_EINVAL, "beta must be finite and >= 0");
     if (o.prec != DI_FP64 && o.prec != DI_FP32_MIXED) return set_error(DI_EINVAL, "prec must be DI_FP64 or DI_FP32_MIXED");
+    if (o.select < DI_SELECT_REF || o.select > DI_SELECT_OP2) return set_error(DI_EINVAL, "select must be 0, 1 or 2");
     return run_solve(g, o, nullptr, nullptr, 0, 1.0, H_out, is_device_ptr(H_out), st);
+}
+
+di_status di_solve_update(di_graph *g_old, di_graph *g_new, const di_solve_opts *opts, double *H_out, di_stats *st) {
+    g_last_error.clear();
+    if (!g_old || !g_new) return set_error(DI_EINVAL, "graph is NULL");
+    if (!opts) return set_error(DI_EINVAL, "opts is NULL");
+    di_solve_opts o = *opts;
+    if (!(o.tol > 0.0) || !std::isfinite(o.tol)) return set_error(DI_EINVAL, "tol must be finite and > 0");
+    if (!(o.beta >= 0.0) || !std::isfinite(o.beta)) return set_error(DI_EINVAL, "beta must be finite and >= 0");
+    if (o.prec != DI_FP64) return set_error(DI_EINVAL, "a graph update continues an FP64 state: prec must be DI_FP64");
+    if (o.select < DI_SELECT_REF || o.select > DI_SELECT_OP2) return set_error(DI_EINVAL, "select must be 0, 1 or 2");
+    if (g_old->n != g_new->n) return set_error(DI_EINVAL, "the updated graph must have the same nodes");
+    if (g_old->d != g_new->d) return set_error(DI_EINVAL, "the updated graph must have the same d");
+    if (g_old->last_prec != DI_FP64 || !g_old->F64)
+        return set_error(DI_EINVAL, "g_old holds no FP64 D-iteration state: solve it with prec = DI_FP64 first");
+    return run_update(g_old, g_new, o, H_out, is_device_ptr(H_out), st);
 }
 
 di_status di_solve(di_graph *g, double tol, int64_t max_edge_pushes, di_prec prec, double *H_out, int normalize,

@@ -3,10 +3,10 @@
 // Each query q has its own personalization vector V_q (its seed distribution;
 // Section 2.1: V is the personalization vector), its own fluid F_q, history H_q
 // and residual R_q.  The fluids are interleaved: row i of Fb holds F_q[i] for the
-// 64 lanes q (256 bytes, FP32), so one read of node i's out-links serves every
-// query.  One sweep:
+// K lanes q (K = 4, 8, 16, 32 or 64; FP32, 4K bytes), so one read of node i's
+// out-links serves every query.  One sweep:
 //
-//   k_bscan    streams Fb (a half-warp per node row, one float4 of 4 queries per
+//   k_bscan    streams Fb (K/4 lanes per node row, one float4 of 4 queries per
 //              lane).  Node i is selected when F_q[i] > T_q for some query q that
 //              has not converged; its whole row is then exchanged -- every lane's
 //              fluid moves -- which is a diffusion of node i for every query (any
@@ -16,14 +16,18 @@
 //              mass are summed per lane and added to per-query accumulators.
 //   k_bpush    adds the row to H_i (FP64) and, unless i is dangling, adds
 //              row * d/outdeg(i) to the row of every child with one
-//              red.global.add.v4.f32 per lane (256 bytes per out-link); the
-//              hottest targets' rows are summed in shared memory first.
+//              red.global.add.v4.f32 per lane (4K bytes per out-link); the
+//              hottest targets' rows are summed in shared memory first.  A
+//              node's out-links are spread over a lane group (up to 8), a warp
+//              (up to 1024) or the whole CTA, as in the single-query push.
 //   k_bfinalize  one thread per query: R_q = |F_q|_1 - removed_q, T_q = beta R_q/n,
 //              a query stops when R_q <= tol (1-d); the while-loop ends when all
 //              have stopped.
 //
 // Then |F_q|_1 is recomputed in FP64 per query to confirm each stop, as for a
-// single solve.  The loop is one CUDA graph (while-conditional node).
+// single solve.  The loop is one CUDA graph (while-conditional node).  The rows
+// are K floats apart for a fresh batch; a serving pool keeps its rows 4*cap_lanes
+// bytes apart and runs the narrowest loop that covers its busy lanes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -228,7 +232,7 @@ __device__ __forceinline__ void bpush_edge(float *__restrict__ Fb, int S, float 
     }
 }
 
-// one selected node's row: H += row; then row * d/outdeg to every child (16 lanes x float4)
+// one selected node's row: H += row; then row * d/outdeg to every child (a float4 of 4 queries per lane)
 template <int K>
 __device__ __forceinline__ void bpush_node(int node, const float4 row, int l16, int cls_node,
                                            const RowRec<float> *__restrict__ rec, const int *__restrict__ col_idx,
@@ -262,7 +266,7 @@ __device__ __forceinline__ void bpush_node(int node, const float4 row, int l16, 
 }
 
 template <int LPN>
-__global__ void __launch_bounds__(kScanThreads) k_bpush(const RowRec<float> *__restrict__ rec,
+__global__ void __launch_bounds__(kScanThreads, 4) k_bpush(const RowRec<float> *__restrict__ rec,
                                                         const int *__restrict__ col_idx, float *__restrict__ Fb,
                                                         double *__restrict__ Hb, int S, const int *__restrict__ region,
                                                         const int *__restrict__ pre, int W,
@@ -307,8 +311,27 @@ __global__ void __launch_bounds__(kScanThreads) k_bpush(const RowRec<float> *__r
             bpush_node<K>(node, row, lq, 3, rec, col_idx, Fb, Hb, S, hot, n_hot, grp, GPC, false, edges);
         }
     }
-    // classes 0, 1, 2: a lane group per node, contiguous ranges per group
-    for (int L = 0; L < 3; ++L) {
+    // class 2: a warp per node, its 32/LPN lane groups taking every (32/LPN)-th out-link
+    {
+        constexpr int GPW = 32 / LPN;
+        const int lane = threadIdx.x & 31, gi = lane / LPN;
+        const int nwarps = gridDim.x * kWarps, gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
+        const int *p2 = pre + 2 * (W + 1);
+        const int tot = __ldg(p2 + W);
+        for (int t = gw; t < tot; t += nwarps) {
+            int pos = 0;
+            if (lane == 0) {
+                const int gs = find_sub(p2, W, t);
+                pos = region[2 * (W + 1) + gs] + (t - __ldg(p2 + gs));
+            }
+            pos = __shfl_sync(kFull, pos, 0);
+            const int node = sel_node[pos];
+            const float4 row = *reinterpret_cast<const float4 *>(sel_rows + (long long)pos * K + 4 * lq);
+            bpush_node<K>(node, row, lq, 2, rec, col_idx, Fb, Hb, S, hot, n_hot, gi, GPW, gi == 0, edges);
+        }
+    }
+    // classes 0, 1: a lane group per node, contiguous ranges per group
+    for (int L = 0; L < 2; ++L) {
         const int *pl = pre + L * (W + 1);
         const int tot = __ldg(pl + W);
         const int per = (tot + ngrp - 1) / ngrp;
@@ -565,7 +588,7 @@ int batch_grid(const di_graph *g, long long work) {
 
 }  // namespace
 
-// widths 8, 16, 32, 64 lanes use slots 0..3
+// widths 4, 8, 16, 32, 64 lanes use slots 0..4
 di_status pool_build_loop(di_graph *g, BatchPool *p, int slot) {
     if (p->exec[slot]) return DI_OK;
     cudaGraph_t graph = nullptr;
@@ -584,11 +607,12 @@ di_status pool_build_loop(di_graph *g, BatchPool *p, int slot) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     e = cudaStreamBeginCaptureToGraph(g->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(e, "cudaStreamBeginCaptureToGraph"); }
-    const int S = p->stride ? p->stride : 8 << slot;
+    const int S = p->stride ? p->stride : slot_width(slot);
     switch (slot) {
-        case 0: capture_batch_body<2>(g, p, handle, S); break;
-        case 1: capture_batch_body<4>(g, p, handle, S); break;
-        case 2: capture_batch_body<8>(g, p, handle, S); break;
+        case 0: capture_batch_body<1>(g, p, handle, S); break;
+        case 1: capture_batch_body<2>(g, p, handle, S); break;
+        case 2: capture_batch_body<4>(g, p, handle, S); break;
+        case 3: capture_batch_body<8>(g, p, handle, S); break;
         default: capture_batch_body<16>(g, p, handle, S); break;
     }
     cudaGraph_t captured = nullptr;
@@ -630,7 +654,7 @@ di_status pool_alloc(di_graph *g, BatchPool *p, int lanes, cudaStream_t s) {
 
 void pool_free(BatchPool *p, cudaStream_t s) {
     if (!p) return;
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < kWidths; ++k) {
         if (p->exec[k]) cudaGraphExecDestroy(p->exec[k]);
         if (p->graph[k]) cudaGraphDestroy(p->graph[k]);
     }
@@ -670,11 +694,11 @@ di_status pool_retire(di_graph *g, BatchPool *p, int K, const LaneRetire &r, cud
 
 di_status pool_launch_round(di_graph *g, BatchPool *p, int slot, const LaneAdmin &a, int round_cap, int lane_max,
                             double beta, cudaStream_t s) {
-    const int S = p->stride ? p->stride : 8 << slot;
+    const int S = p->stride ? p->stride : slot_width(slot);
     k_bround_begin<<<1, kLanes, 0, s>>>(a, g->n, 1.0 - g->d, beta, round_cap, lane_max, p->bq, p->bctl);
     DI_CUDA(cudaGetLastError());
     DI_CUDA(cudaGraphLaunch(p->exec[slot], s));
-    k_bl1_pending<<<batch_grid(g, p->rows * (8 << slot)), 256, 0, s>>>(p->rows, S, p->Fb, p->bq);
+    k_bl1_pending<<<batch_grid(g, p->rows * slot_width(slot)), 256, 0, s>>>(p->rows, S, p->Fb, p->bq);
     k_bconfirm_pending<<<1, kLanes, 0, s>>>(g->n, beta, p->bq);
     DI_CUDA(cudaGetLastError());
     DI_CUDA(cudaMemcpyAsync(p->h_bq, p->bq, sizeof(BatchQ) * kLanes, cudaMemcpyDeviceToHost, s));
@@ -689,9 +713,9 @@ di_status run_query_batch(di_graph *g, int k, const int *seed_ptr, const int *se
     BatchPool *p = g->bp;
     di_status r = pool_alloc(g, p, kLanes, s);
     if (r != DI_OK) return r;
-    // the narrowest row that holds the batch: 8, 16, 32 or 64 queries
+    // the narrowest row that holds the batch: 4, 8, 16, 32 or 64 queries
     const int slot = lane_slot(k);
-    const int K = 8 << slot;
+    const int K = slot_width(slot);
     r = pool_build_loop(g, p, slot);
     if (r != DI_OK) return r;
     const int n = g->n;

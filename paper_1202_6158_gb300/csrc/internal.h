@@ -91,11 +91,13 @@ struct SolveState {
     int body_runs;         // executions of the finalize kernel (one per loop iteration)
     int exact;             // 1 when the sweep now running sums |F|_1 exactly (every kExactEvery sweeps)
     int pad[2];
+    double wscale;         // weighted selection: the threshold of F*w is T * wscale
 };
 
 // batched personalized queries: up to kLanes queries interleaved in one fluid row
 constexpr int kLanes = 64;              // queries per batch (the width of a fluid row)
 constexpr int kBatchHot = 32;           // hot targets whose rows the batched push sums in shared memory
+constexpr int kWidths = 5;              // row widths of the batched loops: 4, 8, 16, 32, 64 lanes
 
 struct BatchQ {            // per query lane
     double R;              // residual after the last sweep
@@ -172,9 +174,9 @@ struct BatchPool {
     unsigned *ticket = nullptr;
     BatchQ *bq = nullptr, *h_bq = nullptr;
     BatchCtl *bctl = nullptr, *h_bctl = nullptr;
-    // captured loops for rows of 8, 16, 32, 64 lanes
-    cudaGraph_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
-    cudaGraphExec_t exec[4] = {nullptr, nullptr, nullptr, nullptr};
+    // captured loops for rows of 4, 8, 16, 32, 64 lanes
+    cudaGraph_t graph[kWidths] = {};
+    cudaGraphExec_t exec[kWidths] = {};
 };
 
 }  // namespace diter
@@ -241,9 +243,12 @@ struct di_graph {
     // batched queries (allocated at the first batch)
     diter::BatchPool *bp = nullptr;
 
-    // captured solve loops: [0] FP64 sweeps, [1] FP32-mixed sweeps, [2] power iteration
-    cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
-    cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
+    // captured solve loops: [0] FP64 sweeps, [1] FP32-mixed sweeps, [2] power iteration,
+    // [3 + 2*(select-1) + prec] weighted sweeps (ALGO-OP select 1, ALGO-OP2 select 2)
+    cudaGraph_t graph[7] = {};
+    cudaGraphExec_t exec[7] = {};
+    float *wsel[2] = {nullptr, nullptr};   // [npad] selection weights of ALGO-OP / ALGO-OP2 (0 on the padding)
+    double wscale[2] = {1.0, 1.0};         // 2^floor(log2(mean weight))
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     diter::SolveState *h_st = nullptr; // pinned host mirror
@@ -264,6 +269,9 @@ di_status validate_v(di_graph *g, const double *V_dev);
 di_status sweep_alloc(di_graph *g);
 di_status run_solve(di_graph *g, const di_solve_opts &o, const int *seeds_dev, const double *seed_w_dev, int nseeds,
                     double wsum, double *H_out, bool out_on_device, di_stats *st);
+// graph update (Section 3.2): continue g_old's FP64 state on g_new
+di_status run_update(di_graph *g_old, di_graph *g_new, const di_solve_opts &o, double *H_out, bool out_on_device,
+                     di_stats *st);
 di_status copy_state(const di_graph *g, double *F_out, bool F_dev, double *H_out, bool H_dev);
 di_status gather_x(di_graph *g, const double *src, double *dst, bool dst_dev);
 
@@ -280,7 +288,9 @@ di_status pool_alloc(di_graph *g, BatchPool *p, int lanes, cudaStream_t s);
 void pool_free(BatchPool *p, cudaStream_t s);
 long long pool_bytes(const di_graph *g, int lanes);
 di_status pool_build_loop(di_graph *g, BatchPool *p, int slot);
-inline int lane_slot(int k) { return k <= 8 ? 0 : (k <= 16 ? 1 : (k <= 32 ? 2 : 3)); }
+// row widths 4, 8, 16, 32, 64 lanes are slots 0..4: the narrowest that holds k lanes
+inline int lane_slot(int k) { return k <= 4 ? 0 : (k <= 8 ? 1 : (k <= 16 ? 2 : (k <= 32 ? 3 : 4))); }
+inline int slot_width(int slot) { return 4 << slot; }
 // one round of the serving loop on stream s: free and start lanes, diffuse, confirm stops, copy the lane states back
 di_status pool_launch_round(di_graph *g, BatchPool *p, int slot, const LaneAdmin &a, int round_cap, int lane_max,
                             double beta, cudaStream_t s);

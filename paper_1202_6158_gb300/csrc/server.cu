@@ -231,7 +231,7 @@ di_status admit_and_launch(di_server *srv, SrvPool &p, double t) {
     di_status st = pool_launch_round(p.g, p.bp, wslot, p.adm, srv->round_sweeps, srv->lane_sweeps, srv->beta, p.s);
     if (st != DI_OK) return st;
     DI_CUDA(cudaEventRecord(p.ev_round, p.s));
-    p.round_width = 8 << wslot;
+    p.round_width = slot_width(wslot);
     p.retire_mask = p.admit_mask = 0;
     p.running = true;
     return DI_OK;
@@ -336,6 +336,15 @@ di_status di_server_create(di_graph *const *graphs, int32_t ngraphs, int64_t mem
         di_server_free(srv);
         return s;
     };
+    // smaller graphs get higher stream priority: their short rounds are dispatched
+    // ahead of the long rounds of large graphs when both wait for SMs
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    cudaGetLastError();
+    std::vector<int> order(ngraphs), rank(ngraphs);
+    for (int i = 0; i < ngraphs; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return graphs[a]->n < graphs[b]->n; });
+    for (int r = 0; r < ngraphs; ++r) rank[order[r]] = r;
     for (int i = 0; i < ngraphs; ++i) {
         di_graph *g = graphs[i];
         cudaError_t e = cudaStreamSynchronize(g->stream);
@@ -348,8 +357,9 @@ di_status di_server_create(di_graph *const *graphs, int32_t ngraphs, int64_t mem
         p->slot = lane_slot(p->K);
         p->lane.resize(p->K);
         p->busy.assign(p->K, 0);
-        e = cudaStreamCreateWithFlags(&p->s, cudaStreamNonBlocking);
-        if (e != cudaSuccess) return fail(cuda_fail(e, "cudaStreamCreateWithFlags"));
+        const int prio = std::max(greatest, least - (ngraphs - 1 - rank[i]));
+        e = cudaStreamCreateWithPriority(&p->s, cudaStreamNonBlocking, prio);
+        if (e != cudaSuccess) return fail(cuda_fail(e, "cudaStreamCreateWithPriority"));
         e = cudaEventCreate(&p->ev_round);
         if (e == cudaSuccess) e = cudaEventCreate(&p->ev_start);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_ret, cudaEventDisableTiming);

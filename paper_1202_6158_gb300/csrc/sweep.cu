@@ -36,6 +36,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "device_common.cuh"
 #include "internal.h"
@@ -82,8 +83,9 @@ __global__ void k_init_seeds(int nseeds, const int *__restrict__ seeds, const do
     }
 }
 
-__global__ void k_init_control(SolveState *st, double R0, double tolR, double beta, double one_minus_d, int n,
-                               long long max_edges, int max_sweeps, int trace_on) {
+__device__ void init_control(SolveState *st, double R0, double tolR, double beta, double one_minus_d, int n,
+                             long long max_edges, int max_sweeps, int trace_on, double wscale) {
+    st->wscale = wscale;
     st->R = R0;
     st->tolR = tolR;
     st->beta = beta;
@@ -99,6 +101,22 @@ __global__ void k_init_control(SolveState *st, double R0, double tolR, double be
     st->body_runs = 0;
     // the while-test of ALGO-REF comes first: nothing to do if R/(1-d) <= target already
     st->done = (R0 <= tolR) ? 1 : 0;
+}
+
+__global__ void k_init_control(SolveState *st, double R0, double tolR, double beta, double one_minus_d, int n,
+                               long long max_edges, int max_sweeps, int trace_on, double wscale) {
+    init_control(st, R0, tolR, beta, one_minus_d, n, max_edges, max_sweeps, trace_on, wscale);
+}
+
+// the same with R_0 = |F_0|_1 summed (fixed order) from the per-CTA partials of k_l1_partials:
+// a continued or updated state starts from whatever fluid it holds
+__global__ void k_init_control_l1(SolveState *st, const ScanPartial *__restrict__ part, int G, double tolR,
+                                  double beta, double one_minus_d, int n, long long max_edges, int max_sweeps,
+                                  int trace_on, double wscale) {
+    if (threadIdx.x != 0) return;
+    double R0 = 0.0;
+    for (int c = 0; c < G; ++c) R0 += part[c].l1d;
+    init_control(st, R0, tolR, beta, one_minus_d, n, max_edges, max_sweeps, trace_on, wscale);
 }
 
 // ------------------------------------------------------------------- scan
@@ -132,13 +150,15 @@ __device__ __forceinline__ long long to_fixed(float x, int S) { return to_fixed(
 template <typename FT>
 struct ScanOps;
 
-// FP64 fluid: the threshold test compares bit patterns as signed integers, which
-// orders non-negative doubles exactly like their values (F >= 0 throughout).
+// FP64 fluid: the threshold test compares |F_i| with T through their bit patterns
+// as integers (sign bit cleared), which orders non-negative doubles exactly like
+// their values.  F is non-negative except after a graph update, whose injected
+// fluid may be negative; either way the test is |F_i| > T.
 template <>
 struct ScanOps<double> {
     using Key = long long;
     __device__ static Key key(double T) { return __double_as_longlong(T); }
-    __device__ static bool above(double f, Key k) { return __double_as_longlong(f) > k; }
+    __device__ static bool above(double f, Key k) { return (__double_as_longlong(f) & 0x7fffffffffffffffLL) > k; }
     // four consecutive values starting at a 32-byte boundary
     __device__ static void load4(const double *p, double v[4], unsigned long long pol) {
         const double2 a = ld_stream(reinterpret_cast<const double2 *>(p), pol);
@@ -155,7 +175,7 @@ template <>
 struct ScanOps<float> {
     using Key = float;
     __device__ static Key key(double T) { return (float)T; }
-    __device__ static bool above(float f, Key k) { return f > k; }
+    __device__ static bool above(float f, Key k) { return fabsf(f) > k; }
     __device__ static void load4(const float *p, float v[4], unsigned long long pol) {
         const float4 a = ld_stream(reinterpret_cast<const float4 *>(p), pol);
         v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
@@ -171,8 +191,11 @@ struct ScanOps<float> {
 // step is processed), and appends the selected nodes (id, sent) of each class to
 // that class's list in ascending id order with a warp prefix sum; the lists'
 // per-sub-chunk capacities are fixed at create time, so no atomics are needed.
-template <typename FT>
+// WGT: ALGO-OP / ALGO-OP2 selection (Section 4.3) as a weighted threshold: node i
+// is selected when (float)|F_i| * w_i > (float)(T * wscale), the product in FP32.
+template <typename FT, bool WGT>
 __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__restrict__ F,
+                                                             const float *__restrict__ wsel,
                                                              const unsigned char *__restrict__ cls,
                                                              const int *__restrict__ region, int W,
                                                              int *__restrict__ fcount, int *__restrict__ pre,
@@ -184,6 +207,7 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
     __shared__ unsigned s_ticket;
     if (st->done) return;
     const typename Ops::Key key = Ops::key(st->T);
+    const float tw = WGT ? (float)(st->T * st->wscale) : 0.f;
     const int S = fixed_scale(st->R);
     const bool exact = (st->sweeps % kExactEvery) == 0;  // the exact |F|_1 of this sweep's start
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -197,15 +221,19 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
     const int nsteps = wchunk / kStep;
     FT cur[4], nxt[4];
     unsigned ccur, cnxt = 0;
+    float4 wcur = make_float4(0.f, 0.f, 0.f, 0.f), wnxt = wcur;
     const unsigned long long pol = evict_first_policy();
     Ops::load4(F + wbeg + 4 * lane, cur, pol);
     ccur = ld_stream(reinterpret_cast<const unsigned *>(cls + wbeg + 4 * lane), pol);
+    if (WGT) wcur = ld_stream(reinterpret_cast<const float4 *>(wsel + wbeg + 4 * lane), pol);
     for (int s = 0; s < nsteps; ++s) {
         const long long i0 = wbeg + (long long)s * kStep + 4 * lane;
         if (s + 1 < nsteps) {
             Ops::load4(F + i0 + kStep, nxt, pol);
             cnxt = ld_stream(reinterpret_cast<const unsigned *>(cls + i0 + kStep), pol);
+            if (WGT) wnxt = ld_stream(reinterpret_cast<const float4 *>(wsel + i0 + kStep), pol);
         }
+        const float wk[4] = {wcur.x, wcur.y, wcur.z, wcur.w};
         int lst[4];
         FT sent[4];
         bool any = false;
@@ -213,7 +241,7 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             sent[k] = cur[k];
-            const bool pick = Ops::above(cur[k], key);
+            const bool pick = WGT ? fabsf((float)cur[k]) * wk[k] > tw : Ops::above(cur[k], key);
             long long fx = 0;
             if (exact || pick) fx = to_fixed(cur[k], S);
             if (exact) l1 += fx;
@@ -261,6 +289,7 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
 #pragma unroll
         for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
         ccur = cnxt;
+        wcur = wnxt;
     }
     if (lane == 0) {
 #pragma unroll
@@ -615,9 +644,15 @@ template <> const RowRec<float> *rec_of<float>(di_graph *g) { return g->rec32; }
 template <typename FT> Sel<FT> *sel_of(di_graph *g) { return reinterpret_cast<Sel<FT> *>(g->sel); }
 
 template <typename FT>
-void launch_scan(di_graph *g, FT *F, cudaStream_t s) {
-    k_sweep_scan<FT><<<g->G, kScanThreads, 0, s>>>(g->chunk / kWarps, F, g->cls, g->region, g->W, g->fcount, g->pre,
-                                                   g->ticket, sel_of<FT>(g), g->part, g->st);
+void launch_scan(di_graph *g, FT *F, const float *wsel, cudaStream_t s) {
+    if (wsel)
+        k_sweep_scan<FT, true><<<g->G, kScanThreads, 0, s>>>(g->chunk / kWarps, F, wsel, g->cls, g->region, g->W,
+                                                             g->fcount, g->pre, g->ticket, sel_of<FT>(g), g->part,
+                                                             g->st);
+    else
+        k_sweep_scan<FT, false><<<g->G, kScanThreads, 0, s>>>(g->chunk / kWarps, F, nullptr, g->cls, g->region, g->W,
+                                                              g->fcount, g->pre, g->ticket, sel_of<FT>(g), g->part,
+                                                              g->st);
 }
 
 template <typename FT>
@@ -652,7 +687,7 @@ di_status gather_out(di_graph *g, const FT *src, const double *partials, int np,
 
 // Build the while-loop graph of one precision: body = scan -> push -> finalize.
 template <typename FT>
-di_status build_sweep_graph(di_graph *g, int slot, FT *F) {
+di_status build_sweep_graph(di_graph *g, int slot, FT *F, const float *wsel) {
     cudaGraph_t graph = nullptr;
     DI_CUDA(cudaGraphCreate(&graph, 0));
     cudaGraphConditionalHandle handle;
@@ -669,7 +704,7 @@ di_status build_sweep_graph(di_graph *g, int slot, FT *F) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     e = cudaStreamBeginCaptureToGraph(g->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(e, "cudaStreamBeginCaptureToGraph"); }
-    launch_scan<FT>(g, F, g->cap);
+    launch_scan<FT>(g, F, wsel, g->cap);
     launch_push<FT>(g, F, g->cap);
     k_sweep_finalize<<<1, 256, 0, g->cap>>>(g->n, g->G, g->part, g->st, g->trace, handle, 1);
     cudaGraph_t captured = nullptr;
@@ -683,29 +718,40 @@ di_status build_sweep_graph(di_graph *g, int slot, FT *F) {
     return DI_OK;
 }
 
+// how a solve starts: F_0 = (1-d)V, F_0 on the seeds of a query, or the state already in F and H
+enum InitKind { kInitV, kInitSeeds, kInitState };
+
 template <typename FT>
-di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, const int *seeds, const double *seed_w,
-                     int nseeds, double wsum, double *H_out, bool out_dev, di_stats *stats) {
+di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, InitKind init, const int *seeds,
+                     const double *seed_w, int nseeds, double wsum, double *H_out, bool out_dev, di_stats *stats) {
     cudaStream_t s = g->stream;
     const int n = g->n;
     const int npad = g->G * g->chunk;
     const double omd = 1.0 - g->d;
+    const float *wsel = o.select ? g->wsel[o.select - 1] : nullptr;
+    const double wscale = o.select ? g->wscale[o.select - 1] : 1.0;
     if (!g->exec[slot]) {
-        di_status r = build_sweep_graph<FT>(g, slot, F);
+        di_status r = build_sweep_graph<FT>(g, slot, F, wsel);
         if (r != DI_OK) return r;
     }
     DI_CUDA(cudaEventRecord(g->ev0, s));
-    if (seeds) {
+    if (init == kInitSeeds) {
         k_init_zero<FT><<<elem_grid(g, npad), 256, 0, s>>>(npad, n, F, g->H);
         k_init_seeds<FT><<<std::max(1, std::min(1024, (nseeds + 255) / 256)), 256, 0, s>>>(nseeds, seeds, seed_w, wsum,
                                                                                           omd, g->new_of, F);
-    } else {
+    } else if (init == kInitV) {
         k_init_state<FT><<<elem_grid(g, npad), 256, 0, s>>>(n, npad, F, g->H, g->V, omd);
     }
     const double beta = o.beta > 0 ? o.beta : 0.5;
     const int max_sweeps = o.max_sweeps > 0 ? o.max_sweeps : 1000000;
-    k_init_control<<<1, 1, 0, s>>>(g->st, omd, o.tol * omd, beta, omd, n, o.max_edge_pushes, max_sweeps,
-                                   o.trace ? 1 : 0);
+    if (init == kInitState) {
+        k_l1_partials<FT><<<g->G, kScanThreads, 0, s>>>(n, g->chunk, F, g->part);
+        k_init_control_l1<<<1, 32, 0, s>>>(g->st, g->part, g->G, o.tol * omd, beta, omd, n, o.max_edge_pushes,
+                                           max_sweeps, o.trace ? 1 : 0, wscale);
+    } else {
+        k_init_control<<<1, 1, 0, s>>>(g->st, omd, o.tol * omd, beta, omd, n, o.max_edge_pushes, max_sweeps,
+                                       o.trace ? 1 : 0, wscale);
+    }
     DI_CUDA(cudaGetLastError());
     int attempts = 0;
     g->prof = di_profile{};
@@ -716,7 +762,7 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, const
             cudaGraphConditionalHandle none = 0;
             for (;;) {
                 DI_CUDA(cudaEventRecord(g->pev[0], s));
-                launch_scan<FT>(g, F, s);
+                launch_scan<FT>(g, F, wsel, s);
                 DI_CUDA(cudaEventRecord(g->pev[1], s));
                 launch_push<FT>(g, F, s);
                 DI_CUDA(cudaEventRecord(g->pev[2], s));
@@ -776,7 +822,7 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, const
         stats->converged = h.done == 1 ? 1 : 0;
         stats->seconds = ms * 1e-3;
         // init (2 kernels, 3 for a seeded query) + 3 per loop iteration + 2 per confirmation
-        stats->kernel_launches = (seeds ? 3 : 2) + 3LL * h.body_runs + 2LL * attempts;
+        stats->kernel_launches = (init == kInitV ? 2 : 3) + 3LL * h.body_runs + 2LL * attempts;
     }
     if (h.done == 3) return set_error(DI_EKERNEL, "residual became non-finite");
     if (h.done != 1) return set_error(DI_ENOTCONVERGED, "stopped by a limit before |F|_1/(1-d) <= tol");
@@ -787,8 +833,10 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, const
 
 int scan_blocks_per_sm() {
     int a = 0, b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_sweep_scan<double>, kScanThreads, 0) != cudaSuccess) a = 4;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep_scan<float>, kScanThreads, 0) != cudaSuccess) b = 4;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_sweep_scan<double, false>, kScanThreads, 0) != cudaSuccess)
+        a = 4;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep_scan<float, false>, kScanThreads, 0) != cudaSuccess)
+        b = 4;
     cudaGetLastError();
     return std::max(1, std::min(a, b));
 }
@@ -821,15 +869,130 @@ static di_status ensure_fluid(di_graph *g, int prec) {
     return DI_OK;
 }
 
+namespace {
+
+// ALGO-OP (select 1): w_i = 1/((#in_i + 1)(#out_i + 1)); ALGO-OP2 (select 2): w_i = 1/(#out_i + 1)
+// (Section 4.3).  The integer product is converted to FP64, divided into 1 and rounded to FP32.
+__global__ void k_sel_weights(int n, int npad, int select, const int *__restrict__ in_ptr,
+                              const RowRec<double> *__restrict__ rec, float *__restrict__ w,
+                              double *__restrict__ partial) {
+    __shared__ double s_red[8];
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += (long long)gridDim.x * blockDim.x) {
+        float v = 0.f;
+        if (i < n) {
+            const long long outd = rec[i].deg;
+            const long long c = select == 1 ? (long long)(in_ptr[i + 1] - in_ptr[i] + 1) * (outd + 1) : outd + 1;
+            v = __double2float_rn(1.0 / (double)c);
+            acc += (double)v;
+        }
+        w[i] = v;
+    }
+    acc = block_sum(acc, s_red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+di_status ensure_weights(di_graph *g, int select) {
+    if (select == 0 || g->wsel[select - 1]) return DI_OK;
+    cudaStream_t s = g->stream;
+    const int npad = g->G * g->chunk;
+    float *w = nullptr;
+    double *partial = nullptr;
+    const int nb = elem_grid(g, npad);
+    DI_CUDA(cudaMallocAsync(&w, sizeof(float) * (size_t)npad, s));
+    DI_CUDA(cudaMallocAsync(&partial, sizeof(double) * (size_t)nb, s));
+    k_sel_weights<<<nb, 256, 0, s>>>(g->n, npad, select, g->in_ptr, g->rec64, w, partial);
+    DI_CUDA(cudaGetLastError());
+    std::vector<double> h(nb);
+    DI_CUDA(cudaMemcpyAsync(h.data(), partial, sizeof(double) * (size_t)nb, cudaMemcpyDeviceToHost, s));
+    DI_CUDA(cudaStreamSynchronize(s));
+    cudaFreeAsync(partial, s);
+    double sum = 0.0;
+    for (double x : h) sum += x;
+    int ex = 0;
+    std::frexp(sum / (double)g->n, &ex);            // mean = m 2^ex, 1/2 <= m < 1
+    g->wscale[select - 1] = std::ldexp(1.0, ex - 1);  // 2^floor(log2(mean))
+    g->wsel[select - 1] = w;
+    return DI_OK;
+}
+
+// The updating equation (Section 3.2).  The old state, in the old graph's numbering,
+// is moved to the new graph's numbering: r_new = new_of_new[perm_old[r_old]].
+__global__ void k_map_state(int n, const int *__restrict__ perm_old, const int *__restrict__ new_of_new,
+                            const double *__restrict__ F_old, const double *__restrict__ H_old,
+                            double *__restrict__ F_new, double *__restrict__ H_new) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const int t = new_of_new[perm_old[r]];
+        F_new[t] = F_old[r];
+        H_new[t] = H_old[r];
+    }
+}
+
+// F[map(j)] += sign * H_i * d/outdeg(i) for every out-link i -> j of one graph.  A warp takes
+// 32 consecutive nodes and walks each one's out-links with all lanes.  map = NULL: same numbering;
+// else j is mapped to new_of_dst[perm_src[j]].
+__global__ void k_inject(int n, const RowRec<double> *__restrict__ rec, const int *__restrict__ col_idx,
+                         const double *__restrict__ H, double sign, const int *__restrict__ perm_src,
+                         const int *__restrict__ new_of_dst, double *__restrict__ F) {
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long w0 = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; w0 < n; w0 += nw * 32) {
+        for (int k = 0; k < 32 && w0 + k < n; ++k) {
+            const int i = (int)(w0 + k);
+            const RowRec<double> rr = rec[i];
+            if (rr.deg == 0) continue;
+            const double v = sign * H[i] * rr.inv;
+            if (v == 0.0) continue;
+            for (int e = lane; e < rr.deg; e += 32) {
+                int j = col_idx[rr.beg + e];
+                if (perm_src) j = new_of_dst[perm_src[j]];
+                atomicAdd(F + j, v);
+            }
+        }
+    }
+}
+
+}  // namespace
+
 di_status run_solve(di_graph *g, const di_solve_opts &o, const int *seeds, const double *seed_w, int nseeds,
                     double wsum, double *H_out, bool out_dev, di_stats *st) {
     di_status r = ensure_fluid(g, o.prec);
     if (r != DI_OK) return r;
+    r = ensure_weights(g, o.select);
+    if (r != DI_OK) return r;
     g->last_prec = o.prec;
     g->last_trace_on = o.trace ? 1 : 0;
+    const InitKind init = seeds ? kInitSeeds : kInitV;
+    const int slot = o.select ? 3 + 2 * (o.select - 1) + o.prec : o.prec;
     if (o.prec == DI_FP64)
-        return solve_impl<double>(g, o, g->F64, 0, seeds, seed_w, nseeds, wsum, H_out, out_dev, st);
-    return solve_impl<float>(g, o, g->F32, 1, seeds, seed_w, nseeds, wsum, H_out, out_dev, st);
+        return solve_impl<double>(g, o, g->F64, slot, init, seeds, seed_w, nseeds, wsum, H_out, out_dev, st);
+    return solve_impl<float>(g, o, g->F32, slot, init, seeds, seed_w, nseeds, wsum, H_out, out_dev, st);
+}
+
+di_status run_update(di_graph *go, di_graph *gn, const di_solve_opts &o, double *H_out, bool out_dev, di_stats *st) {
+    di_status r = ensure_fluid(gn, DI_FP64);
+    if (r != DI_OK) return r;
+    r = ensure_weights(gn, o.select);
+    if (r != DI_OK) return r;
+    const int n = gn->n;
+    if (go != gn) {
+        // both graphs' earlier work is complete before the new graph's stream reads the old state
+        DI_CUDA(cudaStreamSynchronize(go->stream));
+        cudaStream_t s = gn->stream;
+        const int npad = gn->G * gn->chunk;
+        DI_CUDA(cudaMemsetAsync(gn->F64, 0, sizeof(double) * (size_t)npad, s));
+        DI_CUDA(cudaMemsetAsync(gn->H, 0, sizeof(double) * (size_t)npad, s));
+        k_map_state<<<elem_grid(gn, n), 256, 0, s>>>(n, go->perm, gn->new_of, go->F64, go->H, gn->F64, gn->H);
+        // F_0' = F + d P' H - d P H: the old graph's pushes of H are taken back, the new graph's added
+        const int gw = std::max(1, std::min(ceil_div(n, 32 * 8), gn->num_sms * 8));
+        k_inject<<<gw, 256, 0, s>>>(n, go->rec64, go->col_idx, go->H, -1.0, go->perm, gn->new_of, gn->F64);
+        k_inject<<<gw, 256, 0, s>>>(n, gn->rec64, gn->col_idx, gn->H, 1.0, nullptr, nullptr, gn->F64);
+        DI_CUDA(cudaGetLastError());
+    }
+    gn->last_prec = DI_FP64;
+    gn->last_trace_on = o.trace ? 1 : 0;
+    const int slot = o.select ? 3 + 2 * (o.select - 1) : 0;
+    return solve_impl<double>(gn, o, gn->F64, slot, kInitState, nullptr, nullptr, 0, 1.0, H_out, out_dev, st);
 }
 
 di_status gather_x(di_graph *g, const double *src, double *dst, bool dst_dev) {
