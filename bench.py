@@ -217,6 +217,50 @@ def bench_ppr(di, torch, dev, nbatches=3):
             "speedup": (64 / med) / (64 / single), "lane_dtype": "f32 fluid rows, f64 histories"}
 
 
+def bench_update(di, torch, G, g, d, tol, fracs=(1e-4, 1e-3, 1e-2)):
+    """Graph update (Section 3.2) on the headline graph: P' keeps each edge with probability 1-f and gains
+    f*L uniform random edges.  A converged solve on P (bound tol) continues on P' from
+    F_0' = F + d(P'-P)H, against a solve of P' from F_0 = (1-d)V.  Device times include the injection."""
+    import graphgen as gg
+    dev = torch.device("cuda")
+    H = torch.empty(g.n, dtype=torch.float64, device=dev)
+    out = {"what": "edit f of the edges of the headline graph; continue its converged solve (bound %g) on the "
+                   "edited graph vs solving the edited graph from scratch" % tol, "runs": []}
+    for k, f in enumerate(fracs):
+        g2 = gg.modify(g, f, int(f * g.nnz), seed=40 + k)
+        G2 = di.DiGraph(g2.n, g2.row_ptr, g2.col_idx, d)
+        G2.solve(tol, H_out=H)
+        _, sc = G2.solve(tol, H_out=H)
+        G.solve(tol, H_out=H)
+        G2.update_from(G, tol, H_out=H)
+        G.solve(tol, H_out=H)
+        _, su = G2.update_from(G, tol, H_out=H)
+        out["runs"].append({"f": f, "scratch_ms": 1e3 * sc["seconds"], "scratch_edges": sc["edges_pushed"],
+                            "scratch_sweeps": sc["sweeps"], "update_ms": 1e3 * su["seconds"],
+                            "update_edges": su["edges_pushed"], "update_sweeps": su["sweeps"],
+                            "update_bound": su["bound"], "speedup": sc["seconds"] / su["seconds"]})
+        log(f"update f={f}: {out['runs'][-1]}")
+        G2.close()
+    return out
+
+
+def bench_selection(di, torch, graphs, tol):
+    """ALGO-OP / ALGO-OP2 (Section 4.3) as weighted threshold sweeps vs the plain threshold, FP64, bound tol."""
+    dev = torch.device("cuda")
+    out = {}
+    for name, (G, n) in graphs.items():
+        H = torch.empty(n, dtype=torch.float64, device=dev)
+        row = {}
+        for sel in ("ref", "op", "op2"):
+            G.solve(tol, H_out=H, select=sel)
+            _, st = G.solve(tol, H_out=H, select=sel)
+            row[sel] = {"ms": 1e3 * st["seconds"], "sweeps": st["sweeps"], "edges": st["edges_pushed"],
+                        "bound": st["bound"]}
+        out[name] = row
+        log(f"selection {name}: {row}")
+    return out
+
+
 def bench_mixed(di, torch, scale=23, ds=(0.85, 0.99), tol=1e-7, ref_tol=1e-10):
     """FP32-mixed against FP64 D-iteration on R-MAT (scale 23, edge factor 16, a,b,c = .57,.19,.19, duplicates
     removed), V = 1/N, bound 1e-7, d = 0.85 and 0.99.  The FP64 solve to bound 1e-10 is the reference H_ref
@@ -383,6 +427,7 @@ def main():
     ap.add_argument("--no-ppr", action="store_true", help="skip the batched personalized-query measurement")
     ap.add_argument("--no-serve", action="store_true", help="skip the continuous-batching serving measurement")
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-mixed vs FP64 measurement")
+    ap.add_argument("--no-update", action="store_true", help="skip the graph-update and selection measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warm-up below 3 is not allowed; using 3")
@@ -524,6 +569,15 @@ def main():
     if rank == 0 and not args.no_ppr:
         ppr = bench_ppr(di, torch, dev)
 
+    update = selection = None
+    if rank == 0 and not args.no_update:
+        update = bench_update(di, torch, G, g, w["d"], tol)
+        import graphgen as gg
+        gr = gg.rmat_graph(22, 16, seed=1)
+        Gr = di.DiGraph(gr.n, gr.row_ptr, gr.col_idx, 0.85)
+        selection = bench_selection(di, torch, {"zipf24": (G, g.n), "rmat22": (Gr, gr.n)}, tol)
+        Gr.close()
+
     mixed = None
     if rank == 0 and not args.no_mixed:
         mixed = bench_mixed(di, torch)
@@ -563,6 +617,8 @@ def main():
             "ppr_batch": ppr,
             "serving": serve,
             "mixed_precision": mixed,
+            "graph_update": update,
+            "selection": selection,
             "clocks": clk,
             "gpu_launches": launches,
             "host": {"nproc": os.cpu_count()},

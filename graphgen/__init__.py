@@ -64,6 +64,9 @@ def _load():
     lib.gg_seed_set.restype = ctypes.c_int32
     lib.gg_unit.argtypes = [u64, u64, u64]
     lib.gg_unit.restype = ctypes.c_double
+    lib.gg_modify.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_double, ctypes.c_int64, u64, i32p, i32p,
+                              ctypes.c_int64]
+    lib.gg_modify.restype = ctypes.c_int64
     _lib = lib
     return lib
 
@@ -129,6 +132,20 @@ def rmat_graph(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.
         raise ValueError("rmat_graph: bad parameters")
     return Graph(n, row_ptr, col_idx[:tot].copy(),
                  f"rmat(scale={scale},ef={edge_factor},abc=({a},{b},{c}),seed={seed},dedup={dedup})")
+
+
+def modify(g: Graph, drop: float, extra: int, seed: int) -> Graph:
+    """An edited copy: each edge dropped with probability `drop`, `extra` uniform random edges added."""
+    lib = _load()
+    cap = len(g.col_idx) + int(extra)
+    row_ptr = np.empty(g.n + 1, dtype=np.int32)
+    col_idx = np.empty(max(cap, 1), dtype=np.int32)
+    tot = lib.gg_modify(g.n, _p(np.ascontiguousarray(g.row_ptr, np.int32)),
+                        _p(np.ascontiguousarray(g.col_idx if len(g.col_idx) else np.zeros(1, np.int32), np.int32)),
+                        float(drop), int(extra), seed, _p(row_ptr), _p(col_idx), cap)
+    if tot < 0:
+        raise ValueError("modify: output capacity exceeded")
+    return Graph(g.n, row_ptr, col_idx[:tot].copy(), f"modify({g.name},drop={drop},extra={extra},seed={seed})")
 
 
 def seed_set(n: int, smin: int, smax: int, seed: int, q: int) -> np.ndarray:

@@ -280,6 +280,46 @@ i64 gg_rmat(int scale, i32 edge_factor, double a, double b, double c, u64 seed, 
  * Personalization seed sets for query q: size uniform in {smin..smax}, members
  * distinct and uniform over [0,n).  out must hold smax ints; returns the size.
  */
+/*
+ * An edited copy of a graph (an "updated" web graph): every edge is kept unless
+ * its draw falls below drop, and `extra` new edges, drawn as (source, target)
+ * pairs uniform over the nodes, are appended to their source rows.  Writes row_ptr2[n+1] and col_idx2
+ * (capacity cap); returns the edge count, or -1 if cap is too small.
+ */
+i64 gg_modify(i32 n, const i32 *row_ptr, const i32 *col_idx, double drop, i64 extra, u64 seed,
+              i32 *row_ptr2, i32 *col_idx2, i64 cap) {
+    i32 *add = (i32 *)calloc((size_t)n, sizeof(i32));
+    for (i64 k = 0; k < extra; ++k) add[below(draw(seed, 21, 2 * (u64)k), (u64)n)] += 1;
+    i64 at = 0;
+    i64 k_next = 0;
+    /* the k-th extra edge goes to the k-th slot of its source, in draw order */
+    i32 **tgt = (i32 **)calloc((size_t)n, sizeof(i32 *));
+    i32 *fill = (i32 *)calloc((size_t)n, sizeof(i32));
+    for (i32 i = 0; i < n; ++i)
+        if (add[i]) tgt[i] = (i32 *)malloc(sizeof(i32) * (size_t)add[i]);
+    for (; k_next < extra; ++k_next) {
+        i32 src = (i32)below(draw(seed, 21, 2 * (u64)k_next), (u64)n);
+        tgt[src][fill[src]++] = (i32)below(draw(seed, 21, 2 * (u64)k_next + 1), (u64)n);
+    }
+    row_ptr2[0] = 0;
+    for (i32 i = 0; i < n; ++i) {
+        for (i32 e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            if (unit(draw(seed, 20, (u64)e)) < drop) continue;
+            if (at >= cap) { at = -1; goto done; }
+            col_idx2[at++] = col_idx[e];
+        }
+        for (i32 k = 0; k < add[i]; ++k) {
+            if (at >= cap) { at = -1; goto done; }
+            col_idx2[at++] = tgt[i][k];
+        }
+        row_ptr2[i + 1] = (i32)at;
+    }
+done:
+    for (i32 i = 0; i < n; ++i) free(tgt[i]);
+    free(tgt); free(fill); free(add);
+    return at;
+}
+
 i32 gg_seed_set(i32 n, i32 smin, i32 smax, u64 seed, i64 q, i32 *out) {
     if (n <= 0 || smin < 1 || smax < smin) return -1;
     if (smax > n) smax = n;

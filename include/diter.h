@@ -96,8 +96,10 @@ typedef struct {
  * DI_SELECT_OP / _OP2 diffuse every node with (float)|F_i| * w_i >
  * (float)(T * s), w_i = 1/((#in_i+1)(#out_i+1)) or 1/(#out_i+1) rounded to
  * FP32, and s the power of two nearest below the mean of w (so that T * s is on
- * the scale of F * w).  Any choice converges to the same X (Section 2.2); only
- * the number of steps differs.
+ * the scale of F * w).  With weights the threshold is never raised: after a
+ * sweep that diffused something T = min(T, beta R/n), after an empty one T/2.
+ * Any choice converges to the same X (Section 2.2); only the number of steps
+ * differs.
  */
 typedef enum { DI_SELECT_REF = 0, DI_SELECT_OP = 1, DI_SELECT_OP2 = 2 } di_select;
 
@@ -192,6 +194,35 @@ di_status di_solve(di_graph *g, double tol, int64_t max_edge_pushes, di_prec pre
 
 /* di_solve with every option (defaults when opts fields are zero, see di_solve_opts). */
 di_status di_solve_ex(di_graph *g, const di_solve_opts *opts, double *H_out, di_stats *st);
+
+/*
+ * Autotuner.  Solves g to base->tol (base->prec, limits, V) once per candidate
+ * and keeps the fastest by device time:
+ *   beta              0.125, 0.25, 0.5, 1, 2 (the threshold schedule T = beta R/n;
+ *                     the paper only says the threshold is lowered progressively)
+ *   select            DI_SELECT_REF, _OP, _OP2 (Section 4.3)
+ *   push_ctas_per_sm  2, 4, 8 (the push grid; never below the scan grid)
+ * Every candidate's result is a valid solve (any choice converges, Section 2.2);
+ * only the time differs.  The winning push_ctas_per_sm stays set on g; beta and
+ * select are returned for the caller to pass in di_solve_opts.
+ *   best    receives the fastest candidate
+ *   tried   host di_tune_result[cap] (may be NULL): every candidate in the order tried;
+ *           *ntried receives their number
+ * The cutoffs of the out-degree classes (8 and 1024 out-links) are fixed at
+ * graph creation and are not tuned.
+ */
+typedef struct {
+    double beta;
+    int32_t select;
+    int32_t push_ctas_per_sm;
+    double ms;               /* device time of the candidate's solve */
+    int64_t edges_pushed;
+    int32_t sweeps;
+    int32_t pad;
+} di_tune_result;
+
+di_status di_autotune(di_graph *g, const di_solve_opts *base, di_tune_result *best, di_tune_result *tried,
+                      int32_t cap, int32_t *ntried);
 
 /*
  * Continue a solve after the graph changed (Section 3.2, updating equation).

@@ -75,7 +75,8 @@ def _bind(lib):
     lib.orc_init.restype = ctypes.c_double
     lib.orc_diter.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_double, f64p, f64p, ctypes.c_double,
                               ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_int64,
-                              ctypes.POINTER(ctypes.c_float), ctypes.c_double, ctypes.POINTER(Stats)]
+                              ctypes.POINTER(ctypes.c_float), ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                              ctypes.c_int64, ctypes.POINTER(Stats)]
     lib.orc_update_inject.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, ctypes.c_double, f64p, f64p]
     lib.orc_diter.restype = ctypes.c_int
     lib.orc_power.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_double, f64p, ctypes.c_double,
@@ -154,10 +155,11 @@ def selection_weights(n, row_ptr, col_idx, select):
 
 
 def run(n, row_ptr, col_idx, d, F, H, R, tol, mode="sweep", beta=0.5, seed=0, max_pushes=1 << 62, lib=None,
-        select=None):
+        select=None, trace=None):
     """Continue D-iteration on the state (F, H, R) in place (ALGO-REF, Sections 2.2 and 3.3).
 
     select = "op" / "op2" chooses nodes by |F_i| w_i (Section 4.3) in the MAX and sweep orders.
+    trace: a float64 array of shape (cap, 3) that receives (T, R, selected) per snapshot sweep.
     """
     lib = lib or load()
     rp, rpp = _i32(row_ptr)
@@ -168,7 +170,11 @@ def run(n, row_ptr, col_idx, d, F, H, R, tol, mode="sweep", beta=0.5, seed=0, ma
     if select is not None and select != "ref":
         w, wscale = selection_weights(n, rp, ci[:int(rp[n])], select)
         wp = w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
-    rc = lib.orc_diter(n, rpp, cip, d, _f64(F), _f64(H), R, tol, m, beta, seed, max_pushes, wp, wscale,
+    tp, tcap = None, 0
+    if trace is not None:
+        assert trace.dtype == np.float64 and trace.flags["C_CONTIGUOUS"] and trace.shape[1] == 3
+        tp, tcap = _f64(trace), trace.shape[0]
+    rc = lib.orc_diter(n, rpp, cip, d, _f64(F), _f64(H), R, tol, m, beta, seed, max_pushes, wp, wscale, tp, tcap,
                        ctypes.byref(st))
     if rc < 0:
         raise ValueError(f"oracle: unknown mode {mode}")
@@ -176,10 +182,10 @@ def run(n, row_ptr, col_idx, d, F, H, R, tol, mode="sweep", beta=0.5, seed=0, ma
 
 
 def diter(n, row_ptr, col_idx, d, V, tol, mode="sweep", beta=0.5, seed=0, max_pushes=1 << 62, lib=None,
-          select=None):
+          select=None, trace=None):
     """D-iteration from the initial state to R/(1-d) <= tol (ALGO-REF, Sections 2.2, 3.3, 4)."""
     F, H, R = init(n, d, V, lib)
-    return run(n, row_ptr, col_idx, d, F, H, R, tol, mode, beta, seed, max_pushes, lib, select)
+    return run(n, row_ptr, col_idx, d, F, H, R, tol, mode, beta, seed, max_pushes, lib, select, trace)
 
 
 def update(n, rp_old, ci_old, rp_new, ci_new, d, F, H, lib=None):

@@ -149,6 +149,10 @@ static double l1_norm(i32 n, const double *F) {
  * made in FP32 (a selection rule only decides which diffusions happen, and any
  * choice converges, Section 2.2); wscale is the power of two nearest below the
  * mean weight, which keeps the weighted threshold on the scale of F * w.
+ * With weights the threshold is only ever lowered (the paper: the threshold is
+ * scaled down progressively): after a sweep that diffused something,
+ * T = min(T, beta R / N); after an empty one, T / 2.  Raising it again after the
+ * halvings (the plain rule) would oscillate when the weights span many orders.
  */
 static double pick_key(const double *F, const float *wsel, i32 i) {
     return wsel ? fabs(F[i]) * (double)wsel[i] : fabs(F[i]);
@@ -195,11 +199,13 @@ static int above(double f, const float *wsel, i32 i, double T, double wscale) {
  * Zero-fluid picks of PER / RAND are skipped without counting (Section 4.2).
  * The sequential orders test the stop rule after every diffusion, like the
  * while-loop of ALGO-REF; ORC_SWEEP tests it between sweeps.
+ * ORC_SWEEP can record (T, R at the sweep start, nodes selected) per sweep in
+ * trace[3 * trace_cap] (NULL: no record).
  * Returns 0 if converged, 1 if max_pushes was reached first.
  */
 int orc_diter(i32 n, const i32 *row_ptr, const i32 *col_idx, double d, double *F, double *H, double R,
               double tol, int mode, double beta, u64 seed, i64 max_pushes, const float *wsel, double wscale,
-              orc_stats *st) {
+              double *trace, i64 trace_cap, orc_stats *st) {
     memset(st, 0, sizeof(*st));
     if (mode < ORC_PER || mode > ORC_SWEEP) return -1;
     const int sweeping = (mode == ORC_THRESH || mode == ORC_SWEEP);
@@ -217,7 +223,9 @@ int orc_diter(i32 n, const i32 *row_ptr, const i32 *col_idx, double d, double *F
         if (sweeping) {
             if (!first) {
                 R = l1_norm(n, F);
-                T = last_empty ? T / 2.0 : beta * R / (double)n;
+                if (last_empty) T = T / 2.0;
+                else if (wsel) T = fmin(T, beta * R / (double)n);   /* weighted: never raised */
+                else T = beta * R / (double)n;
             }
             first = 0;
         }
@@ -259,6 +267,11 @@ int orc_diter(i32 n, const i32 *row_ptr, const i32 *col_idx, double d, double *F
         } else {
             i32 ns = 0;
             for (i32 i = 0; i < n; ++i) if (above(F[i], wsel, i, T, wscale)) S[ns++] = i;
+            if (trace && st->sweeps < trace_cap) {    /* (T, R at the sweep start, nodes selected) */
+                trace[3 * st->sweeps] = T;
+                trace[3 * st->sweeps + 1] = R;
+                trace[3 * st->sweeps + 2] = (double)ns;
+            }
             for (i32 k = 0; k < ns; ++k) {
                 i32 i = S[k];
                 sent[k] = F[i];

@@ -19,10 +19,10 @@ import numpy as np
 
 from . import _lib
 from ._lib import (DI_EINVAL, DI_ENOMEM, DI_ENOTCONVERGED, DI_FP32_MIXED, DI_FP64, DI_OK, DiError, check,
-                   di_completion, di_profile, di_server_graph_stats, di_solve_opts, di_stats, di_sweep_record, ptr)
+                   di_completion, di_profile, di_server_graph_stats, di_tune_result, di_solve_opts, di_stats, di_sweep_record, ptr)
 
 __all__ = ["DiGraph", "DiError", "DI_FP64", "DI_FP32_MIXED", "DI_OK", "DI_EINVAL", "DI_ENOTCONVERGED",
-           "di_graph_create", "di_free", "di_solve", "di_solve_ex", "di_solve_update", "di_query", "di_query_batch", "di_power", "di_power_ex", "di_graph_export",
+           "di_graph_create", "di_free", "di_solve", "di_solve_ex", "di_solve_update", "di_autotune", "di_query", "di_query_batch", "di_power", "di_power_ex", "di_graph_export",
            "di_get_trace", "di_get_state", "di_get_profile", "di_power_noalloc", "di_version", "load",
            "di_plan_lanes", "di_server_create", "di_server_lanes", "di_server_submit", "di_server_poll",
            "di_server_pending", "di_server_stats", "di_server_free", "di_clock", "DiServer"]
@@ -74,6 +74,17 @@ def di_solve_ex(handle, H_out, tol, beta=0.5, max_edge_pushes=0, max_sweeps=0, p
     ok = (DI_OK, DI_ENOTCONVERGED) if allow_unconverged else (DI_OK,)
     rc = check(load().di_solve_ex(handle, ctypes.byref(o), ptr(H_out), ctypes.byref(st)), ok)
     return rc, st.as_dict()
+
+
+def di_autotune(handle, tol, prec=DI_FP64, max_sweeps=0, max_edge_pushes=0):
+    """Time one solve per (beta, select, push CTAs per SM) candidate; returns (best, tried)."""
+    o = _opts(tol, 0.5, max_edge_pushes, max_sweeps, prec, 0, 0, 0, 0)
+    best = di_tune_result()
+    cap = 64
+    tried = (di_tune_result * cap)()
+    n = ctypes.c_int32(0)
+    check(load().di_autotune(handle, ctypes.byref(o), ctypes.byref(best), tried, cap, ctypes.byref(n)))
+    return best.as_dict(), [tried[i].as_dict() for i in range(min(n.value, cap))]
 
 
 def di_solve_update(old_handle, new_handle, H_out, tol, beta=0.5, max_edge_pushes=0, max_sweeps=0, trace=0,
@@ -204,6 +215,10 @@ class DiGraph:
         H = H_out if H_out is not None else np.empty(self.n, dtype=np.float64)
         _rc, st = di_solve_ex(self.handle, H, tol, **kw)
         return H, st
+
+    def autotune(self, tol, prec=DI_FP64, **kw):
+        """Fastest (beta, select, push grid) for this graph and target; the push grid stays set."""
+        return di_autotune(self.handle, tol, prec, **kw)
 
     def update_from(self, old, tol, H_out=None, **kw):
         """Continue `old`'s last FP64 solve on this (updated) graph (Section 3.2); returns (H, stats)."""

@@ -90,7 +90,8 @@ struct SolveState {
     int trace_on;
     int body_runs;         // executions of the finalize kernel (one per loop iteration)
     int exact;             // 1 when the sweep now running sums |F|_1 exactly (every kExactEvery sweeps)
-    int pad[2];
+    int weighted;          // ALGO-OP / OP2 selection: the threshold is never raised
+    int pad;
     double wscale;         // weighted selection: the threshold of F*w is T * wscale
 };
 
@@ -187,6 +188,7 @@ struct di_graph {
     double d = 0.85;
     int dev = 0;
     int num_sms = 152;
+    int push_per_sm = 4;               // push CTAs per SM at least (the push grid never shrinks below the scan's)
     cudaStream_t stream = nullptr;     // user stream
     cudaStream_t cap = nullptr;        // private stream used for graph capture
 
@@ -305,8 +307,11 @@ void *kernel_ptr(void *p);
 
 // helpers
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
-// push CTAs: the pushes scale with edges, not nodes, so small graphs still get 4 CTAs per SM
-inline int push_grid(const di_graph *g) { return g->G > 4 * g->num_sms ? g->G : 4 * g->num_sms; }
+// push CTAs: the pushes scale with edges, not nodes, so small graphs still get push_per_sm CTAs per SM
+inline int push_grid(const di_graph *g) {
+    const int m = g->push_per_sm * g->num_sms;
+    return g->G > m ? g->G : m;
+}
 
 }  // namespace diter
 

@@ -84,8 +84,9 @@ __global__ void k_init_seeds(int nseeds, const int *__restrict__ seeds, const do
 }
 
 __device__ void init_control(SolveState *st, double R0, double tolR, double beta, double one_minus_d, int n,
-                             long long max_edges, int max_sweeps, int trace_on, double wscale) {
+                             long long max_edges, int max_sweeps, int trace_on, double wscale, int weighted) {
     st->wscale = wscale;
+    st->weighted = weighted;
     st->R = R0;
     st->tolR = tolR;
     st->beta = beta;
@@ -104,19 +105,19 @@ __device__ void init_control(SolveState *st, double R0, double tolR, double beta
 }
 
 __global__ void k_init_control(SolveState *st, double R0, double tolR, double beta, double one_minus_d, int n,
-                               long long max_edges, int max_sweeps, int trace_on, double wscale) {
-    init_control(st, R0, tolR, beta, one_minus_d, n, max_edges, max_sweeps, trace_on, wscale);
+                               long long max_edges, int max_sweeps, int trace_on, double wscale, int weighted) {
+    init_control(st, R0, tolR, beta, one_minus_d, n, max_edges, max_sweeps, trace_on, wscale, weighted);
 }
 
 // the same with R_0 = |F_0|_1 summed (fixed order) from the per-CTA partials of k_l1_partials:
 // a continued or updated state starts from whatever fluid it holds
 __global__ void k_init_control_l1(SolveState *st, const ScanPartial *__restrict__ part, int G, double tolR,
                                   double beta, double one_minus_d, int n, long long max_edges, int max_sweeps,
-                                  int trace_on, double wscale) {
+                                  int trace_on, double wscale, int weighted) {
     if (threadIdx.x != 0) return;
     double R0 = 0.0;
     for (int c = 0; c < G; ++c) R0 += part[c].l1d;
-    init_control(st, R0, tolR, beta, one_minus_d, n, max_edges, max_sweeps, trace_on, wscale);
+    init_control(st, R0, tolR, beta, one_minus_d, n, max_edges, max_sweeps, trace_on, wscale, weighted);
 }
 
 // ------------------------------------------------------------------- scan
@@ -564,7 +565,9 @@ __global__ void k_sweep_finalize(int n, int G, const ScanPartial *__restrict__ p
         trace[st->sweeps - 1] = r;
     }
     st->R = R;
+    // T = beta R/n, halved after an empty sweep; with weights (ALGO-OP) it is never raised
     double Tn = (sr == 0) ? 0.5 * Tused : st->beta * R / (double)n;
+    if (sr != 0 && st->weighted) Tn = fmin(Tused, Tn);
     if (!(Tn > 0.0)) Tn = 0.0;
     st->T = Tn;
     int done = 0;
@@ -734,7 +737,8 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, InitK
         di_status r = build_sweep_graph<FT>(g, slot, F, wsel);
         if (r != DI_OK) return r;
     }
-    DI_CUDA(cudaEventRecord(g->ev0, s));
+    // a graph update records ev0 itself, before its injection kernels
+    if (init != kInitState) DI_CUDA(cudaEventRecord(g->ev0, s));
     if (init == kInitSeeds) {
         k_init_zero<FT><<<elem_grid(g, npad), 256, 0, s>>>(npad, n, F, g->H);
         k_init_seeds<FT><<<std::max(1, std::min(1024, (nseeds + 255) / 256)), 256, 0, s>>>(nseeds, seeds, seed_w, wsum,
@@ -747,10 +751,10 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, InitK
     if (init == kInitState) {
         k_l1_partials<FT><<<g->G, kScanThreads, 0, s>>>(n, g->chunk, F, g->part);
         k_init_control_l1<<<1, 32, 0, s>>>(g->st, g->part, g->G, o.tol * omd, beta, omd, n, o.max_edge_pushes,
-                                           max_sweeps, o.trace ? 1 : 0, wscale);
+                                           max_sweeps, o.trace ? 1 : 0, wscale, o.select ? 1 : 0);
     } else {
         k_init_control<<<1, 1, 0, s>>>(g->st, omd, o.tol * omd, beta, omd, n, o.max_edge_pushes, max_sweeps,
-                                       o.trace ? 1 : 0, wscale);
+                                       o.trace ? 1 : 0, wscale, o.select ? 1 : 0);
     }
     DI_CUDA(cudaGetLastError());
     int attempts = 0;
@@ -928,27 +932,39 @@ __global__ void k_map_state(int n, const int *__restrict__ perm_old, const int *
     }
 }
 
-// F[map(j)] += sign * H_i * d/outdeg(i) for every out-link i -> j of one graph.  A warp takes
-// 32 consecutive nodes and walks each one's out-links with all lanes.  map = NULL: same numbering;
-// else j is mapped to new_of_dst[perm_src[j]].
-__global__ void k_inject(int n, const RowRec<double> *__restrict__ rec, const int *__restrict__ col_idx,
-                         const double *__restrict__ H, double sign, const int *__restrict__ perm_src,
-                         const int *__restrict__ new_of_dst, double *__restrict__ F) {
-    const int lane = threadIdx.x & 31;
-    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long w0 = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; w0 < n; w0 += nw * 32) {
-        for (int k = 0; k < 32 && w0 + k < n; ++k) {
-            const int i = (int)(w0 + k);
+// F[j] += sign * H_i * d/outdeg(i) for every out-link i -> j of one graph, in its own numbering.
+// A thread takes a node with up to 32 out-links; longer rows are queued in shared memory and
+// walked by a warp each.
+__global__ void __launch_bounds__(256) k_inject(int n, const RowRec<double> *__restrict__ rec,
+                                                const int *__restrict__ col_idx, const double *__restrict__ H,
+                                                double sign, double *__restrict__ F) {
+    __shared__ int s_long[256];
+    __shared__ int s_nlong;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += (long long)gridDim.x * blockDim.x) {
+        if (threadIdx.x == 0) s_nlong = 0;
+        __syncthreads();
+        const long long i = base + threadIdx.x;
+        if (i < n) {
             const RowRec<double> rr = rec[i];
-            if (rr.deg == 0) continue;
-            const double v = sign * H[i] * rr.inv;
-            if (v == 0.0) continue;
-            for (int e = lane; e < rr.deg; e += 32) {
-                int j = col_idx[rr.beg + e];
-                if (perm_src) j = new_of_dst[perm_src[j]];
-                atomicAdd(F + j, v);
+            const double v = rr.deg > 0 ? sign * H[i] * rr.inv : 0.0;
+            if (v != 0.0) {
+                if (rr.deg <= 32) {
+                    for (int e = 0; e < rr.deg; ++e) atomicAdd(F + col_idx[rr.beg + e], v);
+                } else {
+                    s_long[atomicAdd(&s_nlong, 1)] = (int)i;
+                }
             }
         }
+        __syncthreads();
+        const int nl = s_nlong;
+        for (int k = wid; k < nl; k += nwarp) {
+            const int i2 = s_long[k];
+            const RowRec<double> rr = rec[i2];
+            const double v = sign * H[i2] * rr.inv;
+            for (int e = lane; e < rr.deg; e += 32) atomicAdd(F + col_idx[rr.beg + e], v);
+        }
+        __syncthreads();
     }
 }
 
@@ -975,23 +991,34 @@ di_status run_update(di_graph *go, di_graph *gn, const di_solve_opts &o, double 
     r = ensure_weights(gn, o.select);
     if (r != DI_OK) return r;
     const int n = gn->n;
+    const int slot = o.select ? 3 + 2 * (o.select - 1) : 0;
+    if (!gn->exec[slot]) {  // capture before timing starts, as a solve does
+        r = build_sweep_graph<double>(gn, slot, gn->F64, o.select ? gn->wsel[o.select - 1] : nullptr);
+        if (r != DI_OK) return r;
+    }
+    // both graphs' earlier work is complete before the new graph's stream reads the old state
+    DI_CUDA(cudaStreamSynchronize(go->stream));
+    DI_CUDA(cudaEventRecord(gn->ev0, gn->stream));
     if (go != gn) {
-        // both graphs' earlier work is complete before the new graph's stream reads the old state
-        DI_CUDA(cudaStreamSynchronize(go->stream));
         cudaStream_t s = gn->stream;
         const int npad = gn->G * gn->chunk;
+        // F_0' = F + d P' H - d P H.  The old graph's pushes of H are taken back in the old
+        // numbering (tmp = F - dPH), the state is mapped into the new numbering, and the new
+        // graph's pushes of H are added there.
+        double *tmp = nullptr;
+        DI_CUDA(cudaMallocAsync(&tmp, sizeof(double) * (size_t)n, s));
+        DI_CUDA(cudaMemcpyAsync(tmp, go->F64, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+        const int gi = std::max(1, std::min(ceil_div(n, 256), gn->num_sms * 8));
+        k_inject<<<gi, 256, 0, s>>>(n, go->rec64, go->col_idx, go->H, -1.0, tmp);
         DI_CUDA(cudaMemsetAsync(gn->F64, 0, sizeof(double) * (size_t)npad, s));
         DI_CUDA(cudaMemsetAsync(gn->H, 0, sizeof(double) * (size_t)npad, s));
-        k_map_state<<<elem_grid(gn, n), 256, 0, s>>>(n, go->perm, gn->new_of, go->F64, go->H, gn->F64, gn->H);
-        // F_0' = F + d P' H - d P H: the old graph's pushes of H are taken back, the new graph's added
-        const int gw = std::max(1, std::min(ceil_div(n, 32 * 8), gn->num_sms * 8));
-        k_inject<<<gw, 256, 0, s>>>(n, go->rec64, go->col_idx, go->H, -1.0, go->perm, gn->new_of, gn->F64);
-        k_inject<<<gw, 256, 0, s>>>(n, gn->rec64, gn->col_idx, gn->H, 1.0, nullptr, nullptr, gn->F64);
+        k_map_state<<<elem_grid(gn, n), 256, 0, s>>>(n, go->perm, gn->new_of, tmp, go->H, gn->F64, gn->H);
+        k_inject<<<gi, 256, 0, s>>>(n, gn->rec64, gn->col_idx, gn->H, 1.0, gn->F64);
         DI_CUDA(cudaGetLastError());
+        cudaFreeAsync(tmp, s);
     }
     gn->last_prec = DI_FP64;
     gn->last_trace_on = o.trace ? 1 : 0;
-    const int slot = o.select ? 3 + 2 * (o.select - 1) : 0;
     return solve_impl<double>(gn, o, gn->F64, slot, kInitState, nullptr, nullptr, 0, 1.0, H_out, out_dev, st);
 }
 

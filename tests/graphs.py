@@ -69,3 +69,19 @@ def modify(n, row_ptr, col_idx, rng, drop=0.1, add=0.1):
         new = dangling[int(rng.integers(0, len(dangling)))]
         keep += [(new, int(rng.integers(0, n))) for _ in range(3)]
     return csr(n, keep)
+
+
+def hub_graph(n, hubs, rng, max_deg=4):
+    """A random graph plus `hubs` nodes that link to and from every other node: the ALGO-OP
+    weights 1/((#in+1)(#out+1)) then span several orders of magnitude."""
+    edges = []
+    for h in range(hubs):
+        for j in range(n):
+            if j != h:
+                edges.append((h, j))
+                edges.append((j, h))
+    rp0, ci0 = random_graph(n, 0.1, max_deg, rng)
+    for i in range(n):
+        for j in ci0[rp0[i]:rp0[i + 1]]:
+            edges.append((i, int(j)))
+    return csr(n, edges)

@@ -189,3 +189,20 @@ def test_select_is_validated(di):
     with di.DiGraph(n, rp, ci, D) as G:
         with pytest.raises(di.DiError, match="select"):
             G.solve(1e-6, select=3)
+
+
+# ------------------------------------------------------------------ autotuner
+
+def test_autotune_picks_a_valid_fastest_candidate(di):
+    n, rp, ci = SEL_CASES["zipf_2e14"]
+    V = gg.uniform_v(n)
+    with di.DiGraph(n, rp, ci, D) as G:
+        best, tried = G.autotune(1e-10)
+        assert len(tried) == 45
+        assert best["ms"] == min(t["ms"] for t in tried if t["ms"] >= 0)
+        assert {t["select"] for t in tried} == {0, 1, 2}
+        assert {t["push_ctas_per_sm"] for t in tried} == {2, 4, 8}
+        # the tuned settings give a correct solve
+        H, st = G.solve(1e-12, beta=best["beta"], select=best["select"])
+    r = oracle.diter(n, rp, ci, D, V, 1e-13, mode="sweep")
+    assert np.abs(H - r.H).sum() <= st["bound"] + 1e-12

@@ -75,3 +75,25 @@ def test_unit_draws_uniform():
     u = np.array([gg.unit_draw(1, 7, k) for k in range(20000)])
     assert 0 <= u.min() and u.max() < 1
     assert abs(u.mean() - 0.5) < 0.01
+
+
+def test_modify_is_seeded_and_keeps_row_order():
+    g = gg.rmat_graph(10, 8, seed=4)
+    a = gg.modify(g, 0.1, 200, seed=9)
+    b = gg.modify(g, 0.1, 200, seed=9)
+    assert np.array_equal(a.row_ptr, b.row_ptr) and np.array_equal(a.col_idx, b.col_idx)
+    kept = 0
+    for i in range(g.n):
+        old = g.col_idx[g.row_ptr[i]:g.row_ptr[i + 1]].tolist()
+        new = a.col_idx[a.row_ptr[i]:a.row_ptr[i + 1]].tolist()
+        # the kept edges are a subsequence of the old row, the rest are appended extras
+        it = iter(old)
+        k = 0
+        while k < len(new) and any(x == new[k] for x in it):
+            k += 1
+        kept += k
+        assert all(0 <= j < g.n for j in new)
+    assert a.nnz - kept <= 200 + 0 and kept <= g.nnz
+    assert abs((g.nnz - kept) / g.nnz - 0.1) < 0.03
+    c = gg.modify(g, 0.0, 0, seed=1)
+    assert np.array_equal(c.row_ptr, g.row_ptr) and np.array_equal(c.col_idx, g.col_idx)

@@ -34,6 +34,7 @@ MUTANTS = {
     "signed_fluid_never_selected": ("if (!wsel) return fabs(f) > T;", "if (!wsel) return f > T;"),
     "op_argmax_ignores_weight": ("return wsel ? fabs(F[i]) * (double)wsel[i] : fabs(F[i]);", "return fabs(F[i]);"),
     "op_sweep_ignores_scale": ("float t = (float)(T * wscale);", "float t = (float)T;"),
+    "op_threshold_raised": ("else if (wsel) T = fmin(T, beta * R / (double)n);", "else if (wsel) T = beta * R / (double)n;"),
 }
 
 
@@ -68,7 +69,12 @@ def _battery(lib):
         ok &= bool(r1.R >= r1.l1F - 1e-15)
     # ALGO-OP / OP2 (Section 4.3): first argmax pick, first weighted sweep, convergence
     F0 = (1 - D) * V
+    rph, cih = graphs.hub_graph(80, 3, np.random.default_rng(0))
+    Vh = graphs.random_v(80, np.random.default_rng(1))
     for sel in ("op", "op2"):
+        tr = np.zeros((100000, 3))
+        r = oracle.diter(80, rph, cih, D, Vh, 1e-10, mode="sweep", max_pushes=400000, lib=lib, select=sel, trace=tr)
+        ok &= bool(r.converged and np.all(np.diff(tr[:r.sweeps, 0]) <= 0))
         w, wscale = oracle.selection_weights(n, rp, ci, sel)
         i_star = int(np.argmax(np.abs(F0) * w.astype(np.float64)))
         r = oracle.diter(n, rp, ci, D, V, 0.0, mode="max", max_pushes=1, lib=lib, select=sel)

@@ -402,3 +402,38 @@ def test_op_orders_reach_the_fixed_point(sel, mode):
         assert r.converged
         assert np.abs(X - r.H).sum() <= r.l1F / (1 - D) + 1e-13
         assert np.all(r.H <= X + 1e-15)
+
+
+@pytest.mark.parametrize("sel", [None, "op", "op2"])
+def test_threshold_schedule(sel):
+    """T_0 = beta R_0/N; after an empty sweep T/2; after a non-empty one beta R/N, or with weights
+    min(T, beta R/N) (never raised).  The sweep's set is {i : |F_i| > T} or, weighted,
+    {i : (float)|F_i| w_i > (float)(T wscale)}; checked on the recorded (T, R, count) of every sweep."""
+    rng = np.random.default_rng(0)
+    n = 80
+    rp, ci = graphs.hub_graph(n, 3, rng)
+    V = graphs.random_v(n, rng)
+    tr = np.zeros((100000, 3))
+    r = oracle.diter(n, rp, ci, D, V, 1e-11, mode="sweep", select=sel, trace=tr)
+    assert r.converged
+    T, R, cnt = tr[:r.sweeps, 0], tr[:r.sweeps, 1], tr[:r.sweeps, 2]
+    assert T[0] == 0.5 * (1 - D) / n
+    for k in range(r.sweeps - 1):
+        if cnt[k] == 0:
+            assert T[k + 1] == T[k] / 2
+        elif sel is None:
+            assert T[k + 1] == 0.5 * R[k + 1] / n
+        else:
+            assert T[k + 1] == min(T[k], 0.5 * R[k + 1] / n)
+    if sel is not None:
+        assert np.all(np.diff(T) <= 0)
+    if sel == "op":
+        assert (cnt == 0).any(), "the ALGO-OP run should meet empty sweeps on this graph"
+    # the first sweep's set, replayed from F_0
+    F0 = (1 - D) * V
+    if sel is None:
+        S1 = np.flatnonzero(np.abs(F0) > T[0])
+    else:
+        w, wscale = oracle.selection_weights(n, rp, ci, sel)
+        S1 = np.flatnonzero(np.float32(np.abs(F0)) * w > np.float32(T[0] * wscale))
+    assert cnt[0] == len(S1)
