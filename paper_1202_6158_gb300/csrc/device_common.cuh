@@ -19,6 +19,13 @@ __device__ __forceinline__ void red_add(double *p, double v) {
 __device__ __forceinline__ void red_add(float *p, float v) {
     asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v));
 }
+// the same with an L2 eviction policy (evict_last keeps the updated lines of F and H in L2)
+__device__ __forceinline__ void red_add(double *p, double v, unsigned long long pol) {
+    asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol));
+}
+__device__ __forceinline__ void red_add(float *p, float v, unsigned long long pol) {
+    asm volatile("red.global.add.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol));
+}
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -46,6 +53,11 @@ __device__ T block_sum(T v, T *sh) {
 // pass over all of F does not push the push kernel's working set out of L2.  (F is
 // written by the scan itself, so its loads stay on the coherent path; the class
 // bytes are read-only.)
+__device__ __forceinline__ unsigned long long evict_last_policy() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
 __device__ __forceinline__ unsigned long long evict_first_policy() {
     unsigned long long p;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));

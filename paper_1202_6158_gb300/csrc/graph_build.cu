@@ -426,6 +426,25 @@ di_status validate_v(di_graph *g, const double *V_dev) {
     return DI_OK;
 }
 
+// 64-bit fingerprint of every input row (its out-degree and its targets in order), kept in
+// input numbering: a graph update compares the fingerprints of two graphs to find the rows
+// whose out-links changed (Section 3.2: only those rows inject fluid).  SplitMix64 mixing.
+__device__ __forceinline__ unsigned long long fp_mix(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_row_hash(int n, const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
+                           unsigned long long *__restrict__ out) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int beg = row_ptr[v], end = row_ptr[v + 1];
+        unsigned long long h = fp_mix(0x243f6a8885a308d3ull ^ (unsigned long long)(end - beg));
+        for (int e = beg; e < end; ++e) h = fp_mix(h + 0x9e3779b97f4a7c15ull + (unsigned long long)(unsigned)col_idx[e]);
+        out[v] = h;
+    }
+}
+
 di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_dev) {
     cudaStream_t s = g->stream;
     const int n = g->n;
@@ -451,6 +470,8 @@ di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_de
         if (hf & kNotMonotone) return set_error(DI_EINVAL, "row_ptr must be non-decreasing");
         if (hf & kColRange) return set_error(DI_EINVAL, "col_idx has an entry outside [0, n)");
     }
+    DI_CUDA(cudaMallocAsync(&g->rowhash, sizeof(unsigned long long) * (size_t)n, s));
+    k_row_hash<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, g->row_ptr, g->col_idx, g->rowhash);
 
     // 1b. internal numbering: the hot targets -- the kHotSlots largest in-degrees (at least
     //     kHotMinInDeg), ties by lower input id, found by a stable LSD radix sort -- become ids

@@ -44,7 +44,7 @@ constexpr int kExactEvery = 4;          // the scan sums |F|_1 exactly every thi
 constexpr int kHotSlots = 256;          // most-linked-to targets accumulated in shared memory by the push
 constexpr int kHotMinInDeg = 32;        // a target needs at least this many in-links to get a slot
 
-// one selected node of a sweep and the fluid it hands over
+// one selected node of a sweep that has out-links, and the fluid it hands over
 template <typename FT>
 struct __align__(16) Sel {
     int node;
@@ -209,6 +209,7 @@ struct di_graph {
     int n_long_tasks = 0;
     int *hot_ids = nullptr;            // [kHotSlots] input id of each hot target (internal ids 0..n_hot-1)
     int n_hot = 0;
+    unsigned long long *rowhash = nullptr;  // [n] fingerprint of each input row (input numbering)
     int *perm = nullptr;               // [n] internal -> input id
     int *new_of = nullptr;             // [n] input -> internal id
 
@@ -228,6 +229,7 @@ struct di_graph {
     diter::SolveState *st = nullptr;
     di_sweep_record *trace = nullptr;
     int last_prec = -1;
+    int changed_rows = 0;              // rows whose out-links differed in the last graph update
     int last_trace_on = 0;
     di_profile prof = {};
     float *sweep_ms = nullptr;         // host: [kTraceCap][2] scan and push event times of a profiled solve

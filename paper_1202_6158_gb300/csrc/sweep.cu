@@ -5,16 +5,17 @@
 //
 //   k_sweep_scan<FT>   streams F and the one-byte out-degree class of every node
 //                      (no dependent loads, no block barriers).  It sums |F|_1 in
-//                      exact 64-bit fixed point, selects S = {i : F_i > T} (for
+//                      exact 64-bit fixed point, selects S = {i : |F_i| > T} (for
 //                      FP64 an integer compare of the bit patterns), zeroes F_i for
-//                      the selected nodes and appends (i, sent) to the list of the
-//                      node's class, in ascending id, with warp prefix sums; each
-//                      warp writes at offsets fixed at create time, so there are
-//                      no atomics.  It also sums the removed mass: (1-d)*sent for
-//                      nodes with children, sent for dangling ones (Section 3.3).
-//   k_sweep_push<FT>   adds sent to H_i (the J_i F step of Section 2.2) and pushes
-//                      d*sent/outdeg_i along every out-link (ALGO-REF's inner loop)
-//                      with red.global.add; a CTA per node above kOutCut2
+//                      the selected nodes, adds sent to H_i (the J_i F step of
+//                      Section 2.2, a red.add in node order) and appends (i, sent)
+//                      of the nodes with children to the list of the node's class,
+//                      in ascending id, with warp prefix sums; each warp writes at
+//                      offsets fixed at create time, so there are no atomics.  It
+//                      also sums the removed mass: (1-d)*sent for nodes with
+//                      children, sent for dangling ones (Section 3.3).
+//   k_sweep_push<FT>   pushes d*sent/outdeg_i along every out-link (ALGO-REF's inner
+//                      loop) with red.global.add; a CTA per node above kOutCut2
 //                      out-links, a warp per node above kOutCut1, a lane per node
 //                      otherwise; 128-bit column-index loads; the most-linked-to
 //                      targets are summed in shared memory first.
@@ -43,10 +44,6 @@
 
 namespace diter {
 namespace {
-
-template <typename FT> struct Vec;
-template <> struct Vec<double> { using T = double2; static constexpr int N = 2; };
-template <> struct Vec<float> { using T = float4; static constexpr int N = 4; };
 
 // ------------------------------------------------------------------- init
 
@@ -202,7 +199,8 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
                                                              int *__restrict__ fcount, int *__restrict__ pre,
                                                              unsigned *__restrict__ ticket, Sel<FT> *__restrict__ sel,
                                                              ScanPartial *__restrict__ part,
-                                                             const SolveState *__restrict__ st) {
+                                                             const SolveState *__restrict__ st,
+                                                             double *__restrict__ H) {
     using Ops = ScanOps<FT>;
     __shared__ long long s_red[kWarps];
     __shared__ unsigned s_ticket;
@@ -223,7 +221,7 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
     FT cur[4], nxt[4];
     unsigned ccur, cnxt = 0;
     float4 wcur = make_float4(0.f, 0.f, 0.f, 0.f), wnxt = wcur;
-    const unsigned long long pol = evict_first_policy();
+    const unsigned long long pol = evict_first_policy(), pol_h = evict_last_policy();
     Ops::load4(F + wbeg + 4 * lane, cur, pol);
     ccur = ld_stream(reinterpret_cast<const unsigned *>(cls + wbeg + 4 * lane), pol);
     if (WGT) wcur = ld_stream(reinterpret_cast<const float4 *>(wsel + wbeg + 4 * lane), pol);
@@ -251,11 +249,16 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
                 const int c = (ccur >> (8 * k)) & 0xff;
                 any = true;
                 srcs += 1;
-                lst[k] = c;
-                packed += 1u << (8 * c);
                 cur[k] = (FT)0;                 // J_i F leaves F ...
-                if (c == 0) s_dng += fx;        // ... and a dangling node's fluid leaves the system (Section 3.3)
-                else { s_out += fx; entries += 1; }
+                red_add(H + i0 + k, (double)sent[k], pol_h);  // ... into the history (H' = H + J_S F)
+                if (c == 0) {
+                    s_dng += fx;                // a dangling node's fluid leaves the system (Section 3.3)
+                } else {
+                    s_out += fx;
+                    entries += 1;
+                    lst[k] = c;                 // nodes with children go to the push lists
+                    packed += 1u << (8 * c);
+                }
             }
         }
         if (any) Ops::store4(F + i0, cur);
@@ -332,8 +335,9 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
 // power-law graphs a single target can receive a few percent of all pushes, and
 // same-address reductions serialize in one L2 slice.
 template <typename FT>
-__device__ __forceinline__ void push_one(FT *__restrict__ F, FT *hot, int n_hot, int c, FT w) {
-    if (c >= n_hot) red_add(F + c, w);
+__device__ __forceinline__ void push_one(FT *__restrict__ F, FT *hot, int n_hot, int c, FT w,
+                                         unsigned long long pol) {
+    if (c >= n_hot) red_add(F + c, w, pol);
     else atomicAdd(hot + c, w);
 }
 
@@ -342,47 +346,46 @@ __device__ __forceinline__ void push_one(FT *__restrict__ F, FT *hot, int n_hot,
 // then the tail.
 template <typename FT>
 __device__ __forceinline__ void push_row_lanes(const int *__restrict__ col_idx, FT *__restrict__ F, FT *hot, int n_hot,
-                                               int beg, int deg, FT w, int lane, int width) {
+                                               int beg, int deg, FT w, int lane, int width, unsigned long long pol) {
     const int head = min(deg, (4 - (beg & 3)) & 3);
-    if (lane < head) push_one(F, hot, n_hot, __ldg(col_idx + beg + lane), w);
+    if (lane < head) push_one(F, hot, n_hot, __ldg(col_idx + beg + lane), w, pol);
     const int body = (deg - head) >> 2;
     const int4 *v4 = reinterpret_cast<const int4 *>(col_idx + beg + head);
     int k = lane;
     for (; k + width < body; k += 2 * width) {
         const int4 q = __ldg(v4 + k);
         const int4 r = __ldg(v4 + k + width);
-        push_one(F, hot, n_hot, q.x, w);
-        push_one(F, hot, n_hot, q.y, w);
-        push_one(F, hot, n_hot, q.z, w);
-        push_one(F, hot, n_hot, q.w, w);
-        push_one(F, hot, n_hot, r.x, w);
-        push_one(F, hot, n_hot, r.y, w);
-        push_one(F, hot, n_hot, r.z, w);
-        push_one(F, hot, n_hot, r.w, w);
+        push_one(F, hot, n_hot, q.x, w, pol);
+        push_one(F, hot, n_hot, q.y, w, pol);
+        push_one(F, hot, n_hot, q.z, w, pol);
+        push_one(F, hot, n_hot, q.w, w, pol);
+        push_one(F, hot, n_hot, r.x, w, pol);
+        push_one(F, hot, n_hot, r.y, w, pol);
+        push_one(F, hot, n_hot, r.z, w, pol);
+        push_one(F, hot, n_hot, r.w, w, pol);
     }
     if (k < body) {
         const int4 q = __ldg(v4 + k);
-        push_one(F, hot, n_hot, q.x, w);
-        push_one(F, hot, n_hot, q.y, w);
-        push_one(F, hot, n_hot, q.z, w);
-        push_one(F, hot, n_hot, q.w, w);
+        push_one(F, hot, n_hot, q.x, w, pol);
+        push_one(F, hot, n_hot, q.y, w, pol);
+        push_one(F, hot, n_hot, q.z, w, pol);
+        push_one(F, hot, n_hot, q.w, w, pol);
     }
     const int t = head + 4 * body + lane;
-    if (t < deg) push_one(F, hot, n_hot, __ldg(col_idx + beg + t), w);
+    if (t < deg) push_one(F, hot, n_hot, __ldg(col_idx + beg + t), w, pol);
 }
 
-// The push.  The selected nodes of each class are numbered 0..total-1 through the
-// prefix sums of the scan, and spread over the whole grid: a CTA per node of the
-// largest class, a warp per node of the middle class, and for the smallest class
-// and the dangling nodes contiguous ranges of 64 per warp (a lane per node, two in
-// flight).  For every selected node i it adds sent to H_i (the J_i F step of
-// Section 2.2) and, unless i is dangling, adds d*sent/outdeg(i) to F_j along every
-// out-link (ALGO-REF's inner loop), every load of a node issued before its
-// reductions.
+// The push.  The selected nodes with children of each class are numbered
+// 0..total-1 through the prefix sums of the scan, and spread over the whole grid: a
+// CTA per node of the largest class, a warp per node of the middle class, and for
+// the smallest class contiguous ranges of 64 per warp (a lane per node, two in
+// flight).  The scan already moved each node's fluid into H; the push adds
+// d*sent/outdeg(i) to F_j along every out-link (ALGO-REF's inner loop), every load
+// of a node issued before its reductions.
 template <typename FT>
 __global__ void __launch_bounds__(kScanThreads) k_sweep_push(const RowRec<FT> *__restrict__ rec,
                                                              const int *__restrict__ col_idx, FT *__restrict__ F,
-                                                             double *__restrict__ H, const int *__restrict__ region,
+                                                             const int *__restrict__ region,
                                                              const int *__restrict__ pre, int W,
                                                              const Sel<FT> *__restrict__ sel, int n_hot,
                                                              ScanPartial *__restrict__ part, int G,
@@ -393,9 +396,10 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_push(const RowRec<FT> *_
     if (st->done) return;
     for (int t = threadIdx.x; t < kHotSlots; t += kScanThreads) hot[t] = (FT)0;
     __syncthreads();
+    const unsigned long long pol = evict_last_policy();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nwarps = gridDim.x * kWarps, gw = blockIdx.x * kWarps + w;
-    const int *pre3 = pre + 3 * (W + 1), *pre2 = pre + 2 * (W + 1), *pre1 = pre + 1 * (W + 1), *pre0 = pre;
+    const int *pre3 = pre + 3 * (W + 1), *pre2 = pre + 2 * (W + 1), *pre1 = pre + 1 * (W + 1);
     long long edges = 0;
     // class 3: the whole CTA per node
     const int tot3 = __ldg(pre3 + W);
@@ -408,13 +412,8 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_push(const RowRec<FT> *_
         const Sel<FT> e = sel[s_idx];
         __syncthreads();
         const RowRec<FT> rr = rec[e.node];
-        const int b = rr.beg, deg = rr.deg;
-        const FT wv = e.sent * rr.inv;
-        if (threadIdx.x == 0) {
-            H[e.node] += (double)e.sent;
-            edges += deg;
-        }
-        push_row_lanes(col_idx, F, hot, n_hot, b, deg, wv, threadIdx.x, kScanThreads);
+        if (threadIdx.x == 0) edges += rr.deg;
+        push_row_lanes(col_idx, F, hot, n_hot, rr.beg, rr.deg, e.sent * rr.inv, threadIdx.x, kScanThreads, pol);
     }
     // class 2: a warp per node
     const int tot2 = __ldg(pre2 + W);
@@ -427,29 +426,8 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_push(const RowRec<FT> *_
         idx = __shfl_sync(kFull, idx, 0);
         const Sel<FT> e = sel[idx];
         const RowRec<FT> rr = rec[e.node];
-        const int b = rr.beg, deg = rr.deg;
-        const FT wv = e.sent * rr.inv;
-        if (lane == 0) {
-            H[e.node] += (double)e.sent;
-            edges += deg;
-        }
-        push_row_lanes(col_idx, F, hot, n_hot, b, deg, wv, lane, 32);
-    }
-    // class 0: dangling nodes only move their fluid into H; a contiguous range per warp
-    {
-        const int tot0 = __ldg(pre0 + W);
-        const int per = (tot0 + nwarps - 1) / nwarps;
-        const int t_beg = min(tot0, gw * per), t_end = min(tot0, t_beg + per);
-        int gl = 0;
-        if (t_beg < t_end) {
-            if (lane == 0) gl = find_sub(pre0, W, t_beg);
-            gl = __shfl_sync(kFull, gl, 0);
-        }
-        for (int t = t_beg + lane; t < t_end; t += 32) {
-            while (__ldg(pre0 + gl + 1) <= t) ++gl;
-            const Sel<FT> e = sel[region[0 * (W + 1) + gl] + (t - __ldg(pre0 + gl))];
-            H[e.node] += (double)e.sent;
-        }
+        if (lane == 0) edges += rr.deg;
+        push_row_lanes(col_idx, F, hot, n_hot, rr.beg, rr.deg, e.sent * rr.inv, lane, 32, pol);
     }
     // class 1: a lane per node, two nodes in flight, a contiguous range per warp
     {
@@ -477,21 +455,17 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_push(const RowRec<FT> *_
             const int b0 = r0.beg, d0 = r0.deg;
             const int b1 = r1.beg, d1 = has1 ? r1.deg : 0;
             const FT w0 = e0.sent * r0.inv, w1 = e1.sent * r1.inv;
-            const double h0 = H[e0.node];
-            const double h1 = has1 ? H[e1.node] : 0.0;
             int c0[kOutCut1], c1[kOutCut1];
 #pragma unroll
             for (int k = 0; k < kOutCut1; ++k) {
                 c0[k] = k < d0 ? __ldg(col_idx + b0 + k) : 0;
                 c1[k] = k < d1 ? __ldg(col_idx + b1 + k) : 0;
             }
-            H[e0.node] = h0 + (double)e0.sent;
-            if (has1) H[e1.node] = h1 + (double)e1.sent;
             edges += d0 + d1;
 #pragma unroll
             for (int k = 0; k < kOutCut1; ++k) {
-                if (k < d0) push_one(F, hot, n_hot, c0[k], w0);
-                if (k < d1) push_one(F, hot, n_hot, c1[k], w1);
+                if (k < d0) push_one(F, hot, n_hot, c0[k], w0, pol);
+                if (k < d1) push_one(F, hot, n_hot, c1[k], w1, pol);
             }
         }
     }
@@ -638,9 +612,6 @@ __global__ void k_gather_out(int n, const int *__restrict__ new_of, const FT *__
         out[i] = (double)src[new_of[i]] * scale;
 }
 
-template <typename FT> const FT *inv_deg_of(di_graph *g);
-template <> const double *inv_deg_of<double>(di_graph *g) { return g->inv_deg; }
-template <> const float *inv_deg_of<float>(di_graph *g) { return g->inv_deg32; }
 template <typename FT> const RowRec<FT> *rec_of(di_graph *g);
 template <> const RowRec<double> *rec_of<double>(di_graph *g) { return g->rec64; }
 template <> const RowRec<float> *rec_of<float>(di_graph *g) { return g->rec32; }
@@ -651,17 +622,17 @@ void launch_scan(di_graph *g, FT *F, const float *wsel, cudaStream_t s) {
     if (wsel)
         k_sweep_scan<FT, true><<<g->G, kScanThreads, 0, s>>>(g->chunk / kWarps, F, wsel, g->cls, g->region, g->W,
                                                              g->fcount, g->pre, g->ticket, sel_of<FT>(g), g->part,
-                                                             g->st);
+                                                             g->st, g->H);
     else
         k_sweep_scan<FT, false><<<g->G, kScanThreads, 0, s>>>(g->chunk / kWarps, F, nullptr, g->cls, g->region, g->W,
                                                               g->fcount, g->pre, g->ticket, sel_of<FT>(g), g->part,
-                                                              g->st);
+                                                              g->st, g->H);
 }
 
 template <typename FT>
 void launch_push(di_graph *g, FT *F, cudaStream_t s) {
-    k_sweep_push<FT><<<push_grid(g), kScanThreads, 0, s>>>(rec_of<FT>(g), g->col_idx, F, g->H, g->region, g->pre,
-                                                           g->W, sel_of<FT>(g), g->n_hot, g->part, g->G, g->st);
+    k_sweep_push<FT><<<push_grid(g), kScanThreads, 0, s>>>(rec_of<FT>(g), g->col_idx, F, g->region, g->pre, g->W,
+                                                           sel_of<FT>(g), g->n_hot, g->part, g->G, g->st);
 }
 
 int elem_grid(di_graph *g, long long work) {
@@ -932,40 +903,52 @@ __global__ void k_map_state(int n, const int *__restrict__ perm_old, const int *
     }
 }
 
-// F[j] += sign * H_i * d/outdeg(i) for every out-link i -> j of one graph, in its own numbering.
-// A thread takes a node with up to 32 out-links; longer rows are queued in shared memory and
-// walked by a warp each.
-__global__ void __launch_bounds__(256) k_inject(int n, const RowRec<double> *__restrict__ rec,
-                                                const int *__restrict__ col_idx, const double *__restrict__ H,
-                                                double sign, double *__restrict__ F) {
+// The injection F_0' = F + d(P' - P)H, row by row.  Rows whose fingerprints agree are the same
+// in both graphs and cancel; a changed row of input node v takes back H_v d/#out_old along its
+// old out-links (targets mapped into the new numbering) and adds H_v d/#out_new along its new
+// ones.  A thread takes a node whose rows have up to 32 out-links; longer ones are queued in
+// shared memory and walked by a warp each.
+struct InjectArgs {
+    int n;
+    const unsigned long long *hash_old, *hash_new;
+    const int *new_of_old, *perm_old, *new_of_new;
+    const RowRec<double> *rec_old, *rec_new;
+    const int *col_old, *col_new;
+    const double *H;   // new numbering
+    double *F;         // new numbering
+};
+
+__device__ __forceinline__ void inject_row(const InjectArgs &a, int v, int lane, int width) {
+    const int ro = a.new_of_old[v], rn = a.new_of_new[v];
+    const double h = a.H[rn];
+    if (h == 0.0) return;
+    const RowRec<double> o = a.rec_old[ro], w = a.rec_new[rn];
+    const double vo = -h * o.inv, vn = h * w.inv;
+    for (int e = lane; e < o.deg; e += width) atomicAdd(a.F + a.new_of_new[a.perm_old[a.col_old[o.beg + e]]], vo);
+    for (int e = lane; e < w.deg; e += width) atomicAdd(a.F + a.col_new[w.beg + e], vn);
+}
+
+__global__ void __launch_bounds__(256) k_inject_changed(InjectArgs a, int *__restrict__ changed) {
     __shared__ int s_long[256];
     __shared__ int s_nlong;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < n; base += (long long)gridDim.x * blockDim.x) {
+    int mine = 0;
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < a.n; base += (long long)gridDim.x * blockDim.x) {
         if (threadIdx.x == 0) s_nlong = 0;
         __syncthreads();
-        const long long i = base + threadIdx.x;
-        if (i < n) {
-            const RowRec<double> rr = rec[i];
-            const double v = rr.deg > 0 ? sign * H[i] * rr.inv : 0.0;
-            if (v != 0.0) {
-                if (rr.deg <= 32) {
-                    for (int e = 0; e < rr.deg; ++e) atomicAdd(F + col_idx[rr.beg + e], v);
-                } else {
-                    s_long[atomicAdd(&s_nlong, 1)] = (int)i;
-                }
-            }
+        const long long v = base + threadIdx.x;
+        if (v < a.n && a.hash_old[v] != a.hash_new[v]) {
+            mine += 1;
+            const int dl = max(a.rec_old[a.new_of_old[v]].deg, a.rec_new[a.new_of_new[v]].deg);
+            if (dl <= 32) inject_row(a, (int)v, 0, 1);
+            else s_long[atomicAdd(&s_nlong, 1)] = (int)v;
         }
         __syncthreads();
         const int nl = s_nlong;
-        for (int k = wid; k < nl; k += nwarp) {
-            const int i2 = s_long[k];
-            const RowRec<double> rr = rec[i2];
-            const double v = sign * H[i2] * rr.inv;
-            for (int e = lane; e < rr.deg; e += 32) atomicAdd(F + col_idx[rr.beg + e], v);
-        }
+        for (int k = wid; k < nl; k += nwarp) inject_row(a, s_long[k], lane, 32);
         __syncthreads();
     }
+    if (mine) atomicAdd(changed, mine);
 }
 
 }  // namespace
@@ -1002,20 +985,30 @@ di_status run_update(di_graph *go, di_graph *gn, const di_solve_opts &o, double 
     if (go != gn) {
         cudaStream_t s = gn->stream;
         const int npad = gn->G * gn->chunk;
-        // F_0' = F + d P' H - d P H.  The old graph's pushes of H are taken back in the old
-        // numbering (tmp = F - dPH), the state is mapped into the new numbering, and the new
-        // graph's pushes of H are added there.
-        double *tmp = nullptr;
-        DI_CUDA(cudaMallocAsync(&tmp, sizeof(double) * (size_t)n, s));
-        DI_CUDA(cudaMemcpyAsync(tmp, go->F64, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
-        const int gi = std::max(1, std::min(ceil_div(n, 256), gn->num_sms * 8));
-        k_inject<<<gi, 256, 0, s>>>(n, go->rec64, go->col_idx, go->H, -1.0, tmp);
+        // the state in the new numbering, then F_0' = F + d(P' - P)H over the changed rows only
         DI_CUDA(cudaMemsetAsync(gn->F64, 0, sizeof(double) * (size_t)npad, s));
         DI_CUDA(cudaMemsetAsync(gn->H, 0, sizeof(double) * (size_t)npad, s));
-        k_map_state<<<elem_grid(gn, n), 256, 0, s>>>(n, go->perm, gn->new_of, tmp, go->H, gn->F64, gn->H);
-        k_inject<<<gi, 256, 0, s>>>(n, gn->rec64, gn->col_idx, gn->H, 1.0, gn->F64);
+        k_map_state<<<elem_grid(gn, n), 256, 0, s>>>(n, go->perm, gn->new_of, go->F64, go->H, gn->F64, gn->H);
+        InjectArgs a;
+        a.n = n;
+        a.hash_old = go->rowhash;
+        a.hash_new = gn->rowhash;
+        a.new_of_old = go->new_of;
+        a.perm_old = go->perm;
+        a.new_of_new = gn->new_of;
+        a.rec_old = go->rec64;
+        a.rec_new = gn->rec64;
+        a.col_old = go->col_idx;
+        a.col_new = gn->col_idx;
+        a.H = gn->H;
+        a.F = gn->F64;
+        int *changed = nullptr;
+        DI_CUDA(cudaMallocAsync(&changed, sizeof(int), s));
+        DI_CUDA(cudaMemsetAsync(changed, 0, sizeof(int), s));
+        k_inject_changed<<<std::max(1, std::min(ceil_div(n, 256), gn->num_sms * 8)), 256, 0, s>>>(a, changed);
         DI_CUDA(cudaGetLastError());
-        cudaFreeAsync(tmp, s);
+        DI_CUDA(cudaMemcpyAsync(&gn->changed_rows, changed, sizeof(int), cudaMemcpyDeviceToHost, s));
+        cudaFreeAsync(changed, s);
     }
     gn->last_prec = DI_FP64;
     gn->last_trace_on = o.trace ? 1 : 0;
