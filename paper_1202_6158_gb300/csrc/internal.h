@@ -229,7 +229,6 @@ struct di_graph {
     diter::SolveState *st = nullptr;
     di_sweep_record *trace = nullptr;
     int last_prec = -1;
-    int changed_rows = 0;              // rows whose out-links differed in the last graph update
     int last_trace_on = 0;
     di_profile prof = {};
     float *sweep_ms = nullptr;         // host: [kTraceCap][2] scan and push event times of a profiled solve

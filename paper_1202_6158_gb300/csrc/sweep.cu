@@ -905,17 +905,18 @@ __global__ void k_map_state(int n, const int *__restrict__ perm_old, const int *
 
 // The injection F_0' = F + d(P' - P)H, row by row.  Rows whose fingerprints agree are the same
 // in both graphs and cancel; a changed row of input node v takes back H_v d/#out_old along its
-// old out-links (targets mapped into the new numbering) and adds H_v d/#out_new along its new
-// ones.  A thread takes a node whose rows have up to 32 out-links; longer ones are queued in
-// shared memory and walked by a warp each.
+// old out-links (targets renumbered by old_to_new) and adds H_v d/#out_new along its new ones.
 struct InjectArgs {
     int n;
     const unsigned long long *hash_old, *hash_new;
-    const int *new_of_old, *perm_old, *new_of_new;
+    const int *new_of_old, *new_of_new;
+    const int *old_to_new;  // [n] old internal id -> new internal id
     const RowRec<double> *rec_old, *rec_new;
     const int *col_old, *col_new;
-    const double *H;   // new numbering
-    double *F;         // new numbering
+    const double *H;        // new numbering
+    double *F;              // new numbering
+    int *long_rows;         // changed rows with more than 32 out-links in either graph
+    int *n_long;
 };
 
 __device__ __forceinline__ void inject_row(const InjectArgs &a, int v, int lane, int width) {
@@ -924,31 +925,30 @@ __device__ __forceinline__ void inject_row(const InjectArgs &a, int v, int lane,
     if (h == 0.0) return;
     const RowRec<double> o = a.rec_old[ro], w = a.rec_new[rn];
     const double vo = -h * o.inv, vn = h * w.inv;
-    for (int e = lane; e < o.deg; e += width) atomicAdd(a.F + a.new_of_new[a.perm_old[a.col_old[o.beg + e]]], vo);
+    for (int e = lane; e < o.deg; e += width) atomicAdd(a.F + a.old_to_new[a.col_old[o.beg + e]], vo);
     for (int e = lane; e < w.deg; e += width) atomicAdd(a.F + a.col_new[w.beg + e], vn);
 }
 
-__global__ void __launch_bounds__(256) k_inject_changed(InjectArgs a, int *__restrict__ changed) {
-    __shared__ int s_long[256];
-    __shared__ int s_nlong;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    int mine = 0;
-    for (long long base = (long long)blockIdx.x * blockDim.x; base < a.n; base += (long long)gridDim.x * blockDim.x) {
-        if (threadIdx.x == 0) s_nlong = 0;
-        __syncthreads();
-        const long long v = base + threadIdx.x;
-        if (v < a.n && a.hash_old[v] != a.hash_new[v]) {
-            mine += 1;
-            const int dl = max(a.rec_old[a.new_of_old[v]].deg, a.rec_new[a.new_of_new[v]].deg);
-            if (dl <= 32) inject_row(a, (int)v, 0, 1);
-            else s_long[atomicAdd(&s_nlong, 1)] = (int)v;
-        }
-        __syncthreads();
-        const int nl = s_nlong;
-        for (int k = wid; k < nl; k += nwarp) inject_row(a, s_long[k], lane, 32);
-        __syncthreads();
+__global__ void k_old_to_new(int n, const int *__restrict__ perm_old, const int *__restrict__ new_of_new,
+                             int *__restrict__ out) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+        out[r] = new_of_new[perm_old[r]];
+}
+
+// a thread per changed row of up to 32 out-links; longer ones are listed for k_inject_long
+__global__ void k_inject_changed(InjectArgs a) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += gridDim.x * blockDim.x) {
+        if (a.hash_old[v] == a.hash_new[v]) continue;
+        const int dl = max(a.rec_old[a.new_of_old[v]].deg, a.rec_new[a.new_of_new[v]].deg);
+        if (dl <= 32) inject_row(a, v, 0, 1);
+        else a.long_rows[atomicAdd(a.n_long, 1)] = v;
     }
-    if (mine) atomicAdd(changed, mine);
+}
+
+// a CTA per long changed row
+__global__ void k_inject_long(InjectArgs a) {
+    const int cnt = *a.n_long;
+    for (int k = blockIdx.x; k < cnt; k += gridDim.x) inject_row(a, a.long_rows[k], threadIdx.x, blockDim.x);
 }
 
 }  // namespace
@@ -994,7 +994,6 @@ di_status run_update(di_graph *go, di_graph *gn, const di_solve_opts &o, double 
         a.hash_old = go->rowhash;
         a.hash_new = gn->rowhash;
         a.new_of_old = go->new_of;
-        a.perm_old = go->perm;
         a.new_of_new = gn->new_of;
         a.rec_old = go->rec64;
         a.rec_new = gn->rec64;
@@ -1002,13 +1001,24 @@ di_status run_update(di_graph *go, di_graph *gn, const di_solve_opts &o, double 
         a.col_new = gn->col_idx;
         a.H = gn->H;
         a.F = gn->F64;
-        int *changed = nullptr;
-        DI_CUDA(cudaMallocAsync(&changed, sizeof(int), s));
-        DI_CUDA(cudaMemsetAsync(changed, 0, sizeof(int), s));
-        k_inject_changed<<<std::max(1, std::min(ceil_div(n, 256), gn->num_sms * 8)), 256, 0, s>>>(a, changed);
+        // scratch: the composed renumbering, the long-row list (at most L/33 rows of either
+        // graph have more than 32 out-links) and its count
+        const long long cap = (go->nnz + gn->nnz) / 33 + 1;
+        int *o2n = nullptr, *lrows = nullptr, *cnt = nullptr;
+        DI_CUDA(cudaMallocAsync(&o2n, sizeof(int) * (size_t)n, s));
+        DI_CUDA(cudaMallocAsync(&lrows, sizeof(int) * (size_t)cap, s));
+        DI_CUDA(cudaMallocAsync(&cnt, sizeof(int), s));
+        DI_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int), s));
+        a.old_to_new = o2n;
+        a.long_rows = lrows;
+        a.n_long = cnt;
+        k_old_to_new<<<elem_grid(gn, n), 256, 0, s>>>(n, go->perm, gn->new_of, o2n);
+        k_inject_changed<<<elem_grid(gn, n), 256, 0, s>>>(a);
+        k_inject_long<<<gn->num_sms * 4, 256, 0, s>>>(a);
         DI_CUDA(cudaGetLastError());
-        DI_CUDA(cudaMemcpyAsync(&gn->changed_rows, changed, sizeof(int), cudaMemcpyDeviceToHost, s));
-        cudaFreeAsync(changed, s);
+        cudaFreeAsync(o2n, s);
+        cudaFreeAsync(lrows, s);
+        cudaFreeAsync(cnt, s);
     }
     gn->last_prec = DI_FP64;
     gn->last_trace_on = o.trace ? 1 : 0;
