@@ -156,7 +156,6 @@ di_status di_graph_create(int32_t n, const int32_t *row_ptr, const int32_t *col_
     }
     if ((r = build_graph(g, g->row_ptr, g->col_idx)) != DI_OK) return fail(r);
     if ((r = sweep_alloc(g)) != DI_OK) return fail(r);
-    if ((r = power_alloc(g)) != DI_OK) return fail(r);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(cuda_fail(e, "graph create"));
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_fail(e, "graph create"));
     *out = g;
@@ -197,6 +196,10 @@ di_status di_graph_export(const di_graph *g, int32_t *perm, int32_t *outdeg, int
                           int32_t *bin_of, int32_t *in_bin_of, int32_t *cuts) {
     g_last_error.clear();
     if (check_graph(g) != DI_OK) return DI_EINVAL;
+    if (in_ptr || in_src || in_bin_of) {
+        di_status tr = build_transpose(const_cast<di_graph *>(g));  // built on first use
+        if (tr != DI_OK) return tr;
+    }
     cudaStream_t s = g->stream;
     const size_t n = (size_t)g->n;
     if (outdeg) {

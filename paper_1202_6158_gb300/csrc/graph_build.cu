@@ -338,9 +338,41 @@ __global__ void k_expand_rows(int n, long long nnz, const int *__restrict__ row_
     }
 }
 
-__global__ void k_count_in(long long nnz, const int *__restrict__ col_idx, int *__restrict__ indeg) {
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (long long)gridDim.x * blockDim.x)
-        atomicAdd(&indeg[col_idx[e]], 1);
+// In-degrees.  On power-law graphs a few targets take percents of all edges and their
+// global atomics serialize in one L2 slice, so each CTA first counts its tile of kCountTile
+// edges in a small shared-memory hash table (open addressing, a few probes) and adds each
+// table entry to global memory once; targets that find no slot go straight to global memory.
+constexpr int kCountTile = 4096, kCountSlots = 2048, kCountProbes = 4;
+
+__global__ void __launch_bounds__(256) k_count_in(long long nnz, const int *__restrict__ col_idx,
+                                                  int *__restrict__ indeg) {
+    __shared__ int s_key[kCountSlots], s_cnt[kCountSlots];
+    for (long long t0 = (long long)blockIdx.x * kCountTile; t0 < nnz; t0 += (long long)gridDim.x * kCountTile) {
+        for (int k = threadIdx.x; k < kCountSlots; k += blockDim.x) {
+            s_key[k] = -1;
+            s_cnt[k] = 0;
+        }
+        __syncthreads();
+        const long long t1 = min(nnz, t0 + kCountTile);
+        for (long long e = t0 + threadIdx.x; e < t1; e += blockDim.x) {
+            const int j = col_idx[e];
+            unsigned h = ((unsigned)j * 2654435761u) >> 21;  // 11 bits: kCountSlots = 2048
+            bool done = false;
+            for (int p = 0; p < kCountProbes && !done; ++p) {
+                const int slot = (h + p) & (kCountSlots - 1);
+                const int prev = atomicCAS(&s_key[slot], -1, j);
+                if (prev == -1 || prev == j) {
+                    atomicAdd(&s_cnt[slot], 1);
+                    done = true;
+                }
+            }
+            if (!done) atomicAdd(&indeg[j], 1);
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < kCountSlots; k += blockDim.x)
+            if (s_key[k] >= 0) atomicAdd(&indeg[s_key[k]], s_cnt[k]);
+        __syncthreads();
+    }
 }
 
 // key that sorts nodes by in-degree, largest first (a stable sort keeps ascending ids on ties)
@@ -435,14 +467,43 @@ __device__ __forceinline__ unsigned long long fp_mix(unsigned long long z) {
     return z ^ (z >> 31);
 }
 
+// fingerprint = mix(#out, sum over the row's positions p of mix(target_p, p)): the sum lets a
+// warp share a long row; the position term keeps it order-sensitive
+__device__ __forceinline__ unsigned long long fp_edge(int t, int p) {
+    return fp_mix(((unsigned long long)(unsigned)t << 32 | (unsigned)p) + 0x9e3779b97f4a7c15ull);
+}
+
 __global__ void k_row_hash(int n, const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
                            unsigned long long *__restrict__ out) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        const int beg = row_ptr[v], end = row_ptr[v + 1];
-        unsigned long long h = fp_mix(0x243f6a8885a308d3ull ^ (unsigned long long)(end - beg));
-        for (int e = beg; e < end; ++e) h = fp_mix(h + 0x9e3779b97f4a7c15ull + (unsigned long long)(unsigned)col_idx[e]);
-        out[v] = h;
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int w0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; w0 < n; w0 += nw * 32) {
+        const int v = w0 + lane;
+        int beg = 0, deg = 0;
+        unsigned long long acc = 0;
+        if (v < n) {
+            beg = row_ptr[v];
+            deg = row_ptr[v + 1] - beg;
+            if (deg <= 64)
+                for (int p = 0; p < deg; ++p) acc += fp_edge(col_idx[beg + p], p);
+        }
+        // rows above 64 out-links: the whole warp, one row at a time
+        unsigned longs = __ballot_sync(0xffffffffu, v < n && deg > 64);
+        while (longs) {
+            const int src = __ffs(longs) - 1;
+            longs &= longs - 1;
+            const int b = __shfl_sync(0xffffffffu, beg, src), dg = __shfl_sync(0xffffffffu, deg, src);
+            unsigned long long part = 0;
+            for (int p = lane; p < dg; p += 32) part += fp_edge(col_idx[b + p], p);
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            if (lane == src) acc = part;
+        }
+        if (v < n) out[v] = fp_mix(0x243f6a8885a308d3ull ^ (unsigned long long)deg) + acc;
     }
+}
+
+int count_grid(const di_graph *g, long long L) {
+    return (int)std::max(1LL, std::min((L + kCountTile - 1) / kCountTile, (long long)g->num_sms * 8));
 }
 
 di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_dev) {
@@ -471,7 +532,8 @@ di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_de
         if (hf & kColRange) return set_error(DI_EINVAL, "col_idx has an entry outside [0, n)");
     }
     DI_CUDA(cudaMallocAsync(&g->rowhash, sizeof(unsigned long long) * (size_t)n, s));
-    k_row_hash<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, g->row_ptr, g->col_idx, g->rowhash);
+    k_row_hash<<<std::max(1, std::min(ceil_div(n, 256), g->num_sms * 8)), 256, 0, s>>>(n, g->row_ptr, g->col_idx,
+                                                                                    g->rowhash);
 
     // 1b. internal numbering: the hot targets -- the kHotSlots largest in-degrees (at least
     //     kHotMinInDeg), ties by lower input id, found by a stable LSD radix sort -- become ids
@@ -487,7 +549,7 @@ di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_de
         DI_CUDA(cudaMallocAsync(&vb, sizeof(int) * (size_t)n, s));
         DI_CUDA(cudaMallocAsync(&cnt, sizeof(int), s));
         DI_CUDA(cudaMemsetAsync(indeg, 0, sizeof(int) * (size_t)n, s));
-        if (L > 0) k_count_in<<<grid_for(L, 256, g->num_sms), 256, 0, s>>>(L, g->col_idx, indeg);
+        if (L > 0) k_count_in<<<count_grid(g, L), 256, 0, s>>>(L, g->col_idx, indeg);
         k_indeg_key_direct<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, indeg, ka);
         k_iota<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, va);
         for (int p = 0; p < 4; ++p) {
@@ -597,12 +659,28 @@ di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_de
         }
     }
 
+    DI_CUDA(cudaGetLastError());
+    return DI_OK;
+}
+
+// The in-link side (power iteration, exports, ALGO-OP weights), built at its first use:
+// a solve never reads it.
+di_status build_transpose(di_graph *g) {
+    if (g->transposed) return DI_OK;
+    cudaStream_t s = g->stream;
+    // what an earlier attempt that failed part-way left behind
+    void *partial[] = {g->in_ptr, g->in_src, g->in_bin_of, g->pull_ids, g->long_prefix};
+    for (void *b : partial)
+        if (b) cudaFreeAsync(b, s);
+    g->in_ptr = g->in_src = g->in_bin_of = g->pull_ids = g->long_prefix = nullptr;
+    const int n = g->n;
+    const long long L = g->nnz;
     // 3. in-link CSR: stable LSD radix sort of (target, source) pairs in source order
     DI_CUDA(cudaMallocAsync(&g->in_ptr, sizeof(int) * (size_t)(n + 1), s));
     DI_CUDA(cudaMallocAsync(&g->in_src, sizeof(int) * (size_t)std::max<long long>(L, 1), s));
     DI_CUDA(cudaMemsetAsync(g->in_ptr, 0, sizeof(int) * (size_t)(n + 1), s));
     if (L > 0) {
-        k_count_in<<<grid_for(L, 256, g->num_sms), 256, 0, s>>>(L, g->col_idx, g->in_ptr);
+        k_count_in<<<count_grid(g, L), 256, 0, s>>>(L, g->col_idx, g->in_ptr);
         int *ka = nullptr, *kb = nullptr, *va = nullptr, *vtmp = nullptr;
         DI_CUDA(cudaMallocAsync(&ka, sizeof(int) * (size_t)L, s));
         DI_CUDA(cudaMallocAsync(&kb, sizeof(int) * (size_t)L, s));
@@ -680,6 +758,7 @@ di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_de
         g->n_long_tasks = tot;
     }
     DI_CUDA(cudaGetLastError());
+    g->transposed = true;
     return DI_OK;
 }
 

@@ -194,7 +194,8 @@ struct di_graph {
 
     // graph
     int *row_ptr = nullptr, *col_idx = nullptr;
-    int *in_ptr = nullptr, *in_src = nullptr;
+    int *in_ptr = nullptr, *in_src = nullptr;   // built at first use (build_transpose)
+    bool transposed = false;
     int *bin_of = nullptr, *in_bin_of = nullptr, *pull_ids = nullptr;
     unsigned char *cls = nullptr;      // [npad] out-degree class per node, 0 on the padding
     double *V = nullptr;               // NULL: uniform 1/n
@@ -266,6 +267,7 @@ di_status cuda_fail(cudaError_t e, const char *what);
 
 // graph ingest (graph_build.cu)
 di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_dev);
+di_status build_transpose(di_graph *g);   // the in-link CSR and its bins, at first use
 di_status validate_v(di_graph *g, const double *V_dev);
 
 // sweeps (sweep.cu)

@@ -275,6 +275,11 @@ di_status power_alloc(di_graph *g) {
 
 di_status run_power(di_graph *g, double tol, int max_iter, int profile, double *X_out, bool out_dev, di_stats *st) {
     cudaStream_t s = g->stream;
+    if (!g->X) {  // the in-link side and the iterates, at the first power iteration
+        di_status r = build_transpose(g);
+        if (r == DI_OK) r = power_alloc(g);
+        if (r != DI_OK) return r;
+    }
     if (!g->exec[2]) {
         di_status r = build_power_graph(g);
         if (r != DI_OK) return r;

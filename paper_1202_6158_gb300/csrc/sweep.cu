@@ -869,6 +869,8 @@ __global__ void k_sel_weights(int n, int npad, int select, const int *__restrict
 
 di_status ensure_weights(di_graph *g, int select) {
     if (select == 0 || g->wsel[select - 1]) return DI_OK;
+    di_status tr = build_transpose(g);  // #in_i
+    if (tr != DI_OK) return tr;
     cudaStream_t s = g->stream;
     const int npad = g->G * g->chunk;
     float *w = nullptr;
