@@ -53,6 +53,41 @@ __device__ T block_sum(T v, T *sh) {
 // pass over all of F does not push the push kernel's working set out of L2.  (F is
 // written by the scan itself, so its loads stay on the coherent path; the class
 // bytes are read-only.)
+// ---- bulk copies (TMA, 1-D) into shared memory, completed on an mbarrier
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+// global -> shared, bytes a multiple of 16, both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_copy(unsigned dst, const void *src, unsigned bytes, unsigned bar,
+                                          unsigned long long pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+        ::"r"(dst), "l"(src), "r"(bytes), "r"(bar), "l"(pol) : "memory");
+}
+
+// one bounded wait for the given phase: false if it did not complete within `limit` polls
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned phase, int limit) {
+    for (int it = 0; it < limit; ++it) {
+        unsigned ok;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(ok) : "r"(bar), "r"(phase) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 __device__ __forceinline__ unsigned long long evict_last_policy() {
     unsigned long long p;
     asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
@@ -86,13 +121,14 @@ __device__ __forceinline__ unsigned ld_stream(const unsigned *a, unsigned long l
 // nodes evenly over all its warps whatever their distribution over the chunks.
 // Each thread sums a contiguous run of sub-chunks for every list, one block scan
 // covers the four lists, then each thread writes its run.
-__device__ void prefix_counts(const int *__restrict__ fcount, int W, int *__restrict__ pre) {
-    constexpr int kCap = 8192;                     // sub-chunks staged per pass (32 KB)
-    __shared__ int s_c[kCap];
+// s_c: kCap ints of shared memory to stage the counts in
+// lists first_list..kLists-1 (the others are left as they are)
+__device__ void prefix_counts_staged(const int *__restrict__ fcount, int W, int *__restrict__ pre, int *s_c,
+                                     const int kCap, int first_list = 0) {
     __shared__ int s_w[kWarps];
     __shared__ int s_carry;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int L = 0; L < kLists; ++L) {
+    for (int L = first_list; L < kLists; ++L) {
         if (threadIdx.x == 0) s_carry = 0;
         for (int base = 0; base < W; base += kCap) {
             const int m = min(kCap, W - base);
@@ -128,6 +164,12 @@ __device__ void prefix_counts(const int *__restrict__ fcount, int W, int *__rest
         if (threadIdx.x == 0) pre[L * (W + 1) + W] = s_carry;
         __syncthreads();
     }
+}
+
+__device__ void prefix_counts(const int *__restrict__ fcount, int W, int *__restrict__ pre) {
+    constexpr int kCap = 8192;                     // sub-chunks staged per pass (32 KB)
+    __shared__ int s_c[kCap];
+    prefix_counts_staged(fcount, W, pre, s_c, kCap);
 }
 
 // sub-chunk holding item t of a list: the last g with pre[g] <= t

@@ -70,7 +70,7 @@ struct __align__(16) ScanPartial {
     long long srcs;    // selected nodes
     long long entries; // selected nodes with out-links
     double l1d;        // FP64 sum, used by the exact confirmation kernel
-    double pad;
+    long long err;     // 1: a bulk-copy wait of the scan gave up (the solve stops with DI_ETIMEOUT)
 };
 
 // device-resident control block of one solve
@@ -86,7 +86,7 @@ struct SolveState {
     long long max_edges;
     int sweeps;
     int max_sweeps;
-    int done;              // 0 running, 1 converged, 2 limit reached, 3 non-finite residual
+    int done;              // 0 running, 1 converged, 2 limit reached, 3 non-finite residual, 4 scan wait timed out
     int trace_on;
     int body_runs;         // executions of the finalize kernel (one per loop iteration)
     int exact;             // 1 when the sweep now running sums |F|_1 exactly (every kExactEvery sweeps)
@@ -310,6 +310,14 @@ void *kernel_ptr(void *p);
 
 // helpers
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+template <typename FT> inline const RowRec<FT> *rec_of(const di_graph *g);
+template <> inline const RowRec<double> *rec_of<double>(const di_graph *g) { return g->rec64; }
+template <> inline const RowRec<float> *rec_of<float>(const di_graph *g) { return g->rec32; }
+template <typename FT> inline Sel<FT> *sel_of(const di_graph *g) { return reinterpret_cast<Sel<FT> *>(g->sel); }
+
+// the push of one sweep on stream s (push.cu)
+template <typename FT> void launch_push(di_graph *g, FT *F, cudaStream_t s);
+
 // push CTAs: the pushes scale with edges, not nodes, so small graphs still get push_per_sm CTAs per SM
 inline int push_grid(const di_graph *g) {
     const int m = g->push_per_sm * g->num_sms;

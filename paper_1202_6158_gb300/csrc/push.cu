@@ -1,0 +1,177 @@
+// push.cu -- the push of a threshold sweep: along every out-link of the nodes the
+// scan selected, F_j += d * sent / outdeg(i) (the inner loop of ALGO-REF, Section 2.2).
+//
+// The scan (sweep.cu) has already taken each selected node's fluid out of F and added
+// it to H, and listed the nodes with children per out-degree class, in ascending id,
+// at per-warp offsets; this kernel spreads those lists over the whole grid.
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace diter {
+namespace {
+
+// One elementary step F_j += w.  Edges into the hot targets (the most-linked-to
+// nodes, internal ids 0..n_hot-1) are summed in the CTA's shared memory: on
+// power-law graphs a single target can receive a few percent of all pushes, and
+// same-address reductions serialize in one L2 slice.
+template <typename FT>
+__device__ __forceinline__ void push_one(FT *__restrict__ F, FT *hot, int n_hot, int c, FT w,
+                                         unsigned long long pol) {
+    if (c >= n_hot) red_add(F + c, w, pol);
+    else atomicAdd(hot + c, w);
+}
+
+// Rows of the warp and CTA classes: the head up to a 16-byte boundary, then int4
+// loads two at a time (all loads of a step are issued before its reductions),
+// then the tail.
+template <typename FT>
+__device__ __forceinline__ void push_row_lanes(const int *__restrict__ col_idx, FT *__restrict__ F, FT *hot, int n_hot,
+                                               int beg, int deg, FT w, int lane, int width, unsigned long long pol) {
+    const int head = min(deg, (4 - (beg & 3)) & 3);
+    if (lane < head) push_one(F, hot, n_hot, __ldg(col_idx + beg + lane), w, pol);
+    const int body = (deg - head) >> 2;
+    const int4 *v4 = reinterpret_cast<const int4 *>(col_idx + beg + head);
+    int k = lane;
+    for (; k + width < body; k += 2 * width) {
+        const int4 q = __ldg(v4 + k);
+        const int4 r = __ldg(v4 + k + width);
+        push_one(F, hot, n_hot, q.x, w, pol);
+        push_one(F, hot, n_hot, q.y, w, pol);
+        push_one(F, hot, n_hot, q.z, w, pol);
+        push_one(F, hot, n_hot, q.w, w, pol);
+        push_one(F, hot, n_hot, r.x, w, pol);
+        push_one(F, hot, n_hot, r.y, w, pol);
+        push_one(F, hot, n_hot, r.z, w, pol);
+        push_one(F, hot, n_hot, r.w, w, pol);
+    }
+    if (k < body) {
+        const int4 q = __ldg(v4 + k);
+        push_one(F, hot, n_hot, q.x, w, pol);
+        push_one(F, hot, n_hot, q.y, w, pol);
+        push_one(F, hot, n_hot, q.z, w, pol);
+        push_one(F, hot, n_hot, q.w, w, pol);
+    }
+    const int t = head + 4 * body + lane;
+    if (t < deg) push_one(F, hot, n_hot, __ldg(col_idx + beg + t), w, pol);
+}
+
+// The push.  The selected nodes with children of each class are numbered
+// 0..total-1 through the prefix sums of the scan, and spread over the whole grid: a
+// CTA per node of the largest class, a warp per node of the middle class, and for
+// the smallest class contiguous ranges of 64 per warp (a lane per node, two in
+// flight).  The scan already moved each node's fluid into H; the push adds
+// d*sent/outdeg(i) to F_j along every out-link (ALGO-REF's inner loop), every load
+// of a node issued before its reductions.
+template <typename FT>
+__global__ void __launch_bounds__(kScanThreads) k_sweep_push(const RowRec<FT> *__restrict__ rec,
+                                                             const int *__restrict__ col_idx, FT *__restrict__ F,
+                                                             const int *__restrict__ region,
+                                                             const int *__restrict__ pre, int W,
+                                                             const Sel<FT> *__restrict__ sel, int n_hot,
+                                                             ScanPartial *__restrict__ part, int G,
+                                                             const SolveState *__restrict__ st) {
+    __shared__ FT hot[kHotSlots];
+    __shared__ long long s_red[kWarps];
+    __shared__ int s_idx;
+    if (st->done) return;
+    for (int t = threadIdx.x; t < kHotSlots; t += kScanThreads) hot[t] = (FT)0;
+    __syncthreads();
+    const unsigned long long pol = evict_last_policy();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nwarps = gridDim.x * kWarps, gw = blockIdx.x * kWarps + w;
+    const int *pre3 = pre + 3 * (W + 1), *pre2 = pre + 2 * (W + 1), *pre1 = pre + 1 * (W + 1);
+    long long edges = 0;
+    // class 3: the whole CTA per node
+    const int tot3 = __ldg(pre3 + W);
+    for (int t = blockIdx.x; t < tot3; t += gridDim.x) {
+        if (threadIdx.x == 0) {
+            const int gs = find_sub(pre3, W, t);
+            s_idx = region[3 * (W + 1) + gs] + (t - __ldg(pre3 + gs));
+        }
+        __syncthreads();
+        const Sel<FT> e = sel[s_idx];
+        __syncthreads();
+        const RowRec<FT> rr = rec[e.node];
+        if (threadIdx.x == 0) edges += rr.deg;
+        push_row_lanes(col_idx, F, hot, n_hot, rr.beg, rr.deg, e.sent * rr.inv, threadIdx.x, kScanThreads, pol);
+    }
+    // class 2: a warp per node
+    const int tot2 = __ldg(pre2 + W);
+    for (int t = gw; t < tot2; t += nwarps) {
+        int idx = 0;
+        if (lane == 0) {
+            const int gs = find_sub(pre2, W, t);
+            idx = region[2 * (W + 1) + gs] + (t - __ldg(pre2 + gs));
+        }
+        idx = __shfl_sync(kFull, idx, 0);
+        const Sel<FT> e = sel[idx];
+        const RowRec<FT> rr = rec[e.node];
+        if (lane == 0) edges += rr.deg;
+        push_row_lanes(col_idx, F, hot, n_hot, rr.beg, rr.deg, e.sent * rr.inv, lane, 32, pol);
+    }
+    // class 1: a lane per node, two nodes in flight, a contiguous range per warp
+    {
+        const int tot1 = __ldg(pre1 + W);
+        const int per = (tot1 + nwarps - 1) / nwarps;
+        const int t_beg = min(tot1, gw * per), t_end = min(tot1, t_beg + per);
+        int gs = 0;
+        if (t_beg < t_end) {
+            if (lane == 0) gs = find_sub(pre1, W, t_beg);
+            gs = __shfl_sync(kFull, gs, 0);
+        }
+        int ga = gs;
+        for (int t0 = t_beg; t0 < t_end; t0 += 64) {
+            const int ta = t0 + lane, tb = t0 + 32 + lane;
+            const bool has0 = ta < t_end, has1 = tb < t_end;
+            if (!has0) break;
+            while (__ldg(pre1 + ga + 1) <= ta) ++ga;
+            int gb = ga;
+            if (has1)
+                while (__ldg(pre1 + gb + 1) <= tb) ++gb;
+            const Sel<FT> e0 = sel[region[1 * (W + 1) + ga] + (ta - __ldg(pre1 + ga))];
+            const Sel<FT> e1 = has1 ? sel[region[1 * (W + 1) + gb] + (tb - __ldg(pre1 + gb))] : e0;
+            ga = gb;
+            const RowRec<FT> r0 = rec[e0.node], r1 = rec[e1.node];
+            const int b0 = r0.beg, d0 = r0.deg;
+            const int b1 = r1.beg, d1 = has1 ? r1.deg : 0;
+            const FT w0 = e0.sent * r0.inv, w1 = e1.sent * r1.inv;
+            int c0[kOutCut1], c1[kOutCut1];
+#pragma unroll
+            for (int k = 0; k < kOutCut1; ++k) {
+                c0[k] = k < d0 ? __ldg(col_idx + b0 + k) : 0;
+                c1[k] = k < d1 ? __ldg(col_idx + b1 + k) : 0;
+            }
+            edges += d0 + d1;
+#pragma unroll
+            for (int k = 0; k < kOutCut1; ++k) {
+                if (k < d0) push_one(F, hot, n_hot, c0[k], w0, pol);
+                if (k < d1) push_one(F, hot, n_hot, c1[k], w1, pol);
+            }
+        }
+    }
+    // the CTA's sums for the hot targets go to F once
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_hot; t += kScanThreads) {
+        const FT v = hot[t];
+        if (v != (FT)0) red_add(F + t, v);
+    }
+    const long long be = block_sum(edges, s_red);
+    // the scan zeroed the G partials' edge counts; the push grid may be wider than G
+    if (threadIdx.x == 0 && be)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&part[blockIdx.x % G].edges), (unsigned long long)be);
+}
+
+}  // namespace
+
+template <typename FT>
+void launch_push(di_graph *g, FT *F, cudaStream_t s) {
+    k_sweep_push<FT><<<push_grid(g), kScanThreads, 0, s>>>(rec_of<FT>(g), g->col_idx, F, g->region, g->pre, g->W,
+                                                           sel_of<FT>(g), g->n_hot, g->part, g->G, g->st);
+}
+
+template void launch_push<double>(di_graph *, double *, cudaStream_t);
+template void launch_push<float>(di_graph *, float *, cudaStream_t);
+
+}  // namespace diter

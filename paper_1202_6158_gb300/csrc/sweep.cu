@@ -163,6 +163,10 @@ struct ScanOps<double> {
         const double2 b = ld_stream(reinterpret_cast<const double2 *>(p) + 1, pol);
         v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
     }
+    __device__ static void load4_shared(const unsigned char *p, double v[4]) {
+        const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
     __device__ static void store4(double *p, const double v[4]) {
         reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
         reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
@@ -178,19 +182,39 @@ struct ScanOps<float> {
         const float4 a = ld_stream(reinterpret_cast<const float4 *>(p), pol);
         v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
     }
+    __device__ static void load4_shared(const unsigned char *p, float v[4]) {
+        const float4 a = *reinterpret_cast<const float4 *>(p);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
     __device__ static void store4(float *p, const float v[4]) {
         *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
     }
 };
 
-// The sweep scan streams F and the one-byte out-degree class of every node and
-// does no dependent load: each warp owns a sub-chunk of chunk/8 nodes, reads it
-// 128 nodes per step (4 per lane, the next step's loads issued before the current
-// step is processed), and appends the selected nodes (id, sent) of each class to
-// that class's list in ascending id order with a warp prefix sum; the lists'
-// per-sub-chunk capacities are fixed at create time, so no atomics are needed.
+// The sweep scan streams F and the one-byte out-degree class of every node: each
+// warp owns a sub-chunk of chunk/8 nodes and streams it through shared memory with
+// bulk copies (TMA, 1-D), 128 nodes per step and kStages steps in flight, so the
+// loads never stall on a dependency; lane i takes nodes 4i..4i+3 of a step.  The
+// selected nodes (id, sent) of each class are appended to that class's list in
+// ascending id order with a warp prefix sum; the lists' per-sub-chunk capacities are
+// fixed at create time, so no atomics are needed.
 // WGT: ALGO-OP / ALGO-OP2 selection (Section 4.3) as a weighted threshold: node i
 // is selected when (float)|F_i| * w_i > (float)(T * wscale), the product in FP32.
+//
+// The ring of one warp: per stage 128 values of F, their 128 class bytes (and 128
+// selection weights); every size is a multiple of 16 bytes and every source offset a
+// multiple of 128 nodes, so every copy is 16-byte aligned.
+template <typename FT, bool WGT>
+struct ScanRing {
+    static constexpr int kF = kStep * (int)sizeof(FT);
+    static constexpr int kC = kStep;
+    static constexpr int kW = WGT ? kStep * 4 : 0;
+    static constexpr int kBytes = kF + kC + kW;
+    static constexpr int kStages = WGT ? 3 : 4;
+    static constexpr int kWarpBytes = kBytes * kStages;
+};
+constexpr int kScanWaitLimit = 1 << 20;  // polls of a stage's mbarrier before the scan gives up
+
 template <typename FT, bool WGT>
 __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__restrict__ F,
                                                              const float *__restrict__ wsel,
@@ -202,14 +226,20 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
                                                              const SolveState *__restrict__ st,
                                                              double *__restrict__ H) {
     using Ops = ScanOps<FT>;
+    using Ring = ScanRing<FT, WGT>;
+    __shared__ __align__(128) unsigned char s_ring[kWarps * Ring::kWarpBytes];
+    __shared__ __align__(8) unsigned long long s_bar[kWarps * Ring::kStages];
+    __shared__ unsigned char s_q[kWarps][kStep];  // the selected nodes of a step, by position in the step
     __shared__ long long s_red[kWarps];
     __shared__ unsigned s_ticket;
+    __shared__ int s_err;
     if (st->done) return;
     const typename Ops::Key key = Ops::key(st->T);
     const float tw = WGT ? (float)(st->T * st->wscale) : 0.f;
     const int S = fixed_scale(st->R);
     const bool exact = (st->sweeps % kExactEvery) == 0;  // the exact |F|_1 of this sweep's start
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
     const int g = blockIdx.x * kWarps + w;
     const long long wbeg = (long long)g * wchunk;
     int run[kLists], start[kLists];
@@ -218,82 +248,124 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
     long long l1 = 0, s_out = 0, s_dng = 0;  // fixed point: |F|_1, fluid of selected nodes with / without children
     int srcs = 0, entries = 0;
     const int nsteps = wchunk / kStep;
-    FT cur[4], nxt[4];
-    unsigned ccur, cnxt = 0;
-    float4 wcur = make_float4(0.f, 0.f, 0.f, 0.f), wnxt = wcur;
     const unsigned long long pol = evict_first_policy(), pol_h = evict_last_policy();
-    Ops::load4(F + wbeg + 4 * lane, cur, pol);
-    ccur = ld_stream(reinterpret_cast<const unsigned *>(cls + wbeg + 4 * lane), pol);
-    if (WGT) wcur = ld_stream(reinterpret_cast<const float4 *>(wsel + wbeg + 4 * lane), pol);
-    for (int s = 0; s < nsteps; ++s) {
-        const long long i0 = wbeg + (long long)s * kStep + 4 * lane;
-        if (s + 1 < nsteps) {
-            Ops::load4(F + i0 + kStep, nxt, pol);
-            cnxt = ld_stream(reinterpret_cast<const unsigned *>(cls + i0 + kStep), pol);
-            if (WGT) wnxt = ld_stream(reinterpret_cast<const float4 *>(wsel + i0 + kStep), pol);
-        }
+    // this warp's ring: lane 0 keeps kStages steps in flight
+    unsigned char *ring = s_ring + w * Ring::kWarpBytes;
+    unsigned char *q = s_q[w];
+    const unsigned ring_s = smem_addr(ring), bar0 = smem_addr(&s_bar[w * Ring::kStages]);
+    auto issue = [&](int t) {
+        const int k = t % Ring::kStages;
+        const unsigned bar = bar0 + 8u * k, dst = ring_s + (unsigned)(k * Ring::kBytes);
+        const long long base = wbeg + (long long)t * kStep;
+        mbar_expect_tx(bar, Ring::kBytes);
+        bulk_copy(dst, F + base, Ring::kF, bar, pol);
+        bulk_copy(dst + Ring::kF, cls + base, Ring::kC, bar, pol);
+        if (WGT) bulk_copy(dst + Ring::kF + Ring::kC, wsel + base, Ring::kW, bar, pol);
+    };
+    if (threadIdx.x == 0) s_err = 0;
+    __syncthreads();
+    if (lane == 0) {
+        for (int k = 0; k < Ring::kStages; ++k) mbar_init(bar0 + 8u * k, 1);
+        fence_barrier_init();
+        for (int t = 0; t < Ring::kStages && t < nsteps; ++t) issue(t);
+    }
+    __syncwarp();
+    int s = 0;
+    bool ok = true;
+    for (; s < nsteps; ++s) {
+        const int slot = s % Ring::kStages;
+        ok = __all_sync(kFull, mbar_wait(bar0 + 8u * slot, (unsigned)((s / Ring::kStages) & 1), kScanWaitLimit));
+        if (!ok) break;
+        const unsigned char *stg = ring + slot * Ring::kBytes;
+        const FT *stg_f = reinterpret_cast<const FT *>(stg);
+        const long long step0 = wbeg + (long long)s * kStep;
+        FT cur[4];
+        Ops::load4_shared(stg + 4 * (int)sizeof(FT) * lane, cur);
+        float4 wcur = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (WGT) wcur = *reinterpret_cast<const float4 *>(stg + Ring::kF + Ring::kC + 16 * lane);
         const float wk[4] = {wcur.x, wcur.y, wcur.z, wcur.w};
-        int lst[4];
-        FT sent[4];
-        bool any = false;
-        unsigned packed = 0;  // per-list counts of this lane, 8 bits each
+        // 1. which of this lane's four nodes are selected; the exact |F|_1 every kExactEvery sweeps
+        unsigned pm = 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            sent[k] = cur[k];
             const bool pick = WGT ? fabsf((float)cur[k]) * wk[k] > tw : Ops::above(cur[k], key);
-            long long fx = 0;
-            if (exact || pick) fx = to_fixed(cur[k], S);
-            if (exact) l1 += fx;
-            lst[k] = -1;
-            if (pick) {
-                const int c = (ccur >> (8 * k)) & 0xff;
-                any = true;
-                srcs += 1;
-                cur[k] = (FT)0;                 // J_i F leaves F ...
-                red_add(H + i0 + k, (double)sent[k], pol_h);  // ... into the history (H' = H + J_S F)
-                if (c == 0) {
-                    s_dng += fx;                // a dangling node's fluid leaves the system (Section 3.3)
-                } else {
-                    s_out += fx;
-                    entries += 1;
-                    lst[k] = c;                 // nodes with children go to the push lists
-                    packed += 1u << (8 * c);
+            pm |= pick ? 1u << k : 0u;
+            if (exact) l1 += to_fixed(cur[k], S);
+        }
+        // 2. the selected nodes of the step, in ascending position, into the warp's queue
+        const int np = __popc(pm);
+        int incl = np;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(kFull, incl, 31);
+        if (total) {
+            if (pm) {
+                int at = incl - np;
+                FT z[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    z[k] = cur[k];
+                    if (pm >> k & 1u) {
+                        q[at++] = (unsigned char)(4 * lane + k);
+                        z[k] = (FT)0;           // J_i F leaves F ...
+                    }
+                }
+                Ops::store4(F + step0 + 4 * lane, z);
+            }
+            __syncwarp();
+            // 3. a lane per selected node: history, removed mass, list position
+            for (int r = 0; r < total; r += 32) {
+                const int t = r + lane;
+                const bool has = t < total;
+                const int idx = has ? q[t] : 0;
+                const FT v = stg_f[idx];
+                const int c = has ? stg[Ring::kF + idx] : 0;
+                const long long node = step0 + idx;
+                if (has) {
+                    const long long fx = to_fixed(v, S);
+                    red_add(H + node, (double)v, pol_h);   // ... into the history (H' = H + J_S F)
+                    srcs += 1;
+                    if (c == 0) {
+                        s_dng += fx;            // a dangling node's fluid leaves the system (Section 3.3)
+                    } else {
+                        s_out += fx;
+                        entries += 1;
+                    }
+                }
+                // nodes with children go to their class's list, in ascending id
+#pragma unroll
+                for (int L = 1; L < kLists; ++L) {
+                    const bool mine = has && c == L;
+                    const unsigned bits = __ballot_sync(kFull, mine);
+                    if (mine) {
+                        Sel<FT> e;
+                        e.node = (int)node;
+                        e.pad = 0;
+                        e.sent = v;
+                        sel[run[L] + __popc(bits & lt)] = e;
+                    }
+                    run[L] += __popc(bits);
                 }
             }
         }
-        if (any) Ops::store4(F + i0, cur);
-        // one warp prefix sum gives the offsets of all four lists (each field stays below 256)
-        if (__any_sync(kFull, packed)) {
-            unsigned x = packed;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned y = __shfl_up_sync(kFull, x, o);
-                if (lane >= o) x += y;
-            }
-            const unsigned excl = x - packed, total = __shfl_sync(kFull, x, 31);
-            unsigned loc = 0;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int L = lst[k];
-                if (L >= 0) {
-                    const int sh = 8 * L;
-                    const int base = L == 0 ? run[0] : (L == 1 ? run[1] : (L == 2 ? run[2] : run[3]));
-                    const int idx = base + (int)((excl >> sh) & 0xff) + (int)((loc >> sh) & 0xff);
-                    loc += 1u << sh;
-                    Sel<FT> e;
-                    e.node = (int)(i0 + k);
-                    e.pad = 0;
-                    e.sent = sent[k];
-                    sel[idx] = e;
-                }
-            }
-#pragma unroll
-            for (int L = 0; L < kLists; ++L) run[L] += (int)((total >> (8 * L)) & 0xff);
+        // the slot is read: lane 0 refills it with the step kStages ahead
+        __syncwarp();
+        if (lane == 0 && s + Ring::kStages < nsteps) {
+            fence_proxy_async();
+            issue(s + Ring::kStages);
         }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
-        ccur = cnxt;
-        wcur = wnxt;
+    }
+    if (!ok) {
+        // a wait gave up: wait (bounded again) for this warp's copies still in flight, then report
+        if (lane == 0) {
+            for (int t = s; t < nsteps && t < s + Ring::kStages; ++t)
+                mbar_wait(bar0 + 8u * (t % Ring::kStages), (unsigned)((t / Ring::kStages) & 1), kScanWaitLimit);
+            atomicExch(&s_err, 1);
+        }
+        __syncwarp();
     }
     if (lane == 0) {
 #pragma unroll
@@ -313,172 +385,21 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
         p.srcs = bsr;
         p.entries = ben;
         p.l1d = 0.0;
-        p.pad = 0.0;
+        p.err = s_err;
         part[blockIdx.x] = p;
     }
-    // every CTA publishes its counts, then takes a ticket; the last one builds the prefixes
+    // every CTA publishes its counts, then takes a ticket; the last one builds the prefixes,
+    // staging them in the (now idle) ring
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1u);
     __syncthreads();
     if (s_ticket == gridDim.x - 1) {
         __threadfence();
-        prefix_counts(fcount, W, pre);
+        // list 0 (dangling nodes) stays empty: the scan finishes those nodes itself
+        prefix_counts_staged(fcount, W, pre, reinterpret_cast<int *>(s_ring), (int)(sizeof(s_ring) / sizeof(int)), 1);
         if (threadIdx.x == 0) *ticket = 0u;
     }
-}
-
-// ------------------------------------------------------------------- push
-
-// One elementary step F_j += w.  Edges into the hot targets (the most-linked-to
-// nodes, internal ids 0..n_hot-1) are summed in the CTA's shared memory: on
-// power-law graphs a single target can receive a few percent of all pushes, and
-// same-address reductions serialize in one L2 slice.
-template <typename FT>
-__device__ __forceinline__ void push_one(FT *__restrict__ F, FT *hot, int n_hot, int c, FT w,
-                                         unsigned long long pol) {
-    if (c >= n_hot) red_add(F + c, w, pol);
-    else atomicAdd(hot + c, w);
-}
-
-// Rows of the warp and CTA classes: the head up to a 16-byte boundary, then int4
-// loads two at a time (all loads of a step are issued before its reductions),
-// then the tail.
-template <typename FT>
-__device__ __forceinline__ void push_row_lanes(const int *__restrict__ col_idx, FT *__restrict__ F, FT *hot, int n_hot,
-                                               int beg, int deg, FT w, int lane, int width, unsigned long long pol) {
-    const int head = min(deg, (4 - (beg & 3)) & 3);
-    if (lane < head) push_one(F, hot, n_hot, __ldg(col_idx + beg + lane), w, pol);
-    const int body = (deg - head) >> 2;
-    const int4 *v4 = reinterpret_cast<const int4 *>(col_idx + beg + head);
-    int k = lane;
-    for (; k + width < body; k += 2 * width) {
-        const int4 q = __ldg(v4 + k);
-        const int4 r = __ldg(v4 + k + width);
-        push_one(F, hot, n_hot, q.x, w, pol);
-        push_one(F, hot, n_hot, q.y, w, pol);
-        push_one(F, hot, n_hot, q.z, w, pol);
-        push_one(F, hot, n_hot, q.w, w, pol);
-        push_one(F, hot, n_hot, r.x, w, pol);
-        push_one(F, hot, n_hot, r.y, w, pol);
-        push_one(F, hot, n_hot, r.z, w, pol);
-        push_one(F, hot, n_hot, r.w, w, pol);
-    }
-    if (k < body) {
-        const int4 q = __ldg(v4 + k);
-        push_one(F, hot, n_hot, q.x, w, pol);
-        push_one(F, hot, n_hot, q.y, w, pol);
-        push_one(F, hot, n_hot, q.z, w, pol);
-        push_one(F, hot, n_hot, q.w, w, pol);
-    }
-    const int t = head + 4 * body + lane;
-    if (t < deg) push_one(F, hot, n_hot, __ldg(col_idx + beg + t), w, pol);
-}
-
-// The push.  The selected nodes with children of each class are numbered
-// 0..total-1 through the prefix sums of the scan, and spread over the whole grid: a
-// CTA per node of the largest class, a warp per node of the middle class, and for
-// the smallest class contiguous ranges of 64 per warp (a lane per node, two in
-// flight).  The scan already moved each node's fluid into H; the push adds
-// d*sent/outdeg(i) to F_j along every out-link (ALGO-REF's inner loop), every load
-// of a node issued before its reductions.
-template <typename FT>
-__global__ void __launch_bounds__(kScanThreads) k_sweep_push(const RowRec<FT> *__restrict__ rec,
-                                                             const int *__restrict__ col_idx, FT *__restrict__ F,
-                                                             const int *__restrict__ region,
-                                                             const int *__restrict__ pre, int W,
-                                                             const Sel<FT> *__restrict__ sel, int n_hot,
-                                                             ScanPartial *__restrict__ part, int G,
-                                                             const SolveState *__restrict__ st) {
-    __shared__ FT hot[kHotSlots];
-    __shared__ long long s_red[kWarps];
-    __shared__ int s_idx;
-    if (st->done) return;
-    for (int t = threadIdx.x; t < kHotSlots; t += kScanThreads) hot[t] = (FT)0;
-    __syncthreads();
-    const unsigned long long pol = evict_last_policy();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int nwarps = gridDim.x * kWarps, gw = blockIdx.x * kWarps + w;
-    const int *pre3 = pre + 3 * (W + 1), *pre2 = pre + 2 * (W + 1), *pre1 = pre + 1 * (W + 1);
-    long long edges = 0;
-    // class 3: the whole CTA per node
-    const int tot3 = __ldg(pre3 + W);
-    for (int t = blockIdx.x; t < tot3; t += gridDim.x) {
-        if (threadIdx.x == 0) {
-            const int gs = find_sub(pre3, W, t);
-            s_idx = region[3 * (W + 1) + gs] + (t - __ldg(pre3 + gs));
-        }
-        __syncthreads();
-        const Sel<FT> e = sel[s_idx];
-        __syncthreads();
-        const RowRec<FT> rr = rec[e.node];
-        if (threadIdx.x == 0) edges += rr.deg;
-        push_row_lanes(col_idx, F, hot, n_hot, rr.beg, rr.deg, e.sent * rr.inv, threadIdx.x, kScanThreads, pol);
-    }
-    // class 2: a warp per node
-    const int tot2 = __ldg(pre2 + W);
-    for (int t = gw; t < tot2; t += nwarps) {
-        int idx = 0;
-        if (lane == 0) {
-            const int gs = find_sub(pre2, W, t);
-            idx = region[2 * (W + 1) + gs] + (t - __ldg(pre2 + gs));
-        }
-        idx = __shfl_sync(kFull, idx, 0);
-        const Sel<FT> e = sel[idx];
-        const RowRec<FT> rr = rec[e.node];
-        if (lane == 0) edges += rr.deg;
-        push_row_lanes(col_idx, F, hot, n_hot, rr.beg, rr.deg, e.sent * rr.inv, lane, 32, pol);
-    }
-    // class 1: a lane per node, two nodes in flight, a contiguous range per warp
-    {
-        const int tot1 = __ldg(pre1 + W);
-        const int per = (tot1 + nwarps - 1) / nwarps;
-        const int t_beg = min(tot1, gw * per), t_end = min(tot1, t_beg + per);
-        int gs = 0;
-        if (t_beg < t_end) {
-            if (lane == 0) gs = find_sub(pre1, W, t_beg);
-            gs = __shfl_sync(kFull, gs, 0);
-        }
-        int ga = gs;
-        for (int t0 = t_beg; t0 < t_end; t0 += 64) {
-            const int ta = t0 + lane, tb = t0 + 32 + lane;
-            const bool has0 = ta < t_end, has1 = tb < t_end;
-            if (!has0) break;
-            while (__ldg(pre1 + ga + 1) <= ta) ++ga;
-            int gb = ga;
-            if (has1)
-                while (__ldg(pre1 + gb + 1) <= tb) ++gb;
-            const Sel<FT> e0 = sel[region[1 * (W + 1) + ga] + (ta - __ldg(pre1 + ga))];
-            const Sel<FT> e1 = has1 ? sel[region[1 * (W + 1) + gb] + (tb - __ldg(pre1 + gb))] : e0;
-            ga = gb;
-            const RowRec<FT> r0 = rec[e0.node], r1 = rec[e1.node];
-            const int b0 = r0.beg, d0 = r0.deg;
-            const int b1 = r1.beg, d1 = has1 ? r1.deg : 0;
-            const FT w0 = e0.sent * r0.inv, w1 = e1.sent * r1.inv;
-            int c0[kOutCut1], c1[kOutCut1];
-#pragma unroll
-            for (int k = 0; k < kOutCut1; ++k) {
-                c0[k] = k < d0 ? __ldg(col_idx + b0 + k) : 0;
-                c1[k] = k < d1 ? __ldg(col_idx + b1 + k) : 0;
-            }
-            edges += d0 + d1;
-#pragma unroll
-            for (int k = 0; k < kOutCut1; ++k) {
-                if (k < d0) push_one(F, hot, n_hot, c0[k], w0, pol);
-                if (k < d1) push_one(F, hot, n_hot, c1[k], w1, pol);
-            }
-        }
-    }
-    // the CTA's sums for the hot targets go to F once
-    __syncthreads();
-    for (int t = threadIdx.x; t < n_hot; t += kScanThreads) {
-        const FT v = hot[t];
-        if (v != (FT)0) red_add(F + t, v);
-    }
-    const long long be = block_sum(edges, s_red);
-    // the scan zeroed the G partials' edge counts; the push grid may be wider than G
-    if (threadIdx.x == 0 && be)
-        atomicAdd(reinterpret_cast<unsigned long long *>(&part[blockIdx.x % G].edges), (unsigned long long)be);
 }
 
 // --------------------------------------------------------------- finalize
@@ -496,8 +417,9 @@ __global__ void k_sweep_finalize(int n, int G, const ScanPartial *__restrict__ p
         return;
     }
     (void)s_d;
-    long long fl1 = 0, fout = 0, fdng = 0, ed = 0, sr = 0, en = 0;
+    long long fl1 = 0, fout = 0, fdng = 0, ed = 0, sr = 0, en = 0, er = 0;
     for (int c = threadIdx.x; c < G; c += blockDim.x) {
+        er |= part[c].err;
         fl1 += part[c].l1;
         fout += part[c].out;
         fdng += part[c].dng;
@@ -511,6 +433,7 @@ __global__ void k_sweep_finalize(int n, int G, const ScanPartial *__restrict__ p
     ed = block_sum(ed, s_l);
     sr = block_sum(sr, s_l);
     en = block_sum(en, s_l);
+    er = block_sum(er, s_l);
     if (threadIdx.x != 0) return;
     st->body_runs += 1;
     const double Tused = st->T;
@@ -545,7 +468,8 @@ __global__ void k_sweep_finalize(int n, int G, const ScanPartial *__restrict__ p
     if (!(Tn > 0.0)) Tn = 0.0;
     st->T = Tn;
     int done = 0;
-    if (!isfinite(R)) done = 3;
+    if (er) done = 4;
+    else if (!isfinite(R)) done = 3;
     else if (R <= st->tolR) done = 1;
     else if (st->sweeps >= st->max_sweeps || (st->max_edges > 0 && st->edges >= st->max_edges)) done = 2;
     st->done = done;
@@ -612,10 +536,6 @@ __global__ void k_gather_out(int n, const int *__restrict__ new_of, const FT *__
         out[i] = (double)src[new_of[i]] * scale;
 }
 
-template <typename FT> const RowRec<FT> *rec_of(di_graph *g);
-template <> const RowRec<double> *rec_of<double>(di_graph *g) { return g->rec64; }
-template <> const RowRec<float> *rec_of<float>(di_graph *g) { return g->rec32; }
-template <typename FT> Sel<FT> *sel_of(di_graph *g) { return reinterpret_cast<Sel<FT> *>(g->sel); }
 
 template <typename FT>
 void launch_scan(di_graph *g, FT *F, const float *wsel, cudaStream_t s) {
@@ -629,11 +549,6 @@ void launch_scan(di_graph *g, FT *F, const float *wsel, cudaStream_t s) {
                                                               g->st, g->H);
 }
 
-template <typename FT>
-void launch_push(di_graph *g, FT *F, cudaStream_t s) {
-    k_sweep_push<FT><<<push_grid(g), kScanThreads, 0, s>>>(rec_of<FT>(g), g->col_idx, F, g->region, g->pre, g->W,
-                                                           sel_of<FT>(g), g->n_hot, g->part, g->G, g->st);
-}
 
 int elem_grid(di_graph *g, long long work) {
     long long b = (work + 255) / 256;
@@ -800,6 +715,7 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, InitK
         stats->kernel_launches = (init == kInitV ? 2 : 3) + 3LL * h.body_runs + 2LL * attempts;
     }
     if (h.done == 3) return set_error(DI_EKERNEL, "residual became non-finite");
+    if (h.done == 4) return set_error(DI_ETIMEOUT, "a bulk-copy wait of the sweep scan gave up");
     if (h.done != 1) return set_error(DI_ENOTCONVERGED, "stopped by a limit before |F|_1/(1-d) <= tol");
     return DI_OK;
 }
