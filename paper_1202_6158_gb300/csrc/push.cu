@@ -57,17 +57,18 @@ __device__ __forceinline__ void push_row_lanes(const int *__restrict__ col_idx, 
     if (t < deg) push_one(F, hot, n_hot, __ldg(col_idx + beg + t), w, pol);
 }
 
-// The push.  The selected nodes with children of each class are numbered
-// 0..total-1 through the prefix sums of the scan, and spread over the whole grid: a
-// CTA per node of the largest class, a warp per node of the middle class, and for
-// the smallest class contiguous ranges of 64 per warp (a lane per node, two in
-// flight).  The scan already moved each node's fluid into H; the push adds
+// The push.  The selected nodes with children of the largest class (a CTA per node)
+// are numbered 0..total-1 through the prefix sums of the scan and spread over all
+// CTAs; the middle class (a warp per node) and the smallest class (a lane per node,
+// two in flight) are taken per scan sub-chunk: push warp w walks the lists the scan's
+// warp w wrote.  The scan already moved each node's fluid into H; the push adds
 // d*sent/outdeg(i) to F_j along every out-link (ALGO-REF's inner loop), every load
 // of a node issued before its reductions.
 template <typename FT>
 __global__ void __launch_bounds__(kScanThreads) k_sweep_push(const RowRec<FT> *__restrict__ rec,
                                                              const int *__restrict__ col_idx, FT *__restrict__ F,
                                                              const int *__restrict__ region,
+                                                             const int *__restrict__ fcount,
                                                              const int *__restrict__ pre, int W,
                                                              const Sel<FT> *__restrict__ sel, int n_hot,
                                                              ScanPartial *__restrict__ part, int G,
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_push(const RowRec<FT> *_
     const unsigned long long pol = evict_last_policy();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nwarps = gridDim.x * kWarps, gw = blockIdx.x * kWarps + w;
-    const int *pre3 = pre + 3 * (W + 1), *pre2 = pre + 2 * (W + 1), *pre1 = pre + 1 * (W + 1);
+    const int *pre3 = pre + 3 * (W + 1);
     long long edges = 0;
     // class 3: the whole CTA per node
     const int tot3 = __ldg(pre3 + W);
@@ -97,42 +98,27 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_push(const RowRec<FT> *_
         if (threadIdx.x == 0) edges += rr.deg;
         push_row_lanes(col_idx, F, hot, n_hot, rr.beg, rr.deg, e.sent * rr.inv, threadIdx.x, kScanThreads, pol);
     }
-    // class 2: a warp per node
-    const int tot2 = __ldg(pre2 + W);
-    for (int t = gw; t < tot2; t += nwarps) {
-        int idx = 0;
-        if (lane == 0) {
-            const int gs = find_sub(pre2, W, t);
-            idx = region[2 * (W + 1) + gs] + (t - __ldg(pre2 + gs));
+    // classes 2 and 1: push warp w takes the lists of scan sub-chunk w (and w + nwarps, ...):
+    // the scan's per-warp counts are nearly even, and entries are read in list order
+    for (int gs = gw; gs < W; gs += nwarps) {
+        // class 2: a warp per node
+        {
+            const int b = __ldg(region + 2 * (W + 1) + gs), c = __ldcg(fcount + 2 * W + gs);
+            for (int k = 0; k < c; ++k) {
+                const Sel<FT> e = sel[b + k];
+                const RowRec<FT> rr = rec[e.node];
+                if (lane == 0) edges += rr.deg;
+                push_row_lanes(col_idx, F, hot, n_hot, rr.beg, rr.deg, e.sent * rr.inv, lane, 32, pol);
+            }
         }
-        idx = __shfl_sync(kFull, idx, 0);
-        const Sel<FT> e = sel[idx];
-        const RowRec<FT> rr = rec[e.node];
-        if (lane == 0) edges += rr.deg;
-        push_row_lanes(col_idx, F, hot, n_hot, rr.beg, rr.deg, e.sent * rr.inv, lane, 32, pol);
-    }
-    // class 1: a lane per node, two nodes in flight, a contiguous range per warp
-    {
-        const int tot1 = __ldg(pre1 + W);
-        const int per = (tot1 + nwarps - 1) / nwarps;
-        const int t_beg = min(tot1, gw * per), t_end = min(tot1, t_beg + per);
-        int gs = 0;
-        if (t_beg < t_end) {
-            if (lane == 0) gs = find_sub(pre1, W, t_beg);
-            gs = __shfl_sync(kFull, gs, 0);
-        }
-        int ga = gs;
-        for (int t0 = t_beg; t0 < t_end; t0 += 64) {
-            const int ta = t0 + lane, tb = t0 + 32 + lane;
-            const bool has0 = ta < t_end, has1 = tb < t_end;
+        // class 1: a lane per node, two nodes in flight
+        const int b = __ldg(region + 1 * (W + 1) + gs), c = __ldcg(fcount + 1 * W + gs);
+        for (int k0 = 0; k0 < c; k0 += 64) {
+            const int ta = k0 + lane, tb = k0 + 32 + lane;
+            const bool has0 = ta < c, has1 = tb < c;
             if (!has0) break;
-            while (__ldg(pre1 + ga + 1) <= ta) ++ga;
-            int gb = ga;
-            if (has1)
-                while (__ldg(pre1 + gb + 1) <= tb) ++gb;
-            const Sel<FT> e0 = sel[region[1 * (W + 1) + ga] + (ta - __ldg(pre1 + ga))];
-            const Sel<FT> e1 = has1 ? sel[region[1 * (W + 1) + gb] + (tb - __ldg(pre1 + gb))] : e0;
-            ga = gb;
+            const Sel<FT> e0 = sel[b + ta];
+            const Sel<FT> e1 = has1 ? sel[b + tb] : e0;
             const RowRec<FT> r0 = rec[e0.node], r1 = rec[e1.node];
             const int b0 = r0.beg, d0 = r0.deg;
             const int b1 = r1.beg, d1 = has1 ? r1.deg : 0;
@@ -167,8 +153,9 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_push(const RowRec<FT> *_
 
 template <typename FT>
 void launch_push(di_graph *g, FT *F, cudaStream_t s) {
-    k_sweep_push<FT><<<push_grid(g), kScanThreads, 0, s>>>(rec_of<FT>(g), g->col_idx, F, g->region, g->pre, g->W,
-                                                           sel_of<FT>(g), g->n_hot, g->part, g->G, g->st);
+    k_sweep_push<FT><<<push_grid(g), kScanThreads, 0, s>>>(rec_of<FT>(g), g->col_idx, F, g->region, g->fcount,
+                                                           g->pre, g->W, sel_of<FT>(g), g->n_hot, g->part, g->G,
+                                                           g->st);
 }
 
 template void launch_push<double>(di_graph *, double *, cudaStream_t);
