@@ -54,6 +54,23 @@ void *kernel_ptr(void *p) {
     return nullptr;
 }
 
+// Graph creation and solves allocate their buffers with cudaMallocAsync from the device's
+// default memory pool.  By default the pool hands freed memory back to the driver at every
+// synchronization, so the next allocation of the same size goes to the driver again; keeping
+// freed memory in the pool (this process only, for its lifetime) makes repeated creates and
+// solves allocate from the pool.
+static void keep_pool_memory(int dev) {
+    static bool done[64] = {};
+    if (dev < 0 || dev >= 64 || done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        unsigned long long keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done[dev] = true;
+}
+
 static di_status copy_in(void *dst, const void *src, size_t bytes, cudaStream_t s) {
     if (bytes == 0) return DI_OK;
     DI_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
@@ -129,6 +146,7 @@ di_status di_graph_create(int32_t n, const int32_t *row_ptr, const int32_t *col_
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->dev);
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaDeviceGetAttribute"));
     g->num_sms = sms > 0 ? sms : 152;
+    keep_pool_memory(g->dev);
     if ((e = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking)) != cudaSuccess)
         return fail(cuda_fail(e, "cudaStreamCreate"));
     if ((e = cudaEventCreate(&g->ev0)) != cudaSuccess) return fail(cuda_fail(e, "cudaEventCreate"));

@@ -60,12 +60,12 @@ __device__ __forceinline__ void push_row_lanes(const int *__restrict__ col_idx, 
 // The push.  The selected nodes with children of the largest class (a CTA per node)
 // are numbered 0..total-1 through the prefix sums of the scan and spread over all
 // CTAs; the middle class (a warp per node) and the smallest class (a lane per node,
-// two in flight) are taken per scan sub-chunk: push warp w walks the lists the scan's
+// four in flight) are taken per scan sub-chunk: push warp w walks the lists the scan's
 // warp w wrote.  The scan already moved each node's fluid into H; the push adds
 // d*sent/outdeg(i) to F_j along every out-link (ALGO-REF's inner loop), every load
 // of a node issued before its reductions.
 template <typename FT>
-__global__ void __launch_bounds__(kScanThreads) k_sweep_push(const RowRec<FT> *__restrict__ rec,
+__global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT> *__restrict__ rec,
                                                              const int *__restrict__ col_idx, FT *__restrict__ F,
                                                              const int *__restrict__ region,
                                                              const int *__restrict__ fcount,
@@ -101,40 +101,61 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_push(const RowRec<FT> *_
     // classes 2 and 1: push warp w takes the lists of scan sub-chunk w (and w + nwarps, ...):
     // the scan's per-warp counts are nearly even, and entries are read in list order
     for (int gs = gw; gs < W; gs += nwarps) {
-        // class 2: a warp per node
+        // class 2: a warp per node; lane j first fetches the entry and row record of node j of
+        // each group of 32, so only the column loads remain on each node's path
         {
             const int b = __ldg(region + 2 * (W + 1) + gs), c = __ldcg(fcount + 2 * W + gs);
-            for (int k = 0; k < c; ++k) {
-                const Sel<FT> e = sel[b + k];
-                const RowRec<FT> rr = rec[e.node];
-                if (lane == 0) edges += rr.deg;
-                push_row_lanes(col_idx, F, hot, n_hot, rr.beg, rr.deg, e.sent * rr.inv, lane, 32, pol);
+            for (int k0 = 0; k0 < c; k0 += 32) {
+                int mb = 0, md = 0;
+                FT mw = (FT)0;
+                if (k0 + lane < c) {
+                    const Sel<FT> e = sel[b + k0 + lane];
+                    const RowRec<FT> rr = rec[e.node];
+                    mb = rr.beg;
+                    md = rr.deg;
+                    mw = e.sent * rr.inv;
+                    edges += md;
+                }
+                const int m = min(32, c - k0);
+                for (int j = 0; j < m; ++j) {
+                    const int rb = __shfl_sync(kFull, mb, j), rd = __shfl_sync(kFull, md, j);
+                    const FT rw = __shfl_sync(kFull, mw, j);
+                    push_row_lanes(col_idx, F, hot, n_hot, rb, rd, rw, lane, 32, pol);
+                }
             }
         }
-        // class 1: a lane per node, two nodes in flight
+        // class 1: a lane per node, kInFlight nodes per lane at a time
+        constexpr int kInFlight = 4;
         const int b = __ldg(region + 1 * (W + 1) + gs), c = __ldcg(fcount + 1 * W + gs);
-        for (int k0 = 0; k0 < c; k0 += 64) {
-            const int ta = k0 + lane, tb = k0 + 32 + lane;
-            const bool has0 = ta < c, has1 = tb < c;
-            if (!has0) break;
-            const Sel<FT> e0 = sel[b + ta];
-            const Sel<FT> e1 = has1 ? sel[b + tb] : e0;
-            const RowRec<FT> r0 = rec[e0.node], r1 = rec[e1.node];
-            const int b0 = r0.beg, d0 = r0.deg;
-            const int b1 = r1.beg, d1 = has1 ? r1.deg : 0;
-            const FT w0 = e0.sent * r0.inv, w1 = e1.sent * r1.inv;
-            int c0[kOutCut1], c1[kOutCut1];
+        for (int k0 = 0; k0 < c; k0 += 32 * kInFlight) {
+            int rb[kInFlight], rd[kInFlight];
+            FT rw[kInFlight];
 #pragma unroll
-            for (int k = 0; k < kOutCut1; ++k) {
-                c0[k] = k < d0 ? __ldg(col_idx + b0 + k) : 0;
-                c1[k] = k < d1 ? __ldg(col_idx + b1 + k) : 0;
+            for (int u = 0; u < kInFlight; ++u) {
+                const int t = k0 + 32 * u + lane;
+                rd[u] = 0;
+                rb[u] = 0;
+                rw[u] = (FT)0;
+                if (t < c) {
+                    const Sel<FT> e = sel[b + t];
+                    const RowRec<FT> rr = rec[e.node];
+                    rb[u] = rr.beg;
+                    rd[u] = rr.deg;
+                    rw[u] = e.sent * rr.inv;
+                }
             }
-            edges += d0 + d1;
+            int cc[kInFlight][kOutCut1];
 #pragma unroll
-            for (int k = 0; k < kOutCut1; ++k) {
-                if (k < d0) push_one(F, hot, n_hot, c0[k], w0, pol);
-                if (k < d1) push_one(F, hot, n_hot, c1[k], w1, pol);
+            for (int u = 0; u < kInFlight; ++u) {
+                edges += rd[u];
+#pragma unroll
+                for (int k = 0; k < kOutCut1; ++k) cc[u][k] = k < rd[u] ? __ldg(col_idx + rb[u] + k) : 0;
             }
+#pragma unroll
+            for (int k = 0; k < kOutCut1; ++k)
+#pragma unroll
+                for (int u = 0; u < kInFlight; ++u)
+                    if (k < rd[u]) push_one(F, hot, n_hot, cc[u][k], rw[u], pol);
         }
     }
     // the CTA's sums for the hot targets go to F once
