@@ -166,15 +166,29 @@ __device__ void prefix_counts_staged(const int *__restrict__ fcount, int W, int 
     }
 }
 
-__device__ void prefix_counts(const int *__restrict__ fcount, int W, int *__restrict__ pre) {
+__device__ void prefix_counts(const int *__restrict__ fcount, int W, int *__restrict__ pre, int first_list = 0) {
     constexpr int kCap = 8192;                     // sub-chunks staged per pass (32 KB)
     __shared__ int s_c[kCap];
-    prefix_counts_staged(fcount, W, pre, s_c, kCap);
+    prefix_counts_staged(fcount, W, pre, s_c, kCap, first_list);
 }
 
 // sub-chunk holding item t of a list: the last g with pre[g] <= t
 __device__ __forceinline__ int find_sub(const int *__restrict__ pre, int W, int t) {
     int lo = 0, hi = W;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(pre + mid) <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// the same, knowing the answer is at least lo: a few steps forward, then a binary search
+__device__ __forceinline__ int find_sub_from(const int *__restrict__ pre, int W, int t, int lo) {
+    for (int k = 0; k < 4; ++k) {
+        if (__ldg(pre + lo + 1) > t) return lo;
+        ++lo;
+    }
+    int hi = W;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
         if (__ldg(pre + mid) <= t) lo = mid; else hi = mid;

@@ -57,18 +57,18 @@ __device__ __forceinline__ void push_row_lanes(const int *__restrict__ col_idx, 
     if (t < deg) push_one(F, hot, n_hot, __ldg(col_idx + beg + t), w, pol);
 }
 
-// The push.  The selected nodes with children of the largest class (a CTA per node)
-// are numbered 0..total-1 through the prefix sums of the scan and spread over all
-// CTAs; the middle class (a warp per node) and the smallest class (a lane per node,
-// four in flight) are taken per scan sub-chunk: push warp w walks the lists the scan's
-// warp w wrote.  The scan already moved each node's fluid into H; the push adds
+// The push.  The selected nodes with children of each class are numbered 0..total-1
+// through the prefix sums of the scan: the largest class (a CTA per node) and the
+// middle class (a warp per node) are strided over the CTAs / warps, which spreads heavy
+// rows evenly whatever the id order (R-MAT puts its heaviest rows on the lowest ids),
+// and the smallest class (a lane per node, four in flight, at most 8 out-links each) is
+// split into even rank ranges per warp.  The scan already moved each node's fluid into H; the push adds
 // d*sent/outdeg(i) to F_j along every out-link (ALGO-REF's inner loop), every load
 // of a node issued before its reductions.
 template <typename FT>
 __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT> *__restrict__ rec,
                                                              const int *__restrict__ col_idx, FT *__restrict__ F,
                                                              const int *__restrict__ region,
-                                                             const int *__restrict__ fcount,
                                                              const int *__restrict__ pre, int W,
                                                              const Sel<FT> *__restrict__ sel, int n_hot,
                                                              ScanPartial *__restrict__ part, int G,
@@ -98,52 +98,71 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
         if (threadIdx.x == 0) edges += rr.deg;
         push_row_lanes(col_idx, F, hot, n_hot, rr.beg, rr.deg, e.sent * rr.inv, threadIdx.x, kScanThreads, pol);
     }
-    // classes 2 and 1: push warp w takes the lists of scan sub-chunk w (and w + nwarps, ...):
-    // the scan's per-warp counts are nearly even, and entries are read in list order
-    for (int gs = gw; gs < W; gs += nwarps) {
-        // class 2: a warp per node; lane j first fetches the entry and row record of node j of
-        // each group of 32, so only the column loads remain on each node's path
-        {
-            const int b = __ldg(region + 2 * (W + 1) + gs), c = __ldcg(fcount + 2 * W + gs);
-            for (int k0 = 0; k0 < c; k0 += 32) {
-                int mb = 0, md = 0;
-                FT mw = (FT)0;
-                if (k0 + lane < c) {
-                    const Sel<FT> e = sel[b + k0 + lane];
-                    const RowRec<FT> rr = rec[e.node];
-                    mb = rr.beg;
-                    md = rr.deg;
-                    mw = e.sent * rr.inv;
-                    edges += md;
-                }
-                const int m = min(32, c - k0);
-                for (int j = 0; j < m; ++j) {
-                    const int rb = __shfl_sync(kFull, mb, j), rd = __shfl_sync(kFull, md, j);
-                    const FT rw = __shfl_sync(kFull, mw, j);
-                    push_row_lanes(col_idx, F, hot, n_hot, rb, rd, rw, lane, 32, pol);
-                }
+    // classes 2 and 1: each warp takes an even range of ranks of the class's list (ranks
+    // number the list entries over all sub-chunks, so the split is even however the selected
+    // nodes fall over the sub-chunks); a lane finds the sub-chunk of its rank from the
+    // warp's current one
+    {
+        // class 2: a warp per node, strided over the ranks (rank t to warp t mod nwarps), which
+        // interleaves heavy and light rows on any id order; lane j first finds and fetches the
+        // entry and row record of the warp's j-th node of each group of 32, so only the column
+        // loads remain on each node's path
+        const int *p2 = pre + 2 * (W + 1), *r2 = region + 2 * (W + 1);
+        const int tot = __ldg(p2 + W);
+        for (long long k0 = 0; gw + k0 * nwarps < tot; k0 += 32) {
+            const long long t = gw + (k0 + lane) * nwarps;
+            int mb = 0, md = 0;
+            FT mw = (FT)0;
+            if (t < tot) {
+                const int mg = find_sub(p2, W, (int)t);
+                const Sel<FT> e = sel[__ldg(r2 + mg) + ((int)t - __ldg(p2 + mg))];
+                const RowRec<FT> rr = rec[e.node];
+                mb = rr.beg;
+                md = rr.deg;
+                mw = e.sent * rr.inv;
+                edges += md;
+            }
+            const int m = (int)min(32LL, (tot - gw - k0 * nwarps + nwarps - 1) / nwarps);
+            for (int j = 0; j < m; ++j) {
+                const int rb = __shfl_sync(kFull, mb, j), rd = __shfl_sync(kFull, md, j);
+                const FT rw = __shfl_sync(kFull, mw, j);
+                push_row_lanes(col_idx, F, hot, n_hot, rb, rd, rw, lane, 32, pol);
             }
         }
+    }
+    {
         // class 1: a lane per node, kInFlight nodes per lane at a time
         constexpr int kInFlight = 4;
-        const int b = __ldg(region + 1 * (W + 1) + gs), c = __ldcg(fcount + 1 * W + gs);
-        for (int k0 = 0; k0 < c; k0 += 32 * kInFlight) {
+        const int *p1 = pre + 1 * (W + 1), *r1 = region + 1 * (W + 1);
+        const int tot = __ldg(p1 + W);
+        const int per = (tot + nwarps - 1) / nwarps;
+        const int t_beg = min(tot, gw * per), t_end = min(tot, t_beg + per);
+        int gs = 0;
+        if (t_beg < t_end) {
+            if (lane == 0) gs = find_sub(p1, W, t_beg);
+            gs = __shfl_sync(kFull, gs, 0);
+        }
+        for (int t0 = t_beg; t0 < t_end; t0 += 32 * kInFlight) {
             int rb[kInFlight], rd[kInFlight];
             FT rw[kInFlight];
+            int mg = gs;
 #pragma unroll
             for (int u = 0; u < kInFlight; ++u) {
-                const int t = k0 + 32 * u + lane;
+                const int t = t0 + 32 * u + lane;
                 rd[u] = 0;
                 rb[u] = 0;
                 rw[u] = (FT)0;
-                if (t < c) {
-                    const Sel<FT> e = sel[b + t];
+                if (t < t_end) {
+                    mg = find_sub_from(p1, W, t, mg);
+                    const Sel<FT> e = sel[__ldg(r1 + mg) + (t - __ldg(p1 + mg))];
                     const RowRec<FT> rr = rec[e.node];
                     rb[u] = rr.beg;
                     rd[u] = rr.deg;
                     rw[u] = e.sent * rr.inv;
                 }
             }
+            // every lane's last rank is below the next group's first: restart from the largest
+            gs = __reduce_max_sync(kFull, (unsigned)mg);
             int cc[kInFlight][kOutCut1];
 #pragma unroll
             for (int u = 0; u < kInFlight; ++u) {
@@ -174,8 +193,8 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
 
 template <typename FT>
 void launch_push(di_graph *g, FT *F, cudaStream_t s) {
-    k_sweep_push<FT><<<push_grid(g), kScanThreads, 0, s>>>(rec_of<FT>(g), g->col_idx, F, g->region, g->fcount,
-                                                           g->pre, g->W, sel_of<FT>(g), g->n_hot, g->part, g->G,
+    k_sweep_push<FT><<<push_grid(g), kScanThreads, 0, s>>>(rec_of<FT>(g), g->col_idx, F, g->region, g->pre,
+                                                           g->W, sel_of<FT>(g), g->n_hot, g->part, g->G,
                                                            g->st);
 }
 

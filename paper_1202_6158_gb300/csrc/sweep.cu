@@ -396,9 +396,8 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
     __syncthreads();
     if (s_ticket == gridDim.x - 1) {
         __threadfence();
-        // only the CTA-per-node list is spread by rank; the push walks the others per sub-chunk,
-        // and list 0 (dangling nodes) stays empty: the scan finishes those nodes itself
-        prefix_counts_staged(fcount, W, pre, reinterpret_cast<int *>(s_ring), (int)(sizeof(s_ring) / sizeof(int)), 3);
+        // list 0 (dangling nodes) stays empty: the scan finishes those nodes itself
+        prefix_counts_staged(fcount, W, pre, reinterpret_cast<int *>(s_ring), (int)(sizeof(s_ring) / sizeof(int)), 1);
         if (threadIdx.x == 0) *ticket = 0u;
     }
 }
