@@ -232,37 +232,35 @@ __device__ __forceinline__ void bpush_edge(float *__restrict__ Fb, int S, float 
     }
 }
 
-// one selected node's row: H += row; then row * d/outdeg to every child (a float4 of 4 queries per lane)
+// H_i += row for the 4 queries of this lane (FP64; node i is pushed by one lane group only)
+__device__ __forceinline__ void bpush_h(double *__restrict__ Hb, int S, int node, int l16, const float4 row) {
+    double2 *hp = reinterpret_cast<double2 *>(Hb + (long long)node * S + 4 * l16);
+    double2 a = hp[0], b = hp[1];
+    a.x += row.x;
+    a.y += row.y;
+    b.x += row.z;
+    b.y += row.w;
+    hp[0] = a;
+    hp[1] = b;
+}
+
+// row * d/outdeg to every child of a row {beg, deg}; this lane group takes out-links
+// e_beg, e_beg + e_step, ...
 template <int K>
-__device__ __forceinline__ void bpush_node(int node, const float4 row, int l16, int cls_node,
-                                           const RowRec<float> *__restrict__ rec, const int *__restrict__ col_idx,
-                                           float *__restrict__ Fb, double *__restrict__ Hb, int S, float *hot, int n_hot,
-                                           int e_beg, int e_step, bool do_h, long long &edges) {
-    if (do_h) {
-        double2 *hp = reinterpret_cast<double2 *>(Hb + (long long)node * S + 4 * l16);
-        double2 a = hp[0], b = hp[1];
-        a.x += row.x;
-        a.y += row.y;
-        b.x += row.z;
-        b.y += row.w;
-        hp[0] = a;
-        hp[1] = b;
-    }
-    if (cls_node == 0) return;
-    const RowRec<float> rr = rec[node];
-    const float4 wv = make_float4(row.x * rr.inv, row.y * rr.inv, row.z * rr.inv, row.w * rr.inv);
-    if (do_h && l16 == 0) edges += rr.deg;
+__device__ __forceinline__ void bpush_row(int beg, int deg, float inv, const float4 row, int l16,
+                                          const int *__restrict__ col_idx, float *__restrict__ Fb, int S, float *hot,
+                                          int n_hot, int e_beg, int e_step) {
+    const float4 wv = make_float4(row.x * inv, row.y * inv, row.z * inv, row.w * inv);
     int e = e_beg;
-    const int end = rr.deg;
-    for (; e + 3 * e_step < end; e += 4 * e_step) {
-        const int j0 = __ldg(col_idx + rr.beg + e), j1 = __ldg(col_idx + rr.beg + e + e_step);
-        const int j2 = __ldg(col_idx + rr.beg + e + 2 * e_step), j3 = __ldg(col_idx + rr.beg + e + 3 * e_step);
+    for (; e + 3 * e_step < deg; e += 4 * e_step) {
+        const int j0 = __ldg(col_idx + beg + e), j1 = __ldg(col_idx + beg + e + e_step);
+        const int j2 = __ldg(col_idx + beg + e + 2 * e_step), j3 = __ldg(col_idx + beg + e + 3 * e_step);
         bpush_edge<K>(Fb, S, hot, n_hot, j0, l16, wv);
         bpush_edge<K>(Fb, S, hot, n_hot, j1, l16, wv);
         bpush_edge<K>(Fb, S, hot, n_hot, j2, l16, wv);
         bpush_edge<K>(Fb, S, hot, n_hot, j3, l16, wv);
     }
-    for (; e < end; e += e_step) bpush_edge<K>(Fb, S, hot, n_hot, __ldg(col_idx + rr.beg + e), l16, wv);
+    for (; e < deg; e += e_step) bpush_edge<K>(Fb, S, hot, n_hot, __ldg(col_idx + beg + e), l16, wv);
 }
 
 template <int LPN>
@@ -297,53 +295,94 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_bpush(const RowRec<float> *
             __syncthreads();
             const int node = sel_node[pos];
             const float4 row = *reinterpret_cast<const float4 *>(sel_rows + (long long)pos * K + 4 * lq);
+            const RowRec<float> rr = rec[node];
             if (grp == 0) {  // H once
-                double2 *hp = reinterpret_cast<double2 *>(Hb + (long long)node * S + 4 * lq);
-                double2 a = hp[0], b = hp[1];
-                a.x += row.x;
-                a.y += row.y;
-                b.x += row.z;
-                b.y += row.w;
-                hp[0] = a;
-                hp[1] = b;
-                if (lq == 0) edges += rec[node].deg;
+                bpush_h(Hb, S, node, lq, row);
+                if (lq == 0) edges += rr.deg;
             }
-            bpush_node<K>(node, row, lq, 3, rec, col_idx, Fb, Hb, S, hot, n_hot, grp, GPC, false, edges);
+            bpush_row<K>(rr.beg, rr.deg, rr.inv, row, lq, col_idx, Fb, S, hot, n_hot, grp, GPC);
         }
     }
-    // class 2: a warp per node, its 32/LPN lane groups taking every (32/LPN)-th out-link
+    // class 2: a warp per node, its 32/LPN lane groups taking every (32/LPN)-th out-link.  The
+    // ranks are strided over the warps (rank t to warp t mod nwarps); lane j first finds and
+    // loads the list position, node and row record of the warp's j-th node of each group of 32
     {
         constexpr int GPW = 32 / LPN;
         const int lane = threadIdx.x & 31, gi = lane / LPN;
         const int nwarps = gridDim.x * kWarps, gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
-        const int *p2 = pre + 2 * (W + 1);
+        const int *p2 = pre + 2 * (W + 1), *r2 = region + 2 * (W + 1);
         const int tot = __ldg(p2 + W);
-        for (int t = gw; t < tot; t += nwarps) {
-            int pos = 0;
-            if (lane == 0) {
-                const int gs = find_sub(p2, W, t);
-                pos = region[2 * (W + 1) + gs] + (t - __ldg(p2 + gs));
+        for (long long k0 = 0; gw + k0 * nwarps < tot; k0 += 32) {
+            const long long t = gw + (k0 + lane) * nwarps;
+            int mpos = 0, mnode = 0, mb = 0, md = 0;
+            float mi = 0.f;
+            if (t < tot) {
+                const int gs = find_sub(p2, W, (int)t);
+                mpos = __ldg(r2 + gs) + ((int)t - __ldg(p2 + gs));
+                mnode = sel_node[mpos];
+                const RowRec<float> rr = rec[mnode];
+                mb = rr.beg;
+                md = rr.deg;
+                mi = rr.inv;
             }
-            pos = __shfl_sync(kFull, pos, 0);
-            const int node = sel_node[pos];
-            const float4 row = *reinterpret_cast<const float4 *>(sel_rows + (long long)pos * K + 4 * lq);
-            bpush_node<K>(node, row, lq, 2, rec, col_idx, Fb, Hb, S, hot, n_hot, gi, GPW, gi == 0, edges);
+            const int m = (int)min(32LL, (tot - gw - k0 * nwarps + nwarps - 1) / nwarps);
+            for (int j = 0; j < m; ++j) {
+                const int pos = __shfl_sync(kFull, mpos, j), node = __shfl_sync(kFull, mnode, j);
+                const int rb = __shfl_sync(kFull, mb, j), rd = __shfl_sync(kFull, md, j);
+                const float ri = __shfl_sync(kFull, mi, j);
+                const float4 row = *reinterpret_cast<const float4 *>(sel_rows + (long long)pos * K + 4 * lq);
+                if (gi == 0) {
+                    bpush_h(Hb, S, node, lq, row);
+                    if (lq == 0) edges += rd;
+                }
+                bpush_row<K>(rb, rd, ri, row, lq, col_idx, Fb, S, hot, n_hot, gi, GPW);
+            }
         }
     }
-    // classes 0, 1: a lane group per node, contiguous ranges per group
-    for (int L = 0; L < 2; ++L) {
-        const int *pl = pre + L * (W + 1);
-        const int tot = __ldg(pl + W);
-        const int per = (tot + ngrp - 1) / ngrp;
-        const int t_beg = min(tot, ggrp * per), t_end = min(tot, t_beg + per);
-        if (t_beg >= t_end) continue;
-        int gl = find_sub(pl, W, t_beg);
-        for (int t = t_beg; t < t_end; ++t) {
-            while (__ldg(pl + gl + 1) <= t) ++gl;
-            const int pos = region[L * (W + 1) + gl] + (t - __ldg(pl + gl));
-            const int node = sel_node[pos];
-            const float4 row = *reinterpret_cast<const float4 *>(sel_rows + (long long)pos * K + 4 * lq);
-            bpush_node<K>(node, row, lq, L, rec, col_idx, Fb, Hb, S, hot, n_hot, 0, 1, true, edges);
+    // classes 0, 1: a lane group per node, contiguous rank ranges per group; lane q of a
+    // group first finds and loads the position, node and row record of the group's q-th
+    // node of each run of LPN
+    {
+        const int lane = threadIdx.x & 31;
+        const unsigned gmask = (LPN == 32 ? kFull : ((1u << LPN) - 1u)) << (lane & ~(LPN - 1));
+        for (int L = 0; L < 2; ++L) {
+            const int *pl = pre + L * (W + 1), *rl = region + L * (W + 1);
+            const int tot = __ldg(pl + W);
+            const int per = (tot + ngrp - 1) / ngrp;
+            const int t_beg = min(tot, ggrp * per), t_end = min(tot, t_beg + per);
+            int gl = 0;
+            if (t_beg < t_end) gl = find_sub(pl, W, t_beg);   // the same in every lane of the group
+            for (int i0 = 0; i0 < per; i0 += LPN) {
+                const int t = t_beg + i0 + lq;
+                int mpos = 0, mnode = 0, mb = 0, md = 0, mg = gl;
+                float mi = 0.f;
+                if (t < t_end) {
+                    mg = find_sub_from(pl, W, t, gl);
+                    mpos = __ldg(rl + mg) + (t - __ldg(pl + mg));
+                    mnode = sel_node[mpos];
+                    if (L == 1) {
+                        const RowRec<float> rr = rec[mnode];
+                        mb = rr.beg;
+                        md = rr.deg;
+                        mi = rr.inv;
+                    }
+                }
+#pragma unroll
+                for (int o = 1; o < LPN; o <<= 1) mg = max(mg, __shfl_xor_sync(gmask, mg, o, LPN));
+                gl = mg;
+                const int m = min(LPN, t_end - (t_beg + i0));
+                for (int j = 0; j < m; ++j) {
+                    const int pos = __shfl_sync(gmask, mpos, j, LPN), node = __shfl_sync(gmask, mnode, j, LPN);
+                    const float4 row = *reinterpret_cast<const float4 *>(sel_rows + (long long)pos * K + 4 * lq);
+                    bpush_h(Hb, S, node, lq, row);
+                    if (L == 1) {
+                        const int rb = __shfl_sync(gmask, mb, j, LPN), rd = __shfl_sync(gmask, md, j, LPN);
+                        const float ri = __shfl_sync(gmask, mi, j, LPN);
+                        if (lq == 0) edges += rd;
+                        bpush_row<K>(rb, rd, ri, row, lq, col_idx, Fb, S, hot, n_hot, 0, 1);
+                    }
+                }
+            }
         }
     }
     __syncthreads();
@@ -445,13 +484,26 @@ __global__ void k_bconfirm(int n, BatchQ *__restrict__ bq, BatchCtl *__restrict_
     if (threadIdx.x == 0 && s_open && ctl->all_done == 1) ctl->all_done = 0;
 }
 
-// out[q][i] = Hb[new_of[i]][q] for the first k queries, back in the caller's numbering
-__global__ void k_bgather(int n, int k, int K, const int *__restrict__ new_of, const double *__restrict__ Hb,
-                          double *__restrict__ out) {
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < (long long)n * K;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(t / K), q = (int)(t % K);
-        if (q < k) out[(long long)q * n + i] = Hb[(long long)new_of[i] * K + q];
+// out[q][i] = Hb[new_of[i]][q] for the first k queries, back in the caller's numbering.  A
+// CTA transposes a tile of kGatherTile nodes through shared memory: it reads their K-wide
+// rows, then writes kGatherTile consecutive outputs of each query.
+constexpr int kGatherTile = 32;
+__global__ void __launch_bounds__(256) k_bgather(int n, int k, int K, const int *__restrict__ new_of,
+                                                 const double *__restrict__ Hb, double *__restrict__ out) {
+    __shared__ double tile[kGatherTile][kLanes + 1];
+    const int ntiles = (n + kGatherTile - 1) / kGatherTile;
+    for (int b = blockIdx.x; b < ntiles; b += gridDim.x) {
+        const int i0 = b * kGatherTile;
+        for (int t = threadIdx.x; t < kGatherTile * K; t += blockDim.x) {
+            const int ii = t / K, q = t % K;
+            if (i0 + ii < n && q < k) tile[ii][q] = Hb[(long long)new_of[i0 + ii] * K + q];
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < kGatherTile * k; t += blockDim.x) {
+            const int q = t / kGatherTile, ii = t % kGatherTile;
+            if (i0 + ii < n) out[(long long)q * n + i0 + ii] = tile[ii][q];
+        }
+        __syncthreads();
     }
 }
 
@@ -767,7 +819,8 @@ di_status run_query_batch(di_graph *g, int k, const int *seed_ptr, const int *se
             DI_CUDA(cudaMallocAsync(&tmp, sizeof(double) * (size_t)n * k, s));
             dst = tmp;
         }
-        k_bgather<<<grid, 256, 0, s>>>(n, k, K, g->new_of, p->Hb, dst);
+        k_bgather<<<std::max(1, std::min((n + kGatherTile - 1) / kGatherTile, g->num_sms * 8)), 256, 0, s>>>(
+            n, k, K, g->new_of, p->Hb, dst);
         DI_CUDA(cudaGetLastError());
         if (tmp) {
             DI_CUDA(cudaMemcpyAsync(H_out, tmp, sizeof(double) * (size_t)n * k, cudaMemcpyDeviceToHost, s));
