@@ -41,6 +41,9 @@
 namespace diter {
 namespace {
 
+// a sweep pulls when the previous sweep's selected nodes held at least 1/kPullShare of all out-links
+constexpr long long kPullShare = 4;
+
 __device__ __forceinline__ void red_add_v4(float *p, float4 v) {
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w));
 }
@@ -83,6 +86,8 @@ __global__ void k_bctl_init(int k, BatchQ *__restrict__ bq, BatchCtl *__restrict
         ctl->max_sweeps = max_sweeps;
         ctl->edges = 0;
         ctl->srcs = 0;
+        ctl->sel_edges = 0;
+        ctl->pull = 0;
         ctl->beta = beta;
         ctl->body_runs = 0;
         ctl->round_sweeps = 0;
@@ -103,8 +108,8 @@ __global__ void __launch_bounds__(kScanThreads) k_bscan(int wchunk, int S, float
                                                         const int *__restrict__ region, int W,
                                                         int *__restrict__ fcount, int *__restrict__ pre,
                                                         unsigned *__restrict__ ticket, int *__restrict__ sel_node,
-                                                        float *__restrict__ sel_rows, BatchQ *__restrict__ bq,
-                                                        BatchCtl *__restrict__ ctl, double d) {
+                                                        float *__restrict__ sel_rows, int *__restrict__ spos,
+                                                        BatchQ *__restrict__ bq, BatchCtl *__restrict__ ctl, double d) {
     constexpr int K = 4 * LPN, NPS = 32 / LPN;
     __shared__ double s_l1[K], s_rem[K];
     __shared__ int s_sel[K];
@@ -131,6 +136,7 @@ __global__ void __launch_bounds__(kScanThreads) k_bscan(int wchunk, int S, float
     float l1[4] = {0.f, 0.f, 0.f, 0.f}, rem[4] = {0.f, 0.f, 0.f, 0.f};
     int sel4[4] = {0, 0, 0, 0};
     int nsel = 0;
+    const bool pull = ctl->pull != 0;  // the push kernel reads the lists, the pull kernel the positions
     const int nsteps = wchunk / NPS;
     float4 cur = *reinterpret_cast<const float4 *>(Fb + (wbeg + h) * S + 4 * lq);
     int ccur = cls[wbeg + h];
@@ -173,6 +179,7 @@ __global__ void __launch_bounds__(kScanThreads) k_bscan(int wchunk, int S, float
             }
             *reinterpret_cast<float4 *>(Fb + node * S + 4 * lq) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        if (pull && lq == 0) spos[node] = act ? pos : -1;
         cur = nxt;
         ccur = cnxt;
     }
@@ -275,12 +282,12 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_bpush(const RowRec<float> *
     __shared__ float hot[kBatchHot * K];
     __shared__ long long s_red[kWarps];
     __shared__ int s_idx;
-    if (ctl->all_done) return;
+    if (ctl->all_done || ctl->pull) return;
     for (int t = threadIdx.x; t < kBatchHot * K; t += kScanThreads) hot[t] = 0.f;
     __syncthreads();
     const int grp = threadIdx.x / LPN, lq = threadIdx.x % LPN;
     const int ngrp = gridDim.x * GPC, ggrp = blockIdx.x * GPC + grp;
-    long long edges = 0;
+    long long edges = 0;  // out-links of the pushed nodes
     // class 3: the whole CTA per node, each lane group taking every GPC-th out-link
     {
         const int *p3 = pre + 3 * (W + 1);
@@ -391,13 +398,123 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_bpush(const RowRec<float> *
         if (v != 0.f) atomicAdd(Fb + (long long)(t / K) * S + t % K, v);
     }
     const long long be = block_sum(edges, s_red);
-    if (threadIdx.x == 0 && be) atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->edges),
-                                          (unsigned long long)be);
+    if (threadIdx.x == 0 && be)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->sel_edges), (unsigned long long)be);
+}
+
+__device__ __forceinline__ bool nonzero4(const float4 r) { return r.x != 0.f || r.y != 0.f || r.z != 0.f || r.w != 0.f; }
+
+__device__ __forceinline__ void fma4(float4 &acc, const float4 r, float w) {
+    acc.x = fmaf(r.x, w, acc.x);
+    acc.y = fmaf(r.y, w, acc.y);
+    acc.z = fmaf(r.z, w, acc.z);
+    acc.w = fmaf(r.w, w, acc.w);
+}
+
+// The pull direction of a dense sweep: the same diffusion as k_bpush, read from the target
+// side.  First every selected node's row goes to H (contiguous rank ranges per lane group).
+// Then the in-links, in target order, are cut into even ranges, one per lane group: the
+// group walks its range, gathers row(src) * d/outdeg(src) of every selected source from the
+// compact list of the sweep (small enough to stay in L2), sums the in-links of one target
+// in registers and adds the sum to the target's row with one red.global.add.v4.f32 per lane
+// (an atomic only because a target's in-links may straddle two ranges).
+template <int LPN>
+__global__ void __launch_bounds__(kScanThreads, 4) k_bpull(const RowRec<float> *__restrict__ rec,
+                                                        const int *__restrict__ in_src,
+                                                        const int *__restrict__ in_dst,
+                                                        const float *__restrict__ inv_deg, long long nnz,
+                                                        const int *__restrict__ spos, float *__restrict__ Fb,
+                                                        double *__restrict__ Hb, int S, const int *__restrict__ region,
+                                                        const int *__restrict__ pre, int W,
+                                                        const int *__restrict__ sel_node,
+                                                        const float *__restrict__ sel_rows,
+                                                        BatchCtl *__restrict__ ctl) {
+    constexpr int K = 4 * LPN, GPC = kScanThreads / LPN;
+    __shared__ long long s_red[kWarps];
+    if (ctl->all_done || !ctl->pull) return;
+    const int lane = threadIdx.x & 31, grp = threadIdx.x / LPN, lq = threadIdx.x % LPN;
+    const int ngrp = gridDim.x * GPC, ggrp = blockIdx.x * GPC + grp;
+    const unsigned gmask = (LPN == 32 ? kFull : ((1u << LPN) - 1u)) << (lane & ~(LPN - 1));
+    // H_i += row_i for every selected node, all classes; their out-links are counted here
+    long long edges = 0;
+    for (int L = 0; L < kLists; ++L) {
+        const int *pl = pre + L * (W + 1), *rl = region + L * (W + 1);
+        const int tot = __ldg(pl + W);
+        const int per = (tot + ngrp - 1) / ngrp;
+        const int t_beg = min(tot, ggrp * per), t_end = min(tot, t_beg + per);
+        int gl = 0;
+        if (t_beg < t_end) gl = find_sub(pl, W, t_beg);
+        for (int i0 = 0; i0 < per; i0 += LPN) {
+            const int t = t_beg + i0 + lq;
+            int mpos = 0, mnode = 0, mg = gl;
+            if (t < t_end) {
+                mg = find_sub_from(pl, W, t, gl);
+                mpos = __ldg(rl + mg) + (t - __ldg(pl + mg));
+                mnode = sel_node[mpos];
+                if (L > 0) edges += __ldg(&rec[mnode].deg);
+            }
+#pragma unroll
+            for (int o = 1; o < LPN; o <<= 1) mg = max(mg, __shfl_xor_sync(gmask, mg, o, LPN));
+            gl = mg;
+            const int m = min(LPN, t_end - (t_beg + i0));
+            for (int j = 0; j < m; ++j) {
+                const int pos = __shfl_sync(gmask, mpos, j, LPN), node = __shfl_sync(gmask, mnode, j, LPN);
+                bpush_h(Hb, S, node, lq, *reinterpret_cast<const float4 *>(sel_rows + (long long)pos * K + 4 * lq));
+            }
+        }
+    }
+    // the in-links
+    constexpr int kU = 4;  // rows gathered before they are summed
+    const long long per = (nnz + ngrp - 1) / ngrp;
+    const long long e_beg = min(nnz, (long long)ggrp * per), e_end = min(nnz, e_beg + per);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    int cur = -1;
+    for (long long i0 = 0; i0 < per; i0 += LPN) {
+        const long long e = e_beg + i0 + lq;
+        int mdst = -1, mpos = -1;
+        float mw = 0.f;
+        if (e < e_end) {
+            const int src = __ldg(in_src + e);
+            mdst = __ldg(in_dst + e);
+            mpos = __ldg(spos + src);
+            mw = __ldg(inv_deg + src);
+        }
+        const int m = (int)min((long long)LPN, e_end - e_beg - i0);
+        for (int j0 = 0; j0 < m; j0 += kU) {
+            float4 r[kU];
+            int dd[kU];
+            float ww[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int j = (j0 + u) & (LPN - 1);
+                const int pj = __shfl_sync(gmask, mpos, j, LPN);
+                dd[u] = __shfl_sync(gmask, mdst, j, LPN);
+                ww[u] = __shfl_sync(gmask, mw, j, LPN);
+                r[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (j0 + u < m && pj >= 0) r[u] = *reinterpret_cast<const float4 *>(sel_rows + (long long)pj * K + 4 * lq);
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                if (j0 + u < m) {
+                    if (dd[u] != cur) {
+                        if (cur >= 0 && nonzero4(acc)) red_add_v4(Fb + (long long)cur * S + 4 * lq, acc);
+                        acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                        cur = dd[u];
+                    }
+                    fma4(acc, r[u], ww[u]);
+                }
+            }
+        }
+    }
+    if (cur >= 0 && nonzero4(acc)) red_add_v4(Fb + (long long)cur * S + 4 * lq, acc);
+    const long long be = block_sum(edges, s_red);
+    if (threadIdx.x == 0 && be)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&ctl->sel_edges), (unsigned long long)be);
 }
 
 // one thread per lane.  The loop ends when no lane is open or at the sweep limit; a
 // serving round also ends after round_cap sweeps, or when a lane stops (stop_on_done).
-__global__ void k_bfinalize(int n, BatchQ *__restrict__ bq, BatchCtl *__restrict__ ctl,
+__global__ void k_bfinalize(int n, long long pull_edges, BatchQ *__restrict__ bq, BatchCtl *__restrict__ ctl,
                             cudaGraphConditionalHandle handle, int in_graph) {
     __shared__ int s_open, s_newly;
     if (ctl->all_done) {
@@ -440,6 +557,11 @@ __global__ void k_bfinalize(int n, BatchQ *__restrict__ bq, BatchCtl *__restrict
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        // the next sweep pulls when this one's selected nodes held at least pull_edges out-links
+        const long long se = ctl->sel_edges;
+        ctl->edges += se;
+        ctl->sel_edges = 0;
+        ctl->pull = se >= pull_edges ? 1 : 0;
         ctl->body_runs += 1;
         ctl->sweeps += 1;
         ctl->round_sweeps += 1;
@@ -627,11 +749,16 @@ template <int LPN>
 void capture_batch_body(di_graph *g, BatchPool *p, cudaGraphConditionalHandle handle, int S) {
     const int nhot = std::min(g->n_hot, kBatchHot);
     k_bscan<LPN><<<g->G, kScanThreads, 0, g->cap>>>(g->chunk / kWarps, S, p->Fb, g->cls, g->region, g->W, p->fcount,
-                                                    p->pre, p->ticket, p->selb_node, p->selb_rows, p->bq, p->bctl,
-                                                    g->d);
+                                                    p->pre, p->ticket, p->selb_node, p->selb_rows, p->spos, p->bq,
+                                                    p->bctl, g->d);
     k_bpush<LPN><<<push_grid(g), kScanThreads, 0, g->cap>>>(g->rec32, g->col_idx, p->Fb, p->Hb, S, g->region, p->pre, g->W,
                                                     p->selb_node, p->selb_rows, nhot, p->bctl);
-    k_bfinalize<<<1, kLanes, 0, g->cap>>>(g->n, p->bq, p->bctl, handle, 1);
+    k_bpull<LPN><<<push_grid(g), kScanThreads, 0, g->cap>>>(g->rec32, g->in_src, g->in_dst, g->inv_deg32, g->nnz, p->spos,
+                                                    p->Fb, p->Hb, S, g->region, p->pre, g->W, p->selb_node,
+                                                    p->selb_rows, p->bctl);
+    // rows of 4 lanes always push: their 16-byte reductions cost no more than the pull's gathers
+    const long long pull_edges = LPN >= 2 ? std::max(1LL, (g->nnz + kPullShare - 1) / kPullShare) : LLONG_MAX;
+    k_bfinalize<<<1, kLanes, 0, g->cap>>>(g->n, pull_edges, p->bq, p->bctl, handle, 1);
 }
 
 int batch_grid(const di_graph *g, long long work) {
@@ -679,13 +806,19 @@ di_status pool_build_loop(di_graph *g, BatchPool *p, int slot) {
 }
 
 long long pool_bytes(const di_graph *g, int lanes) {
-    const long long rows = (long long)g->G * g->chunk, n = g->n;
-    return lanes * (4 * rows + 12 * n) + 4 * n + (long long)sizeof(int) * kLists * (2 * g->W + 1) +
-           (long long)(sizeof(BatchQ) * kLanes + sizeof(BatchCtl)) + 256;
+    const long long rows = (long long)g->G * g->chunk, n = g->n, L = g->nnz;
+    // the graph's in-link CSR, its bins and in_dst, unless an earlier call built them
+    const long long tr = (g->transposed ? 0 : 4 * (n + 1) + 4 * L + 8 * n + 4 * (n + 1)) + (g->in_dst ? 0 : 4 * L);
+    return lanes * (4 * rows + 12 * n) + 4 * n + 4 * rows + (long long)sizeof(int) * kLists * (2 * g->W + 1) +
+           (long long)(sizeof(BatchQ) * kLanes + sizeof(BatchCtl)) + 256 + tr;
 }
 
 di_status pool_alloc(di_graph *g, BatchPool *p, int lanes, cudaStream_t s) {
     if (p->Fb) return DI_OK;
+    {
+        di_status r = build_in_dst(g);  // the in-links of the pull direction
+        if (r != DI_OK) return r;
+    }
     const long long rows = (long long)g->G * g->chunk;
     p->rows = rows;
     p->cap_lanes = lanes;
@@ -693,6 +826,7 @@ di_status pool_alloc(di_graph *g, BatchPool *p, int lanes, cudaStream_t s) {
     DI_CUDA(cudaMallocAsync(&p->Hb, sizeof(double) * lanes * (size_t)g->n, s));
     DI_CUDA(cudaMallocAsync(&p->selb_rows, sizeof(float) * lanes * (size_t)g->n, s));
     DI_CUDA(cudaMallocAsync(&p->selb_node, sizeof(int) * (size_t)g->n, s));
+    DI_CUDA(cudaMallocAsync(&p->spos, sizeof(int) * (size_t)rows, s));
     DI_CUDA(cudaMallocAsync(&p->fcount, sizeof(int) * kLists * (size_t)g->W, s));
     DI_CUDA(cudaMallocAsync(&p->pre, sizeof(int) * kLists * (size_t)(g->W + 1), s));
     DI_CUDA(cudaMallocAsync(&p->ticket, sizeof(unsigned), s));
@@ -710,7 +844,7 @@ void pool_free(BatchPool *p, cudaStream_t s) {
         if (p->exec[k]) cudaGraphExecDestroy(p->exec[k]);
         if (p->graph[k]) cudaGraphDestroy(p->graph[k]);
     }
-    void *bufs[] = {p->Fb, p->Hb, p->selb_rows, p->selb_node, p->fcount, p->pre, p->ticket, p->bq, p->bctl};
+    void *bufs[] = {p->Fb, p->Hb, p->selb_rows, p->selb_node, p->spos, p->fcount, p->pre, p->ticket, p->bq, p->bctl};
     for (void *b : bufs)
         if (b) cudaFreeAsync(b, s);
     cudaStreamSynchronize(s);

@@ -762,4 +762,15 @@ di_status build_transpose(di_graph *g) {
     return DI_OK;
 }
 
+di_status build_in_dst(di_graph *g) {
+    if (g->in_dst) return DI_OK;
+    di_status r = build_transpose(g);
+    if (r != DI_OK) return r;
+    const long long L = g->nnz;
+    DI_CUDA(cudaMallocAsync(&g->in_dst, sizeof(int) * (size_t)std::max<long long>(L, 1), g->stream));
+    if (L > 0) k_expand_rows<<<grid_for(L, 256, g->num_sms), 256, 0, g->stream>>>(g->n, L, g->in_ptr, g->in_dst);
+    DI_CUDA(cudaGetLastError());
+    return DI_OK;
+}
+
 }  // namespace diter

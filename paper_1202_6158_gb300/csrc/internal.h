@@ -128,7 +128,8 @@ struct BatchCtl {
     int stop_on_done;      // the loop also returns when a lane stops
     int lane_max_sweeps;   // a lane stops (done = 2) after this many sweeps
     int newly;             // a lane stopped in the current launch
-    int pad;
+    int pull;              // this sweep's direction: 0 push from the selected rows, 1 pull into every row
+    long long sel_edges;   // out-links of the sweep's selected nodes, summed by the scan
 };
 
 // lanes to free and lanes to start, applied by the kernel that opens a round of the serving loop
@@ -171,6 +172,7 @@ struct BatchPool {
     double *Hb = nullptr;              // [n][K] histories, FP64
     float *selb_rows = nullptr;        // [n][K] rows of the selected nodes of a sweep
     int *selb_node = nullptr;          // [n]
+    int *spos = nullptr;               // [rows] list position of each node selected in the sweep, -1 otherwise
     int *fcount = nullptr, *pre = nullptr;
     unsigned *ticket = nullptr;
     BatchQ *bq = nullptr, *h_bq = nullptr;
@@ -195,6 +197,7 @@ struct di_graph {
     // graph
     int *row_ptr = nullptr, *col_idx = nullptr;
     int *in_ptr = nullptr, *in_src = nullptr;   // built at first use (build_transpose)
+    int *in_dst = nullptr;                      // [L] target of each in-link, built with the first batch pool
     bool transposed = false;
     int *bin_of = nullptr, *in_bin_of = nullptr, *pull_ids = nullptr;
     unsigned char *cls = nullptr;      // [npad] out-degree class per node, 0 on the padding
@@ -267,6 +270,7 @@ di_status cuda_fail(cudaError_t e, const char *what);
 
 // graph ingest (graph_build.cu)
 di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_dev);
+di_status build_in_dst(di_graph *g);  // the transpose, then in_dst
 di_status build_transpose(di_graph *g);   // the in-link CSR and its bins, at first use
 di_status validate_v(di_graph *g, const double *V_dev);
 
