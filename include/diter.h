@@ -82,7 +82,10 @@ typedef struct {
     int32_t profile;         /* 1: launch each sweep's kernels from the host with CUDA events around
                                 each one (same kernels and arguments, no graph); read with di_get_profile */
     int32_t select;          /* a di_select value: which nodes a sweep diffuses (default DI_SELECT_REF) */
-    int32_t pad;
+    int32_t direction;       /* 0: every sweep pushes along the selected nodes' out-links; 1: a sweep
+                                pulls along every node's in-links instead when the previous sweep
+                                diffused at least a quarter of all out-links (the same diffusion; the
+                                in-link CSR is built at first use, 8 bytes per link) */
 } di_solve_opts;
 
 /*
@@ -113,6 +116,8 @@ typedef struct {
     int64_t pushed;        /* selected nodes with at least one out-link (frontier entries) */
     double scan_ms;        /* CUDA-event time of the sweep's scan kernel (profiled solves, else 0) */
     double push_ms;        /* CUDA-event time of the sweep's push kernel (profiled solves, else 0) */
+    int32_t pull;          /* 1: the sweep pulled along the in-links (di_solve_opts.direction), 0: pushed */
+    int32_t pad;
 } di_sweep_record;
 
 typedef struct {

@@ -61,15 +61,15 @@ def di_solve(handle, tol, H_out, max_edge_pushes=0, prec=DI_FP64, normalize=0, a
     return rc, st.as_dict()
 
 
-def _opts(tol, beta, max_edge_pushes, max_sweeps, prec, normalize, trace, profile, select):
+def _opts(tol, beta, max_edge_pushes, max_sweeps, prec, normalize, trace, profile, select, direction=0):
     sel = _lib.SELECT[select] if isinstance(select, str) else int(select)
     return di_solve_opts(float(tol), float(beta), int(max_edge_pushes), int(max_sweeps), int(prec), int(normalize),
-                         int(trace), int(profile), sel, 0)
+                         int(trace), int(profile), sel, int(direction))
 
 
 def di_solve_ex(handle, H_out, tol, beta=0.5, max_edge_pushes=0, max_sweeps=0, prec=DI_FP64, normalize=0, trace=0,
-                profile=0, allow_unconverged=False, select="ref"):
-    o = _opts(tol, beta, max_edge_pushes, max_sweeps, prec, normalize, trace, profile, select)
+                profile=0, allow_unconverged=False, select="ref", direction=0):
+    o = _opts(tol, beta, max_edge_pushes, max_sweeps, prec, normalize, trace, profile, select, direction)
     st = di_stats()
     ok = (DI_OK, DI_ENOTCONVERGED) if allow_unconverged else (DI_OK,)
     rc = check(load().di_solve_ex(handle, ctypes.byref(o), ptr(H_out), ctypes.byref(st)), ok)
@@ -88,9 +88,9 @@ def di_autotune(handle, tol, prec=DI_FP64, max_sweeps=0, max_edge_pushes=0):
 
 
 def di_solve_update(old_handle, new_handle, H_out, tol, beta=0.5, max_edge_pushes=0, max_sweeps=0, trace=0,
-                    profile=0, allow_unconverged=False, select="ref"):
+                    profile=0, allow_unconverged=False, select="ref", direction=0):
     """Continue old_handle's FP64 state on the updated graph new_handle (Section 3.2)."""
-    o = _opts(tol, beta, max_edge_pushes, max_sweeps, DI_FP64, 0, trace, profile, select)
+    o = _opts(tol, beta, max_edge_pushes, max_sweeps, DI_FP64, 0, trace, profile, select, direction)
     st = di_stats()
     ok = (DI_OK, DI_ENOTCONVERGED) if allow_unconverged else (DI_OK,)
     rc = check(load().di_solve_update(old_handle, new_handle, ctypes.byref(o), ptr(H_out), ctypes.byref(st)), ok)

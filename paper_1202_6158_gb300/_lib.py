@@ -43,13 +43,14 @@ class di_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("beta", ctypes.c_double), ("max_edge_pushes", ctypes.c_int64),
                 ("max_sweeps", ctypes.c_int32), ("prec", ctypes.c_int32), ("normalize", ctypes.c_int32),
                 ("trace", ctypes.c_int32), ("profile", ctypes.c_int32), ("select", ctypes.c_int32),
-                ("pad", ctypes.c_int32)]
+                ("direction", ctypes.c_int32)]
 
 
 class di_sweep_record(ctypes.Structure):
     _fields_ = [("l1_F", ctypes.c_double), ("removed", ctypes.c_double), ("R", ctypes.c_double), ("T", ctypes.c_double),
                 ("sources", ctypes.c_int64), ("edges", ctypes.c_int64), ("pushed", ctypes.c_int64),
-                ("scan_ms", ctypes.c_double), ("push_ms", ctypes.c_double)]
+                ("scan_ms", ctypes.c_double), ("push_ms", ctypes.c_double), ("pull", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
 
 class di_profile(ctypes.Structure):

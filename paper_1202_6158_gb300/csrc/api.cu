@@ -80,12 +80,12 @@ static di_status copy_in(void *dst, const void *src, size_t bytes, cudaStream_t 
 static void free_graph(di_graph *g) {
     if (!g) return;
     if (g->stream || g->cap) cudaStreamSynchronize(g->stream);
-    for (int k = 0; k < 7; ++k) {
+    for (int k = 0; k < kSweepSlots; ++k) {
         if (g->exec[k]) cudaGraphExecDestroy(g->exec[k]);
         if (g->graph[k]) cudaGraphDestroy(g->graph[k]);
     }
     pool_free(g->bp, g->stream);
-    void *bufs[] = {g->row_ptr, g->col_idx, g->in_ptr, g->in_src, g->in_dst, g->bin_of, g->in_bin_of, g->pull_ids, g->V,
+    void *bufs[] = {g->row_ptr, g->col_idx, g->in_ptr, g->in_src, g->in_dst, g->wpull, g->bin_of, g->in_bin_of, g->pull_ids, g->V,
                     g->inv_deg, g->inv_deg32, g->hot_ids, g->perm, g->new_of, g->rec64, g->rec32,
                     g->wsel[0], g->wsel[1], g->rowhash, g->long_prefix, g->region, g->fcount, g->pre, g->ticket, g->sel, g->cls, g->F64, g->F32, g->H, g->part, g->st,
                     g->trace, g->X, g->Z[0], g->Z[1], g->Ylong, g->ppart, g->pst};

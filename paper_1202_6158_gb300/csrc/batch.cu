@@ -41,9 +41,6 @@
 namespace diter {
 namespace {
 
-// a sweep pulls when the previous sweep's selected nodes held at least 1/kPullShare of all out-links
-constexpr long long kPullShare = 4;
-
 __device__ __forceinline__ void red_add_v4(float *p, float4 v) {
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w));
 }

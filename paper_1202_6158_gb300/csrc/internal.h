@@ -91,11 +91,20 @@ struct SolveState {
     int body_runs;         // executions of the finalize kernel (one per loop iteration)
     int exact;             // 1 when the sweep now running sums |F|_1 exactly (every kExactEvery sweeps)
     int weighted;          // ALGO-OP / OP2 selection: the threshold is never raised
-    int pad;
+    int pull;              // this sweep's direction: 0 push from the class lists, 1 pull along the in-links
     double wscale;         // weighted selection: the threshold of F*w is T * wscale
+    long long pull_edges;  // a sweep that diffused at least this many out-links is dense
+    int dense;             // the last sweep was dense: a second dense sweep makes the next one pull
+    int pad2;
 };
 
 // batched personalized queries: up to kLanes queries interleaved in one fluid row
+// captured sweep loops: 7 selection / precision variants, each push-only or with the pull direction
+constexpr int kSweepSlots = 14;
+// a sweep pulls (when allowed) if the previous sweep's selected nodes held at least 1/kPullShare
+// of all out-links
+constexpr long long kPullShare = 4;
+
 constexpr int kLanes = 64;              // queries per batch (the width of a fluid row)
 constexpr int kBatchHot = 32;           // hot targets whose rows the batched push sums in shared memory
 constexpr int kWidths = 5;              // row widths of the batched loops: 4, 8, 16, 32, 64 lanes
@@ -252,8 +261,9 @@ struct di_graph {
 
     // captured solve loops: [0] FP64 sweeps, [1] FP32-mixed sweeps, [2] power iteration,
     // [3 + 2*(select-1) + prec] weighted sweeps (ALGO-OP select 1, ALGO-OP2 select 2)
-    cudaGraph_t graph[7] = {};
-    cudaGraphExec_t exec[7] = {};
+    cudaGraph_t graph[diter::kSweepSlots] = {};
+    cudaGraphExec_t exec[diter::kSweepSlots] = {};
+    void *wpull = nullptr;             // [npad] FP64 or FP32: sent * d/outdeg of the nodes a pull sweep selected, else 0
     float *wsel[2] = {nullptr, nullptr};   // [npad] selection weights of ALGO-OP / ALGO-OP2 (0 on the padding)
     double wscale[2] = {1.0, 1.0};         // 2^floor(log2(mean weight))
 
@@ -321,6 +331,7 @@ template <typename FT> inline Sel<FT> *sel_of(const di_graph *g) { return reinte
 
 // the push of one sweep on stream s (push.cu)
 template <typename FT> void launch_push(di_graph *g, FT *F, cudaStream_t s);
+template <typename FT> void launch_pull(di_graph *g, FT *F, cudaStream_t s);
 
 // push CTAs: the pushes scale with edges, not nodes, so small graphs still get push_per_sm CTAs per SM
 inline int push_grid(const di_graph *g) {

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
     __shared__ FT hot[kHotSlots];
     __shared__ long long s_red[kWarps];
     __shared__ int s_idx;
-    if (st->done) return;
+    if (st->done || st->pull) return;
     for (int t = threadIdx.x; t < kHotSlots; t += kScanThreads) hot[t] = (FT)0;
     __syncthreads();
     const unsigned long long pol = evict_last_policy();
@@ -191,6 +191,101 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
 
 }  // namespace
 
+// The pull direction of a dense sweep: the same diffusion of S read from the target side,
+// F_j += sum over in-links (i -> j) of w_i, where the scan wrote w_i = sent_i * d/outdeg_i for
+// the selected nodes and 0 for the others.  The in-links, in target order, are cut into
+// even ranges per warp.  The out-links pushed are counted by the scan on these sweeps.
+//  * FP32: lane l takes link e0 + l and a segmented warp sum over equal targets (a shuffle
+//    tree) leaves one red.add per target and 32 links.
+//  * FP64: FP64 arithmetic is scarce on this GPU (a shuffle tree made the pull slower than
+//    the push), so each lane takes kPullRun consecutive links and sums them serially per
+//    target, one add per link, then adds each target's sum with one red.add.
+// Either way a target with many in-links gets a reduction per 32 or kPullRun links where
+// the push makes one per link.
+constexpr int kPullRun = 8;
+
+template <typename FT>
+__global__ void __launch_bounds__(kScanThreads, 4) k_sweep_pull(const int *__restrict__ in_src,
+                                                             const int *__restrict__ in_dst,
+                                                             const FT *__restrict__ w, long long nnz,
+                                                             FT *__restrict__ F, const SolveState *__restrict__ st) {
+    if (st->done || !st->pull) return;
+    constexpr bool kTree = sizeof(FT) == 4;
+    constexpr int kU = 4;  // shuffle tree: steps of 32 links loaded before they are summed
+    constexpr int kStepLinks = kTree ? 32 * kU : 32 * kPullRun;
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = (long long)gridDim.x * kWarps, gw = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    // ranges of whole steps, so that every full run starts on a 32-byte boundary
+    const long long per = (nnz + nwarps - 1) / nwarps + kStepLinks - 1;
+    const long long span = per - per % kStepLinks;
+    const long long e_beg = min(nnz, gw * span), e_end = min(nnz, e_beg + span);
+    const unsigned long long pol = evict_last_policy();
+    for (long long e0 = e_beg; e0 < e_end; e0 += kStepLinks) {
+        if constexpr (kTree) {
+            int dst[kU], src[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const long long e = e0 + 32 * u + lane;
+                const bool in = e < e_end;
+                dst[u] = in ? __ldg(in_dst + e) : -1;
+                src[u] = in ? __ldg(in_src + e) : -1;
+            }
+            FT v[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) v[u] = src[u] >= 0 ? __ldg(w + src[u]) : (FT)0;
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                // inclusive sums over the runs of equal targets (targets ascend along the links)
+                FT a = v[u];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const FT y = __shfl_up_sync(kFull, a, o);
+                    const int dy = __shfl_up_sync(kFull, dst[u], o);
+                    if (lane >= o && dy == dst[u]) a += y;
+                }
+                const int dn = __shfl_down_sync(kFull, dst[u], 1);
+                const bool last = dst[u] >= 0 && (lane == 31 || dn != dst[u]);
+                if (last && a != (FT)0) red_add(F + dst[u], a, pol);
+            }
+        } else {
+            const long long eb = e0 + (long long)kPullRun * lane;
+            int src[kPullRun], dst[kPullRun];
+            if (eb + kPullRun <= e_end) {
+                const int4 *ps = reinterpret_cast<const int4 *>(in_src + eb);
+                const int4 *pd = reinterpret_cast<const int4 *>(in_dst + eb);
+#pragma unroll
+                for (int h = 0; h < kPullRun / 4; ++h) {
+                    const int4 a = __ldg(ps + h), b = __ldg(pd + h);
+                    src[4 * h] = a.x; src[4 * h + 1] = a.y; src[4 * h + 2] = a.z; src[4 * h + 3] = a.w;
+                    dst[4 * h] = b.x; dst[4 * h + 1] = b.y; dst[4 * h + 2] = b.z; dst[4 * h + 3] = b.w;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kPullRun; ++k) {
+                    const bool in = eb + k < e_end;
+                    src[k] = in ? __ldg(in_src + eb + k) : -1;
+                    dst[k] = in ? __ldg(in_dst + eb + k) : -1;
+                }
+            }
+            FT v[kPullRun];
+#pragma unroll
+            for (int k = 0; k < kPullRun; ++k) v[k] = src[k] >= 0 ? __ldg(w + src[k]) : (FT)0;
+            int cur = dst[0];
+            FT acc = v[0];
+#pragma unroll
+            for (int k = 1; k < kPullRun; ++k) {
+                if (dst[k] != cur) {
+                    if (cur >= 0 && acc != (FT)0) red_add(F + cur, acc, pol);
+                    cur = dst[k];
+                    acc = (FT)0;
+                }
+                acc += v[k];
+            }
+            if (cur >= 0 && acc != (FT)0) red_add(F + cur, acc, pol);
+        }
+    }
+}
+
 template <typename FT>
 void launch_push(di_graph *g, FT *F, cudaStream_t s) {
     k_sweep_push<FT><<<push_grid(g), kScanThreads, 0, s>>>(rec_of<FT>(g), g->col_idx, F, g->region, g->pre,
@@ -200,5 +295,14 @@ void launch_push(di_graph *g, FT *F, cudaStream_t s) {
 
 template void launch_push<double>(di_graph *, double *, cudaStream_t);
 template void launch_push<float>(di_graph *, float *, cudaStream_t);
+
+template <typename FT>
+void launch_pull(di_graph *g, FT *F, cudaStream_t s) {
+    k_sweep_pull<FT><<<push_grid(g), kScanThreads, 0, s>>>(g->in_src, g->in_dst, static_cast<const FT *>(g->wpull),
+                                                           g->nnz, F, g->st);
+}
+
+template void launch_pull<double>(di_graph *, double *, cudaStream_t);
+template void launch_pull<float>(di_graph *, float *, cudaStream_t);
 
 }  // namespace diter

@@ -37,6 +37,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <limits>
 #include <vector>
 
 #include "device_common.cuh"
@@ -81,7 +82,11 @@ __global__ void k_init_seeds(int nseeds, const int *__restrict__ seeds, const do
 }
 
 __device__ void init_control(SolveState *st, double R0, double tolR, double beta, double one_minus_d, int n,
-                             long long max_edges, int max_sweeps, int trace_on, double wscale, int weighted) {
+                             long long max_edges, int max_sweeps, int trace_on, double wscale, int weighted,
+                             long long pull_edges) {
+    st->pull = 0;  // the first two sweeps push
+    st->dense = 0;
+    st->pull_edges = pull_edges;
     st->wscale = wscale;
     st->weighted = weighted;
     st->R = R0;
@@ -102,19 +107,20 @@ __device__ void init_control(SolveState *st, double R0, double tolR, double beta
 }
 
 __global__ void k_init_control(SolveState *st, double R0, double tolR, double beta, double one_minus_d, int n,
-                               long long max_edges, int max_sweeps, int trace_on, double wscale, int weighted) {
-    init_control(st, R0, tolR, beta, one_minus_d, n, max_edges, max_sweeps, trace_on, wscale, weighted);
+                               long long max_edges, int max_sweeps, int trace_on, double wscale, int weighted,
+                               long long pull_edges) {
+    init_control(st, R0, tolR, beta, one_minus_d, n, max_edges, max_sweeps, trace_on, wscale, weighted, pull_edges);
 }
 
 // the same with R_0 = |F_0|_1 summed (fixed order) from the per-CTA partials of k_l1_partials:
 // a continued or updated state starts from whatever fluid it holds
 __global__ void k_init_control_l1(SolveState *st, const ScanPartial *__restrict__ part, int G, double tolR,
                                   double beta, double one_minus_d, int n, long long max_edges, int max_sweeps,
-                                  int trace_on, double wscale, int weighted) {
+                                  int trace_on, double wscale, int weighted, long long pull_edges) {
     if (threadIdx.x != 0) return;
     double R0 = 0.0;
     for (int c = 0; c < G; ++c) R0 += part[c].l1d;
-    init_control(st, R0, tolR, beta, one_minus_d, n, max_edges, max_sweeps, trace_on, wscale, weighted);
+    init_control(st, R0, tolR, beta, one_minus_d, n, max_edges, max_sweeps, trace_on, wscale, weighted, pull_edges);
 }
 
 // ------------------------------------------------------------------- scan
@@ -204,6 +210,14 @@ struct ScanOps<float> {
 // The ring of one warp: per stage 128 values of F, their 128 class bytes (and 128
 // selection weights); every size is a multiple of 16 bytes and every source offset a
 // multiple of 128 nodes, so every copy is 16-byte aligned.
+// d/outdeg from a row record read as four ints
+template <typename FT>
+__device__ __forceinline__ FT rec_inv(int4 r);
+template <>
+__device__ __forceinline__ double rec_inv<double>(int4 r) { return __hiloint2double(r.w, r.z); }
+template <>
+__device__ __forceinline__ float rec_inv<float>(int4 r) { return __int_as_float(r.z); }
+
 template <typename FT, bool WGT>
 struct ScanRing {
     static constexpr int kF = kStep * (int)sizeof(FT);
@@ -224,7 +238,9 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
                                                              unsigned *__restrict__ ticket, Sel<FT> *__restrict__ sel,
                                                              ScanPartial *__restrict__ part,
                                                              const SolveState *__restrict__ st,
-                                                             double *__restrict__ H) {
+                                                             double *__restrict__ H,
+                                                             const RowRec<FT> *__restrict__ rec, int n,
+                                                             FT *__restrict__ wpull) {
     using Ops = ScanOps<FT>;
     using Ring = ScanRing<FT, WGT>;
     __shared__ __align__(128) unsigned char s_ring[kWarps * Ring::kWarpBytes];
@@ -238,6 +254,8 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
     const float tw = WGT ? (float)(st->T * st->wscale) : 0.f;
     const int S = fixed_scale(st->R);
     const bool exact = (st->sweeps % kExactEvery) == 0;  // the exact |F|_1 of this sweep's start
+    // a pull sweep writes sent * d/outdeg of every node (0 if not selected) instead of the lists
+    const bool pull = st->pull != 0;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const int g = blockIdx.x * kWarps + w;
@@ -247,6 +265,7 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
     for (int L = 0; L < kLists; ++L) start[L] = run[L] = region[L * (W + 1) + g];
     long long l1 = 0, s_out = 0, s_dng = 0;  // fixed point: |F|_1, fluid of selected nodes with / without children
     int srcs = 0, entries = 0;
+    long long pedges = 0;  // out-links of the selected nodes, counted here on pull sweeps
     const int nsteps = wchunk / kStep;
     const unsigned long long pol = evict_first_policy(), pol_h = evict_last_policy();
     // this warp's ring: lane 0 keeps kStages steps in flight
@@ -274,6 +293,13 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
     bool ok = true;
     for (; s < nsteps; ++s) {
         const int slot = s % Ring::kStages;
+        int4 rr[4];  // pull sweeps: the row records of this lane's four nodes, loaded before the wait
+        if (pull) {
+            const long long i0 = wbeg + (long long)s * kStep + 4 * lane;
+            const int4 *rp = reinterpret_cast<const int4 *>(rec + i0);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) rr[k] = i0 + k < n ? __ldg(rp + k) : make_int4(0, 0, 0, 0);  // padding: none
+        }
         ok = __all_sync(kFull, mbar_wait(bar0 + 8u * slot, (unsigned)((s / Ring::kStages) & 1), kScanWaitLimit));
         if (!ok) break;
         const unsigned char *stg = ring + slot * Ring::kBytes;
@@ -291,6 +317,16 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
             const bool pick = WGT ? fabsf((float)cur[k]) * wk[k] > tw : Ops::above(cur[k], key);
             pm |= pick ? 1u << k : 0u;
             if (exact) l1 += to_fixed(cur[k], S);
+        }
+        if (pull) {
+            FT wv[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const bool pk = (pm >> k & 1u) != 0;
+                wv[k] = pk ? cur[k] * rec_inv<FT>(rr[k]) : (FT)0;
+                pedges += pk ? rr[k].y : 0;
+            }
+            Ops::store4(wpull + wbeg + (long long)s * kStep + 4 * lane, wv);
         }
         // 2. the selected nodes of the step, in ascending position, into the warp's queue
         const int np = __popc(pm);
@@ -337,7 +373,7 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
                 }
                 // nodes with children go to their class's list, in ascending id
 #pragma unroll
-                for (int L = 1; L < kLists; ++L) {
+                for (int L = 1; L < kLists && !pull; ++L) {
                     const bool mine = has && c == L;
                     const unsigned bits = __ballot_sync(kFull, mine);
                     if (mine) {
@@ -376,12 +412,13 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
     const long long bdng = block_sum(s_dng, s_red);
     const long long bsr = block_sum((long long)srcs, s_red);
     const long long ben = block_sum((long long)entries, s_red);
+    const long long bpe = pull ? block_sum(pedges, s_red) : 0;
     if (threadIdx.x == 0) {
         ScanPartial p;
         p.l1 = bl1;
         p.out = bout;
         p.dng = bdng;
-        p.edges = 0;
+        p.edges = bpe;  // push sweeps: added by the push kernel
         p.srcs = bsr;
         p.entries = ben;
         p.l1d = 0.0;
@@ -445,9 +482,15 @@ __global__ void k_sweep_finalize(int n, int G, const ScanPartial *__restrict__ p
     // removed mass: (1-d)*sent for nodes with children, sent for dangling nodes (Section 3.3)
     const double rem = st->one_minus_d * ldexp((double)fout, -S) + ldexp((double)fdng, -S);
     const double R = l1 - rem;  // |F|_1 after the sweep (exact arithmetic)
+    const int pulled = st->pull;
     st->sweeps += 1;
     st->edges += ed;
     st->srcs += sr;
+    // the next sweep pulls after two dense sweeps in a row: one dense sweep (the first sweep from
+    // a uniform F_0 selects every node) is often followed by sparse ones
+    const int dense = ed >= st->pull_edges ? 1 : 0;
+    st->pull = dense && st->dense ? 1 : 0;
+    st->dense = dense;
     if (st->trace_on && st->sweeps <= kTraceCap) {
         di_sweep_record r;
         r.l1_F = l1;
@@ -459,6 +502,8 @@ __global__ void k_sweep_finalize(int n, int G, const ScanPartial *__restrict__ p
         r.pushed = en;
         r.scan_ms = 0.0;
         r.push_ms = 0.0;
+        r.pull = pulled;
+        r.pad = 0;
         trace[st->sweeps - 1] = r;
     }
     st->R = R;
@@ -542,11 +587,11 @@ void launch_scan(di_graph *g, FT *F, const float *wsel, cudaStream_t s) {
     if (wsel)
         k_sweep_scan<FT, true><<<g->G, kScanThreads, 0, s>>>(g->chunk / kWarps, F, wsel, g->cls, g->region, g->W,
                                                              g->fcount, g->pre, g->ticket, sel_of<FT>(g), g->part,
-                                                             g->st, g->H);
+                                                             g->st, g->H, rec_of<FT>(g), g->n, static_cast<FT *>(g->wpull));
     else
         k_sweep_scan<FT, false><<<g->G, kScanThreads, 0, s>>>(g->chunk / kWarps, F, nullptr, g->cls, g->region, g->W,
                                                               g->fcount, g->pre, g->ticket, sel_of<FT>(g), g->part,
-                                                              g->st, g->H);
+                                                              g->st, g->H, rec_of<FT>(g), g->n, static_cast<FT *>(g->wpull));
 }
 
 
@@ -595,6 +640,7 @@ di_status build_sweep_graph(di_graph *g, int slot, FT *F, const float *wsel) {
     if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(e, "cudaStreamBeginCaptureToGraph"); }
     launch_scan<FT>(g, F, wsel, g->cap);
     launch_push<FT>(g, F, g->cap);
+    if (slot >= kSweepSlots / 2) launch_pull<FT>(g, F, g->cap);  // returns at once on push sweeps
     k_sweep_finalize<<<1, 256, 0, g->cap>>>(g->n, g->G, g->part, g->st, g->trace, handle, 1);
     cudaGraph_t captured = nullptr;
     e = cudaStreamEndCapture(g->cap, &captured);
@@ -634,13 +680,16 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, InitK
     }
     const double beta = o.beta > 0 ? o.beta : 0.5;
     const int max_sweeps = o.max_sweeps > 0 ? o.max_sweeps : 1000000;
+    // a sweep pulls when the previous one diffused a kPullShare-th of all out-links
+    const long long pull_edges =
+        o.direction ? std::max(1LL, (g->nnz + kPullShare - 1) / kPullShare) : std::numeric_limits<long long>::max();
     if (init == kInitState) {
         k_l1_partials<FT><<<g->G, kScanThreads, 0, s>>>(n, g->chunk, F, g->part);
         k_init_control_l1<<<1, 32, 0, s>>>(g->st, g->part, g->G, o.tol * omd, beta, omd, n, o.max_edge_pushes,
-                                           max_sweeps, o.trace ? 1 : 0, wscale, o.select ? 1 : 0);
+                                           max_sweeps, o.trace ? 1 : 0, wscale, o.select ? 1 : 0, pull_edges);
     } else {
         k_init_control<<<1, 1, 0, s>>>(g->st, omd, o.tol * omd, beta, omd, n, o.max_edge_pushes, max_sweeps,
-                                       o.trace ? 1 : 0, wscale, o.select ? 1 : 0);
+                                       o.trace ? 1 : 0, wscale, o.select ? 1 : 0, pull_edges);
     }
     DI_CUDA(cudaGetLastError());
     int attempts = 0;
@@ -655,6 +704,7 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, InitK
                 launch_scan<FT>(g, F, wsel, s);
                 DI_CUDA(cudaEventRecord(g->pev[1], s));
                 launch_push<FT>(g, F, s);
+                if (o.direction) launch_pull<FT>(g, F, s);
                 DI_CUDA(cudaEventRecord(g->pev[2], s));
                 k_sweep_finalize<<<1, 256, 0, s>>>(n, g->G, g->part, g->st, g->trace, none, 0);
                 DI_CUDA(cudaEventRecord(g->pev[3], s));
@@ -783,6 +833,15 @@ __global__ void k_sel_weights(int n, int npad, int select, const int *__restrict
     if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
 
+// the pull direction's inputs: the in-links with their targets, and the per-node pushed values
+static di_status ensure_pull(di_graph *g) {
+    if (g->wpull) return DI_OK;
+    di_status r = build_in_dst(g);
+    if (r != DI_OK) return r;
+    DI_CUDA(cudaMallocAsync(&g->wpull, sizeof(double) * (size_t)g->G * g->chunk, g->stream));
+    return DI_OK;
+}
+
 di_status ensure_weights(di_graph *g, int select) {
     if (select == 0 || g->wsel[select - 1]) return DI_OK;
     di_status tr = build_transpose(g);  // #in_i
@@ -879,8 +938,12 @@ di_status run_solve(di_graph *g, const di_solve_opts &o, const int *seeds, const
     if (r != DI_OK) return r;
     g->last_prec = o.prec;
     g->last_trace_on = o.trace ? 1 : 0;
+    if (o.direction) {
+        r = ensure_pull(g);
+        if (r != DI_OK) return r;
+    }
     const InitKind init = seeds ? kInitSeeds : kInitV;
-    const int slot = o.select ? 3 + 2 * (o.select - 1) + o.prec : o.prec;
+    const int slot = (o.select ? 3 + 2 * (o.select - 1) + o.prec : o.prec) + (o.direction ? kSweepSlots / 2 : 0);
     if (o.prec == DI_FP64)
         return solve_impl<double>(g, o, g->F64, slot, init, seeds, seed_w, nseeds, wsum, H_out, out_dev, st);
     return solve_impl<float>(g, o, g->F32, slot, init, seeds, seed_w, nseeds, wsum, H_out, out_dev, st);
@@ -891,8 +954,12 @@ di_status run_update(di_graph *go, di_graph *gn, const di_solve_opts &o, double 
     if (r != DI_OK) return r;
     r = ensure_weights(gn, o.select);
     if (r != DI_OK) return r;
+    if (o.direction) {
+        r = ensure_pull(gn);
+        if (r != DI_OK) return r;
+    }
     const int n = gn->n;
-    const int slot = o.select ? 3 + 2 * (o.select - 1) : 0;
+    const int slot = (o.select ? 3 + 2 * (o.select - 1) : 0) + (o.direction ? kSweepSlots / 2 : 0);
     if (!gn->exec[slot]) {  // capture before timing starts, as a solve does
         r = build_sweep_graph<double>(gn, slot, gn->F64, o.select ? gn->wsel[o.select - 1] : nullptr);
         if (r != DI_OK) return r;

@@ -16,7 +16,7 @@ namespace {
 
 // launch dimensions are part of the captured loops: drop them when the push grid changes
 void drop_sweep_graphs(di_graph *g) {
-    for (int k = 0; k < 7; ++k) {
+    for (int k = 0; k < kSweepSlots; ++k) {
         if (k == 2) continue;  // the power iteration does not use the push
         if (g->exec[k]) cudaGraphExecDestroy(g->exec[k]);
         if (g->graph[k]) cudaGraphDestroy(g->graph[k]);

@@ -118,13 +118,15 @@ def _solve(di, n, rp, ci, tol, V=None, **kw):
     return H, F, st, tr
 
 
+@pytest.mark.parametrize("direction", [0, 1])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_fp64_tight_parity_with_oracle_sweeps(di, name):
-    """Both to bound <= 1e-13: |H_gpu - H_oracle|_1 <= 1e-12, same sweeps and elementary steps."""
+def test_fp64_tight_parity_with_oracle_sweeps(di, name, direction):
+    """Both to bound <= 1e-13: |H_gpu - H_oracle|_1 <= 1e-12, same sweeps and elementary steps.
+    direction=1 pulls along the in-links on dense sweeps: the same diffusion of the same sets."""
     n, rp, ci = CASES[name]
     V = gg.uniform_v(n)
     tol = 1e-13
-    H, F, st, _ = _solve(di, n, rp, ci, tol)
+    H, F, st, _ = _solve(di, n, rp, ci, tol, direction=direction)
     r = oracle.diter(n, rp, ci, D, V, tol, mode="sweep", beta=BETA)
     assert st["converged"] == 1 and st["bound"] <= tol
     assert abs(st["l1_F"] - np.abs(F).sum()) <= 1e-15 + 1e-12 * st["l1_F"]
@@ -171,8 +173,9 @@ def test_ragged_sizes(di, n):
     assert st["sweeps"] == r.sweeps
 
 
-def test_theorem1_on_device_state(di):
-    """After k sweeps the device state satisfies H + F = F_0 + dPH (Theorem 1)."""
+@pytest.mark.parametrize("direction", [0, 1])
+def test_theorem1_on_device_state(di, direction):
+    """After k sweeps the device state satisfies H + F = F_0 + dPH (Theorem 1), for both directions."""
     import scipy.sparse as sp
     n, rp, ci = CASES["zipf_2e14_hubs"]
     deg = np.diff(rp)
@@ -180,7 +183,7 @@ def test_theorem1_on_device_state(di):
     P = sp.csr_matrix((1.0 / deg[src], (ci, src)), shape=(n, n))
     F0 = (1 - D) * gg.uniform_v(n)
     for k in [1, 2, 5, 20]:
-        H, F, st, _ = _solve(di, n, rp, ci, 1e-14, max_sweeps=k, allow_unconverged=True)
+        H, F, st, _ = _solve(di, n, rp, ci, 1e-14, max_sweeps=k, allow_unconverged=True, direction=direction)
         assert st["sweeps"] == k
         resid = H + F - F0 - D * (P @ H)
         assert np.abs(resid).max() <= 1e-15
@@ -189,21 +192,31 @@ def test_theorem1_on_device_state(di):
         assert np.abs(F - r.F).sum() <= 1e-13
 
 
-def test_trace_records(di):
+@pytest.mark.parametrize("direction", [0, 1])
+def test_trace_records(di, direction):
     n, rp, ci = CASES["rmat_12"]
-    H, F, st, tr = _solve(di, n, rp, ci, 1e-10, trace=1)
+    H, F, st, tr = _solve(di, n, rp, ci, 1e-10, trace=1, direction=direction)
     assert len(tr) == st["sweeps"]
+    # the first two sweeps push; with direction=1 a sweep pulls exactly when the two before it
+    # each diffused at least a quarter of the out-links (dense sweeps, as on this R-MAT graph)
+    nnz = len(ci)
+    dense = [4 * t["edges"] >= nnz for t in tr]
+    assert tr[0]["pull"] == 0 and tr[1]["pull"] == 0
+    for k in range(2, len(tr)):
+        assert tr[k]["pull"] == (1 if direction and dense[k - 1] and dense[k - 2] else 0)
+    assert (sum(t["pull"] for t in tr) > 0) == bool(direction)
     assert sum(t["edges"] for t in tr) == st["edges_pushed"]
     assert all(tr[k + 1]["l1_F"] <= tr[k]["l1_F"] * (1 + 1e-12) for k in range(len(tr) - 1))
     assert tr[-1]["R"] <= 1e-10 * (1 - D)
 
 
-def test_fp32_mixed_precision(di):
+@pytest.mark.parametrize("direction", [0, 1])
+def test_fp32_mixed_precision(di, direction):
     """FP32 fluid and pushes, FP64 H and residual: |H - H_oracle|_1 <= 2e-6."""
     for name in ["uniform_1e4", "zipf_2e14_hubs", "rmat_12"]:
         n, rp, ci = CASES[name]
         V = gg.uniform_v(n)
-        H, F, st, _ = _solve(di, n, rp, ci, 1e-7, prec=di.DI_FP32_MIXED)
+        H, F, st, _ = _solve(di, n, rp, ci, 1e-7, prec=di.DI_FP32_MIXED, direction=direction)
         r = oracle.diter(n, rp, ci, D, V, 1e-12, mode="sweep", beta=BETA)
         assert np.abs(H - r.H).sum() <= 2e-6, name
         assert st["bound"] <= 1e-7 * (1 + 1e-6)
