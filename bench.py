@@ -48,6 +48,9 @@ WORKLOADS = {
                    label="Zipf N=2^20 (reduced size for quick runs), d=0.85, V=1/N, FP64, L1 bound 1e-8"),
     "uniform1e4": dict(kind="uniform", n=10000, dmax=20, d=0.85, tol=1e-10 / 0.15,
                        label="uniform outdeg U{0..20}, N=10^4, d=0.85, V=1/N, FP64, |F|_1 < 1e-10"),
+    "rmat22": dict(kind="rmat", scale=22, d=0.85, tol=1e-8,
+                   label="R-MAT scale 22, edge factor 16, (a,b,c)=(.57,.19,.19), duplicates removed, d=0.85, V=1/N, "
+                         "FP64, L1 bound 1e-8 (profiling case for dense sweeps)"),
 }
 
 
@@ -60,6 +63,8 @@ def make_graph(w, seed=1):
     if w["kind"] == "zipf":
         return gg.zipf_graph(w["n"], alpha=w["alpha"], kmax=w["kmax"], dangling_frac=w["dangling"],
                              target_exp=w["target_exp"], seed=seed)
+    if w["kind"] == "rmat":
+        return gg.rmat_graph(w["scale"], 16, seed=seed)
     return gg.uniform_graph(w["n"], w["dmax"], seed=seed)
 
 
@@ -274,18 +279,22 @@ def bench_mixed(di, torch, scale=23, ds=(0.85, 0.99), tol=1e-7, ref_tol=1e-10):
         G = di.DiGraph(g.n, g.row_ptr, g.col_idx, d)
         Href = torch.empty(g.n, dtype=torch.float64, device=dev)
         H = torch.empty(g.n, dtype=torch.float64, device=dev)
-        G.solve(tol, H_out=H)                       # warm-up: graph capture, buffers
-        G.solve(tol, H_out=H, prec=di.DI_FP32_MIXED)
+        for direction in (0, 1):                    # warm-up: graph capture, buffers, in-link CSR
+            G.solve(tol, H_out=H, direction=direction)
+            G.solve(tol, H_out=H, prec=di.DI_FP32_MIXED, direction=direction)
         _, sref = G.solve(ref_tol, H_out=Href)
         run = {"d": d}
-        for name, prec in (("fp64", di.DI_FP64), ("fp32_mixed", di.DI_FP32_MIXED)):
-            _, st = G.solve(tol, H_out=H, prec=prec)
-            torch.cuda.synchronize()
-            err = float((H - Href).abs().sum().item()) + ref_tol
-            run[name] = {"ms": 1e3 * st["seconds"], "edge_pushes_per_s": st["edges_pushed"] / st["seconds"],
-                         "sweeps": st["sweeps"], "edges": st["edges_pushed"], "bound": st["bound"],
-                         "l1_error_vs_reference": err}
+        # push only, and with the pull direction on dense sweeps (di_solve_opts.direction = 1)
+        for suffix, direction in (("", 0), ("_pull", 1)):
+            for name, prec in (("fp64", di.DI_FP64), ("fp32_mixed", di.DI_FP32_MIXED)):
+                _, st = G.solve(tol, H_out=H, prec=prec, direction=direction)
+                torch.cuda.synchronize()
+                err = float((H - Href).abs().sum().item()) + ref_tol
+                run[name + suffix] = {"ms": 1e3 * st["seconds"], "edge_pushes_per_s": st["edges_pushed"] / st["seconds"],
+                                      "sweeps": st["sweeps"], "edges": st["edges_pushed"], "bound": st["bound"],
+                                      "l1_error_vs_reference": err}
         run["fp32_speedup"] = run["fp64"]["ms"] / run["fp32_mixed"]["ms"]
+        run["fp32_speedup_pull"] = run["fp64_pull"]["ms"] / run["fp32_mixed_pull"]["ms"]
         out["runs"].append(run)
         log(f"mixed precision d={d}: {run}")
         G.close()
@@ -421,6 +430,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="zipf24", choices=sorted(WORKLOADS))
     ap.add_argument("--beta", type=float, default=0.5)
+    ap.add_argument("--direction", type=int, default=0, choices=[0, 1],
+                    help="1: dense sweeps pull along the in-links (di_solve_opts.direction)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-pushes", type=int, default=0, help="diffusions in the oracle sample (0: 8N, more than the full solve needs)")
     ap.add_argument("--no-cpu", action="store_true")
@@ -471,7 +482,7 @@ def main():
 
     # ---- warm-up, then K timed solves on device-resident inputs
     for _ in range(args.warmup):
-        G.solve(tol, H_out=H, beta=args.beta)
+        G.solve(tol, H_out=H, beta=args.beta, direction=args.direction)
     torch.cuda.synchronize()
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -482,7 +493,7 @@ def main():
         torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(args.steps):
-            _, st = G.solve(tol, H_out=H, beta=args.beta)
+            _, st = G.solve(tol, H_out=H, beta=args.beta, direction=args.direction)
             edges += st["edges_pushed"]
             launches += st["kernel_launches"]
             sweeps.append(st["sweeps"])
@@ -512,7 +523,7 @@ def main():
     pull_bytes_iter = g.nnz * (4 + 8) + g.n * (4 + 4 + 3 * 8 + 8)   # in_src + gather, per row: id, in_ptr, x rw, z, 1/deg
 
     # ---- profiled solve: per-kernel CUDA-event times and algorithmic bytes from the trace
-    G.solve(tol, H_out=H, beta=args.beta, profile=1, trace=1)
+    G.solve(tol, H_out=H, beta=args.beta, profile=1, trace=1, direction=args.direction)
     prof = G.profile()
     trace = G.trace()
     s_f = 8
@@ -548,7 +559,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         with di.DiGraph(g.n, rp_h, ci_h, w["d"]) as Ge:
-            _, est = Ge.solve(tol, H_out=H_h, beta=args.beta)
+            _, est = Ge.solve(tol, H_out=H_h, beta=args.beta, direction=args.direction)
             e2e_edges += est["edges_pushed"]
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
@@ -599,6 +610,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w["label"], "n": g.n, "nnz": g.nnz, "d": w["d"], "tol": tol, "beta": args.beta,
+                       "direction": "push, pull on dense sweeps" if args.direction else "push",
                        "parallelism": "replicas" if world > 1 else "single-gpu",
                        "l2": "inputs larger than L2 (CSR + F + H of the solve exceed 129 MB)"},
             "time_to_residual_ms": {"diter": max_ms / args.steps, "power": pms,

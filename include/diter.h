@@ -207,9 +207,10 @@ di_status di_solve_ex(di_graph *g, const di_solve_opts *opts, double *H_out, di_
  *                     the paper only says the threshold is lowered progressively)
  *   select            DI_SELECT_REF, _OP, _OP2 (Section 4.3)
  *   push_ctas_per_sm  2, 4, 8 (the push grid; never below the scan grid)
+ *   direction         0, 1 (push only, or pull on dense sweeps)
  * Every candidate's result is a valid solve (any choice converges, Section 2.2);
- * only the time differs.  The winning push_ctas_per_sm stays set on g; beta and
- * select are returned for the caller to pass in di_solve_opts.
+ * only the time differs.  The winning push_ctas_per_sm stays set on g; beta,
+ * select and direction are returned for the caller to pass in di_solve_opts.
  *   best    receives the fastest candidate
  *   tried   host di_tune_result[cap] (may be NULL): every candidate in the order tried;
  *           *ntried receives their number
@@ -223,7 +224,7 @@ typedef struct {
     double ms;               /* device time of the candidate's solve */
     int64_t edges_pushed;
     int32_t sweeps;
-    int32_t pad;
+    int32_t direction;       /* di_solve_opts.direction of the candidate */
 } di_tune_result;
 
 di_status di_autotune(di_graph *g, const di_solve_opts *base, di_tune_result *best, di_tune_result *tried,

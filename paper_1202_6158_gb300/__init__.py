@@ -77,10 +77,10 @@ def di_solve_ex(handle, H_out, tol, beta=0.5, max_edge_pushes=0, max_sweeps=0, p
 
 
 def di_autotune(handle, tol, prec=DI_FP64, max_sweeps=0, max_edge_pushes=0):
-    """Time one solve per (beta, select, push CTAs per SM) candidate; returns (best, tried)."""
+    """Time one solve per (beta, select, direction, push CTAs per SM) candidate; returns (best, tried)."""
     o = _opts(tol, 0.5, max_edge_pushes, max_sweeps, prec, 0, 0, 0, 0)
     best = di_tune_result()
-    cap = 64
+    cap = 128
     tried = (di_tune_result * cap)()
     n = ctypes.c_int32(0)
     check(load().di_autotune(handle, ctypes.byref(o), ctypes.byref(best), tried, cap, ctypes.byref(n)))

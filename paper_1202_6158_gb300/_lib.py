@@ -70,7 +70,7 @@ class di_completion(ctypes.Structure):
 class di_tune_result(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_double), ("select", ctypes.c_int32), ("push_ctas_per_sm", ctypes.c_int32),
                 ("ms", ctypes.c_double), ("edges_pushed", ctypes.c_int64), ("sweeps", ctypes.c_int32),
-                ("pad", ctypes.c_int32)]
+                ("direction", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}

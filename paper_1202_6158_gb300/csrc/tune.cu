@@ -1,5 +1,5 @@
 // tune.cu -- the autotuner: a timed solve per candidate (threshold schedule beta,
-// node choice, push grid), the fastest kept.
+// node choice, push grid, direction), the fastest kept.
 //
 // Every candidate is a complete solve to the caller's target, so every result is
 // valid (any sequence of diffusions converges to the same X, Section 2.2); the
@@ -49,6 +49,7 @@ extern "C" di_status di_autotune(di_graph *g, const di_solve_opts *base, di_tune
     const double betas[] = {0.125, 0.25, 0.5, 1.0, 2.0};
     const int grids[] = {2, 4, 8};
     const int selects[] = {DI_SELECT_REF, DI_SELECT_OP, DI_SELECT_OP2};
+    const int directions[] = {0, 1};
     const int saved = g->push_per_sm;
     di_tune_result top = {};
     top.ms = -1.0;
@@ -60,10 +61,12 @@ extern "C" di_status di_autotune(di_graph *g, const di_solve_opts *base, di_tune
             g->push_per_sm = pg;
         }
         for (int sel : selects) {
+            for (int dir : directions) {
             for (double b : betas) {
                 di_solve_opts o = *base;
                 o.beta = b;
                 o.select = sel;
+                o.direction = dir;
                 o.trace = 0;
                 o.profile = 0;
                 o.normalize = 0;
@@ -84,9 +87,11 @@ extern "C" di_status di_autotune(di_graph *g, const di_solve_opts *base, di_tune
                 t.ms = r == DI_OK ? st.seconds * 1e3 : -1.0;  // a candidate stopped by a limit never wins
                 t.edges_pushed = st.edges_pushed;
                 t.sweeps = st.sweeps;
+                t.direction = dir;
                 if (count < cap) tried[count] = t;
                 ++count;
                 if (t.ms >= 0.0 && (top.ms < 0.0 || t.ms < top.ms)) top = t;
+            }
             }
         }
     }

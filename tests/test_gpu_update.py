@@ -198,11 +198,12 @@ def test_autotune_picks_a_valid_fastest_candidate(di):
     V = gg.uniform_v(n)
     with di.DiGraph(n, rp, ci, D) as G:
         best, tried = G.autotune(1e-10)
-        assert len(tried) == 45
+        assert len(tried) == 90
         assert best["ms"] == min(t["ms"] for t in tried if t["ms"] >= 0)
         assert {t["select"] for t in tried} == {0, 1, 2}
         assert {t["push_ctas_per_sm"] for t in tried} == {2, 4, 8}
+        assert {t["direction"] for t in tried} == {0, 1}
         # the tuned settings give a correct solve
-        H, st = G.solve(1e-12, beta=best["beta"], select=best["select"])
+        H, st = G.solve(1e-12, beta=best["beta"], select=best["select"], direction=best["direction"])
     r = oracle.diter(n, rp, ci, D, V, 1e-13, mode="sweep")
     assert np.abs(H - r.H).sum() <= st["bound"] + 1e-12
