@@ -29,9 +29,9 @@ namespace diter {
 constexpr int kScanThreads = 256;       // threads of the sweep scan / push CTAs
 constexpr int kScanVec = 2;             // fluid elements per thread per tile (16 B of FP64)
 constexpr int kScanTile = kScanThreads * kScanVec;
-constexpr int kChunkAlign = 1024;       // scan chunks are multiples of 8 warp steps
 constexpr int kWarps = kScanThreads / 32;  // warps per scan / push CTA; each owns a sub-chunk
-constexpr int kStep = 128;              // nodes a warp reads per step (4 per lane)
+constexpr int kStep = 256;              // nodes a warp reads per step (8 per lane)
+constexpr int kChunkAlign = kWarps * kStep;  // scan chunks are multiples of 8 warp steps
 constexpr int kLists = 4;               // selected nodes: 0 dangling, 1 thread, 2 warp, 3 CTA per source
 constexpr int kMaxScanBlocks = 152 * 8; // 8 CTAs per SM on 152 SMs
 constexpr int kOutCut1 = 8;             // out-degree <= cut1: one thread per source

@@ -199,17 +199,20 @@ struct ScanOps<float> {
 
 // The sweep scan streams F and the one-byte out-degree class of every node: each
 // warp owns a sub-chunk of chunk/8 nodes and streams it through shared memory with
-// bulk copies (TMA, 1-D), 128 nodes per step and kStages steps in flight, so the
-// loads never stall on a dependency; lane i takes nodes 4i..4i+3 of a step.  The
+// bulk copies (TMA, 1-D), kStep = 256 nodes per step and kStages steps in flight, so
+// the loads never stall on a dependency; lane i takes nodes 8i..8i+7 of a step (the
+// step's fixed costs -- prefix sum, barrier wait, refill -- are spread over 8 nodes
+// per lane).  The
 // selected nodes (id, sent) of each class are appended to that class's list in
 // ascending id order with a warp prefix sum; the lists' per-sub-chunk capacities are
 // fixed at create time, so no atomics are needed.
 // WGT: ALGO-OP / ALGO-OP2 selection (Section 4.3) as a weighted threshold: node i
 // is selected when (float)|F_i| * w_i > (float)(T * wscale), the product in FP32.
 //
-// The ring of one warp: per stage 128 values of F, their 128 class bytes (and 128
+// The ring of one warp: per stage 256 values of F, their 256 class bytes (and 256
 // selection weights); every size is a multiple of 16 bytes and every source offset a
-// multiple of 128 nodes, so every copy is 16-byte aligned.
+// multiple of 256 nodes, so every copy is 16-byte aligned.
+
 // d/outdeg from a row record read as four ints
 template <typename FT>
 __device__ __forceinline__ FT rec_inv(int4 r);
@@ -218,13 +221,16 @@ __device__ __forceinline__ double rec_inv<double>(int4 r) { return __hiloint2dou
 template <>
 __device__ __forceinline__ float rec_inv<float>(int4 r) { return __int_as_float(r.z); }
 
+constexpr int kPer = kStep / 32;  // nodes per lane and step
+static_assert(kPer % 4 == 0 && kStep <= 256, "groups of four nodes per lane; step positions fit a byte");
+
 template <typename FT, bool WGT>
 struct ScanRing {
     static constexpr int kF = kStep * (int)sizeof(FT);
     static constexpr int kC = kStep;
     static constexpr int kW = WGT ? kStep * 4 : 0;
     static constexpr int kBytes = kF + kC + kW;
-    static constexpr int kStages = WGT ? 3 : 4;
+    static constexpr int kStages = WGT ? 2 : 3;
     static constexpr int kWarpBytes = kBytes * kStages;
 };
 constexpr int kScanWaitLimit = 1 << 20;  // polls of a stage's mbarrier before the scan gives up
@@ -293,40 +299,41 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
     bool ok = true;
     for (; s < nsteps; ++s) {
         const int slot = s % Ring::kStages;
-        int4 rr[4];  // pull sweeps: the row records of this lane's four nodes, loaded before the wait
-        if (pull) {
-            const long long i0 = wbeg + (long long)s * kStep + 4 * lane;
-            const int4 *rp = reinterpret_cast<const int4 *>(rec + i0);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) rr[k] = i0 + k < n ? __ldg(rp + k) : make_int4(0, 0, 0, 0);  // padding: none
-        }
         ok = __all_sync(kFull, mbar_wait(bar0 + 8u * slot, (unsigned)((s / Ring::kStages) & 1), kScanWaitLimit));
         if (!ok) break;
         const unsigned char *stg = ring + slot * Ring::kBytes;
         const FT *stg_f = reinterpret_cast<const FT *>(stg);
         const long long step0 = wbeg + (long long)s * kStep;
-        FT cur[4];
-        Ops::load4_shared(stg + 4 * (int)sizeof(FT) * lane, cur);
-        float4 wcur = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (WGT) wcur = *reinterpret_cast<const float4 *>(stg + Ring::kF + Ring::kC + 16 * lane);
-        const float wk[4] = {wcur.x, wcur.y, wcur.z, wcur.w};
-        // 1. which of this lane's four nodes are selected; the exact |F|_1 every kExactEvery sweeps
+        // 1. which of this lane's kPer nodes (kPer/4 groups of four) are selected; the exact |F|_1
+        //    every kExactEvery sweeps; on pull sweeps sent * d/outdeg of each of them
         unsigned pm = 0;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const bool pick = WGT ? fabsf((float)cur[k]) * wk[k] > tw : Ops::above(cur[k], key);
-            pm |= pick ? 1u << k : 0u;
-            if (exact) l1 += to_fixed(cur[k], S);
-        }
-        if (pull) {
-            FT wv[4];
+        for (int h = 0; h < kPer / 4; ++h) {
+            const int j0 = kPer * lane + 4 * h;  // position in the step of the group's first node
+            FT cur[4];
+            Ops::load4_shared(stg + (int)sizeof(FT) * j0, cur);
+            float4 wcur = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (WGT) wcur = *reinterpret_cast<const float4 *>(stg + Ring::kF + Ring::kC + 4 * j0);
+            const float wk[4] = {wcur.x, wcur.y, wcur.z, wcur.w};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const bool pk = (pm >> k & 1u) != 0;
-                wv[k] = pk ? cur[k] * rec_inv<FT>(rr[k]) : (FT)0;
-                pedges += pk ? rr[k].y : 0;
+                const bool pick = WGT ? fabsf((float)cur[k]) * wk[k] > tw : Ops::above(cur[k], key);
+                pm |= pick ? 1u << (4 * h + k) : 0u;
+                if (exact) l1 += to_fixed(cur[k], S);
             }
-            Ops::store4(wpull + wbeg + (long long)s * kStep + 4 * lane, wv);
+            if (pull) {
+                const long long i0 = step0 + j0;
+                const int4 *rp = reinterpret_cast<const int4 *>(rec + i0);
+                FT wv[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const bool pk = (pm >> (4 * h + k) & 1u) != 0;
+                    const int4 rr = pk && i0 + k < n ? __ldg(rp + k) : make_int4(0, 0, 0, 0);
+                    wv[k] = pk ? cur[k] * rec_inv<FT>(rr) : (FT)0;
+                    pedges += rr.y;
+                }
+                Ops::store4(wpull + i0, wv);
+            }
         }
         // 2. the selected nodes of the step, in ascending position, into the warp's queue
         const int np = __popc(pm);
@@ -340,16 +347,22 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
         if (total) {
             if (pm) {
                 int at = incl - np;
-                FT z[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    z[k] = cur[k];
-                    if (pm >> k & 1u) {
-                        q[at++] = (unsigned char)(4 * lane + k);
-                        z[k] = (FT)0;           // J_i F leaves F ...
+                for (int h = 0; h < kPer / 4; ++h) {
+                    const unsigned gm = (pm >> (4 * h)) & 0xfu;
+                    if (!gm) continue;
+                    const int j0 = kPer * lane + 4 * h;
+                    FT z[4];
+                    Ops::load4_shared(stg + (int)sizeof(FT) * j0, z);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (gm >> k & 1u) {
+                            q[at++] = (unsigned char)(j0 + k);
+                            z[k] = (FT)0;           // J_i F leaves F ...
+                        }
                     }
+                    Ops::store4(F + step0 + j0, z);
                 }
-                Ops::store4(F + step0 + 4 * lane, z);
             }
             __syncwarp();
             // 3. a lane per selected node: history, removed mass, list position
