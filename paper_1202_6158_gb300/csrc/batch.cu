@@ -41,6 +41,8 @@
 namespace diter {
 namespace {
 
+constexpr int kBScanDepth = 4;  // steps of fluid rows each warp of the batched scan keeps in flight
+
 __device__ __forceinline__ void red_add_v4(float *p, float4 v) {
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w));
 }
@@ -135,50 +137,65 @@ __global__ void __launch_bounds__(kScanThreads) k_bscan(int wchunk, int S, float
     int nsel = 0;
     const bool pull = ctl->pull != 0;  // the push kernel reads the lists, the pull kernel the positions
     const int nsteps = wchunk / NPS;
-    float4 cur = *reinterpret_cast<const float4 *>(Fb + (wbeg + h) * S + 4 * lq);
-    int ccur = cls[wbeg + h];
-    for (int s = 0; s < nsteps; ++s) {
-        const long long node = wbeg + (long long)NPS * s + h;
-        float4 nxt = make_float4(0.f, 0.f, 0.f, 0.f);
-        int cnxt = 0;
-        if (s + 1 < nsteps) {
-            nxt = *reinterpret_cast<const float4 *>(Fb + (node + NPS) * S + 4 * lq);
-            cnxt = cls[node + NPS];
-        }
-        const float v[4] = {cur.x, cur.y, cur.z, cur.w};
-        bool above = false;
+    // kBScanDepth steps of rows in flight per warp (a register ring, unrolled so it stays in registers)
+    float4 buf[kBScanDepth];
+    int cb[kBScanDepth];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            l1[k] += v[k];
-            const bool a = v[k] > T4[k];
-            above |= a;
-            sel4[k] += a ? 1 : 0;
+    for (int d = 0; d < kBScanDepth; ++d) {
+        buf[d] = make_float4(0.f, 0.f, 0.f, 0.f);
+        cb[d] = 0;
+        if (d < nsteps) {
+            buf[d] = *reinterpret_cast<const float4 *>(Fb + (wbeg + (long long)NPS * d + h) * S + 4 * lq);
+            cb[d] = cls[wbeg + (long long)NPS * d + h];
         }
-        const unsigned bal = __ballot_sync(kFull, above);
-        const bool act = (bal & gmask) != 0;
-        // ordered positions: one bit per group leader for each class
-        const bool leader = lq == 0;
-        int pos = 0;
+    }
+    // nsteps is a multiple of kBScanDepth: a warp's sub-chunk is a multiple of kStep (256) nodes
+    // and a step covers NPS <= 32 of them
+    static_assert((kStep / 32) % kBScanDepth == 0, "whole rounds of the register ring per sub-chunk");
+    for (int s0 = 0; s0 < nsteps; s0 += kBScanDepth) {
 #pragma unroll
-        for (int L = 0; L < kLists; ++L) {
-            const unsigned bits = __ballot_sync(kFull, leader && act && ccur == L);
-            if (ccur == L) pos = run[L] + __popc(bits & lt & ~gmask & ((1u << (h * LPN)) - 1u));
-            run[L] += __popc(bits);
-        }
-        if (act) {
-            const float f = ccur == 0 ? 1.f : omd;  // a dangling node's fluid leaves entirely (Section 3.3)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) rem[k] += f * v[k];
-            *reinterpret_cast<float4 *>(sel_rows + (long long)pos * K + 4 * lq) = cur;
-            if (lq == 0) {
-                sel_node[pos] = (int)node;
-                nsel += 1;
+        for (int dd = 0; dd < kBScanDepth; ++dd) {
+            const int s = s0 + dd;
+            const long long node = wbeg + (long long)NPS * s + h;
+            const float4 cur = buf[dd];
+            const int ccur = cb[dd];
+            if (s + kBScanDepth < nsteps) {
+                buf[dd] = *reinterpret_cast<const float4 *>(Fb + (node + (long long)NPS * kBScanDepth) * S + 4 * lq);
+                cb[dd] = cls[node + (long long)NPS * kBScanDepth];
             }
-            *reinterpret_cast<float4 *>(Fb + node * S + 4 * lq) = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float v[4] = {cur.x, cur.y, cur.z, cur.w};
+            bool above = false;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                l1[k] += v[k];
+                const bool a = v[k] > T4[k];
+                above |= a;
+                sel4[k] += a ? 1 : 0;
+            }
+            const unsigned bal = __ballot_sync(kFull, above);
+            const bool act = (bal & gmask) != 0;
+            // ordered positions: one bit per group leader for each class
+            const bool leader = lq == 0;
+            int pos = 0;
+#pragma unroll
+            for (int L = 0; L < kLists; ++L) {
+                const unsigned bits = __ballot_sync(kFull, leader && act && ccur == L);
+                if (ccur == L) pos = run[L] + __popc(bits & lt & ~gmask & ((1u << (h * LPN)) - 1u));
+                run[L] += __popc(bits);
+            }
+            if (act) {
+                const float f = ccur == 0 ? 1.f : omd;  // a dangling node's fluid leaves entirely (Section 3.3)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) rem[k] += f * v[k];
+                *reinterpret_cast<float4 *>(sel_rows + (long long)pos * K + 4 * lq) = cur;
+                if (lq == 0) {
+                    sel_node[pos] = (int)node;
+                    nsel += 1;
+                }
+                *reinterpret_cast<float4 *>(Fb + node * S + 4 * lq) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            if (pull && lq == 0) spos[node] = act ? pos : -1;
         }
-        if (pull && lq == 0) spos[node] = act ? pos : -1;
-        cur = nxt;
-        ccur = cnxt;
     }
     if (lane == 0) {
 #pragma unroll
