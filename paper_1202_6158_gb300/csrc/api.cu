@@ -85,10 +85,10 @@ static void free_graph(di_graph *g) {
         if (g->graph[k]) cudaGraphDestroy(g->graph[k]);
     }
     pool_free(g->bp, g->stream);
-    void *bufs[] = {g->row_ptr, g->col_idx, g->in_ptr, g->in_src, g->in_dst, g->wpull, g->bin_of, g->in_bin_of, g->pull_ids, g->V,
+    void *bufs[] = {g->row_ptr, g->col_idx, g->in_ptr, g->in_src, g->in_dst, g->wpull, g->bin_of, g->V,
                     g->inv_deg, g->inv_deg32, g->hot_ids, g->perm, g->new_of, g->rec64, g->rec32,
-                    g->wsel[0], g->wsel[1], g->rowhash, g->long_prefix, g->region, g->fcount, g->pre, g->ticket, g->sel, g->cls, g->F64, g->F32, g->H, g->part, g->st,
-                    g->trace, g->X, g->Z[0], g->Z[1], g->Ylong, g->ppart, g->pst};
+                    g->wsel[0], g->wsel[1], g->rowhash, g->region, g->fcount, g->pre, g->ticket, g->sel, g->cls, g->F64, g->F32, g->H, g->part, g->st,
+                    g->trace, g->X, g->Z[0], g->Z[1], g->Y, g->ppart, g->pst};
     for (void *b : bufs)
         if (b) cudaFreeAsync(b, g->stream);
     cudaStreamSynchronize(g->stream);
@@ -232,7 +232,13 @@ di_status di_graph_export(const di_graph *g, int32_t *perm, int32_t *outdeg, int
     if (r == DI_OK) r = copy_out(in_ptr, g->in_ptr, sizeof(int) * (n + 1), s);
     if (r == DI_OK) r = copy_out(in_src, g->in_src, sizeof(int) * (size_t)g->nnz, s);
     if (r == DI_OK) r = copy_out(bin_of, g->bin_of, sizeof(int) * n, s);
-    if (r == DI_OK) r = copy_out(in_bin_of, g->in_bin_of, sizeof(int) * n, s);
+    if (r == DI_OK && in_bin_of) {
+        int *tmp = nullptr;
+        DI_CUDA(cudaMallocAsync(&tmp, sizeof(int) * (size_t)n, s));
+        r = in_degree_classes(const_cast<di_graph *>(g), tmp);
+        if (r == DI_OK) r = copy_out(in_bin_of, tmp, sizeof(int) * n, s);
+        cudaFreeAsync(tmp, s);
+    }
     if (r != DI_OK) return r;
     DI_CUDA(cudaStreamSynchronize(s));
     if (cuts) {

@@ -157,14 +157,6 @@ __global__ void k_iota(int n, int *__restrict__ out) {
 }
 
 // number of pull chunk tasks of each long row
-__global__ void k_long_tasks(int nlong, const int *__restrict__ ids, const int *__restrict__ in_ptr, int chunk,
-                             int *__restrict__ ntasks) {
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nlong; r += (long long)gridDim.x * blockDim.x) {
-        int j = ids[r];
-        ntasks[r] = (in_ptr[j + 1] - in_ptr[j] + chunk - 1) / chunk;
-    }
-}
-
 // ----------------------------------------------------------- generic scan
 
 constexpr int kScanItems = 16;
@@ -669,10 +661,10 @@ di_status build_transpose(di_graph *g) {
     if (g->transposed) return DI_OK;
     cudaStream_t s = g->stream;
     // what an earlier attempt that failed part-way left behind
-    void *partial[] = {g->in_ptr, g->in_src, g->in_bin_of, g->pull_ids, g->long_prefix};
+    void *partial[] = {g->in_ptr, g->in_src};
     for (void *b : partial)
         if (b) cudaFreeAsync(b, s);
-    g->in_ptr = g->in_src = g->in_bin_of = g->pull_ids = g->long_prefix = nullptr;
+    g->in_ptr = g->in_src = nullptr;
     const int n = g->n;
     const long long L = g->nnz;
     // 3. in-link CSR: stable LSD radix sort of (target, source) pairs in source order
@@ -712,53 +704,16 @@ di_status build_transpose(di_graph *g) {
         if (r != DI_OK) return r;
     }
 
-    // 4. in-degree bins and the ids of each bin, ascending (one stable pass)
-    DI_CUDA(cudaMallocAsync(&g->in_bin_of, sizeof(int) * (size_t)n, s));
-    DI_CUDA(cudaMallocAsync(&g->pull_ids, sizeof(int) * (size_t)n, s));
-    k_in_bins<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, g->in_ptr, kInCut1, kInCut2, g->in_bin_of);
-    {
-        int *iota = nullptr, *ksorted = nullptr;
-        DI_CUDA(cudaMallocAsync(&iota, sizeof(int) * (size_t)n, s));
-        DI_CUDA(cudaMallocAsync(&ksorted, sizeof(int) * (size_t)n, s));
-        k_iota<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, iota);
-        di_status r = radix_pass(g->in_bin_of, iota, ksorted, g->pull_ids, n, 0, 3, s);
-        cudaFreeAsync(iota, s);
-        if (r != DI_OK) { cudaFreeAsync(ksorted, s); return r; }
-        // bin sizes: per-tile histograms of the bin ids, summed on the host
-        int counts[3] = {0, 0, 0};
-        int ntiles = ceil_div(n, kRadixTile);
-        int *th = nullptr;
-        DI_CUDA(cudaMallocAsync(&th, sizeof(int) * 4 * (size_t)ntiles, s));
-        k_radix_hist<<<ntiles, kRadixThreads, 0, s>>>(g->in_bin_of, n, 0, 3, 4, th, ntiles);
-        std::vector<int> hth(4 * (size_t)ntiles);
-        cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaMemcpyAsync(hth.data(), th, sizeof(int) * hth.size(), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        cudaFreeAsync(th, s);
-        cudaFreeAsync(ksorted, s);
-        if (e != cudaSuccess) return cuda_fail(e, "in-degree bins");
-        for (int b = 0; b < 3; ++b)
-            for (int t = 0; t < ntiles; ++t) counts[b] += hth[(size_t)b * ntiles + t];
-        for (int b = 0; b < 3; ++b) g->in_bin_count[b] = counts[b];
-        g->n_long_rows = counts[2];
-    }
-
-    // 5. chunk tasks of the longest in-rows
-    DI_CUDA(cudaMallocAsync(&g->long_prefix, sizeof(int) * (size_t)(g->n_long_rows + 1), s));
-    DI_CUDA(cudaMemsetAsync(g->long_prefix, 0, sizeof(int) * (size_t)(g->n_long_rows + 1), s));
-    if (g->n_long_rows > 0) {
-        const int *long_ids = g->pull_ids + g->in_bin_count[0] + g->in_bin_count[1];
-        k_long_tasks<<<grid_for(g->n_long_rows, 256, g->num_sms), 256, 0, s>>>(g->n_long_rows, long_ids, g->in_ptr,
-                                                                              kPullChunk, g->long_prefix);
-        di_status r = exclusive_scan(g->long_prefix, g->long_prefix, (long long)g->n_long_rows + 1, s);
-        if (r != DI_OK) return r;
-        int tot = 0;
-        DI_CUDA(cudaMemcpyAsync(&tot, g->long_prefix + g->n_long_rows, sizeof(int), cudaMemcpyDeviceToHost, s));
-        DI_CUDA(cudaStreamSynchronize(s));
-        g->n_long_tasks = tot;
-    }
     DI_CUDA(cudaGetLastError());
     g->transposed = true;
+    return DI_OK;
+}
+
+// in-degree class of every node (0 up to kInCut1 in-links, 1 up to kInCut2, 2 above) into a
+// device buffer of n ints; the in-link CSR must exist
+di_status in_degree_classes(di_graph *g, int *out_dev) {
+    k_in_bins<<<grid_for(g->n, 256, g->num_sms), 256, 0, g->stream>>>(g->n, g->in_ptr, kInCut1, kInCut2, out_dev);
+    DI_CUDA(cudaGetLastError());
     return DI_OK;
 }
 

@@ -9,7 +9,6 @@
 //   hot_ids int32[n_hot]                        input ids of the hot targets = internal 0..n_hot-1
 //   in_ptr  int32[n+1], in_src  int32[L]        in-link CSR, sources ascending
 //   bin_of  int32[n], cls uint8[npad]           out-degree class (0 dangling, 1 thread, 2 warp, 3 CTA)
-//   in_bin_of int32[n], pull_ids int32[n]       in-degree bin and ids grouped by it
 //   F64 / F32  [n padded to 4]                  fluid F (one of the two per solve)
 //   H       double[n]                           history H
 //   sel     Sel[n]                              per-sweep selected nodes (id, sent); list L of
@@ -36,9 +35,8 @@ constexpr int kLists = 4;               // selected nodes: 0 dangling, 1 thread,
 constexpr int kMaxScanBlocks = 152 * 8; // 8 CTAs per SM on 152 SMs
 constexpr int kOutCut1 = 8;             // out-degree <= cut1: one thread per source
 constexpr int kOutCut2 = 1024;          // out-degree <= cut2: one warp per source; above: whole CTA
-constexpr int kInCut1 = 8;              // in-degree <= cut1: one thread per row (pull)
-constexpr int kInCut2 = 2048;           // in-degree <= cut2: one warp per row; above: chunked
-constexpr int kPullChunk = 2048;        // in-links per chunk task for the longest rows
+constexpr int kInCut1 = 8;              // in-degree classes reported by di_graph_export: <= cut1,
+constexpr int kInCut2 = 2048;           // <= cut2, above
 constexpr int kTraceCap = 4096;         // sweep records kept when tracing
 constexpr int kExactEvery = 4;          // the scan sums |F|_1 exactly every this many sweeps
 constexpr int kHotSlots = 256;          // most-linked-to targets accumulated in shared memory by the push
@@ -208,7 +206,7 @@ struct di_graph {
     int *in_ptr = nullptr, *in_src = nullptr;   // built at first use (build_transpose)
     int *in_dst = nullptr;                      // [L] target of each in-link, built with the first batch pool
     bool transposed = false;
-    int *bin_of = nullptr, *in_bin_of = nullptr, *pull_ids = nullptr;
+    int *bin_of = nullptr;
     unsigned char *cls = nullptr;      // [npad] out-degree class per node, 0 on the padding
     double *V = nullptr;               // NULL: uniform 1/n
     double *inv_deg = nullptr;         // d / outdeg(i), 0 for dangling nodes (FP64)
@@ -216,10 +214,6 @@ struct di_graph {
     diter::RowRec<double> *rec64 = nullptr;  // [n] {row start, outdeg, d/outdeg}
     diter::RowRec<float> *rec32 = nullptr;   // [n] the same with d/outdeg in FP32
     int bin_count[4] = {0, 0, 0, 0};   // static out-degree class sizes
-    int in_bin_count[3] = {0, 0, 0};
-    int n_long_rows = 0;               // rows of in-degree bin 2
-    int *long_prefix = nullptr;        // [n_long_rows + 1] exclusive prefix of chunk tasks
-    int n_long_tasks = 0;
     int *hot_ids = nullptr;            // [kHotSlots] input id of each hot target (internal ids 0..n_hot-1)
     int n_hot = 0;
     unsigned long long *rowhash = nullptr;  // [n] fingerprint of each input row (input numbering)
@@ -250,10 +244,9 @@ struct di_graph {
     // power iteration
     double *X = nullptr;
     double *Z[2] = {nullptr, nullptr};
-    double *Ylong = nullptr;           // accumulators of the chunked rows
+    double *Y = nullptr;               // [n] the product being formed: (1-d)V + the gathered z
     diter::PowerPartial *ppart = nullptr;
     diter::PowerState *pst = nullptr;
-    int pull_blocks[3] = {0, 0, 0};
     double pprof_ms[2] = {0.0, 0.0};   // profiled power iteration: pull, finalize
 
     // batched queries (allocated at the first batch)
@@ -281,6 +274,7 @@ di_status cuda_fail(cudaError_t e, const char *what);
 // graph ingest (graph_build.cu)
 di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_dev);
 di_status build_in_dst(di_graph *g);  // the transpose, then in_dst
+di_status in_degree_classes(di_graph *g, int *out_dev);
 di_status build_transpose(di_graph *g);   // the in-link CSR and its bins, at first use
 di_status validate_v(di_graph *g, const double *V_dev);
 

@@ -5,33 +5,31 @@
 // Each product is a pull ("collection", Section 1) over the in-link lists:
 //   y_j = (1-d)V_j + sum_{i -> j} z_i,   z_i = d * x_i / outdeg(i)  (0 if dangling)
 // with z of the current iterate kept in one of two buffers so the gather never
-// sees a value of the product being formed.  Rows are grouped by in-degree at
-// create time: a thread per row up to kInCut1 in-links, a warp per row up to
-// kInCut2, and above that chunk tasks of kPullChunk in-links, one warp each,
-// whose sums meet in a per-row accumulator.  The per-row epilogue (|y - x|,
-// x = y, z = d*y/outdeg) is fused into the pull; one CTA finishes the chunked
-// rows, reduces |X_{k+1} - X_k|_1 in fixed order and drives the CUDA-graph
-// while-loop.
+// sees a value of the product being formed.  Three kernels per product:
+//   k_pgather     the in-links, in target order, cut into even ranges: each lane takes
+//                 kPowRun consecutive links, gathers z of their sources, sums them
+//                 serially per target (one FP64 add per link) and adds each target's sum
+//                 to the accumulator Y with one red.add;
+//   k_pepilogue   streams the nodes: |y - x|, x = y, z = d*y/outdeg, Y = (1-d)V for the
+//                 next product, with per-CTA sums of |y - x|;
+//   k_power_finalize  one CTA reduces |X_{k+1} - X_k|_1 in fixed order and drives the
+//                 CUDA-graph while-loop.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 
+#include "device_common.cuh"
 #include "internal.h"
 
 namespace diter {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-    return v;
-}
+constexpr int kPowRun = 8;  // consecutive in-links per lane and step of the gather
 
 __device__ double block_sum_d(double v, double *sh) {
-    v = warp_sum_d(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
     __syncthreads();
     double r = 0.0;
@@ -43,95 +41,78 @@ __device__ double block_sum_d(double v, double *sh) {
 
 struct PullArgs {
     int n;
-    const int *in_ptr, *in_src, *pull_ids, *long_ids, *long_prefix;
+    long long nnz;
+    const int *in_src, *in_dst;
     const double *inv_deg;  // d / outdeg, 0 for dangling nodes
-    int cnt0, cnt1, nlong, ntasks;
-    int BA, BB;
-    const double *V;  // NULL: uniform
+    const double *V;        // NULL: uniform
     double omd, d, u, omdu;
-    double *X, *Z0, *Z1, *Ylong;
+    double *X, *Z0, *Z1, *Y;
     PowerPartial *pp;
     PowerState *pst;
 };
 
-__device__ __forceinline__ double v_of(const PullArgs &a, int j) { return a.V ? a.V[j] : a.u; }
 // (1-d) V_j
 __device__ __forceinline__ double omdv_of(const PullArgs &a, int j) { return a.V ? a.omd * a.V[j] : a.omdu; }
 
-// finish row j with its new value y; returns |y - x_j|
-__device__ __forceinline__ double finish_row(const PullArgs &a, double *zn, int j, double y) {
-    double dlt = fabs(y - a.X[j]);
-    a.X[j] = y;
-    zn[j] = y * a.inv_deg[j];
-    return dlt;
+__global__ void __launch_bounds__(256, 4) k_pgather(PullArgs a) {
+    if (a.pst->done) return;
+    const double *__restrict__ zc = a.pst->cur ? a.Z1 : a.Z0;
+    constexpr int kStepLinks = 32 * kPowRun;
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = (long long)gridDim.x * 8, gw = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    // ranges of whole steps, so that every full run starts on a 32-byte boundary
+    const long long per = (a.nnz + nwarps - 1) / nwarps + kStepLinks - 1;
+    const long long span = per - per % kStepLinks;
+    const long long e_beg = min(a.nnz, gw * span), e_end = min(a.nnz, e_beg + span);
+    for (long long e0 = e_beg; e0 < e_end; e0 += kStepLinks) {
+        const long long eb = e0 + (long long)kPowRun * lane;
+        int src[kPowRun], dst[kPowRun];
+        if (eb + kPowRun <= e_end) {
+            const int4 *ps = reinterpret_cast<const int4 *>(a.in_src + eb);
+            const int4 *pd = reinterpret_cast<const int4 *>(a.in_dst + eb);
+#pragma unroll
+            for (int h = 0; h < kPowRun / 4; ++h) {
+                const int4 x = __ldg(ps + h), y = __ldg(pd + h);
+                src[4 * h] = x.x; src[4 * h + 1] = x.y; src[4 * h + 2] = x.z; src[4 * h + 3] = x.w;
+                dst[4 * h] = y.x; dst[4 * h + 1] = y.y; dst[4 * h + 2] = y.z; dst[4 * h + 3] = y.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kPowRun; ++k) {
+                const bool in = eb + k < e_end;
+                src[k] = in ? __ldg(a.in_src + eb + k) : -1;
+                dst[k] = in ? __ldg(a.in_dst + eb + k) : -1;
+            }
+        }
+        double v[kPowRun];
+#pragma unroll
+        for (int k = 0; k < kPowRun; ++k) v[k] = src[k] >= 0 ? zc[src[k]] : 0.0;
+        int cur = dst[0];
+        double acc = v[0];
+#pragma unroll
+        for (int k = 1; k < kPowRun; ++k) {
+            if (dst[k] != cur) {
+                if (cur >= 0 && acc != 0.0) red_add(a.Y + cur, acc);
+                cur = dst[k];
+                acc = 0.0;
+            }
+            acc += v[k];
+        }
+        if (cur >= 0 && acc != 0.0) red_add(a.Y + cur, acc);
+    }
 }
 
-// sum of z over a row of at most kInCut1 in-links: index loads, then gathers, then
-// the adds in ascending order
-__device__ __forceinline__ double short_row_sum(const PullArgs &a, const double *__restrict__ zc, int b, int e) {
-    int s[kInCut1];
-#pragma unroll
-    for (int t = 0; t < kInCut1; ++t) s[t] = b + t < e ? __ldg(a.in_src + b + t) : -1;
-    double z[kInCut1];
-#pragma unroll
-    for (int t = 0; t < kInCut1; ++t) z[t] = s[t] >= 0 ? zc[s[t]] : 0.0;
-    double acc = 0.0;
-#pragma unroll
-    for (int t = 0; t < kInCut1; ++t)
-        if (s[t] >= 0) acc += z[t];
-    return acc;
-}
-
-__global__ void __launch_bounds__(256) k_pull(PullArgs a) {
+__global__ void __launch_bounds__(256) k_pepilogue(PullArgs a) {
     __shared__ double sh[8];
     if (a.pst->done) return;
-    const int cur = a.pst->cur;
-    const double *__restrict__ zc = cur ? a.Z1 : a.Z0;
-    double *zn = cur ? a.Z0 : a.Z1;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double *__restrict__ zn = a.pst->cur ? a.Z0 : a.Z1;
     double delta = 0.0;
-    if ((int)blockIdx.x < a.BA) {
-        const long long stride = (long long)a.BA * 256;
-        long long r = (long long)blockIdx.x * 256 + threadIdx.x;
-        for (; r + stride < a.cnt0; r += 2 * stride) {  // two rows in flight
-            const int j0 = a.pull_ids[r], j1 = a.pull_ids[r + stride];
-            const int b0 = a.in_ptr[j0], e0 = a.in_ptr[j0 + 1], b1 = a.in_ptr[j1], e1 = a.in_ptr[j1 + 1];
-            const double s0 = short_row_sum(a, zc, b0, e0);
-            const double s1 = short_row_sum(a, zc, b1, e1);
-            delta += finish_row(a, zn, j0, omdv_of(a, j0) + s0);
-            delta += finish_row(a, zn, j1, omdv_of(a, j1) + s1);
-        }
-        if (r < a.cnt0) {
-            const int j = a.pull_ids[r];
-            delta += finish_row(a, zn, j, omdv_of(a, j) + short_row_sum(a, zc, a.in_ptr[j], a.in_ptr[j + 1]));
-        }
-    } else if ((int)blockIdx.x < a.BA + a.BB) {
-        const long long wid = (long long)(blockIdx.x - a.BA) * 8 + w, nw = (long long)a.BB * 8;
-        for (long long r = wid; r < a.cnt1; r += nw) {
-            const int j = a.pull_ids[a.cnt0 + r];
-            const int b = a.in_ptr[j], e = a.in_ptr[j + 1];
-            double acc = 0.0;
-            for (int k = b + lane; k < e; k += 32) acc += zc[a.in_src[k]];
-            acc = warp_sum_d(acc);
-            if (lane == 0) delta += finish_row(a, zn, j, omdv_of(a, j) + acc);
-        }
-    } else {
-        const int BC = gridDim.x - a.BA - a.BB;
-        const long long wid = (long long)(blockIdx.x - a.BA - a.BB) * 8 + w, nw = (long long)BC * 8;
-        for (long long t = wid; t < a.ntasks; t += nw) {
-            int lo = 0, hi = a.nlong;  // last r with long_prefix[r] <= t
-            while (hi - lo > 1) {
-                int mid = (lo + hi) >> 1;
-                if (a.long_prefix[mid] <= t) lo = mid; else hi = mid;
-            }
-            const int j = a.long_ids[lo];
-            const long long b = (long long)a.in_ptr[j] + (t - a.long_prefix[lo]) * (long long)kPullChunk;
-            const long long e = min((long long)a.in_ptr[j + 1], b + kPullChunk);
-            double acc = 0.0;
-            for (long long k = b + lane; k < e; k += 32) acc += zc[a.in_src[k]];
-            acc = warp_sum_d(acc);
-            if (lane == 0) atomicAdd(&a.Ylong[lo], acc);
-        }
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < a.n; j += (long long)gridDim.x * blockDim.x) {
+        const double y = a.Y[j];
+        delta += fabs(y - a.X[j]);
+        a.X[j] = y;
+        zn[j] = y * a.inv_deg[j];
+        a.Y[j] = omdv_of(a, (int)j);  // the next product starts from (1-d)V
     }
     delta = block_sum_d(delta, sh);
     if (threadIdx.x == 0) a.pp[blockIdx.x].delta = delta;
@@ -143,27 +124,17 @@ __global__ void k_power_finalize(PullArgs a, int nparts, cudaGraphConditionalHan
         if (threadIdx.x == 0 && in_graph) cudaGraphSetConditional(handle, 0);
         return;
     }
-    const int cur = a.pst->cur;
-    double *zn = cur ? a.Z0 : a.Z1;
-    double delta = 0.0;
-    for (int r = threadIdx.x; r < a.nlong; r += blockDim.x) {
-        const int j = a.long_ids[r];
-        delta += finish_row(a, zn, j, a.Ylong[r]);
-        a.Ylong[r] = omdv_of(a, j);
-    }
-    delta = block_sum_d(delta, sh);
     double parts = 0.0;
     for (int c = threadIdx.x; c < nparts; c += blockDim.x) parts += a.pp[c].delta;
     parts = block_sum_d(parts, sh);
     if (threadIdx.x != 0) return;
     PowerState *p = a.pst;
-    const double dl = parts + delta;
-    p->delta = dl;
+    p->delta = parts;
     p->iters += 1;
-    p->cur = cur ^ 1;
+    p->cur ^= 1;
     int done = 0;
-    if (!isfinite(dl)) done = 3;
-    else if (dl * p->d / (1.0 - p->d) < p->tol) done = 1;
+    if (!isfinite(parts)) done = 3;
+    else if (parts * p->d / (1.0 - p->d) < p->tol) done = 1;
     else if (p->iters >= p->max_iters) done = 2;
     p->done = done;
     if (done && in_graph) cudaGraphSetConditional(handle, 0);
@@ -174,9 +145,8 @@ __global__ void k_power_init(PullArgs a, double tol, int max_iters) {
         a.X[i] = 0.0;
         a.Z0[i] = 0.0;
         a.Z1[i] = 0.0;
+        a.Y[i] = omdv_of(a, (int)i);
     }
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < a.nlong; r += (long long)gridDim.x * blockDim.x)
-        a.Ylong[r] = omdv_of(a, a.long_ids[r]);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.pst->delta = 0.0;
         a.pst->tol = tol;
@@ -191,18 +161,10 @@ __global__ void k_power_init(PullArgs a, double tol, int max_iters) {
 PullArgs make_args(di_graph *g) {
     PullArgs a;
     a.n = g->n;
-    a.in_ptr = g->in_ptr;
+    a.nnz = g->nnz;
     a.in_src = g->in_src;
+    a.in_dst = g->in_dst;
     a.inv_deg = g->inv_deg;
-    a.pull_ids = g->pull_ids;
-    a.cnt0 = g->in_bin_count[0];
-    a.cnt1 = g->in_bin_count[1];
-    a.nlong = g->n_long_rows;
-    a.long_ids = g->pull_ids + g->in_bin_count[0] + g->in_bin_count[1];
-    a.long_prefix = g->long_prefix;
-    a.ntasks = g->n_long_tasks;
-    a.BA = g->pull_blocks[0];
-    a.BB = g->pull_blocks[1];
     a.V = g->V;
     a.omd = 1.0 - g->d;
     a.d = g->d;
@@ -211,20 +173,23 @@ PullArgs make_args(di_graph *g) {
     a.X = g->X;
     a.Z0 = g->Z[0];
     a.Z1 = g->Z[1];
-    a.Ylong = g->Ylong;
+    a.Y = g->Y;
     a.pp = g->ppart;
     a.pst = g->pst;
     return a;
 }
 
-int role_blocks(long long work, int per_block, int cap) {
-    if (work <= 0) return 0;
-    return (int)std::max(1LL, std::min((work + per_block - 1) / per_block, (long long)cap));
+int gather_grid(const di_graph *g) { return g->num_sms * 4; }
+int epilogue_grid(const di_graph *g) { return std::max(1, std::min(g->num_sms * 8, (g->n + 255) / 256)); }
+
+void launch_product(di_graph *g, const PullArgs &a, cudaStream_t s) {
+    k_pgather<<<gather_grid(g), 256, 0, s>>>(a);
+    k_pepilogue<<<epilogue_grid(g), 256, 0, s>>>(a);
 }
 
 di_status build_power_graph(di_graph *g) {
     PullArgs a = make_args(g);
-    const int nparts = g->pull_blocks[0] + g->pull_blocks[1] + g->pull_blocks[2];
+    const int nparts = epilogue_grid(g);
     cudaGraph_t graph = nullptr;
     DI_CUDA(cudaGraphCreate(&graph, 0));
     cudaGraphConditionalHandle handle;
@@ -241,7 +206,7 @@ di_status build_power_graph(di_graph *g) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     e = cudaStreamBeginCaptureToGraph(g->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(e, "cudaStreamBeginCaptureToGraph"); }
-    k_pull<<<nparts, 256, 0, g->cap>>>(a);
+    launch_product(g, a, g->cap);
     k_power_finalize<<<1, 256, 0, g->cap>>>(a, nparts, handle, 1);
     cudaGraph_t captured = nullptr;
     e = cudaStreamEndCapture(g->cap, &captured);
@@ -258,15 +223,11 @@ di_status build_power_graph(di_graph *g) {
 
 di_status power_alloc(di_graph *g) {
     cudaStream_t s = g->stream;
-    const int cap = g->num_sms * 8;
-    g->pull_blocks[0] = role_blocks(g->in_bin_count[0], 256, cap);
-    g->pull_blocks[1] = role_blocks(g->in_bin_count[1], 8, cap);
-    g->pull_blocks[2] = role_blocks(g->n_long_tasks, 8, cap);
-    const int nparts = std::max(1, g->pull_blocks[0] + g->pull_blocks[1] + g->pull_blocks[2]);
+    const int nparts = epilogue_grid(g);
     DI_CUDA(cudaMallocAsync(&g->X, sizeof(double) * (size_t)g->n, s));
     DI_CUDA(cudaMallocAsync(&g->Z[0], sizeof(double) * (size_t)g->n, s));
     DI_CUDA(cudaMallocAsync(&g->Z[1], sizeof(double) * (size_t)g->n, s));
-    DI_CUDA(cudaMallocAsync(&g->Ylong, sizeof(double) * (size_t)std::max(1, g->n_long_rows), s));
+    DI_CUDA(cudaMallocAsync(&g->Y, sizeof(double) * (size_t)g->n, s));
     DI_CUDA(cudaMallocAsync(&g->ppart, sizeof(PowerPartial) * (size_t)nparts, s));
     DI_CUDA(cudaMallocAsync(&g->pst, sizeof(PowerState), s));
     DI_CUDA(cudaMemsetAsync(g->pst, 0, sizeof(PowerState), s));
@@ -276,7 +237,7 @@ di_status power_alloc(di_graph *g) {
 di_status run_power(di_graph *g, double tol, int max_iter, int profile, double *X_out, bool out_dev, di_stats *st) {
     cudaStream_t s = g->stream;
     if (!g->X) {  // the in-link side and the iterates, at the first power iteration
-        di_status r = build_transpose(g);
+        di_status r = build_in_dst(g);
         if (r == DI_OK) r = power_alloc(g);
         if (r != DI_OK) return r;
     }
@@ -285,18 +246,19 @@ di_status run_power(di_graph *g, double tol, int max_iter, int profile, double *
         if (r != DI_OK) return r;
     }
     PullArgs a = make_args(g);
-    const int nparts = g->pull_blocks[0] + g->pull_blocks[1] + g->pull_blocks[2];
+    const int nparts = epilogue_grid(g);
     DI_CUDA(cudaEventRecord(g->ev0, s));
     const int grid = std::max(1, std::min(g->num_sms * 8, (g->n + 255) / 256));
     k_power_init<<<grid, 256, 0, s>>>(a, tol, max_iter);
     DI_CUDA(cudaGetLastError());
     g->pprof_ms[0] = g->pprof_ms[1] = 0.0;
     if (profile) {
-        // the graph body's two kernels launched from the host with events around each
+        // the graph body's kernels launched from the host with events around the product
+        // (gather and epilogue) and the finalize
         cudaGraphConditionalHandle none = 0;
         for (;;) {
             DI_CUDA(cudaEventRecord(g->pev[0], s));
-            k_pull<<<nparts, 256, 0, s>>>(a);
+            launch_product(g, a, s);
             DI_CUDA(cudaEventRecord(g->pev[1], s));
             k_power_finalize<<<1, 256, 0, s>>>(a, nparts, none, 0);
             DI_CUDA(cudaEventRecord(g->pev[2], s));
@@ -332,7 +294,7 @@ di_status run_power(di_graph *g, double tol, int max_iter, int profile, double *
         st->sweeps = h.iters;
         st->converged = h.done == 1 ? 1 : 0;
         st->seconds = ms * 1e-3;
-        st->kernel_launches = 1 + 2LL * h.iters;  // init + (pull, finalize) per product
+        st->kernel_launches = 1 + 3LL * h.iters;  // init + (gather, epilogue, finalize) per product
     }
     if (h.done == 3) return set_error(DI_EKERNEL, "power iteration became non-finite");
     if (h.done != 1) return set_error(DI_ENOTCONVERGED, "power iteration hit max_iter before the stop rule");
