@@ -520,7 +520,8 @@ def main():
 
     # ---- profiled power iteration: pull kernel CUDA-event time
     _, ppst = G.power(tol, X_out=X, profile=1)
-    pull_bytes_iter = g.nnz * (4 + 8) + g.n * (4 + 4 + 3 * 8 + 8)   # in_src + gather, per row: id, in_ptr, x rw, z, 1/deg
+    # per in-link: source, target, z gather; per node: Y read + reset, x read + write, z write, d/outdeg
+    pull_bytes_iter = g.nnz * (4 + 4 + 8) + g.n * (2 * 8 + 2 * 8 + 8 + 8)
 
     # ---- profiled solve: per-kernel CUDA-event times and algorithmic bytes from the trace
     G.solve(tol, H_out=H, beta=args.beta, profile=1, trace=1, direction=args.direction)
@@ -547,7 +548,7 @@ def main():
                 "avg_launch_us": 1e3 * kd["ms"] / max(1, kd["launches"]),
                 "per_kernel": {k: {"ms_total": v["ms"], "launches": v["launches"],
                                    "GBps": v["alg_bytes"] / (v["ms"] * 1e-3) / 1e9 if v["ms"] > 0 else None}
-                               for k, v in list(kernels.items()) + [("pull (power iteration)", pull)]},
+                               for k, v in list(kernels.items()) + [("power iteration product", pull)]},
                 "finalize_ms_total": prof["finalize_ms"]}
 
     # ---- end to end through the C ABI with pinned host buffers
