@@ -403,6 +403,7 @@ __global__ void k_perm_deg(int n, const int *__restrict__ perm, const int *__res
 }
 
 // edge e of the relabeled CSR: its row r by binary search, then the input edge it copies
+// (one thread per edge keeps hub rows of tens of thousands of out-links balanced)
 __global__ void k_perm_cols(int n, long long nnz, const int *__restrict__ perm, const int *__restrict__ new_of,
                             const int *__restrict__ row_ptr_in, const int *__restrict__ col_in,
                             const int *__restrict__ row_ptr_out, int *__restrict__ col_out) {
@@ -465,8 +466,10 @@ __device__ __forceinline__ unsigned long long fp_edge(int t, int p) {
     return fp_mix(((unsigned long long)(unsigned)t << 32 | (unsigned)p) + 0x9e3779b97f4a7c15ull);
 }
 
+// the fingerprint of every input row, from the relabeled CSR: internal row r is input row
+// perm[r] with its targets renumbered and their order kept, so perm maps both back
 __global__ void k_row_hash(int n, const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
-                           unsigned long long *__restrict__ out) {
+                           const int *__restrict__ perm, unsigned long long *__restrict__ out) {
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int w0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; w0 < n; w0 += nw * 32) {
@@ -477,7 +480,7 @@ __global__ void k_row_hash(int n, const int *__restrict__ row_ptr, const int *__
             beg = row_ptr[v];
             deg = row_ptr[v + 1] - beg;
             if (deg <= 64)
-                for (int p = 0; p < deg; ++p) acc += fp_edge(col_idx[beg + p], p);
+                for (int p = 0; p < deg; ++p) acc += fp_edge(perm[col_idx[beg + p]], p);
         }
         // rows above 64 out-links: the whole warp, one row at a time
         unsigned longs = __ballot_sync(0xffffffffu, v < n && deg > 64);
@@ -486,11 +489,11 @@ __global__ void k_row_hash(int n, const int *__restrict__ row_ptr, const int *__
             longs &= longs - 1;
             const int b = __shfl_sync(0xffffffffu, beg, src), dg = __shfl_sync(0xffffffffu, deg, src);
             unsigned long long part = 0;
-            for (int p = lane; p < dg; p += 32) part += fp_edge(col_idx[b + p], p);
+            for (int p = lane; p < dg; p += 32) part += fp_edge(perm[col_idx[b + p]], p);
             for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
             if (lane == src) acc = part;
         }
-        if (v < n) out[v] = fp_mix(0x243f6a8885a308d3ull ^ (unsigned long long)deg) + acc;
+        if (v < n) out[perm[v]] = fp_mix(0x243f6a8885a308d3ull ^ (unsigned long long)deg) + acc;
     }
 }
 
@@ -523,9 +526,6 @@ di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_de
         if (hf & kNotMonotone) return set_error(DI_EINVAL, "row_ptr must be non-decreasing");
         if (hf & kColRange) return set_error(DI_EINVAL, "col_idx has an entry outside [0, n)");
     }
-    DI_CUDA(cudaMallocAsync(&g->rowhash, sizeof(unsigned long long) * (size_t)n, s));
-    k_row_hash<<<std::max(1, std::min(ceil_div(n, 256), g->num_sms * 8)), 256, 0, s>>>(n, g->row_ptr, g->col_idx,
-                                                                                    g->rowhash);
 
     // 1b. internal numbering: the hot targets -- the kHotSlots largest in-degrees (at least
     //     kHotMinInDeg), ties by lower input id, found by a stable LSD radix sort -- become ids
@@ -706,6 +706,16 @@ di_status build_transpose(di_graph *g) {
 
     DI_CUDA(cudaGetLastError());
     g->transposed = true;
+    return DI_OK;
+}
+
+// row fingerprints, at the first graph update that reads them
+di_status ensure_rowhash(di_graph *g) {
+    if (g->rowhash) return DI_OK;
+    DI_CUDA(cudaMallocAsync(&g->rowhash, sizeof(unsigned long long) * (size_t)g->n, g->stream));
+    k_row_hash<<<std::max(1, std::min(ceil_div(g->n, 256), g->num_sms * 8)), 256, 0, g->stream>>>(
+        g->n, g->row_ptr, g->col_idx, g->perm, g->rowhash);
+    DI_CUDA(cudaGetLastError());
     return DI_OK;
 }
 

@@ -216,7 +216,7 @@ struct di_graph {
     int bin_count[4] = {0, 0, 0, 0};   // static out-degree class sizes
     int *hot_ids = nullptr;            // [kHotSlots] input id of each hot target (internal ids 0..n_hot-1)
     int n_hot = 0;
-    unsigned long long *rowhash = nullptr;  // [n] fingerprint of each input row (input numbering)
+    unsigned long long *rowhash = nullptr;  // [n] fingerprint of each input row (input numbering), at first update
     int *perm = nullptr;               // [n] internal -> input id
     int *new_of = nullptr;             // [n] input -> internal id
 
@@ -275,6 +275,7 @@ di_status cuda_fail(cudaError_t e, const char *what);
 di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_dev);
 di_status build_in_dst(di_graph *g);  // the transpose, then in_dst
 di_status in_degree_classes(di_graph *g, int *out_dev);
+di_status ensure_rowhash(di_graph *g);  // fingerprints of the input rows (graph updates)
 di_status build_transpose(di_graph *g);   // the in-link CSR and its bins, at first use
 di_status validate_v(di_graph *g, const double *V_dev);
 

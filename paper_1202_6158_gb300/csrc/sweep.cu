@@ -977,6 +977,11 @@ di_status run_update(di_graph *go, di_graph *gn, const di_solve_opts &o, double 
         r = build_sweep_graph<double>(gn, slot, gn->F64, o.select ? gn->wsel[o.select - 1] : nullptr);
         if (r != DI_OK) return r;
     }
+    if (go != gn) {  // the row fingerprints that find the changed rows, at the first update
+        r = ensure_rowhash(go);
+        if (r == DI_OK) r = ensure_rowhash(gn);
+        if (r != DI_OK) return r;
+    }
     // both graphs' earlier work is complete before the new graph's stream reads the old state
     DI_CUDA(cudaStreamSynchronize(go->stream));
     DI_CUDA(cudaEventRecord(gn->ev0, gn->stream));
