@@ -58,14 +58,15 @@ def update_cases():
 CASES = update_cases()
 
 
+@pytest.mark.parametrize("direction", [0, 1])
 @pytest.mark.parametrize("name", sorted(CASES))
 @pytest.mark.parametrize("tol0", [1e-2, 1e-6])
-def test_update_reaches_new_fixed_point(di, name, tol0):
+def test_update_reaches_new_fixed_point(di, name, tol0, direction):
     n, rp, ci, rp2, ci2 = CASES[name]
     V = gg.uniform_v(n)
     with di.DiGraph(n, rp, ci, D) as Go, di.DiGraph(n, rp2, ci2, D) as Gn:
         Go.solve(tol0)
-        H, st = Gn.update_from(Go, 1e-12)
+        H, st = Gn.update_from(Go, 1e-12, direction=direction)
         F, H2 = Gn.state()
     assert np.array_equal(H, H2)
     assert st["converged"] == 1 and st["bound"] <= 1e-12
@@ -81,14 +82,15 @@ def test_update_reaches_new_fixed_point(di, name, tol0):
     assert np.abs(r1.H - H).sum() <= st["bound"] + r1.l1F / (1 - D) + 1e-12
 
 
-def test_injection_keeps_theorem1_for_new_graph(di):
+@pytest.mark.parametrize("direction", [0, 1])
+def test_injection_keeps_theorem1_for_new_graph(di, direction):
     n, rp, ci, rp2, ci2 = CASES["zipf_2e14"]
     F0 = (1 - D) * gg.uniform_v(n)
     P2 = sparse_P(n, rp2, ci2)
     with di.DiGraph(n, rp, ci, D) as Go, di.DiGraph(n, rp2, ci2, D) as Gn:
         Go.solve(1e-3)
         for k in (1, 3, 10):
-            H, st = Gn.update_from(Go, 1e-14, max_sweeps=k, allow_unconverged=True)
+            H, st = Gn.update_from(Go, 1e-14, max_sweeps=k, allow_unconverged=True, direction=direction)
             F, H2 = Gn.state()
             assert st["sweeps"] == k
             if k == 1:
