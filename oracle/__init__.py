@@ -104,6 +104,14 @@ def _f64(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+def _vec(V, n):
+    """V as a contiguous float64 array of exactly n entries (the C side reads n values)."""
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    if V.shape != (n,):
+        raise ValueError(f"oracle: V must have shape ({n},), got {V.shape}")
+    return V
+
+
 @dataclass
 class DiterResult:
     H: np.ndarray
@@ -125,7 +133,7 @@ class DiterResult:
 def init(n, d, V, lib=None):
     """ALGO-REF initialization (Section 2.2): H = 0, F = (1-d)V, R = 1-d."""
     lib = lib or load()
-    V = np.ascontiguousarray(V, dtype=np.float64)
+    V = _vec(V, n)
     F = np.empty(n, dtype=np.float64)
     H = np.empty(n, dtype=np.float64)
     R = lib.orc_init(n, d, _f64(V), _f64(F), _f64(H))
@@ -215,7 +223,7 @@ def power(n, row_ptr, col_idx, d, V, tol, max_iter=100000, lib=None):
     lib = lib or load()
     rp, rpp = _i32(row_ptr)
     ci, cip = _i32(col_idx if len(col_idx) else np.zeros(1, np.int32))
-    V = np.ascontiguousarray(V, dtype=np.float64)
+    V = _vec(V, n)
     X = np.empty(n, dtype=np.float64)
     it = ctypes.c_int64(0)
     delta = ctypes.c_double(0)
