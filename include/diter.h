@@ -83,9 +83,9 @@ typedef struct {
                                 each one (same kernels and arguments, no graph); read with di_get_profile */
     int32_t select;          /* a di_select value: which nodes a sweep diffuses (default DI_SELECT_REF) */
     int32_t direction;       /* 0: every sweep pushes along the selected nodes' out-links; 1: a sweep
-                                pulls along every node's in-links instead when the previous sweep
-                                diffused at least a quarter of all out-links (the same diffusion; the
-                                in-link CSR is built at first use, 8 bytes per link) */
+                                pulls along every node's in-links instead when each of the two
+                                sweeps before it diffused at least half of all out-links (the same
+                                diffusion; the in-link CSR is built at first use, 12 bytes per link) */
 } di_solve_opts;
 
 /*

@@ -771,7 +771,7 @@ void capture_batch_body(di_graph *g, BatchPool *p, cudaGraphConditionalHandle ha
                                                     p->Fb, p->Hb, S, g->region, p->pre, g->W, p->selb_node,
                                                     p->selb_rows, p->bctl);
     // rows of 4 lanes always push: their 16-byte reductions cost no more than the pull's gathers
-    const long long pull_edges = LPN >= 2 ? std::max(1LL, (g->nnz + kPullShare - 1) / kPullShare) : LLONG_MAX;
+    const long long pull_edges = LPN >= 2 ? std::max(1LL, (g->nnz + kPullShareBatch - 1) / kPullShareBatch) : LLONG_MAX;
     k_bfinalize<<<1, kLanes, 0, g->cap>>>(g->n, pull_edges, p->bq, p->bctl, handle, 1);
 }
 

@@ -99,9 +99,12 @@ struct SolveState {
 // batched personalized queries: up to kLanes queries interleaved in one fluid row
 // captured sweep loops: 7 selection / precision variants, each push-only or with the pull direction
 constexpr int kSweepSlots = 14;
-// a sweep pulls (when allowed) if the previous sweep's selected nodes held at least 1/kPullShare
-// of all out-links
-constexpr long long kPullShare = 4;
+// a sweep is dense when its selected nodes hold at least 1/kPullShareBatch (batch) or
+// 1/kPullShareSolve (single solve) of all out-links; a batch pulls after one dense sweep, a
+// single solve after two in a row (one FP64 pull sweep costs about as much as pushing 0.7 L
+// out-links)
+constexpr long long kPullShareBatch = 4;
+constexpr long long kPullShareSolve = 2;
 
 constexpr int kLanes = 64;              // queries per batch (the width of a fluid row)
 constexpr int kBatchHot = 32;           // hot targets whose rows the batched push sums in shared memory

@@ -693,9 +693,9 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, InitK
     }
     const double beta = o.beta > 0 ? o.beta : 0.5;
     const int max_sweeps = o.max_sweeps > 0 ? o.max_sweeps : 1000000;
-    // a sweep pulls when the previous one diffused a kPullShare-th of all out-links
-    const long long pull_edges =
-        o.direction ? std::max(1LL, (g->nnz + kPullShare - 1) / kPullShare) : std::numeric_limits<long long>::max();
+    // a sweep that diffused at least half of all out-links is dense
+    const long long pull_edges = o.direction ? std::max(1LL, (g->nnz + kPullShareSolve - 1) / kPullShareSolve)
+                                             : std::numeric_limits<long long>::max();
     if (init == kInitState) {
         k_l1_partials<FT><<<g->G, kScanThreads, 0, s>>>(n, g->chunk, F, g->part);
         k_init_control_l1<<<1, 32, 0, s>>>(g->st, g->part, g->G, o.tol * omd, beta, omd, n, o.max_edge_pushes,

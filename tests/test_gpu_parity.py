@@ -198,9 +198,9 @@ def test_trace_records(di, direction):
     H, F, st, tr = _solve(di, n, rp, ci, 1e-10, trace=1, direction=direction)
     assert len(tr) == st["sweeps"]
     # the first two sweeps push; with direction=1 a sweep pulls exactly when the two before it
-    # each diffused at least a quarter of the out-links (dense sweeps, as on this R-MAT graph)
+    # each diffused at least half of the out-links (dense sweeps, as on this R-MAT graph)
     nnz = len(ci)
-    dense = [4 * t["edges"] >= nnz for t in tr]
+    dense = [2 * t["edges"] >= nnz for t in tr]
     assert tr[0]["pull"] == 0 and tr[1]["pull"] == 0
     for k in range(2, len(tr)):
         assert tr[k]["pull"] == (1 if direction and dense[k - 1] and dense[k - 2] else 0)
