@@ -173,6 +173,20 @@ def dist_env():
     return rank, world, local
 
 
+def aggregate_ranks(dist, dev, sums, maxes):
+    """Whole-job figures of a replicas run: the work of all ranks adds up (sums) and the time
+    is the slowest rank's (maxes).  dist is torch.distributed with a process group, or None for
+    one process; dev is the device the reduction tensors live on (cuda for NCCL, cpu for gloo)."""
+    if dist is None:
+        return [float(x) for x in sums], [float(x) for x in maxes]
+    import torch
+    t = torch.tensor([float(x) for x in sums], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    m = torch.tensor([float(x) for x in maxes], dtype=torch.float64, device=dev)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()], [float(x) for x in m.tolist()]
+
+
 def cpu_baseline(g, w, max_pushes, cores=1):
     """The oracle (sequential FP64 snapshot sweeps, as it stands) on a bounded sample of the same solve."""
     import graphgen as gg
@@ -568,14 +582,7 @@ def main():
     d2h = 8 * g.n
 
     # ---- aggregate over ranks: sum of work, max of time
-    tot_edges, max_ms, tot_e2e_edges, max_e2e = edges, ms, e2e_edges, e2e_s
-    if dist is not None:
-        t = torch.tensor([edges, e2e_edges], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        tm = torch.tensor([ms, e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        tot_edges, tot_e2e_edges = float(t[0]), float(t[1])
-        max_ms, max_e2e = float(tm[0]), float(tm[1])
+    (tot_edges, tot_e2e_edges), (max_ms, max_e2e) = aggregate_ranks(dist, dev, [edges, e2e_edges], [ms, e2e_s])
 
     ppr = None
     if rank == 0 and not args.no_ppr:
