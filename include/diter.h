@@ -86,6 +86,8 @@ typedef struct {
                                 pulls along every node's in-links instead when each of the two
                                 sweeps before it diffused at least half of all out-links (the same
                                 diffusion; the in-link CSR is built at first use, 12 bytes per link) */
+    int32_t scan_wait_polls; /* polls of each bulk-copy wait of the sweep scan before the solve stops
+                                with DI_ETIMEOUT (0: 2^20; a small value makes a watchdog) */
 } di_solve_opts;
 
 /*
@@ -463,6 +465,18 @@ const char *di_last_error(void);
 
 /* Library version string. */
 const char *di_version(void);
+
+/*
+ * Self-test of the bounded waits.  Every wait of the sweep scan on a bulk copy
+ * gives up after a bounded number of polls, records the failure and returns, so
+ * that a copy that never lands stops the solve with DI_ETIMEOUT instead of
+ * hanging the GPU.  This call runs that same wait, with `polls` polls (> 0), in
+ * `ctas` CTAs (1..1024) on an mbarrier that nothing ever completes, and writes
+ * to *gave_up the number of CTAs whose wait ran out (all of them when the
+ * mechanism works).  Launched on the default stream; no device memory is left
+ * allocated.  Returns DI_EINVAL on bad arguments, DI_ECUDA on a CUDA error.
+ */
+di_status di_selftest_wait(int32_t polls, int32_t ctas, int32_t *gave_up);
 
 #ifdef __cplusplus
 }

@@ -18,12 +18,12 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (DI_EINVAL, DI_ENOMEM, DI_ENOTCONVERGED, DI_FP32_MIXED, DI_FP64, DI_OK, DiError, check,
+from ._lib import (DI_EINVAL, DI_ENOMEM, DI_ENOTCONVERGED, DI_ETIMEOUT, DI_FP32_MIXED, DI_FP64, DI_OK, DiError, check,
                    di_completion, di_profile, di_server_graph_stats, di_tune_result, di_solve_opts, di_stats, di_sweep_record, ptr)
 
-__all__ = ["DiGraph", "DiError", "DI_FP64", "DI_FP32_MIXED", "DI_OK", "DI_EINVAL", "DI_ENOTCONVERGED",
+__all__ = ["DiGraph", "DiError", "DI_FP64", "DI_FP32_MIXED", "DI_OK", "DI_EINVAL", "DI_ENOTCONVERGED", "DI_ETIMEOUT",
            "di_graph_create", "di_free", "di_solve", "di_solve_ex", "di_solve_update", "di_autotune", "di_query", "di_query_batch", "di_power", "di_power_ex", "di_graph_export",
-           "di_get_trace", "di_get_state", "di_get_profile", "di_power_noalloc", "di_version", "load",
+           "di_get_trace", "di_get_state", "di_get_profile", "di_power_noalloc", "di_version", "di_selftest_wait", "load",
            "di_plan_lanes", "di_server_create", "di_server_lanes", "di_server_submit", "di_server_poll",
            "di_server_pending", "di_server_stats", "di_server_free", "di_clock", "DiServer"]
 
@@ -34,6 +34,13 @@ def load():
 
 def di_version() -> str:
     return load().di_version().decode()
+
+
+def di_selftest_wait(polls=64, ctas=8) -> int:
+    """Run the scan's bounded wait on a barrier nothing completes; returns how many CTAs gave up."""
+    n = ctypes.c_int32(0)
+    check(load().di_selftest_wait(int(polls), int(ctas), ctypes.byref(n)))
+    return n.value
 
 
 def di_graph_create(n, row_ptr, col_idx, d, V=None, stream=None) -> int:
@@ -61,15 +68,17 @@ def di_solve(handle, tol, H_out, max_edge_pushes=0, prec=DI_FP64, normalize=0, a
     return rc, st.as_dict()
 
 
-def _opts(tol, beta, max_edge_pushes, max_sweeps, prec, normalize, trace, profile, select, direction=0):
+def _opts(tol, beta, max_edge_pushes, max_sweeps, prec, normalize, trace, profile, select, direction=0,
+          scan_wait_polls=0):
     sel = _lib.SELECT[select] if isinstance(select, str) else int(select)
     return di_solve_opts(float(tol), float(beta), int(max_edge_pushes), int(max_sweeps), int(prec), int(normalize),
-                         int(trace), int(profile), sel, int(direction))
+                         int(trace), int(profile), sel, int(direction), int(scan_wait_polls))
 
 
 def di_solve_ex(handle, H_out, tol, beta=0.5, max_edge_pushes=0, max_sweeps=0, prec=DI_FP64, normalize=0, trace=0,
-                profile=0, allow_unconverged=False, select="ref", direction=0):
-    o = _opts(tol, beta, max_edge_pushes, max_sweeps, prec, normalize, trace, profile, select, direction)
+                profile=0, allow_unconverged=False, select="ref", direction=0, scan_wait_polls=0):
+    o = _opts(tol, beta, max_edge_pushes, max_sweeps, prec, normalize, trace, profile, select, direction,
+              scan_wait_polls)
     st = di_stats()
     ok = (DI_OK, DI_ENOTCONVERGED) if allow_unconverged else (DI_OK,)
     rc = check(load().di_solve_ex(handle, ctypes.byref(o), ptr(H_out), ctypes.byref(st)), ok)
@@ -217,7 +226,7 @@ class DiGraph:
         return H, st
 
     def autotune(self, tol, prec=DI_FP64, **kw):
-        """Fastest (beta, select, push grid) for this graph and target; the push grid stays set."""
+        """Fastest (beta, select, direction, push grid) for this graph and target; the push grid stays set."""
         return di_autotune(self.handle, tol, prec, **kw)
 
     def update_from(self, old, tol, H_out=None, **kw):

@@ -43,7 +43,7 @@ class di_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("beta", ctypes.c_double), ("max_edge_pushes", ctypes.c_int64),
                 ("max_sweeps", ctypes.c_int32), ("prec", ctypes.c_int32), ("normalize", ctypes.c_int32),
                 ("trace", ctypes.c_int32), ("profile", ctypes.c_int32), ("select", ctypes.c_int32),
-                ("direction", ctypes.c_int32)]
+                ("direction", ctypes.c_int32), ("scan_wait_polls", ctypes.c_int32)]
 
 
 class di_sweep_record(ctypes.Structure):
@@ -128,6 +128,7 @@ def load(path: str = LIB_PATH):
         "di_clock": ([], f64),
         "di_last_error": ([], ctypes.c_char_p),
         "di_version": ([], ctypes.c_char_p),
+        "di_selftest_wait": ([i32, i32, ctypes.POINTER(i32)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

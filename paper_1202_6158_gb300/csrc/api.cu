@@ -119,6 +119,15 @@ const char *di_last_error(void) { return g_last_error.c_str(); }
 
 const char *di_version(void) { return "libditer 0.1 (D-iteration, sm_103a)"; }
 
+di_status di_selftest_wait(int32_t polls, int32_t ctas, int32_t *gave_up) {
+    g_last_error.clear();
+    if (!gave_up) return set_error(DI_EINVAL, "gave_up is NULL");
+    if (polls < 1 || polls > (1 << 24)) return set_error(DI_EINVAL, "polls must be in [1, 2^24]");
+    if (ctas < 1 || ctas > 1024) return set_error(DI_EINVAL, "ctas must be in [1, 1024]");
+    *gave_up = 0;
+    return selftest_wait(polls, ctas, gave_up);
+}
+
 di_status di_graph_create(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, int64_t nnz, double d,
                           const double *V, void *stream, di_graph **out) {
     g_last_error.clear();
@@ -271,6 +280,8 @@ di_status di_solve_ex(di_graph *g, const di_solve_opts *opts, double *H_out, di_
     if (!(o.beta >= 0.0) || !std::isfinite(o.beta)) return set_error(DI_EINVAL, "beta must be finite and >= 0");
     if (o.prec != DI_FP64 && o.prec != DI_FP32_MIXED) return set_error(DI_EINVAL, "prec must be DI_FP64 or DI_FP32_MIXED");
     if (o.select < DI_SELECT_REF || o.select > DI_SELECT_OP2) return set_error(DI_EINVAL, "select must be 0, 1 or 2");
+    if (o.direction != 0 && o.direction != 1) return set_error(DI_EINVAL, "direction must be 0 or 1");
+    if (o.scan_wait_polls < 0) return set_error(DI_EINVAL, "scan_wait_polls must be >= 0");
     return run_solve(g, o, nullptr, nullptr, 0, 1.0, H_out, is_device_ptr(H_out), st);
 }
 
@@ -283,6 +294,8 @@ di_status di_solve_update(di_graph *g_old, di_graph *g_new, const di_solve_opts 
     if (!(o.beta >= 0.0) || !std::isfinite(o.beta)) return set_error(DI_EINVAL, "beta must be finite and >= 0");
     if (o.prec != DI_FP64) return set_error(DI_EINVAL, "a graph update continues an FP64 state: prec must be DI_FP64");
     if (o.select < DI_SELECT_REF || o.select > DI_SELECT_OP2) return set_error(DI_EINVAL, "select must be 0, 1 or 2");
+    if (o.direction != 0 && o.direction != 1) return set_error(DI_EINVAL, "direction must be 0 or 1");
+    if (o.scan_wait_polls < 0) return set_error(DI_EINVAL, "scan_wait_polls must be >= 0");
     if (g_old->n != g_new->n) return set_error(DI_EINVAL, "the updated graph must have the same nodes");
     if (g_old->d != g_new->d) return set_error(DI_EINVAL, "the updated graph must have the same d");
     if (g_old->last_prec != DI_FP64 || !g_old->F64)

@@ -93,7 +93,7 @@ struct SolveState {
     double wscale;         // weighted selection: the threshold of F*w is T * wscale
     long long pull_edges;  // a sweep that diffused at least this many out-links is dense
     int dense;             // the last sweep was dense: a second dense sweep makes the next one pull
-    int pad2;
+    int wait_polls;        // polls of each bulk-copy wait of the scan before the solve gives up
 };
 
 // batched personalized queries: up to kLanes queries interleaved in one fluid row
@@ -279,6 +279,7 @@ di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_de
 di_status build_in_dst(di_graph *g);  // the transpose, then in_dst
 di_status in_degree_classes(di_graph *g, int *out_dev);
 di_status ensure_rowhash(di_graph *g);  // fingerprints of the input rows (graph updates)
+di_status selftest_wait(int polls, int ctas, int *gave_up);
 di_status build_transpose(di_graph *g);   // the in-link CSR and its bins, at first use
 di_status validate_v(di_graph *g, const double *V_dev);
 

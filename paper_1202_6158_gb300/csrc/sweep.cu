@@ -83,7 +83,8 @@ __global__ void k_init_seeds(int nseeds, const int *__restrict__ seeds, const do
 
 __device__ void init_control(SolveState *st, double R0, double tolR, double beta, double one_minus_d, int n,
                              long long max_edges, int max_sweeps, int trace_on, double wscale, int weighted,
-                             long long pull_edges) {
+                             long long pull_edges, int wait_polls) {
+    st->wait_polls = wait_polls;
     st->pull = 0;  // the first two sweeps push
     st->dense = 0;
     st->pull_edges = pull_edges;
@@ -108,19 +109,21 @@ __device__ void init_control(SolveState *st, double R0, double tolR, double beta
 
 __global__ void k_init_control(SolveState *st, double R0, double tolR, double beta, double one_minus_d, int n,
                                long long max_edges, int max_sweeps, int trace_on, double wscale, int weighted,
-                               long long pull_edges) {
-    init_control(st, R0, tolR, beta, one_minus_d, n, max_edges, max_sweeps, trace_on, wscale, weighted, pull_edges);
+                               long long pull_edges, int wait_polls) {
+    init_control(st, R0, tolR, beta, one_minus_d, n, max_edges, max_sweeps, trace_on, wscale, weighted, pull_edges,
+                 wait_polls);
 }
 
 // the same with R_0 = |F_0|_1 summed (fixed order) from the per-CTA partials of k_l1_partials:
 // a continued or updated state starts from whatever fluid it holds
 __global__ void k_init_control_l1(SolveState *st, const ScanPartial *__restrict__ part, int G, double tolR,
                                   double beta, double one_minus_d, int n, long long max_edges, int max_sweeps,
-                                  int trace_on, double wscale, int weighted, long long pull_edges) {
+                                  int trace_on, double wscale, int weighted, long long pull_edges, int wait_polls) {
     if (threadIdx.x != 0) return;
     double R0 = 0.0;
     for (int c = 0; c < G; ++c) R0 += part[c].l1d;
-    init_control(st, R0, tolR, beta, one_minus_d, n, max_edges, max_sweeps, trace_on, wscale, weighted, pull_edges);
+    init_control(st, R0, tolR, beta, one_minus_d, n, max_edges, max_sweeps, trace_on, wscale, weighted, pull_edges,
+                 wait_polls);
 }
 
 // ------------------------------------------------------------------- scan
@@ -262,6 +265,7 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
     const bool exact = (st->sweeps % kExactEvery) == 0;  // the exact |F|_1 of this sweep's start
     // a pull sweep writes sent * d/outdeg of every node (0 if not selected) instead of the lists
     const bool pull = st->pull != 0;
+    const int wlim = st->wait_polls;  // the copies still in flight after a timeout are awaited with the full limit
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const int g = blockIdx.x * kWarps + w;
@@ -299,7 +303,7 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
     bool ok = true;
     for (; s < nsteps; ++s) {
         const int slot = s % Ring::kStages;
-        ok = __all_sync(kFull, mbar_wait(bar0 + 8u * slot, (unsigned)((s / Ring::kStages) & 1), kScanWaitLimit));
+        ok = __all_sync(kFull, mbar_wait(bar0 + 8u * slot, (unsigned)((s / Ring::kStages) & 1), wlim));
         if (!ok) break;
         const unsigned char *stg = ring + slot * Ring::kBytes;
         const FT *stg_f = reinterpret_cast<const FT *>(stg);
@@ -450,6 +454,19 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
         prefix_counts_staged(fcount, W, pre, reinterpret_cast<int *>(s_ring), (int)(sizeof(s_ring) / sizeof(int)), 1);
         if (threadIdx.x == 0) *ticket = 0u;
     }
+}
+
+// the bounded wait of the scan on a barrier that nothing completes: every CTA must give up
+__global__ void k_selftest_wait(int polls, int *__restrict__ gave_up) {
+    __shared__ __align__(8) unsigned long long bar;
+    const unsigned b = smem_addr(&bar);
+    if (threadIdx.x == 0) {
+        mbar_init(b, 1);  // one arrival completes phase 0; none ever comes
+        fence_barrier_init();
+    }
+    __syncthreads();
+    const bool ok = __all_sync(kFull, mbar_wait(b, 0u, polls));
+    if (threadIdx.x == 0 && !ok) atomicAdd(gave_up, 1);
 }
 
 // --------------------------------------------------------------- finalize
@@ -696,13 +713,14 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, InitK
     // a sweep that diffused at least half of all out-links is dense
     const long long pull_edges = o.direction ? std::max(1LL, (g->nnz + kPullShareSolve - 1) / kPullShareSolve)
                                              : std::numeric_limits<long long>::max();
+    const int wait_polls = o.scan_wait_polls > 0 ? o.scan_wait_polls : kScanWaitLimit;
     if (init == kInitState) {
         k_l1_partials<FT><<<g->G, kScanThreads, 0, s>>>(n, g->chunk, F, g->part);
         k_init_control_l1<<<1, 32, 0, s>>>(g->st, g->part, g->G, o.tol * omd, beta, omd, n, o.max_edge_pushes,
-                                           max_sweeps, o.trace ? 1 : 0, wscale, o.select ? 1 : 0, pull_edges);
+                                           max_sweeps, o.trace ? 1 : 0, wscale, o.select ? 1 : 0, pull_edges, wait_polls);
     } else {
         k_init_control<<<1, 1, 0, s>>>(g->st, omd, o.tol * omd, beta, omd, n, o.max_edge_pushes, max_sweeps,
-                                       o.trace ? 1 : 0, wscale, o.select ? 1 : 0, pull_edges);
+                                       o.trace ? 1 : 0, wscale, o.select ? 1 : 0, pull_edges, wait_polls);
     }
     DI_CUDA(cudaGetLastError());
     int attempts = 0;
@@ -942,6 +960,20 @@ __global__ void k_inject_long(InjectArgs a) {
 }
 
 }  // namespace
+
+di_status selftest_wait(int polls, int ctas, int *gave_up) {
+    int *d = nullptr;
+    DI_CUDA(cudaMalloc(&d, sizeof(int)));
+    cudaError_t e = cudaMemset(d, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        k_selftest_wait<<<ctas, 32>>>(polls, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(gave_up, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "di_selftest_wait");
+    return DI_OK;
+}
 
 di_status run_solve(di_graph *g, const di_solve_opts &o, const int *seeds, const double *seed_w, int nseeds,
                     double wsum, double *H_out, bool out_dev, di_stats *st) {

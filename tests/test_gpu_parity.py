@@ -344,3 +344,35 @@ def test_power_and_diter_agree(di):
         X, stp = g.power(1e-11)
         H, std = g.solve(1e-11)
     assert np.abs(X - H).sum() <= 2e-11
+
+
+def test_bounded_wait_gives_up(di):
+    """The scan's bounded wait, on an mbarrier that nothing completes, gives up in every CTA
+    and returns; the context stays usable."""
+    assert di.di_selftest_wait(64, 8) == 8
+    with pytest.raises(di.DiError):
+        di.di_selftest_wait(0, 8)
+    n, rp, ci = CASES["uniform_1e4"]
+    H, F, st, _ = _solve(di, n, rp, ci, 1e-10)
+    assert st["converged"] == 1
+
+
+def test_scan_wait_watchdog_keeps_results_valid(di):
+    """With one poll per bulk-copy wait (a watchdog far shorter than a DRAM load) every solve
+    either converges to the oracle's answer or stops with DI_ETIMEOUT; a wait that ran out
+    leaves the graph and the context usable."""
+    g = gg.uniform_graph(1 << 18, 20, seed=5)
+    V = gg.uniform_v(g.n)
+    r = oracle.diter(g.n, g.row_ptr, g.col_idx, D, V, 1e-10, mode="sweep", beta=BETA)
+    with di.DiGraph(g.n, g.row_ptr, g.col_idx, D) as G:
+        for _ in range(3):
+            try:
+                H, st = G.solve(1e-10, beta=BETA, scan_wait_polls=1)
+                assert np.abs(H - r.H).sum() <= max(st["bound"], r.l1F / (1 - D)) + 1e-12
+            except di.DiError as e:
+                assert e.status == di.DI_ETIMEOUT
+        with pytest.raises(di.DiError):
+            G.solve(1e-8, beta=BETA, scan_wait_polls=-1)
+        H, st = G.solve(1e-10, beta=BETA)
+    assert st["converged"] == 1
+    assert np.abs(H - r.H).sum() <= max(st["bound"], r.l1F / (1 - D)) + 1e-12
