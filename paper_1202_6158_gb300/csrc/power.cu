@@ -7,7 +7,8 @@
 // with z of the current iterate kept in one of two buffers so the gather never
 // sees a value of the product being formed.  Three kernels per product:
 //   k_pgather     the in-links, in target order, cut into even ranges: each lane takes
-//                 kPowRun consecutive links, gathers z of their sources, sums them
+//                 kPowRun (32) consecutive links, gathers z of their sources (32 random
+//                 8-byte loads in flight per lane hide the DRAM latency), sums them
 //                 serially per target (one FP64 add per link) and adds each target's sum
 //                 to the accumulator Y with one red.add;
 //   k_pepilogue   streams the nodes: |y - x|, x = y, z = d*y/outdeg, Y = (1-d)V for the
@@ -25,7 +26,7 @@
 namespace diter {
 namespace {
 
-constexpr int kPowRun = 8;  // consecutive in-links per lane and step of the gather
+constexpr int kPowRun = 32;  // consecutive in-links per lane and step of the gather (gathers in flight)
 
 __device__ double block_sum_d(double v, double *sh) {
 #pragma unroll
@@ -54,7 +55,7 @@ struct PullArgs {
 // (1-d) V_j
 __device__ __forceinline__ double omdv_of(const PullArgs &a, int j) { return a.V ? a.omd * a.V[j] : a.omdu; }
 
-__global__ void __launch_bounds__(256, 4) k_pgather(PullArgs a) {
+__global__ void __launch_bounds__(256, 2) k_pgather(PullArgs a) {
     if (a.pst->done) return;
     const double *__restrict__ zc = a.pst->cur ? a.Z1 : a.Z0;
     constexpr int kStepLinks = 32 * kPowRun;
@@ -179,7 +180,7 @@ PullArgs make_args(di_graph *g) {
     return a;
 }
 
-int gather_grid(const di_graph *g) { return g->num_sms * 4; }
+int gather_grid(const di_graph *g) { return g->num_sms * 2; }  // one wave at 2 CTAs per SM
 int epilogue_grid(const di_graph *g) { return std::max(1, std::min(g->num_sms * 8, (g->n + 255) / 256)); }
 
 void launch_product(di_graph *g, const PullArgs &a, cudaStream_t s) {

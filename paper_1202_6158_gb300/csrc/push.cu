@@ -202,10 +202,10 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
 //    target, one add per link, then adds each target's sum with one red.add.
 // Either way a target with many in-links gets a reduction per 32 or kPullRun links where
 // the push makes one per link.
-constexpr int kPullRun = 8;
+constexpr int kPullRun = 16;
 
 template <typename FT>
-__global__ void __launch_bounds__(kScanThreads, 4) k_sweep_pull(const int *__restrict__ in_src,
+__global__ void __launch_bounds__(kScanThreads, 3) k_sweep_pull(const int *__restrict__ in_src,
                                                              const int *__restrict__ in_dst,
                                                              const FT *__restrict__ w, long long nnz,
                                                              FT *__restrict__ F, const SolveState *__restrict__ st) {
@@ -298,8 +298,9 @@ template void launch_push<float>(di_graph *, float *, cudaStream_t);
 
 template <typename FT>
 void launch_pull(di_graph *g, FT *F, cudaStream_t s) {
-    k_sweep_pull<FT><<<push_grid(g), kScanThreads, 0, s>>>(g->in_src, g->in_dst, static_cast<const FT *>(g->wpull),
-                                                           g->nnz, F, g->st);
+    // one wave at 3 CTAs per SM (16 gathers in flight per lane in FP64)
+    k_sweep_pull<FT><<<g->num_sms * 3, kScanThreads, 0, s>>>(g->in_src, g->in_dst, static_cast<const FT *>(g->wpull),
+                                                             g->nnz, F, g->st);
 }
 
 template void launch_pull<double>(di_graph *, double *, cudaStream_t);
