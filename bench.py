@@ -30,6 +30,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -86,7 +87,7 @@ class ClockSampler:
 
     def __init__(self, gpu_index=0):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"diter_clocks_{os.getpid()}.csv")
         self.gpu = gpu_index
 
     def __enter__(self):
