@@ -162,6 +162,24 @@ def test_against_gaussian_elimination(di, seed):
     assert np.all(H <= X + 1e-15)
 
 
+@pytest.mark.parametrize("d", [0.01, 0.5, 0.99])
+def test_damping_extremes_against_elimination(di, d):
+    """d near 0 (almost no diffusion: H is close to (1-d)V after a sweep or two) and d near 1
+    (about ln(1e-12)/ln(d) sweeps): |X - H|_1 <= bound and 0 <= H <= X against dense
+    elimination, for both sweep directions."""
+    rng = np.random.default_rng(77)
+    n = 300
+    rp, ci = graphs.random_graph(n, 0.1, 12, rng)
+    V = graphs.random_v(n, rng)
+    X = ge.pagerank_dense(n, rp, ci, d, V)
+    for direction in (0, 1):
+        with di.DiGraph(n, rp, ci, d, V=V) as g:
+            H, st = g.solve(1e-12, beta=BETA, direction=direction)
+        assert st["converged"] == 1
+        assert np.abs(X - H).sum() <= st["bound"] + 1e-14
+        assert np.all(H >= 0) and np.all(H <= X + 1e-15)
+
+
 @pytest.mark.parametrize("n", [1, 2, 3, 1023, 1024, 1025, 4097, 70001])
 def test_ragged_sizes(di, n):
     rng = np.random.default_rng(n)
