@@ -85,7 +85,11 @@ typedef struct {
     int32_t direction;       /* 0: every sweep pushes along the selected nodes' out-links; 1: a sweep
                                 pulls along every node's in-links instead when each of the two
                                 sweeps before it diffused at least half of all out-links (the same
-                                diffusion; the in-link CSR is built at first use, 12 bytes per link) */
+                                diffusion; the in-link CSR, 12 bytes per link, is built before the
+                                first such solve); 2: the same, but the in-link CSR is built only
+                                when the first pull is due (the loop pauses for it and resumes
+                                where it stopped), so graphs whose sweeps never turn dense pay
+                                nothing */
     int32_t scan_wait_polls; /* polls of each bulk-copy wait of the sweep scan before the solve stops
                                 with DI_ETIMEOUT (0: 2^20; a small value makes a watchdog) */
 } di_solve_opts;

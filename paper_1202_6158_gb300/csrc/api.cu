@@ -280,7 +280,7 @@ di_status di_solve_ex(di_graph *g, const di_solve_opts *opts, double *H_out, di_
     if (!(o.beta >= 0.0) || !std::isfinite(o.beta)) return set_error(DI_EINVAL, "beta must be finite and >= 0");
     if (o.prec != DI_FP64 && o.prec != DI_FP32_MIXED) return set_error(DI_EINVAL, "prec must be DI_FP64 or DI_FP32_MIXED");
     if (o.select < DI_SELECT_REF || o.select > DI_SELECT_OP2) return set_error(DI_EINVAL, "select must be 0, 1 or 2");
-    if (o.direction != 0 && o.direction != 1) return set_error(DI_EINVAL, "direction must be 0 or 1");
+    if (o.direction < 0 || o.direction > 2) return set_error(DI_EINVAL, "direction must be 0, 1 or 2");
     if (o.scan_wait_polls < 0) return set_error(DI_EINVAL, "scan_wait_polls must be >= 0");
     return run_solve(g, o, nullptr, nullptr, 0, 1.0, H_out, is_device_ptr(H_out), st);
 }
@@ -294,7 +294,7 @@ di_status di_solve_update(di_graph *g_old, di_graph *g_new, const di_solve_opts 
     if (!(o.beta >= 0.0) || !std::isfinite(o.beta)) return set_error(DI_EINVAL, "beta must be finite and >= 0");
     if (o.prec != DI_FP64) return set_error(DI_EINVAL, "a graph update continues an FP64 state: prec must be DI_FP64");
     if (o.select < DI_SELECT_REF || o.select > DI_SELECT_OP2) return set_error(DI_EINVAL, "select must be 0, 1 or 2");
-    if (o.direction != 0 && o.direction != 1) return set_error(DI_EINVAL, "direction must be 0 or 1");
+    if (o.direction < 0 || o.direction > 2) return set_error(DI_EINVAL, "direction must be 0, 1 or 2");
     if (o.scan_wait_polls < 0) return set_error(DI_EINVAL, "scan_wait_polls must be >= 0");
     if (g_old->n != g_new->n) return set_error(DI_EINVAL, "the updated graph must have the same nodes");
     if (g_old->d != g_new->d) return set_error(DI_EINVAL, "the updated graph must have the same d");

@@ -94,6 +94,8 @@ struct SolveState {
     long long pull_edges;  // a sweep that diffused at least this many out-links is dense
     int dense;             // the last sweep was dense: a second dense sweep makes the next one pull
     int wait_polls;        // polls of each bulk-copy wait of the scan before the solve gives up
+    int pause_pull;        // the in-link CSR is not built yet: a due pull stops the loop (done = 5) instead
+    int pad3;
 };
 
 // batched personalized queries: up to kLanes queries interleaved in one fluid row

@@ -46,6 +46,8 @@
 namespace diter {
 namespace {
 
+di_status ensure_pull(di_graph *g);  // the pull direction's inputs, built at first use (below)
+
 // ------------------------------------------------------------------- init
 
 template <typename FT>
@@ -83,8 +85,9 @@ __global__ void k_init_seeds(int nseeds, const int *__restrict__ seeds, const do
 
 __device__ void init_control(SolveState *st, double R0, double tolR, double beta, double one_minus_d, int n,
                              long long max_edges, int max_sweeps, int trace_on, double wscale, int weighted,
-                             long long pull_edges, int wait_polls) {
+                             long long pull_edges, int wait_polls, int pause_pull) {
     st->wait_polls = wait_polls;
+    st->pause_pull = pause_pull;
     st->pull = 0;  // the first two sweeps push
     st->dense = 0;
     st->pull_edges = pull_edges;
@@ -109,21 +112,28 @@ __device__ void init_control(SolveState *st, double R0, double tolR, double beta
 
 __global__ void k_init_control(SolveState *st, double R0, double tolR, double beta, double one_minus_d, int n,
                                long long max_edges, int max_sweeps, int trace_on, double wscale, int weighted,
-                               long long pull_edges, int wait_polls) {
+                               long long pull_edges, int wait_polls, int pause_pull) {
     init_control(st, R0, tolR, beta, one_minus_d, n, max_edges, max_sweeps, trace_on, wscale, weighted, pull_edges,
-                 wait_polls);
+                 wait_polls, pause_pull);
 }
 
 // the same with R_0 = |F_0|_1 summed (fixed order) from the per-CTA partials of k_l1_partials:
 // a continued or updated state starts from whatever fluid it holds
 __global__ void k_init_control_l1(SolveState *st, const ScanPartial *__restrict__ part, int G, double tolR,
                                   double beta, double one_minus_d, int n, long long max_edges, int max_sweeps,
-                                  int trace_on, double wscale, int weighted, long long pull_edges, int wait_polls) {
+                                  int trace_on, double wscale, int weighted, long long pull_edges, int wait_polls,
+                                  int pause_pull) {
     if (threadIdx.x != 0) return;
     double R0 = 0.0;
     for (int c = 0; c < G; ++c) R0 += part[c].l1d;
     init_control(st, R0, tolR, beta, one_minus_d, n, max_edges, max_sweeps, trace_on, wscale, weighted, pull_edges,
-                 wait_polls);
+                 wait_polls, pause_pull);
+}
+
+// a loop paused for the in-link CSR resumes where it stopped, its next sweep pulling
+__global__ void k_resume_pull(SolveState *st) {
+    if (st->done == 5) st->done = 0;
+    st->pause_pull = 0;
 }
 
 // ------------------------------------------------------------------- scan
@@ -547,6 +557,7 @@ __global__ void k_sweep_finalize(int n, int G, const ScanPartial *__restrict__ p
     else if (!isfinite(R)) done = 3;
     else if (R <= st->tolR) done = 1;
     else if (st->sweeps >= st->max_sweeps || (st->max_edges > 0 && st->edges >= st->max_edges)) done = 2;
+    else if (st->pull && st->pause_pull) done = 5;  // a pull is due but the in-link CSR is not built: ask the host
     st->done = done;
     if (done && in_graph) cudaGraphSetConditional(handle, 0);
 }
@@ -695,6 +706,11 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, InitK
     const double omd = 1.0 - g->d;
     const float *wsel = o.select ? g->wsel[o.select - 1] : nullptr;
     const double wscale = o.select ? g->wscale[o.select - 1] : 1.0;
+    // `slot` is the push-only loop; the loop with the pull kernel sits kSweepSlots/2 further on.
+    // direction 2 before the in-link CSR exists runs push-only and pauses when a pull is due.
+    bool pulls = o.direction == 1 || (o.direction == 2 && g->wpull != nullptr);
+    const int pause_pull = o.direction == 2 && !pulls ? 1 : 0;
+    if (pulls) slot += kSweepSlots / 2;
     if (!g->exec[slot]) {
         di_status r = build_sweep_graph<FT>(g, slot, F, wsel);
         if (r != DI_OK) return r;
@@ -717,16 +733,33 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, InitK
     if (init == kInitState) {
         k_l1_partials<FT><<<g->G, kScanThreads, 0, s>>>(n, g->chunk, F, g->part);
         k_init_control_l1<<<1, 32, 0, s>>>(g->st, g->part, g->G, o.tol * omd, beta, omd, n, o.max_edge_pushes,
-                                           max_sweeps, o.trace ? 1 : 0, wscale, o.select ? 1 : 0, pull_edges, wait_polls);
+                                           max_sweeps, o.trace ? 1 : 0, wscale, o.select ? 1 : 0, pull_edges, wait_polls,
+                                           pause_pull);
     } else {
         k_init_control<<<1, 1, 0, s>>>(g->st, omd, o.tol * omd, beta, omd, n, o.max_edge_pushes, max_sweeps,
-                                       o.trace ? 1 : 0, wscale, o.select ? 1 : 0, pull_edges, wait_polls);
+                                       o.trace ? 1 : 0, wscale, o.select ? 1 : 0, pull_edges, wait_polls, pause_pull);
     }
     DI_CUDA(cudaGetLastError());
     int attempts = 0;
     g->prof = di_profile{};
+    g->h_st->done = 0;  // the host copy of the previous solve's stop code is not this solve's
     for (int attempt = 0; attempt < 8; ++attempt) {
         ++attempts;
+        if (g->h_st->done == 5) {
+            // the loop paused for the in-link CSR: build it and the loop with the pull kernel,
+            // then resume from the same state (this pause is not a confirmation attempt)
+            di_status r = ensure_pull(g);
+            if (r != DI_OK) return r;
+            pulls = true;
+            slot += kSweepSlots / 2;
+            if (!g->exec[slot]) {
+                r = build_sweep_graph<FT>(g, slot, F, wsel);
+                if (r != DI_OK) return r;
+            }
+            k_resume_pull<<<1, 1, 0, s>>>(g->st);
+            DI_CUDA(cudaGetLastError());
+            --attempt;
+        }
         if (o.profile) {
             // same kernels and arguments as the graph body, launched from the host with events around each
             cudaGraphConditionalHandle none = 0;
@@ -735,7 +768,7 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, InitK
                 launch_scan<FT>(g, F, wsel, s);
                 DI_CUDA(cudaEventRecord(g->pev[1], s));
                 launch_push<FT>(g, F, s);
-                if (o.direction) launch_pull<FT>(g, F, s);
+                if (pulls) launch_pull<FT>(g, F, s);
                 DI_CUDA(cudaEventRecord(g->pev[2], s));
                 k_sweep_finalize<<<1, 256, 0, s>>>(n, g->G, g->part, g->st, g->trace, none, 0);
                 DI_CUDA(cudaEventRecord(g->pev[3], s));
@@ -764,7 +797,7 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, InitK
         DI_CUDA(cudaGetLastError());
         DI_CUDA(cudaMemcpyAsync(g->h_st, g->st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
         DI_CUDA(cudaStreamSynchronize(s));
-        if (g->h_st->done != 0) break;
+        if (g->h_st->done != 0 && g->h_st->done != 5) break;
     }
     DI_CUDA(cudaEventRecord(g->ev1, s));
     // outputs, in the caller's numbering
@@ -865,7 +898,7 @@ __global__ void k_sel_weights(int n, int npad, int select, const int *__restrict
 }
 
 // the pull direction's inputs: the in-links with their targets, and the per-node pushed values
-static di_status ensure_pull(di_graph *g) {
+di_status ensure_pull(di_graph *g) {
     if (g->wpull) return DI_OK;
     di_status r = build_in_dst(g);
     if (r != DI_OK) return r;
@@ -983,12 +1016,12 @@ di_status run_solve(di_graph *g, const di_solve_opts &o, const int *seeds, const
     if (r != DI_OK) return r;
     g->last_prec = o.prec;
     g->last_trace_on = o.trace ? 1 : 0;
-    if (o.direction) {
+    if (o.direction == 1) {
         r = ensure_pull(g);
         if (r != DI_OK) return r;
     }
     const InitKind init = seeds ? kInitSeeds : kInitV;
-    const int slot = (o.select ? 3 + 2 * (o.select - 1) + o.prec : o.prec) + (o.direction ? kSweepSlots / 2 : 0);
+    const int slot = o.select ? 3 + 2 * (o.select - 1) + o.prec : o.prec;  // the push-only loop
     if (o.prec == DI_FP64)
         return solve_impl<double>(g, o, g->F64, slot, init, seeds, seed_w, nseeds, wsum, H_out, out_dev, st);
     return solve_impl<float>(g, o, g->F32, slot, init, seeds, seed_w, nseeds, wsum, H_out, out_dev, st);
@@ -999,14 +1032,16 @@ di_status run_update(di_graph *go, di_graph *gn, const di_solve_opts &o, double 
     if (r != DI_OK) return r;
     r = ensure_weights(gn, o.select);
     if (r != DI_OK) return r;
-    if (o.direction) {
+    if (o.direction == 1) {
         r = ensure_pull(gn);
         if (r != DI_OK) return r;
     }
     const int n = gn->n;
-    const int slot = (o.select ? 3 + 2 * (o.select - 1) : 0) + (o.direction ? kSweepSlots / 2 : 0);
-    if (!gn->exec[slot]) {  // capture before timing starts, as a solve does
-        r = build_sweep_graph<double>(gn, slot, gn->F64, o.select ? gn->wsel[o.select - 1] : nullptr);
+    const int slot = o.select ? 3 + 2 * (o.select - 1) : 0;  // the push-only loop
+    const bool pulls = o.direction == 1 || (o.direction == 2 && gn->wpull != nullptr);
+    const int cslot = slot + (pulls ? kSweepSlots / 2 : 0);
+    if (!gn->exec[cslot]) {  // capture before timing starts, as a solve does
+        r = build_sweep_graph<double>(gn, cslot, gn->F64, o.select ? gn->wsel[o.select - 1] : nullptr);
         if (r != DI_OK) return r;
     }
     if (go != gn) {  // the row fingerprints that find the changed rows, at the first update

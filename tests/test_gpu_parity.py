@@ -118,11 +118,12 @@ def _solve(di, n, rp, ci, tol, V=None, **kw):
     return H, F, st, tr
 
 
-@pytest.mark.parametrize("direction", [0, 1])
+@pytest.mark.parametrize("direction", [0, 1, 2])
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_fp64_tight_parity_with_oracle_sweeps(di, name, direction):
     """Both to bound <= 1e-13: |H_gpu - H_oracle|_1 <= 1e-12, same sweeps and elementary steps.
-    direction=1 pulls along the in-links on dense sweeps: the same diffusion of the same sets."""
+    direction=1 pulls along the in-links on dense sweeps: the same diffusion of the same sets;
+    direction=2 does the same after pausing the loop to build the in-link CSR."""
     n, rp, ci = CASES[name]
     V = gg.uniform_v(n)
     tol = 1e-13
@@ -210,7 +211,7 @@ def test_theorem1_on_device_state(di, direction):
         assert np.abs(F - r.F).sum() <= 1e-13
 
 
-@pytest.mark.parametrize("direction", [0, 1])
+@pytest.mark.parametrize("direction", [0, 1, 2])
 def test_trace_records(di, direction):
     n, rp, ci = CASES["rmat_12"]
     H, F, st, tr = _solve(di, n, rp, ci, 1e-10, trace=1, direction=direction)
