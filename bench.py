@@ -229,12 +229,16 @@ def bench_ppr(di, torch, dev, nbatches=3):
         G.query(seeds[q], 1e-6, H_out=h1)
     torch.cuda.synchronize()
     single = time.perf_counter() - t0
+    # one more batch with the sweep kernels launched from the host between events: the split of device
+    # time over scan, push-or-pull and finalize (the captured loop above runs the same kernels)
+    _, _, stp = G.query_batch(seeds, 1e-6, H_out=H, profile=1)
     G.close()
     med = float(np.median(lat))
     return {"workload": "R-MAT scale 20 (n=%d, L=%d), 64 queries x 1-32 seeds, d=0.85, per-query bound 1e-6" % (g.n, g.nnz),
             "batched_queries_per_s": 64 / med, "batch_ms": 1e3 * med, "sweeps": sta["sweeps"],
             "max_bound": max(s["bound"] for s in stq), "single_fp64_queries_per_s": 64 / single,
-            "speedup": (64 / med) / (64 / single), "lane_dtype": "f32 fluid rows, f64 histories"}
+            "speedup": (64 / med) / (64 / single), "lane_dtype": "f32 fluid rows, f64 histories",
+            "kernel_ms": {k: round(v, 3) if isinstance(v, float) else v for k, v in stp["profile"].items()}}
 
 
 def bench_update(di, torch, G, g, d, tol, fracs=(1e-4, 1e-3, 1e-2)):

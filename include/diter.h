@@ -131,7 +131,7 @@ typedef struct {
     double push_ms;        /* summed CUDA-event time of the push kernel */
     double finalize_ms;    /* summed CUDA-event time of the finalize kernel */
     int32_t sweeps;        /* launches of each of the three kernels */
-    int32_t pad;
+    int32_t pull_sweeps;   /* of those, the sweeps that pulled (push_ms then holds the pull kernel) */
 } di_profile;
 
 /* ------------------------------------------------------------------ graphs */
@@ -287,6 +287,18 @@ di_status di_query(di_graph *g, const int32_t *seeds, const double *w, int32_t n
  */
 di_status di_query_batch(di_graph *g, int32_t k, const int32_t *seed_ptr, const int32_t *seeds, const double *w,
                          double tol, double *H_out, di_stats *st_q, di_stats *st_all);
+
+/*
+ * di_query_batch with a profiling switch.  profile = 1 launches each sweep's
+ * kernels (scan, push, pull, finalize) from the host with CUDA events around
+ * them, instead of the captured loop (the same kernels and arguments), and
+ * fills *prof (host): scan_ms, push_ms (the push and pull kernels of each
+ * sweep together), finalize_ms, sweeps, pull_sweeps.  profile = 0 is
+ * di_query_batch; prof may then be NULL.
+ */
+di_status di_query_batch_ex(di_graph *g, int32_t k, const int32_t *seed_ptr, const int32_t *seeds, const double *w,
+                            double tol, int32_t profile, double *H_out, di_stats *st_q, di_stats *st_all,
+                            di_profile *prof);
 
 /*
  * Power iteration on the uncompleted P (MAT-ITER, Section 4): X_0 = 0,

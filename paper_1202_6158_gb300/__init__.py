@@ -22,7 +22,7 @@ from ._lib import (DI_EINVAL, DI_ENOMEM, DI_ENOTCONVERGED, DI_ETIMEOUT, DI_FP32_
                    di_completion, di_profile, di_server_graph_stats, di_tune_result, di_solve_opts, di_stats, di_sweep_record, ptr)
 
 __all__ = ["DiGraph", "DiError", "DI_FP64", "DI_FP32_MIXED", "DI_OK", "DI_EINVAL", "DI_ENOTCONVERGED", "DI_ETIMEOUT",
-           "di_graph_create", "di_free", "di_solve", "di_solve_ex", "di_solve_update", "di_autotune", "di_query", "di_query_batch", "di_power", "di_power_ex", "di_graph_export",
+           "di_graph_create", "di_free", "di_solve", "di_solve_ex", "di_solve_update", "di_autotune", "di_query", "di_query_batch", "di_query_batch_ex", "di_power", "di_power_ex", "di_graph_export",
            "di_get_trace", "di_get_state", "di_get_profile", "di_power_noalloc", "di_version", "di_selftest_wait", "load",
            "di_plan_lanes", "di_server_create", "di_server_lanes", "di_server_submit", "di_server_poll",
            "di_server_pending", "di_server_stats", "di_server_free", "di_clock", "DiServer"]
@@ -118,6 +118,14 @@ def di_query_batch(handle, seed_lists, tol, H_out, weights=None):
 
     Returns (per-query stats list, batch stats).  H_out is double[k][n] (host or device).
     """
+    st_q, st_all, _ = di_query_batch_ex(handle, seed_lists, tol, H_out, weights, profile=0)
+    return st_q, st_all
+
+
+def di_query_batch_ex(handle, seed_lists, tol, H_out, weights=None, profile=0):
+    """di_query_batch with the profiling switch: profile=1 launches the sweep kernels from the
+    host with events around them.  Returns (per-query stats, batch stats, profile dict or None).
+    """
     k = len(seed_lists)
     seed_ptr = np.zeros(k + 1, np.int32)
     seed_ptr[1:] = np.cumsum([len(s) for s in seed_lists])
@@ -128,9 +136,10 @@ def di_query_batch(handle, seed_lists, tol, H_out, weights=None):
         w = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float64) for x in weights]), dtype=np.float64)
     st_q = (di_stats * max(k, 1))()
     st_all = di_stats()
-    check(load().di_query_batch(handle, k, ptr(seed_ptr), ptr(seeds), ptr(w), float(tol), ptr(H_out), st_q,
-                                ctypes.byref(st_all)))
-    return [st_q[i].as_dict() for i in range(k)], st_all.as_dict()
+    prof = di_profile()
+    check(load().di_query_batch_ex(handle, k, ptr(seed_ptr), ptr(seeds), ptr(w), float(tol), int(profile),
+                                   ptr(H_out), st_q, ctypes.byref(st_all), ctypes.byref(prof)))
+    return [st_q[i].as_dict() for i in range(k)], st_all.as_dict(), prof.as_dict() if profile else None
 
 
 def di_power(handle, tol, X_out, max_iter=0, allow_unconverged=False):
@@ -186,7 +195,7 @@ def di_get_state(handle, F_out=None, H_out=None):
 def di_get_profile(handle) -> dict:
     p = di_profile()
     check(load().di_get_profile(handle, ctypes.byref(p)))
-    return {"scan_ms": p.scan_ms, "push_ms": p.push_ms, "finalize_ms": p.finalize_ms, "sweeps": p.sweeps}
+    return p.as_dict()
 
 
 class DiGraph:
@@ -242,10 +251,13 @@ class DiGraph:
         st = di_query(self.handle, s, ww, tol, H, prec)
         return H, st
 
-    def query_batch(self, seed_lists, tol, H_out=None, weights=None):
-        """Personalized queries solved together; returns (H [k, n], per-query stats, batch stats)."""
+    def query_batch(self, seed_lists, tol, H_out=None, weights=None, profile=0):
+        """Personalized queries solved together; returns (H [k, n], per-query stats, batch stats).
+        With profile=1 the batch stats carry the kernel split under "profile"."""
         H = H_out if H_out is not None else np.empty((len(seed_lists), self.n), dtype=np.float64)
-        st_q, st_all = di_query_batch(self.handle, seed_lists, tol, H, weights)
+        st_q, st_all, prof = di_query_batch_ex(self.handle, seed_lists, tol, H, weights, profile)
+        if prof is not None:
+            st_all["profile"] = prof
         return H, st_q, st_all
 
     def power(self, tol, X_out=None, max_iter=0, allow_unconverged=False, profile=0):

@@ -55,7 +55,10 @@ class di_sweep_record(ctypes.Structure):
 
 class di_profile(ctypes.Structure):
     _fields_ = [("scan_ms", ctypes.c_double), ("push_ms", ctypes.c_double), ("finalize_ms", ctypes.c_double),
-                ("sweeps", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("sweeps", ctypes.c_int32), ("pull_sweeps", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class di_completion(ctypes.Structure):
@@ -111,6 +114,8 @@ def load(path: str = LIB_PATH):
         "di_query": ([vp, vp, vp, i32, f64, ctypes.c_int, vp, ctypes.POINTER(di_stats)], ctypes.c_int),
         "di_power": ([vp, f64, i32, vp, ctypes.POINTER(di_stats)], ctypes.c_int),
         "di_query_batch": ([vp, i32, vp, vp, vp, f64, vp, vp, ctypes.POINTER(di_stats)], ctypes.c_int),
+        "di_query_batch_ex": ([vp, i32, vp, vp, vp, f64, i32, vp, vp, ctypes.POINTER(di_stats),
+                               ctypes.POINTER(di_profile)], ctypes.c_int),
         "di_power_ex": ([vp, f64, i32, i32, vp, ctypes.POINTER(di_stats), ctypes.POINTER(f64), ctypes.POINTER(f64)],
                         ctypes.c_int),
         "di_get_trace": ([vp, vp, i32, ctypes.POINTER(i32)], ctypes.c_int),

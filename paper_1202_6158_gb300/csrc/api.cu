@@ -360,7 +360,15 @@ di_status di_query(di_graph *g, const int32_t *seeds, const double *w, int32_t n
 
 di_status di_query_batch(di_graph *g, int32_t k, const int32_t *seed_ptr, const int32_t *seeds, const double *w,
                          double tol, double *H_out, di_stats *st_q, di_stats *st_all) {
+    return di_query_batch_ex(g, k, seed_ptr, seeds, w, tol, 0, H_out, st_q, st_all, nullptr);
+}
+
+di_status di_query_batch_ex(di_graph *g, int32_t k, const int32_t *seed_ptr, const int32_t *seeds, const double *w,
+                            double tol, int32_t profile, double *H_out, di_stats *st_q, di_stats *st_all,
+                            di_profile *prof) {
     g_last_error.clear();
+    if (profile != 0 && profile != 1) return set_error(DI_EINVAL, "profile must be 0 or 1");
+    if (profile && !prof) return set_error(DI_EINVAL, "prof is NULL");
     if (check_graph(g) != DI_OK) return DI_EINVAL;
     if (k < 1 || k > kLanes) return set_error(DI_EINVAL, "a batch holds 1 to 64 queries");
     if (!seed_ptr || !seeds) return set_error(DI_EINVAL, "seed_ptr and seeds are required");
@@ -393,7 +401,7 @@ di_status di_query_batch(di_graph *g, int32_t k, const int32_t *seed_ptr, const 
         if (!(sum > 0.0)) return set_error(DI_EINVAL, "each query's seed weights need a positive sum");
     }
     return run_query_batch(g, k, hp.data(), hs.data(), w ? hw.data() : nullptr, tol, 0.5, 1000000, H_out,
-                           is_device_ptr(H_out), st_q, st_all);
+                           is_device_ptr(H_out), st_q, st_all, profile ? prof : nullptr);
 }
 
 di_status di_power(di_graph *g, double tol, int32_t max_iter, double *X_out, di_stats *st) {

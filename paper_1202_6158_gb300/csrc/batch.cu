@@ -759,20 +759,63 @@ __global__ void k_blane_retire(LaneRetire rl, int n, int K, const int *__restric
     }
 }
 
+// one sweep of the batched loop on stream st: scan, push, pull, finalize.  In a capture the
+// finalize drives the while-loop (in_graph = 1); a profiled loop passes four events, recorded
+// before the scan, after it, after the push and pull, and after the finalize.
 template <int LPN>
-void capture_batch_body(di_graph *g, BatchPool *p, cudaGraphConditionalHandle handle, int S) {
+void launch_batch_sweep(di_graph *g, BatchPool *p, int S, cudaStream_t st, cudaGraphConditionalHandle handle,
+                        int in_graph, cudaEvent_t *ev) {
     const int nhot = std::min(g->n_hot, kBatchHot);
-    k_bscan<LPN><<<g->G, kScanThreads, 0, g->cap>>>(g->chunk / kWarps, S, p->Fb, g->cls, g->region, g->W, p->fcount,
-                                                    p->pre, p->ticket, p->selb_node, p->selb_rows, p->spos, p->bq,
-                                                    p->bctl, g->d);
-    k_bpush<LPN><<<push_grid(g), kScanThreads, 0, g->cap>>>(g->rec32, g->col_idx, p->Fb, p->Hb, S, g->region, p->pre, g->W,
-                                                    p->selb_node, p->selb_rows, nhot, p->bctl);
-    k_bpull<LPN><<<push_grid(g), kScanThreads, 0, g->cap>>>(g->rec32, g->in_src, g->in_dst, g->inv_deg32, g->nnz, p->spos,
-                                                    p->Fb, p->Hb, S, g->region, p->pre, g->W, p->selb_node,
-                                                    p->selb_rows, p->bctl);
+    if (ev) cudaEventRecord(ev[0], st);
+    k_bscan<LPN><<<g->G, kScanThreads, 0, st>>>(g->chunk / kWarps, S, p->Fb, g->cls, g->region, g->W, p->fcount,
+                                                p->pre, p->ticket, p->selb_node, p->selb_rows, p->spos, p->bq,
+                                                p->bctl, g->d);
+    if (ev) cudaEventRecord(ev[1], st);
+    k_bpush<LPN><<<push_grid(g), kScanThreads, 0, st>>>(g->rec32, g->col_idx, p->Fb, p->Hb, S, g->region, p->pre, g->W,
+                                                        p->selb_node, p->selb_rows, nhot, p->bctl);
+    k_bpull<LPN><<<push_grid(g), kScanThreads, 0, st>>>(g->rec32, g->in_src, g->in_dst, g->inv_deg32, g->nnz, p->spos,
+                                                        p->Fb, p->Hb, S, g->region, p->pre, g->W, p->selb_node,
+                                                        p->selb_rows, p->bctl);
+    if (ev) cudaEventRecord(ev[2], st);
     // rows of 4 lanes always push: their 16-byte reductions cost no more than the pull's gathers
     const long long pull_edges = LPN >= 2 ? std::max(1LL, (g->nnz + kPullShareBatch - 1) / kPullShareBatch) : LLONG_MAX;
-    k_bfinalize<<<1, kLanes, 0, g->cap>>>(g->n, pull_edges, p->bq, p->bctl, handle, 1);
+    k_bfinalize<<<1, kLanes, 0, st>>>(g->n, pull_edges, p->bq, p->bctl, handle, in_graph);
+    if (ev) cudaEventRecord(ev[3], st);
+}
+
+template <int LPN>
+void capture_batch_body(di_graph *g, BatchPool *p, cudaGraphConditionalHandle handle, int S) {
+    launch_batch_sweep<LPN>(g, p, S, g->cap, handle, 1, nullptr);
+}
+
+// the batched loop launched from the host, sweep by sweep, with CUDA events around the kernels
+di_status profile_batch_loop(di_graph *g, BatchPool *p, int slot, int S, cudaStream_t st, di_profile *prof) {
+    cudaGraphConditionalHandle none = 0;
+    int pulling = p->h_bctl->pull;  // the direction the next sweep takes
+    for (int sw = 0; sw < (1 << 24); ++sw) {
+        switch (slot) {
+            case 0: launch_batch_sweep<1>(g, p, S, st, none, 0, g->pev); break;
+            case 1: launch_batch_sweep<2>(g, p, S, st, none, 0, g->pev); break;
+            case 2: launch_batch_sweep<4>(g, p, S, st, none, 0, g->pev); break;
+            case 3: launch_batch_sweep<8>(g, p, S, st, none, 0, g->pev); break;
+            default: launch_batch_sweep<16>(g, p, S, st, none, 0, g->pev); break;
+        }
+        DI_CUDA(cudaGetLastError());
+        DI_CUDA(cudaMemcpyAsync(p->h_bctl, p->bctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, st));
+        DI_CUDA(cudaStreamSynchronize(st));
+        float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+        DI_CUDA(cudaEventElapsedTime(&t0, g->pev[0], g->pev[1]));
+        DI_CUDA(cudaEventElapsedTime(&t1, g->pev[1], g->pev[2]));
+        DI_CUDA(cudaEventElapsedTime(&t2, g->pev[2], g->pev[3]));
+        prof->scan_ms += t0;
+        prof->push_ms += t1;
+        prof->finalize_ms += t2;
+        prof->sweeps += 1;
+        prof->pull_sweeps += pulling;
+        pulling = p->h_bctl->pull;
+        if (p->h_bctl->all_done) break;  // this sweep's finalize ended the loop, as in the graph
+    }
+    return DI_OK;
 }
 
 int batch_grid(const di_graph *g, long long work) {
@@ -907,7 +950,8 @@ di_status pool_launch_round(di_graph *g, BatchPool *p, int slot, const LaneAdmin
 }
 
 di_status run_query_batch(di_graph *g, int k, const int *seed_ptr, const int *seeds, const double *w, double tol,
-                          double beta, int max_sweeps, double *H_out, bool out_dev, di_stats *st_q, di_stats *st_all) {
+                          double beta, int max_sweeps, double *H_out, bool out_dev, di_stats *st_q, di_stats *st_all,
+                          di_profile *prof) {
     cudaStream_t s = g->stream;
     if (!g->bp) g->bp = new BatchPool();
     BatchPool *p = g->bp;
@@ -949,9 +993,19 @@ di_status run_query_batch(di_graph *g, int k, const int *seed_ptr, const int *se
     k_bctl_init<<<1, kLanes, 0, s>>>(k, p->bq, p->bctl, tol, omd, beta, n, max_sweeps);
     DI_CUDA(cudaGetLastError());
     int attempts = 0;
+    if (prof) {
+        *prof = di_profile{};
+        DI_CUDA(cudaMemcpyAsync(p->h_bctl, p->bctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
+        DI_CUDA(cudaStreamSynchronize(s));
+    }
     for (int attempt = 0; attempt < 8; ++attempt) {
         ++attempts;
-        DI_CUDA(cudaGraphLaunch(p->exec[slot], s));
+        if (prof) {
+            di_status pr = profile_batch_loop(g, p, slot, K, s, prof);
+            if (pr != DI_OK) return pr;
+        } else {
+            DI_CUDA(cudaGraphLaunch(p->exec[slot], s));
+        }
         k_bzero_exact<<<1, kLanes, 0, s>>>(p->bq);
         k_bl1_exact<<<grid, 256, 0, s>>>(rows, K, K, p->Fb, p->bq);
         k_bconfirm<<<1, kLanes, 0, s>>>(n, p->bq, p->bctl);
@@ -1011,7 +1065,8 @@ di_status run_query_batch(di_graph *g, int k, const int *seed_ptr, const int *se
         st_all->sweeps = c.sweeps;
         st_all->converged = all_conv ? 1 : 0;
         st_all->seconds = ms * 1e-3;
-        st_all->kernel_launches = 3 + 3LL * c.body_runs + 3LL * attempts;
+        // init (3), scan + push + pull + finalize per loop body, confirmation (3) per attempt, gather
+        st_all->kernel_launches = 3 + 4LL * c.body_runs + 3LL * attempts + (H_out ? 1 : 0);
     }
     if (c.all_done == 2 || !all_conv) return set_error(DI_ENOTCONVERGED, "a batched query stopped at a limit");
     return DI_OK;

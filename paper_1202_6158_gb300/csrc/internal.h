@@ -303,7 +303,8 @@ int scan_blocks_per_sm();
 
 // batched queries (batch.cu)
 di_status run_query_batch(di_graph *g, int k, const int *seed_ptr, const int *seeds, const double *w, double tol,
-                          double beta, int max_sweeps, double *H_out, bool out_dev, di_stats *st_q, di_stats *st_all);
+                          double beta, int max_sweeps, double *H_out, bool out_dev, di_stats *st_q, di_stats *st_all,
+                          di_profile *prof);  // prof != NULL: the loop launched from the host, timed
 di_status pool_alloc(di_graph *g, BatchPool *p, int lanes, cudaStream_t s);
 void pool_free(BatchPool *p, cudaStream_t s);
 long long pool_bytes(const di_graph *g, int lanes);

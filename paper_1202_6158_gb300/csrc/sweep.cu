@@ -741,6 +741,7 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, InitK
     }
     DI_CUDA(cudaGetLastError());
     int attempts = 0;
+    int pulling = 0;  // the device's pull flag before the next sweep (a profiled loop counts pull sweeps)
     g->prof = di_profile{};
     g->h_st->done = 0;  // the host copy of the previous solve's stop code is not this solve's
     for (int attempt = 0; attempt < 8; ++attempt) {
@@ -787,6 +788,8 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, InitK
                     g->sweep_ms[2 * g->prof.sweeps + 1] = t1;
                 }
                 g->prof.sweeps += 1;
+                g->prof.pull_sweeps += pulls && pulling;
+                pulling = g->h_st->pull;
                 if (g->h_st->done != 0) break;
             }
         } else {
@@ -797,6 +800,7 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, InitK
         DI_CUDA(cudaGetLastError());
         DI_CUDA(cudaMemcpyAsync(g->h_st, g->st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
         DI_CUDA(cudaStreamSynchronize(s));
+        pulling = g->h_st->pull;
         if (g->h_st->done != 0 && g->h_st->done != 5) break;
     }
     DI_CUDA(cudaEventRecord(g->ev1, s));

@@ -105,3 +105,25 @@ def test_device_output_and_limits(di, graphs):
             G.query_batch([[g.n + 1]], 1e-6)
         with pytest.raises(di.DiError, match="at least one seed"):
             G.query_batch([[1], []], 1e-6)
+
+
+def test_profiled_batch_matches_the_captured_loop(di, graphs):
+    """profile=1 launches the same sweep kernels from the host with events: the same answers
+    within the bounds, one profiled sweep per loop sweep, positive kernel times."""
+    g = graphs["rmat12"]
+    seeds = gg.seed_sets(g.n, 64, 1, 32, seed=23)
+    tol = 1e-6
+    with di.DiGraph(g.n, g.row_ptr, g.col_idx, D) as G:
+        H, st_q, st_all = G.query_batch(seeds, tol)
+        Hp, st_qp, st_allp = G.query_batch(seeds, tol, profile=1)
+    prof = st_allp["profile"]
+    assert "profile" not in st_all
+    assert st_allp["converged"] == 1 and all(s["bound"] <= tol for s in st_qp)
+    assert prof["sweeps"] == st_allp["sweeps"]
+    assert 0 <= prof["pull_sweeps"] <= prof["sweeps"]
+    assert prof["scan_ms"] > 0 and prof["push_ms"] > 0 and prof["finalize_ms"] > 0
+    for q in range(64):
+        assert np.abs(H[q] - Hp[q]).sum() <= st_q[q]["bound"] + st_qp[q]["bound"] + 2 * FP32_ALLOW
+    with di.DiGraph(g.n, g.row_ptr, g.col_idx, D) as G:
+        with pytest.raises(di.DiError, match="profile"):
+            di.di_query_batch_ex(G.handle, seeds[:2], tol, np.empty((2, g.n)), profile=2)

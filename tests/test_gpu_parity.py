@@ -229,6 +229,24 @@ def test_trace_records(di, direction):
     assert tr[-1]["R"] <= 1e-10 * (1 - D)
 
 
+@pytest.mark.parametrize("direction", [0, 1, 2])
+def test_profiled_solve_counts_pull_sweeps(di, direction):
+    """profile=1 launches the sweep kernels from the host with events; it counts one sweep per
+    loop sweep and, of those, the ones the trace records as pulls, and diffuses the same sets."""
+    n, rp, ci = CASES["rmat_12"]
+    with di.DiGraph(n, rp, ci, D) as g:
+        H0, st0 = g.solve(1e-10, beta=BETA, direction=direction)
+        H, st = g.solve(1e-10, beta=BETA, trace=1, profile=1, direction=direction)
+        tr = g.trace()
+        prof = g.profile()
+    assert prof["sweeps"] == st["sweeps"] == st0["sweeps"] == len(tr)
+    assert prof["pull_sweeps"] == sum(t["pull"] for t in tr)
+    assert (prof["pull_sweeps"] > 0) == bool(direction)
+    assert prof["scan_ms"] > 0 and prof["push_ms"] > 0 and prof["finalize_ms"] > 0
+    assert st["edges_pushed"] == st0["edges_pushed"]
+    assert np.abs(H - H0).sum() <= 1e-13
+
+
 @pytest.mark.parametrize("direction", [0, 1])
 def test_fp32_mixed_precision(di, direction):
     """FP32 fluid and pushes, FP64 H and residual: |H - H_oracle|_1 <= 2e-6."""
