@@ -402,18 +402,80 @@ __global__ void k_perm_deg(int n, const int *__restrict__ perm, const int *__res
         deg[r] = r < n ? row_ptr[perm[r] + 1] - row_ptr[perm[r]] : 0;
 }
 
-// edge e of the relabeled CSR: its row r by binary search, then the input edge it copies
-// (one thread per edge keeps hub rows of tens of thousands of out-links balanced)
-__global__ void k_perm_cols(int n, long long nnz, const int *__restrict__ perm, const int *__restrict__ new_of,
-                            const int *__restrict__ row_ptr_in, const int *__restrict__ col_in,
-                            const int *__restrict__ row_ptr_out, int *__restrict__ col_out) {
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (long long)gridDim.x * blockDim.x) {
-        int lo = 0, hi = n;
-        while (hi - lo > 1) {
-            int mid = lo + (hi - lo) / 2;
-            if ((long long)row_ptr_out[mid] <= e) lo = mid; else hi = mid;
+// The internal numbering puts the nh <= kHotSlots hot targets first and keeps every other
+// node in input order, so the relabeled CSR is the input CSR with nh rows moved to the front.
+// Its edges come from nh + 1 runs of the input: the hot rows, then the input with those rows
+// cut out -- nh + 1 segments between them.  k_hot_segments builds that table (one CTA):
+//   tab[0 .. nh]            hot row k's first input edge (k < nh)
+//   tab[kSeg .. kSeg+nh]    non-hot segment k's first input edge
+//   tab[2kSeg .. 2kSeg+nh+1] edges of the non-hot segments before segment k (a prefix)
+constexpr int kSeg = kHotSlots + 2;
+
+__global__ void __launch_bounds__(kHotSlots) k_hot_segments(int nh, long long nnz, const int *__restrict__ hot,
+                                                           const int *__restrict__ row_ptr_in, int *__restrict__ tab) {
+    __shared__ int s_sorted[kHotSlots];
+    __shared__ int s_len[kHotSlots + 1];
+    const int t = threadIdx.x;
+    // hot ids in ascending input order: each id's rank among them (ids are distinct)
+    if (t < nh) {
+        const int h = hot[t];
+        int rank = 0;
+        for (int j = 0; j < nh; ++j) rank += hot[j] < h;
+        s_sorted[rank] = h;
+        tab[t] = row_ptr_in[h];
+    }
+    __syncthreads();
+    // non-hot segment k: from the end of the (k-1)-th hot row (input order) to the start of the k-th
+    for (int k = t; k <= nh; k += blockDim.x) {
+        const int a = k == 0 ? 0 : row_ptr_in[s_sorted[k - 1] + 1];
+        const int b = k == nh ? (int)nnz : row_ptr_in[s_sorted[k]];
+        tab[kSeg + k] = a;
+        s_len[k] = b - a;
+    }
+    __syncthreads();
+    if (t == 0) {
+        int c = 0;
+        for (int k = 0; k <= nh; ++k) {
+            tab[2 * kSeg + k] = c;
+            c += s_len[k];
         }
-        const long long src_e = (long long)row_ptr_in[perm[lo]] + (e - row_ptr_out[lo]);
+        tab[2 * kSeg + nh + 1] = c;
+    }
+}
+
+// edge e of the relabeled CSR copies one input edge, its column renumbered: in a hot row k
+// (e below the hot rows' total) edge e - row_ptr_out[k] of that row, else the (e - hot total)-th
+// edge of the input outside the hot rows, found in the segment table (shared memory)
+__global__ void __launch_bounds__(256) k_perm_cols(int nh, long long nnz, const int *__restrict__ tab,
+                                                   const int *__restrict__ new_of, const int *__restrict__ col_in,
+                                                   const int *__restrict__ row_ptr_out, int *__restrict__ col_out) {
+    __shared__ int s_hot_out[kHotSlots + 1], s_hot_in[kHotSlots], s_seg[kHotSlots + 1], s_cum[kHotSlots + 2];
+    for (int k = threadIdx.x; k <= nh + 1; k += blockDim.x) {
+        if (k <= nh) s_hot_out[k] = row_ptr_out[k];
+        if (k < nh) s_hot_in[k] = tab[k];
+        if (k <= nh) s_seg[k] = tab[kSeg + k];
+        s_cum[k] = tab[2 * kSeg + k];
+    }
+    __syncthreads();
+    const long long hot_total = s_hot_out[nh];
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (long long)gridDim.x * blockDim.x) {
+        long long src_e;
+        if (e < hot_total) {
+            int lo = 0, hi = nh;  // the last hot row k < nh with row_ptr_out[k] <= e
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s_hot_out[mid] <= e) lo = mid; else hi = mid;
+            }
+            src_e = (long long)s_hot_in[lo] + (e - s_hot_out[lo]);
+        } else {
+            const long long o = e - hot_total;
+            int lo = 0, hi = nh + 1;  // the last segment k <= nh with cum[k] <= o (it is not empty)
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s_cum[mid] <= o) lo = mid; else hi = mid;
+            }
+            src_e = (long long)s_seg[lo] + (o - s_cum[lo]);
+        }
         col_out[e] = new_of[col_in[src_e]];
     }
 }
@@ -580,9 +642,13 @@ di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_de
         k_perm_deg<<<grid_for((long long)n + 1, 256, g->num_sms), 256, 0, s>>>(n, g->perm, g->row_ptr, rp2);
         di_status r = exclusive_scan(rp2, rp2, (long long)n + 1, s);
         if (r != DI_OK) return r;
-        if (L > 0)
-            k_perm_cols<<<grid_for(L, 256, g->num_sms), 256, 0, s>>>(n, L, g->perm, g->new_of, g->row_ptr, g->col_idx,
-                                                                    rp2, ci2);
+        if (L > 0) {
+            int *tab = nullptr;
+            DI_CUDA(cudaMallocAsync(&tab, sizeof(int) * 3 * kSeg, s));
+            k_hot_segments<<<1, kHotSlots, 0, s>>>(hk, L, g->hot_ids, g->row_ptr, tab);
+            k_perm_cols<<<grid_for(L, 256, g->num_sms), 256, 0, s>>>(hk, L, tab, g->new_of, g->col_idx, rp2, ci2);
+            cudaFreeAsync(tab, s);
+        }
         cudaFreeAsync(g->row_ptr, s);
         cudaFreeAsync(g->col_idx, s);
         g->row_ptr = rp2;

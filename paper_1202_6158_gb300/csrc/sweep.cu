@@ -484,8 +484,7 @@ __global__ void k_selftest_wait(int polls, int *__restrict__ gave_up) {
 __global__ void k_sweep_finalize(int n, int G, const ScanPartial *__restrict__ part, SolveState *__restrict__ st,
                                  di_sweep_record *__restrict__ trace, cudaGraphConditionalHandle handle,
                                  int in_graph) {
-    __shared__ double s_d[8];
-    __shared__ long long s_l[8];
+    __shared__ long long s_l[7][kScanThreads / 32];
     if (st->done) {  // converged before this body ran: leave the loop
         if (threadIdx.x == 0) {
             st->body_runs += 1;
@@ -493,25 +492,38 @@ __global__ void k_sweep_finalize(int n, int G, const ScanPartial *__restrict__ p
         }
         return;
     }
-    (void)s_d;
-    long long fl1 = 0, fout = 0, fdng = 0, ed = 0, sr = 0, en = 0, er = 0;
+    // the seven sums of the per-CTA partials, reduced together: warp trees, then thread 0 over
+    // the warps (integer sums, so exact in any order)
+    long long v[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int c = threadIdx.x; c < G; c += blockDim.x) {
-        er |= part[c].err;
-        fl1 += part[c].l1;
-        fout += part[c].out;
-        fdng += part[c].dng;
-        ed += part[c].edges;
-        sr += part[c].srcs;
-        en += part[c].entries;
+        const ScanPartial p = part[c];
+        v[0] += p.l1;
+        v[1] += p.out;
+        v[2] += p.dng;
+        v[3] += p.edges;
+        v[4] += p.srcs;
+        v[5] += p.entries;
+        v[6] |= p.err;
     }
-    fl1 = block_sum(fl1, s_l);
-    fout = block_sum(fout, s_l);
-    fdng = block_sum(fdng, s_l);
-    ed = block_sum(ed, s_l);
-    sr = block_sum(sr, s_l);
-    en = block_sum(en, s_l);
-    er = block_sum(er, s_l);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) v[k] += __shfl_down_sync(kFull, v[k], o);
+    }
+    const int wid = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) s_l[k][wid] = v[k];
+    }
+    __syncthreads();
     if (threadIdx.x != 0) return;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        long long a = 0;
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) a += s_l[k][w2];
+        v[k] = a;
+    }
+    const long long fl1 = v[0], fout = v[1], fdng = v[2], ed = v[3], sr = v[4], en = v[5], er = v[6];
     st->body_runs += 1;
     const double Tused = st->T;
     const int S = fixed_scale(st->R);  // the scale the scan used (st->R is still the previous residual)
