@@ -581,10 +581,18 @@ def main():
     e2e_edges = 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    split = np.zeros(3)  # host wall clock: create (copies in, ingest), solve (H out), free
     for _ in range(args.e2e_steps):
-        with di.DiGraph(g.n, rp_h, ci_h, w["d"]) as Ge:
-            _, est = Ge.solve(tol, H_out=H_h, beta=args.beta, direction=args.direction)
-            e2e_edges += est["edges_pushed"]
+        ta = time.perf_counter()
+        Ge = di.DiGraph(g.n, rp_h, ci_h, w["d"])
+        torch.cuda.synchronize()
+        tb = time.perf_counter()
+        _, est = Ge.solve(tol, H_out=H_h, beta=args.beta, direction=args.direction)
+        tc = time.perf_counter()
+        Ge.close()
+        torch.cuda.synchronize()
+        split += [tb - ta, tc - tb, time.perf_counter() - tc]
+        e2e_edges += est["edges_pushed"]
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     h2d = 4 * (g.n + 1) + 4 * g.nnz
@@ -641,7 +649,9 @@ def main():
             "e2e": {"value": tot_e2e_edges / max_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
                     "what": "pinned host CSR -> di_graph_create (copy, validation, ingest) -> di_solve to host H -> "
-                            "di_free, host wall clock"},
+                            "di_free, host wall clock",
+                    "split_ms": {k: round(1e3 * v / args.e2e_steps, 3)
+                                 for k, v in zip(("create", "solve_to_host", "free"), split)}},
             "cpu_baseline": cpu,
             "ppr_batch": ppr,
             "serving": serve,

@@ -172,8 +172,10 @@ di_status di_graph_create(int32_t n, const int32_t *row_ptr, const int32_t *col_
         return fail(cuda_fail(e, "cudaMallocAsync(row_ptr)"));
     if ((e = cudaMallocAsync(&g->col_idx, sizeof(int) * (size_t)std::max<int64_t>(nnz, 1), s)) != cudaSuccess)
         return fail(cuda_fail(e, "cudaMallocAsync(col_idx)"));
+    // a host col_idx is copied by build_graph, in pieces overlapped with its in-degree count
+    const bool col_on_host = nnz > 0 && !is_device_ptr(col_idx);
     di_status r = copy_in(g->row_ptr, row_ptr, sizeof(int) * (size_t)(n + 1), s);
-    if (r == DI_OK) r = copy_in(g->col_idx, col_idx, sizeof(int) * (size_t)nnz, s);
+    if (r == DI_OK && !col_on_host) r = copy_in(g->col_idx, col_idx, sizeof(int) * (size_t)nnz, s);
     if (r != DI_OK) return fail(r);
     if (V) {
         if ((e = cudaMallocAsync(&g->V, sizeof(double) * (size_t)n, s)) != cudaSuccess)
@@ -181,7 +183,7 @@ di_status di_graph_create(int32_t n, const int32_t *row_ptr, const int32_t *col_
         if ((r = copy_in(g->V, V, sizeof(double) * (size_t)n, s)) != DI_OK) return fail(r);
         if ((r = validate_v(g, g->V)) != DI_OK) return fail(r);
     }
-    if ((r = build_graph(g, g->row_ptr, g->col_idx)) != DI_OK) return fail(r);
+    if ((r = build_graph(g, col_on_host ? col_idx : nullptr)) != DI_OK) return fail(r);
     if ((r = sweep_alloc(g)) != DI_OK) return fail(r);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(cuda_fail(e, "graph create"));
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_fail(e, "graph create"));

@@ -4,12 +4,15 @@
 // out-link CSR of the problem statement (Section 2.1: column j of P spreads
 // 1/outdeg(j) over the children of j; Section 3.3: dangling columns stay zero):
 //   * validation of the CSR and of V (error flags, no traps);
-//   * out-degree bins (0 dangling, 1 thread, 2 warp, 3 CTA) and, per sweep-scan
-//     chunk, the offsets at which each bin's selected nodes are written;
-//   * the in-link CSR (a stable LSD radix sort of (target, source) pairs, so
-//     every in-row lists its sources in ascending order and the result is
-//     unique, hence bit-exact against any correct construction);
-//   * in-degree bins for the pull kernel and the chunk tasks of its longest rows.
+//   * the internal numbering (the most-linked-to targets first, every other node
+//     in input order) and the CSR relabeled to it;
+//   * out-degree bins (0 dangling, 1 thread, 2 warp, 3 CTA), the packed row
+//     records and, per sweep-scan chunk, the offsets at which each bin's
+//     selected nodes are written;
+//   * at first use: the in-link CSR (a stable LSD radix sort of (target, source)
+//     pairs, so every in-row lists its sources in ascending order and the result
+//     is unique, hence bit-exact against any correct construction), the target of
+//     each in-link, in-degree classes (exports) and row fingerprints (updates).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -60,8 +63,8 @@ __device__ int block_excl_scan(int v, int *total) {
 
 enum : int { kBadRowPtr0 = 1, kBadRowPtrN = 2, kNotMonotone = 4, kColRange = 8, kVNeg = 16, kVNonFinite = 32 };
 
-__global__ void k_validate_csr(int n, long long nnz, const int *__restrict__ row_ptr, const int *__restrict__ col_idx,
-                               int *flags) {
+// row starts; the column range is checked by the in-degree count that reads every column
+__global__ void k_validate_rows(int n, long long nnz, const int *__restrict__ row_ptr, int *flags) {
     long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     long long stride = (long long)gridDim.x * blockDim.x;
     int f = 0;
@@ -71,10 +74,6 @@ __global__ void k_validate_csr(int n, long long nnz, const int *__restrict__ row
     }
     for (long long i = tid; i < n; i += stride)
         if (row_ptr[i + 1] < row_ptr[i]) f |= kNotMonotone;
-    for (long long e = tid; e < nnz; e += stride) {
-        int j = col_idx[e];
-        if (j < 0 || j >= n) f |= kColRange;
-    }
     if (f) atomicOr(flags, f);
 }
 
@@ -334,11 +333,13 @@ __global__ void k_expand_rows(int n, long long nnz, const int *__restrict__ row_
 // global atomics serialize in one L2 slice, so each CTA first counts its tile of kCountTile
 // edges in a small shared-memory hash table (open addressing, a few probes) and adds each
 // table entry to global memory once; targets that find no slot go straight to global memory.
+// A column outside [0, n) is not counted; it sets kColRange in *flags (when flags is given).
 constexpr int kCountTile = 4096, kCountSlots = 2048, kCountProbes = 4;
 
-__global__ void __launch_bounds__(256) k_count_in(long long nnz, const int *__restrict__ col_idx,
-                                                  int *__restrict__ indeg) {
+__global__ void __launch_bounds__(256) k_count_in(long long nnz, const int *__restrict__ col_idx, int n,
+                                                  int *__restrict__ indeg, int *__restrict__ flags) {
     __shared__ int s_key[kCountSlots], s_cnt[kCountSlots];
+    bool bad = false;
     for (long long t0 = (long long)blockIdx.x * kCountTile; t0 < nnz; t0 += (long long)gridDim.x * kCountTile) {
         for (int k = threadIdx.x; k < kCountSlots; k += blockDim.x) {
             s_key[k] = -1;
@@ -348,6 +349,10 @@ __global__ void __launch_bounds__(256) k_count_in(long long nnz, const int *__re
         const long long t1 = min(nnz, t0 + kCountTile);
         for (long long e = t0 + threadIdx.x; e < t1; e += blockDim.x) {
             const int j = col_idx[e];
+            if ((unsigned)j >= (unsigned)n) {
+                bad = true;
+                continue;
+            }
             unsigned h = ((unsigned)j * 2654435761u) >> 21;  // 11 bits: kCountSlots = 2048
             bool done = false;
             for (int p = 0; p < kCountProbes && !done; ++p) {
@@ -365,6 +370,7 @@ __global__ void __launch_bounds__(256) k_count_in(long long nnz, const int *__re
             if (s_key[k] >= 0) atomicAdd(&indeg[s_key[k]], s_cnt[k]);
         __syncthreads();
     }
+    if (bad && flags) atomicOr(flags, kColRange);
 }
 
 // key that sorts nodes by in-degree, largest first (a stable sort keeps ascending ids on ties)
@@ -563,25 +569,62 @@ int count_grid(const di_graph *g, long long L) {
     return (int)std::max(1LL, std::min((L + kCountTile - 1) / kCountTile, (long long)g->num_sms * 8));
 }
 
-di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_dev) {
+constexpr int kCopyChunks = 8;  // pieces of a host col_idx, each counted as soon as it lands
+
+// in-degrees of g->col_idx into indeg (zeroed), column range errors into *flags.  From a host
+// col_idx the copy runs on the second stream in kCopyChunks pieces; the first stream counts each
+// piece after its copy, so the counting of one piece overlaps the copy of the next.
+cudaError_t count_columns(di_graph *g, const int *col_host, int *indeg, int *flags) {
+    cudaStream_t s = g->stream;
+    const long long L = g->nnz;
+    if (!col_host) {
+        k_count_in<<<count_grid(g, L), 256, 0, s>>>(L, g->col_idx, g->n, indeg, flags);
+        return cudaGetLastError();
+    }
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    // the copies start after the first stream's work so far (the allocation of col_idx)
+    e = cudaEventRecord(ev, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(g->cap, ev, 0);
+    const long long step = ceil_div(ceil_div(L, (long long)kCopyChunks), (long long)kCountTile) * kCountTile;
+    for (long long a = 0; e == cudaSuccess && a < L; a += step) {
+        const long long m = std::min(step, L - a);
+        e = cudaMemcpyAsync(g->col_idx + a, col_host + a, sizeof(int) * (size_t)m, cudaMemcpyHostToDevice, g->cap);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, g->cap);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev, 0);
+        if (e == cudaSuccess) {
+            k_count_in<<<count_grid(g, m), 256, 0, s>>>(m, g->col_idx + a, g->n, indeg, flags);
+            e = cudaGetLastError();
+        }
+    }
+    if (e != cudaSuccess) cudaStreamSynchronize(g->cap);  // no copy may still be writing after a failure
+    cudaEventDestroy(ev);
+    return e;
+}
+
+di_status build_graph(di_graph *g, const int *col_host) {
     cudaStream_t s = g->stream;
     const int n = g->n;
     const long long L = g->nnz;
-    (void)row_ptr_dev;
-    (void)col_idx_dev;
 
-    // 1. validation of the CSR copy
+    // 1. validation and in-degrees: k_validate_rows checks the row starts, the in-degree count
+    //    the columns (it reads each of them once); one host check of the flags after both
+    int *indeg = nullptr;
     {
         int *flags = nullptr;
         DI_CUDA(cudaMallocAsync(&flags, sizeof(int), s));
         DI_CUDA(cudaMemsetAsync(flags, 0, sizeof(int), s));
-        k_validate_csr<<<grid_for(std::max<long long>(n, L), 256, g->num_sms), 256, 0, s>>>(n, L, g->row_ptr, g->col_idx,
-                                                                                          flags);
-        int hf = 0;
+        DI_CUDA(cudaMallocAsync(&indeg, sizeof(int) * (size_t)n, s));
+        DI_CUDA(cudaMemsetAsync(indeg, 0, sizeof(int) * (size_t)n, s));
+        k_validate_rows<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, L, g->row_ptr, flags);
         cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess && L > 0) e = count_columns(g, col_host, indeg, flags);
+        int hf = 0;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         cudaFreeAsync(flags, s);
+        if (e == cudaSuccess && hf) cudaFreeAsync(indeg, s);
         if (e != cudaSuccess) return cuda_fail(e, "validate CSR");
         if (hf & kBadRowPtr0) return set_error(DI_EINVAL, "row_ptr[0] must be 0");
         if (hf & kBadRowPtrN) return set_error(DI_EINVAL, "row_ptr[n] must equal nnz");
@@ -595,15 +638,12 @@ di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_de
     //     hot targets' fluid in shared memory with a single compare; the rest stay spread over
     //     the L2 slices as the input spreads them.
     {
-        int *indeg = nullptr, *ka = nullptr, *kb = nullptr, *va = nullptr, *vb = nullptr, *cnt = nullptr;
-        DI_CUDA(cudaMallocAsync(&indeg, sizeof(int) * (size_t)n, s));
+        int *ka = nullptr, *kb = nullptr, *va = nullptr, *vb = nullptr, *cnt = nullptr;
         DI_CUDA(cudaMallocAsync(&ka, sizeof(int) * (size_t)n, s));
         DI_CUDA(cudaMallocAsync(&kb, sizeof(int) * (size_t)n, s));
         DI_CUDA(cudaMallocAsync(&va, sizeof(int) * (size_t)n, s));
         DI_CUDA(cudaMallocAsync(&vb, sizeof(int) * (size_t)n, s));
         DI_CUDA(cudaMallocAsync(&cnt, sizeof(int), s));
-        DI_CUDA(cudaMemsetAsync(indeg, 0, sizeof(int) * (size_t)n, s));
-        if (L > 0) k_count_in<<<count_grid(g, L), 256, 0, s>>>(L, g->col_idx, indeg);
         k_indeg_key_direct<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, indeg, ka);
         k_iota<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, va);
         for (int p = 0; p < 4; ++p) {
@@ -738,7 +778,7 @@ di_status build_transpose(di_graph *g) {
     DI_CUDA(cudaMallocAsync(&g->in_src, sizeof(int) * (size_t)std::max<long long>(L, 1), s));
     DI_CUDA(cudaMemsetAsync(g->in_ptr, 0, sizeof(int) * (size_t)(n + 1), s));
     if (L > 0) {
-        k_count_in<<<count_grid(g, L), 256, 0, s>>>(L, g->col_idx, g->in_ptr);
+        k_count_in<<<count_grid(g, L), 256, 0, s>>>(L, g->col_idx, n, g->in_ptr, nullptr);
         int *ka = nullptr, *kb = nullptr, *va = nullptr, *vtmp = nullptr;
         DI_CUDA(cudaMallocAsync(&ka, sizeof(int) * (size_t)L, s));
         DI_CUDA(cudaMallocAsync(&kb, sizeof(int) * (size_t)L, s));

@@ -277,7 +277,9 @@ di_status set_error(di_status s, const std::string &msg);
 di_status cuda_fail(cudaError_t e, const char *what);
 
 // graph ingest (graph_build.cu)
-di_status build_graph(di_graph *g, const int *row_ptr_dev, const int *col_idx_dev);
+// g->row_ptr holds the CSR's row starts; col_host non-NULL: the caller's host col_idx, copied
+// into g->col_idx here in chunks that overlap the in-degree count (else g->col_idx holds it)
+di_status build_graph(di_graph *g, const int *col_host);
 di_status build_in_dst(di_graph *g);  // the transpose, then in_dst
 di_status in_degree_classes(di_graph *g, int *out_dev);
 di_status ensure_rowhash(di_graph *g);  // fingerprints of the input rows (graph updates)

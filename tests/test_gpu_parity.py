@@ -98,6 +98,18 @@ def test_derived_structures_bit_exact(di, name):
     assert np.array_equal(ex["in_bin_of"], in_bin_of)
 
 
+def test_host_and_device_inputs_build_the_same_graph(di):
+    """A host col_idx is copied in pieces overlapped with the in-degree count; a device one is
+    copied whole: the derived structures are the same."""
+    n, rp, ci = CASES["zipf_2e14_hubs"]
+    with di.DiGraph(n, rp, ci, D) as gh, \
+            di.DiGraph(n, torch.from_numpy(rp).cuda(), torch.from_numpy(ci).cuda(), D) as gd:
+        eh, ed = gh.export(), gd.export()
+        assert np.array_equal(gh.hot_targets(), gd.hot_targets())
+    for k in eh:
+        assert np.array_equal(eh[k], ed[k]), k
+
+
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_hot_targets_bit_exact(di, name):
     """The push's shared-memory targets: top-256 in-degree (>= 32), ties by lower id."""
@@ -329,6 +341,14 @@ def test_invalid_inputs(di):
     bad[5] = n
     with pytest.raises(di.DiError, match="col_idx"):
         di.DiGraph(n, rp, bad, D)
+    # a host col_idx is copied and counted in pieces: an error in the last piece, and from
+    # device memory (one piece)
+    bad = ci.copy()
+    bad[-1] = -1
+    with pytest.raises(di.DiError, match="col_idx"):
+        di.DiGraph(n, rp, bad, D)
+    with pytest.raises(di.DiError, match="col_idx"):
+        di.DiGraph(n, torch.from_numpy(rp).cuda(), torch.from_numpy(bad).cuda(), D)
     rp2 = rp.copy()
     rp2[10], rp2[11] = rp2[11], rp2[10] - 1
     with pytest.raises(di.DiError):
