@@ -974,16 +974,56 @@ struct InjectArgs {
     double *F;              // new numbering
     int *long_rows;         // changed rows with more than 32 out-links in either graph
     int *n_long;
+    int n_hot;              // the new graph's hot targets (ids 0..n_hot-1), summed per CTA in shared memory
 };
 
-__device__ __forceinline__ void inject_row(const InjectArgs &a, int v, int lane, int width) {
+// one injected amount: the hot targets, which take a large share of all links and whose
+// same-address reductions would serialize in one L2 slice, are summed in shared memory
+__device__ __forceinline__ void inject_one(const InjectArgs &a, double *s_hot, int c, double val) {
+    if (c < a.n_hot) atomicAdd(s_hot + c, val);
+    else atomicAdd(a.F + c, val);
+}
+
+__device__ __forceinline__ void hot_zero(double *s_hot) {
+    for (int k = threadIdx.x; k < kHotSlots; k += blockDim.x) s_hot[k] = 0.0;
+    __syncthreads();
+}
+
+__device__ __forceinline__ void hot_flush(const InjectArgs &a, const double *s_hot) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < a.n_hot; k += blockDim.x)
+        if (s_hot[k] != 0.0) atomicAdd(a.F + k, s_hot[k]);
+}
+
+constexpr int kInjectRun = 4;
+
+__device__ __forceinline__ void inject_row(const InjectArgs &a, double *s_hot, int v, int lane, int width) {
     const int ro = a.new_of_old[v], rn = a.new_of_new[v];
     const double h = a.H[rn];
     if (h == 0.0) return;
     const RowRec<double> o = a.rec_old[ro], w = a.rec_new[rn];
     const double vo = -h * o.inv, vn = h * w.inv;
-    for (int e = lane; e < o.deg; e += width) atomicAdd(a.F + a.old_to_new[a.col_old[o.beg + e]], vo);
-    for (int e = lane; e < w.deg; e += width) atomicAdd(a.F + a.col_new[w.beg + e], vn);
+    // kInjectRun out-links per thread and pass, their loads issued together: a long row is a
+    // chain of dependent loads (column, renumbering) and reductions, bound by their latency
+    constexpr int U = kInjectRun;
+    for (int e0 = lane; e0 < o.deg; e0 += U * width) {
+        int c[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) c[k] = e0 + k * width < o.deg ? a.col_old[o.beg + e0 + k * width] : -1;
+#pragma unroll
+        for (int k = 0; k < U; ++k) c[k] = c[k] >= 0 ? a.old_to_new[c[k]] : -1;
+#pragma unroll
+        for (int k = 0; k < U; ++k)
+            if (c[k] >= 0) inject_one(a, s_hot, c[k], vo);
+    }
+    for (int e0 = lane; e0 < w.deg; e0 += U * width) {
+        int c[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) c[k] = e0 + k * width < w.deg ? a.col_new[w.beg + e0 + k * width] : -1;
+#pragma unroll
+        for (int k = 0; k < U; ++k)
+            if (c[k] >= 0) inject_one(a, s_hot, c[k], vn);
+    }
 }
 
 __global__ void k_old_to_new(int n, const int *__restrict__ perm_old, const int *__restrict__ new_of_new,
@@ -994,18 +1034,24 @@ __global__ void k_old_to_new(int n, const int *__restrict__ perm_old, const int 
 
 // a thread per changed row of up to 32 out-links; longer ones are listed for k_inject_long
 __global__ void k_inject_changed(InjectArgs a) {
+    __shared__ double s_hot[kHotSlots];
+    hot_zero(s_hot);
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += gridDim.x * blockDim.x) {
         if (a.hash_old[v] == a.hash_new[v]) continue;
         const int dl = max(a.rec_old[a.new_of_old[v]].deg, a.rec_new[a.new_of_new[v]].deg);
-        if (dl <= 32) inject_row(a, v, 0, 1);
+        if (dl <= 32) inject_row(a, s_hot, v, 0, 1);
         else a.long_rows[atomicAdd(a.n_long, 1)] = v;
     }
+    hot_flush(a, s_hot);
 }
 
 // a CTA per long changed row
 __global__ void k_inject_long(InjectArgs a) {
+    __shared__ double s_hot[kHotSlots];
+    hot_zero(s_hot);
     const int cnt = *a.n_long;
-    for (int k = blockIdx.x; k < cnt; k += gridDim.x) inject_row(a, a.long_rows[k], threadIdx.x, blockDim.x);
+    for (int k = blockIdx.x; k < cnt; k += gridDim.x) inject_row(a, s_hot, a.long_rows[k], threadIdx.x, blockDim.x);
+    hot_flush(a, s_hot);
 }
 
 }  // namespace
@@ -1087,6 +1133,7 @@ di_status run_update(di_graph *go, di_graph *gn, const di_solve_opts &o, double 
         a.col_new = gn->col_idx;
         a.H = gn->H;
         a.F = gn->F64;
+        a.n_hot = std::min(gn->n_hot, kHotSlots);
         // scratch: the composed renumbering, the long-row list (at most L/33 rows of either
         // graph have more than 32 out-links) and its count
         const long long cap = (go->nnz + gn->nnz) / 33 + 1;
