@@ -317,15 +317,40 @@ di_status radix_pass(const int *keys_in, const int *vals_in, int *keys_out, int 
 
 // --------------------------------------------------------------- transpose
 
-// source node of every edge position: the row whose range holds e
+// source node of every edge position: the row whose range holds e.  A warp takes a tile of
+// kExpandRuns x 32 consecutive positions, lane j the positions j, j + 32, ...: a binary search
+// over all rows finds the row of its first one, and each later one is found by galloping
+// forward from the previous row (a few loads, wherever empty rows lie between).
+constexpr int kExpandRuns = 16;
+
+__device__ __forceinline__ int row_from(const int *__restrict__ row_ptr, int n, long long e, int lo) {
+    // row_ptr[lo] <= e < row_ptr[n]: the last r >= lo with row_ptr[r] <= e
+    int hi = lo + 1;
+    long long step = 1;
+    while (hi < n && (long long)row_ptr[hi] <= e) {
+        lo = hi;
+        step <<= 1;
+        hi = (int)min((long long)n, (long long)lo + step);
+    }
+    while (hi - lo > 1) {
+        const int mid = lo + (hi - lo) / 2;
+        if ((long long)row_ptr[mid] <= e) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 __global__ void k_expand_rows(int n, long long nnz, const int *__restrict__ row_ptr, int *__restrict__ src) {
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (long long)gridDim.x * blockDim.x) {
-        int lo = 0, hi = n;  // find the last i with row_ptr[i] <= e
-        while (hi - lo > 1) {
-            int mid = lo + (hi - lo) / 2;
-            if ((long long)row_ptr[mid] <= e) lo = mid; else hi = mid;
+    const int lane = threadIdx.x & 31;
+    const long long tile = 32LL * kExpandRuns, tiles = (nnz + tile - 1) / tile;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < tiles; t += nw) {
+        int r = 0;
+        for (int k = 0; k < kExpandRuns; ++k) {
+            const long long e = t * tile + 32LL * k + lane;
+            if (e >= nnz) break;
+            r = row_from(row_ptr, n, e, r);  // rows only move forward along the lane's positions
+            src[e] = r;
         }
-        src[e] = lo;
     }
 }
 
