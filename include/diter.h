@@ -272,8 +272,10 @@ di_status di_query(di_graph *g, const int32_t *seeds, const double *w, int32_t n
  * holds k; 4 bytes per lane), so each read of a node's
  * out-links serves every query; histories are FP64.  A sweep selects node i when
  * some query that has not stopped has F_q[i] > T_q (T_q = 0.5 R_q/n), moves the
- * whole row into H and pushes it along the out-links.  Each query stops when its
- * own |F_q|_1/(1-d) <= tol, confirmed in FP64.
+ * whole row into H and diffuses it along the out-links: pushed, or, after a sweep
+ * whose selected nodes held at least a quarter of all out-links (rows of 8 lanes
+ * or more), gathered target by target along the in-links (the same diffusion).
+ * Each query stops when its own |F_q|_1/(1-d) <= tol, confirmed in FP64.
  *   k         1 <= k <= 64 queries
  *   seed_ptr  host or device int32[k+1]: query q's seeds are seeds[seed_ptr[q] ..
  *             seed_ptr[q+1]), at least one each (duplicates add their weights)
@@ -289,12 +291,14 @@ di_status di_query_batch(di_graph *g, int32_t k, const int32_t *seed_ptr, const 
                          double tol, double *H_out, di_stats *st_q, di_stats *st_all);
 
 /*
- * di_query_batch with a profiling switch.  profile = 1 launches each sweep's
- * kernels (scan, push, pull, finalize) from the host with CUDA events around
- * them, instead of the captured loop (the same kernels and arguments), and
- * fills *prof (host): scan_ms, push_ms (the push and pull kernels of each
- * sweep together), finalize_ms, sweeps, pull_sweeps.  profile = 0 is
- * di_query_batch; prof may then be NULL.
+ * di_query_batch (the same computation, Section 2.1) with a profiling switch.
+ * profile = 1 launches each sweep's kernels (scan, push, pull, finalize) from
+ * the host with CUDA events around them, instead of the captured loop (the same
+ * kernels and arguments), and fills *prof (host): scan_ms, push_ms (the push and
+ * pull kernels of each sweep together), finalize_ms, sweeps, pull_sweeps.
+ * profile = 0 is di_query_batch; prof may then be NULL.  Errors: those of
+ * di_query_batch, and DI_EINVAL for profile not 0 or 1, or profile = 1 with
+ * prof NULL.
  */
 di_status di_query_batch_ex(di_graph *g, int32_t k, const int32_t *seed_ptr, const int32_t *seeds, const double *w,
                             double tol, int32_t profile, double *H_out, di_stats *st_q, di_stats *st_all,
