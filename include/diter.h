@@ -91,7 +91,11 @@ typedef struct {
                                 where it stopped), so graphs whose sweeps never turn dense pay
                                 nothing */
     int32_t scan_wait_polls; /* polls of each bulk-copy wait of the sweep scan before the solve stops
-                                with DI_ETIMEOUT (0: 2^20; a small value makes a watchdog) */
+                                with DI_ETIMEOUT (0: 2^20; a small value makes a watchdog).  A warp
+                                that gave up then waits, with 2^20 polls, for its copies still in
+                                flight; if that wait gives up too, copies may land after the kernel
+                                returned, and every later call on the graph returns DI_ETIMEOUT
+                                until di_free */
 } di_solve_opts;
 
 /*
@@ -455,26 +459,33 @@ double di_clock(void);
 
 /*
  * di_power without any device allocation.  The paper has no counterpart: this
- * is a service for callers that cannot call cudaMalloc -- code running while a
- * CUDA graph is being captured, services that must not grow their device memory
- * after start-up or that hand out memory only from their own pools, plug-ins in
- * a host program that owns the GPU's allocator.  It runs the same power
- * iteration as di_power (X_0 = 0, X_{k+1} = dPX_k + (1-d)/n with the uniform V,
- * stop when |X_{k+1} - X_k|_1 * d/(1-d) < tol) on the caller's device arrays:
+ * is a service for callers that cannot call cudaMalloc -- services that must
+ * not grow their device memory after start-up or that hand out memory only
+ * from their own pools, plug-ins in a host program that owns the GPU's
+ * allocator.  It runs the same power iteration as di_power (X_0 = 0,
+ * X_{k+1} = dPX_k + (1-d)/n with the uniform V, stop when
+ * |X_{k+1} - X_k|_1 * d/(1-d) < tol) on the caller's device arrays:
  *   n        nodes, 1 <= n <= 65536 (larger n is rejected with DI_EINVAL)
  *   in_ptr   device int32[n+1], in_src device int32[nnz]: the in-link lists
  *            (row j lists every i with an edge i -> j; any order)
  *   row_ptr  device int32[n+1]: the out-link row pointers (out-degrees)
  *   X_out    device double[n], receives X
+ * Every array must be device memory of the current GPU (or managed memory);
+ * host memory and another GPU's memory are rejected with DI_EINVAL.
  * Its working memory (about 1 MB: two n-sized buffers, partial sums, a control
- * block) is one static array inside the library, present on every GPU that
- * loads the library until the process exits.  Every call shares that array and
- * it keeps the last call's contents, so calls that overlap on the GPU (two
- * streams, two host threads) race: issue them one after another.  The first
- * call on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture begins.  The inputs are
- * checked on the device first (DI_EINVAL names the bad array).  Nothing here
- * calls cudaMalloc, cudaFree or any allocating routine.
+ * block) is one static array inside the library.  It is committed on a GPU when
+ * the library's module for it is loaded there, which with CUDA's lazy module
+ * loading is the first call on that GPU; a caller that must not grow its device
+ * memory later should make one call during its start-up.  The array then stays
+ * until the process exits.  Every call shares that array and it keeps the last
+ * call's contents, so calls that overlap on the GPU (two streams, two host
+ * threads) race: issue them one after another.  The first call on a device
+ * also looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture begins.  The call waits for its stream:
+ * after the input checks and after every 16 products it copies a small status
+ * block to the host and synchronizes the stream.  The inputs are checked on the
+ * device first (DI_EINVAL names the bad array).  Nothing here calls cudaMalloc,
+ * cudaFree or any allocating routine.
  */
 di_status di_power_noalloc(int32_t n, const int32_t *in_ptr, const int32_t *in_src, int64_t nnz,
                            const int32_t *row_ptr, double d, double tol, int32_t max_iter, double *X_out,

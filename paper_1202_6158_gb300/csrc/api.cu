@@ -106,6 +106,9 @@ static void free_graph(di_graph *g) {
 
 static di_status check_graph(const di_graph *g) {
     if (!g) return set_error(DI_EINVAL, "graph is NULL");
+    if (g->untrusted)
+        return set_error(DI_ETIMEOUT, "an earlier sweep scan gave up waiting with bulk copies in flight; "
+                                      "this graph's device state is not trusted: free it");
     return DI_OK;
 }
 
@@ -194,7 +197,7 @@ di_status di_graph_create(int32_t n, const int32_t *row_ptr, const int32_t *col_
 void di_free(di_graph *g) { free_graph(g); }
 
 di_status di_graph_info(const di_graph *g, int32_t *n, int64_t *nnz, double *d) {
-    if (check_graph(g) != DI_OK) return DI_EINVAL;
+    if (di_status cr = check_graph(g); cr != DI_OK) return cr;
     if (n) *n = g->n;
     if (nnz) *nnz = g->nnz;
     if (d) *d = g->d;
@@ -224,7 +227,7 @@ extern "C" {
 di_status di_graph_export(const di_graph *g, int32_t *perm, int32_t *outdeg, int32_t *in_ptr, int32_t *in_src,
                           int32_t *bin_of, int32_t *in_bin_of, int32_t *cuts) {
     g_last_error.clear();
-    if (check_graph(g) != DI_OK) return DI_EINVAL;
+    if (di_status cr = check_graph(g); cr != DI_OK) return cr;
     if (in_ptr || in_src || in_bin_of) {
         di_status tr = build_transpose(const_cast<di_graph *>(g));  // built on first use
         if (tr != DI_OK) return tr;
@@ -263,7 +266,7 @@ di_status di_graph_export(const di_graph *g, int32_t *perm, int32_t *outdeg, int
 
 di_status di_graph_hot_targets(const di_graph *g, int32_t *ids, int32_t *count) {
     g_last_error.clear();
-    if (check_graph(g) != DI_OK) return DI_EINVAL;
+    if (di_status cr = check_graph(g); cr != DI_OK) return cr;
     if (count) *count = g->n_hot;
     if (ids && g->n_hot > 0) {
         di_status r = copy_out(ids, g->hot_ids, sizeof(int) * (size_t)g->n_hot, g->stream);
@@ -275,7 +278,7 @@ di_status di_graph_hot_targets(const di_graph *g, int32_t *ids, int32_t *count) 
 
 di_status di_solve_ex(di_graph *g, const di_solve_opts *opts, double *H_out, di_stats *st) {
     g_last_error.clear();
-    if (check_graph(g) != DI_OK) return DI_EINVAL;
+    if (di_status cr = check_graph(g); cr != DI_OK) return cr;
     if (!opts) return set_error(DI_EINVAL, "opts is NULL");
     di_solve_opts o = *opts;
     if (!(o.tol > 0.0) || !std::isfinite(o.tol)) return set_error(DI_EINVAL, "tol must be finite and > 0");
@@ -290,6 +293,8 @@ di_status di_solve_ex(di_graph *g, const di_solve_opts *opts, double *H_out, di_
 di_status di_solve_update(di_graph *g_old, di_graph *g_new, const di_solve_opts *opts, double *H_out, di_stats *st) {
     g_last_error.clear();
     if (!g_old || !g_new) return set_error(DI_EINVAL, "graph is NULL");
+    if (di_status cr = check_graph(g_old); cr != DI_OK) return cr;
+    if (di_status cr = check_graph(g_new); cr != DI_OK) return cr;
     if (!opts) return set_error(DI_EINVAL, "opts is NULL");
     di_solve_opts o = *opts;
     if (!(o.tol > 0.0) || !std::isfinite(o.tol)) return set_error(DI_EINVAL, "tol must be finite and > 0");
@@ -320,7 +325,7 @@ di_status di_solve(di_graph *g, double tol, int64_t max_edge_pushes, di_prec pre
 di_status di_query(di_graph *g, const int32_t *seeds, const double *w, int32_t nseeds, double tol, di_prec prec,
                    double *H_out, di_stats *st) {
     g_last_error.clear();
-    if (check_graph(g) != DI_OK) return DI_EINVAL;
+    if (di_status cr = check_graph(g); cr != DI_OK) return cr;
     if (nseeds < 1 || !seeds) return set_error(DI_EINVAL, "a query needs at least one seed");
     if (!(tol > 0.0) || !std::isfinite(tol)) return set_error(DI_EINVAL, "tol must be finite and > 0");
     if (prec != DI_FP64 && prec != DI_FP32_MIXED) return set_error(DI_EINVAL, "prec must be DI_FP64 or DI_FP32_MIXED");
@@ -371,7 +376,7 @@ di_status di_query_batch_ex(di_graph *g, int32_t k, const int32_t *seed_ptr, con
     g_last_error.clear();
     if (profile != 0 && profile != 1) return set_error(DI_EINVAL, "profile must be 0 or 1");
     if (profile && !prof) return set_error(DI_EINVAL, "prof is NULL");
-    if (check_graph(g) != DI_OK) return DI_EINVAL;
+    if (di_status cr = check_graph(g); cr != DI_OK) return cr;
     if (k < 1 || k > kLanes) return set_error(DI_EINVAL, "a batch holds 1 to 64 queries");
     if (!seed_ptr || !seeds) return set_error(DI_EINVAL, "seed_ptr and seeds are required");
     if (!(tol > 0.0) || !std::isfinite(tol)) return set_error(DI_EINVAL, "tol must be finite and > 0");
@@ -408,7 +413,7 @@ di_status di_query_batch_ex(di_graph *g, int32_t k, const int32_t *seed_ptr, con
 
 di_status di_power(di_graph *g, double tol, int32_t max_iter, double *X_out, di_stats *st) {
     g_last_error.clear();
-    if (check_graph(g) != DI_OK) return DI_EINVAL;
+    if (di_status cr = check_graph(g); cr != DI_OK) return cr;
     if (!(tol > 0.0) || !std::isfinite(tol)) return set_error(DI_EINVAL, "tol must be finite and > 0");
     if (max_iter <= 0) max_iter = 100000;
     return run_power(g, tol, max_iter, 0, X_out, is_device_ptr(X_out), st);
@@ -417,7 +422,7 @@ di_status di_power(di_graph *g, double tol, int32_t max_iter, double *X_out, di_
 di_status di_power_ex(di_graph *g, double tol, int32_t max_iter, int32_t profile, double *X_out, di_stats *st,
                       double *pull_ms, double *finalize_ms) {
     g_last_error.clear();
-    if (check_graph(g) != DI_OK) return DI_EINVAL;
+    if (di_status cr = check_graph(g); cr != DI_OK) return cr;
     if (!(tol > 0.0) || !std::isfinite(tol)) return set_error(DI_EINVAL, "tol must be finite and > 0");
     if (max_iter <= 0) max_iter = 100000;
     di_status r = run_power(g, tol, max_iter, profile, X_out, is_device_ptr(X_out), st);
@@ -428,7 +433,7 @@ di_status di_power_ex(di_graph *g, double tol, int32_t max_iter, int32_t profile
 
 di_status di_get_trace(const di_graph *g, di_sweep_record *out, int32_t cap, int32_t *count) {
     g_last_error.clear();
-    if (check_graph(g) != DI_OK) return DI_EINVAL;
+    if (di_status cr = check_graph(g); cr != DI_OK) return cr;
     int avail = g->last_trace_on ? std::min(g->h_st->sweeps, kTraceCap) : 0;
     if (count) *count = avail;
     int k = std::min(avail, std::max(0, (int)cap));
@@ -446,7 +451,7 @@ di_status di_get_trace(const di_graph *g, di_sweep_record *out, int32_t cap, int
 
 di_status di_get_profile(const di_graph *g, di_profile *out) {
     g_last_error.clear();
-    if (check_graph(g) != DI_OK) return DI_EINVAL;
+    if (di_status cr = check_graph(g); cr != DI_OK) return cr;
     if (!out) return set_error(DI_EINVAL, "out is NULL");
     *out = g->prof;
     return DI_OK;
@@ -454,7 +459,7 @@ di_status di_get_profile(const di_graph *g, di_profile *out) {
 
 di_status di_get_state(const di_graph *g, double *F_out, double *H_out) {
     g_last_error.clear();
-    if (check_graph(g) != DI_OK) return DI_EINVAL;
+    if (di_status cr = check_graph(g); cr != DI_OK) return cr;
     if (g->last_prec < 0) return set_error(DI_EINVAL, "no D-iteration solve has run on this graph");
     return copy_state(g, F_out, is_device_ptr(F_out), H_out, is_device_ptr(H_out));
 }

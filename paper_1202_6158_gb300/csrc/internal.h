@@ -95,7 +95,7 @@ struct SolveState {
     int dense;             // the last sweep was dense: a second dense sweep makes the next one pull
     int wait_polls;        // polls of each bulk-copy wait of the scan before the solve gives up
     int pause_pull;        // the in-link CSR is not built yet: a due pull stops the loop (done = 5) instead
-    int pad3;
+    int undrained;         // a timed-out scan warp returned with bulk copies possibly still landing
 };
 
 // batched personalized queries: up to kLanes queries interleaved in one fluid row
@@ -203,6 +203,7 @@ struct di_graph {
     int dev = 0;
     int num_sms = 152;
     int push_per_sm = 4;               // push CTAs per SM at least (the push grid never shrinks below the scan's)
+    bool untrusted = false;            // a scan wait timed out twice: copies may have landed late (DI_ETIMEOUT)
     cudaStream_t stream = nullptr;     // user stream
     cudaStream_t cap = nullptr;        // private stream used for graph capture
 

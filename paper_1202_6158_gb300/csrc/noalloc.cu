@@ -1,16 +1,17 @@
 // noalloc.cu -- a power iteration that allocates no device memory.
 //
-// Some callers cannot call cudaMalloc at all: code that runs while a CUDA graph
-// is being captured (an allocation would break the capture), services that must
-// not grow their memory footprint after start-up or that hand out device memory
-// only from their own pre-sized pools, and plug-ins loaded into a host program
-// that owns the GPU's allocator.  di_power_noalloc serves them: it computes the
-// same power iteration as di_power (X_0 = 0, X_{k+1} = dPX_k + (1-d)/n, stop
-// when |X_{k+1} - X_k|_1 * d/(1-d) < tol) directly on device arrays the caller
+// Some callers cannot call cudaMalloc at all: services that must not grow their
+// device memory after start-up or that hand out device memory only from their
+// own pre-sized pools, and plug-ins loaded into a host program that owns the
+// GPU's allocator.  di_power_noalloc serves them: it computes the same power
+// iteration as di_power (X_0 = 0, X_{k+1} = dPX_k + (1-d)/n, stop when
+// |X_{k+1} - X_k|_1 * d/(1-d) < tol) directly on device arrays the caller
 // already owns, and keeps its working memory -- the two buffers of d*x/outdeg,
 // the per-CTA partial sums and a small control block -- in one fixed-size
-// static __device__ array.  That array exists on every GPU that loads this
-// library, from load until process exit, whether or not the function is used.
+// static __device__ array.  The array is committed on a GPU when this file's
+// module is loaded there; with CUDA's lazy module loading that is the first
+// call on that GPU, so a caller that must not grow its footprint later makes
+// one call during its own start-up.  It then stays until the process exits.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -146,13 +147,21 @@ di_status na_scratch(unsigned char **out) {
     return DI_OK;
 }
 
+// device memory of the current GPU, or managed memory; another GPU's memory is rejected
+// because the kernels would reach it only through peer access that may not be enabled
 bool on_device(const void *p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -171,7 +180,7 @@ extern "C" di_status di_power_noalloc(int32_t n, const int32_t *in_ptr, const in
     if (!(d > 0.0 && d < 1.0)) return set_error(DI_EINVAL, "di_power_noalloc: d must satisfy 0 < d < 1");
     if (!(tol > 0.0) || !std::isfinite(tol)) return set_error(DI_EINVAL, "di_power_noalloc: tol must be finite and > 0");
     if (!on_device(in_ptr) || (nnz > 0 && !on_device(in_src)) || !on_device(row_ptr) || !on_device(X_out))
-        return set_error(DI_EINVAL, "di_power_noalloc: every array must be device memory");
+        return set_error(DI_EINVAL, "di_power_noalloc: every array must be device memory of the current GPU");
     if (max_iter <= 0) max_iter = 100000;
     unsigned char *base = nullptr;
     di_status r = na_scratch(&base);

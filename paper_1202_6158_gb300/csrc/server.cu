@@ -323,6 +323,8 @@ di_status di_server_create(di_graph *const *graphs, int32_t ngraphs, int64_t mem
     std::vector<int64_t> lane_b(ngraphs), fixed_b(ngraphs);
     for (int i = 0; i < ngraphs; ++i) {
         if (!graphs[i]) return set_error(DI_EINVAL, "graph " + std::to_string(i) + " is NULL");
+        if (graphs[i]->untrusted)
+            return set_error(DI_ETIMEOUT, "graph " + std::to_string(i) + " had a sweep scan time out: free it");
         lane_b[i] = pool_bytes(graphs[i], 1) - pool_bytes(graphs[i], 0);
         fixed_b[i] = pool_bytes(graphs[i], 0) + 8LL * graphs[i]->n;
     }

@@ -106,6 +106,7 @@ __device__ void init_control(SolveState *st, double R0, double tolR, double beta
     st->max_sweeps = max_sweeps;
     st->trace_on = trace_on;
     st->body_runs = 0;
+    st->undrained = 0;
     // the while-test of ALGO-REF comes first: nothing to do if R/(1-d) <= target already
     st->done = (R0 <= tolR) ? 1 : 0;
 }
@@ -423,10 +424,14 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
     }
     if (!ok) {
         // a wait gave up: wait (bounded again) for this warp's copies still in flight, then report
+        // (bit 1); if that wait gives up too, copies may still land in this CTA's shared memory
+        // after it returns, and the graph is no longer trusted (bit 2)
         if (lane == 0) {
+            bool drained = true;
             for (int t = s; t < nsteps && t < s + Ring::kStages; ++t)
-                mbar_wait(bar0 + 8u * (t % Ring::kStages), (unsigned)((t / Ring::kStages) & 1), kScanWaitLimit);
-            atomicExch(&s_err, 1);
+                drained &= mbar_wait(bar0 + 8u * (t % Ring::kStages), (unsigned)((t / Ring::kStages) & 1),
+                                     kScanWaitLimit);
+            atomicOr(&s_err, drained ? 1 : 3);
         }
         __syncwarp();
     }
@@ -565,8 +570,10 @@ __global__ void k_sweep_finalize(int n, int G, const ScanPartial *__restrict__ p
     if (!(Tn > 0.0)) Tn = 0.0;
     st->T = Tn;
     int done = 0;
-    if (er) done = 4;
-    else if (!isfinite(R)) done = 3;
+    if (er) {
+        done = 4;
+        if (er & 2) st->undrained = 1;
+    } else if (!isfinite(R)) done = 3;
     else if (R <= st->tolR) done = 1;
     else if (st->sweeps >= st->max_sweeps || (st->max_edges > 0 && st->edges >= st->max_edges)) done = 2;
     else if (st->pull && st->pause_pull) done = 5;  // a pull is due but the in-link CSR is not built: ask the host
@@ -845,6 +852,11 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, InitK
         stats->kernel_launches = (init == kInitV ? 2 : 3) + 3LL * h.body_runs + 2LL * attempts;
     }
     if (h.done == 3) return set_error(DI_EKERNEL, "residual became non-finite");
+    if (h.done == 4 && h.undrained) {
+        g->untrusted = true;  // sticky: every later call on this graph fails until di_free
+        return set_error(DI_ETIMEOUT, "a bulk-copy wait of the sweep scan gave up with copies still in flight; "
+                                      "the graph must be freed");
+    }
     if (h.done == 4) return set_error(DI_ETIMEOUT, "a bulk-copy wait of the sweep scan gave up");
     if (h.done != 1) return set_error(DI_ENOTCONVERGED, "stopped by a limit before |F|_1/(1-d) <= tol");
     return DI_OK;

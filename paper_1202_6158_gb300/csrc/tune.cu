@@ -41,6 +41,7 @@ using namespace diter;
 extern "C" di_status di_autotune(di_graph *g, const di_solve_opts *base, di_tune_result *best, di_tune_result *tried,
                                  int32_t cap, int32_t *ntried) {
     if (!g) return set_error(DI_EINVAL, "graph is NULL");
+    if (g->untrusted) return set_error(DI_ETIMEOUT, "an earlier sweep scan timed out on this graph: free it");
     if (!base || !best) return set_error(DI_EINVAL, "NULL argument");
     if (!(base->tol > 0.0)) return set_error(DI_EINVAL, "tol must be finite and > 0");
     if (base->prec != DI_FP64 && base->prec != DI_FP32_MIXED)

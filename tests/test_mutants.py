@@ -35,6 +35,9 @@ MUTANTS = {
     "op_argmax_ignores_weight": ("return wsel ? fabs(F[i]) * (double)wsel[i] : fabs(F[i]);", "return fabs(F[i]);"),
     "op_sweep_ignores_scale": ("float t = (float)(T * wscale);", "float t = (float)T;"),
     "op_threshold_raised": ("else if (wsel) T = fmin(T, beta * R / (double)n);", "else if (wsel) T = beta * R / (double)n;"),
+    "outdeg_off_by_one": ("outdeg[i] = row_ptr[i + 1] - row_ptr[i];", "outdeg[i] = row_ptr[i + 1] - row_ptr[i] - 1;"),
+    "outdeg_next_row": ("outdeg[i] = row_ptr[i + 1] - row_ptr[i];",
+                        "outdeg[i] = row_ptr[i + (i + 1 < n ? 2 : 1)] - row_ptr[i + (i + 1 < n ? 1 : 0)];"),
 }
 
 
@@ -89,6 +92,10 @@ def _battery(lib):
     in_ptr, in_src = oracle.transpose(n, rp, ci, lib=lib)
     want = [i for _j, i in sorted((int(j), i) for i in range(n) for j in ci[rp[i]:rp[i + 1]])]
     ok &= in_src.tolist() == want
+    # out-degrees against a count of the sources in an edge list
+    edges = [(int(i), int(j)) for i, j in np.random.default_rng(9).integers(0, 30, (120, 2))] + [(29, 29)]
+    rpe, _cie = graphs.csr(30, edges)
+    ok &= oracle.outdeg(30, rpe, lib=lib).tolist() == [sum(1 for i, _j in edges if i == k) for k in range(30)]
     return ok
 
 

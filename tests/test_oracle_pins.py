@@ -256,6 +256,33 @@ def test_power_converges_to_fixed_point():
 
 # ------------------------------------------------------ transpose and bins
 
+def outdeg_case(seed):
+    """A multigraph given as an edge list (self-loops and repeated links kept, some rows empty,
+    the last row non-empty) and its CSR; the out-degrees are counted from the list itself."""
+    rng = np.random.default_rng(seed)
+    n = 60
+    edges = [(int(rng.integers(0, n - 10)), int(rng.integers(0, n))) for _ in range(250)]  # rows 50..58 empty
+    edges += [(n - 1, 0), (n - 1, n - 1), (n - 1, n - 1), (3, 3)]
+    rp, ci = graphs.csr(n, edges)
+    return n, rp, edges
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_outdeg_brute_force(seed):
+    """#out_i (Section 2.1: column i of P holds 1/#out_i on each listed link) is the number of
+    times i appears as a source in the edge list, multi-edges and self-loops included."""
+    n, rp, edges = outdeg_case(seed)
+    want = [sum(1 for i, _j in edges if i == k) for k in range(n)]
+    got = oracle.outdeg(n, rp)
+    assert got.tolist() == want
+    assert 0 in want and int(got.sum()) == len(edges)
+
+
+def test_outdeg_edge_cases():
+    assert oracle.outdeg(1, np.array([0, 0], np.int32)).tolist() == [0]
+    assert oracle.outdeg(3, np.array([0, 2, 2, 5], np.int32)).tolist() == [2, 0, 3]
+
+
 def test_transpose_brute_force():
     n, rp, ci, _ = _rand_case(20, n=70)
     in_ptr, in_src = oracle.transpose(n, rp, ci)
