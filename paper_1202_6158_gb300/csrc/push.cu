@@ -57,25 +57,105 @@ __device__ __forceinline__ void push_row_lanes(const int *__restrict__ col_idx, 
     if (t < deg) push_one(F, hot, n_hot, __ldg(col_idx + beg + t), w, pol);
 }
 
+// Enumerate the class-3 (hub) entries of the sweep and cut their rows into chunks of
+// kHubChunk out-links: every CTA builds the same table in shared memory -- the list
+// position of each entry (s_pos) and the exclusive prefix sums of the chunk counts
+// (s_pre, te + 1 values) -- from the per-warp list counts of the scan.  Thread t takes the
+// sub-chunks t, t + 256, ...; entries are numbered thread by thread, so the enumeration
+// is the same in every CTA.  te is the class's list total (the caller checks te <= kHubCap);
+// it receives the number of entries in the table.  Returns the number of chunks (valid in
+// every thread).
+template <typename FT>
+__device__ int hub_chunks(const RowRec<FT> *__restrict__ rec, const Sel<FT> *__restrict__ sel,
+                          const int *__restrict__ region, const int *__restrict__ fcount, int W, int &te,
+                          int *s_pos, int *s_pre, int *s_scan) {
+    const int *r3 = region + 3 * (W + 1), *f3 = fcount + 3 * W;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // 1. entries per thread, an exclusive block scan, then each thread lists its entries
+    int ents = 0;
+#pragma unroll 4
+    for (int gg = threadIdx.x; gg < W; gg += kScanThreads) ents += __ldcg(f3 + gg);
+    int x = ents;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_scan[w] = x;
+    __syncthreads();
+    int oe = x - ents, listed = 0;
+    for (int k = 0; k < kWarps; ++k) {
+        oe += k < w ? s_scan[k] : 0;
+        listed += s_scan[k];
+    }
+    te = min(te, listed);  // the same count as the list total; never more than the table holds
+    if (ents) {
+        for (int gg = threadIdx.x; gg < W; gg += kScanThreads) {
+            const int c = __ldcg(f3 + gg);
+            const int b = c ? __ldg(r3 + gg) : 0;
+            for (int k = 0; k < c; ++k, ++oe)
+                if (oe < te) s_pos[oe] = b + k;
+        }
+    }
+    __syncthreads();
+    // 2. chunks of every entry
+    for (int e = threadIdx.x; e < te; e += kScanThreads) {
+        const int deg = rec[sel[s_pos[e]].node].deg;
+        s_pre[e] = (deg + kHubChunk - 1) / kHubChunk;
+    }
+    __syncthreads();
+    // 3. exclusive prefix over the chunk counts: a contiguous run per thread, then a block scan
+    const int per = (te + kScanThreads - 1) / kScanThreads;
+    const int e0 = min(te, (int)threadIdx.x * per), e1 = min(te, e0 + per);
+    int run = 0;
+    for (int e = e0; e < e1; ++e) run += s_pre[e];
+    x = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();  // every thread has read s_scan of step 1
+    if (lane == 31) s_scan[w] = x;
+    __syncthreads();
+    int off = x - run, total = 0;
+    for (int k = 0; k < kWarps; ++k) {
+        off += k < w ? s_scan[k] : 0;
+        total += s_scan[k];
+    }
+    for (int e = e0; e < e1; ++e) {
+        const int c = s_pre[e];
+        s_pre[e] = off;
+        off += c;
+    }
+    if (threadIdx.x == 0) s_pre[te] = total;
+    __syncthreads();
+    return total;
+}
+
 // The push.  The selected nodes with children of each class are numbered 0..total-1
-// through the prefix sums of the scan: the largest class (a CTA per node) and the
-// middle class (a warp per node) are strided over the CTAs / warps, which spreads heavy
-// rows evenly whatever the id order (R-MAT puts its heaviest rows on the lowest ids),
-// and the smallest class (a lane per node, four in flight, at most 8 out-links each) is
-// split into even rank ranges per warp.  The scan already moved each node's fluid into H; the push adds
-// d*sent/outdeg(i) to F_j along every out-link (ALGO-REF's inner loop), every load
-// of a node issued before its reductions.
+// through the prefix sums of the scan.  The middle class (a warp per node) is strided
+// over the warps, which spreads heavy rows evenly whatever the id order (R-MAT puts its
+// heaviest rows on the lowest ids), and the smallest class (a lane per node, four in
+// flight, at most 8 out-links each) is split into even rank ranges per warp.  The largest
+// class comes last: its rows (up to 50,000 out-links on the Zipf workload) are cut into
+// chunks of kHubChunk out-links that are strided over the CTAs, so no CTA carries a whole
+// hub.  The scan already moved each node's fluid into H; the push adds d*sent/outdeg(i)
+// to F_j along every out-link (ALGO-REF's inner loop), every load of a node issued before
+// its reductions.
 template <typename FT>
 __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT> *__restrict__ rec,
                                                              const int *__restrict__ col_idx, FT *__restrict__ F,
                                                              const int *__restrict__ region,
-                                                             const int *__restrict__ pre, int W,
+                                                             const int *__restrict__ pre,
+                                                             const int *__restrict__ fcount, int W,
                                                              const Sel<FT> *__restrict__ sel, int n_hot,
                                                              ScanPartial *__restrict__ part, int G,
                                                              const SolveState *__restrict__ st) {
     __shared__ FT hot[kHotSlots];
     __shared__ long long s_red[kWarps];
     __shared__ int s_idx;
+    __shared__ int s_hpos[kHubCap], s_hpre[kHubCap + 1], s_scan[kWarps];
     if (st->done || st->pull) return;
     for (int t = threadIdx.x; t < kHotSlots; t += kScanThreads) hot[t] = (FT)0;
     __syncthreads();
@@ -84,29 +164,32 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
     const int nwarps = gridDim.x * kWarps, gw = blockIdx.x * kWarps + w;
     const int *pre3 = pre + 3 * (W + 1);
     long long edges = 0;
-    // class 3: the whole CTA per node
     const int tot3 = __ldg(pre3 + W);
-    for (int t = blockIdx.x; t < tot3; t += gridDim.x) {
-        if (threadIdx.x == 0) {
-            const int gs = find_sub(pre3, W, t);
-            s_idx = region[3 * (W + 1) + gs] + (t - __ldg(pre3 + gs));
+    if (tot3 > kHubCap) {
+        // more hubs than the chunk table holds (dense sweeps of hub-rich graphs): the whole
+        // CTA per node, nodes strided over the CTAs
+        for (int t = blockIdx.x; t < tot3; t += gridDim.x) {
+            if (threadIdx.x == 0) {
+                const int gs = find_sub(pre3, W, t);
+                s_idx = region[3 * (W + 1) + gs] + (t - __ldg(pre3 + gs));
+            }
+            __syncthreads();
+            const Sel<FT> e = sel[s_idx];
+            __syncthreads();
+            const RowRec<FT> rr = rec[e.node];
+            if (threadIdx.x == 0) edges += rr.deg;
+            push_row_lanes(col_idx, F, hot, n_hot, rr.beg, rr.deg, e.sent * rr.inv, threadIdx.x, kScanThreads, pol);
         }
-        __syncthreads();
-        const Sel<FT> e = sel[s_idx];
-        __syncthreads();
-        const RowRec<FT> rr = rec[e.node];
-        if (threadIdx.x == 0) edges += rr.deg;
-        push_row_lanes(col_idx, F, hot, n_hot, rr.beg, rr.deg, e.sent * rr.inv, threadIdx.x, kScanThreads, pol);
     }
     // classes 2 and 1: each warp takes an even range of ranks of the class's list (ranks
     // number the list entries over all sub-chunks, so the split is even however the selected
     // nodes fall over the sub-chunks); a lane finds the sub-chunk of its rank from the
     // warp's current one
     {
-        // class 2: a warp per node, strided over the ranks (rank t to warp t mod nwarps), which
-        // interleaves heavy and light rows on any id order; lane j first finds and fetches the
-        // entry and row record of the warp's j-th node of each group of 32, so only the column
-        // loads remain on each node's path
+        // class 2: a half-warp per node, strided over the ranks (rank t to warp t mod nwarps),
+        // which interleaves heavy and light rows on any id order; lane j first finds and fetches
+        // the entry and row record of the warp's j-th node of each group of 32, so only the
+        // column loads remain on each node's path
         const int *p2 = pre + 2 * (W + 1), *r2 = region + 2 * (W + 1);
         const int tot = __ldg(p2 + W);
         for (long long k0 = 0; gw + k0 * nwarps < tot; k0 += 32) {
@@ -123,16 +206,21 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
                 edges += md;
             }
             const int m = (int)min(32LL, (tot - gw - k0 * nwarps + nwarps - 1) / nwarps);
-            for (int j = 0; j < m; ++j) {
-                const int rb = __shfl_sync(kFull, mb, j), rd = __shfl_sync(kFull, md, j);
-                const FT rw = __shfl_sync(kFull, mw, j);
-                push_row_lanes(col_idx, F, hot, n_hot, rb, rd, rw, lane, 32, pol);
+            // two nodes at a time, one per half-warp: a node's column loads and reductions are
+            // a dependent round trip, and two halves keep two of them in flight
+            const int half = lane >> 4;
+            for (int j = 0; j < m; j += 2) {
+                const int src = (j + half) & 31;
+                const int rb = __shfl_sync(kFull, mb, src), rd = __shfl_sync(kFull, md, src);
+                const FT rw = __shfl_sync(kFull, mw, src);
+                push_row_lanes(col_idx, F, hot, n_hot, rb, j + half < m ? rd : 0, rw, lane & 15, 16, pol);
             }
         }
     }
     {
-        // class 1: a lane per node, kInFlight nodes per lane at a time
+        // class 1: a lane per node, kInFlight nodes per lane at a time (at most 8 out-links each)
         constexpr int kInFlight = 4;
+        static_assert(kOutCut1 <= 8 && kInFlight == 4, "class-1 rows are pushed in two groups of four links");
         const int *p1 = pre + 1 * (W + 1), *r1 = region + 1 * (W + 1);
         const int tot = __ldg(p1 + W);
         const int per = (tot + nwarps - 1) / nwarps;
@@ -143,38 +231,90 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
             gs = __shfl_sync(kFull, gs, 0);
         }
         for (int t0 = t_beg; t0 < t_end; t0 += 32 * kInFlight) {
-            int rb[kInFlight], rd[kInFlight];
-            FT rw[kInFlight];
+            // list positions first (the prefix sums stay in L1), then every entry load, then
+            // every row record, so that each step has all of its loads in flight together
+            int pos[kInFlight];
             int mg = gs;
 #pragma unroll
             for (int u = 0; u < kInFlight; ++u) {
                 const int t = t0 + 32 * u + lane;
-                rd[u] = 0;
-                rb[u] = 0;
-                rw[u] = (FT)0;
+                pos[u] = -1;
                 if (t < t_end) {
                     mg = find_sub_from(p1, W, t, mg);
-                    const Sel<FT> e = sel[__ldg(r1 + mg) + (t - __ldg(p1 + mg))];
-                    const RowRec<FT> rr = rec[e.node];
-                    rb[u] = rr.beg;
-                    rd[u] = rr.deg;
-                    rw[u] = e.sent * rr.inv;
+                    pos[u] = __ldg(r1 + mg) + (t - __ldg(p1 + mg));
                 }
             }
             // every lane's last rank is below the next group's first: restart from the largest
             gs = __reduce_max_sync(kFull, (unsigned)mg);
-            int cc[kInFlight][kOutCut1];
+            int node[kInFlight];
+            FT sent[kInFlight];
+#pragma unroll
+            for (int u = 0; u < kInFlight; ++u) {
+                node[u] = 0;
+                sent[u] = (FT)0;
+                if (pos[u] >= 0) {
+                    const Sel<FT> e = sel[pos[u]];
+                    node[u] = e.node;
+                    sent[u] = e.sent;
+                }
+            }
+            int rb[kInFlight], rd[kInFlight];
+            FT rw[kInFlight];
+#pragma unroll
+            for (int u = 0; u < kInFlight; ++u) {
+                rb[u] = 0;
+                rd[u] = 0;
+                rw[u] = (FT)0;
+                if (pos[u] >= 0) {
+                    const RowRec<FT> rr = rec[node[u]];
+                    rb[u] = rr.beg;
+                    rd[u] = rr.deg;
+                    rw[u] = sent[u] * rr.inv;
+                }
+            }
+            // the first four out-links of every node (most rows have one to three), then the rest
+            int cc[kInFlight][4];
 #pragma unroll
             for (int u = 0; u < kInFlight; ++u) {
                 edges += rd[u];
 #pragma unroll
-                for (int k = 0; k < kOutCut1; ++k) cc[u][k] = k < rd[u] ? __ldg(col_idx + rb[u] + k) : 0;
+                for (int k = 0; k < 4; ++k) cc[u][k] = k < rd[u] ? __ldg(col_idx + rb[u] + k) : 0;
             }
 #pragma unroll
-            for (int k = 0; k < kOutCut1; ++k)
+            for (int k = 0; k < 4; ++k)
 #pragma unroll
                 for (int u = 0; u < kInFlight; ++u)
                     if (k < rd[u]) push_one(F, hot, n_hot, cc[u][k], rw[u], pol);
+            if (__any_sync(kFull, rd[0] > 4 || rd[1] > 4 || rd[2] > 4 || rd[3] > 4)) {
+#pragma unroll
+                for (int u = 0; u < kInFlight; ++u)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) cc[u][k] = k + 4 < rd[u] ? __ldg(col_idx + rb[u] + 4 + k) : 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+#pragma unroll
+                    for (int u = 0; u < kInFlight; ++u)
+                        if (k + 4 < rd[u]) push_one(F, hot, n_hot, cc[u][k], rw[u], pol);
+            }
+        }
+    }
+    // class 3: chunks of kHubChunk out-links of the hub rows, strided over the CTAs
+    if (tot3 > 0 && tot3 <= kHubCap) {
+        __syncthreads();
+        int ne = tot3;
+        const int nch = hub_chunks(rec, sel, region, fcount, W, ne, s_hpos, s_hpre, s_scan);
+        for (int t = blockIdx.x; t < nch; t += gridDim.x) {
+            int lo = 0, hi = ne;  // the entry holding chunk t: the last e with s_hpre[e] <= t
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s_hpre[mid] <= t) lo = mid; else hi = mid;
+            }
+            const Sel<FT> e = sel[s_hpos[lo]];
+            const RowRec<FT> rr = rec[e.node];
+            const int off = (t - s_hpre[lo]) * kHubChunk;
+            const int len = min(kHubChunk, rr.deg - off);
+            if (threadIdx.x == 0) edges += len;
+            push_row_lanes(col_idx, F, hot, n_hot, rr.beg + off, len, e.sent * rr.inv, threadIdx.x, kScanThreads, pol);
         }
     }
     // the CTA's sums for the hot targets go to F once
@@ -289,7 +429,7 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_sweep_pull(const int *__res
 template <typename FT>
 void launch_push(di_graph *g, FT *F, cudaStream_t s) {
     k_sweep_push<FT><<<push_grid(g), kScanThreads, 0, s>>>(rec_of<FT>(g), g->col_idx, F, g->region, g->pre,
-                                                           g->W, sel_of<FT>(g), g->n_hot, g->part, g->G,
+                                                           g->fcount, g->W, sel_of<FT>(g), g->n_hot, g->part, g->G,
                                                            g->st);
 }
 

@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
     int srcs = 0, entries = 0;
     long long pedges = 0;  // out-links of the selected nodes, counted here on pull sweeps
     const int nsteps = wchunk / kStep;
-    const unsigned long long pol = evict_first_policy(), pol_h = evict_last_policy();
+    const unsigned long long pol = evict_first_policy();
     // this warp's ring: lane 0 keeps kStages steps in flight
     unsigned char *ring = s_ring + w * Ring::kWarpBytes;
     unsigned char *q = s_q[w];
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
                 const long long node = step0 + idx;
                 if (has) {
                     const long long fx = to_fixed(v, S);
-                    red_add(H + node, (double)v, pol_h);   // ... into the history (H' = H + J_S F)
+                    red_add(H + node, (double)v, pol);     // ... into the history (H' = H + J_S F), evict-first
                     srcs += 1;
                     if (c == 0) {
                         s_dng += fx;            // a dangling node's fluid leaves the system (Section 3.3)
