@@ -145,11 +145,11 @@ def push_sources_digest():
 
 
 def push_traffic():
-    """DRAM bytes per push launch from the committed ncu summary, if the push sources are unchanged since.
+    """DRAM bytes per push launch from the committed ncu summary of the push kernel on this
+    workload (under profiles/), if the push sources are unchanged since it was taken.
 
-    profiles/push_sweep_zipf24.md records the digest of the push kernel's sources it
-    was taken with; a different digest means the kernel changed and the counters no
-    longer apply.
+    The summary records the digest of the push kernel's sources it was taken with; a
+    different digest means the kernel changed and the counters no longer apply.
     """
     summ = os.path.join(ROOT, "profiles", "push_sweep_zipf24.md")
     if not os.path.exists(summ):
@@ -196,11 +196,100 @@ def cpu_baseline(g, w, max_pushes, cores=1):
     t0 = time.perf_counter()
     r = oracle.diter(g.n, g.row_ptr, g.col_idx, w["d"], V, w["tol"], mode="sweep", beta=0.5, max_pushes=max_pushes)
     dt = time.perf_counter() - t0
-    return {"value": r.edges / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": r.edges / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "_H": r.H,
             "sample": f"oracle snapshot sweeps (beta=0.5) from F_0 on the same graph, cut at {max_pushes} diffusions: "
                       f"{r.sweeps} sweeps, {r.edges} edge pushes in {dt:.1f} s on 1 host core "
                       f"({'converged' if r.converged else 'not converged'})",
             "seconds": dt, "edges": int(r.edges), "sweeps": int(r.sweeps), "converged": bool(r.converged)}
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def cpu_power_baselines(g, w, sample_products=6):
+    """MAT-ITER on the host: the oracle's power iteration on one core over a bounded sample of
+    products (the rate per product is the same at every product), and the OpenMP pull version
+    on all host cores to the paper's stop rule at the workload's tolerance."""
+    import graphgen as gg
+    import oracle
+    V = gg.uniform_v(g.n)
+    out = {}
+    t0 = time.perf_counter()
+    _, it, _, _ = oracle.power(g.n, g.row_ptr, g.col_idx, w["d"], V, w["tol"], max_iter=sample_products)
+    dt = time.perf_counter() - t0
+    out["power_cpu"] = {"value": it * g.nnz / dt, "unit": UNIT, "cores": 1, "kind": "oracle MAT-ITER",
+                        "ms_per_product": 1e3 * dt / it,
+                        "sample": f"the oracle's power iteration from X_0 = 0, cut at {it} products, {dt:.1f} s"}
+    try:
+        in_ptr, in_src = oracle.transpose(g.n, g.row_ptr, g.col_idx)
+        deg = oracle.outdeg(g.n, g.row_ptr)
+        t0 = time.perf_counter()
+        _, it, _, ok, used = oracle.power_omp(g.n, in_ptr, in_src, deg, w["d"], V, w["tol"], threads=0)
+        dt = time.perf_counter() - t0
+        out["power_cpu_omp"] = {"value": it * g.nnz / dt, "unit": UNIT, "cores": used, "kind": "OpenMP MAT-ITER",
+                                "time_to_residual_ms": 1e3 * dt, "products": it, "converged": bool(ok),
+                                "sample": f"the full power iteration to the stop rule at tol {w['tol']:g} on "
+                                          f"{used} threads (in-link lists built beforehand, not timed)"}
+    except (OSError, subprocess.SubprocessError) as e:
+        out["power_cpu_omp"] = {"unavailable": f"OpenMP build failed: {e}"}
+    return out
+
+
+def _oracle_rmat_worker(scale, d, tol, path):
+    """Spawned process: the oracle's snapshot-sweep solve of R-MAT `scale` (edge factor 16,
+    seed 1, V = 1/N) to bound `tol`; H goes to `path` (.npy)."""
+    import graphgen as gg
+    import oracle
+    g = gg.rmat_graph(scale, 16, seed=1)
+    t0 = time.perf_counter()
+    r = oracle.diter(g.n, g.row_ptr, g.col_idx, d, gg.uniform_v(g.n), tol, mode="sweep", beta=0.5)
+    np.save(path, r.H)
+    with open(path + ".json", "w") as f:
+        json.dump({"seconds": time.perf_counter() - t0, "sweeps": int(r.sweeps), "edges": int(r.edges),
+                   "bound": r.l1F / (1 - d), "converged": bool(r.converged)}, f)
+
+
+class OracleInBackground:
+    """The oracle's config-3 solve (R-MAT scale 23, d = 0.85, bound 1e-7) in a spawned process,
+    started before the first GPU call and joined before the timed CPU baselines run."""
+
+    def __init__(self, scale=23, d=0.85, tol=1e-7):
+        import multiprocessing as mp
+        self.path = os.path.join(tempfile.gettempdir(), f"diter_oracle_rmat{scale}_{os.getpid()}.npy")
+        self.proc = mp.get_context("spawn").Process(target=_oracle_rmat_worker, args=(scale, d, tol, self.path))
+        self.proc.start()
+
+    def result(self, timeout=900):
+        """(H, info) once the solve has finished, or (None, reason)."""
+        self.proc.join(timeout)
+        if self.proc.is_alive():
+            self.proc.terminate()
+            self.proc.join(5)
+            return None, "oracle solve did not finish in %d s" % timeout
+        if self.proc.exitcode != 0 or not os.path.exists(self.path):
+            return None, "oracle process exited with code %s" % self.proc.exitcode
+        H = np.load(self.path)
+        with open(self.path + ".json") as f:
+            info = json.load(f)
+        for q in (self.path, self.path + ".json"):
+            os.remove(q)
+        return H, info
 
 
 def bench_ppr(di, torch, dev, nbatches=3):
@@ -221,24 +310,44 @@ def bench_ppr(di, torch, dev, nbatches=3):
         torch.cuda.synchronize()
         lat.append(time.perf_counter() - t0)
     h1 = torch.empty(g.n, dtype=torch.float64, device=dev)
-    for q in range(2):
-        G.query(seeds[q], 1e-6, H_out=h1)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for q in range(64):
-        G.query(seeds[q], 1e-6, H_out=h1)
-    torch.cuda.synchronize()
-    single = time.perf_counter() - t0
+    single = {}
+    for name, prec in (("fp64", di.DI_FP64), ("fp32_mixed", di.DI_FP32_MIXED)):
+        for q in range(2):
+            G.query(seeds[q], 1e-6, H_out=h1, prec=prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for q in range(64):
+            G.query(seeds[q], 1e-6, H_out=h1, prec=prec)
+        torch.cuda.synchronize()
+        single[name] = time.perf_counter() - t0
     # one more batch with the sweep kernels launched from the host between events: the split of device
     # time over scan, push-or-pull and finalize (the captured loop above runs the same kernels)
     _, _, stp = G.query_batch(seeds, 1e-6, H_out=H, profile=1)
+    # the autotuner for this width, then the same batches with its settings
+    t0 = time.perf_counter()
+    best, tried = G.autotune_batch(seeds, 1e-6)
+    tune_s = time.perf_counter() - t0
+    G.query_batch(seeds, 1e-6, H_out=H)
+    torch.cuda.synchronize()
+    tlat = []
+    for _ in range(nbatches):
+        t0 = time.perf_counter()
+        _, stq_t, sta_t = G.query_batch(seeds, 1e-6, H_out=H)
+        torch.cuda.synchronize()
+        tlat.append(time.perf_counter() - t0)
     G.close()
-    med = float(np.median(lat))
+    med, tmed = float(np.median(lat)), float(np.median(tlat))
     return {"workload": "R-MAT scale 20 (n=%d, L=%d), 64 queries x 1-32 seeds, d=0.85, per-query bound 1e-6" % (g.n, g.nnz),
             "batched_queries_per_s": 64 / med, "batch_ms": 1e3 * med, "sweeps": sta["sweeps"],
-            "max_bound": max(s["bound"] for s in stq), "single_fp64_queries_per_s": 64 / single,
-            "speedup": (64 / med) / (64 / single), "lane_dtype": "f32 fluid rows, f64 histories",
-            "kernel_ms": {k: round(v, 3) if isinstance(v, float) else v for k, v in stp["profile"].items()}}
+            "max_bound": max(s["bound"] for s in stq), "single_fp64_queries_per_s": 64 / single["fp64"],
+            "single_fp32_mixed_queries_per_s": 64 / single["fp32_mixed"],
+            "speedup": (64 / med) / (64 / single["fp64"]),
+            "speedup_same_precision": (64 / med) / (64 / single["fp32_mixed"]),
+            "lane_dtype": "f32 fluid rows, f64 histories",
+            "kernel_ms": {k: round(v, 3) if isinstance(v, float) else v for k, v in stp["profile"].items()},
+            "tuned": {"queries_per_s": 64 / tmed, "batch_ms": 1e3 * tmed, "vs_default": med / tmed,
+                      "max_bound": max(s["bound"] for s in stq_t), "converged": bool(sta_t["converged"]),
+                      "best": best, "candidates": len(tried), "tuning_s": tune_s}}
 
 
 def bench_update(di, torch, G, g, d, tol, fracs=(1e-4, 1e-3, 1e-2)):
@@ -285,14 +394,18 @@ def bench_selection(di, torch, graphs, tol):
     return out
 
 
-def bench_mixed(di, torch, scale=23, ds=(0.85, 0.99), tol=1e-7, ref_tol=1e-10):
-    """FP32-mixed against FP64 D-iteration on R-MAT (scale 23, edge factor 16, a,b,c = .57,.19,.19, duplicates
-    removed), V = 1/N, bound 1e-7, d = 0.85 and 0.99.  The FP64 solve to bound 1e-10 is the reference H_ref
-    (|X - H_ref|_1 <= 1e-10); the error of each result is |H - H_ref|_1 + 1e-10."""
+def bench_mixed(di, torch, zipf=None, scale=23, ds=(0.85, 0.99), tol=1e-7, ref_tol=1e-10):
+    """FP32-mixed against FP64 D-iteration.  R-MAT (scale 23, edge factor 16, a,b,c = .57,.19,.19,
+    duplicates removed), V = 1/N, bound 1e-7, d = 0.85 and 0.99, push only and with pull sweeps;
+    and the headline Zipf graph (`zipf` = (DiGraph, graph, workload)) at its bound.  The FP64
+    solve to bound 1e-10 is the reference H_ref (|X - H_ref|_1 <= 1e-10); the error of each
+    result is |H - H_ref|_1 + 1e-10.  The d = 0.85 R-MAT results are kept on the host in
+    `keep` so that the caller can add their distance to the oracle's solve."""
     import graphgen as gg
     g = gg.rmat_graph(scale, 16, seed=1)
     out = {"workload": "R-MAT scale %d (n=%d, L=%d), V=1/N, L1 bound %g, FP32-mixed vs FP64" % (scale, g.n, g.nnz, tol),
            "reference": "FP64 D-iteration to bound %g" % ref_tol, "runs": []}
+    keep = {}
     dev = torch.device("cuda")
     for d in ds:
         G = di.DiGraph(g.n, g.row_ptr, g.col_idx, d)
@@ -312,12 +425,33 @@ def bench_mixed(di, torch, scale=23, ds=(0.85, 0.99), tol=1e-7, ref_tol=1e-10):
                 run[name + suffix] = {"ms": 1e3 * st["seconds"], "edge_pushes_per_s": st["edges_pushed"] / st["seconds"],
                                       "sweeps": st["sweeps"], "edges": st["edges_pushed"], "bound": st["bound"],
                                       "l1_error_vs_reference": err}
+                if d == 0.85:
+                    keep[name + suffix] = H.cpu().numpy()
         run["fp32_speedup"] = run["fp64"]["ms"] / run["fp32_mixed"]["ms"]
         run["fp32_speedup_pull"] = run["fp64_pull"]["ms"] / run["fp32_mixed_pull"]["ms"]
         out["runs"].append(run)
         log(f"mixed precision d={d}: {run}")
         G.close()
-    return out
+    if zipf is not None:
+        Gz, gz, wz = zipf
+        Href = torch.empty(gz.n, dtype=torch.float64, device=dev)
+        H = torch.empty(gz.n, dtype=torch.float64, device=dev)
+        Gz.solve(wz["tol"], H_out=H, prec=di.DI_FP32_MIXED)
+        Gz.solve(ref_tol, H_out=Href)
+        zr = {"workload": "the headline Zipf graph (n=%d, L=%d), d=%g, bound %g" % (gz.n, gz.nnz, wz["d"], wz["tol"])}
+        for name, prec in (("fp64", di.DI_FP64), ("fp32_mixed", di.DI_FP32_MIXED)):
+            ms = []
+            for _ in range(5):
+                _, st = Gz.solve(wz["tol"], H_out=H, prec=prec)
+                ms.append(1e3 * st["seconds"])
+            torch.cuda.synchronize()
+            zr[name] = {"ms": float(np.median(ms)), "edge_pushes_per_s": st["edges_pushed"] / (1e-3 * float(np.median(ms))),
+                        "sweeps": st["sweeps"], "edges": st["edges_pushed"], "bound": st["bound"],
+                        "l1_error_vs_reference": float((H - Href).abs().sum().item()) + ref_tol}
+        zr["fp32_speedup"] = zr["fp64"]["ms"] / zr["fp32_mixed"]["ms"]
+        out["zipf24"] = zr
+        log(f"mixed precision zipf: {zr}")
+    return out, keep
 
 
 def serve_trace(gs, rate, duration, seed):
@@ -335,7 +469,7 @@ def serve_run(di, srv, gs, ring, trace, tol, warm):
     """Open-loop replay through the server; latency = result in host memory - scheduled arrival."""
     arr, gof, seeds = trace
     arrival = {}
-    lat = []
+    lat, arr_counted = [], []
     per_g = [[] for _ in gs]
     t0 = di.di_clock() + 0.02
     i, n = 0, len(arr)
@@ -351,6 +485,7 @@ def serve_run(di, srv, gs, ring, trace, tol, warm):
             a, k, counted = arrival.pop(c["ticket"])
             if counted:
                 lat.append(c["t_done"] - a)
+                arr_counted.append(a)
                 per_g[k].append(c["t_done"] - a)
                 t_first = a if t_first is None else min(t_first, a)
                 t_last = c["t_done"] if t_last is None else max(t_last, c["t_done"])
@@ -359,15 +494,30 @@ def serve_run(di, srv, gs, ring, trace, tol, warm):
         if now - t0 > 300:
             raise RuntimeError("serving trace did not drain in 300 s")
     lat = np.array(lat) * 1e3
+    dur = max(1e-9, t_last - t_first) if len(lat) else 1.0
+    h = len(lat) // 2  # completions in arrival order of the counted queries: first and second half
+    order = np.argsort(np.array(arr_counted)) if arr_counted else np.zeros(0, int)
+    lat_o = lat[order] if len(order) == len(lat) else lat
     return {"offered_per_s": n / arr[-1] if n else 0.0, "queries": int(len(lat)),
-            "queries_per_s": len(lat) / (t_last - t_first) if len(lat) else 0.0,
+            "queries_per_s": len(lat) / dur if len(lat) else 0.0,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "p99_ms_halves": [float(np.percentile(lat_o[:h], 99)) if h else None,
+                              float(np.percentile(lat_o[h:], 99)) if h else None],
             "p50_ms_per_graph": [round(float(np.percentile(np.array(v) * 1e3, 50)), 2) if v else None
-                                 for v in per_g]}
+                                 for v in per_g],
+            "served_per_s_per_graph": [round(len(v) / dur, 1) for v in per_g]}
 
 
-def serve_one_at_a_time(di, Gs, gs, ring, trace, tol, count):
-    """The same arrival stream's first `count` queries, one at a time (di_query, FP64) in arrival order."""
+def stable(r, offered):
+    """An open-loop run kept up with its arrivals: it served at least 95% of the offered rate and
+    its p99 latency did not grow over the stream (second half within 1.5x the first, + 50 ms)."""
+    a, b = r["p99_ms_halves"]
+    return a is not None and r["queries_per_s"] >= 0.95 * offered and b <= 1.5 * a + 50.0
+
+
+def serve_one_at_a_time(di, Gs, gs, ring, trace, tol, count, prec=None):
+    """The same arrival stream's first `count` queries, one at a time (di_query, FP64 unless prec
+    says otherwise) in arrival order."""
     arr, gof, seeds = trace
     lat, t_first, t_end = [], None, None
     t0 = di.di_clock() + 0.02
@@ -376,7 +526,7 @@ def serve_one_at_a_time(di, Gs, gs, ring, trace, tol, count):
         while di.di_clock() < a:
             pass
         k = int(gof[i])
-        Gs[k].query(seeds[i], tol, H_out=ring[k][0])
+        Gs[k].query(seeds[i], tol, H_out=ring[k][0], prec=di.DI_FP64 if prec is None else prec)
         t_end = di.di_clock()
         lat.append(t_end - a)
         t_first = a if t_first is None else t_first
@@ -386,7 +536,8 @@ def serve_one_at_a_time(di, Gs, gs, ring, trace, tol, count):
 
 
 def bench_serve(di, torch, scales=(16, 18, 20, 21, 22, 23), tol=1e-6, budget=120e9,
-                runs=((2000.0, 2.0), (100.0, 4.0)), warm=0.5, base_count=100):
+                runs=((2000.0, 2.0), (100.0, 4.0)), warm=0.5, base_count=100,
+                ladder_rates=(150.0, 250.0, 350.0, 450.0, 600.0, 800.0), ladder_s=4.0):
     """Continuous batching over six R-MAT graphs (edge factor 16, d = 0.85), Poisson arrivals, graph uniform,
     seed sets U{1..16}, per-query bound 1e-6, lane pools under a 120 GB budget; every H copied to pinned host
     memory.  Queries arriving in the first `warm` seconds of a trace are not counted."""
@@ -407,14 +558,43 @@ def bench_serve(di, torch, scales=(16, 18, 20, 21, 22, 23), tol=1e-6, budget=120
             trace = serve_trace(gs, rate, dur, int(rate))
             out["poisson_%d" % int(rate)] = serve_run(di, srv, gs, ring, trace, tol, warm)
             log(f"serving at {rate} q/s: {out['poisson_%d' % int(rate)]}")
+        # the highest offered rate the server keeps up with (a ladder of short streams)
+        ladder = []
+        for rate in ladder_rates:
+            r = serve_run(di, srv, gs, ring, serve_trace(gs, rate, ladder_s, 1000 + int(rate)), tol, warm)
+            ok = stable(r, r["offered_per_s"])
+            ladder.append({"offered_per_s": round(r["offered_per_s"], 1), "queries_per_s": round(r["queries_per_s"], 1),
+                           "p50_ms": round(r["p50_ms"], 2), "p99_ms": round(r["p99_ms"], 2),
+                           "p99_ms_halves": [round(x, 2) for x in r["p99_ms_halves"]], "stable": ok})
+            log(f"serving ladder {rate} q/s: {ladder[-1]}")
+            if not ok:
+                break
+        good = [x for x in ladder if x["stable"]]
+        out["sustainable"] = {"queries_per_s": good[-1]["queries_per_s"] if good else None,
+                              "p99_ms": good[-1]["p99_ms"] if good else None,
+                              "offered_per_s": good[-1]["offered_per_s"] if good else None,
+                              "rule": "highest offered rate of the ladder whose %g-s stream served >= 95%% of it "
+                                      "with the second half's p99 within 1.5x the first's + 50 ms" % ladder_s,
+                              "ladder": ladder}
         out["device_ms_per_graph"] = [round(srv.stats(k)["device_ms"], 1) for k in range(len(gs))]
     trace = serve_trace(gs, runs[0][0], runs[0][1], int(runs[0][0]))
     out["one_at_a_time"] = serve_one_at_a_time(di, Gs, gs, ring, trace, tol, base_count)
     out["one_at_a_time"]["what"] = "first %d queries of the %d q/s trace, di_query FP64 one by one" % (
         base_count, int(runs[0][0]))
+    out["one_at_a_time_fp32_mixed"] = serve_one_at_a_time(di, Gs, gs, ring, trace, tol, base_count,
+                                                          prec=di.DI_FP32_MIXED)
+    out["one_at_a_time_fp32_mixed"]["what"] = "the same queries, di_query FP32-mixed (the lanes' precision)"
     for G in Gs:
         G.close()
     return out
+
+
+def run_config(args, w, g, world):
+    """The `config` object of both arms' JSON lines: the workload and the solve's settings."""
+    return {"workload": w["label"], "n": g.n, "nnz": g.nnz, "d": w["d"], "tol": w["tol"], "beta": args.beta,
+            "direction": "push, pull on dense sweeps" if args.direction else "push",
+            "parallelism": "replicas" if world > 1 else "single-gpu",
+            "l2": "inputs larger than L2 (CSR + F + H of the solve exceed 129 MB)"}
 
 
 def run_reference(args, w):
@@ -429,6 +609,7 @@ def run_reference(args, w):
     vals, secs = [], []
     for k in range(args.warmup + args.steps):
         cb = cpu_baseline(g, w, cap)
+        cb.pop("_H")
         if k >= args.warmup:
             vals.append(cb["value"])
             secs.append(cb["seconds"])
@@ -436,7 +617,7 @@ def run_reference(args, w):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w["label"], "n": g.n, "nnz": g.nnz},
+            "config": run_config(args, w, g, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cb["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
@@ -469,6 +650,9 @@ def main():
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)
+    rank0 = dist_env()[0] == 0
+    # the oracle's config-3 solve runs on a host core while the GPU measurements run
+    orc_bg = OracleInBackground() if rank0 and not args.no_mixed and not args.no_cpu else None
 
     import torch
     import paper_1202_6158_gb300 as di
@@ -616,17 +800,38 @@ def main():
 
     mixed = None
     if rank == 0 and not args.no_mixed:
-        mixed = bench_mixed(di, torch)
+        mixed, keep = bench_mixed(di, torch, zipf=(G, g, w))
+        if orc_bg is not None:
+            Ho, info = orc_bg.result()
+            run = mixed["runs"][0]
+            if Ho is None:
+                run["oracle"] = {"unavailable": info}
+            else:
+                run["oracle"] = dict(info, what="the oracle's snapshot-sweep solve on one host core, same graph, "
+                                               "d=0.85, bound 1e-7")
+                for key, Hk in keep.items():
+                    run[key]["l1_error_vs_oracle"] = float(np.abs(Hk - Ho).sum())
+            log(f"mixed precision vs oracle: {run.get('oracle')}")
+            orc_bg = None
 
     serve = None
     if rank == 0 and not args.no_serve:
         serve = bench_serve(di, torch)
 
+    if orc_bg is not None:
+        orc_bg.result()  # nothing may run on the host cores while the CPU baselines are timed
     cpu = None
     if rank == 0 and not args.no_cpu:
         cap = args.cpu_pushes if args.cpu_pushes > 0 else 8 * g.n
         cpu = cpu_baseline(g, w, cap)
         cpu.pop("seconds", None)
+        Ho = cpu.pop("_H")
+        if cpu["converged"]:
+            # the headline device solve (the last timed step's H) against the oracle's full solve
+            cpu["headline_l1_error_vs_oracle"] = float(np.abs(H.cpu().numpy() - Ho).sum())
+        cpu.update(cpu_power_baselines(g, w))
+        cpu["cpu_model"] = cpu_model()
+        cpu["nproc"] = os.cpu_count()
 
     if rank == 0:
         value = tot_edges / (max_ms * 1e-3)
@@ -634,10 +839,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w["label"], "n": g.n, "nnz": g.nnz, "d": w["d"], "tol": tol, "beta": args.beta,
-                       "direction": "push, pull on dense sweeps" if args.direction else "push",
-                       "parallelism": "replicas" if world > 1 else "single-gpu",
-                       "l2": "inputs larger than L2 (CSR + F + H of the solve exceed 129 MB)"},
+            "config": run_config(args, w, g, world),
             "time_to_residual_ms": {"diter": max_ms / args.steps, "power": pms,
                                     "speedup_vs_power": pms / (max_ms / args.steps)},
             "diter": {"edges_per_solve": edges // args.steps, "sweeps": sweeps[-1], "bound": bound,

@@ -218,27 +218,71 @@ di_status di_solve_ex(di_graph *g, const di_solve_opts *opts, double *H_out, di_
  *   select            DI_SELECT_REF, _OP, _OP2 (Section 4.3)
  *   push_ctas_per_sm  2, 4, 8 (the push grid; never below the scan grid)
  *   direction         0, 1 (push only, or pull on dense sweeps)
+ * every combination of these, then, with the fastest of them, the cutoffs of the
+ * out-degree classes (cut1, cut2): a node with at most cut1 out-links is pushed by
+ * one thread, up to cut2 by a half-warp, and above that its row is cut into chunks
+ * spread over the CTAs; candidates (8, 1024) (the creation default), (4, 1024),
+ * (8, 256), (8, 4096) and (4, 256).
  * Every candidate's result is a valid solve (any choice converges, Section 2.2);
- * only the time differs.  The winning push_ctas_per_sm stays set on g; beta,
- * select and direction are returned for the caller to pass in di_solve_opts.
+ * only the time differs.  The winning push_ctas_per_sm and cutoffs stay set on g
+ * (the cutoffs are shared with di_query_batch and the server); beta, select and
+ * direction are returned for the caller to pass in di_solve_opts.
  *   best    receives the fastest candidate
  *   tried   host di_tune_result[cap] (may be NULL): every candidate in the order tried;
  *           *ntried receives their number
- * The cutoffs of the out-degree classes (8 and 1024 out-links) are fixed at
- * graph creation and are not tuned.
  */
 typedef struct {
     double beta;
     int32_t select;
     int32_t push_ctas_per_sm;
-    double ms;               /* device time of the candidate's solve */
+    double ms;               /* device time of the candidate's solve; -1 if it stopped at a limit */
     int64_t edges_pushed;
     int32_t sweeps;
     int32_t direction;       /* di_solve_opts.direction of the candidate */
+    int32_t cut1;            /* out-degree class cutoffs of the candidate */
+    int32_t cut2;
 } di_tune_result;
 
 di_status di_autotune(di_graph *g, const di_solve_opts *base, di_tune_result *best, di_tune_result *tried,
                       int32_t cap, int32_t *ntried);
+
+/*
+ * Autotuner of the batched personalized queries (di_query_batch) for the width of
+ * a batch of k queries.  Runs the batch (k, seed_ptr, seeds, w as for
+ * di_query_batch, per-query bound tol) once per candidate and keeps the fastest by
+ * device time, one setting at a time in this order, each with the best of the ones
+ * before it (a coordinate search):
+ *   cut1, cut2     the out-degree class cutoffs, as for di_autotune
+ *   beta           0.25, 0.5, 1 (T_q = beta R_q / n)
+ *   pull_share     2, 4, 8, 16: a sweep is dense (the next one pulls) when its
+ *                  selected nodes hold at least L / pull_share out-links
+ *   push_ctas_per_sm  2, 4, 8 (grid of the batched push and pull)
+ *   lanes          the narrowest row that holds k queries (4, 8, 16, 32 or 64), or
+ *                  the next wider one
+ * Every candidate is a complete batch; a candidate whose queries do not all reach
+ * tol never wins.  The winners stay set on g for batches of that width: later
+ * di_query_batch calls with the same lane width use them (a cache per graph and
+ * width; the cutoffs are shared with single solves and the server).
+ *   best   receives the fastest candidate; tried/cap/*ntried as for di_autotune.
+ * Errors: DI_EINVAL for the batch arguments as di_query_batch, DI_ENOTCONVERGED if
+ * no candidate converged.
+ */
+typedef struct {
+    double beta;
+    double ms;               /* device time of the candidate's batch; -1 if a query stopped at a limit */
+    double max_bound;        /* largest per-query bound |F_q|_1/(1-d) of the candidate */
+    int64_t edges_pushed;
+    int32_t sweeps;
+    int32_t lanes;           /* row width the batch ran with */
+    int32_t pull_share;
+    int32_t push_ctas_per_sm;
+    int32_t cut1;
+    int32_t cut2;
+} di_batch_tune_result;
+
+di_status di_autotune_batch(di_graph *g, int32_t k, const int32_t *seed_ptr, const int32_t *seeds, const double *w,
+                            double tol, di_batch_tune_result *best, di_batch_tune_result *tried, int32_t cap,
+                            int32_t *ntried);
 
 /*
  * Continue a solve after the graph changed (Section 3.2, updating equation).

@@ -16,6 +16,8 @@ Contents (each function cites the passage it follows):
 * :func:`selection_weights` -- the ALGO-OP / ALGO-OP2 weights of Section 4.3,
   used by ``select="op"`` / ``"op2"`` in :func:`run` and :func:`diter`.
 * :func:`transpose`, :func:`bins` -- in-link lists and degree bins.
+* :func:`power_omp`    -- the same MAT-ITER on all host cores (OpenMP, ``power_omp.c``,
+  a separate library): a timed CPU baseline, pinned to :func:`power` by the tests.
 * :mod:`oracle.ge`     -- dense Gaussian elimination of (I - dP)X = (1-d)V in FP64
   and in exact rationals (Section 2.1's fixed point written out).
 
@@ -56,6 +58,39 @@ def build(force: bool = False, out: str | None = None, defines: tuple = ()) -> s
     subprocess.run(cmd, check=True)
     os.replace(tmp, target)
     return target
+
+
+_OMP_SRC = os.path.join(_HERE, "power_omp.c")
+_OMP_LIB = os.path.join(_HERE, "libpower_omp.so")
+_omp = None
+
+
+def build_omp(force: bool = False) -> str:
+    """Compile ``power_omp.c`` with gcc and OpenMP (the timed multi-core CPU baseline)."""
+    if not force and os.path.exists(_OMP_LIB) and os.path.getmtime(_OMP_LIB) >= os.path.getmtime(_OMP_SRC):
+        return _OMP_LIB
+    fd, tmp = tempfile.mkstemp(suffix=".so", dir=_HERE)
+    os.close(fd)
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-Wall", "-fopenmp", "-o", tmp,
+           _OMP_SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _OMP_LIB)
+    return _OMP_LIB
+
+
+def load_omp():
+    global _omp
+    if _omp is None:
+        lib = ctypes.CDLL(build_omp())
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        f64p = ctypes.POINTER(ctypes.c_double)
+        lib.pomp_threads.argtypes = [ctypes.c_int]
+        lib.pomp_threads.restype = ctypes.c_int
+        lib.pomp_power.argtypes = [ctypes.c_int32, i32p, i32p, i32p, ctypes.c_double, f64p, ctypes.c_double,
+                                   ctypes.c_int64, f64p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
+        lib.pomp_power.restype = ctypes.c_int
+        _omp = lib
+    return _omp
 
 
 class Stats(ctypes.Structure):
@@ -229,6 +264,24 @@ def power(n, row_ptr, col_idx, d, V, tol, max_iter=100000, lib=None):
     delta = ctypes.c_double(0)
     rc = lib.orc_power(n, rpp, cip, d, _f64(V), tol, max_iter, _f64(X), ctypes.byref(it), ctypes.byref(delta))
     return X, int(it.value), float(delta.value), rc == 0
+
+
+def power_omp(n, in_ptr, in_src, outdeg_, d, V, tol, max_iter=100000, threads=0):
+    """MAT-ITER (Section 4) on `threads` host cores (0: all), as a pull over the in-link lists
+    in_ptr/in_src with out-degrees outdeg_; returns (X, iterations, last |X_n - X_{n-1}|_1, ok,
+    threads used)."""
+    lib = load_omp()
+    used = lib.pomp_threads(int(threads))
+    ip, ipp = _i32(in_ptr)
+    L = int(ip[-1])
+    isrc, isp = _i32(in_src if L else np.zeros(1, np.int32))
+    od, odp = _i32(outdeg_)
+    V = _vec(V, n)
+    X = np.empty(n, dtype=np.float64)
+    it = ctypes.c_int64(0)
+    delta = ctypes.c_double(0)
+    rc = lib.pomp_power(n, ipp, isp, odp, d, _f64(V), tol, max_iter, _f64(X), ctypes.byref(it), ctypes.byref(delta))
+    return X, int(it.value), float(delta.value), rc == 0, used
 
 
 def outdeg(n, row_ptr, lib=None):

@@ -19,10 +19,11 @@ import numpy as np
 
 from . import _lib
 from ._lib import (DI_EINVAL, DI_ENOMEM, DI_ENOTCONVERGED, DI_ETIMEOUT, DI_FP32_MIXED, DI_FP64, DI_OK, DiError, check,
-                   di_completion, di_profile, di_server_graph_stats, di_tune_result, di_solve_opts, di_stats, di_sweep_record, ptr)
+                   di_batch_tune_result, di_completion, di_profile, di_server_graph_stats, di_tune_result, di_solve_opts,
+                   di_stats, di_sweep_record, ptr)
 
 __all__ = ["DiGraph", "DiError", "DI_FP64", "DI_FP32_MIXED", "DI_OK", "DI_EINVAL", "DI_ENOTCONVERGED", "DI_ETIMEOUT",
-           "di_graph_create", "di_free", "di_solve", "di_solve_ex", "di_solve_update", "di_autotune", "di_query", "di_query_batch", "di_query_batch_ex", "di_power", "di_power_ex", "di_graph_export",
+           "di_graph_create", "di_free", "di_solve", "di_solve_ex", "di_solve_update", "di_autotune", "di_autotune_batch", "di_query", "di_query_batch", "di_query_batch_ex", "di_power", "di_power_ex", "di_graph_export",
            "di_get_trace", "di_get_state", "di_get_profile", "di_power_noalloc", "di_version", "di_selftest_wait", "load",
            "di_plan_lanes", "di_server_create", "di_server_lanes", "di_server_submit", "di_server_poll",
            "di_server_pending", "di_server_stats", "di_server_free", "di_clock", "DiServer"]
@@ -122,10 +123,8 @@ def di_query_batch(handle, seed_lists, tol, H_out, weights=None):
     return st_q, st_all
 
 
-def di_query_batch_ex(handle, seed_lists, tol, H_out, weights=None, profile=0):
-    """di_query_batch with the profiling switch: profile=1 launches the sweep kernels from the
-    host with events around them.  Returns (per-query stats, batch stats, profile dict or None).
-    """
+def _batch_arrays(seed_lists, weights):
+    """seed_ptr, seeds and weights (or None) of a batch, as the C calls take them."""
     k = len(seed_lists)
     seed_ptr = np.zeros(k + 1, np.int32)
     seed_ptr[1:] = np.cumsum([len(s) for s in seed_lists])
@@ -134,6 +133,27 @@ def di_query_batch_ex(handle, seed_lists, tol, H_out, weights=None, profile=0):
     w = None
     if weights is not None:
         w = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float64) for x in weights]), dtype=np.float64)
+    return seed_ptr, seeds, w
+
+
+def di_autotune_batch(handle, seed_lists, tol, weights=None, cap=64):
+    """Tune the batched loop for this batch's row width (class cutoffs, beta, dense-sweep share,
+    grid, width); returns (best, tried) as dicts.  The winners stay set on the graph."""
+    seed_ptr, seeds, w = _batch_arrays(seed_lists, weights)
+    best = di_batch_tune_result()
+    tried = (di_batch_tune_result * cap)()
+    n = ctypes.c_int32(0)
+    check(load().di_autotune_batch(handle, len(seed_lists), ptr(seed_ptr), ptr(seeds), ptr(w), float(tol),
+                                   ctypes.byref(best), tried, cap, ctypes.byref(n)))
+    return best.as_dict(), [tried[i].as_dict() for i in range(min(n.value, cap))]
+
+
+def di_query_batch_ex(handle, seed_lists, tol, H_out, weights=None, profile=0):
+    """di_query_batch with the profiling switch: profile=1 launches the sweep kernels from the
+    host with events around them.  Returns (per-query stats, batch stats, profile dict or None).
+    """
+    k = len(seed_lists)
+    seed_ptr, seeds, w = _batch_arrays(seed_lists, weights)
     st_q = (di_stats * max(k, 1))()
     st_all = di_stats()
     prof = di_profile()
@@ -250,6 +270,9 @@ class DiGraph:
         ww = np.ascontiguousarray(w, dtype=np.float64) if isinstance(w, (list, np.ndarray)) else w
         st = di_query(self.handle, s, ww, tol, H, prec)
         return H, st
+
+    def autotune_batch(self, seed_lists, tol, weights=None):
+        return di_autotune_batch(self.handle, seed_lists, tol, weights)
 
     def query_batch(self, seed_lists, tol, H_out=None, weights=None, profile=0):
         """Personalized queries solved together; returns (H [k, n], per-query stats, batch stats).

@@ -73,10 +73,20 @@ class di_completion(ctypes.Structure):
 class di_tune_result(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_double), ("select", ctypes.c_int32), ("push_ctas_per_sm", ctypes.c_int32),
                 ("ms", ctypes.c_double), ("edges_pushed", ctypes.c_int64), ("sweeps", ctypes.c_int32),
-                ("direction", ctypes.c_int32)]
+                ("direction", ctypes.c_int32), ("cut1", ctypes.c_int32), ("cut2", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+class di_batch_tune_result(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("ms", ctypes.c_double), ("max_bound", ctypes.c_double),
+                ("edges_pushed", ctypes.c_int64), ("sweeps", ctypes.c_int32), ("lanes", ctypes.c_int32),
+                ("pull_share", ctypes.c_int32), ("push_ctas_per_sm", ctypes.c_int32), ("cut1", ctypes.c_int32),
+                ("cut2", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class di_server_graph_stats(ctypes.Structure):
@@ -110,6 +120,8 @@ def load(path: str = LIB_PATH):
         "di_solve_ex": ([vp, ctypes.POINTER(di_solve_opts), vp, ctypes.POINTER(di_stats)], ctypes.c_int),
         "di_autotune": ([vp, ctypes.POINTER(di_solve_opts), ctypes.POINTER(di_tune_result), vp, i32,
                          ctypes.POINTER(i32)], ctypes.c_int),
+        "di_autotune_batch": ([vp, i32, vp, vp, vp, f64, ctypes.POINTER(di_batch_tune_result), vp, i32,
+                               ctypes.POINTER(i32)], ctypes.c_int),
         "di_solve_update": ([vp, vp, ctypes.POINTER(di_solve_opts), vp, ctypes.POINTER(di_stats)], ctypes.c_int),
         "di_query": ([vp, vp, vp, i32, f64, ctypes.c_int, vp, ctypes.POINTER(di_stats)], ctypes.c_int),
         "di_power": ([vp, f64, i32, vp, ctypes.POINTER(di_stats)], ctypes.c_int),

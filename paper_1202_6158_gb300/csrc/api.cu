@@ -104,6 +104,43 @@ static void free_graph(di_graph *g) {
     delete g;
 }
 
+// The arguments of a batch of k personalized queries, checked and copied to the host:
+// hp = seed_ptr[k+1], hs = seeds, hw = weights (empty when w is NULL).
+di_status batch_args(di_graph *g, int k, const int32_t *seed_ptr, const int32_t *seeds, const double *w, double tol,
+                     std::vector<int32_t> &hp, std::vector<int32_t> &hs, std::vector<double> &hw) {
+    if (k < 1 || k > kLanes) return set_error(DI_EINVAL, "a batch holds 1 to 64 queries");
+    if (!seed_ptr || !seeds) return set_error(DI_EINVAL, "seed_ptr and seeds are required");
+    if (!(tol > 0.0) || !std::isfinite(tol)) return set_error(DI_EINVAL, "tol must be finite and > 0");
+    cudaStream_t s = g->stream;
+    hp.assign((size_t)k + 1, 0);
+    DI_CUDA(cudaMemcpyAsync(hp.data(), seed_ptr, sizeof(int32_t) * (k + 1),
+                            is_device_ptr(seed_ptr) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
+    DI_CUDA(cudaStreamSynchronize(s));
+    if (hp[0] != 0) return set_error(DI_EINVAL, "seed_ptr[0] must be 0");
+    for (int q = 0; q < k; ++q)
+        if (hp[q + 1] <= hp[q]) return set_error(DI_EINVAL, "every query needs at least one seed");
+    const int total = hp[k];
+    hs.assign((size_t)total, 0);
+    hw.assign(w ? (size_t)total : 0, 0.0);
+    DI_CUDA(cudaMemcpyAsync(hs.data(), seeds, sizeof(int32_t) * total,
+                            is_device_ptr(seeds) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
+    if (w)
+        DI_CUDA(cudaMemcpyAsync(hw.data(), w, sizeof(double) * total,
+                                is_device_ptr(w) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
+    DI_CUDA(cudaStreamSynchronize(s));
+    for (int q = 0; q < k; ++q) {
+        double sum = 0.0;
+        for (int t = hp[q]; t < hp[q + 1]; ++t) {
+            if (hs[t] < 0 || hs[t] >= g->n) return set_error(DI_EINVAL, "seed id outside [0, n)");
+            const double wt = w ? hw[t] : 1.0;
+            if (!std::isfinite(wt) || wt < 0.0) return set_error(DI_EINVAL, "seed weights must be finite and >= 0");
+            sum += wt;
+        }
+        if (!(sum > 0.0)) return set_error(DI_EINVAL, "each query's seed weights need a positive sum");
+    }
+    return DI_OK;
+}
+
 static di_status check_graph(const di_graph *g) {
     if (!g) return set_error(DI_EINVAL, "graph is NULL");
     if (g->untrusted)
@@ -256,8 +293,8 @@ di_status di_graph_export(const di_graph *g, int32_t *perm, int32_t *outdeg, int
     if (r != DI_OK) return r;
     DI_CUDA(cudaStreamSynchronize(s));
     if (cuts) {
-        cuts[0] = kOutCut1;
-        cuts[1] = kOutCut2;
+        cuts[0] = g->cut1;
+        cuts[1] = g->cut2;
         cuts[2] = kInCut1;
         cuts[3] = kInCut2;
     }
@@ -377,37 +414,10 @@ di_status di_query_batch_ex(di_graph *g, int32_t k, const int32_t *seed_ptr, con
     if (profile != 0 && profile != 1) return set_error(DI_EINVAL, "profile must be 0 or 1");
     if (profile && !prof) return set_error(DI_EINVAL, "prof is NULL");
     if (di_status cr = check_graph(g); cr != DI_OK) return cr;
-    if (k < 1 || k > kLanes) return set_error(DI_EINVAL, "a batch holds 1 to 64 queries");
-    if (!seed_ptr || !seeds) return set_error(DI_EINVAL, "seed_ptr and seeds are required");
-    if (!(tol > 0.0) || !std::isfinite(tol)) return set_error(DI_EINVAL, "tol must be finite and > 0");
-    cudaStream_t s = g->stream;
-    std::vector<int32_t> hp((size_t)k + 1);
-    DI_CUDA(cudaMemcpyAsync(hp.data(), seed_ptr, sizeof(int32_t) * (k + 1),
-                            is_device_ptr(seed_ptr) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
-    DI_CUDA(cudaStreamSynchronize(s));
-    if (hp[0] != 0) return set_error(DI_EINVAL, "seed_ptr[0] must be 0");
-    for (int q = 0; q < k; ++q)
-        if (hp[q + 1] <= hp[q]) return set_error(DI_EINVAL, "every query needs at least one seed");
-    const int total = hp[k];
-    std::vector<int32_t> hs((size_t)total);
-    std::vector<double> hw(w ? (size_t)total : 0);
-    DI_CUDA(cudaMemcpyAsync(hs.data(), seeds, sizeof(int32_t) * total,
-                            is_device_ptr(seeds) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
-    if (w)
-        DI_CUDA(cudaMemcpyAsync(hw.data(), w, sizeof(double) * total,
-                                is_device_ptr(w) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
-    DI_CUDA(cudaStreamSynchronize(s));
-    for (int q = 0; q < k; ++q) {
-        double sum = 0.0;
-        for (int t = hp[q]; t < hp[q + 1]; ++t) {
-            if (hs[t] < 0 || hs[t] >= g->n) return set_error(DI_EINVAL, "seed id outside [0, n)");
-            const double wt = w ? hw[t] : 1.0;
-            if (!std::isfinite(wt) || wt < 0.0) return set_error(DI_EINVAL, "seed weights must be finite and >= 0");
-            sum += wt;
-        }
-        if (!(sum > 0.0)) return set_error(DI_EINVAL, "each query's seed weights need a positive sum");
-    }
-    return run_query_batch(g, k, hp.data(), hs.data(), w ? hw.data() : nullptr, tol, 0.5, 1000000, H_out,
+    std::vector<int32_t> hp, hs;
+    std::vector<double> hw;
+    if (di_status r = batch_args(g, k, seed_ptr, seeds, w, tol, hp, hs, hw); r != DI_OK) return r;
+    return run_query_batch(g, k, hp.data(), hs.data(), w ? hw.data() : nullptr, tol, -1.0, 1000000, H_out,
                            is_device_ptr(H_out), st_q, st_all, profile ? prof : nullptr);
 }
 

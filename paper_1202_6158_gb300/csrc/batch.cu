@@ -771,14 +771,20 @@ void launch_batch_sweep(di_graph *g, BatchPool *p, int S, cudaStream_t st, cudaG
                                                 p->pre, p->ticket, p->selb_node, p->selb_rows, p->spos, p->bq,
                                                 p->bctl, g->d);
     if (ev) cudaEventRecord(ev[1], st);
-    k_bpush<LPN><<<push_grid(g), kScanThreads, 0, st>>>(g->rec32, g->col_idx, p->Fb, p->Hb, S, g->region, p->pre, g->W,
-                                                        p->selb_node, p->selb_rows, nhot, p->bctl);
-    k_bpull<LPN><<<push_grid(g), kScanThreads, 0, st>>>(g->rec32, g->in_src, g->in_dst, g->inv_deg32, g->nnz, p->spos,
-                                                        p->Fb, p->Hb, S, g->region, p->pre, g->W, p->selb_node,
-                                                        p->selb_rows, p->bctl);
+    // the width's settings (di_autotune_batch): push and pull grid, and the share of all
+    // out-links that makes a sweep dense
+    constexpr int slot = LPN == 1 ? 0 : (LPN == 2 ? 1 : (LPN == 4 ? 2 : (LPN == 8 ? 3 : 4)));
+    const BatchTune &bt = g->btune[slot];
+    const int grid = std::max(g->G, bt.push_per_sm * g->num_sms);
+    k_bpush<LPN><<<grid, kScanThreads, 0, st>>>(g->rec32, g->col_idx, p->Fb, p->Hb, S, g->region, p->pre, g->W,
+                                                p->selb_node, p->selb_rows, nhot, p->bctl);
+    k_bpull<LPN><<<grid, kScanThreads, 0, st>>>(g->rec32, g->in_src, g->in_dst, g->inv_deg32, g->nnz, p->spos,
+                                                p->Fb, p->Hb, S, g->region, p->pre, g->W, p->selb_node,
+                                                p->selb_rows, p->bctl);
     if (ev) cudaEventRecord(ev[2], st);
     // rows of 4 lanes always push: their 16-byte reductions cost no more than the pull's gathers
-    const long long pull_edges = LPN >= 2 ? std::max(1LL, (g->nnz + kPullShareBatch - 1) / kPullShareBatch) : LLONG_MAX;
+    const long long share = std::max(1, bt.pull_share);
+    const long long pull_edges = LPN >= 2 ? std::max(1LL, (g->nnz + share - 1) / share) : LLONG_MAX;
     k_bfinalize<<<1, kLanes, 0, st>>>(g->n, pull_edges, p->bq, p->bctl, handle, in_graph);
     if (ev) cudaEventRecord(ev[3], st);
 }
@@ -957,9 +963,12 @@ di_status run_query_batch(di_graph *g, int k, const int *seed_ptr, const int *se
     BatchPool *p = g->bp;
     di_status r = pool_alloc(g, p, kLanes, s);
     if (r != DI_OK) return r;
-    // the narrowest row that holds the batch: 4, 8, 16, 32 or 64 queries
-    const int slot = lane_slot(k);
+    // the narrowest row that holds the batch (4, 8, 16, 32 or 64 queries), or the width the
+    // autotuner chose for it; beta < 0 takes that width's tuned threshold schedule
+    int slot = lane_slot(k);
+    if (g->btune[slot].exec_slot >= 0) slot = g->btune[slot].exec_slot;
     const int K = slot_width(slot);
+    if (beta < 0.0) beta = g->btune[slot].beta;
     r = pool_build_loop(g, p, slot);
     if (r != DI_OK) return r;
     const int n = g->n;

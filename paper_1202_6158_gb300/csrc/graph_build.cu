@@ -747,13 +747,8 @@ di_status build_graph(di_graph *g, const int *col_host) {
     DI_CUDA(cudaMallocAsync(&g->inv_deg32, sizeof(float) * (size_t)n, s));
     DI_CUDA(cudaMallocAsync(&g->rec64, sizeof(RowRec<double>) * (size_t)n, s));
     DI_CUDA(cudaMallocAsync(&g->rec32, sizeof(RowRec<float>) * (size_t)n, s));
-    k_out_bins<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, g->row_ptr, kOutCut1, kOutCut2, g->d, g->bin_of, g->cls,
-                                                           g->inv_deg, g->inv_deg32, g->rec64, g->rec32);
     {
         const int W = g->W;
-        int *cnt = nullptr;
-        DI_CUDA(cudaMallocAsync(&cnt, sizeof(int) * (kLists * (size_t)W + 1), s));
-        DI_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (kLists * (size_t)W + 1), s));
         DI_CUDA(cudaMallocAsync(&g->region, sizeof(int) * kLists * (size_t)(W + 1), s));
         DI_CUDA(cudaMallocAsync(&g->fcount, sizeof(int) * kLists * (size_t)W, s));
         DI_CUDA(cudaMemsetAsync(g->fcount, 0, sizeof(int) * kLists * (size_t)W, s));
@@ -761,28 +756,49 @@ di_status build_graph(di_graph *g, const int *col_host) {
         DI_CUDA(cudaMemsetAsync(g->pre, 0, sizeof(int) * kLists * (size_t)(W + 1), s));
         DI_CUDA(cudaMallocAsync(&g->ticket, sizeof(unsigned), s));
         DI_CUDA(cudaMemsetAsync(g->ticket, 0, sizeof(unsigned), s));
-        k_sub_counts<<<W, 256, 0, s>>>(n, g->chunk / kWarps, g->cls, cnt, W);
-        {
-            di_status r = exclusive_scan(cnt, cnt, (long long)kLists * W + 1, s);
-            if (r != DI_OK) return r;
-        }
-        k_region_layout<<<grid_for((long long)kLists * (W + 1), 256, g->num_sms), 256, 0, s>>>(W, cnt, g->region);
-        std::vector<int> h(kLists * (size_t)(W + 1));
-        cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(h.data(), g->region, sizeof(int) * h.size(), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        cudaFreeAsync(cnt, s);
-        if (e != cudaSuccess) return cuda_fail(e, "frontier regions");
-        long long prev = 0;
-        for (int L = 0; L < kLists; ++L) {
-            long long end = h[(size_t)L * (W + 1) + W];
-            g->bin_count[L] = (int)(end - prev);
-            prev = end;
-        }
+    }
+    {
+        di_status r = set_out_classes(g, kOutCut1, kOutCut2);
+        if (r != DI_OK) return r;
     }
 
     DI_CUDA(cudaGetLastError());
+    return DI_OK;
+}
+
+// Out-degree classes (0 dangling, 1 up to cut1 out-links, 2 up to cut2, 3 above), the packed
+// row records, and the per-warp frontier regions of the sweep scan for those classes.  Run at
+// creation and again when the autotuner changes the cutoffs; the buffers keep their sizes (the
+// regions of all classes together always hold n entries), so captured loops stay valid.
+di_status set_out_classes(di_graph *g, int cut1, int cut2) {
+    cudaStream_t s = g->stream;
+    const int n = g->n;
+    g->cut1 = cut1;
+    g->cut2 = cut2;
+    k_out_bins<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, g->row_ptr, cut1, cut2, g->d, g->bin_of, g->cls,
+                                                           g->inv_deg, g->inv_deg32, g->rec64, g->rec32);
+    const int W = g->W;
+    int *cnt = nullptr;
+    DI_CUDA(cudaMallocAsync(&cnt, sizeof(int) * (kLists * (size_t)W + 1), s));
+    DI_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (kLists * (size_t)W + 1), s));
+    k_sub_counts<<<W, 256, 0, s>>>(n, g->chunk / kWarps, g->cls, cnt, W);
+    {
+        di_status r = exclusive_scan(cnt, cnt, (long long)kLists * W + 1, s);
+        if (r != DI_OK) return r;
+    }
+    k_region_layout<<<grid_for((long long)kLists * (W + 1), 256, g->num_sms), 256, 0, s>>>(W, cnt, g->region);
+    std::vector<int> h(kLists * (size_t)(W + 1));
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), g->region, sizeof(int) * h.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(cnt, s);
+    if (e != cudaSuccess) return cuda_fail(e, "frontier regions");
+    long long prev = 0;
+    for (int L = 0; L < kLists; ++L) {
+        long long end = h[(size_t)L * (W + 1) + W];
+        g->bin_count[L] = (int)(end - prev);
+        prev = end;
+    }
     return DI_OK;
 }
 

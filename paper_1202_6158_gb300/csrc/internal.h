@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <vector>
 
 #include "../../include/diter.h"
 
@@ -177,6 +178,15 @@ struct PowerPartial {
 
 // interleaved query lanes with their own sweep scratch: the buffers of di_query_batch,
 // and of each graph a serving loop holds
+// settings of the batched loop for one row width, chosen by di_autotune_batch
+struct BatchTune {
+    double beta = 0.5;                 // T_q = beta R_q / n
+    int pull_share = (int)kPullShareBatch;  // a sweep is dense when its nodes hold >= L / pull_share out-links
+    int push_per_sm = 4;               // CTAs per SM of the batched push and pull kernels
+    int exec_slot = -1;                // the width to run batches of this width with (-1: the same)
+    int tuned = 0;
+};
+
 struct BatchPool {
     int cap_lanes = 0;                 // lanes per row the buffers hold
     int stride = 0;                    // floats between rows: 0 = the loop's width (a fresh batch packs its rows);
@@ -205,6 +215,8 @@ struct di_graph {
     int dev = 0;
     int num_sms = 152;
     int push_per_sm = 4;               // push CTAs per SM at least (the push grid never shrinks below the scan's)
+    int cut1 = diter::kOutCut1, cut2 = diter::kOutCut2;  // out-degree class cutoffs in use (set_out_classes)
+    diter::BatchTune btune[diter::kWidths];   // batched-query settings per row width (di_autotune_batch)
     bool untrusted = false;            // a scan wait timed out twice: copies may have landed late (DI_ETIMEOUT)
     cudaStream_t stream = nullptr;     // user stream
     cudaStream_t cap = nullptr;        // private stream used for graph capture
@@ -314,6 +326,9 @@ di_status pool_alloc(di_graph *g, BatchPool *p, int lanes, cudaStream_t s);
 void pool_free(BatchPool *p, cudaStream_t s);
 long long pool_bytes(const di_graph *g, int lanes);
 di_status pool_build_loop(di_graph *g, BatchPool *p, int slot);
+di_status set_out_classes(di_graph *g, int cut1, int cut2);
+di_status batch_args(di_graph *g, int k, const int32_t *seed_ptr, const int32_t *seeds, const double *w, double tol,
+                     std::vector<int32_t> &hp, std::vector<int32_t> &hs, std::vector<double> &hw);
 // row widths 4, 8, 16, 32, 64 lanes are slots 0..4: the narrowest that holds k lanes
 inline int lane_slot(int k) { return k <= 4 ? 0 : (k <= 8 ? 1 : (k <= 16 ? 2 : (k <= 32 ? 3 : 4))); }
 inline int slot_width(int slot) { return 4 << slot; }

@@ -13,8 +13,8 @@ import pytest
 from paper_1202_6158_gb300 import _lib
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-STRUCTS = ["di_stats", "di_solve_opts", "di_sweep_record", "di_profile", "di_tune_result", "di_completion",
-           "di_server_graph_stats"]
+STRUCTS = ["di_stats", "di_solve_opts", "di_sweep_record", "di_profile", "di_tune_result", "di_batch_tune_result",
+           "di_completion", "di_server_graph_stats"]
 
 
 def c_sizes():

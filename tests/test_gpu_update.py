@@ -200,12 +200,56 @@ def test_autotune_picks_a_valid_fastest_candidate(di):
     V = gg.uniform_v(n)
     with di.DiGraph(n, rp, ci, D) as G:
         best, tried = G.autotune(1e-10)
-        assert len(tried) == 90
+        # 90 combinations of beta, rule, grid and direction, then 4 more class cutoffs
+        assert len(tried) == 94
         assert best["ms"] == min(t["ms"] for t in tried if t["ms"] >= 0)
         assert {t["select"] for t in tried} == {0, 1, 2}
         assert {t["push_ctas_per_sm"] for t in tried} == {2, 4, 8}
         assert {t["direction"] for t in tried} == {0, 1}
+        assert {(t["cut1"], t["cut2"]) for t in tried} == {(8, 1024), (4, 1024), (8, 256), (8, 4096), (4, 256)}
+        assert all(t["ms"] >= 0 for t in tried)  # every candidate converged
+        # the winning cutoffs stay on the graph: its classes are the oracle's bins for them
+        ex = G.export()
+        assert list(ex["cuts"][:2]) == [best["cut1"], best["cut2"]]
+        bin_of, _, _ = oracle.bins(n, *relabel_rp(n, rp, ex["perm"]), [0, best["cut1"], best["cut2"]])
+        assert np.array_equal(ex["bin_of"], bin_of)
         # the tuned settings give a correct solve
         H, st = G.solve(1e-12, beta=best["beta"], select=best["select"], direction=best["direction"])
     r = oracle.diter(n, rp, ci, D, V, 1e-13, mode="sweep")
     assert np.abs(H - r.H).sum() <= st["bound"] + 1e-12
+
+
+def relabel_rp(n, rp, perm):
+    """(n, row pointers) of the CSR in the numbering perm (row r = input row perm[r])."""
+    deg = np.diff(rp)[np.asarray(perm)]
+    return (np.concatenate([[0], np.cumsum(deg)]).astype(np.int32),)
+
+
+@pytest.mark.parametrize("k", [8, 64])
+def test_autotune_batch_keeps_the_fastest_valid_candidate(di, k):
+    """di_autotune_batch: every candidate batch converges, the fastest is kept and stays set on
+    the graph, and a batch run with the tuned settings matches the oracle query by query
+    within max(bound) + 2e-6 (FP32 fluid rows)."""
+    g = gg.rmat_graph(13, 16, seed=5)
+    seeds = gg.seed_sets(g.n, k, 1, 16, seed=9)
+    tol = 1e-6
+    with di.DiGraph(g.n, g.row_ptr, g.col_idx, D) as G:
+        best, tried = G.autotune_batch(seeds, tol)
+        ok = [t for t in tried if t["ms"] >= 0]
+        assert len(ok) == len(tried) >= 12
+        assert all(t["max_bound"] <= tol for t in tried)
+        assert best["ms"] == min(t["ms"] for t in ok)
+        assert {t["pull_share"] for t in tried} == {2, 4, 8, 16}
+        assert {t["push_ctas_per_sm"] for t in tried} == {2, 4, 8}
+        assert {t["beta"] for t in tried} == {0.25, 0.5, 1.0}
+        widths = {t["lanes"] for t in tried}
+        assert widths == ({k, 2 * k} if k < 64 else {64})
+        ex = G.export()
+        assert list(ex["cuts"][:2]) == [best["cut1"], best["cut2"]]
+        H, st_q, st_all = G.query_batch(seeds, tol)
+        assert st_all["converged"] == 1
+    for q in (0, k // 2, k - 1):
+        V = np.zeros(g.n)
+        np.add.at(V, np.asarray(seeds[q]), 1.0 / len(seeds[q]))
+        r = oracle.diter(g.n, g.row_ptr, g.col_idx, D, V, 1e-12, mode="sweep")
+        assert np.abs(H[q] - r.H).sum() <= max(st_q[q]["bound"], r.l1F / (1 - D)) + 2e-6

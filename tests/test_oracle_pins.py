@@ -464,3 +464,25 @@ def test_threshold_schedule(sel):
         w, wscale = oracle.selection_weights(n, rp, ci, sel)
         S1 = np.flatnonzero(np.float32(np.abs(F0)) * w > np.float32(T[0] * wscale))
     assert cnt[0] == len(S1)
+
+
+# ------------------------------------------------ timed multi-core CPU baseline
+
+@pytest.mark.parametrize("threads", [1, 3])
+def test_power_omp_matches_power(threads):
+    """The OpenMP MAT-ITER (a pull over in-links) against orc_power (a push over out-links):
+    the same number of products and the same iterate to rounding, on a graph with dangling
+    nodes, multi-edges and self-loops; and both against elimination."""
+    n, rp, ci, V = _rand_case(31, n=300, p_dang=0.15, max_deg=9)
+    in_ptr, in_src = oracle.transpose(n, rp, ci)
+    deg = oracle.outdeg(n, rp)
+    X, it, delta, ok = oracle.power(n, rp, ci, D, V, 1e-13)
+    Xo, ito, deltao, oko, used = oracle.power_omp(n, in_ptr, in_src, deg, D, V, 1e-13, threads=threads)
+    assert ok and oko and used >= 1
+    assert abs(it - ito) <= 1
+    assert np.abs(X - Xo).sum() <= 1e-13
+    assert np.abs(ge.pagerank_dense(n, rp, ci, D, V) - Xo).sum() <= 1e-12
+    # a cut at k products gives the partial series, like orc_power
+    X3, _, _, _ = oracle.power(n, rp, ci, D, V, 1e-13, max_iter=3)
+    Xo3, it3, _, ok3, _ = oracle.power_omp(n, in_ptr, in_src, deg, D, V, 1e-13, max_iter=3, threads=threads)
+    assert it3 == 3 and not ok3 and np.abs(X3 - Xo3).max() <= 1e-15
