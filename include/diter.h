@@ -90,12 +90,13 @@ typedef struct {
                                 when the first pull is due (the loop pauses for it and resumes
                                 where it stopped), so graphs whose sweeps never turn dense pay
                                 nothing */
-    int32_t scan_wait_polls; /* polls of each bulk-copy wait of the sweep scan before the solve stops
-                                with DI_ETIMEOUT (0: 2^20; a small value makes a watchdog).  A warp
-                                that gave up then waits, with 2^20 polls, for its copies still in
-                                flight; if that wait gives up too, copies may land after the kernel
-                                returned, and every later call on the graph returns DI_ETIMEOUT
-                                until di_free */
+    int32_t scan_wait_polls; /* polls of each bulk-copy wait of the sweep scan, and of the push's
+                                staging of hub rows, before the solve stops with DI_ETIMEOUT (0:
+                                2^20; a small value makes a watchdog).  A warp or CTA that gave up
+                                then waits, with 2^20 polls, for its copies still in flight; if
+                                that wait gives up too, copies may land after the kernel returned,
+                                and every later call on the graph returns DI_ETIMEOUT until
+                                di_free */
 } di_solve_opts;
 
 /*

@@ -703,7 +703,10 @@ di_status build_graph(di_graph *g, const int *col_host) {
         // relabeled CSR
         int *rp2 = nullptr, *ci2 = nullptr;
         DI_CUDA(cudaMallocAsync(&rp2, sizeof(int) * (size_t)(n + 1), s));
-        DI_CUDA(cudaMallocAsync(&ci2, sizeof(int) * (size_t)std::max<long long>(L, 1), s));
+        // kColPad ints past the last link: the push stages hub rows with 16-byte bulk copies
+        // whose end is rounded up
+        DI_CUDA(cudaMallocAsync(&ci2, sizeof(int) * (size_t)(std::max<long long>(L, 1) + kColPad), s));
+        DI_CUDA(cudaMemsetAsync(ci2 + std::max<long long>(L, 1), 0, sizeof(int) * kColPad, s));
         k_perm_deg<<<grid_for((long long)n + 1, 256, g->num_sms), 256, 0, s>>>(n, g->perm, g->row_ptr, rp2);
         di_status r = exclusive_scan(rp2, rp2, (long long)n + 1, s);
         if (r != DI_OK) return r;

@@ -41,6 +41,7 @@ constexpr int kInCut2 = 2048;           // <= cut2, above
 constexpr int kTraceCap = 4096;         // sweep records kept when tracing
 constexpr int kExactEvery = 4;          // the scan sums |F|_1 exactly every this many sweeps
 constexpr int kHubChunk = 2048;         // out-links per chunk of a hub row (class 3) in the push
+constexpr int kColPad = 4;              // zero ints allocated past the last column index
 constexpr int kHubCap = 2048;           // hub entries a push CTA enumerates in shared memory per sweep
 constexpr int kHotSlots = 256;          // most-linked-to targets accumulated in shared memory by the push
 constexpr int kHotMinInDeg = 32;        // a target needs at least this many in-links to get a slot

@@ -12,6 +12,8 @@
 namespace diter {
 namespace {
 
+constexpr int kPushWaitLimit = 1 << 20;  // polls of a stage's mbarrier while draining after a timeout
+
 // One elementary step F_j += w.  Edges into the hot targets (the most-linked-to
 // nodes, internal ids 0..n_hot-1) are summed in the CTA's shared memory: on
 // power-law graphs a single target can receive a few percent of all pushes, and
@@ -156,10 +158,13 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
     __shared__ long long s_red[kWarps];
     __shared__ int s_idx;
     __shared__ int s_hpos[kHubCap], s_hpre[kHubCap + 1], s_scan[kWarps];
+    __shared__ __align__(128) int s_hcol[2][kHubChunk + 8];  // two stages of a hub chunk's column indices
+    __shared__ __align__(8) unsigned long long s_hbar[2];
     if (st->done || st->pull) return;
     for (int t = threadIdx.x; t < kHotSlots; t += kScanThreads) hot[t] = (FT)0;
     __syncthreads();
-    const unsigned long long pol = evict_last_policy();
+    const unsigned long long pol = evict_last_policy(), pol_col = evict_first_policy();
+    const int wait_polls = st->wait_polls;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nwarps = gridDim.x * kWarps, gw = blockIdx.x * kWarps + w;
     const int *pre3 = pre + 3 * (W + 1);
@@ -298,23 +303,83 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
             }
         }
     }
-    // class 3: chunks of kHubChunk out-links of the hub rows, strided over the CTAs
-    if (tot3 > 0 && tot3 <= kHubCap) {
+    // class 3: chunks of kHubChunk out-links of the hub rows, strided over the CTAs.  Each
+    // chunk's column indices are staged in shared memory by a 1-D bulk copy (TMA) into one of
+    // two stages, the next chunk's copy in flight while a chunk is pushed.  (Setting up the
+    // table and the first copies before the other classes, so that the copies land while they
+    // run, was slower: the table's dependent loads then delay every warp.)
+    const bool hubs = tot3 > 0 && tot3 <= kHubCap;
+    int ne = tot3, nch = 0, mine = 0;
+    const int first = blockIdx.x, step = gridDim.x;
+    // chunk i of this CTA: its row, start and length (the same in every thread)
+    auto locate = [&](int i, int &beg, int &len, FT &wv) {
+        const int t = first + i * step;
+        int lo = 0, hi = ne;  // the entry holding chunk t: the last e with s_hpre[e] <= t
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s_hpre[mid] <= t) lo = mid; else hi = mid;
+        }
+        const Sel<FT> e = sel[s_hpos[lo]];
+        const RowRec<FT> rr = rec[e.node];
+        const int off = (t - s_hpre[lo]) * kHubChunk;
+        beg = rr.beg + off;
+        len = min(kHubChunk, rr.deg - off);
+        wv = e.sent * rr.inv;
+    };
+    // a copy covers [beg & ~3, (beg + len + 3) & ~3): 16-byte aligned at both ends, inside the
+    // column array (kColPad ints are allocated past its end)
+    auto issue = [&](int k, int beg, int len) {
+        const int a0 = beg & ~3, a1 = (beg + len + 3) & ~3;
+        const unsigned bar = smem_addr(&s_hbar[k]);
+        mbar_expect_tx(bar, 4u * (unsigned)(a1 - a0));
+        bulk_copy(smem_addr(s_hcol[k]), col_idx + a0, 4u * (unsigned)(a1 - a0), bar, pol_col);
+    };
+    int cb[2] = {0, 0}, cl[2] = {0, 0};
+    FT cw[2] = {(FT)0, (FT)0};
+    if (hubs) {
         __syncthreads();
-        int ne = tot3;
-        const int nch = hub_chunks(rec, sel, region, fcount, W, ne, s_hpos, s_hpre, s_scan);
-        for (int t = blockIdx.x; t < nch; t += gridDim.x) {
-            int lo = 0, hi = ne;  // the entry holding chunk t: the last e with s_hpre[e] <= t
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (s_hpre[mid] <= t) lo = mid; else hi = mid;
+        nch = hub_chunks(rec, sel, region, fcount, W, ne, s_hpos, s_hpre, s_scan);
+        mine = first < nch ? (nch - 1 - first) / step + 1 : 0;  // chunks of this CTA
+        if (threadIdx.x == 0 && mine > 0) {
+            mbar_init(smem_addr(&s_hbar[0]), 1);
+            mbar_init(smem_addr(&s_hbar[1]), 1);
+            fence_barrier_init();
+        }
+        __syncthreads();
+        for (int i = 0; i < 2 && i < mine; ++i) {
+            locate(i, cb[i], cl[i], cw[i]);
+            if (threadIdx.x == 0) issue(i, cb[i], cl[i]);
+        }
+    }
+    if (hubs) {
+        bool ok = true;
+        int i = 0;
+        for (; i < mine; ++i) {
+            const int k = i & 1;
+            ok = __all_sync(kFull, mbar_wait(smem_addr(&s_hbar[k]), (unsigned)((i >> 1) & 1), wait_polls));
+            if (__syncthreads_or(!ok)) {
+                ok = false;
+                break;
             }
-            const Sel<FT> e = sel[s_hpos[lo]];
-            const RowRec<FT> rr = rec[e.node];
-            const int off = (t - s_hpre[lo]) * kHubChunk;
-            const int len = min(kHubChunk, rr.deg - off);
-            if (threadIdx.x == 0) edges += len;
-            push_row_lanes(col_idx, F, hot, n_hot, rr.beg + off, len, e.sent * rr.inv, threadIdx.x, kScanThreads, pol);
+            const int *cols = s_hcol[k] + (cb[k] & 3);
+            if (threadIdx.x == 0) edges += cl[k];
+            for (int j = threadIdx.x; j < cl[k]; j += kScanThreads) push_one(F, hot, n_hot, cols[j], cw[k], pol);
+            __syncthreads();  // every thread is done with stage k
+            if (i + 2 < mine) {
+                locate(i + 2, cb[k], cl[k], cw[k]);
+                if (threadIdx.x == 0) {
+                    fence_proxy_async();
+                    issue(k, cb[k], cl[k]);
+                }
+            }
+        }
+        if (!ok && threadIdx.x == 0) {
+            // a copy did not land in time: wait (bounded again) for the ones still in flight,
+            // then stop the solve (DI_ETIMEOUT), or mark the graph untrusted if they never land
+            bool drained = true;
+            for (int j = i; j < mine && j < i + 2; ++j)
+                drained &= mbar_wait(smem_addr(&s_hbar[j & 1]), (unsigned)((j >> 1) & 1), kPushWaitLimit);
+            atomicOr(reinterpret_cast<unsigned long long *>(&part[blockIdx.x % G].err), drained ? 1ull : 3ull);
         }
     }
     // the CTA's sums for the hot targets go to F once

@@ -414,11 +414,17 @@ def test_bounded_wait_gives_up(di):
     assert st["converged"] == 1
 
 
-def test_scan_wait_watchdog_keeps_results_valid(di):
+@pytest.mark.parametrize("family", ["uniform", "zipf_hubs"])
+def test_scan_wait_watchdog_keeps_results_valid(di, family):
     """With one poll per bulk-copy wait (a watchdog far shorter than a DRAM load) every solve
     either converges to the oracle's answer or stops with DI_ETIMEOUT; a wait that ran out
-    leaves the graph and the context usable."""
-    g = gg.uniform_graph(1 << 18, 20, seed=5)
+    leaves the graph and the context usable.  The Zipf graph has rows above 1024 out-links,
+    whose chunks the push stages with bulk copies behind the same bounded waits."""
+    if family == "uniform":
+        g = gg.uniform_graph(1 << 18, 20, seed=5)
+    else:
+        g = gg.zipf_graph(1 << 16, kmax=20000, seed=5)
+        assert int(np.diff(g.row_ptr).max()) > 2 * 2048
     V = gg.uniform_v(g.n)
     r = oracle.diter(g.n, g.row_ptr, g.col_idx, D, V, 1e-10, mode="sweep", beta=BETA)
     with di.DiGraph(g.n, g.row_ptr, g.col_idx, D) as G:
@@ -432,4 +438,22 @@ def test_scan_wait_watchdog_keeps_results_valid(di):
             G.solve(1e-8, beta=BETA, scan_wait_polls=-1)
         H, st = G.solve(1e-10, beta=BETA)
     assert st["converged"] == 1
+    assert np.abs(H - r.H).sum() <= max(st["bound"], r.l1F / (1 - D)) + 1e-12
+
+
+def test_more_hubs_than_the_chunk_table(di):
+    """2500 nodes with 1100 out-links each: the first sweep selects more class-3 rows than the
+    push's chunk table holds (2048), so it pushes them a CTA per row; later sweeps select
+    fewer and cut them into chunks.  Same sweeps, elementary steps and H as the oracle."""
+    rng = np.random.default_rng(12)
+    n = 4000
+    edges = [(i, int(j)) for i in range(2500) for j in rng.choice(n, 1100, replace=False)]
+    rp, ci = graphs.csr(n, edges)
+    V = gg.uniform_v(n)
+    tol = 1e-10
+    H, F, st, tr = _solve(di, n, rp, ci, tol, trace=1)
+    r = oracle.diter(n, rp, ci, D, V, tol, mode="sweep", beta=BETA)
+    assert st["converged"] == 1
+    assert tr[0]["pushed"] == 2500
+    assert st["sweeps"] == r.sweeps and st["edges_pushed"] == r.edges
     assert np.abs(H - r.H).sum() <= max(st["bound"], r.l1F / (1 - D)) + 1e-12
