@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(kScanThreads) k_bscan(int wchunk, int S, float
     float l1[4] = {0.f, 0.f, 0.f, 0.f}, rem[4] = {0.f, 0.f, 0.f, 0.f};
     int sel4[4] = {0, 0, 0, 0};
     int nsel = 0;
+    int hub_chunks = 0;  // chunks of the hub rows this lane listed (group leaders only)
     const bool pull = ctl->pull != 0;  // the push kernel reads the lists, the pull kernel the positions
     const int nsteps = wchunk / NPS;
     // kBScanDepth steps of rows in flight per warp (a register ring, unrolled so it stays in registers)
@@ -158,7 +159,8 @@ __global__ void __launch_bounds__(kScanThreads) k_bscan(int wchunk, int S, float
             const int s = s0 + dd;
             const long long node = wbeg + (long long)NPS * s + h;
             const float4 cur = buf[dd];
-            const int ccur = cb[dd];
+            const int cbyte = cb[dd];               // class byte: 2 + chunks for a hub row
+            const int ccur = class_of_byte(cbyte);
             if (s + kBScanDepth < nsteps) {
                 buf[dd] = *reinterpret_cast<const float4 *>(Fb + (node + (long long)NPS * kBScanDepth) * S + 4 * lq);
                 cb[dd] = cls[node + (long long)NPS * kBScanDepth];
@@ -183,6 +185,7 @@ __global__ void __launch_bounds__(kScanThreads) k_bscan(int wchunk, int S, float
                 if (ccur == L) pos = run[L] + __popc(bits & lt & ~gmask & ((1u << (h * LPN)) - 1u));
                 run[L] += __popc(bits);
             }
+            if (leader && act && ccur == 3) hub_chunks += cbyte - 2;
             if (act) {
                 const float f = ccur == 0 ? 1.f : omd;  // a dangling node's fluid leaves entirely (Section 3.3)
 #pragma unroll
@@ -197,9 +200,11 @@ __global__ void __launch_bounds__(kScanThreads) k_bscan(int wchunk, int S, float
             if (pull && lq == 0) spos[node] = act ? pos : -1;
         }
     }
+    hub_chunks = __reduce_add_sync(kFull, hub_chunks);
     if (lane == 0) {
 #pragma unroll
         for (int L = 0; L < kLists; ++L) fcount[L * W + g] = run[L] - start[L];
+        fcount[kChunkRow * W + g] = hub_chunks;
     }
     // per-query sums: the groups of a warp, then the CTA, then one atomic per query
 #pragma unroll
@@ -288,40 +293,60 @@ template <int LPN>
 __global__ void __launch_bounds__(kScanThreads, 4) k_bpush(const RowRec<float> *__restrict__ rec,
                                                         const int *__restrict__ col_idx, float *__restrict__ Fb,
                                                         double *__restrict__ Hb, int S, const int *__restrict__ region,
-                                                        const int *__restrict__ pre, int W,
+                                                        const int *__restrict__ pre,
+                                                        const int *__restrict__ fcount, int W,
                                                         const int *__restrict__ sel_node,
                                                         const float *__restrict__ sel_rows, int n_hot,
                                                         BatchCtl *__restrict__ ctl) {
     constexpr int K = 4 * LPN, GPC = kScanThreads / LPN;   // lane groups per CTA
     __shared__ float hot[kBatchHot * K];
     __shared__ long long s_red[kWarps];
-    __shared__ int s_idx;
     if (ctl->all_done || ctl->pull) return;
     for (int t = threadIdx.x; t < kBatchHot * K; t += kScanThreads) hot[t] = 0.f;
     __syncthreads();
     const int grp = threadIdx.x / LPN, lq = threadIdx.x % LPN;
     const int ngrp = gridDim.x * GPC, ggrp = blockIdx.x * GPC + grp;
     long long edges = 0;  // out-links of the pushed nodes
-    // class 3: the whole CTA per node, each lane group taking every GPC-th out-link
+    // class 3: the hub rows, cut into chunks of at most kHubChunk out-links; CTA b takes the
+    // contiguous chunk range [b nch / grid, (b+1) nch / grid), each lane group taking every GPC-th
+    // out-link of a chunk.  The chunks are numbered sub-chunk by sub-chunk through the prefix sums
+    // of the scan's per-warp chunk counts, then entry by entry; a row's first chunk also adds its
+    // fluid row to H.
     {
-        const int *p3 = pre + 3 * (W + 1);
-        const int tot = __ldg(p3 + W);
-        for (int t = blockIdx.x; t < tot; t += gridDim.x) {
-            if (threadIdx.x == 0) {
-                const int gs = find_sub(p3, W, t);
-                s_idx = region[3 * (W + 1) + gs] + (t - __ldg(p3 + gs));
+        const int *pch = pre + kChunkRow * (W + 1), *r3 = region + 3 * (W + 1), *f3 = fcount + 3 * W;
+        const int nch = __ldg(pch + W);
+        const int c0 = (int)((long long)blockIdx.x * nch / gridDim.x);
+        const int c1 = (int)((long long)(blockIdx.x + 1) * nch / gridDim.x);
+        if (c0 < c1) {
+            // the walk's state is the same in every thread (broadcast loads)
+            int gs = find_sub(pch, W, c0);
+            int e = __ldg(r3 + gs), e_end = e + __ldcg(f3 + gs), cum = __ldg(pch + gs);
+            int node = sel_node[e];
+            RowRec<float> rr = rec[node];
+            int nc = hub_chunk_count(rr.deg);
+            for (int c = c0; c < c1; ++c) {
+                while (c >= cum + nc) {
+                    cum += nc;
+                    if (++e >= e_end) {
+                        do {
+                            ++gs;
+                        } while (__ldcg(f3 + gs) == 0);
+                        e = __ldg(r3 + gs);
+                        e_end = e + __ldcg(f3 + gs);
+                    }
+                    node = sel_node[e];
+                    rr = rec[node];
+                    nc = hub_chunk_count(rr.deg);
+                }
+                const int clen = hub_chunk_len(rr.deg, nc), j = c - cum;
+                const int off = j * clen, len = min(clen, rr.deg - off);
+                const float4 row = *reinterpret_cast<const float4 *>(sel_rows + (long long)e * K + 4 * lq);
+                if (grp == 0) {
+                    if (j == 0) bpush_h(Hb, S, node, lq, row);  // H once per row
+                    if (lq == 0) edges += len;
+                }
+                bpush_row<K>(rr.beg + off, len, rr.inv, row, lq, col_idx, Fb, S, hot, n_hot, grp, GPC);
             }
-            __syncthreads();
-            const int pos = s_idx;
-            __syncthreads();
-            const int node = sel_node[pos];
-            const float4 row = *reinterpret_cast<const float4 *>(sel_rows + (long long)pos * K + 4 * lq);
-            const RowRec<float> rr = rec[node];
-            if (grp == 0) {  // H once
-                bpush_h(Hb, S, node, lq, row);
-                if (lq == 0) edges += rr.deg;
-            }
-            bpush_row<K>(rr.beg, rr.deg, rr.inv, row, lq, col_idx, Fb, S, hot, n_hot, grp, GPC);
         }
     }
     // class 2: a warp per node, its 32/LPN lane groups taking every (32/LPN)-th out-link.  The
@@ -776,8 +801,8 @@ void launch_batch_sweep(di_graph *g, BatchPool *p, int S, cudaStream_t st, cudaG
     constexpr int slot = LPN == 1 ? 0 : (LPN == 2 ? 1 : (LPN == 4 ? 2 : (LPN == 8 ? 3 : 4)));
     const BatchTune &bt = g->btune[slot];
     const int grid = std::max(g->G, bt.push_per_sm * g->num_sms);
-    k_bpush<LPN><<<grid, kScanThreads, 0, st>>>(g->rec32, g->col_idx, p->Fb, p->Hb, S, g->region, p->pre, g->W,
-                                                p->selb_node, p->selb_rows, nhot, p->bctl);
+    k_bpush<LPN><<<grid, kScanThreads, 0, st>>>(g->rec32, g->col_idx, p->Fb, p->Hb, S, g->region, p->pre,
+                                                p->fcount, g->W, p->selb_node, p->selb_rows, nhot, p->bctl);
     k_bpull<LPN><<<grid, kScanThreads, 0, st>>>(g->rec32, g->in_src, g->in_dst, g->inv_deg32, g->nnz, p->spos,
                                                 p->Fb, p->Hb, S, g->region, p->pre, g->W, p->selb_node,
                                                 p->selb_rows, p->bctl);
@@ -872,7 +897,7 @@ long long pool_bytes(const di_graph *g, int lanes) {
     const long long rows = (long long)g->G * g->chunk, n = g->n, L = g->nnz;
     // the graph's in-link CSR, its bins and in_dst, unless an earlier call built them
     const long long tr = (g->transposed ? 0 : 4 * (n + 1) + 4 * L + 8 * n + 4 * (n + 1)) + (g->in_dst ? 0 : 4 * L);
-    return lanes * (4 * rows + 12 * n) + 4 * n + 4 * rows + (long long)sizeof(int) * kLists * (2 * g->W + 1) +
+    return lanes * (4 * rows + 12 * n) + 4 * n + 4 * rows + (long long)sizeof(int) * kCountRows * (2 * g->W + 1) +
            (long long)(sizeof(BatchQ) * kLanes + sizeof(BatchCtl)) + 256 + tr;
 }
 
@@ -890,8 +915,8 @@ di_status pool_alloc(di_graph *g, BatchPool *p, int lanes, cudaStream_t s) {
     DI_CUDA(cudaMallocAsync(&p->selb_rows, sizeof(float) * lanes * (size_t)g->n, s));
     DI_CUDA(cudaMallocAsync(&p->selb_node, sizeof(int) * (size_t)g->n, s));
     DI_CUDA(cudaMallocAsync(&p->spos, sizeof(int) * (size_t)rows, s));
-    DI_CUDA(cudaMallocAsync(&p->fcount, sizeof(int) * kLists * (size_t)g->W, s));
-    DI_CUDA(cudaMallocAsync(&p->pre, sizeof(int) * kLists * (size_t)(g->W + 1), s));
+    DI_CUDA(cudaMallocAsync(&p->fcount, sizeof(int) * kCountRows * (size_t)g->W, s));
+    DI_CUDA(cudaMallocAsync(&p->pre, sizeof(int) * kCountRows * (size_t)(g->W + 1), s));
     DI_CUDA(cudaMallocAsync(&p->ticket, sizeof(unsigned), s));
     DI_CUDA(cudaMallocAsync(&p->bq, sizeof(BatchQ) * kLanes, s));
     DI_CUDA(cudaMallocAsync(&p->bctl, sizeof(BatchCtl), s));

@@ -122,13 +122,13 @@ __device__ __forceinline__ unsigned ld_stream(const unsigned *a, unsigned long l
 // Each thread sums a contiguous run of sub-chunks for every list, one block scan
 // covers the four lists, then each thread writes its run.
 // s_c: kCap ints of shared memory to stage the counts in
-// lists first_list..kLists-1 (the others are left as they are)
+// rows first_list..kCountRows-1: the lists, then the hub chunk counts (the others are left as they are)
 __device__ void prefix_counts_staged(const int *__restrict__ fcount, int W, int *__restrict__ pre, int *s_c,
                                      const int kCap, int first_list = 0) {
     __shared__ int s_w[kWarps];
     __shared__ int s_carry;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int L = first_list; L < kLists; ++L) {
+    for (int L = first_list; L < kCountRows; ++L) {
         if (threadIdx.x == 0) s_carry = 0;
         for (int base = 0; base < W; base += kCap) {
             const int m = min(kCap, W - base);

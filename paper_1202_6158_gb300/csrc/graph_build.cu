@@ -103,7 +103,7 @@ __global__ void k_out_bins(int n, const int *__restrict__ row_ptr, int cut1, int
         const int deg = row_ptr[i + 1] - beg;
         int b = deg == 0 ? 0 : (deg <= cut1 ? 1 : (deg <= cut2 ? 2 : 3));
         bin_of[i] = b;
-        cls[i] = (unsigned char)b;
+        cls[i] = (unsigned char)(b < 3 ? b : 2 + hub_chunk_count(deg));
         double w = deg ? d / (double)deg : 0.0;
         inv_deg[i] = w;
         inv_deg32[i] = (float)w;
@@ -127,7 +127,7 @@ __global__ void k_sub_counts(int n, int wchunk, const unsigned char *__restrict_
     __syncthreads();
     const long long beg = (long long)blockIdx.x * wchunk, end = min((long long)n, beg + wchunk);
     int l[kLists] = {0, 0, 0, 0};
-    for (long long i = beg + threadIdx.x; i < end; i += blockDim.x) l[cls[i]] += 1;
+    for (long long i = beg + threadIdx.x; i < end; i += blockDim.x) l[class_of_byte(cls[i])] += 1;
     for (int L = 0; L < kLists; ++L) atomicAdd(&c[L], l[L]);
     __syncthreads();
     if (threadIdx.x < kLists) cnt[threadIdx.x * W + blockIdx.x] = c[threadIdx.x];
@@ -753,10 +753,10 @@ di_status build_graph(di_graph *g, const int *col_host) {
     {
         const int W = g->W;
         DI_CUDA(cudaMallocAsync(&g->region, sizeof(int) * kLists * (size_t)(W + 1), s));
-        DI_CUDA(cudaMallocAsync(&g->fcount, sizeof(int) * kLists * (size_t)W, s));
-        DI_CUDA(cudaMemsetAsync(g->fcount, 0, sizeof(int) * kLists * (size_t)W, s));
-        DI_CUDA(cudaMallocAsync(&g->pre, sizeof(int) * kLists * (size_t)(W + 1), s));
-        DI_CUDA(cudaMemsetAsync(g->pre, 0, sizeof(int) * kLists * (size_t)(W + 1), s));
+        DI_CUDA(cudaMallocAsync(&g->fcount, sizeof(int) * kCountRows * (size_t)W, s));
+        DI_CUDA(cudaMemsetAsync(g->fcount, 0, sizeof(int) * kCountRows * (size_t)W, s));
+        DI_CUDA(cudaMallocAsync(&g->pre, sizeof(int) * kCountRows * (size_t)(W + 1), s));
+        DI_CUDA(cudaMemsetAsync(g->pre, 0, sizeof(int) * kCountRows * (size_t)(W + 1), s));
         DI_CUDA(cudaMallocAsync(&g->ticket, sizeof(unsigned), s));
         DI_CUDA(cudaMemsetAsync(g->ticket, 0, sizeof(unsigned), s));
     }
@@ -769,7 +769,8 @@ di_status build_graph(di_graph *g, const int *col_host) {
     return DI_OK;
 }
 
-// Out-degree classes (0 dangling, 1 up to cut1 out-links, 2 up to cut2, 3 above), the packed
+// Out-degree classes (0 dangling, 1 up to cut1 out-links, 2 up to cut2, 3 above; the class byte
+// of a class-3 node is 2 + the number of chunks its row is pushed in), the packed
 // row records, and the per-warp frontier regions of the sweep scan for those classes.  Run at
 // creation and again when the autotuner changes the cutoffs; the buffers keep their sizes (the
 // regions of all classes together always hold n entries), so captured loops stay valid.

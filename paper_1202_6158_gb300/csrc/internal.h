@@ -8,7 +8,8 @@
 //   row_ptr int32[n+1], col_idx int32[L]        out-link CSR in internal ids
 //   hot_ids int32[n_hot]                        input ids of the hot targets = internal 0..n_hot-1
 //   in_ptr  int32[n+1], in_src  int32[L]        in-link CSR, sources ascending
-//   bin_of  int32[n], cls uint8[npad]           out-degree class (0 dangling, 1 thread, 2 warp, 3 CTA)
+//   bin_of  int32[n], cls uint8[npad]           out-degree class (0 dangling, 1 thread, 2 warp, 3 hub
+//                                               row; a hub's class byte is 2 + its chunk count)
 //   F64 / F32  [n padded to 4]                  fluid F (one of the two per solve)
 //   H       double[n]                           history H
 //   sel     Sel[n]                              per-sweep selected nodes (id, sent); list L of
@@ -32,7 +33,9 @@ constexpr int kScanTile = kScanThreads * kScanVec;
 constexpr int kWarps = kScanThreads / 32;  // warps per scan / push CTA; each owns a sub-chunk
 constexpr int kStep = 256;              // nodes a warp reads per step (8 per lane)
 constexpr int kChunkAlign = kWarps * kStep;  // scan chunks are multiples of 8 warp steps
-constexpr int kLists = 4;               // selected nodes: 0 dangling, 1 thread, 2 warp, 3 CTA per source
+constexpr int kLists = 4;               // selected nodes: 0 dangling, 1 thread, 2 warp, 3 chunked hub rows
+constexpr int kChunkRow = kLists;       // row of fcount / pre holding each sub-chunk's hub chunk count
+constexpr int kCountRows = kLists + 1;  // rows of fcount / pre: the lists, then the hub chunks
 constexpr int kMaxScanBlocks = 152 * 8; // 8 CTAs per SM on 152 SMs
 constexpr int kOutCut1 = 8;             // out-degree <= cut1: one thread per source
 constexpr int kOutCut2 = 1024;          // out-degree <= cut2: one warp per source; above: whole CTA
@@ -40,9 +43,9 @@ constexpr int kInCut1 = 8;              // in-degree classes reported by di_grap
 constexpr int kInCut2 = 2048;           // <= cut2, above
 constexpr int kTraceCap = 4096;         // sweep records kept when tracing
 constexpr int kExactEvery = 4;          // the scan sums |F|_1 exactly every this many sweeps
-constexpr int kHubChunk = 2048;         // out-links per chunk of a hub row (class 3) in the push
+constexpr int kHubChunk = 1024;         // out-links per chunk of a hub row (class 3) in the push
+constexpr int kMaxHubChunks = 253;      // chunks of one hub row at most (its class byte is 2 + chunks)
 constexpr int kColPad = 4;              // zero ints allocated past the last column index
-constexpr int kHubCap = 2048;           // hub entries a push CTA enumerates in shared memory per sweep
 constexpr int kHotSlots = 256;          // most-linked-to targets accumulated in shared memory by the push
 constexpr int kHotMinInDeg = 32;        // a target needs at least this many in-links to get a slot
 
@@ -179,6 +182,16 @@ struct PowerPartial {
 
 // interleaved query lanes with their own sweep scratch: the buffers of di_query_batch,
 // and of each graph a serving loop holds
+// A hub row (class 3) is pushed in chunks: ceil(deg / kHubChunk) of them, at most kMaxHubChunks,
+// of equal length ceil(deg / chunks).  The class byte of a hub node is 2 + its chunk count, so the
+// sweep scans count the chunks of the rows they list without reading the row records.
+__host__ __device__ inline int hub_chunk_count(int deg) {
+    const int c = (deg + kHubChunk - 1) / kHubChunk;
+    return c < kMaxHubChunks ? c : kMaxHubChunks;
+}
+__host__ __device__ inline int hub_chunk_len(int deg, int chunks) { return (deg + chunks - 1) / chunks; }
+__host__ __device__ inline int class_of_byte(int c) { return c < 3 ? c : 3; }
+
 // settings of the batched loop for one row width, chosen by di_autotune_batch
 struct BatchTune {
     double beta = 0.5;                 // T_q = beta R_q / n
@@ -246,8 +259,9 @@ struct di_graph {
     int chunk = 0;                     // nodes per scan CTA (multiple of kChunkAlign)
     int W = 0;                         // warp sub-chunks, G * kWarps, chunk / kWarps nodes each
     int *region = nullptr;             // [kLists][W+1]: offset of each list's entries per sub-chunk
-    int *fcount = nullptr;             // [kLists][W]: entries written per sub-chunk in the last sweep
-    int *pre = nullptr;                // [kLists][W+1]: exclusive prefix of fcount, per list (last scan CTA)
+    int *fcount = nullptr;             // [kCountRows][W]: entries written per sub-chunk in the last sweep, per
+                                       // list, then the chunks of the hub rows listed
+    int *pre = nullptr;                // [kCountRows][W+1]: exclusive prefix of fcount per row (last scan CTA)
     unsigned *ticket = nullptr;        // finished scan CTAs of the current sweep
     void *sel = nullptr;               // Sel<FT>[n]: the selected nodes of a sweep
     double *F64 = nullptr;

@@ -59,81 +59,61 @@ __device__ __forceinline__ void push_row_lanes(const int *__restrict__ col_idx, 
     if (t < deg) push_one(F, hot, n_hot, __ldg(col_idx + beg + t), w, pol);
 }
 
-// Enumerate the class-3 (hub) entries of the sweep and cut their rows into chunks of
-// kHubChunk out-links: every CTA builds the same table in shared memory -- the list
-// position of each entry (s_pos) and the exclusive prefix sums of the chunk counts
-// (s_pre, te + 1 values) -- from the per-warp list counts of the scan.  Thread t takes the
-// sub-chunks t, t + 256, ...; entries are numbered thread by thread, so the enumeration
-// is the same in every CTA.  te is the class's list total (the caller checks te <= kHubCap);
-// it receives the number of entries in the table.  Returns the number of chunks (valid in
-// every thread).
+// Walks the hub chunks [c0, c1) of a sweep in order (every thread of a CTA holds the same
+// state).  Chunks are numbered sub-chunk by sub-chunk through the prefix sums of the scan's per
+// warp chunk counts (pch), then entry by entry within a sub-chunk's list-3 region; an entry's
+// chunk count is in its Sel record.  A chunk is a stretch of one hub row: start, length and
+// the weight d*sent/outdeg of that row.
 template <typename FT>
-__device__ int hub_chunks(const RowRec<FT> *__restrict__ rec, const Sel<FT> *__restrict__ sel,
-                          const int *__restrict__ region, const int *__restrict__ fcount, int W, int &te,
-                          int *s_pos, int *s_pre, int *s_scan) {
-    const int *r3 = region + 3 * (W + 1), *f3 = fcount + 3 * W;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    // 1. entries per thread, an exclusive block scan, then each thread lists its entries
-    int ents = 0;
-#pragma unroll 4
-    for (int gg = threadIdx.x; gg < W; gg += kScanThreads) ents += __ldcg(f3 + gg);
-    int x = ents;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(kFull, x, o);
-        if (lane >= o) x += y;
+struct HubWalk {
+    const RowRec<FT> *rec;
+    const Sel<FT> *sel;
+    const int *r3, *f3, *pch;
+    int W, g, e, e_end, cum, nc, beg, deg, clen;
+    FT w;
+    __device__ void load_entry() {
+        const Sel<FT> x = sel[e];
+        const RowRec<FT> rr = rec[x.node];
+        nc = x.pad;
+        beg = rr.beg;
+        deg = rr.deg;
+        clen = hub_chunk_len(deg, nc);
+        w = x.sent * rr.inv;
     }
-    if (lane == 31) s_scan[w] = x;
-    __syncthreads();
-    int oe = x - ents, listed = 0;
-    for (int k = 0; k < kWarps; ++k) {
-        oe += k < w ? s_scan[k] : 0;
-        listed += s_scan[k];
-    }
-    te = min(te, listed);  // the same count as the list total; never more than the table holds
-    if (ents) {
-        for (int gg = threadIdx.x; gg < W; gg += kScanThreads) {
-            const int c = __ldcg(f3 + gg);
-            const int b = c ? __ldg(r3 + gg) : 0;
-            for (int k = 0; k < c; ++k, ++oe)
-                if (oe < te) s_pos[oe] = b + k;
+    // position on chunk c (the first chunk this CTA takes)
+    __device__ void start(int c) {
+        g = find_sub(pch, W, c);
+        e = __ldg(r3 + g);
+        e_end = e + __ldcg(f3 + g);
+        cum = __ldg(pch + g);
+        load_entry();
+        while (cum + nc <= c) {  // the sub-chunk's entries hold chunk c
+            cum += nc;
+            ++e;
+            load_entry();
         }
     }
-    __syncthreads();
-    // 2. chunks of every entry
-    for (int e = threadIdx.x; e < te; e += kScanThreads) {
-        const int deg = rec[sel[s_pos[e]].node].deg;
-        s_pre[e] = (deg + kHubChunk - 1) / kHubChunk;
+    // the next chunk after c - 1: the same entry, the next entry, or the first of a later sub-chunk
+    __device__ void advance_to(int c) {
+        while (c >= cum + nc) {
+            cum += nc;
+            if (++e >= e_end) {
+                do {
+                    ++g;
+                } while (__ldcg(f3 + g) == 0);
+                e = __ldg(r3 + g);
+                e_end = e + __ldcg(f3 + g);
+            }
+            load_entry();
+        }
     }
-    __syncthreads();
-    // 3. exclusive prefix over the chunk counts: a contiguous run per thread, then a block scan
-    const int per = (te + kScanThreads - 1) / kScanThreads;
-    const int e0 = min(te, (int)threadIdx.x * per), e1 = min(te, e0 + per);
-    int run = 0;
-    for (int e = e0; e < e1; ++e) run += s_pre[e];
-    x = run;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(kFull, x, o);
-        if (lane >= o) x += y;
+    __device__ void chunk(int c, int &cb, int &cl, FT &cw) const {
+        const int off = (c - cum) * clen;
+        cb = beg + off;
+        cl = min(clen, deg - off);
+        cw = w;
     }
-    __syncthreads();  // every thread has read s_scan of step 1
-    if (lane == 31) s_scan[w] = x;
-    __syncthreads();
-    int off = x - run, total = 0;
-    for (int k = 0; k < kWarps; ++k) {
-        off += k < w ? s_scan[k] : 0;
-        total += s_scan[k];
-    }
-    for (int e = e0; e < e1; ++e) {
-        const int c = s_pre[e];
-        s_pre[e] = off;
-        off += c;
-    }
-    if (threadIdx.x == 0) s_pre[te] = total;
-    __syncthreads();
-    return total;
-}
+};
 
 // The push.  The selected nodes with children of each class are numbered 0..total-1
 // through the prefix sums of the scan.  The middle class (a warp per node) is strided
@@ -156,10 +136,8 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
                                                              const SolveState *__restrict__ st) {
     __shared__ FT hot[kHotSlots];
     __shared__ long long s_red[kWarps];
-    __shared__ int s_idx;
-    __shared__ int s_hpos[kHubCap], s_hpre[kHubCap + 1], s_scan[kWarps];
-    __shared__ __align__(128) int s_hcol[2][kHubChunk + 8];  // two stages of a hub chunk's column indices
-    __shared__ __align__(8) unsigned long long s_hbar[2];
+    __shared__ __align__(128) int s_hcol[kWarps][kHubChunk + 8];  // a hub chunk's column indices, per warp
+    __shared__ __align__(8) unsigned long long s_hbar[kWarps];
     if (st->done || st->pull) return;
     for (int t = threadIdx.x; t < kHotSlots; t += kScanThreads) hot[t] = (FT)0;
     __syncthreads();
@@ -167,25 +145,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
     const int wait_polls = st->wait_polls;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nwarps = gridDim.x * kWarps, gw = blockIdx.x * kWarps + w;
-    const int *pre3 = pre + 3 * (W + 1);
     long long edges = 0;
-    const int tot3 = __ldg(pre3 + W);
-    if (tot3 > kHubCap) {
-        // more hubs than the chunk table holds (dense sweeps of hub-rich graphs): the whole
-        // CTA per node, nodes strided over the CTAs
-        for (int t = blockIdx.x; t < tot3; t += gridDim.x) {
-            if (threadIdx.x == 0) {
-                const int gs = find_sub(pre3, W, t);
-                s_idx = region[3 * (W + 1) + gs] + (t - __ldg(pre3 + gs));
-            }
-            __syncthreads();
-            const Sel<FT> e = sel[s_idx];
-            __syncthreads();
-            const RowRec<FT> rr = rec[e.node];
-            if (threadIdx.x == 0) edges += rr.deg;
-            push_row_lanes(col_idx, F, hot, n_hot, rr.beg, rr.deg, e.sent * rr.inv, threadIdx.x, kScanThreads, pol);
-        }
-    }
     // classes 2 and 1: each warp takes an even range of ranks of the class's list (ranks
     // number the list entries over all sub-chunks, so the split is even however the selected
     // nodes fall over the sub-chunks); a lane finds the sub-chunk of its rank from the
@@ -303,83 +263,83 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
             }
         }
     }
-    // class 3: chunks of kHubChunk out-links of the hub rows, strided over the CTAs.  Each
-    // chunk's column indices are staged in shared memory by a 1-D bulk copy (TMA) into one of
-    // two stages, the next chunk's copy in flight while a chunk is pushed.  (Setting up the
-    // table and the first copies before the other classes, so that the copies land while they
-    // run, was slower: the table's dependent loads then delay every warp.)
-    const bool hubs = tot3 > 0 && tot3 <= kHubCap;
-    int ne = tot3, nch = 0, mine = 0;
-    const int first = blockIdx.x, step = gridDim.x;
-    // chunk i of this CTA: its row, start and length (the same in every thread)
-    auto locate = [&](int i, int &beg, int &len, FT &wv) {
-        const int t = first + i * step;
-        int lo = 0, hi = ne;  // the entry holding chunk t: the last e with s_hpre[e] <= t
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (s_hpre[mid] <= t) lo = mid; else hi = mid;
-        }
-        const Sel<FT> e = sel[s_hpos[lo]];
-        const RowRec<FT> rr = rec[e.node];
-        const int off = (t - s_hpre[lo]) * kHubChunk;
-        beg = rr.beg + off;
-        len = min(kHubChunk, rr.deg - off);
-        wv = e.sent * rr.inv;
-    };
-    // a copy covers [beg & ~3, (beg + len + 3) & ~3): 16-byte aligned at both ends, inside the
-    // column array (kColPad ints are allocated past its end)
-    auto issue = [&](int k, int beg, int len) {
-        const int a0 = beg & ~3, a1 = (beg + len + 3) & ~3;
-        const unsigned bar = smem_addr(&s_hbar[k]);
-        mbar_expect_tx(bar, 4u * (unsigned)(a1 - a0));
-        bulk_copy(smem_addr(s_hcol[k]), col_idx + a0, 4u * (unsigned)(a1 - a0), bar, pol_col);
-    };
-    int cb[2] = {0, 0}, cl[2] = {0, 0};
-    FT cw[2] = {(FT)0, (FT)0};
-    if (hubs) {
-        __syncthreads();
-        nch = hub_chunks(rec, sel, region, fcount, W, ne, s_hpos, s_hpre, s_scan);
-        mine = first < nch ? (nch - 1 - first) / step + 1 : 0;  // chunks of this CTA
-        if (threadIdx.x == 0 && mine > 0) {
-            mbar_init(smem_addr(&s_hbar[0]), 1);
-            mbar_init(smem_addr(&s_hbar[1]), 1);
-            fence_barrier_init();
-        }
-        __syncthreads();
-        for (int i = 0; i < 2 && i < mine; ++i) {
-            locate(i, cb[i], cl[i], cw[i]);
-            if (threadIdx.x == 0) issue(i, cb[i], cl[i]);
-        }
-    }
-    if (hubs) {
-        bool ok = true;
-        int i = 0;
-        for (; i < mine; ++i) {
-            const int k = i & 1;
-            ok = __all_sync(kFull, mbar_wait(smem_addr(&s_hbar[k]), (unsigned)((i >> 1) & 1), wait_polls));
-            if (__syncthreads_or(!ok)) {
-                ok = false;
-                break;
+    // class 3: the hub rows, cut into chunks of at most kHubChunk out-links.  CTA b takes the
+    // contiguous chunk range [b nch / grid, (b+1) nch / grid) and its warps take every 8th chunk
+    // of it.  A chunk's column indices are staged in the warp's shared memory by a 1-D bulk copy
+    // (TMA); the next chunk is located (its list entry and row record) while the copy is in
+    // flight.  A CTA per hub row, or the whole CTA on one chunk at a time, left the chunks'
+    // dependent loads on the critical path: slower on R-MAT, whose dense sweeps list thousands
+    // of hub rows.
+    {
+        const int *pch = pre + kChunkRow * (W + 1);
+        const int nch = __ldg(pch + W);
+        const int cb0 = (int)((long long)blockIdx.x * nch / gridDim.x);
+        const int cb1 = (int)((long long)(blockIdx.x + 1) * nch / gridDim.x);
+        int c = cb0 + w;
+        if (c < cb1) {
+            HubWalk<FT> hw{rec, sel, region + 3 * (W + 1), fcount + 3 * W, pch, W};
+            hw.start(c);
+            const unsigned bar = smem_addr(&s_hbar[w]);
+            int *stage = s_hcol[w];
+            // a copy covers [beg & ~3, (beg + len + 3) & ~3): 16-byte aligned at both ends, inside
+            // the column array (kColPad ints are allocated past its end); a chunk longer than the
+            // stage (a row of more than kMaxHubChunks * kHubChunk links) is read directly instead
+            auto issue = [&](int beg, int len) {
+                if (len > kHubChunk) {
+                    mbar_expect_tx(bar, 0u);
+                    return;
+                }
+                const int a0 = beg & ~3, a1 = (beg + len + 3) & ~3;
+                mbar_expect_tx(bar, 4u * (unsigned)(a1 - a0));
+                bulk_copy(smem_addr(stage), col_idx + a0, 4u * (unsigned)(a1 - a0), bar, pol_col);
+            };
+            if (lane == 0) {
+                mbar_init(bar, 1);
+                fence_barrier_init();
             }
-            const int *cols = s_hcol[k] + (cb[k] & 3);
-            if (threadIdx.x == 0) edges += cl[k];
-            for (int j = threadIdx.x; j < cl[k]; j += kScanThreads) push_one(F, hot, n_hot, cols[j], cw[k], pol);
-            __syncthreads();  // every thread is done with stage k
-            if (i + 2 < mine) {
-                locate(i + 2, cb[k], cl[k], cw[k]);
-                if (threadIdx.x == 0) {
-                    fence_proxy_async();
-                    issue(k, cb[k], cl[k]);
+            __syncwarp();
+            int cb, cl;
+            FT cw;
+            hw.chunk(c, cb, cl, cw);
+            if (lane == 0) issue(cb, cl);
+            bool ok = true;
+            unsigned phase = 0;
+            while (c < cb1) {
+                const int nx = c + kWarps;
+                int nb = 0, nl = 0;
+                FT nw = (FT)0;
+                if (nx < cb1) {  // the next chunk's entry and record, while this copy lands
+                    hw.advance_to(nx);
+                    hw.chunk(nx, nb, nl, nw);
+                }
+                ok = __all_sync(kFull, mbar_wait(bar, phase, wait_polls));
+                if (!ok) break;
+                phase ^= 1u;
+                if (lane == 0) edges += cl;
+                if (cl > kHubChunk) {
+                    push_row_lanes(col_idx, F, hot, n_hot, cb, cl, cw, lane, 32, pol);
+                } else {
+                    const int *cols = stage + (cb & 3);
+                    for (int j = lane; j < cl; j += 32) push_one(F, hot, n_hot, cols[j], cw, pol);
+                }
+                __syncwarp();  // every lane is done with the stage
+                c = nx;
+                if (c < cb1) {
+                    cb = nb;
+                    cl = nl;
+                    cw = nw;
+                    if (lane == 0) {
+                        fence_proxy_async();
+                        issue(cb, cl);
+                    }
                 }
             }
-        }
-        if (!ok && threadIdx.x == 0) {
-            // a copy did not land in time: wait (bounded again) for the ones still in flight,
-            // then stop the solve (DI_ETIMEOUT), or mark the graph untrusted if they never land
-            bool drained = true;
-            for (int j = i; j < mine && j < i + 2; ++j)
-                drained &= mbar_wait(smem_addr(&s_hbar[j & 1]), (unsigned)((j >> 1) & 1), kPushWaitLimit);
-            atomicOr(reinterpret_cast<unsigned long long *>(&part[blockIdx.x % G].err), drained ? 1ull : 3ull);
+            if (!ok && lane == 0) {
+                // the copy did not land in time: wait (bounded again) for it, then stop the solve
+                // (DI_ETIMEOUT), or mark the graph untrusted if it never lands
+                const bool drained = mbar_wait(bar, phase, kPushWaitLimit);
+                atomicOr(reinterpret_cast<unsigned long long *>(&part[blockIdx.x % G].err), drained ? 1ull : 3ull);
+            }
         }
     }
     // the CTA's sums for the hot targets go to F once

@@ -286,6 +286,7 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
     for (int L = 0; L < kLists; ++L) start[L] = run[L] = region[L * (W + 1) + g];
     long long l1 = 0, s_out = 0, s_dng = 0;  // fixed point: |F|_1, fluid of selected nodes with / without children
     int srcs = 0, entries = 0;
+    int hub_chunks = 0;    // chunks of the hub rows this lane listed
     long long pedges = 0;  // out-links of the selected nodes, counted here on pull sweeps
     const int nsteps = wchunk / kStep;
     const unsigned long long pol = evict_first_policy();
@@ -386,7 +387,8 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
                 const bool has = t < total;
                 const int idx = has ? q[t] : 0;
                 const FT v = stg_f[idx];
-                const int c = has ? stg[Ring::kF + idx] : 0;
+                const int cb = has ? stg[Ring::kF + idx] : 0;  // class byte: 2 + chunks for a hub row
+                const int c = class_of_byte(cb);
                 const long long node = step0 + idx;
                 if (has) {
                     const long long fx = to_fixed(v, S);
@@ -407,9 +409,10 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
                     if (mine) {
                         Sel<FT> e;
                         e.node = (int)node;
-                        e.pad = 0;
+                        e.pad = L == 3 ? cb - 2 : 0;  // a hub row's chunk count
                         e.sent = v;
                         sel[run[L] + __popc(bits & lt)] = e;
+                        if (L == 3) hub_chunks += cb - 2;
                     }
                     run[L] += __popc(bits);
                 }
@@ -435,9 +438,11 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
         }
         __syncwarp();
     }
+    hub_chunks = __reduce_add_sync(kFull, hub_chunks);
     if (lane == 0) {
 #pragma unroll
         for (int L = 0; L < kLists; ++L) fcount[L * W + g] = run[L] - start[L];
+        fcount[kChunkRow * W + g] = hub_chunks;
     }
     const long long bl1 = block_sum(l1, s_red);
     const long long bout = block_sum(s_out, s_red);
@@ -497,8 +502,8 @@ __global__ void k_sweep_finalize(int n, int G, const ScanPartial *__restrict__ p
         }
         return;
     }
-    // the seven sums of the per-CTA partials, reduced together: warp trees, then thread 0 over
-    // the warps (integer sums, so exact in any order)
+    // the six sums of the per-CTA partials and the OR of their error bits, reduced together:
+    // warp trees, then thread 0 over the warps (integers, so exact in any order)
     long long v[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int c = threadIdx.x; c < G; c += blockDim.x) {
         const ScanPartial p = part[c];
@@ -513,7 +518,8 @@ __global__ void k_sweep_finalize(int n, int G, const ScanPartial *__restrict__ p
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-        for (int k = 0; k < 7; ++k) v[k] += __shfl_down_sync(kFull, v[k], o);
+        for (int k = 0; k < 6; ++k) v[k] += __shfl_down_sync(kFull, v[k], o);
+        v[6] |= __shfl_down_sync(kFull, v[6], o);  // the error bits are OR-ed, not added
     }
     const int wid = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
@@ -525,7 +531,7 @@ __global__ void k_sweep_finalize(int n, int G, const ScanPartial *__restrict__ p
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
         long long a = 0;
-        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) a += s_l[k][w2];
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) a = k < 6 ? a + s_l[k][w2] : (a | s_l[k][w2]);
         v[k] = a;
     }
     const long long fl1 = v[0], fout = v[1], fdng = v[2], ed = v[3], sr = v[4], en = v[5], er = v[6];

@@ -441,10 +441,10 @@ def test_scan_wait_watchdog_keeps_results_valid(di, family):
     assert np.abs(H - r.H).sum() <= max(st["bound"], r.l1F / (1 - D)) + 1e-12
 
 
-def test_more_hubs_than_the_chunk_table(di):
-    """2500 nodes with 1100 out-links each: the first sweep selects more class-3 rows than the
-    push's chunk table holds (2048), so it pushes them a CTA per row; later sweeps select
-    fewer and cut them into chunks.  Same sweeps, elementary steps and H as the oracle."""
+def test_many_hub_rows(di):
+    """2500 nodes with 1100 out-links each (all above the 1024-link cutoff): every sweep cuts
+    thousands of hub rows into chunks spread over the CTAs.  Same sweeps, elementary steps and
+    H as the oracle."""
     rng = np.random.default_rng(12)
     n = 4000
     edges = [(i, int(j)) for i in range(2500) for j in rng.choice(n, 1100, replace=False)]
