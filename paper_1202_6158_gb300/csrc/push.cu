@@ -120,9 +120,9 @@ struct HubWalk {
 // over the warps, which spreads heavy rows evenly whatever the id order (R-MAT puts its
 // heaviest rows on the lowest ids), and the smallest class (a lane per node, four in
 // flight, at most 8 out-links each) is split into even rank ranges per warp.  The largest
-// class comes last: its rows (up to 50,000 out-links on the Zipf workload) are cut into
-// chunks of kHubChunk out-links that are strided over the CTAs, so no CTA carries a whole
-// hub.  The scan already moved each node's fluid into H; the push adds d*sent/outdeg(i)
+// class comes first: its rows (up to 50,000 out-links on the Zipf workload) are cut into
+// chunks of kHubChunk out-links spread over the CTAs and their warps, so no CTA carries a
+// whole hub.  The scan already moved each node's fluid into H; the push adds d*sent/outdeg(i)
 // to F_j along every out-link (ALGO-REF's inner loop), every load of a node issued before
 // its reductions.
 template <typename FT>
@@ -146,6 +146,87 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nwarps = gridDim.x * kWarps, gw = blockIdx.x * kWarps + w;
     long long edges = 0;
+    // class 3: the hub rows, cut into chunks of at most kHubChunk out-links.  CTA b takes the
+    // contiguous chunk range [b nch / grid, (b+1) nch / grid) and its warps take every 8th chunk
+    // of it.  A chunk's column indices are staged in the warp's shared memory by a 1-D bulk copy
+    // (TMA); the next chunk is located (its list entry and row record) while the copy is in
+    // flight.  A CTA per hub row, or the whole CTA on one chunk at a time, left the chunks'
+    // dependent loads on the critical path: slower on R-MAT, whose dense sweeps list thousands
+    // of hub rows.  The hubs go first: their per-link weights d*sent/outdeg are the smallest,
+    // and with FP32 fluid a small weight added after the larger ones of the other classes is
+    // rounded away more often (R-MAT 2^23: 1.5e-7 against 6e-7 in L1 from FP64).
+    {
+        const int *pch = pre + kChunkRow * (W + 1);
+        const int nch = __ldg(pch + W);
+        const int cb0 = (int)((long long)blockIdx.x * nch / gridDim.x);
+        const int cb1 = (int)((long long)(blockIdx.x + 1) * nch / gridDim.x);
+        int c = cb0 + w;
+        if (c < cb1) {
+            HubWalk<FT> hw{rec, sel, region + 3 * (W + 1), fcount + 3 * W, pch, W};
+            hw.start(c);
+            const unsigned bar = smem_addr(&s_hbar[w]);
+            int *stage = s_hcol[w];
+            // a copy covers [beg & ~3, (beg + len + 3) & ~3): 16-byte aligned at both ends, inside
+            // the column array (kColPad ints are allocated past its end); a chunk longer than the
+            // stage (a row of more than kMaxHubChunks * kHubChunk links) is read directly instead
+            auto issue = [&](int beg, int len) {
+                if (len > kHubChunk) {
+                    mbar_expect_tx(bar, 0u);
+                    return;
+                }
+                const int a0 = beg & ~3, a1 = (beg + len + 3) & ~3;
+                mbar_expect_tx(bar, 4u * (unsigned)(a1 - a0));
+                bulk_copy(smem_addr(stage), col_idx + a0, 4u * (unsigned)(a1 - a0), bar, pol_col);
+            };
+            if (lane == 0) {
+                mbar_init(bar, 1);
+                fence_barrier_init();
+            }
+            __syncwarp();
+            int cb, cl;
+            FT cw;
+            hw.chunk(c, cb, cl, cw);
+            if (lane == 0) issue(cb, cl);
+            bool ok = true;
+            unsigned phase = 0;
+            while (c < cb1) {
+                const int nx = c + kWarps;
+                int nb = 0, nl = 0;
+                FT nw = (FT)0;
+                if (nx < cb1) {  // the next chunk's entry and record, while this copy lands
+                    hw.advance_to(nx);
+                    hw.chunk(nx, nb, nl, nw);
+                }
+                ok = __all_sync(kFull, mbar_wait(bar, phase, wait_polls));
+                if (!ok) break;
+                phase ^= 1u;
+                if (lane == 0) edges += cl;
+                if (cl > kHubChunk) {
+                    push_row_lanes(col_idx, F, hot, n_hot, cb, cl, cw, lane, 32, pol);
+                } else {
+                    const int *cols = stage + (cb & 3);
+                    for (int j = lane; j < cl; j += 32) push_one(F, hot, n_hot, cols[j], cw, pol);
+                }
+                __syncwarp();  // every lane is done with the stage
+                c = nx;
+                if (c < cb1) {
+                    cb = nb;
+                    cl = nl;
+                    cw = nw;
+                    if (lane == 0) {
+                        fence_proxy_async();
+                        issue(cb, cl);
+                    }
+                }
+            }
+            if (!ok && lane == 0) {
+                // the copy did not land in time: wait (bounded again) for it, then stop the solve
+                // (DI_ETIMEOUT), or mark the graph untrusted if it never lands
+                const bool drained = mbar_wait(bar, phase, kPushWaitLimit);
+                atomicOr(reinterpret_cast<unsigned long long *>(&part[blockIdx.x % G].err), drained ? 1ull : 3ull);
+            }
+        }
+    }
     // classes 2 and 1: each warp takes an even range of ranks of the class's list (ranks
     // number the list entries over all sub-chunks, so the split is even however the selected
     // nodes fall over the sub-chunks); a lane finds the sub-chunk of its rank from the
@@ -260,85 +341,6 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
 #pragma unroll
                     for (int u = 0; u < kInFlight; ++u)
                         if (k + 4 < rd[u]) push_one(F, hot, n_hot, cc[u][k], rw[u], pol);
-            }
-        }
-    }
-    // class 3: the hub rows, cut into chunks of at most kHubChunk out-links.  CTA b takes the
-    // contiguous chunk range [b nch / grid, (b+1) nch / grid) and its warps take every 8th chunk
-    // of it.  A chunk's column indices are staged in the warp's shared memory by a 1-D bulk copy
-    // (TMA); the next chunk is located (its list entry and row record) while the copy is in
-    // flight.  A CTA per hub row, or the whole CTA on one chunk at a time, left the chunks'
-    // dependent loads on the critical path: slower on R-MAT, whose dense sweeps list thousands
-    // of hub rows.
-    {
-        const int *pch = pre + kChunkRow * (W + 1);
-        const int nch = __ldg(pch + W);
-        const int cb0 = (int)((long long)blockIdx.x * nch / gridDim.x);
-        const int cb1 = (int)((long long)(blockIdx.x + 1) * nch / gridDim.x);
-        int c = cb0 + w;
-        if (c < cb1) {
-            HubWalk<FT> hw{rec, sel, region + 3 * (W + 1), fcount + 3 * W, pch, W};
-            hw.start(c);
-            const unsigned bar = smem_addr(&s_hbar[w]);
-            int *stage = s_hcol[w];
-            // a copy covers [beg & ~3, (beg + len + 3) & ~3): 16-byte aligned at both ends, inside
-            // the column array (kColPad ints are allocated past its end); a chunk longer than the
-            // stage (a row of more than kMaxHubChunks * kHubChunk links) is read directly instead
-            auto issue = [&](int beg, int len) {
-                if (len > kHubChunk) {
-                    mbar_expect_tx(bar, 0u);
-                    return;
-                }
-                const int a0 = beg & ~3, a1 = (beg + len + 3) & ~3;
-                mbar_expect_tx(bar, 4u * (unsigned)(a1 - a0));
-                bulk_copy(smem_addr(stage), col_idx + a0, 4u * (unsigned)(a1 - a0), bar, pol_col);
-            };
-            if (lane == 0) {
-                mbar_init(bar, 1);
-                fence_barrier_init();
-            }
-            __syncwarp();
-            int cb, cl;
-            FT cw;
-            hw.chunk(c, cb, cl, cw);
-            if (lane == 0) issue(cb, cl);
-            bool ok = true;
-            unsigned phase = 0;
-            while (c < cb1) {
-                const int nx = c + kWarps;
-                int nb = 0, nl = 0;
-                FT nw = (FT)0;
-                if (nx < cb1) {  // the next chunk's entry and record, while this copy lands
-                    hw.advance_to(nx);
-                    hw.chunk(nx, nb, nl, nw);
-                }
-                ok = __all_sync(kFull, mbar_wait(bar, phase, wait_polls));
-                if (!ok) break;
-                phase ^= 1u;
-                if (lane == 0) edges += cl;
-                if (cl > kHubChunk) {
-                    push_row_lanes(col_idx, F, hot, n_hot, cb, cl, cw, lane, 32, pol);
-                } else {
-                    const int *cols = stage + (cb & 3);
-                    for (int j = lane; j < cl; j += 32) push_one(F, hot, n_hot, cols[j], cw, pol);
-                }
-                __syncwarp();  // every lane is done with the stage
-                c = nx;
-                if (c < cb1) {
-                    cb = nb;
-                    cl = nl;
-                    cw = nw;
-                    if (lane == 0) {
-                        fence_proxy_async();
-                        issue(cb, cl);
-                    }
-                }
-            }
-            if (!ok && lane == 0) {
-                // the copy did not land in time: wait (bounded again) for it, then stop the solve
-                // (DI_ETIMEOUT), or mark the graph untrusted if it never lands
-                const bool drained = mbar_wait(bar, phase, kPushWaitLimit);
-                atomicOr(reinterpret_cast<unsigned long long *>(&part[blockIdx.x % G].err), drained ? 1ull : 3ull);
             }
         }
     }
