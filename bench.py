@@ -606,6 +606,7 @@ def bench_serve(di, torch, scales=(16, 18, 20, 21, 22, 23), tol=1e-6, budget=120
 def run_config(args, w, g, world):
     """The `config` object of both arms' JSON lines: the workload and the solve's settings."""
     return {"workload": w["label"], "n": g.n, "nnz": g.nnz, "d": w["d"], "tol": w["tol"], "beta": args.beta,
+            "precision": "FP64" if args.prec == "fp64" else "FP32-mixed",
             "direction": "push, pull on dense sweeps" if args.direction else "push",
             "parallelism": "replicas" if world > 1 else "single-gpu",
             "l2": "inputs larger than L2 (CSR + F + H of the solve exceed 129 MB)"}
@@ -647,6 +648,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="zipf24", choices=sorted(WORKLOADS))
     ap.add_argument("--beta", type=float, default=0.5)
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"],
+                    help="fluid precision of the timed and profiled solves (fp32: FP32-mixed)")
     ap.add_argument("--direction", type=int, default=0, choices=[0, 1],
                     help="1: dense sweeps pull along the in-links (di_solve_opts.direction)")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -671,6 +674,7 @@ def main():
     import torch
     import paper_1202_6158_gb300 as di
 
+    prec = di.DI_FP64 if args.prec == "fp64" else di.DI_FP32_MIXED
     rank, world, local = dist_env()
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU")
@@ -703,7 +707,7 @@ def main():
 
     # ---- warm-up, then K timed solves on device-resident inputs
     for _ in range(args.warmup):
-        G.solve(tol, H_out=H, beta=args.beta, direction=args.direction)
+        G.solve(tol, H_out=H, beta=args.beta, direction=args.direction, prec=prec)
     torch.cuda.synchronize()
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -714,7 +718,7 @@ def main():
         torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(args.steps):
-            _, st = G.solve(tol, H_out=H, beta=args.beta, direction=args.direction)
+            _, st = G.solve(tol, H_out=H, beta=args.beta, direction=args.direction, prec=prec)
             edges += st["edges_pushed"]
             launches += st["kernel_launches"]
             sweeps.append(st["sweeps"])
@@ -745,11 +749,11 @@ def main():
     pull_bytes_iter = g.nnz * (4 + 4 + 8) + g.n * (2 * 8 + 2 * 8 + 8 + 8)
 
     # ---- profiled solve: per-kernel CUDA-event times and algorithmic bytes from the trace
-    G.solve(tol, H_out=H, beta=args.beta, profile=1, trace=1, direction=args.direction)
+    G.solve(tol, H_out=H, beta=args.beta, profile=1, trace=1, direction=args.direction, prec=prec)
     prof = G.profile()
     trace = G.trace()
-    s_f = 8
-    push_bytes = sum(20 * t["edges"] + 16 * t["pushed"] for t in trace)
+    s_f = 8 if prec == di.DI_FP64 else 4
+    push_bytes = sum((4 + 2 * s_f) * t["edges"] + 16 * t["pushed"] for t in trace)
     scan_bytes = sum(g.n * s_f + t["sources"] * (s_f + 16 + 8) + 16 * t["pushed"] for t in trace)
     hbm_peak, peak_kind = load_peaks()
     kernels = {
@@ -760,7 +764,8 @@ def main():
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     kd = kernels[dom]
     achieved = kd["alg_bytes"] / (kd["ms"] * 1e-3) / 1e9 if kd["ms"] > 0 else None
-    traffic = push_traffic() if dom == "push" else None
+    # the committed DRAM summary is for the FP64 headline workload's push
+    traffic = push_traffic() if dom == "push" and args.workload == "zipf24" and prec == di.DI_FP64 else None
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": (achieved / hbm_peak) if achieved else None, "traffic": traffic,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else
@@ -852,7 +857,8 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if prec == di.DI_FP64 else "f32 fluid, f64 history",
+            "data": "synthetic",
             "config": run_config(args, w, g, world),
             "time_to_residual_ms": {"diter": max_ms / args.steps, "power": pms,
                                     "speedup_vs_power": pms / (max_ms / args.steps)},
