@@ -15,6 +15,8 @@
 //     each in-link, in-degree classes (exports) and row fingerprints (updates).
 #include <cuda_runtime.h>
 
+#include <climits>
+
 #include <algorithm>
 #include <vector>
 
@@ -398,19 +400,141 @@ __global__ void __launch_bounds__(256) k_count_in(long long nnz, const int *__re
     if (bad && flags) atomicOr(flags, kColRange);
 }
 
-// key that sorts nodes by in-degree, largest first (a stable sort keeps ascending ids on ties)
-__global__ void k_indeg_key_direct(int n, const int *__restrict__ indeg, int *__restrict__ key) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        key[i] = 0x7fffffff - indeg[i];
+
+// ---- the hot targets: the k largest in-degrees, ties by lower id, without sorting all n
+//
+// A most-significant-digit-first radix select finds t, the k-th largest in-degree: four
+// passes over the in-degrees, each a 256-bin histogram of one byte among the nodes whose
+// higher bytes match the prefix found so far, and a one-thread step that picks the bin
+// holding the k-th largest.  The nodes above t (fewer than k) and the first k - #above
+// nodes equal to t in id order (an ordered compaction) are then sorted by (in-degree
+// descending, id ascending) in one CTA.
+
+struct HotSel {
+    unsigned prefix;  // the bytes of t found so far (high bits)
+    int need;         // how many of the k still lie at or below the current prefix
+    int above;        // nodes with in-degree > t (after the last pass)
+    int ncand;        // candidates written
+};
+
+__global__ void k_hot_hist(int n, const int *__restrict__ indeg, int pass, const HotSel *__restrict__ hs,
+                           unsigned *__restrict__ hist) {
+    __shared__ unsigned h[256];
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) h[b] = 0u;
+    __syncthreads();
+    const int shift = 24 - 8 * pass;
+    const unsigned pre = hs->prefix;
+    const unsigned hmask = pass == 0 ? 0u : (0xffffffffu << (32 - 8 * pass));
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const unsigned v = (unsigned)indeg[i];
+        if ((v & hmask) == pre) atomicAdd(&h[(v >> shift) & 0xffu], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < 256; b += blockDim.x)
+        if (h[b]) atomicAdd(&hist[b], h[b]);
 }
 
-// number of the first k sorted ids whose in-degree reaches the minimum
-__global__ void k_count_hot(int k, const int *__restrict__ sorted_key, int min_deg, int *__restrict__ count) {
+// one thread: the bin of this pass that holds the need-th largest; clears the histogram
+__global__ void k_hot_pick(int pass, HotSel *__restrict__ hs, unsigned *__restrict__ hist) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int c = 0;
-    while (c < k && 0x7fffffff - sorted_key[c] >= min_deg) ++c;
-    *count = c;
+    const int shift = 24 - 8 * pass;
+    int need = hs->need;
+    int b = 255;
+    for (; b > 0; --b) {
+        const int c = (int)hist[b];
+        if (c >= need) break;
+        need -= c;
+    }
+    hs->prefix |= (unsigned)b << shift;
+    hs->need = need;  // the need-th largest among the nodes of bin b
+    for (int j = 0; j < 256; ++j) hist[j] = 0u;
 }
+
+constexpr int kTieBlock = 4096;  // ids per block of the ordered tie compaction
+
+// nodes above t go to the candidates (any order); per block of ids, the number equal to t
+__global__ void k_hot_above(int n, const int *__restrict__ indeg, HotSel *__restrict__ hs, int *__restrict__ cand,
+                            int cap, int *__restrict__ ties) {
+    __shared__ int s_t;
+    if (threadIdx.x == 0) s_t = 0;
+    __syncthreads();
+    const int t = (int)hs->prefix;
+    const long long beg = (long long)blockIdx.x * kTieBlock, end = min((long long)n, beg + kTieBlock);
+    int c = 0;
+    for (long long i = beg + threadIdx.x; i < end; i += blockDim.x) {
+        const int v = indeg[i];
+        if (v > t) {
+            const int at = atomicAdd(&hs->above, 1);
+            if (at < cap) cand[at] = (int)i;
+        } else if (v == t) {
+            ++c;
+        }
+    }
+    if (c) atomicAdd(&s_t, c);
+    __syncthreads();
+    if (threadIdx.x == 0) ties[blockIdx.x] = s_t;
+}
+
+// the first (k - above) nodes equal to t, in id order, after the nodes above t
+__global__ void k_hot_ties(int n, int k, const int *__restrict__ indeg, const HotSel *__restrict__ hs,
+                           const int *__restrict__ tie_off, int *__restrict__ cand) {
+    __shared__ int s_w[32];
+    const int t = (int)hs->prefix, above = min(hs->above, k), want = k - above;
+    int base = tie_off[blockIdx.x];
+    if (base >= want) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const long long beg = (long long)blockIdx.x * kTieBlock, end = min((long long)n, beg + kTieBlock);
+    for (long long i0 = beg; i0 < end && base < want; i0 += blockDim.x) {
+        const long long i = i0 + threadIdx.x;
+        const bool is = i < end && indeg[i] == t;
+        const unsigned bal = __ballot_sync(0xffffffffu, is);
+        if (lane == 0) s_w[w] = __popc(bal);
+        __syncthreads();
+        int off = 0, tot = 0;
+        for (int j = 0; j < nw; ++j) {
+            off += j < w ? s_w[j] : 0;
+            tot += s_w[j];
+        }
+        const int r = base + off + __popc(bal & ((1u << lane) - 1u));
+        if (is && r < want) cand[above + r] = (int)i;
+        base += tot;
+        __syncthreads();
+    }
+}
+
+// one CTA of kHotSlots threads: sort the k candidates by (in-degree descending, id ascending)
+// and count those with at least min_deg in-links
+__global__ void k_hot_sort(int k, const int *__restrict__ indeg, const int *__restrict__ cand, int min_deg,
+                           int *__restrict__ hot_ids, int *__restrict__ count) {
+    __shared__ long long key[kHotSlots];
+    const int t = threadIdx.x;
+    // larger in-degree first, then lower id: sort ascending on (-indeg, id)
+    key[t] = t < k ? ((long long)(0x7fffffff - indeg[cand[t]]) << 32) | (unsigned)cand[t] : LLONG_MAX;
+    __syncthreads();
+    for (int size = 2; size <= kHotSlots; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const int j = t ^ stride;
+            if (j > t) {
+                const bool up = (t & size) == 0;
+                const long long a = key[t], b = key[j];
+                if ((a > b) == up) {
+                    key[t] = b;
+                    key[j] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    int c = 0;
+    if (t < k) {
+        const int id = (int)(key[t] & 0xffffffffLL);
+        hot_ids[t] = id;
+        c = indeg[id] >= min_deg ? 1 : 0;
+    }
+    const int total = __syncthreads_count(c);
+    if (t == 0) *count = total;  // the qualifying ones are a prefix of the sorted order
+}
+
 
 // flag[i] = 1 everywhere, then 0 for the first k ids of the in-degree order (the hot targets)
 __global__ void k_hot_flags(int n, int *__restrict__ flag) {
@@ -658,7 +782,7 @@ di_status build_graph(di_graph *g, const int *col_host) {
     }
 
     // 1b. internal numbering: the hot targets -- the kHotSlots largest in-degrees (at least
-    //     kHotMinInDeg), ties by lower input id, found by a stable LSD radix sort -- become ids
+    //     kHotMinInDeg), ties by lower input id, found by a radix select -- become ids
     //     0..n_hot-1; every other node keeps its input order after them.  The push sums the
     //     hot targets' fluid in shared memory with a single compare; the rest stay spread over
     //     the L2 slices as the input spreads them.
@@ -669,28 +793,44 @@ di_status build_graph(di_graph *g, const int *col_host) {
         DI_CUDA(cudaMallocAsync(&va, sizeof(int) * (size_t)n, s));
         DI_CUDA(cudaMallocAsync(&vb, sizeof(int) * (size_t)n, s));
         DI_CUDA(cudaMallocAsync(&cnt, sizeof(int), s));
-        k_indeg_key_direct<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, indeg, ka);
-        k_iota<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, va);
-        for (int p = 0; p < 4; ++p) {
-            di_status r = radix_pass(ka, va, kb, vb, n, 8 * p, 0xff, s);
-            if (r != DI_OK) return r;
-            std::swap(ka, kb);
-            std::swap(va, vb);
-        }
-        // va: ids by in-degree, largest first; ka: the sorted keys
+        // the k largest in-degrees (ties by lower id): radix select, then one small sort
         const int k = std::min(kHotSlots, n);
-        k_count_hot<<<1, 32, 0, s>>>(k, ka, kHotMinInDeg, cnt);
+        DI_CUDA(cudaMallocAsync(&g->hot_ids, sizeof(int) * kHotSlots, s));
+        {
+            HotSel *hs = nullptr;
+            unsigned *hist = nullptr;
+            int *cand = nullptr, *ties = nullptr;
+            const int nblk = ceil_div(n, kTieBlock);
+            DI_CUDA(cudaMallocAsync(&hs, sizeof(HotSel), s));
+            DI_CUDA(cudaMallocAsync(&hist, sizeof(unsigned) * 256, s));
+            DI_CUDA(cudaMallocAsync(&cand, sizeof(int) * kHotSlots, s));
+            DI_CUDA(cudaMallocAsync(&ties, sizeof(int) * (size_t)(nblk + 1), s));
+            HotSel h0 = {0u, k, 0, 0};
+            DI_CUDA(cudaMemcpyAsync(hs, &h0, sizeof(HotSel), cudaMemcpyHostToDevice, s));
+            DI_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned) * 256, s));
+            for (int pass = 0; pass < 4; ++pass) {
+                k_hot_hist<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, indeg, pass, hs, hist);
+                k_hot_pick<<<1, 32, 0, s>>>(pass, hs, hist);
+            }
+            k_hot_above<<<nblk, 256, 0, s>>>(n, indeg, hs, cand, kHotSlots, ties);
+            di_status r = exclusive_scan(ties, ties, nblk, s);
+            if (r != DI_OK) return r;
+            k_hot_ties<<<nblk, 256, 0, s>>>(n, k, indeg, hs, ties, cand);
+            k_hot_sort<<<1, kHotSlots, 0, s>>>(k, indeg, cand, kHotMinInDeg, g->hot_ids, cnt);
+            cudaFreeAsync(hs, s);
+            cudaFreeAsync(hist, s);
+            cudaFreeAsync(cand, s);
+            cudaFreeAsync(ties, s);
+        }
         int hk = 0;
         DI_CUDA(cudaMemcpyAsync(&hk, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
         DI_CUDA(cudaStreamSynchronize(s));
         g->n_hot = hk;
-        DI_CUDA(cudaMallocAsync(&g->hot_ids, sizeof(int) * kHotSlots, s));
-        if (hk > 0) DI_CUDA(cudaMemcpyAsync(g->hot_ids, va, sizeof(int) * hk, cudaMemcpyDeviceToDevice, s));
         // perm: the hot ids in in-degree order, then every other id ascending (a stable
         // two-bucket pass on "not hot" puts the hot ids first; they are then overwritten
         // with their in-degree order)
         k_hot_flags<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, kb);           // kb[i] = 1
-        if (hk > 0) k_mark_hot<<<1, 256, 0, s>>>(hk, va, kb);                      // kb[hot] = 0
+        if (hk > 0) k_mark_hot<<<1, 256, 0, s>>>(hk, g->hot_ids, kb);              // kb[hot] = 0
         k_iota<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, vb);
         {
             di_status r = radix_pass(kb, vb, ka, va + 0, n, 0, 1, s);  // va <- ids, hot first (ascending)

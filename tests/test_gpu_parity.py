@@ -51,6 +51,15 @@ def case_graphs():
     rp, ci = graphs.complete(50)
     out["complete_50"] = (50, rp, ci)
     out["empty_7"] = (7, np.zeros(8, np.int32), np.zeros(0, np.int32))
+    # in-degree ties at the hot-target cutoff spread over many id blocks: 100 targets with 50
+    # in-links, then 2858 (every 7th id) with exactly 40; the 156 lowest of those are hot
+    n = 20011
+    tgt = [(j, 50) for j in range(3, n, 197)][:100]
+    taken = {j for j, _ in tgt}
+    tgt += [(j, 40) for j in range(0, n, 7) if j not in taken]
+    edges = [(int(src), j) for j, c in tgt for src in rng.choice(n, c, replace=False)]
+    rp, ci = graphs.csr(n, edges)
+    out["ties_20011"] = (n, rp, ci)
     return out
 
 
