@@ -177,7 +177,8 @@ di_status di_graph_info(const di_graph *g, int32_t *n, int64_t *nnz, double *d);
  *   in_ptr   int32[n+1], in_src int32[nnz]: in-link lists, sources ascending
  *   bin_of   int32[n]: out-degree bin (0 dangling, 1..3 by the cut values)
  *   in_bin_of int32[n]: in-degree class (0: <= in_cut1 in-links, 1: <= in_cut2, 2: above)
- *   cuts     int32[4]: {out_cut1, out_cut2, in_cut1, in_cut2}
+ *   cuts     int32[4]: {out_cut1, out_cut2, in_cut1, in_cut2}; the out-degree cutoffs are the
+ *            graph's current ones (8 and 1024 at creation; the autotuners may change them)
  * Any pointer may be NULL to skip that array.  Inputs (V, seeds) and outputs
  * (H, F, X) of every other call are in the caller's numbering.
  */

@@ -466,3 +466,36 @@ def test_many_hub_rows(di):
     assert tr[0]["pushed"] == 2500
     assert st["sweeps"] == r.sweeps and st["edges_pushed"] == r.edges
     assert np.abs(H - r.H).sum() <= max(st["bound"], r.l1F / (1 - D)) + 1e-12
+
+
+def test_giant_hub_row(di):
+    """A row of 270,000 out-links: more than 253 chunks of 1024, so its chunks are longer than
+    a staging buffer and the push reads them directly.  FP64 and FP32-mixed, both directions,
+    and a batch of queries seeded on the hub, against the oracle."""
+    rng = np.random.default_rng(21)
+    n = 300000
+    rp0, ci0 = graphs.random_graph(n, 0.2, 6, rng)
+    hub = rng.choice(np.arange(1, n), 270000, replace=False).astype(np.int32)
+    deg = np.diff(rp0)
+    deg[0] = len(hub)
+    rp = np.concatenate([[0], np.cumsum(deg)]).astype(np.int32)
+    ci = np.concatenate([hub, ci0[rp0[1]:]]).astype(np.int32)
+    V = gg.uniform_v(n)
+    tol = 1e-11
+    r = oracle.diter(n, rp, ci, D, V, tol, mode="sweep", beta=BETA)
+    with di.DiGraph(n, rp, ci, D) as g:
+        for prec, ptol, allow in ((di.DI_FP64, tol, 1e-12), (di.DI_FP32_MIXED, 1e-7, 2e-6)):
+            for direction in (0, 1):
+                H, st = g.solve(ptol, beta=BETA, prec=prec, direction=direction)
+                assert st["converged"] == 1
+                if prec == di.DI_FP64:
+                    assert st["sweeps"] == r.sweeps and st["edges_pushed"] == r.edges
+                assert np.abs(H - r.H).sum() <= max(st["bound"], r.l1F / (1 - D)) + allow
+        seeds = [[0], [0, 5, 9], [17]]
+        Hb, stq, sta = g.query_batch(seeds, 1e-8)
+    assert sta["converged"] == 1
+    for q, sd in enumerate(seeds):
+        Vq = np.zeros(n)
+        Vq[sd] = 1.0 / len(sd)
+        rq = oracle.diter(n, rp, ci, D, Vq, 1e-12, mode="sweep", beta=BETA)
+        assert np.abs(Hb[q] - rq.H).sum() <= stq[q]["bound"] + 2e-6
