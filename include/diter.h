@@ -387,6 +387,29 @@ di_status di_get_trace(const di_graph *g, di_sweep_record *out, int32_t cap, int
 di_status di_get_state(const di_graph *g, double *F_out, double *H_out);
 
 /*
+ * Load a saved state (F, H) into the graph: the resume half of a checkpoint
+ * whose save half is di_get_state.  The state must satisfy Theorem 1 on this
+ * graph, H + F = F_0 + dPH with F_0 = (1-d)V: the call computes the residual
+ * Z = F_0 - H - F + dPH and accepts the state only when
+ *   max_j |Z_j| <= rtol * max_j (|H_j| + |F_j| + F_0,j).
+ * A state kept by a global solve (di_solve, di_solve_ex, di_solve_update) of
+ * this graph, or of a graph with the same nodes, links, V and d, satisfies it
+ * up to rounding (about 1e-14 relative in FP64; an FP32-mixed state about 1e-7);
+ * a query's state does not, as its F_0 is the query's.
+ *   F_in, H_in  host or device double[n] each, in the caller's numbering; both
+ *               required.  The call reads them and keeps no pointer.
+ *   rtol        accepted relative deviation (>= 0)
+ *   deviation   host double*, may be NULL: receives the relative deviation,
+ *               also when the state is rejected
+ * On success the graph's FP64 state becomes (F, H), as if its last FP64 solve
+ * had stopped there: di_solve_update(g, g, ...) continues it to a new bound, and
+ * di_get_state returns it.  Returns DI_EINVAL, with the graph's state unchanged,
+ * for a NaN or an infinity in F or H or a deviation above rtol.  It allocates
+ * device scratch of 3 double[n] (plus a copy of each host input) for the call.
+ */
+di_status di_set_state(di_graph *g, const double *F_in, const double *H_in, double rtol, double *deviation);
+
+/*
  * Per-kernel device times of the last solve made with opts.profile = 1.
  *   out  host di_profile*
  */

@@ -2,7 +2,7 @@
 
 Python front end of libditer (include/diter.h).  The names follow the C ABI:
 ``di_graph_create``, ``di_solve``, ``di_solve_ex``, ``di_query``, ``di_power``,
-``di_graph_export``, ``di_get_trace``, ``di_get_state``, ``di_free``; the
+``di_graph_export``, ``di_get_trace``, ``di_get_state``, ``di_set_state``, ``di_free``; the
 :class:`DiGraph` class wraps a graph handle with the same calls as methods.
 Arrays are numpy arrays or torch tensors, on the host or on the device.
 
@@ -24,7 +24,7 @@ from ._lib import (DI_EINVAL, DI_ENOMEM, DI_ENOTCONVERGED, DI_ETIMEOUT, DI_FP32_
 
 __all__ = ["DiGraph", "DiError", "DI_FP64", "DI_FP32_MIXED", "DI_OK", "DI_EINVAL", "DI_ENOTCONVERGED", "DI_ETIMEOUT",
            "di_graph_create", "di_free", "di_solve", "di_solve_ex", "di_solve_update", "di_autotune", "di_autotune_batch", "di_query", "di_query_batch", "di_query_batch_ex", "di_power", "di_power_ex", "di_graph_export",
-           "di_get_trace", "di_get_state", "di_get_profile", "di_power_noalloc", "di_version", "di_selftest_wait", "load",
+           "di_get_trace", "di_get_state", "di_set_state", "di_get_profile", "di_power_noalloc", "di_version", "di_selftest_wait", "load",
            "di_plan_lanes", "di_server_create", "di_server_lanes", "di_server_submit", "di_server_poll",
            "di_server_pending", "di_server_stats", "di_server_free", "di_clock", "DiServer"]
 
@@ -212,6 +212,13 @@ def di_get_state(handle, F_out=None, H_out=None):
     check(load().di_get_state(handle, ptr(F_out), ptr(H_out)))
 
 
+def di_set_state(handle, F_in, H_in, rtol=1e-9) -> float:
+    """Load a saved (F, H) after the library's Theorem 1 check; returns the relative deviation."""
+    dev = ctypes.c_double(0.0)
+    check(load().di_set_state(handle, ptr(F_in), ptr(H_in), float(rtol), ctypes.byref(dev)))
+    return dev.value
+
+
 def di_get_profile(handle) -> dict:
     p = di_profile()
     check(load().di_get_profile(handle, ctypes.byref(p)))
@@ -314,6 +321,10 @@ class DiGraph:
         H = np.empty(self.n, np.float64)
         di_get_state(self.handle, F, H)
         return F, H
+
+    def set_state(self, F, H, rtol=1e-9):
+        return di_set_state(self.handle, np.ascontiguousarray(F, np.float64) if isinstance(F, np.ndarray) else F,
+                            np.ascontiguousarray(H, np.float64) if isinstance(H, np.ndarray) else H, rtol)
 
 
 # ------------------------------------------------------------------ serving

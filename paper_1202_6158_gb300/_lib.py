@@ -132,6 +132,7 @@ def load(path: str = LIB_PATH):
                         ctypes.c_int),
         "di_get_trace": ([vp, vp, i32, ctypes.POINTER(i32)], ctypes.c_int),
         "di_get_state": ([vp, vp, vp], ctypes.c_int),
+        "di_set_state": ([vp, vp, vp, f64, ctypes.POINTER(f64)], ctypes.c_int),
         "di_get_profile": ([vp, ctypes.POINTER(di_profile)], ctypes.c_int),
         "di_power_noalloc": ([i32, vp, vp, i64, vp, f64, f64, i32, vp, ctypes.POINTER(di_stats), vp], ctypes.c_int),
         "di_plan_lanes": ([vp, vp, i32, i64, vp], ctypes.c_int),

@@ -474,4 +474,16 @@ di_status di_get_state(const di_graph *g, double *F_out, double *H_out) {
     return copy_state(g, F_out, is_device_ptr(F_out), H_out, is_device_ptr(H_out));
 }
 
+di_status di_set_state(di_graph *g, const double *F_in, const double *H_in, double rtol, double *deviation) {
+    g_last_error.clear();
+    if (di_status cr = check_graph(g); cr != DI_OK) return cr;
+    if (!F_in || !H_in) return set_error(DI_EINVAL, "F_in and H_in must both be given");
+    if (!(rtol >= 0.0) || !std::isfinite(rtol)) return set_error(DI_EINVAL, "rtol must be finite and >= 0");
+    if (g->n == 0) {
+        if (deviation) *deviation = 0.0;
+        return DI_OK;
+    }
+    return set_state(g, F_in, is_device_ptr(F_in), H_in, is_device_ptr(H_in), rtol, deviation);
+}
+
 }  // extern "C"

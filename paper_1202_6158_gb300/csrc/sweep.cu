@@ -37,6 +37,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <limits>
 #include <vector>
 
@@ -1194,6 +1195,140 @@ di_status copy_state(const di_graph *gc, double *F_out, bool F_dev, double *H_ou
         if (r != DI_OK) return r;
     }
     DI_CUDA(cudaStreamSynchronize(g->stream));
+    return DI_OK;
+}
+
+namespace {
+
+// a saved state in the caller's numbering, moved into the internal one; flags non-finite values
+__global__ void k_state_in(int n, const int *__restrict__ perm, const double *__restrict__ F_in,
+                           const double *__restrict__ H_in, double *__restrict__ F, double *__restrict__ H,
+                           int *__restrict__ bad) {
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+        const double f = F_in[perm[r]], h = H_in[perm[r]];
+        if (!isfinite(f) || !isfinite(h)) atomicOr(bad, 1);
+        F[r] = f;
+        H[r] = h;
+    }
+}
+
+// Theorem 1 residual, first part: Z = F_0 - H - F with F_0 = (1-d)V
+__global__ void k_state_z(int n, double omd, const double *__restrict__ V, const double *__restrict__ F,
+                          const double *__restrict__ H, double *__restrict__ Z) {
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+        Z[r] = omd * (V ? V[r] : 1.0 / (double)n) - H[r] - F[r];
+}
+
+// then Z += dPH: a warp per row i adds d*H_i/#out_i to every child
+__global__ void k_state_dph(int n, const RowRec<double> *__restrict__ rec, const int *__restrict__ col_idx,
+                            const double *__restrict__ H, double *__restrict__ Z) {
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+        const RowRec<double> rr = rec[i];
+        const double w = H[i] * rr.inv;
+        if (w == 0.0) continue;
+        for (int k = lane; k < rr.deg; k += 32) atomicAdd(Z + col_idx[rr.beg + k], w);
+    }
+}
+
+// max_j |Z_j| and max_j (|H_j| + |F_j| + (1-d)V_j), as non-negative doubles ordered by their bits
+__global__ void k_state_max(int n, double omd, const double *__restrict__ V, const double *__restrict__ F,
+                            const double *__restrict__ H, const double *__restrict__ Z,
+                            unsigned long long *__restrict__ out) {
+    double zm = 0.0, sm = 0.0;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+        zm = fmax(zm, fabs(Z[r]));
+        sm = fmax(sm, fabs(H[r]) + fabs(F[r]) + omd * (V ? V[r] : 1.0 / (double)n));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        zm = fmax(zm, __shfl_down_sync(kFull, zm, o));
+        sm = fmax(sm, __shfl_down_sync(kFull, sm, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(out, (unsigned long long)__double_as_longlong(zm));
+        atomicMax(out + 1, (unsigned long long)__double_as_longlong(sm));
+    }
+}
+
+}  // namespace
+
+di_status set_state(di_graph *g, const double *F_in, bool F_dev, const double *H_in, bool H_dev, double rtol,
+                    double *deviation) {
+    cudaStream_t s = g->stream;
+    const int n = g->n;
+    const int npad = g->G * g->chunk;
+    di_status r = ensure_fluid(g, DI_FP64);
+    if (r != DI_OK) return r;
+    double *bufs[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // F_in, H_in copies, F, H, Z
+    int *bad = nullptr;
+    unsigned long long *mx = nullptr;
+    auto release = [&]() {
+        for (double *b : bufs)
+            if (b) cudaFreeAsync(b, s);
+        if (bad) cudaFreeAsync(bad, s);
+        if (mx) cudaFreeAsync(mx, s);
+        cudaStreamSynchronize(s);
+    };
+    const size_t bytes = sizeof(double) * (size_t)n;
+    for (int k = 0; k < 5; ++k) {
+        if ((k == 0 && F_dev) || (k == 1 && H_dev)) continue;
+        if (cudaMallocAsync(&bufs[k], k >= 2 ? sizeof(double) * (size_t)npad : bytes, s) != cudaSuccess) {
+            release();
+            return cuda_fail(cudaGetLastError(), "cudaMallocAsync(state)");
+        }
+    }
+    DI_CUDA(cudaMallocAsync(&bad, sizeof(int), s));
+    DI_CUDA(cudaMallocAsync(&mx, 2 * sizeof(unsigned long long), s));
+    DI_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    DI_CUDA(cudaMemsetAsync(mx, 0, 2 * sizeof(unsigned long long), s));
+    const double *Fs = F_in, *Hs = H_in;
+    if (!F_dev) {
+        DI_CUDA(cudaMemcpyAsync(bufs[0], F_in, bytes, cudaMemcpyHostToDevice, s));
+        Fs = bufs[0];
+    }
+    if (!H_dev) {
+        DI_CUDA(cudaMemcpyAsync(bufs[1], H_in, bytes, cudaMemcpyHostToDevice, s));
+        Hs = bufs[1];
+    }
+    double *F = bufs[2], *H = bufs[3], *Z = bufs[4];
+    DI_CUDA(cudaMemsetAsync(F, 0, sizeof(double) * (size_t)npad, s));
+    DI_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * (size_t)npad, s));
+    const int grid = elem_grid(g, n);
+    k_state_in<<<grid, 256, 0, s>>>(n, g->perm, Fs, Hs, F, H, bad);
+    k_state_z<<<grid, 256, 0, s>>>(n, 1.0 - g->d, g->V, F, H, Z);
+    k_state_dph<<<g->num_sms * 8, 256, 0, s>>>(n, g->rec64, g->col_idx, H, Z);
+    k_state_max<<<grid, 256, 0, s>>>(n, 1.0 - g->d, g->V, F, H, Z, mx);
+    cudaError_t e = cudaGetLastError();
+    int hbad = 0;
+    unsigned long long hm[2] = {0ull, 0ull};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hm, mx, sizeof(hm), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        release();
+        return cuda_fail(e, "state check");
+    }
+    if (hbad) {
+        release();
+        return set_error(DI_EINVAL, "di_set_state: F or H holds a NaN or an infinity");
+    }
+    double zmax, scale;
+    std::memcpy(&zmax, &hm[0], sizeof(double));
+    std::memcpy(&scale, &hm[1], sizeof(double));
+    const double dev = scale > 0.0 ? zmax / scale : zmax;
+    if (deviation) *deviation = dev;
+    if (!(dev <= rtol)) {
+        release();
+        return set_error(DI_EINVAL, "di_set_state: the state breaks Theorem 1 (H + F = (1-d)V + dPH): relative "
+                                    "deviation " + std::to_string(dev) + " > rtol " + std::to_string(rtol));
+    }
+    // accepted: the graph's FP64 state becomes (F, H), as if its last solve had stopped there
+    DI_CUDA(cudaMemcpyAsync(g->F64, F, sizeof(double) * (size_t)npad, cudaMemcpyDeviceToDevice, s));
+    DI_CUDA(cudaMemcpyAsync(g->H, H, sizeof(double) * (size_t)npad, cudaMemcpyDeviceToDevice, s));
+    g->last_prec = DI_FP64;
+    g->last_trace_on = 0;
+    release();
     return DI_OK;
 }
 
