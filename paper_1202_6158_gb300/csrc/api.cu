@@ -251,6 +251,10 @@ __global__ void k_outdeg(int n, const int *__restrict__ row_ptr, int *__restrict
 }
 }  // namespace
 
+// the Theorem 1 check and load of a saved state (sweep.cu)
+di_status set_state(di_graph *g, const double *F_in, bool F_dev, const double *H_in, bool H_dev, double rtol,
+                    double *deviation);
+
 static di_status copy_out(void *dst, const void *src_dev, size_t bytes, cudaStream_t s) {
     if (!dst || bytes == 0) return DI_OK;
     DI_CUDA(cudaMemcpyAsync(dst, src_dev, bytes, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,

@@ -342,8 +342,6 @@ void pool_free(BatchPool *p, cudaStream_t s);
 long long pool_bytes(const di_graph *g, int lanes);
 di_status pool_build_loop(di_graph *g, BatchPool *p, int slot);
 di_status set_out_classes(di_graph *g, int cut1, int cut2);
-di_status set_state(di_graph *g, const double *F_in, bool F_dev, const double *H_in, bool H_dev, double rtol,
-                    double *deviation);
 di_status batch_args(di_graph *g, int k, const int32_t *seed_ptr, const int32_t *seeds, const double *w, double tol,
                      std::vector<int32_t> &hp, std::vector<int32_t> &hs, std::vector<double> &hw);
 // row widths 4, 8, 16, 32, 64 lanes are slots 0..4: the narrowest that holds k lanes
