@@ -501,6 +501,20 @@ di_status di_server_submit(di_server *s, int32_t graph, const int32_t *seeds, co
  */
 di_status di_server_poll(di_server *s, double wait_s, di_completion *out, int32_t cap, int32_t *nout);
 
+/*
+ * Withdraw a submitted query.  A queued query is removed at once; a query in a
+ * lane stops at the end of the round in flight, and its lane is cleared and
+ * given to the next queued query.  Either way the library writes nothing more
+ * to the query's H_out (the caller may free it when the call returns) and
+ * di_server_poll returns no completion for it.
+ *   cancelled  host int32_t*, may be NULL: 1 when the query was withdrawn, 0
+ *              when the ticket is not queued or running: it finished (its
+ *              completion is, or will be, returned by di_server_poll), was
+ *              cancelled before, or was never issued.  The call returns DI_OK
+ *              in all these cases.
+ */
+di_status di_server_cancel(di_server *s, int64_t ticket, int32_t *cancelled);
+
 /* Counters of one graph's lane pool since the server was created. */
 typedef struct {
     int64_t rounds;          /* launches of the sweep loop */
@@ -513,6 +527,7 @@ typedef struct {
     double device_ms;        /* CUDA-event time of the rounds, from lane admission to the lane-state copy */
     int32_t lanes;
     int32_t pad;
+    int64_t cancelled;       /* queries withdrawn by di_server_cancel */
 } di_server_graph_stats;
 
 di_status di_server_stats(const di_server *s, int32_t graph, di_server_graph_stats *out);

@@ -26,7 +26,7 @@ __all__ = ["DiGraph", "DiError", "DI_FP64", "DI_FP32_MIXED", "DI_OK", "DI_EINVAL
            "di_graph_create", "di_free", "di_solve", "di_solve_ex", "di_solve_update", "di_autotune", "di_autotune_batch", "di_query", "di_query_batch", "di_query_batch_ex", "di_power", "di_power_ex", "di_graph_export",
            "di_get_trace", "di_get_state", "di_set_state", "di_get_profile", "di_power_noalloc", "di_version", "di_selftest_wait", "load",
            "di_plan_lanes", "di_server_create", "di_server_lanes", "di_server_submit", "di_server_poll",
-           "di_server_pending", "di_server_stats", "di_server_free", "di_clock", "DiServer"]
+           "di_server_pending", "di_server_stats", "di_server_cancel", "di_server_free", "di_clock", "DiServer"]
 
 
 def load():
@@ -385,6 +385,12 @@ def di_server_pending(handle) -> tuple:
     return q.value, r.value
 
 
+def di_server_cancel(handle, ticket) -> bool:
+    c = ctypes.c_int32(0)
+    check(load().di_server_cancel(handle, int(ticket), ctypes.byref(c)))
+    return bool(c.value)
+
+
 def di_server_free(handle) -> None:
     if handle:
         load().di_server_free(handle)
@@ -421,6 +427,13 @@ class DiServer:
 
     def pending(self):
         return di_server_pending(self.handle)
+
+    def cancel(self, ticket):
+        """Withdraw a queued or running query; True when it was withdrawn (no completion follows)."""
+        ok = di_server_cancel(self.handle, ticket)
+        if ok:
+            self._keep.pop(ticket, None)
+        return ok
 
     def stats(self, graph):
         return di_server_stats(self.handle, graph)

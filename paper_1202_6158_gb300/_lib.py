@@ -92,7 +92,8 @@ class di_batch_tune_result(ctypes.Structure):
 class di_server_graph_stats(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_int64), ("sweeps", ctypes.c_int64), ("edges_pushed", ctypes.c_int64),
                 ("sources_pushed", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
-                ("width_sweeps", ctypes.c_int64), ("device_ms", ctypes.c_double), ("lanes", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("width_sweeps", ctypes.c_int64), ("device_ms", ctypes.c_double), ("lanes", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("cancelled", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
@@ -142,6 +143,7 @@ def load(path: str = LIB_PATH):
         "di_server_poll": ([vp, f64, vp, i32, ctypes.POINTER(i32)], ctypes.c_int),
         "di_server_stats": ([vp, i32, ctypes.POINTER(di_server_graph_stats)], ctypes.c_int),
         "di_server_pending": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64)], ctypes.c_int),
+        "di_server_cancel": ([vp, i64, ctypes.POINTER(i32)], ctypes.c_int),
         "di_server_free": ([vp], None),
         "di_clock": ([], f64),
         "di_last_error": ([], ctypes.c_char_p),

@@ -38,6 +38,7 @@ struct SrvReq {
     double *out = nullptr;   // the caller's buffer (NULL: result dropped)
     double *kout = nullptr;  // the address the retire kernel writes, NULL when staged or dropped
     double t_submit = 0.0, t_admit = 0.0;
+    bool cancelled = false;  // running lane: cleared, not copied out, at the end of its round
 };
 
 struct SrvPool {
@@ -143,8 +144,16 @@ di_status retire_lanes(SrvPool &p) {
     for (int q = 0; q < p.K; ++q) {
         if (!p.busy[q]) continue;
         const BatchQ &b = p.bp->h_bq[q];
-        if (!(b.active && b.done && b.confirmed)) continue;
         const SrvReq &r = p.lane[q];
+        if (r.cancelled) {  // cleared only: the caller's buffer is not written, no completion
+            direct.lane[direct.count] = q;
+            direct.out[direct.count] = nullptr;
+            direct.count += 1;
+            p.busy[q] = 0;
+            p.retire_mask |= 1ull << q;
+            continue;
+        }
+        if (!(b.active && b.done && b.confirmed)) continue;
         di_completion c = {};
         c.ticket = r.ticket;
         c.graph = p.index;
@@ -439,6 +448,29 @@ di_status di_server_poll(di_server *s, double wait_s, di_completion *out, int32_
         s->done.pop_front();
     }
     if (nout) *nout = k;
+    return DI_OK;
+}
+
+di_status di_server_cancel(di_server *s, int64_t ticket, int32_t *cancelled) {
+    if (!s) return set_error(DI_EINVAL, "server is NULL");
+    if (cancelled) *cancelled = 0;
+    for (SrvPool *p : s->pools) {
+        for (auto it = p->queue.begin(); it != p->queue.end(); ++it) {
+            if (it->ticket != ticket) continue;
+            p->queue.erase(it);
+            p->stats.cancelled += 1;
+            if (cancelled) *cancelled = 1;
+            return DI_OK;
+        }
+        for (int q = 0; q < p->K; ++q) {
+            if (!p->busy[q] || p->lane[q].ticket != ticket || p->lane[q].cancelled) continue;
+            // the lane's round may be in flight: it is cleared when that round ends
+            p->lane[q].cancelled = true;
+            p->stats.cancelled += 1;
+            if (cancelled) *cancelled = 1;
+            return DI_OK;
+        }
+    }
     return DI_OK;
 }
 

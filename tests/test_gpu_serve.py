@@ -119,6 +119,41 @@ def test_lanes_refill_under_a_small_budget(di, graphs):
     G.close()
 
 
+def test_cancel_queued_and_running_queries(di, graphs):
+    g = graphs[1]
+    G = di.DiGraph(g.n, g.row_ptr, g.col_idx, D)
+    lane_bytes = 16 * g.n + 4 * 1024 * 8
+    budget = 12 * lane_bytes + 64 * g.n
+    with di.DiServer([G], mem_budget=budget, round_sweeps=4) as srv:
+        K = srv.lanes()[0]
+        reqs = [{"graph": 0, "seeds": gg.seed_set(g.n, 1, 8, 78, i), "tol": 1e-7, "out": np.full(g.n, -7.0)}
+                for i in range(3 * K)]
+        tickets = [srv.submit(0, r["seeds"], r["tol"], r["out"]) for r in reqs]
+        srv.poll(0.0)  # the first K queries take the lanes and their first round starts
+        assert srv.pending() == (2 * K, K)
+        gone = {1, K + 2, 2 * K + 5}  # one running, two queued
+        for i in sorted(gone):
+            assert srv.cancel(tickets[i])
+        assert srv.pending()[0] == 2 * K - 2
+        assert not srv.cancel(tickets[1])      # already withdrawn
+        assert not srv.cancel(10 ** 12)        # never issued
+        done = {c["ticket"]: c for c in srv.drain(120.0)}
+        assert not srv.cancel(tickets[0])      # finished
+        st = srv.stats(0)
+    assert set(done) == {t for i, t in enumerate(tickets) if i not in gone}
+    assert st["cancelled"] == 3 and st["admitted"] == 3 * K - 2 and st["completed"] == 3 * K - 3
+    for i in gone:
+        assert np.all(reqs[i]["out"] == -7.0)  # never written
+    # every lane was reused after the cancelled one was cleared: later queries are unaffected
+    for i, (t, r) in enumerate(zip(tickets, reqs)):
+        if i in gone:
+            continue
+        Ha, st_a, _ = G.query_batch([r["seeds"]], r["tol"])
+        assert done[t]["status"] == 0
+        assert np.abs(Ha[0] - r["out"]).sum() <= done[t]["bound"] + st_a[0]["bound"] + 2 * FP32_ALLOW
+    G.close()
+
+
 def test_weighted_query_and_dropped_output(di, graphs):
     g = graphs[0]
     G = di.DiGraph(g.n, g.row_ptr, g.col_idx, D)
