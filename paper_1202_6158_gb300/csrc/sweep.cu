@@ -239,6 +239,83 @@ __device__ __forceinline__ float rec_inv<float>(int4 r) { return __int_as_float(
 constexpr int kPer = kStep / 32;  // nodes per lane and step
 static_assert(kPer % 4 == 0 && kStep <= 256, "groups of four nodes per lane; step positions fit a byte");
 
+// The scan CTA's six sums at once (fixed point and counts, so exact in any order):
+// warp trees, one barrier, then thread k < 6 adds value k of the eight warps.
+__device__ __forceinline__ void block_sums6(long long v[6], long long (*sh)[kWarps]) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[k] = warp_sum(v[k]);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) sh[k][w] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        long long a = 0;
+#pragma unroll
+        for (int w2 = 0; w2 < kWarps; ++w2) a += sh[threadIdx.x][w2];
+        sh[threadIdx.x][0] = a;  // read back by thread 0 after the next barrier
+    }
+}
+
+// The list offsets of every warp of the grid, built by the last scan CTA: for rows
+// L = 1 .. kCountRows-1, pre[L*(W+1) + g] = sum of fcount[L*W + j] over j < g and
+// pre[L*(W+1) + W] = the row's total (W = G * kWarps).  Thread t takes the CTAs t,
+// t + 256, ...: it reads each CTA's eight counts of a row with two 16-byte loads and
+// keeps their sum; one warp per row scans those sums; the same thread then writes
+// the CTA's eight offsets.  s_tot holds (kCountRows-1) * G ints.
+__device__ void scan_offsets_last(const int *__restrict__ fcount, int G, int W, int *__restrict__ pre, int *s_tot,
+                                  int *s_rowtot) {
+    constexpr int R = kCountRows - 1;
+    for (int b = threadIdx.x; b < G; b += kScanThreads) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int4 *p = reinterpret_cast<const int4 *>(fcount + (r + 1) * W + b * kWarps);
+            const int4 x = __ldcg(p), y = __ldcg(p + 1);
+            s_tot[r * G + b] = x.x + x.y + x.z + x.w + y.x + y.y + y.z + y.w;
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w < R) {  // warp w: exclusive scan of row w's CTA sums, in place
+        int *t = s_tot + w * G;
+        const int per = (G + 31) / 32, b0 = min(G, lane * per), b1 = min(G, b0 + per);
+        int a = 0;
+        for (int b = b0; b < b1; ++b) a += t[b];
+        int x = a;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_rowtot[w] = x;
+        int run = x - a;
+        for (int b = b0; b < b1; ++b) {
+            const int c = t[b];
+            t[b] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < G; b += kScanThreads) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int4 *p = reinterpret_cast<const int4 *>(fcount + (r + 1) * W + b * kWarps);
+            const int4 x = __ldcg(p), y = __ldcg(p + 1);
+            const int c[kWarps] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+            int *o = pre + (r + 1) * (W + 1) + b * kWarps;
+            int run = s_tot[r * G + b];
+#pragma unroll
+            for (int k = 0; k < kWarps; ++k) {
+                o[k] = run;
+                run += c[k];
+            }
+        }
+    }
+    if (threadIdx.x < R) pre[(threadIdx.x + 1) * (W + 1) + W] = s_rowtot[threadIdx.x];
+}
+static_assert(kWarps == 8, "a CTA's counts of a row are read as two int4");
+
 template <typename FT, bool WGT>
 struct ScanRing {
     static constexpr int kF = kStep * (int)sizeof(FT);
@@ -267,7 +344,8 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
     __shared__ __align__(128) unsigned char s_ring[kWarps * Ring::kWarpBytes];
     __shared__ __align__(8) unsigned long long s_bar[kWarps * Ring::kStages];
     __shared__ unsigned char s_q[kWarps][kStep];  // the selected nodes of a step, by position in the step
-    __shared__ long long s_red[kWarps];
+    __shared__ long long s_red[6][kWarps];
+    __shared__ int s_rowtot[kCountRows - 1];
     __shared__ unsigned s_ticket;
     __shared__ int s_err;
     if (st->done) return;
@@ -445,20 +523,17 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
         for (int L = 0; L < kLists; ++L) fcount[L * W + g] = run[L] - start[L];
         fcount[kChunkRow * W + g] = hub_chunks;
     }
-    const long long bl1 = block_sum(l1, s_red);
-    const long long bout = block_sum(s_out, s_red);
-    const long long bdng = block_sum(s_dng, s_red);
-    const long long bsr = block_sum((long long)srcs, s_red);
-    const long long ben = block_sum((long long)entries, s_red);
-    const long long bpe = pull ? block_sum(pedges, s_red) : 0;
+    long long sums[6] = {l1, s_out, s_dng, (long long)srcs, (long long)entries, pull ? pedges : 0};
+    block_sums6(sums, s_red);
+    __syncthreads();
     if (threadIdx.x == 0) {
         ScanPartial p;
-        p.l1 = bl1;
-        p.out = bout;
-        p.dng = bdng;
-        p.edges = bpe;  // push sweeps: added by the push kernel
-        p.srcs = bsr;
-        p.entries = ben;
+        p.l1 = s_red[0][0];
+        p.out = s_red[1][0];
+        p.dng = s_red[2][0];
+        p.edges = s_red[5][0];  // push sweeps: 0 here, added by the push kernel
+        p.srcs = s_red[3][0];
+        p.entries = s_red[4][0];
         p.l1d = 0.0;
         p.err = s_err;
         part[blockIdx.x] = p;
@@ -472,7 +547,11 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
     if (s_ticket == gridDim.x - 1) {
         __threadfence();
         // list 0 (dangling nodes) stays empty: the scan finishes those nodes itself
-        prefix_counts_staged(fcount, W, pre, reinterpret_cast<int *>(s_ring), (int)(sizeof(s_ring) / sizeof(int)), 1);
+        if ((kCountRows - 1) * (int)gridDim.x <= (int)(sizeof(s_ring) / sizeof(int)))
+            scan_offsets_last(fcount, (int)gridDim.x, W, pre, reinterpret_cast<int *>(s_ring), s_rowtot);
+        else
+            prefix_counts_staged(fcount, W, pre, reinterpret_cast<int *>(s_ring), (int)(sizeof(s_ring) / sizeof(int)),
+                                 1);
         if (threadIdx.x == 0) *ticket = 0u;
     }
 }
