@@ -261,7 +261,9 @@ struct di_graph {
     int *region = nullptr;             // [kLists][W+1]: offset of each list's entries per sub-chunk
     int *fcount = nullptr;             // [kCountRows][W]: entries written per sub-chunk in the last sweep, per
                                        // list, then the chunks of the hub rows listed
-    int *pre = nullptr;                // [kCountRows][W+1]: exclusive prefix of fcount per row (last scan CTA)
+    int *pre = nullptr;                // kCountRows*(W+1) ints: the two-level list offsets the scan writes,
+                                       // [(L-1)G + b] the total of row L in scan CTA b, [L W + g] sub-chunk
+                                       // g's offset within its CTA's part (L = 1 .. kCountRows-1)
     unsigned *ticket = nullptr;        // finished scan CTAs of the current sweep
     void *sel = nullptr;               // Sel<FT>[n]: the selected nodes of a sweep
     double *F64 = nullptr;
@@ -368,6 +370,7 @@ template <typename FT> inline Sel<FT> *sel_of(const di_graph *g) { return reinte
 
 // the push of one sweep on stream s (push.cu)
 template <typename FT> void launch_push(di_graph *g, FT *F, cudaStream_t s);
+di_status push_setup();
 template <typename FT> void launch_pull(di_graph *g, FT *F, cudaStream_t s);
 
 // push CTAs: the pushes scale with edges, not nodes, so small graphs still get push_per_sm CTAs per SM

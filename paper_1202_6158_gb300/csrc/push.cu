@@ -59,6 +59,41 @@ __device__ __forceinline__ void push_row_lanes(const int *__restrict__ col_idx, 
     if (t < deg) push_one(F, hot, n_hot, __ldg(col_idx + beg + t), w, pol);
 }
 
+// The list offsets of one row of a sweep's lists, in the two levels the scan writes into pre:
+//   pre[(L-1) G + b]   the total of row L over scan CTA b (L = 1 .. kCountRows-1),
+//   pre[L W + 8b + k]  the offset of sub-chunk 8b + k (warp k of CTA b) within CTA b's part.
+// Each push CTA turns the CTA totals into an exclusive prefix per row in shared memory
+// (cta[b], the row's total at cta[G]); sub-chunk g's offset is cta[g / 8] plus its local one.
+struct ListOffs {
+    const int *cta;  // shared: G + 1 entries
+    const int *loc;  // global: W = 8G entries
+    int W;
+    __device__ int total() const { return cta[W >> 3]; }
+    __device__ int at(int g) const { return g < W ? cta[g >> 3] + __ldg(loc + g) : total(); }
+    // the sub-chunk holding item t < total: the last g with at(g) <= t (the CTA by a binary
+    // search in shared memory, then the warp among the CTA's eight offsets)
+    __device__ int find(int t) const {
+        int lo = 0, hi = W >> 3;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (cta[mid] <= t) lo = mid; else hi = mid;
+        }
+        const int r = t - cta[lo];
+        const int4 *p = reinterpret_cast<const int4 *>(loc + 8 * lo);
+        const int4 x = __ldg(p), y = __ldg(p + 1);
+        const int k = (x.y <= r) + (x.z <= r) + (x.w <= r) + (y.x <= r) + (y.y <= r) + (y.z <= r) + (y.w <= r);
+        return 8 * lo + k;
+    }
+    // the same, knowing the answer is at least lo: a few steps forward, then a search
+    __device__ int find_from(int t, int lo) const {
+        for (int k = 0; k < 4; ++k) {
+            if (at(lo + 1) > t) return lo;
+            ++lo;
+        }
+        return find(t);
+    }
+};
+
 // Walks the hub chunks [c0, c1) of a sweep in order (every thread of a CTA holds the same
 // state).  Chunks are numbered sub-chunk by sub-chunk through the prefix sums of the scan's per
 // warp chunk counts (pch), then entry by entry within a sub-chunk's list-3 region; an entry's
@@ -68,8 +103,9 @@ template <typename FT>
 struct HubWalk {
     const RowRec<FT> *rec;
     const Sel<FT> *sel;
-    const int *r3, *f3, *pch;
-    int W, g, e, e_end, cum, nc, beg, deg, clen;
+    const int *r3, *f3;
+    ListOffs pch;
+    int g, e, e_end, cum, nc, beg, deg, clen;
     FT w;
     __device__ void load_entry() {
         const Sel<FT> x = sel[e];
@@ -82,10 +118,10 @@ struct HubWalk {
     }
     // position on chunk c (the first chunk this CTA takes)
     __device__ void start(int c) {
-        g = find_sub(pch, W, c);
+        g = pch.find(c);
         e = __ldg(r3 + g);
         e_end = e + __ldcg(f3 + g);
-        cum = __ldg(pch + g);
+        cum = pch.at(g);
         load_entry();
         while (cum + nc <= c) {  // the sub-chunk's entries hold chunk c
             cum += nc;
@@ -138,12 +174,39 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
     __shared__ long long s_red[kWarps];
     __shared__ __align__(128) int s_hcol[kWarps][kHubChunk + 8];  // a hub chunk's column indices, per warp
     __shared__ __align__(8) unsigned long long s_hbar[kWarps];
+    extern __shared__ int s_cta[];  // kCountRows-1 rows of G+1: the CTA-level list offsets
     if (st->done || st->pull) return;
+    constexpr int R = kCountRows - 1;
     for (int t = threadIdx.x; t < kHotSlots; t += kScanThreads) hot[t] = (FT)0;
+    for (int i = threadIdx.x; i < R * G; i += kScanThreads) {
+        const int r = i / G;
+        s_cta[r * (G + 1) + (i - r * G)] = __ldg(pre + i);
+    }
     __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w < R) {  // warp w: exclusive prefix of row w + 1's CTA totals, in place; the total at [G]
+        int *t = s_cta + w * (G + 1);
+        const int per = (G + 31) / 32, b0 = min(G, lane * per), b1 = min(G, b0 + per);
+        int a = 0;
+        for (int b = b0; b < b1; ++b) a += t[b];
+        int x = a;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) t[G] = x;
+        int run = x - a;
+        for (int b = b0; b < b1; ++b) {
+            const int c = t[b];
+            t[b] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    auto offs = [&](int L) { return ListOffs{s_cta + (L - 1) * (G + 1), pre + L * W, W}; };
     const unsigned long long pol = evict_last_policy(), pol_col = evict_first_policy();
     const int wait_polls = st->wait_polls;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nwarps = gridDim.x * kWarps, gw = blockIdx.x * kWarps + w;
     long long edges = 0;
     // class 3: the hub rows, cut into chunks of at most kHubChunk out-links.  CTA b takes the
@@ -156,13 +219,13 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
     // and with FP32 fluid a small weight added after the larger ones of the other classes is
     // rounded away more often (R-MAT 2^23: 1.5e-7 against 6e-7 in L1 from FP64).
     {
-        const int *pch = pre + kChunkRow * (W + 1);
-        const int nch = __ldg(pch + W);
+        const ListOffs pch = offs(kChunkRow);
+        const int nch = pch.total();
         const int cb0 = (int)((long long)blockIdx.x * nch / gridDim.x);
         const int cb1 = (int)((long long)(blockIdx.x + 1) * nch / gridDim.x);
         int c = cb0 + w;
         if (c < cb1) {
-            HubWalk<FT> hw{rec, sel, region + 3 * (W + 1), fcount + 3 * W, pch, W};
+            HubWalk<FT> hw{rec, sel, region + 3 * (W + 1), fcount + 3 * W, pch};
             hw.start(c);
             const unsigned bar = smem_addr(&s_hbar[w]);
             int *stage = s_hcol[w];
@@ -236,15 +299,16 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
         // which interleaves heavy and light rows on any id order; lane j first finds and fetches
         // the entry and row record of the warp's j-th node of each group of 32, so only the
         // column loads remain on each node's path
-        const int *p2 = pre + 2 * (W + 1), *r2 = region + 2 * (W + 1);
-        const int tot = __ldg(p2 + W);
+        const ListOffs p2 = offs(2);
+        const int *r2 = region + 2 * (W + 1);
+        const int tot = p2.total();
         for (long long k0 = 0; gw + k0 * nwarps < tot; k0 += 32) {
             const long long t = gw + (k0 + lane) * nwarps;
             int mb = 0, md = 0;
             FT mw = (FT)0;
             if (t < tot) {
-                const int mg = find_sub(p2, W, (int)t);
-                const Sel<FT> e = sel[__ldg(r2 + mg) + ((int)t - __ldg(p2 + mg))];
+                const int mg = p2.find((int)t);
+                const Sel<FT> e = sel[__ldg(r2 + mg) + ((int)t - p2.at(mg))];
                 const RowRec<FT> rr = rec[e.node];
                 mb = rr.beg;
                 md = rr.deg;
@@ -267,13 +331,14 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
         // class 1: a lane per node, kInFlight nodes per lane at a time (at most 8 out-links each)
         constexpr int kInFlight = 4;
         static_assert(kOutCut1 <= 8 && kInFlight == 4, "class-1 rows are pushed in two groups of four links");
-        const int *p1 = pre + 1 * (W + 1), *r1 = region + 1 * (W + 1);
-        const int tot = __ldg(p1 + W);
+        const ListOffs p1 = offs(1);
+        const int *r1 = region + 1 * (W + 1);
+        const int tot = p1.total();
         const int per = (tot + nwarps - 1) / nwarps;
         const int t_beg = min(tot, gw * per), t_end = min(tot, t_beg + per);
         int gs = 0;
         if (t_beg < t_end) {
-            if (lane == 0) gs = find_sub(p1, W, t_beg);
+            if (lane == 0) gs = p1.find(t_beg);
             gs = __shfl_sync(kFull, gs, 0);
         }
         for (int t0 = t_beg; t0 < t_end; t0 += 32 * kInFlight) {
@@ -286,8 +351,8 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
                 const int t = t0 + 32 * u + lane;
                 pos[u] = -1;
                 if (t < t_end) {
-                    mg = find_sub_from(p1, W, t, mg);
-                    pos[u] = __ldg(r1 + mg) + (t - __ldg(p1 + mg));
+                    mg = p1.find_from(t, mg);
+                    pos[u] = __ldg(r1 + mg) + (t - p1.at(mg));
                 }
             }
             // every lane's last rank is below the next group's first: restart from the largest
@@ -453,9 +518,21 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_sweep_pull(const int *__res
     }
 }
 
+// the push's dynamic shared memory: the CTA-level list offsets of kCountRows-1 rows
+inline size_t push_dyn_smem(const di_graph *g) { return sizeof(int) * (kCountRows - 1) * (size_t)(g->G + 1); }
+
+// allows the largest dynamic shared memory the push can take (G <= kMaxScanBlocks) on the
+// current device; called before a sweep loop is captured
+di_status push_setup() {
+    const int bytes = (int)(sizeof(int) * (kCountRows - 1) * (size_t)(kMaxScanBlocks + 1));
+    DI_CUDA(cudaFuncSetAttribute(k_sweep_push<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    DI_CUDA(cudaFuncSetAttribute(k_sweep_push<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    return DI_OK;
+}
+
 template <typename FT>
 void launch_push(di_graph *g, FT *F, cudaStream_t s) {
-    k_sweep_push<FT><<<push_grid(g), kScanThreads, 0, s>>>(rec_of<FT>(g), g->col_idx, F, g->region, g->pre,
+    k_sweep_push<FT><<<push_grid(g), kScanThreads, push_dyn_smem(g), s>>>(rec_of<FT>(g), g->col_idx, F, g->region, g->pre,
                                                            g->fcount, g->W, sel_of<FT>(g), g->n_hot, g->part, g->G,
                                                            g->st);
 }

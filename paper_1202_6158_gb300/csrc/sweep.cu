@@ -13,7 +13,9 @@
 //                      in ascending id, with warp prefix sums; each warp writes at
 //                      offsets fixed at create time, so there are no atomics.  It
 //                      also sums the removed mass: (1-d)*sent for nodes with
-//                      children, sent for dangling ones (Section 3.3).
+//                      children, sent for dangling ones (Section 3.3).  Each CTA
+//                      writes its list totals and its warps' offsets within them;
+//                      the push builds the CTA-level prefix itself.
 //   k_sweep_push<FT>   pushes d*sent/outdeg_i along every out-link (ALGO-REF's inner
 //                      loop) with red.global.add; a CTA per node above kOutCut2
 //                      out-links, a warp per node above kOutCut1, a lane per node
@@ -258,63 +260,6 @@ __device__ __forceinline__ void block_sums6(long long v[6], long long (*sh)[kWar
     }
 }
 
-// The list offsets of every warp of the grid, built by the last scan CTA: for rows
-// L = 1 .. kCountRows-1, pre[L*(W+1) + g] = sum of fcount[L*W + j] over j < g and
-// pre[L*(W+1) + W] = the row's total (W = G * kWarps).  Thread t takes the CTAs t,
-// t + 256, ...: it reads each CTA's eight counts of a row with two 16-byte loads and
-// keeps their sum; one warp per row scans those sums; the same thread then writes
-// the CTA's eight offsets.  s_tot holds (kCountRows-1) * G ints.
-__device__ void scan_offsets_last(const int *__restrict__ fcount, int G, int W, int *__restrict__ pre, int *s_tot,
-                                  int *s_rowtot) {
-    constexpr int R = kCountRows - 1;
-    for (int b = threadIdx.x; b < G; b += kScanThreads) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int4 *p = reinterpret_cast<const int4 *>(fcount + (r + 1) * W + b * kWarps);
-            const int4 x = __ldcg(p), y = __ldcg(p + 1);
-            s_tot[r * G + b] = x.x + x.y + x.z + x.w + y.x + y.y + y.z + y.w;
-        }
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (w < R) {  // warp w: exclusive scan of row w's CTA sums, in place
-        int *t = s_tot + w * G;
-        const int per = (G + 31) / 32, b0 = min(G, lane * per), b1 = min(G, b0 + per);
-        int a = 0;
-        for (int b = b0; b < b1; ++b) a += t[b];
-        int x = a;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(kFull, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) s_rowtot[w] = x;
-        int run = x - a;
-        for (int b = b0; b < b1; ++b) {
-            const int c = t[b];
-            t[b] = run;
-            run += c;
-        }
-    }
-    __syncthreads();
-    for (int b = threadIdx.x; b < G; b += kScanThreads) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int4 *p = reinterpret_cast<const int4 *>(fcount + (r + 1) * W + b * kWarps);
-            const int4 x = __ldcg(p), y = __ldcg(p + 1);
-            const int c[kWarps] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
-            int *o = pre + (r + 1) * (W + 1) + b * kWarps;
-            int run = s_tot[r * G + b];
-#pragma unroll
-            for (int k = 0; k < kWarps; ++k) {
-                o[k] = run;
-                run += c[k];
-            }
-        }
-    }
-    if (threadIdx.x < R) pre[(threadIdx.x + 1) * (W + 1) + W] = s_rowtot[threadIdx.x];
-}
-static_assert(kWarps == 8, "a CTA's counts of a row are read as two int4");
 
 template <typename FT, bool WGT>
 struct ScanRing {
@@ -333,7 +278,7 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
                                                              const unsigned char *__restrict__ cls,
                                                              const int *__restrict__ region, int W,
                                                              int *__restrict__ fcount, int *__restrict__ pre,
-                                                             unsigned *__restrict__ ticket, Sel<FT> *__restrict__ sel,
+                                                             Sel<FT> *__restrict__ sel,
                                                              ScanPartial *__restrict__ part,
                                                              const SolveState *__restrict__ st,
                                                              double *__restrict__ H,
@@ -345,8 +290,7 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
     __shared__ __align__(8) unsigned long long s_bar[kWarps * Ring::kStages];
     __shared__ unsigned char s_q[kWarps][kStep];  // the selected nodes of a step, by position in the step
     __shared__ long long s_red[6][kWarps];
-    __shared__ int s_rowtot[kCountRows - 1];
-    __shared__ unsigned s_ticket;
+    __shared__ int s_cnt[kCountRows][kWarps];
     __shared__ int s_err;
     if (st->done) return;
     const typename Ops::Key key = Ops::key(st->T);
@@ -520,8 +464,12 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
     hub_chunks = __reduce_add_sync(kFull, hub_chunks);
     if (lane == 0) {
 #pragma unroll
-        for (int L = 0; L < kLists; ++L) fcount[L * W + g] = run[L] - start[L];
+        for (int L = 0; L < kLists; ++L) {
+            fcount[L * W + g] = run[L] - start[L];
+            s_cnt[L][w] = run[L] - start[L];
+        }
         fcount[kChunkRow * W + g] = hub_chunks;
+        s_cnt[kChunkRow][w] = hub_chunks;
     }
     long long sums[6] = {l1, s_out, s_dng, (long long)srcs, (long long)entries, pull ? pedges : 0};
     block_sums6(sums, s_red);
@@ -538,23 +486,26 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
         p.err = s_err;
         part[blockIdx.x] = p;
     }
-    // every CTA publishes its counts, then takes a ticket; the last one builds the prefixes,
-    // staging them in the (now idle) ring
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1u);
-    __syncthreads();
-    if (s_ticket == gridDim.x - 1) {
-        __threadfence();
-        // list 0 (dangling nodes) stays empty: the scan finishes those nodes itself
-        if ((kCountRows - 1) * (int)gridDim.x <= (int)(sizeof(s_ring) / sizeof(int)))
-            scan_offsets_last(fcount, (int)gridDim.x, W, pre, reinterpret_cast<int *>(s_ring), s_rowtot);
-        else
-            prefix_counts_staged(fcount, W, pre, reinterpret_cast<int *>(s_ring), (int)(sizeof(s_ring) / sizeof(int)),
-                                 1);
-        if (threadIdx.x == 0) *ticket = 0u;
+    // The list offsets, in two levels (list 0, the dangling nodes, stays empty: the scan
+    // finishes those nodes itself).  For rows L = 1 .. kCountRows-1 this CTA writes its
+    // total, pre[(L-1) G + b], and the offset of each of its warps within the CTA's part,
+    // pre[L W + 8b + k]; the push kernel turns the CTA totals into a prefix of its own, so no
+    // CTA of the scan waits for the others.  (The barrier in the sums above made s_cnt visible.)
+    if (threadIdx.x < kCountRows - 1) {
+        const int L = threadIdx.x + 1;
+        int o[kWarps], a = 0;
+#pragma unroll
+        for (int k = 0; k < kWarps; ++k) {
+            o[k] = a;
+            a += s_cnt[L][k];
+        }
+        int4 *dst = reinterpret_cast<int4 *>(pre + L * W + kWarps * blockIdx.x);
+        dst[0] = make_int4(o[0], o[1], o[2], o[3]);
+        dst[1] = make_int4(o[4], o[5], o[6], o[7]);
+        pre[(L - 1) * (int)gridDim.x + blockIdx.x] = a;
     }
 }
+static_assert(kWarps == 8, "a CTA's eight warp offsets of a row are stored as two int4");
 
 // the bounded wait of the scan on a barrier that nothing completes: every CTA must give up
 __global__ void k_selftest_wait(int polls, int *__restrict__ gave_up) {
@@ -732,11 +683,11 @@ template <typename FT>
 void launch_scan(di_graph *g, FT *F, const float *wsel, cudaStream_t s) {
     if (wsel)
         k_sweep_scan<FT, true><<<g->G, kScanThreads, 0, s>>>(g->chunk / kWarps, F, wsel, g->cls, g->region, g->W,
-                                                             g->fcount, g->pre, g->ticket, sel_of<FT>(g), g->part,
+                                                             g->fcount, g->pre, sel_of<FT>(g), g->part,
                                                              g->st, g->H, rec_of<FT>(g), g->n, static_cast<FT *>(g->wpull));
     else
         k_sweep_scan<FT, false><<<g->G, kScanThreads, 0, s>>>(g->chunk / kWarps, F, nullptr, g->cls, g->region, g->W,
-                                                              g->fcount, g->pre, g->ticket, sel_of<FT>(g), g->part,
+                                                              g->fcount, g->pre, sel_of<FT>(g), g->part,
                                                               g->st, g->H, rec_of<FT>(g), g->n, static_cast<FT *>(g->wpull));
 }
 
@@ -768,6 +719,8 @@ di_status gather_out(di_graph *g, const FT *src, const double *partials, int np,
 // Build the while-loop graph of one precision: body = scan -> push -> finalize.
 template <typename FT>
 di_status build_sweep_graph(di_graph *g, int slot, FT *F, const float *wsel) {
+    di_status r = push_setup();
+    if (r != DI_OK) return r;
     cudaGraph_t graph = nullptr;
     DI_CUDA(cudaGraphCreate(&graph, 0));
     cudaGraphConditionalHandle handle;
