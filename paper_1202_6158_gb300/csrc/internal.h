@@ -93,7 +93,7 @@ struct SolveState {
     int max_sweeps;
     int done;              // 0 running, 1 converged, 2 limit reached, 3 non-finite residual, 4 scan wait timed out
     int trace_on;
-    int body_runs;         // executions of the finalize kernel (one per loop iteration)
+    int body_runs;         // executions of the finalize kernel (one per sweep of a loop iteration)
     int exact;             // 1 when the sweep now running sums |F|_1 exactly (every kExactEvery sweeps)
     int weighted;          // ALGO-OP / OP2 selection: the threshold is never raised
     int pull;              // this sweep's direction: 0 push from the class lists, 1 pull along the in-links
