@@ -410,6 +410,22 @@ di_status di_get_state(const di_graph *g, double *F_out, double *H_out);
 di_status di_set_state(di_graph *g, const double *F_in, const double *H_in, double rtol, double *deviation);
 
 /*
+ * The debug build (libditer_debug.so, compiled with DI_DEBUG) checks the indices its sweep
+ * kernels compute before using them: list appends of the scan against their warp's region,
+ * list positions and node ids read by the push, pushed-to columns and pull link endpoints
+ * against [0, n).  A failed check records its first failure in a device word and skips the
+ * access (it never traps); the solve, query or update then returns DI_EKERNEL naming the
+ * check and the index.  The release build compiles none of it.
+ *   di_debug_build     1 in the debug build, 0 in the release build
+ *   di_debug_selftest  the debug build records one failure (code 99, index 12345) from a
+ *                      kernel that touches no memory and reports it: returns DI_EKERNEL and
+ *                      writes the recorded word, (99 << 48) | 12345, to *word (may be NULL).
+ *                      The release build returns DI_EINVAL.
+ */
+int32_t di_debug_build(void);
+di_status di_debug_selftest(uint64_t *word);
+
+/*
  * Per-kernel device times of the last solve made with opts.profile = 1.
  *   out  host di_profile*
  */

@@ -24,7 +24,7 @@ from ._lib import (DI_EINVAL, DI_ENOMEM, DI_ENOTCONVERGED, DI_ETIMEOUT, DI_FP32_
 
 __all__ = ["DiGraph", "DiError", "DI_FP64", "DI_FP32_MIXED", "DI_OK", "DI_EINVAL", "DI_ENOTCONVERGED", "DI_ETIMEOUT",
            "di_graph_create", "di_free", "di_solve", "di_solve_ex", "di_solve_update", "di_autotune", "di_autotune_batch", "di_query", "di_query_batch", "di_query_batch_ex", "di_power", "di_power_ex", "di_graph_export",
-           "di_get_trace", "di_get_state", "di_set_state", "di_get_profile", "di_power_noalloc", "di_version", "di_selftest_wait", "load",
+           "di_get_trace", "di_get_state", "di_set_state", "di_get_profile", "di_power_noalloc", "di_version", "di_selftest_wait", "di_debug_build", "di_debug_selftest", "load",
            "di_plan_lanes", "di_server_create", "di_server_lanes", "di_server_submit", "di_server_poll",
            "di_server_pending", "di_server_stats", "di_server_cancel", "di_server_free", "di_clock", "DiServer"]
 
@@ -35,6 +35,18 @@ def load():
 
 def di_version() -> str:
     return load().di_version().decode()
+
+
+def di_debug_build() -> bool:
+    """True when the loaded library is the DI_DEBUG build (device-side index checks)."""
+    return bool(load().di_debug_build())
+
+
+def di_debug_selftest() -> tuple:
+    """Debug build: records one failed check from a kernel and reports it; returns (status, word)."""
+    w = ctypes.c_uint64(0)
+    rc = load().di_debug_selftest(ctypes.byref(w))
+    return rc, w.value
 
 
 def di_selftest_wait(polls=64, ctas=8) -> int:

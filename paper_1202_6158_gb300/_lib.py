@@ -14,7 +14,8 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libditer.so")
+# DI_LIB_VARIANT=debug loads the DI_DEBUG build (device-side index checks) instead
+LIB_PATH = os.path.join(HERE, "libditer_debug.so" if os.environ.get("DI_LIB_VARIANT") == "debug" else "libditer.so")
 
 DI_OK, DI_EINVAL, DI_ENOMEM, DI_ECUDA, DI_ENOTCONVERGED, DI_ETIMEOUT, DI_EKERNEL = range(7)
 DI_FP64, DI_FP32_MIXED = 0, 1
@@ -149,6 +150,8 @@ def load(path: str = LIB_PATH):
         "di_last_error": ([], ctypes.c_char_p),
         "di_version": ([], ctypes.c_char_p),
         "di_selftest_wait": ([i32, i32, ctypes.POINTER(i32)], ctypes.c_int),
+        "di_debug_build": ([], i32),
+        "di_debug_selftest": ([ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

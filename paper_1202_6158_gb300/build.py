@@ -3,6 +3,8 @@
 Each translation unit of ``csrc/`` is compiled in parallel with
 ``-gencode arch=compute_103a,code=sm_103a -lineinfo -O3``, then linked into
 ``paper_1202_6158_gb300/libditer.so`` against the shared CUDA runtime.
+``build(debug=True)`` makes ``libditer_debug.so`` the same way with ``-DDI_DEBUG``:
+the sweep kernels check the indices they compute (see include/diter.h).
 """
 from __future__ import annotations
 
@@ -15,6 +17,7 @@ import tempfile
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libditer.so")
+LIB_DEBUG = os.path.join(HERE, "libditer_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -29,19 +32,22 @@ def sources() -> list:
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     deps.append(os.path.join(HERE, "..", "include", "diter.h"))
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: tuple = ()) -> str:
-    """Compile (if stale) and return the path of libditer.so."""
-    if not force and not _stale():
-        return LIB
+def build(force: bool = False, verbose: bool = False, extra: tuple = (), debug: bool = False) -> str:
+    """Compile (if stale) and return the path of libditer.so (libditer_debug.so with debug=True)."""
+    lib = LIB_DEBUG if debug else LIB
+    if debug:
+        extra = (*extra, "-DDI_DEBUG")
+    if not force and not _stale(lib):
+        return lib
     nvcc = _nvcc()
     cuda_home = os.path.dirname(os.path.dirname(os.path.realpath(nvcc)))
     tmpdir = tempfile.mkdtemp(prefix="diter_build_", dir=HERE)
@@ -66,18 +72,18 @@ def build(force: bool = False, verbose: bool = False, extra: tuple = ()) -> str:
                 failed.append(src)
         if failed:
             raise RuntimeError("nvcc failed on: " + ", ".join(os.path.basename(f) for f in failed))
-        out_tmp = os.path.join(tmpdir, "libditer.so")
+        out_tmp = os.path.join(tmpdir, os.path.basename(lib))
         link = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", out_tmp, *objs,
                 "-Xlinker", "-rpath", "-Xlinker", os.path.join(cuda_home, "lib64")]
         if verbose:
             print(" ".join(link), file=sys.stderr)
         subprocess.run(link, check=True)
-        os.replace(out_tmp, LIB)
+        os.replace(out_tmp, lib)
     finally:
         shutil.rmtree(tmpdir, ignore_errors=True)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv,
                 extra=tuple(a for a in sys.argv[1:] if a.startswith("-X") or a.startswith("--resource"))))

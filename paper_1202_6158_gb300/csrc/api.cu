@@ -471,6 +471,27 @@ di_status di_get_profile(const di_graph *g, di_profile *out) {
     return DI_OK;
 }
 
+int32_t di_debug_build(void) {
+#ifdef DI_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+di_status di_debug_selftest(uint64_t *word) {
+    g_last_error.clear();
+#ifdef DI_DEBUG
+    unsigned long long w = 0;
+    const di_status r = debug_selftest(&w);
+    if (word) *word = (uint64_t)w;
+    return r;
+#else
+    if (word) *word = 0;
+    return set_error(DI_EINVAL, "di_debug_selftest: this library was built without DI_DEBUG");
+#endif
+}
+
 di_status di_get_state(const di_graph *g, double *F_out, double *H_out) {
     g_last_error.clear();
     if (di_status cr = check_graph(g); cr != DI_OK) return cr;

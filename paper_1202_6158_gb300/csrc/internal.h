@@ -103,6 +103,7 @@ struct SolveState {
     int wait_polls;        // polls of each bulk-copy wait of the scan before the solve gives up
     int pause_pull;        // the in-link CSR is not built yet: a due pull stops the loop (done = 5) instead
     int undrained;         // a timed-out scan warp returned with bulk copies possibly still landing
+    int n;                 // nodes (read by the index checks of the DI_DEBUG build)
 };
 
 // batched personalized queries: up to kLanes queries interleaved in one fluid row
@@ -370,6 +371,15 @@ template <typename FT> inline Sel<FT> *sel_of(const di_graph *g) { return reinte
 
 // the push of one sweep on stream s (push.cu)
 template <typename FT> void launch_push(di_graph *g, FT *F, cudaStream_t s);
+#ifdef DI_DEBUG
+// the first failed index check of the sweep kernels since the last call, cleared (0: none)
+unsigned long long dbg_take_sweep();
+unsigned long long dbg_take_push();
+// DI_EKERNEL naming the first failed check, else DI_OK; *word (may be NULL) receives its word
+di_status debug_status(unsigned long long *word = nullptr);
+// records a failure from a kernel that touches no memory, then reports it
+di_status debug_selftest(unsigned long long *word);
+#endif
 di_status push_setup();
 template <typename FT> void launch_pull(di_graph *g, FT *F, cudaStream_t s);
 

@@ -6,6 +6,7 @@
 // at per-warp offsets; this kernel spreads those lists over the whole grid.
 #include <cuda_runtime.h>
 
+#include "dbg.cuh"
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -18,9 +19,12 @@ constexpr int kPushWaitLimit = 1 << 20;  // polls of a stage's mbarrier while dr
 // nodes, internal ids 0..n_hot-1) are summed in the CTA's shared memory: on
 // power-law graphs a single target can receive a few percent of all pushes, and
 // same-address reductions serialize in one L2 slice.
+// (n: the node count, read only by the index check of the DI_DEBUG build)
 template <typename FT>
-__device__ __forceinline__ void push_one(FT *__restrict__ F, FT *hot, int n_hot, int c, FT w,
+__device__ __forceinline__ void push_one(FT *__restrict__ F, FT *hot, int n_hot, int n, int c, FT w,
                                          unsigned long long pol) {
+    (void)n;
+    if (!DI_CHECK(c >= 0 && c < n, 4, c)) return;
     if (c >= n_hot) red_add(F + c, w, pol);
     else atomicAdd(hot + c, w);
 }
@@ -30,33 +34,34 @@ __device__ __forceinline__ void push_one(FT *__restrict__ F, FT *hot, int n_hot,
 // then the tail.
 template <typename FT>
 __device__ __forceinline__ void push_row_lanes(const int *__restrict__ col_idx, FT *__restrict__ F, FT *hot, int n_hot,
-                                               int beg, int deg, FT w, int lane, int width, unsigned long long pol) {
+                                               int n, int beg, int deg, FT w, int lane, int width,
+                                               unsigned long long pol) {
     const int head = min(deg, (4 - (beg & 3)) & 3);
-    if (lane < head) push_one(F, hot, n_hot, __ldg(col_idx + beg + lane), w, pol);
+    if (lane < head) push_one(F, hot, n_hot, n, __ldg(col_idx + beg + lane), w, pol);
     const int body = (deg - head) >> 2;
     const int4 *v4 = reinterpret_cast<const int4 *>(col_idx + beg + head);
     int k = lane;
     for (; k + width < body; k += 2 * width) {
         const int4 q = __ldg(v4 + k);
         const int4 r = __ldg(v4 + k + width);
-        push_one(F, hot, n_hot, q.x, w, pol);
-        push_one(F, hot, n_hot, q.y, w, pol);
-        push_one(F, hot, n_hot, q.z, w, pol);
-        push_one(F, hot, n_hot, q.w, w, pol);
-        push_one(F, hot, n_hot, r.x, w, pol);
-        push_one(F, hot, n_hot, r.y, w, pol);
-        push_one(F, hot, n_hot, r.z, w, pol);
-        push_one(F, hot, n_hot, r.w, w, pol);
+        push_one(F, hot, n_hot, n, q.x, w, pol);
+        push_one(F, hot, n_hot, n, q.y, w, pol);
+        push_one(F, hot, n_hot, n, q.z, w, pol);
+        push_one(F, hot, n_hot, n, q.w, w, pol);
+        push_one(F, hot, n_hot, n, r.x, w, pol);
+        push_one(F, hot, n_hot, n, r.y, w, pol);
+        push_one(F, hot, n_hot, n, r.z, w, pol);
+        push_one(F, hot, n_hot, n, r.w, w, pol);
     }
     if (k < body) {
         const int4 q = __ldg(v4 + k);
-        push_one(F, hot, n_hot, q.x, w, pol);
-        push_one(F, hot, n_hot, q.y, w, pol);
-        push_one(F, hot, n_hot, q.z, w, pol);
-        push_one(F, hot, n_hot, q.w, w, pol);
+        push_one(F, hot, n_hot, n, q.x, w, pol);
+        push_one(F, hot, n_hot, n, q.y, w, pol);
+        push_one(F, hot, n_hot, n, q.z, w, pol);
+        push_one(F, hot, n_hot, n, q.w, w, pol);
     }
     const int t = head + 4 * body + lane;
-    if (t < deg) push_one(F, hot, n_hot, __ldg(col_idx + beg + t), w, pol);
+    if (t < deg) push_one(F, hot, n_hot, n, __ldg(col_idx + beg + t), w, pol);
 }
 
 // The list offsets of one row of a sweep's lists, in the two levels the scan writes into pre:
@@ -176,6 +181,11 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
     __shared__ __align__(8) unsigned long long s_hbar[kWarps];
     extern __shared__ int s_cta[];  // kCountRows-1 rows of G+1: the CTA-level list offsets
     if (st->done || st->pull) return;
+#ifdef DI_DEBUG
+    const int n = st->n;
+#else
+    const int n = 0;
+#endif
     constexpr int R = kCountRows - 1;
     for (int t = threadIdx.x; t < kHotSlots; t += kScanThreads) hot[t] = (FT)0;
     for (int i = threadIdx.x; i < R * G; i += kScanThreads) {
@@ -265,10 +275,10 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
                 phase ^= 1u;
                 if (lane == 0) edges += cl;
                 if (cl > kHubChunk) {
-                    push_row_lanes(col_idx, F, hot, n_hot, cb, cl, cw, lane, 32, pol);
+                    push_row_lanes(col_idx, F, hot, n_hot, n, cb, cl, cw, lane, 32, pol);
                 } else {
                     const int *cols = stage + (cb & 3);
-                    for (int j = lane; j < cl; j += 32) push_one(F, hot, n_hot, cols[j], cw, pol);
+                    for (int j = lane; j < cl; j += 32) push_one(F, hot, n_hot, n, cols[j], cw, pol);
                 }
                 __syncwarp();  // every lane is done with the stage
                 c = nx;
@@ -308,12 +318,17 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
             FT mw = (FT)0;
             if (t < tot) {
                 const int mg = p2.find((int)t);
-                const Sel<FT> e = sel[__ldg(r2 + mg) + ((int)t - p2.at(mg))];
-                const RowRec<FT> rr = rec[e.node];
-                mb = rr.beg;
-                md = rr.deg;
-                mw = e.sent * rr.inv;
-                edges += md;
+                const int pos = __ldg(r2 + mg) + ((int)t - p2.at(mg));
+                if (DI_CHECK(pos < __ldg(r2 + mg + 1), 2, pos)) {
+                    const Sel<FT> e = sel[pos];
+                    if (DI_CHECK(e.node >= 0 && e.node < n, 3, e.node)) {
+                        const RowRec<FT> rr = rec[e.node];
+                        mb = rr.beg;
+                        md = rr.deg;
+                        mw = e.sent * rr.inv;
+                        edges += md;
+                    }
+                }
             }
             const int m = (int)min(32LL, (tot - gw - k0 * nwarps + nwarps - 1) / nwarps);
             // two nodes at a time, one per half-warp: a node's column loads and reductions are
@@ -323,7 +338,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
                 const int src = (j + half) & 31;
                 const int rb = __shfl_sync(kFull, mb, src), rd = __shfl_sync(kFull, md, src);
                 const FT rw = __shfl_sync(kFull, mw, src);
-                push_row_lanes(col_idx, F, hot, n_hot, rb, j + half < m ? rd : 0, rw, lane & 15, 16, pol);
+                push_row_lanes(col_idx, F, hot, n_hot, n, rb, j + half < m ? rd : 0, rw, lane & 15, 16, pol);
             }
         }
     }
@@ -353,6 +368,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
                 if (t < t_end) {
                     mg = p1.find_from(t, mg);
                     pos[u] = __ldg(r1 + mg) + (t - p1.at(mg));
+                    if (!DI_CHECK(pos[u] < __ldg(r1 + mg + 1), 2, pos[u])) pos[u] = -1;
                 }
             }
             // every lane's last rank is below the next group's first: restart from the largest
@@ -367,6 +383,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
                     const Sel<FT> e = sel[pos[u]];
                     node[u] = e.node;
                     sent[u] = e.sent;
+                    if (!DI_CHECK(e.node >= 0 && e.node < n, 3, e.node)) pos[u] = -1;
                 }
             }
             int rb[kInFlight], rd[kInFlight];
@@ -395,7 +412,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
             for (int k = 0; k < 4; ++k)
 #pragma unroll
                 for (int u = 0; u < kInFlight; ++u)
-                    if (k < rd[u]) push_one(F, hot, n_hot, cc[u][k], rw[u], pol);
+                    if (k < rd[u]) push_one(F, hot, n_hot, n, cc[u][k], rw[u], pol);
             if (__any_sync(kFull, rd[0] > 4 || rd[1] > 4 || rd[2] > 4 || rd[3] > 4)) {
 #pragma unroll
                 for (int u = 0; u < kInFlight; ++u)
@@ -405,7 +422,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_sweep_push(const RowRec<FT>
                 for (int k = 0; k < 4; ++k)
 #pragma unroll
                     for (int u = 0; u < kInFlight; ++u)
-                        if (k + 4 < rd[u]) push_one(F, hot, n_hot, cc[u][k], rw[u], pol);
+                        if (k + 4 < rd[u]) push_one(F, hot, n_hot, n, cc[u][k], rw[u], pol);
             }
         }
     }
@@ -442,6 +459,13 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_sweep_pull(const int *__res
                                                              const FT *__restrict__ w, long long nnz,
                                                              FT *__restrict__ F, const SolveState *__restrict__ st) {
     if (st->done || !st->pull) return;
+#ifdef DI_DEBUG
+    const int n = st->n;
+    // a link whose endpoints are outside [0, n) is dropped (src = dst = -1, as past the range)
+    auto check_link = [&](int &s, int &d, long long e) {
+        if (s >= 0 && !DI_CHECK(s < n && d >= 0 && d < n, 5, e)) s = d = -1;
+    };
+#endif
     constexpr bool kTree = sizeof(FT) == 4;
     constexpr int kU = 4;  // shuffle tree: steps of 32 links loaded before they are summed
     constexpr int kStepLinks = kTree ? 32 * kU : 32 * kPullRun;
@@ -461,6 +485,9 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_sweep_pull(const int *__res
                 const bool in = e < e_end;
                 dst[u] = in ? __ldg(in_dst + e) : -1;
                 src[u] = in ? __ldg(in_src + e) : -1;
+#ifdef DI_DEBUG
+                check_link(src[u], dst[u], e);
+#endif
             }
             FT v[kU];
 #pragma unroll
@@ -499,6 +526,10 @@ __global__ void __launch_bounds__(kScanThreads, 3) k_sweep_pull(const int *__res
                     dst[k] = in ? __ldg(in_dst + eb + k) : -1;
                 }
             }
+#ifdef DI_DEBUG
+#pragma unroll
+            for (int k = 0; k < kPullRun; ++k) check_link(src[k], dst[k], eb + k);
+#endif
             FT v[kPullRun];
 #pragma unroll
             for (int k = 0; k < kPullRun; ++k) v[k] = src[k] >= 0 ? __ldg(w + src[k]) : (FT)0;
@@ -546,6 +577,10 @@ void launch_pull(di_graph *g, FT *F, cudaStream_t s) {
     k_sweep_pull<FT><<<g->num_sms * 3, kScanThreads, 0, s>>>(g->in_src, g->in_dst, static_cast<const FT *>(g->wpull),
                                                              g->nnz, F, g->st);
 }
+
+#ifdef DI_DEBUG
+unsigned long long dbg_take_push() { return dbg_take_word(); }
+#endif
 
 template void launch_pull<double>(di_graph *, double *, cudaStream_t);
 template void launch_pull<float>(di_graph *, float *, cudaStream_t);

@@ -43,6 +43,7 @@
 #include <limits>
 #include <vector>
 
+#include "dbg.cuh"
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -110,6 +111,7 @@ __device__ void init_control(SolveState *st, double R0, double tolR, double beta
     st->trace_on = trace_on;
     st->body_runs = 0;
     st->undrained = 0;
+    st->n = n;
     // the while-test of ALGO-REF comes first: nothing to do if R/(1-d) <= target already
     st->done = (R0 <= tolR) ? 1 : 0;
 }
@@ -434,7 +436,8 @@ __global__ void __launch_bounds__(kScanThreads) k_sweep_scan(int wchunk, FT *__r
                         e.node = (int)node;
                         e.pad = L == 3 ? cb - 2 : 0;  // a hub row's chunk count
                         e.sent = v;
-                        sel[run[L] + __popc(bits & lt)] = e;
+                        const int p = run[L] + __popc(bits & lt);
+                        if (DI_CHECK(p < region[L * (W + 1) + g + 1], 1, p)) sel[p] = e;
                         if (L == 3) hub_chunks += cb - 2;
                     }
                     run[L] += __popc(bits);
@@ -901,6 +904,9 @@ di_status solve_impl(di_graph *g, const di_solve_opts &o, FT *F, int slot, InitK
         // + 2 per confirmation
         stats->kernel_launches = (init == kInitV ? 2 : 3) + (pulls ? 4LL : 3LL) * h.body_runs + 2LL * attempts;
     }
+#ifdef DI_DEBUG
+    if (di_status dr = debug_status(); dr != DI_OK) return dr;
+#endif
     if (h.done == 3) return set_error(DI_EKERNEL, "residual became non-finite");
     if (h.done == 4 && h.undrained) {
         g->untrusted = true;  // sticky: every later call on this graph fails until di_free
@@ -1117,6 +1123,41 @@ __global__ void k_inject_long(InjectArgs a) {
 }
 
 }  // namespace
+
+#ifdef DI_DEBUG
+namespace {
+// records one failed check (code 99, index 12345) without touching memory
+__global__ void k_dbg_selftest() {
+    if (threadIdx.x == 0) (void)DI_CHECK(false, 99, 12345);
+}
+}  // namespace
+
+unsigned long long dbg_take_sweep() { return dbg_take_word(); }
+
+// the first failed index check of the sweep kernels (scan, push, pull) since the last call
+di_status debug_status(unsigned long long *word) {
+    unsigned long long w = dbg_take_sweep();
+    const unsigned long long wp = dbg_take_push();
+    if (!w) w = wp;
+    if (word) *word = w;
+    if (!w) return DI_OK;
+    static const char *what[] = {"", "a scan list append beyond its warp's region",
+                                 "a push list position beyond its sub-chunk's region", "a listed node id outside [0, n)",
+                                 "a pushed-to column outside [0, n)", "a pull link endpoint outside [0, n)"};
+    const unsigned code = (unsigned)(w >> 48);
+    const long long idx = (long long)(w & 0xffffffffffffull);
+    const char *msg = code < 6 ? what[code] : (code == 99 ? "the debug self-test" : "unknown check");
+    return set_error(DI_EKERNEL, std::string("debug check ") + std::to_string(code) + " failed (" + msg +
+                                     ") at index " + std::to_string(idx));
+}
+
+di_status debug_selftest(unsigned long long *word) {
+    k_dbg_selftest<<<1, 32>>>();
+    DI_CUDA(cudaGetLastError());
+    DI_CUDA(cudaDeviceSynchronize());
+    return debug_status(word);
+}
+#endif
 
 di_status selftest_wait(int polls, int ctas, int *gave_up) {
     int *d = nullptr;

@@ -58,3 +58,25 @@ def test_host_side_argument_checks_need_no_gpu(lib):
     assert lib.di_graph_create(1, rp, None, 0, 0.0, None, None, ctypes.byref(out)) == 1
     assert lib.di_graph_create(1, None, None, 0, 0.5, None, None, ctypes.byref(out)) == 1
     assert out.value is None
+
+
+@pytest.fixture(scope="module")
+def dlib():
+    from paper_1202_6158_gb300 import build
+    return ctypes.CDLL(build.build(debug=True))
+
+
+def test_debug_build_exports_the_same_boundary(dlib):
+    """libditer_debug.so (DI_DEBUG: device-side index checks) has every entry point too."""
+    for name in declared("diter.h"):
+        assert hasattr(dlib, name), name
+
+
+def test_debug_flag_tells_the_builds_apart(lib, dlib):
+    lib.di_debug_build.restype = ctypes.c_int32
+    dlib.di_debug_build.restype = ctypes.c_int32
+    assert lib.di_debug_build() == 0 and dlib.di_debug_build() == 1
+    # the release build refuses the self-test on the host, before any CUDA call
+    w = ctypes.c_uint64(7)
+    lib.di_debug_selftest.restype = ctypes.c_int
+    assert lib.di_debug_selftest(ctypes.byref(w)) == 1 and w.value == 0
