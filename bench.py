@@ -138,10 +138,10 @@ class ClockSampler:
 
 
 def push_sources_digest():
-    """sha256 over the sources the push kernel is compiled from (push.cu and its two headers)."""
+    """sha256 over the sources the push kernel is compiled from (push.cu and its headers)."""
     import hashlib
     h = hashlib.sha256()
-    for name in ("push.cu", "device_common.cuh", "internal.h"):
+    for name in ("push.cu", "device_common.cuh", "internal.h", "dbg.cuh"):
         with open(os.path.join(ROOT, "paper_1202_6158_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
