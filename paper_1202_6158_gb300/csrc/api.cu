@@ -87,7 +87,7 @@ static void free_graph(di_graph *g) {
     pool_free(g->bp, g->stream);
     void *bufs[] = {g->row_ptr, g->col_idx, g->in_ptr, g->in_src, g->in_dst, g->wpull, g->bin_of, g->V,
                     g->inv_deg, g->inv_deg32, g->hot_ids, g->perm, g->new_of, g->rec64, g->rec32,
-                    g->wsel[0], g->wsel[1], g->rowhash, g->region, g->fcount, g->pre, g->ticket, g->sel, g->cls, g->F64, g->F32, g->H, g->part, g->st,
+                    g->wsel[0], g->wsel[1], g->rowhash, g->region, g->fcount, g->pre, g->sel, g->cls, g->F64, g->F32, g->H, g->part, g->st,
                     g->trace, g->X, g->Z[0], g->Z[1], g->Y, g->ppart, g->pst};
     for (void *b : bufs)
         if (b) cudaFreeAsync(b, g->stream);

@@ -116,11 +116,12 @@ __device__ __forceinline__ unsigned ld_stream(const unsigned *a, unsigned long l
     return v;
 }
 
-// The last scan CTA to finish (a ticket counter, no waiting) turns the per-sub-chunk
+// The last batched-scan CTA to finish (a ticket counter, no waiting) turns the per-sub-chunk
 // counts into exclusive prefix sums per list, so the push can spread the selected
 // nodes evenly over all its warps whatever their distribution over the chunks.
 // Each thread sums a contiguous run of sub-chunks for every list, one block scan
-// covers the four lists, then each thread writes its run.
+// covers the four lists, then each thread writes its run.  (prefix_counts below uses the
+// CTA-parallel pass when its staging buffer holds the CTA sums.)
 // s_c: kCap ints of shared memory to stage the counts in
 // rows first_list..kCountRows-1: the lists, then the hub chunk counts (the others are left as they are)
 __device__ void prefix_counts_staged(const int *__restrict__ fcount, int W, int *__restrict__ pre, int *s_c,
@@ -166,10 +167,73 @@ __device__ void prefix_counts_staged(const int *__restrict__ fcount, int W, int 
     }
 }
 
+// The same prefix sums with the work spread over the CTA (W = G * kWarps, the counts of one
+// scan CTA's eight warps adjacent): thread t takes the scan CTAs t, t + 256, ...; two 16-byte
+// loads per CTA and row give its eight counts, whose sum goes to s_tot; one warp per row scans
+// the CTA sums in place; the same thread then writes the CTA's eight offsets.  s_tot holds
+// (kCountRows - first_list) * G ints.
+__device__ void prefix_counts_by_cta(const int *__restrict__ fcount, int G, int W, int *__restrict__ pre, int *s_tot,
+                                     int first_list) {
+    __shared__ int s_rowtot[kCountRows];
+    const int R = kCountRows - first_list;
+    for (int b = threadIdx.x; b < G; b += kScanThreads) {
+        for (int r = 0; r < R; ++r) {
+            const int4 *p = reinterpret_cast<const int4 *>(fcount + (first_list + r) * W + b * kWarps);
+            const int4 x = __ldcg(p), y = __ldcg(p + 1);
+            s_tot[r * G + b] = x.x + x.y + x.z + x.w + y.x + y.y + y.z + y.w;
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w < R) {  // warp w: exclusive scan of row w's CTA sums, in place
+        int *t = s_tot + w * G;
+        const int per = (G + 31) / 32, b0 = min(G, lane * per), b1 = min(G, b0 + per);
+        int a = 0;
+        for (int b = b0; b < b1; ++b) a += t[b];
+        int x = a;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_rowtot[w] = x;
+        int run = x - a;
+        for (int b = b0; b < b1; ++b) {
+            const int c = t[b];
+            t[b] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < G; b += kScanThreads) {
+        for (int r = 0; r < R; ++r) {
+            const int L = first_list + r;
+            const int4 *p = reinterpret_cast<const int4 *>(fcount + L * W + b * kWarps);
+            const int4 x = __ldcg(p), y = __ldcg(p + 1);
+            const int c[kWarps] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+            int *o = pre + L * (W + 1) + b * kWarps;
+            int run = s_tot[r * G + b];
+#pragma unroll
+            for (int k = 0; k < kWarps; ++k) {
+                o[k] = run;
+                run += c[k];
+            }
+        }
+    }
+    if ((int)threadIdx.x < R) pre[(first_list + threadIdx.x) * (W + 1) + W] = s_rowtot[threadIdx.x];
+    __syncthreads();
+}
+static_assert(kWarps == 8, "a CTA's counts of a row are read as two int4");
+
+// called by the last CTA of a scan grid of G = W / kWarps CTAs
 __device__ void prefix_counts(const int *__restrict__ fcount, int W, int *__restrict__ pre, int first_list = 0) {
     constexpr int kCap = 8192;                     // sub-chunks staged per pass (32 KB)
     __shared__ int s_c[kCap];
-    prefix_counts_staged(fcount, W, pre, s_c, kCap, first_list);
+    const int G = W / kWarps;
+    if ((kCountRows - first_list) * G <= kCap && (int)gridDim.x == G)
+        prefix_counts_by_cta(fcount, G, W, pre, s_c, first_list);
+    else
+        prefix_counts_staged(fcount, W, pre, s_c, kCap, first_list);
 }
 
 // sub-chunk holding item t of a list: the last g with pre[g] <= t

@@ -897,8 +897,6 @@ di_status build_graph(di_graph *g, const int *col_host) {
         DI_CUDA(cudaMemsetAsync(g->fcount, 0, sizeof(int) * kCountRows * (size_t)W, s));
         DI_CUDA(cudaMallocAsync(&g->pre, sizeof(int) * kCountRows * (size_t)(W + 1), s));
         DI_CUDA(cudaMemsetAsync(g->pre, 0, sizeof(int) * kCountRows * (size_t)(W + 1), s));
-        DI_CUDA(cudaMallocAsync(&g->ticket, sizeof(unsigned), s));
-        DI_CUDA(cudaMemsetAsync(g->ticket, 0, sizeof(unsigned), s));
     }
     {
         di_status r = set_out_classes(g, kOutCut1, kOutCut2);

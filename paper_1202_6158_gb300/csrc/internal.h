@@ -265,7 +265,6 @@ struct di_graph {
     int *pre = nullptr;                // kCountRows*(W+1) ints: the two-level list offsets the scan writes,
                                        // [(L-1)G + b] the total of row L in scan CTA b, [L W + g] sub-chunk
                                        // g's offset within its CTA's part (L = 1 .. kCountRows-1)
-    unsigned *ticket = nullptr;        // finished scan CTAs of the current sweep
     void *sel = nullptr;               // Sel<FT>[n]: the selected nodes of a sweep
     double *F64 = nullptr;
     float *F32 = nullptr;
