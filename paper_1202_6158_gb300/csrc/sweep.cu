@@ -1355,35 +1355,37 @@ di_status set_state(di_graph *g, const double *F_in, bool F_dev, const double *H
         cudaStreamSynchronize(s);
     };
     const size_t bytes = sizeof(double) * (size_t)n;
-    for (int k = 0; k < 5; ++k) {
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 5 && e == cudaSuccess; ++k) {
         if ((k == 0 && F_dev) || (k == 1 && H_dev)) continue;
-        if (cudaMallocAsync(&bufs[k], k >= 2 ? sizeof(double) * (size_t)npad : bytes, s) != cudaSuccess) {
-            release();
-            return cuda_fail(cudaGetLastError(), "cudaMallocAsync(state)");
-        }
+        e = cudaMallocAsync(&bufs[k], k >= 2 ? sizeof(double) * (size_t)npad : bytes, s);
     }
-    DI_CUDA(cudaMallocAsync(&bad, sizeof(int), s));
-    DI_CUDA(cudaMallocAsync(&mx, 2 * sizeof(unsigned long long), s));
-    DI_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
-    DI_CUDA(cudaMemsetAsync(mx, 0, 2 * sizeof(unsigned long long), s));
+    if (e == cudaSuccess) e = cudaMallocAsync(&bad, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&mx, 2 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(mx, 0, 2 * sizeof(unsigned long long), s);
     const double *Fs = F_in, *Hs = H_in;
-    if (!F_dev) {
-        DI_CUDA(cudaMemcpyAsync(bufs[0], F_in, bytes, cudaMemcpyHostToDevice, s));
+    if (e == cudaSuccess && !F_dev) {
+        e = cudaMemcpyAsync(bufs[0], F_in, bytes, cudaMemcpyHostToDevice, s);
         Fs = bufs[0];
     }
-    if (!H_dev) {
-        DI_CUDA(cudaMemcpyAsync(bufs[1], H_in, bytes, cudaMemcpyHostToDevice, s));
+    if (e == cudaSuccess && !H_dev) {
+        e = cudaMemcpyAsync(bufs[1], H_in, bytes, cudaMemcpyHostToDevice, s);
         Hs = bufs[1];
     }
     double *F = bufs[2], *H = bufs[3], *Z = bufs[4];
-    DI_CUDA(cudaMemsetAsync(F, 0, sizeof(double) * (size_t)npad, s));
-    DI_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * (size_t)npad, s));
+    if (e == cudaSuccess) e = cudaMemsetAsync(F, 0, sizeof(double) * (size_t)npad, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(H, 0, sizeof(double) * (size_t)npad, s);
+    if (e != cudaSuccess) {
+        release();
+        return cuda_fail(e, "state upload");
+    }
     const int grid = elem_grid(g, n);
     k_state_in<<<grid, 256, 0, s>>>(n, g->perm, Fs, Hs, F, H, bad);
     k_state_z<<<grid, 256, 0, s>>>(n, 1.0 - g->d, g->V, F, H, Z);
     k_state_dph<<<g->num_sms * 8, 256, 0, s>>>(n, g->rec64, g->col_idx, H, Z);
     k_state_max<<<grid, 256, 0, s>>>(n, 1.0 - g->d, g->V, F, H, Z, mx);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     int hbad = 0;
     unsigned long long hm[2] = {0ull, 0ull};
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -1408,11 +1410,12 @@ di_status set_state(di_graph *g, const double *F_in, bool F_dev, const double *H
                                     "deviation " + std::to_string(dev) + " > rtol " + std::to_string(rtol));
     }
     // accepted: the graph's FP64 state becomes (F, H), as if its last solve had stopped there
-    DI_CUDA(cudaMemcpyAsync(g->F64, F, sizeof(double) * (size_t)npad, cudaMemcpyDeviceToDevice, s));
-    DI_CUDA(cudaMemcpyAsync(g->H, H, sizeof(double) * (size_t)npad, cudaMemcpyDeviceToDevice, s));
+    e = cudaMemcpyAsync(g->F64, F, sizeof(double) * (size_t)npad, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->H, H, sizeof(double) * (size_t)npad, cudaMemcpyDeviceToDevice, s);
+    release();
+    if (e != cudaSuccess) return cuda_fail(e, "state load");
     g->last_prec = DI_FP64;
     g->last_trace_on = 0;
-    release();
     return DI_OK;
 }
 
