@@ -25,7 +25,7 @@
 typedef int32_t i32;
 typedef int64_t i64;
 
-/* threads actually used by a parallel region of this build (1 without OpenMP) */
+/* threads actually used by a parallel region (1 when compiled without OpenMP) */
 int pomp_threads(int want) {
 #ifdef _OPENMP
     if (want > 0) omp_set_num_threads(want);
