@@ -97,7 +97,16 @@ __global__ void k_validate_v(int n, const double *__restrict__ V, int *flags, do
 
 // out-degree class and d/outdeg of every node (the one division per node the solves need),
 // and the packed row record {start, outdeg, d/outdeg} the push reads with one access
-__global__ void k_out_bins(int n, const int *__restrict__ row_ptr, int cut1, int cut2, double d, int *__restrict__ bin_of,
+// d/k for k < kInvTable (0 for k = 0): FP64 division is scarce on this GPU (about 59 G/s), and a
+// graph's out-degrees repeat, so each distinct small degree is divided once
+constexpr int kInvTable = 1 << 16;
+__global__ void k_inv_table(double d, double *__restrict__ tab) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < kInvTable; k += gridDim.x * blockDim.x)
+        tab[k] = k ? d / (double)k : 0.0;
+}
+
+__global__ void k_out_bins(int n, const int *__restrict__ row_ptr, int cut1, int cut2, double d,
+                           const double *__restrict__ inv_tab, int *__restrict__ bin_of,
                            unsigned char *__restrict__ cls, double *__restrict__ inv_deg, float *__restrict__ inv_deg32,
                            RowRec<double> *__restrict__ rec64, RowRec<float> *__restrict__ rec32) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -106,7 +115,8 @@ __global__ void k_out_bins(int n, const int *__restrict__ row_ptr, int cut1, int
         int b = deg == 0 ? 0 : (deg <= cut1 ? 1 : (deg <= cut2 ? 2 : 3));
         bin_of[i] = b;
         cls[i] = (unsigned char)(b < 3 ? b : 2 + hub_chunk_count(deg));
-        double w = deg ? d / (double)deg : 0.0;
+        // the same correctly rounded d/deg either way
+        const double w = deg < kInvTable ? __ldg(inv_tab + deg) : d / (double)deg;
         inv_deg[i] = w;
         inv_deg32[i] = (float)w;
         RowRec<double> r64;
@@ -917,8 +927,12 @@ di_status set_out_classes(di_graph *g, int cut1, int cut2) {
     const int n = g->n;
     g->cut1 = cut1;
     g->cut2 = cut2;
-    k_out_bins<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, g->row_ptr, cut1, cut2, g->d, g->bin_of, g->cls,
+    double *tab = nullptr;
+    DI_CUDA(cudaMallocAsync(&tab, sizeof(double) * kInvTable, s));
+    k_inv_table<<<kInvTable / 256, 256, 0, s>>>(g->d, tab);
+    k_out_bins<<<grid_for(n, 256, g->num_sms), 256, 0, s>>>(n, g->row_ptr, cut1, cut2, g->d, tab, g->bin_of, g->cls,
                                                            g->inv_deg, g->inv_deg32, g->rec64, g->rec32);
+    cudaFreeAsync(tab, s);
     const int W = g->W;
     int *cnt = nullptr;
     DI_CUDA(cudaMallocAsync(&cnt, sizeof(int) * (kLists * (size_t)W + 1), s));
