@@ -529,13 +529,14 @@ __global__ void k_sweep_finalize(int n, int G, const ScanPartial *__restrict__ p
                                  di_sweep_record *__restrict__ trace, cudaGraphConditionalHandle handle,
                                  int in_graph) {
     __shared__ long long s_l[7][kScanThreads / 32];
-    if (st->done) {  // converged before this body ran: leave the loop
-        if (threadIdx.x == 0) {
-            st->body_runs += 1;
-            if (in_graph) cudaGraphSetConditional(handle, 0);
-        }
-        return;
-    }
+    // the control block, copied by the first threads while all of them read the partials, so
+    // that thread 0's bookkeeping below reads shared memory; written back once at the end
+    __shared__ SolveState s_st;
+    constexpr int kStWords = (int)(sizeof(SolveState) / sizeof(unsigned long long));
+    static_assert(sizeof(SolveState) % sizeof(unsigned long long) == 0, "copied in 8-byte words");
+    if ((int)threadIdx.x < kStWords)
+        reinterpret_cast<unsigned long long *>(&s_st)[threadIdx.x] =
+            reinterpret_cast<const unsigned long long *>(st)[threadIdx.x];
     // the six sums of the per-CTA partials and the OR of their error bits, reduced together:
     // warp trees, then thread 0 over the warps (integers, so exact in any order)
     long long v[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -562,6 +563,12 @@ __global__ void k_sweep_finalize(int n, int G, const ScanPartial *__restrict__ p
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
+    SolveState &L = s_st;
+    if (L.done) {  // converged before this body ran: leave the loop
+        st->body_runs = L.body_runs + 1;
+        if (in_graph) cudaGraphSetConditional(handle, 0);
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
         long long a = 0;
@@ -569,26 +576,26 @@ __global__ void k_sweep_finalize(int n, int G, const ScanPartial *__restrict__ p
         v[k] = a;
     }
     const long long fl1 = v[0], fout = v[1], fdng = v[2], ed = v[3], sr = v[4], en = v[5], er = v[6];
-    st->body_runs += 1;
-    const double Tused = st->T;
-    const int S = fixed_scale(st->R);  // the scale the scan used (st->R is still the previous residual)
+    L.body_runs += 1;
+    const double Tused = L.T;
+    const int S = fixed_scale(L.R);  // the scale the scan used (L.R is still the previous residual)
     // every kExactEvery sweeps the scan summed all of F; in between |F|_1 is the previous
     // residual (the removed masses are exact, only the pushes' roundings separate them)
-    const bool exact = (st->sweeps % kExactEvery) == 0;
-    const double l1 = exact ? ldexp((double)fl1, -S) : st->R;
+    const bool exact = (L.sweeps % kExactEvery) == 0;
+    const double l1 = exact ? ldexp((double)fl1, -S) : L.R;
     // removed mass: (1-d)*sent for nodes with children, sent for dangling nodes (Section 3.3)
-    const double rem = st->one_minus_d * ldexp((double)fout, -S) + ldexp((double)fdng, -S);
+    const double rem = L.one_minus_d * ldexp((double)fout, -S) + ldexp((double)fdng, -S);
     const double R = l1 - rem;  // |F|_1 after the sweep (exact arithmetic)
-    const int pulled = st->pull;
-    st->sweeps += 1;
-    st->edges += ed;
-    st->srcs += sr;
+    const int pulled = L.pull;
+    L.sweeps += 1;
+    L.edges += ed;
+    L.srcs += sr;
     // the next sweep pulls after two dense sweeps in a row: one dense sweep (the first sweep from
     // a uniform F_0 selects every node) is often followed by sparse ones
-    const int dense = ed >= st->pull_edges ? 1 : 0;
-    st->pull = dense && st->dense ? 1 : 0;
-    st->dense = dense;
-    if (st->trace_on && st->sweeps <= kTraceCap) {
+    const int dense = ed >= L.pull_edges ? 1 : 0;
+    L.pull = dense && L.dense ? 1 : 0;
+    L.dense = dense;
+    if (L.trace_on && L.sweeps <= kTraceCap) {
         di_sweep_record r;
         r.l1_F = l1;
         r.removed = rem;
@@ -601,23 +608,25 @@ __global__ void k_sweep_finalize(int n, int G, const ScanPartial *__restrict__ p
         r.push_ms = 0.0;
         r.pull = pulled;
         r.pad = 0;
-        trace[st->sweeps - 1] = r;
+        trace[L.sweeps - 1] = r;
     }
-    st->R = R;
+    L.R = R;
     // T = beta R/n, halved after an empty sweep; with weights (ALGO-OP) it is never raised
-    double Tn = (sr == 0) ? 0.5 * Tused : st->beta * R / (double)n;
-    if (sr != 0 && st->weighted) Tn = fmin(Tused, Tn);
+    double Tn = (sr == 0) ? 0.5 * Tused : L.beta * R / (double)n;
+    if (sr != 0 && L.weighted) Tn = fmin(Tused, Tn);
     if (!(Tn > 0.0)) Tn = 0.0;
-    st->T = Tn;
+    L.T = Tn;
     int done = 0;
     if (er) {
         done = 4;
-        if (er & 2) st->undrained = 1;
+        if (er & 2) L.undrained = 1;
     } else if (!isfinite(R)) done = 3;
-    else if (R <= st->tolR) done = 1;
-    else if (st->sweeps >= st->max_sweeps || (st->max_edges > 0 && st->edges >= st->max_edges)) done = 2;
-    else if (st->pull && st->pause_pull) done = 5;  // a pull is due but the in-link CSR is not built: ask the host
-    st->done = done;
+    else if (R <= L.tolR) done = 1;
+    else if (L.sweeps >= L.max_sweeps || (L.max_edges > 0 && L.edges >= L.max_edges)) done = 2;
+    else if (L.pull && L.pause_pull) done = 5;  // a pull is due but the in-link CSR is not built: ask the host
+    L.done = done;
+    for (int w = 0; w < kStWords; ++w)
+        reinterpret_cast<unsigned long long *>(st)[w] = reinterpret_cast<const unsigned long long *>(&L)[w];
     if (done && in_graph) cudaGraphSetConditional(handle, 0);
 }
 
